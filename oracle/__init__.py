@@ -1,0 +1,345 @@
+"""Plain FP64 CPU oracle for the adaptive-resolution WCSPH method of
+Muta & Ramachandran (arXiv 2107.01276).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference legs may import this package.  It
+shares no code with the CUDA library (``paper_2107_01276_gb300``) and never
+imports it; the CUDA library never imports this.
+
+The arithmetic lives in ``sph_oracle.c`` (plain C, FP64, FMA contraction
+off).  This module only compiles it with gcc, loads it with ctypes and
+marshals numpy arrays.  Functions whose parity is not pinned by a test
+against the paper or mathematics say so in their docstring.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libsph_oracle.so")
+_SRC = [os.path.join(_HERE, "sph_oracle.c")]
+_HDR = os.path.join(_HERE, "sph_oracle.h")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (no GPU involved)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in _SRC + [_HDR])
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    tmp = _SO + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-fPIC", "-shared", "-o", tmp] + _SRC + ["-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2),
+        ("periodic", ctypes.c_int * 2),
+        ("rho0", ctypes.c_double), ("cs", ctypes.c_double),
+        ("nu", ctypes.c_double), ("U_ref", ctypes.c_double),
+        ("hdx", ctypes.c_double), ("alpha_e", ctypes.c_double),
+        ("split_alpha", ctypes.c_double), ("split_eps", ctypes.c_double),
+        ("pavg_mode", ctypes.c_int), ("edac_diff_denominator", ctypes.c_int),
+        ("edac_rho_factor", ctypes.c_int), ("merge_iters", ctypes.c_int),
+        ("shift_iters", ctypes.c_int),
+    ]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("cap", ctypes.c_int)] + [
+        (k, ctypes.POINTER(ctypes.c_double))
+        for k in ("x", "y", "u", "v", "p", "rho", "m", "h", "mmin", "mmax")
+    ] + [("id", ctypes.POINTER(ctypes.c_longlong))]
+
+
+_RHS_D = ("rho", "beta", "pavg", "drx", "dry", "dpdt", "dudt", "dvdt")
+_RHS_S = tuple("s_" + k for k in ("rho", "beta", "pavg", "drx", "dry",
+                                  "dpdt", "dudt", "dvdt"))
+
+
+class _RhsOut(ctypes.Structure):
+    _fields_ = [(k, ctypes.POINTER(ctypes.c_double)) for k in _RHS_D] + [
+        ("nnb", ctypes.POINTER(ctypes.c_int))] + [
+        (k, ctypes.POINTER(ctypes.c_double)) for k in _RHS_S]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_U64 = ctypes.POINTER(ctypes.c_uint64)
+_P = ctypes.POINTER(Params)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            L.orc_W.restype = ctypes.c_double
+            L.orc_W.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.orc_dWdr.restype = ctypes.c_double
+            L.orc_dWdr.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.orc_is_neighbor.restype = ctypes.c_int
+            L.orc_is_neighbor.argtypes = [_P] + [ctypes.c_double] * 6
+            for f in (L.orc_neighbors_brute, L.orc_neighbors_grid):
+                f.restype = ctypes.c_longlong
+                f.argtypes = [_P, ctypes.c_int, _D, _D, _D, _I, _I,
+                              ctypes.c_longlong]
+            L.orc_neighbors_cross.restype = ctypes.c_longlong
+            L.orc_neighbors_cross.argtypes = [_P, ctypes.c_int, _D, _D, _D,
+                                              ctypes.c_int, _D, _D, _D, _I,
+                                              _I, ctypes.c_longlong]
+            L.orc_max_level.restype = ctypes.c_int
+            L.orc_max_level.argtypes = [_P, ctypes.c_double]
+            L.orc_cell_keys.restype = None
+            L.orc_cell_keys.argtypes = [_P, ctypes.c_double, ctypes.c_int,
+                                        _D, _D, _D, _U64, _I]
+            L.orc_pass_a.restype = ctypes.c_int
+            L.orc_pass_a.argtypes = [_P, ctypes.c_int, _D, _D, _D, _D, _D,
+                                     _I, _I, ctypes.POINTER(_RhsOut)]
+            L.orc_pass_b.restype = None
+            L.orc_pass_b.argtypes = [_P, ctypes.c_double, ctypes.c_int, _D,
+                                     _D, _D, _D, _D, _D, _D, _I, _I,
+                                     ctypes.POINTER(_RhsOut)]
+            L.orc_dt.restype = ctypes.c_double
+            L.orc_dt.argtypes = [_P, ctypes.c_int, _D]
+            L.orc_rhs.restype = ctypes.c_int
+            L.orc_rhs.argtypes = [_P, ctypes.c_double,
+                                  ctypes.POINTER(_State),
+                                  ctypes.POINTER(_RhsOut)]
+            L.orc_step.restype = ctypes.c_int
+            L.orc_step.argtypes = [_P, ctypes.POINTER(_State), ctypes.c_int,
+                                   _D]
+            for f in (L.orc_pec_predict, L.orc_pec_correct):
+                f.restype = None
+                f.argtypes = [_P, ctypes.c_double, ctypes.c_int] + [_D] * 15
+            L.orc_num_threads.restype = ctypes.c_int
+            L.orc_num_threads.argtypes = []
+            _lib = L
+    return _lib
+
+
+PARAM_DEFAULTS = dict(
+    lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(0, 0), rho0=1.0, cs=10.0,
+    nu=0.0, U_ref=1.0, hdx=1.0, alpha_e=1.5, split_alpha=0.9, split_eps=0.4,
+    pavg_mode=0, edac_diff_denominator=1, edac_rho_factor=1, merge_iters=3,
+    shift_iters=3)
+
+
+def params(**kw) -> Params:
+    """Build the oracle parameter block; unspecified fields take the
+    paper's values (alpha_e 1.5, split alpha 0.9, epsilon 0.4, three merge
+    and shift rounds) and the default readings."""
+    d = dict(PARAM_DEFAULTS)
+    for k, v in kw.items():
+        if k in d:
+            d[k] = v
+    P = Params()
+    P.lo[:] = [float(v) for v in d["lo"]]
+    P.hi[:] = [float(v) for v in d["hi"]]
+    P.periodic[:] = [int(v) for v in d["periodic"]]
+    for k in ("rho0", "cs", "nu", "U_ref", "hdx", "alpha_e", "split_alpha",
+              "split_eps"):
+        setattr(P, k, float(d[k]))
+    for k in ("pavg_mode", "edac_diff_denominator", "edac_rho_factor",
+              "merge_iters", "shift_iters"):
+        setattr(P, k, int(d[k]))
+    return P
+
+
+def _d(a):
+    return a.ctypes.data_as(_D)
+
+
+def _i(a):
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def W(r, h):
+    """Quintic spline W(r, h) (section 2, Eq. kernel), elementwise."""
+    L = lib()
+    r, h = np.broadcast_arrays(np.asarray(r, float), np.asarray(h, float))
+    return np.array([L.orc_W(a, b) for a, b in zip(r.ravel(), h.ravel())]
+                    ).reshape(r.shape)
+
+
+def dWdr(r, h):
+    L = lib()
+    r, h = np.broadcast_arrays(np.asarray(r, float), np.asarray(h, float))
+    return np.array([L.orc_dWdr(a, b) for a, b in zip(r.ravel(), h.ravel())]
+                    ).reshape(r.shape)
+
+
+def is_neighbor(P, xi, yi, hi, xj, yj, hj) -> bool:
+    return bool(lib().orc_is_neighbor(ctypes.byref(P), xi, yi, hi, xj, yj,
+                                      hj))
+
+
+def neighbors(P, x, y, h, method: str = "grid"):
+    """CSR (off, nbr) of N(i) = {j : r_ij < 3 max(h_i, h_j)}, ascending j."""
+    x, y, h = _f64(x), _f64(y), _f64(h)
+    n = len(x)
+    f = lib().orc_neighbors_grid if method == "grid" else \
+        lib().orc_neighbors_brute
+    off = np.zeros(n + 1, np.int32)
+    cap = max(64, 48 * n)
+    while True:
+        nbr = np.zeros(cap, np.int32)
+        tot = f(ctypes.byref(P), n, _d(x), _d(y), _d(h), _i(off), _i(nbr),
+                cap)
+        if tot <= cap:
+            return off, nbr[:tot].copy()
+        cap = int(tot)
+
+
+def neighbors_cross(P, xa, ya, ha, xb, yb, hb):
+    xa, ya, ha, xb, yb, hb = map(_f64, (xa, ya, ha, xb, yb, hb))
+    na, nb = len(xa), len(xb)
+    off = np.zeros(na + 1, np.int32)
+    cap = max(64, 48 * na)
+    while True:
+        nbr = np.zeros(cap, np.int32)
+        tot = lib().orc_neighbors_cross(ctypes.byref(P), na, _d(xa), _d(ya),
+                                        _d(ha), nb, _d(xb), _d(yb), _d(hb),
+                                        _i(off), _i(nbr), cap)
+        if tot <= cap:
+            return off, nbr[:tot].copy()
+        cap = int(tot)
+
+
+def max_level(P, c0: float) -> int:
+    return int(lib().orc_max_level(ctypes.byref(P), float(c0)))
+
+
+def cell_keys(P, c0, x, y, h):
+    """Multi-level cell key and level of every particle (definition in
+    sph_oracle.c).  Returns (key uint64[n], level int32[n])."""
+    x, y, h = _f64(x), _f64(y), _f64(h)
+    n = len(x)
+    key = np.zeros(n, np.uint64)
+    lev = np.zeros(n, np.int32)
+    lib().orc_cell_keys(ctypes.byref(P), float(c0), n, _d(x), _d(y), _d(h),
+                        key.ctypes.data_as(_U64), _i(lev))
+    return key, lev
+
+
+def _rhs_out(n):
+    arrs = {k: np.zeros(max(n, 1)) for k in _RHS_D + _RHS_S}
+    arrs["nnb"] = np.zeros(max(n, 1), np.int32)
+    o = _RhsOut()
+    for k in _RHS_D + _RHS_S:
+        setattr(o, k, _d(arrs[k]))
+    o.nnb = _i(arrs["nnb"])
+    return o, arrs
+
+
+def pass_a(P, x, y, h, m, p, off, nbr):
+    x, y, h, m, p = map(_f64, (x, y, h, m, p))
+    n = len(x)
+    o, arrs = _rhs_out(n)
+    off = np.ascontiguousarray(off, np.int32)
+    nbr = np.ascontiguousarray(nbr, np.int32)
+    lib().orc_pass_a(ctypes.byref(P), n, _d(x), _d(y), _d(h), _d(m), _d(p),
+                     _i(off), _i(nbr), ctypes.byref(o))
+    return {k: v[:n] for k, v in arrs.items()}
+
+
+def pass_b(P, dt, x, y, h, m, p, u, v, off, nbr, a):
+    """Pass B with pass-A results ``a`` (rho, beta, pavg, drx, dry) given;
+    the caller may prescribe them (used by the pins)."""
+    x, y, h, m, p, u, v = map(_f64, (x, y, h, m, p, u, v))
+    n = len(x)
+    o, arrs = _rhs_out(n)
+    for k in ("rho", "beta", "pavg", "drx", "dry"):
+        arrs[k][:n] = a[k]
+    off = np.ascontiguousarray(off, np.int32)
+    nbr = np.ascontiguousarray(nbr, np.int32)
+    lib().orc_pass_b(ctypes.byref(P), float(dt), n, _d(x), _d(y), _d(h),
+                     _d(m), _d(p), _d(u), _d(v), _i(off), _i(nbr),
+                     ctypes.byref(o))
+    return {k: v[:n] for k, v in arrs.items()}
+
+
+def dt(P, h) -> float:
+    h = _f64(h)
+    return float(lib().orc_dt(ctypes.byref(P), len(h), _d(h)))
+
+
+STATE_FIELDS = ("x", "y", "u", "v", "p", "rho", "m", "h", "mmin", "mmax")
+
+
+def make_state(fields: dict, cap: int | None = None) -> dict:
+    """Copy a particle dict into capacity-sized FP64 arrays owned here."""
+    n = len(fields["x"])
+    cap = max(n, cap or n, 1)
+    st = {"n": n, "cap": cap}
+    for k in STATE_FIELDS:
+        a = np.zeros(cap)
+        if k in fields:
+            a[:n] = fields[k]
+        st[k] = a
+    ida = np.zeros(cap, np.int64)
+    ida[:n] = fields.get("id", np.arange(n))
+    st["id"] = ida
+    return st
+
+
+def _cstate(st):
+    s = _State()
+    s.n, s.cap = st["n"], st["cap"]
+    for k in STATE_FIELDS:
+        setattr(s, k, _d(st[k]))
+    s.id = st["id"].ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+    return s
+
+
+def rhs(P, dt_, st):
+    """Neighbour search + pass A + pass B at the state ``st``."""
+    n = st["n"]
+    o, arrs = _rhs_out(n)
+    s = _cstate(st)
+    lib().orc_rhs(ctypes.byref(P), float(dt_), ctypes.byref(s),
+                  ctypes.byref(o))
+    return {k: v[:n].copy() for k, v in arrs.items()}
+
+
+def step(P, st, nsteps: int, t: float = 0.0) -> float:
+    """Advance ``st`` in place by nsteps PEC steps; returns the new time."""
+    s = _cstate(st)
+    tt = ctypes.c_double(t)
+    lib().orc_step(ctypes.byref(P), ctypes.byref(s), int(nsteps),
+                   ctypes.byref(tt))
+    st["n"] = s.n
+    return tt.value
+
+
+def pec_stage(P, which, dt_, x0, y0, u0, v0, p0, dudt, dvdt, dpdt, drx,
+              dry):
+    arrs = list(map(_f64, (x0, y0, u0, v0, p0, dudt, dvdt, dpdt, drx, dry)))
+    n = len(arrs[0])
+    out = [np.zeros(n) for _ in range(5)]
+    f = lib().orc_pec_predict if which == "predict" else \
+        lib().orc_pec_correct
+    f(ctypes.byref(P), float(dt_), n, *[_d(a) for a in arrs],
+      *[_d(a) for a in out])
+    return dict(zip(("x", "y", "u", "v", "p"), out))

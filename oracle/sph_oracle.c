@@ -1,0 +1,702 @@
+/*
+ * Plain FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY (see sph_oracle.h).
+ *
+ * Muta & Ramachandran, "Efficient and Accurate Adaptive Resolution for
+ * Weakly-Compressible SPH", arXiv 2107.01276.  Section numbers and equation
+ * labels below are the paper's.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no -ffast-math).
+ * Per-particle sums run over N(i) in ascending neighbour index.  The
+ * OpenMP loops are over independent particles only, so results do not
+ * depend on the thread count.
+ */
+#include "sph_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static const double PI = 3.14159265358979323846;
+/* Point of inflection of the quintic spline in q (section 2.1, shifting). */
+static const double XI_INFLECTION = 0.759298480738450;
+static const int DIM = 2;
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------
+ * Quintic spline, section 2, Eq. (kernel):
+ *   W(q) = sigma2 [(3-q)^5 - 6(2-q)^5 + 15(1-q)^5]  for 0 <= q < 1
+ *        = sigma2 [(3-q)^5 - 6(2-q)^5]               for 1 <= q < 2
+ *        = sigma2 (3-q)^5                             for 2 <= q < 3
+ *        = 0                                          for q >= 3
+ * with sigma2 = 7 / (478 pi h^2), q = r / h.
+ * dW/dr follows by differentiating each power: d/dq (a-q)^5 = -5 (a-q)^4.
+ * ---------------------------------------------------------------------- */
+static double p5(double a) { return a * a * a * a * a; }
+static double p4(double a) { return a * a * a * a; }
+
+static double w_of_q(double q) {
+    if (q >= 3.0) return 0.0;
+    double w = p5(3.0 - q);
+    if (q < 2.0) w -= 6.0 * p5(2.0 - q);
+    if (q < 1.0) w += 15.0 * p5(1.0 - q);
+    return w;
+}
+
+static double dw_of_q(double q) {
+    if (q >= 3.0) return 0.0;
+    double w = -5.0 * p4(3.0 - q);
+    if (q < 2.0) w += 30.0 * p4(2.0 - q);
+    if (q < 1.0) w -= 75.0 * p4(1.0 - q);
+    return w;
+}
+
+static double sigma2(double h) { return 7.0 / (478.0 * PI * h * h); }
+
+double orc_W(double r, double h) { return sigma2(h) * w_of_q(r / h); }
+
+double orc_dWdr(double r, double h) {
+    return sigma2(h) / h * dw_of_q(r / h);
+}
+
+/* ------------------------------------------------------------------------
+ * Neighbour predicate.  The gather sums of section 2 run over every j whose
+ * kernel W(r_ij, h_i), W(r_ij, h_j) or W(r_ij, h_ij) is non-zero; with
+ * support 3h that is r_ij < 3 max(h_i, h_j).  i itself is included.  On a
+ * periodic axis the separation is the minimum image (section 2.2, periodic
+ * ghosts give the same sets).
+ * ---------------------------------------------------------------------- */
+static double min_image(const orc_params *P, int axis, double d) {
+    if (P->periodic[axis]) {
+        double L = P->hi[axis] - P->lo[axis];
+        double half = 0.5 * L;
+        if (d > half)
+            d -= L;
+        else if (d < -half)
+            d += L;
+    }
+    return d;
+}
+
+static void separation(const orc_params *P, double xi, double yi, double xj,
+                       double yj, double *dx, double *dy) {
+    *dx = min_image(P, 0, xi - xj);
+    *dy = min_image(P, 1, yi - yj);
+}
+
+int orc_is_neighbor(const orc_params *P, double xi, double yi, double hi,
+                    double xj, double yj, double hj) {
+    double dx, dy;
+    separation(P, xi, yi, xj, yj, &dx, &dy);
+    double r2 = dx * dx + dy * dy;
+    double R = 3.0 * (hi > hj ? hi : hj);
+    return r2 < R * R;
+}
+
+long long orc_neighbors_brute(const orc_params *P, int n, const double *x,
+                              const double *y, const double *h, int *off,
+                              int *nbr, long long cap) {
+    /* count pass */
+    int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        int c = 0;
+        for (int j = 0; j < n; ++j)
+            c += orc_is_neighbor(P, x[i], y[i], h[i], x[j], y[j], h[j]);
+        cnt[i] = c;
+    }
+    long long tot = 0;
+    for (int i = 0; i < n; ++i) {
+        off[i] = (int)tot;
+        tot += cnt[i];
+    }
+    off[n] = (int)tot;
+    free(cnt);
+    if (tot > cap) return tot;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        int k = off[i];
+        for (int j = 0; j < n; ++j)
+            if (orc_is_neighbor(P, x[i], y[i], h[i], x[j], y[j], h[j]))
+                nbr[k++] = j;
+    }
+    return tot;
+}
+
+long long orc_neighbors_cross(const orc_params *P, int na, const double *xa,
+                              const double *ya, const double *ha, int nb,
+                              const double *xb, const double *yb,
+                              const double *hb, int *off, int *nbr,
+                              long long cap) {
+    int *cnt = (int *)calloc((size_t)na + 1, sizeof(int));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int a = 0; a < na; ++a) {
+        int c = 0;
+        for (int b = 0; b < nb; ++b)
+            c += orc_is_neighbor(P, xa[a], ya[a], ha[a], xb[b], yb[b], hb[b]);
+        cnt[a] = c;
+    }
+    long long tot = 0;
+    for (int a = 0; a < na; ++a) {
+        off[a] = (int)tot;
+        tot += cnt[a];
+    }
+    off[na] = (int)tot;
+    free(cnt);
+    if (tot > cap) return tot;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int a = 0; a < na; ++a) {
+        int k = off[a];
+        for (int b = 0; b < nb; ++b)
+            if (orc_is_neighbor(P, xa[a], ya[a], ha[a], xb[b], yb[b], hb[b]))
+                nbr[k++] = b;
+    }
+    return tot;
+}
+
+/* Uniform bucket grid with bucket side >= 3 h_max, so every neighbour of i
+ * lies in the 3x3 buckets around i's bucket.  Same predicate as the brute
+ * search; the lists are sorted ascending so the two agree entry by entry. */
+static int cmp_int(const void *a, const void *b) {
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+long long orc_neighbors_grid(const orc_params *P, int n, const double *x,
+                             const double *y, const double *h, int *off,
+                             int *nbr, long long cap) {
+    if (n <= 0) {
+        off[0] = 0;
+        return 0;
+    }
+    double hmax = 0.0;
+    for (int i = 0; i < n; ++i)
+        if (h[i] > hmax) hmax = h[i];
+    double side = 3.0 * hmax;
+    int nc[2];
+    double w[2];
+    for (int a = 0; a < 2; ++a) {
+        double L = P->hi[a] - P->lo[a];
+        if (P->periodic[a]) {
+            nc[a] = (int)floor(L / side);
+            if (nc[a] < 1) nc[a] = 1;
+            w[a] = L / nc[a];
+        } else {
+            nc[a] = (int)ceil(L / side);
+            if (nc[a] < 1) nc[a] = 1;
+            w[a] = side;
+        }
+    }
+    long long ncell = (long long)nc[0] * nc[1];
+    int *head = (int *)malloc((size_t)ncell * sizeof(int));
+    int *next = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
+    int *cx = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
+    int *cy = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
+    for (long long c = 0; c < ncell; ++c) head[c] = -1;
+    for (int i = n - 1; i >= 0; --i) {
+        int ix = (int)floor((x[i] - P->lo[0]) / w[0]);
+        int iy = (int)floor((y[i] - P->lo[1]) / w[1]);
+        if (ix < 0) ix = 0;
+        if (ix > nc[0] - 1) ix = nc[0] - 1;
+        if (iy < 0) iy = 0;
+        if (iy > nc[1] - 1) iy = nc[1] - 1;
+        cx[i] = ix;
+        cy[i] = iy;
+        long long c = (long long)iy * nc[0] + ix;
+        next[i] = head[c];
+        head[c] = i;
+    }
+    int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            long long tot = 0;
+            for (int i = 0; i < n; ++i) {
+                off[i] = (int)tot;
+                tot += cnt[i];
+            }
+            off[n] = (int)tot;
+            if (tot > cap) {
+                free(cnt); free(head); free(next); free(cx); free(cy);
+                return tot;
+            }
+        }
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int i = 0; i < n; ++i) {
+            int k = (pass == 1) ? off[i] : 0;
+            int c = 0;
+            int xs[3], ys[3], nxs = 0, nys = 0;
+            /* distinct bucket columns / rows within one bucket of i */
+            for (int d = -1; d <= 1; ++d) {
+                int a = cx[i] + d;
+                if (P->periodic[0]) a = ((a % nc[0]) + nc[0]) % nc[0];
+                if (a < 0 || a >= nc[0]) continue;
+                int dup = 0;
+                for (int t = 0; t < nxs; ++t) dup |= (xs[t] == a);
+                if (!dup) xs[nxs++] = a;
+            }
+            for (int d = -1; d <= 1; ++d) {
+                int b = cy[i] + d;
+                if (P->periodic[1]) b = ((b % nc[1]) + nc[1]) % nc[1];
+                if (b < 0 || b >= nc[1]) continue;
+                int dup = 0;
+                for (int t = 0; t < nys; ++t) dup |= (ys[t] == b);
+                if (!dup) ys[nys++] = b;
+            }
+            for (int s = 0; s < nys; ++s)
+                for (int r = 0; r < nxs; ++r)
+                    for (int j = head[(long long)ys[s] * nc[0] + xs[r]];
+                         j >= 0; j = next[j])
+                        if (orc_is_neighbor(P, x[i], y[i], h[i], x[j], y[j],
+                                            h[j])) {
+                            if (pass == 1) nbr[k + c] = j;
+                            ++c;
+                        }
+            if (pass == 0)
+                cnt[i] = c;
+            else
+                qsort(nbr + k, (size_t)c, sizeof(int), cmp_int);
+        }
+    }
+    long long tot = off[n];
+    free(cnt); free(head); free(next); free(cx); free(cy);
+    return tot;
+}
+
+/* ------------------------------------------------------------------------
+ * Multi-level cell keys.  Definition (a build choice, the paper only asks
+ * for a neighbour search that is rebuilt every iteration, section 3.4):
+ *   level l_i: smallest l >= 0 with c0 2^l >= t where t = (3 h_i) / c0 in
+ *              FP64; capped at the top level, whose cell spans the domain.
+ *   per level and axis: cell side c_l = c0 2^l; on a periodic axis the
+ *              count is max(1, floor(L / c_l)) and the width L / count,
+ *              otherwise the count is max(1, ceil(L / c_l)), width c_l.
+ *   cell index floor((x - lo) / width) clamped to [0, count - 1].
+ *   key = l << 58 | morton(ix, iy), ix on the even bits.
+ * ---------------------------------------------------------------------- */
+int orc_max_level(const orc_params *P, double c0) {
+    double Lmax = P->hi[0] - P->lo[0];
+    double Ly = P->hi[1] - P->lo[1];
+    if (Ly > Lmax) Lmax = Ly;
+    int l = 0;
+    while (ldexp(c0, l) < Lmax) ++l;
+    return l;
+}
+
+static int level_of(double h, double c0, int lmax) {
+    double t = (3.0 * h) / c0;
+    int l;
+    if (t <= 1.0) {
+        l = 0;
+    } else {
+        int e;
+        double f = frexp(t, &e); /* t = f 2^e, f in [0.5, 1) */
+        l = (f == 0.5) ? e - 1 : e;
+    }
+    return l > lmax ? lmax : l;
+}
+
+static void level_grid(const orc_params *P, double c0, int l, int axis,
+                       long long *count, double *width) {
+    double L = P->hi[axis] - P->lo[axis];
+    double c = ldexp(c0, l);
+    long long nc;
+    if (P->periodic[axis]) {
+        nc = (long long)floor(L / c);
+        if (nc < 1) nc = 1;
+        *width = L / (double)nc;
+    } else {
+        nc = (long long)ceil(L / c);
+        if (nc < 1) nc = 1;
+        *width = c;
+    }
+    *count = nc;
+}
+
+static uint64_t spread_bits(uint64_t v) {
+    /* bit k of v goes to bit 2k, plain loop */
+    uint64_t out = 0;
+    for (int k = 0; k < 29; ++k)
+        if (v & (1ULL << k)) out |= 1ULL << (2 * k);
+    return out;
+}
+
+void orc_cell_keys(const orc_params *P, double c0, int n, const double *x,
+                   const double *y, const double *h, uint64_t *key,
+                   int *level) {
+    int lmax = orc_max_level(P, c0);
+    for (int i = 0; i < n; ++i) {
+        int l = level_of(h[i], c0, lmax);
+        long long cnt[2];
+        double w[2];
+        level_grid(P, c0, l, 0, &cnt[0], &w[0]);
+        level_grid(P, c0, l, 1, &cnt[1], &w[1]);
+        long long ix = (long long)floor((x[i] - P->lo[0]) / w[0]);
+        long long iy = (long long)floor((y[i] - P->lo[1]) / w[1]);
+        if (ix < 0) ix = 0;
+        if (ix > cnt[0] - 1) ix = cnt[0] - 1;
+        if (iy < 0) iy = 0;
+        if (iy > cnt[1] - 1) iy = cnt[1] - 1;
+        key[i] = ((uint64_t)l << 58) | spread_bits((uint64_t)ix) |
+                 (spread_bits((uint64_t)iy) << 1);
+        if (level) level[i] = l;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Pass A: summation density (section 2, Eq. sd-gather), variable-h
+ * correction beta (Eq. beta), average pressure (Eq. pavg, N_i counts i
+ * itself) and the limited shifting displacement (section 2.1, Eqs.
+ * shift-deltar and shift-limit).
+ *
+ * Readings: the shifting denominator W(dx, xi h_ij) is taken as the kernel
+ * at its inflection point for smoothing length h_ij = (h_i + h_j)/2, i.e.
+ * W(xi h_ij, h_ij), and grad W_ij as grad_i W(r_ij, h_ij).  At r = 0 the
+ * gradient is zero.  A particle whose beta is zero (no neighbour at r > 0)
+ * gets no shift, and pass B gives it zero rates.
+ * Returns the number of particles with beta == 0.
+ * ---------------------------------------------------------------------- */
+int orc_pass_a(const orc_params *P, int n, const double *x, const double *y,
+               const double *h, const double *m, const double *p,
+               const int *off, const int *nbr, orc_rhs_out *o) {
+    const double w_xi = w_of_q(XI_INFLECTION);
+    int degenerate = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : degenerate)
+    for (int i = 0; i < n; ++i) {
+        double rho = 0.0, srw = 0.0, psum = 0.0, spabs = 0.0;
+        double ax = 0.0, ay = 0.0, sax = 0.0, say = 0.0;
+        int cnt = 0;
+        for (int k = off[i]; k < off[i + 1]; ++k) {
+            int j = nbr[k];
+            double dx, dy;
+            separation(P, x[i], y[i], x[j], y[j], &dx, &dy);
+            double r = sqrt(dx * dx + dy * dy);
+            rho += m[j] * orc_W(r, h[i]);
+            srw += m[j] * r * orc_dWdr(r, h[i]);
+            psum += p[j];
+            spabs += fabs(p[j]);
+            cnt += 1;
+            if (j != i && r > 0.0) {
+                double hb = 0.5 * (h[i] + h[j]);
+                double ratio = w_of_q(r / hb) / w_xi;
+                double f = (m[j] / P->rho0) * (1.0 + 0.24 * p4(ratio)) *
+                           orc_dWdr(r, hb) / r;
+                ax += f * dx;
+                ay += f * dy;
+                sax += fabs(f * dx);
+                say += fabs(f * dy);
+            }
+        }
+        double beta = -srw / (rho * DIM);
+        o->rho[i] = rho;
+        o->beta[i] = beta;
+        o->pavg[i] = psum / cnt;
+        o->nnb[i] = cnt;
+        o->s_rho[i] = rho;
+        o->s_beta[i] = fabs(beta);
+        o->s_pavg[i] = spabs / cnt;
+        double c = -0.5 * h[i] * h[i];
+        double drx = c * ax, dry = c * ay;
+        if (beta == 0.0) {
+            drx = 0.0;
+            dry = 0.0;
+            degenerate += 1;
+        }
+        double mag = sqrt(drx * drx + dry * dry);
+        double lim = 0.25 * h[i];
+        if (mag > lim) {
+            double theta = lim / mag;
+            drx *= theta;
+            dry *= theta;
+        }
+        o->drx[i] = drx;
+        o->dry[i] = dry;
+        o->s_drx[i] = 0.5 * h[i] * h[i] * sax;
+        o->s_dry[i] = 0.5 * h[i] * h[i] * say;
+    }
+    return degenerate;
+}
+
+/* ------------------------------------------------------------------------
+ * Pass B: EDAC pressure rate (section 2, Eq. edac:sph) and momentum rate
+ * (Eq. mom-sph without the A_i/A_j stresses and third line, which the
+ * paper's remark in section 2 says are not used), with
+ *   P_i = (p_i - p_avg,i) / (rho_i^2 beta_i)                (Eq. mom:pre)
+ *   grad W(r_ij, h_ij) = (grad W(h_i) + grad W(h_j)) / 2    (Eq. dw-avg)
+ *   nu_e,i = alpha_e c_s h_i / 8,                           (Eq. edac-alpha)
+ *   nu_e,ij = 4 nu_e,i nu_e,j / (nu_e,i + nu_e,j)           (Eq. nu-cleary)
+ *   eta = 0.001 h_i^2,  (u~_i - u_i) = dr_i / dt            (Eq. shift-tvf)
+ * Readings:
+ *   pavg_mode 0: P_j uses p_avg,i, so a constant pressure offset cancels
+ *     and a linear field gives grad p / rho (literal P_j with p_avg,j
+ *     cancels a linear field to zero force); pavg_mode 1 is literal.
+ *   edac_diff_denominator 1: the pressure-diffusion sum is divided by
+ *     (r^2 + eta) like the viscous sum, which makes it nu_e lap p.
+ *   edac_rho_factor 1: the third sum, an estimate of (u~ - u).grad p / rho,
+ *     is multiplied by rho_i to match the continuum Eq. edac-corr.
+ * Sums run over j != i (every term vanishes at j == i).
+ * ---------------------------------------------------------------------- */
+void orc_pass_b(const orc_params *P, double dt, int n, const double *x,
+                const double *y, const double *h, const double *m,
+                const double *p, const double *u, const double *v,
+                const int *off, const int *nbr, orc_rhs_out *o) {
+    const double c2 = P->cs * P->cs;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        double beta_i = o->beta[i];
+        if (beta_i == 0.0) {
+            o->dpdt[i] = o->dudt[i] = o->dvdt[i] = 0.0;
+            o->s_dpdt[i] = o->s_dudt[i] = o->s_dvdt[i] = 0.0;
+            continue;
+        }
+        double rho_i = o->rho[i];
+        double pavg_i = o->pavg[i];
+        double Pi = (p[i] - pavg_i) / (rho_i * rho_i * beta_i);
+        double Pi_abs = (fabs(p[i]) + fabs(pavg_i)) /
+                        (rho_i * rho_i * fabs(beta_i));
+        double nu_i = P->alpha_e * P->cs * h[i] / 8.0;
+        double eta = 0.001 * h[i] * h[i];
+        double dux = o->drx[i] / dt, duy = o->dry[i] / dt;
+        double div = 0, diff = 0, tvf = 0, ax = 0, ay = 0, vx = 0, vy = 0;
+        double s_div = 0, s_diff = 0, s_tvf = 0, s_ax = 0, s_ay = 0,
+               s_v = 0, s_vx = 0, s_vy = 0;
+        (void)s_v;
+        for (int k = off[i]; k < off[i + 1]; ++k) {
+            int j = nbr[k];
+            if (j == i) continue;
+            double dx, dy;
+            separation(P, x[i], y[i], x[j], y[j], &dx, &dy);
+            double r2 = dx * dx + dy * dy;
+            double r = sqrt(r2);
+            double gi = 0.0, gj = 0.0;
+            if (r > 0.0) {
+                gi = orc_dWdr(r, h[i]) / r;
+                gj = orc_dWdr(r, h[j]) / r;
+            }
+            double gWix = gi * dx, gWiy = gi * dy;
+            double gWjx = gj * dx, gWjy = gj * dy;
+            double gbar = 0.5 * (gi + gj);
+            double rdotgbar = gbar * r2; /* r_ij . gradW(r_ij, h_ij) */
+            double rho_j = o->rho[j], beta_j = o->beta[j];
+            double Vj = m[j] / rho_j;
+            double uij = u[i] - u[j], vij = v[i] - v[j];
+            double pref = (P->pavg_mode == 0) ? pavg_i : o->pavg[j];
+            double Pj = (p[j] - pref) / (rho_j * rho_j * beta_j);
+            double Pj_abs = (fabs(p[j]) + fabs(pref)) /
+                            (rho_j * rho_j * fabs(beta_j));
+            double nu_j = P->alpha_e * P->cs * h[j] / 8.0;
+            double nu_ij = 4.0 * nu_i * nu_j / (nu_i + nu_j);
+            double dden = P->edac_diff_denominator ? (r2 + eta) : 1.0;
+
+            div += Vj * (uij * gWix + vij * gWiy);
+            diff += Vj * nu_ij * (p[i] - p[j]) * rdotgbar / dden;
+            double fx = Pi * gWix + Pj * gWjx;
+            double fy = Pi * gWiy + Pj * gWjy;
+            tvf += m[j] * (dux * fx + duy * fy);
+            ax -= m[j] * fx;
+            ay -= m[j] * fy;
+            double visc = m[j] * (4.0 * P->nu / (rho_i + rho_j)) * rdotgbar /
+                          (r2 + eta);
+            vx += visc * uij;
+            vy += visc * vij;
+
+            double au = fabs(u[i]) + fabs(u[j]), av = fabs(v[i]) + fabs(v[j]);
+            s_div += Vj * (au * fabs(gWix) + av * fabs(gWiy));
+            s_diff += Vj * nu_ij * (fabs(p[i]) + fabs(p[j])) * fabs(rdotgbar) /
+                      dden;
+            double afx = Pi_abs * fabs(gWix) + Pj_abs * fabs(gWjx);
+            double afy = Pi_abs * fabs(gWiy) + Pj_abs * fabs(gWjy);
+            s_tvf += m[j] * (fabs(dux) * afx + fabs(duy) * afy);
+            s_ax += m[j] * afx;
+            s_ay += m[j] * afy;
+            s_vx += fabs(visc) * au;
+            s_vy += fabs(visc) * av;
+        }
+        double rf = P->edac_rho_factor ? rho_i : 1.0;
+        o->dpdt[i] = (P->rho0 * c2 / beta_i) * div + diff / beta_i + rf * tvf;
+        o->dudt[i] = ax + vx / beta_i;
+        o->dvdt[i] = ay + vy / beta_i;
+        double ab = fabs(beta_i);
+        o->s_dpdt[i] = (P->rho0 * c2 / ab) * s_div + s_diff / ab + rf * s_tvf;
+        o->s_dudt[i] = s_ax + s_vx / ab;
+        o->s_dvdt[i] = s_ay + s_vy / ab;
+    }
+}
+
+/* Section 2.4, Eq. timestep, with h_min over the fluid particles and U the
+ * reference speed.  A zero viscosity drops the viscous limit. */
+double orc_dt(const orc_params *P, int n, const double *h) {
+    double hmin = DBL_MAX;
+    for (int i = 0; i < n; ++i)
+        if (h[i] < hmin) hmin = h[i];
+    double dt = 0.25 * (hmin / (P->U_ref + P->cs));
+    if (P->nu > 0.0) {
+        double dv = 0.125 * (hmin * hmin / P->nu);
+        if (dv < dt) dt = dv;
+    }
+    return dt;
+}
+
+static int *g_off = NULL, *g_nbr = NULL;
+static long long g_cap = 0;
+static int g_offn = 0;
+
+static long long neighbors_auto(const orc_params *P, int n, const double *x,
+                                const double *y, const double *h) {
+    if (g_offn < n + 1) {
+        free(g_off);
+        g_off = (int *)malloc((size_t)(n + 1) * sizeof(int));
+        g_offn = n + 1;
+    }
+    for (;;) {
+        long long tot = orc_neighbors_grid(P, n, x, y, h, g_off, g_nbr, g_cap);
+        if (tot <= g_cap) return tot;
+        free(g_nbr);
+        g_cap = tot + tot / 4 + 64;
+        g_nbr = (int *)malloc((size_t)g_cap * sizeof(int));
+    }
+}
+
+int orc_rhs(const orc_params *P, double dt, const orc_state *s,
+            orc_rhs_out *o) {
+    neighbors_auto(P, s->n, s->x, s->y, s->h);
+    int deg = orc_pass_a(P, s->n, s->x, s->y, s->h, s->m, s->p, g_off, g_nbr,
+                         o);
+    orc_pass_b(P, dt, s->n, s->x, s->y, s->h, s->m, s->p, s->u, s->v, g_off,
+               g_nbr, o);
+    return deg;
+}
+
+/* ------------------------------------------------------------------------
+ * PEC integrator, section 2.4, Eqs. int-pre and int-cor.
+ *   predict: u' = u0 + dt/2 a0; u~' = u' + dr0/dt; r' = r0 + dt/2 u~';
+ *            p' = p0 + dt/2 (dp/dt)0
+ *   correct: u = u0 + dt a'; u~ = u + dr'/dt; r = r0 + dt u~;
+ *            p = p0 + dt (dp/dt)'
+ * Positions are wrapped back into the box on periodic axes.
+ * ---------------------------------------------------------------------- */
+static double wrap(const orc_params *P, int axis, double x) {
+    if (P->periodic[axis]) {
+        double L = P->hi[axis] - P->lo[axis];
+        if (x >= P->hi[axis])
+            x -= L;
+        else if (x < P->lo[axis])
+            x += L;
+    }
+    return x;
+}
+
+static void pec_stage(const orc_params *P, double dt, double f, int n,
+                      const double *x0, const double *y0, const double *u0,
+                      const double *v0, const double *p0, const double *dudt,
+                      const double *dvdt, const double *dpdt,
+                      const double *drx, const double *dry, double *x,
+                      double *y, double *u, double *v, double *p) {
+    double fdt = f * dt;
+    for (int i = 0; i < n; ++i) {
+        double un = u0[i] + fdt * dudt[i];
+        double vn = v0[i] + fdt * dvdt[i];
+        double utx = un + drx[i] / dt;
+        double uty = vn + dry[i] / dt;
+        x[i] = wrap(P, 0, x0[i] + fdt * utx);
+        y[i] = wrap(P, 1, y0[i] + fdt * uty);
+        u[i] = un;
+        v[i] = vn;
+        p[i] = p0[i] + fdt * dpdt[i];
+    }
+}
+
+void orc_pec_predict(const orc_params *P, double dt, int n, const double *x0,
+                     const double *y0, const double *u0, const double *v0,
+                     const double *p0, const double *dudt,
+                     const double *dvdt, const double *dpdt,
+                     const double *drx, const double *dry, double *x,
+                     double *y, double *u, double *v, double *p) {
+    pec_stage(P, dt, 0.5, n, x0, y0, u0, v0, p0, dudt, dvdt, dpdt, drx, dry,
+              x, y, u, v, p);
+}
+
+void orc_pec_correct(const orc_params *P, double dt, int n, const double *x0,
+                     const double *y0, const double *u0, const double *v0,
+                     const double *p0, const double *dudt,
+                     const double *dvdt, const double *dpdt,
+                     const double *drx, const double *dry, double *x,
+                     double *y, double *u, double *v, double *p) {
+    pec_stage(P, dt, 1.0, n, x0, y0, u0, v0, p0, dudt, dvdt, dpdt, drx, dry,
+              x, y, u, v, p);
+}
+
+typedef struct {
+    double *buf;
+    orc_rhs_out o;
+} rhs_bufs;
+
+static void rhs_bufs_init(rhs_bufs *b, int n) {
+    int nn = n > 0 ? n : 1;
+    b->buf = (double *)malloc((size_t)nn * 16 * sizeof(double));
+    double *q = b->buf;
+    b->o.rho = q; q += nn;
+    b->o.beta = q; q += nn;
+    b->o.pavg = q; q += nn;
+    b->o.drx = q; q += nn;
+    b->o.dry = q; q += nn;
+    b->o.dpdt = q; q += nn;
+    b->o.dudt = q; q += nn;
+    b->o.dvdt = q; q += nn;
+    b->o.s_rho = q; q += nn;
+    b->o.s_beta = q; q += nn;
+    b->o.s_pavg = q; q += nn;
+    b->o.s_drx = q; q += nn;
+    b->o.s_dry = q; q += nn;
+    b->o.s_dpdt = q; q += nn;
+    b->o.s_dudt = q; q += nn;
+    b->o.s_dvdt = q; q += nn;
+    b->o.nnb = (int *)malloc((size_t)nn * sizeof(int));
+}
+
+static void rhs_bufs_free(rhs_bufs *b) {
+    free(b->buf);
+    free(b->o.nnb);
+}
+
+int orc_step(const orc_params *P, orc_state *s, int nsteps, double *t) {
+    int n = s->n;
+    int nn = n > 0 ? n : 1;
+    rhs_bufs a, b;
+    rhs_bufs_init(&a, n);
+    rhs_bufs_init(&b, n);
+    double *x0 = (double *)malloc((size_t)nn * 5 * sizeof(double));
+    double *y0 = x0 + nn, *u0 = y0 + nn, *v0 = u0 + nn, *p0 = v0 + nn;
+    for (int st = 0; st < nsteps; ++st) {
+        double dt = orc_dt(P, n, s->h);
+        memcpy(x0, s->x, (size_t)n * sizeof(double));
+        memcpy(y0, s->y, (size_t)n * sizeof(double));
+        memcpy(u0, s->u, (size_t)n * sizeof(double));
+        memcpy(v0, s->v, (size_t)n * sizeof(double));
+        memcpy(p0, s->p, (size_t)n * sizeof(double));
+        orc_rhs(P, dt, s, &a.o);
+        orc_pec_predict(P, dt, n, x0, y0, u0, v0, p0, a.o.dudt, a.o.dvdt,
+                        a.o.dpdt, a.o.drx, a.o.dry, s->x, s->y, s->u, s->v,
+                        s->p);
+        orc_rhs(P, dt, s, &b.o);
+        orc_pec_correct(P, dt, n, x0, y0, u0, v0, p0, b.o.dudt, b.o.dvdt,
+                        b.o.dpdt, b.o.drx, b.o.dry, s->x, s->y, s->u, s->v,
+                        s->p);
+        /* density is not integrated: keep the latest summation density */
+        memcpy(s->rho, b.o.rho, (size_t)n * sizeof(double));
+        *t += dt;
+    }
+    free(x0);
+    rhs_bufs_free(&a);
+    rhs_bufs_free(&b);
+    return 0;
+}

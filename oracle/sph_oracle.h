@@ -1,0 +1,123 @@
+/*
+ * Plain FP64 CPU oracle for the adaptive-resolution weakly-compressible SPH
+ * method of Muta & Ramachandran, "Efficient and Accurate Adaptive Resolution
+ * for Weakly-Compressible SPH" (arXiv 2107.01276).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA path; it is
+ * never part of it.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference legs may load it.  It shares no code, header,
+ * constant table or helper with the CUDA library.
+ *
+ * Every routine is a direct transcription of the paper's equations in the
+ * paper's order, in double precision, compiled with FMA contraction off.
+ * Where the paper is silent or ambiguous the reading taken is stated next to
+ * the routine that implements it.
+ *
+ * Arrays are caller-owned host arrays.  Particle i of a set is element i of
+ * every array; "id" is the persistent particle identity.
+ */
+#ifndef SPH_ORACLE_H
+#define SPH_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double lo[2], hi[2];     /* domain box */
+    int periodic[2];         /* 1: periodic along that axis (minimum image) */
+    double rho0;             /* reference density */
+    double cs;               /* artificial speed of sound */
+    double nu;               /* kinematic viscosity */
+    double U_ref;            /* reference speed U in the time-step rule */
+    double hdx;              /* C in h = C (m/rho)^(1/d) */
+    double alpha_e;          /* EDAC viscosity factor, 1.5 in the paper */
+    double split_alpha;      /* child h factor, 0.9 */
+    double split_eps;        /* child ring radius factor, 0.4 */
+    int pavg_mode;           /* 0: p_avg,i subtracted from p_i and p_j; 1: literal p_avg,j for P_j */
+    int edac_diff_denominator; /* 1: pressure-diffusion term divided by r^2 + eta */
+    int edac_rho_factor;     /* 1: third EDAC sum multiplied by rho_i */
+    int merge_iters;         /* merge rounds after a split pass (3) */
+    int shift_iters;         /* shift + Taylor-correction rounds (3) */
+} orc_params;
+
+/* Fluid particle set with capacity; n changes under split/merge. */
+typedef struct {
+    int n, cap;
+    double *x, *y, *u, *v, *p, *rho, *m, *h, *mmin, *mmax;
+    long long *id;
+} orc_state;
+
+/* Per-particle outputs of one right-hand-side evaluation, with the
+ * condition scales S_i = sum of |terms| used by the parity norm. */
+typedef struct {
+    double *rho, *beta, *pavg, *drx, *dry, *dpdt, *dudt, *dvdt;
+    int *nnb;
+    double *s_rho, *s_beta, *s_pavg, *s_drx, *s_dry, *s_dpdt, *s_dudt, *s_dvdt;
+} orc_rhs_out;
+
+/* ---- kernel (section 2, Eq. kernel) ---- */
+double orc_W(double r, double h);
+double orc_dWdr(double r, double h);
+
+/* ---- neighbour predicate and searches (section 2, gather sums) ---- */
+int orc_is_neighbor(const orc_params *P, double xi, double yi, double hi,
+                    double xj, double yj, double hj);
+/* CSR of N(i), each list ascending in j, i itself included.  Returns the
+ * total entry count; if it exceeds cap only off[] is valid. */
+long long orc_neighbors_brute(const orc_params *P, int n, const double *x,
+                              const double *y, const double *h, int *off,
+                              int *nbr, long long cap);
+long long orc_neighbors_grid(const orc_params *P, int n, const double *x,
+                             const double *y, const double *h, int *off,
+                             int *nbr, long long cap);
+/* Cross-set search: for each a in set A, the members b of set B with
+ * r_ab < 3 max(h_a, h_b).  Brute force. */
+long long orc_neighbors_cross(const orc_params *P, int na, const double *xa,
+                              const double *ya, const double *ha, int nb,
+                              const double *xb, const double *yb,
+                              const double *hb, int *off, int *nbr,
+                              long long cap);
+
+/* ---- multi-level cell keys ---- */
+int orc_max_level(const orc_params *P, double c0);
+void orc_cell_keys(const orc_params *P, double c0, int n, const double *x,
+                   const double *y, const double *h, uint64_t *key,
+                   int *level);
+
+/* ---- right-hand side ---- */
+int orc_pass_a(const orc_params *P, int n, const double *x, const double *y,
+               const double *h, const double *m, const double *p,
+               const int *off, const int *nbr, orc_rhs_out *o);
+void orc_pass_b(const orc_params *P, double dt, int n, const double *x,
+                const double *y, const double *h, const double *m,
+                const double *p, const double *u, const double *v,
+                const int *off, const int *nbr, orc_rhs_out *o);
+double orc_dt(const orc_params *P, int n, const double *h);
+/* Neighbour search + pass A + pass B at the current state. */
+int orc_rhs(const orc_params *P, double dt, const orc_state *s,
+            orc_rhs_out *o);
+/* nsteps PEC steps; *t advanced by the sum of the time steps. */
+int orc_step(const orc_params *P, orc_state *s, int nsteps, double *t);
+/* The PEC stage updates alone, for tests with prescribed rates. */
+void orc_pec_predict(const orc_params *P, double dt, int n, const double *x0,
+                     const double *y0, const double *u0, const double *v0,
+                     const double *p0, const double *dudt,
+                     const double *dvdt, const double *dpdt,
+                     const double *drx, const double *dry, double *x,
+                     double *y, double *u, double *v, double *p);
+void orc_pec_correct(const orc_params *P, double dt, int n, const double *x0,
+                     const double *y0, const double *u0, const double *v0,
+                     const double *p0, const double *dudt,
+                     const double *dvdt, const double *dpdt,
+                     const double *drx, const double *dry, double *x,
+                     double *y, double *u, double *v, double *p);
+
+int orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,152 @@
+"""Seeded synthetic particle sets shaped like the paper's workloads.
+
+This module only lays particles out and draws random numbers; it holds none
+of the SPH method's arithmetic, and both the CUDA path and the CPU oracle
+take their inputs from it.  Each generator returns a dict with the particle
+arrays (FP64 numpy) and a ``params`` dict of physical parameters that both
+sides translate into their own parameter blocks.
+
+Workloads (all synthetic; the paper's runs use no external data set):
+  taylor_green   -- Taylor-Green vortex on the periodic unit square, the
+                    initial condition of section 4.1 (Eq. tgv_sol at t = 0).
+  perturbed      -- lattice with position jitter and a smooth h variation,
+                    for parity at sizes the oracle finishes in seconds.
+  graded_strip   -- periodic strip whose spacing varies geometrically over
+                    a 1:ratio range (the pair-kernel sweep), tent-shaped so
+                    the spacing is continuous across the periodic wrap.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def _base_params(**kw):
+    p = dict(lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(1, 1), rho0=1.0,
+             cs=10.0, nu=0.0, U_ref=1.0, hdx=1.0, alpha_e=1.5,
+             split_alpha=0.9, split_eps=0.4, ds_min=0.0, ds_max=0.0,
+             Cr=1.08, pavg_mode=0, edac_diff_denominator=1,
+             edac_rho_factor=1, merge_iters=3, shift_iters=3)
+    p.update(kw)
+    return p
+
+
+def taylor_green(nx: int = 50, Re: float = 100.0, L: float = 1.0,
+                 hdx: float = 1.0, rho0: float = 1.0, cs: float = 10.0,
+                 U: float = 1.0, jitter: float = 0.0, seed: int = 1):
+    """nx*nx lattice on [0, L)^2, periodic; u, v, p from the Taylor-Green
+    closed form at t = 0 (section 4.1), nu = U L / Re."""
+    dx = L / nx
+    g = (np.arange(nx) + 0.5) * dx
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    x, y = X.ravel().copy(), Y.ravel().copy()
+    if jitter > 0:
+        rng = np.random.default_rng(seed)
+        x += jitter * dx * rng.uniform(-1, 1, x.size)
+        y += jitter * dx * rng.uniform(-1, 1, y.size)
+        x %= L
+        y %= L
+    k = 2.0 * math.pi / L
+    u = -U * np.cos(k * x) * np.sin(k * y)
+    v = U * np.sin(k * x) * np.cos(k * y)
+    p = -rho0 * U * U * (np.cos(2 * k * x) + np.cos(2 * k * y)) / 4.0
+    n = x.size
+    parts = dict(x=x, y=y, u=u, v=v, p=p, rho=np.full(n, rho0),
+                 m=np.full(n, rho0 * dx * dx), h=np.full(n, hdx * dx))
+    params = _base_params(lo=(0.0, 0.0), hi=(L, L), periodic=(1, 1),
+                          rho0=rho0, cs=cs, nu=U * L / Re, U_ref=U, hdx=hdx)
+    return dict(particles=parts, params=params, dx=dx, Re=Re, L=L, U=U)
+
+
+def perturbed(nx: int = 40, ny: int = 32, L: float = 1.0, hdx: float = 1.2,
+              h_ratio: float = 2.0, jitter: float = 0.15,
+              periodic=(1, 1), rho0: float = 1.0, cs: float = 10.0,
+              nu: float = 0.01, seed: int = 3):
+    """nx*ny lattice with jitter, random velocities and pressures, and a
+    smooth h variation by ``h_ratio`` across x; masses follow h."""
+    rng = np.random.default_rng(seed)
+    Ly = L * ny / nx
+    dx = L / nx
+    gx = (np.arange(nx) + 0.5) * dx
+    gy = (np.arange(ny) + 0.5) * (Ly / ny)
+    X, Y = np.meshgrid(gx, gy, indexing="xy")
+    x = X.ravel() + jitter * dx * rng.uniform(-1, 1, X.size)
+    y = Y.ravel() + jitter * dx * rng.uniform(-1, 1, X.size)
+    if periodic[0]:
+        x %= L
+    if periodic[1]:
+        y %= Ly
+    n = x.size
+    # spacing varies smoothly (periodic-compatible) by h_ratio
+    s = dx * h_ratio ** (0.5 - 0.5 * np.cos(2 * math.pi * x / L))
+    s = s / h_ratio ** 0.5
+    h = hdx * s
+    m = rho0 * s * s
+    u = rng.normal(0.0, 0.1, n)
+    v = rng.normal(0.0, 0.1, n)
+    rho = rho0 * (1.0 + rng.uniform(-0.01, 0.01, n))
+    p = rng.normal(0.0, 0.2, n)
+    parts = dict(x=x, y=y, u=u, v=v, p=p, rho=rho, m=m, h=h)
+    params = _base_params(lo=(0.0, 0.0), hi=(L, Ly), periodic=tuple(periodic),
+                          rho0=rho0, cs=cs, nu=nu, U_ref=1.0, hdx=hdx)
+    return dict(particles=parts, params=params, dx=dx)
+
+
+def graded_strip(n_target: int = 1 << 20, ratio: float = 250.0,
+                 hdx: float = 1.2, rho0: float = 1.0, cs: float = 10.0,
+                 nu: float = 0.0, seed: int = 4):
+    """Periodic square [0, L)^2 of columns whose spacing grows
+    geometrically from dx_min at x = L/2 to ratio*dx_min at x = 0 and L
+    (a tent, continuous across the wrap).  Column k holds round(L/dx_k)
+    particles at spacing L/ny_k.  h = hdx*dx, m = rho0*dx*dy; u, v ~
+    N(0, 0.1); rho = rho0 (1 + U(-0.01, 0.01)); p = rho0 cs^2 (rho/rho0 - 1).
+    L is chosen so the particle count is close to n_target."""
+    rng = np.random.default_rng(seed)
+    L = 1.0
+    # particle count for dx_min = 1: N(L) ~ 2 * int_0^{L/2} L / dx(x)^2 dx
+    # with dx(x) = ratio^(1 - 2x/L); solve for the scale that gives n_target
+    lr = math.log(ratio)
+    # int_0^{L/2} ratio^(-2(1-2x/L)) dx = L/(4 lr) (1 - ratio^-2)
+    est = 2.0 * L * L / (4.0 * lr) * (1.0 - ratio ** -2)
+    dx_min = math.sqrt(est / n_target)
+    xs, dxs = [], []
+    xpos = 0.0
+    while xpos < L:
+        t = abs(2.0 * xpos / L - 1.0)      # 1 at the ends, 0 at the middle
+        d = dx_min * ratio ** t
+        xs.append(xpos)
+        dxs.append(d)
+        xpos += d
+    # stretch column positions so the last gap closes the period exactly
+    xs = np.array(xs) * (L / xpos)
+    dxs = np.array(dxs) * (L / xpos)
+    cx, cy, cdx, cdy = [], [], [], []
+    for xc, d in zip(xs, dxs):
+        ny = max(1, int(round(L / d)))
+        dy = L / ny
+        yy = (np.arange(ny) + 0.5) * dy
+        cx.append(np.full(ny, xc + 0.5 * d))
+        cy.append(yy)
+        cdx.append(np.full(ny, d))
+        cdy.append(np.full(ny, dy))
+    x = np.concatenate(cx) % L
+    y = np.concatenate(cy)
+    ddx = np.concatenate(cdx)
+    ddy = np.concatenate(cdy)
+    n = x.size
+    s = np.sqrt(ddx * ddy)
+    u = rng.normal(0.0, 0.1, n)
+    v = rng.normal(0.0, 0.1, n)
+    rho = rho0 * (1.0 + rng.uniform(-0.01, 0.01, n))
+    p = rho0 * cs * cs * (rho / rho0 - 1.0)
+    parts = dict(x=x, y=y, u=u, v=v, p=p, rho=rho, m=rho0 * ddx * ddy,
+                 h=hdx * s)
+    params = _base_params(lo=(0.0, 0.0), hi=(L, L), periodic=(1, 1),
+                          rho0=rho0, cs=cs, nu=nu, U_ref=1.0, hdx=hdx,
+                          ds_min=float(s.min()))
+    return dict(particles=parts, params=params, dx_min=float(s.min()))
+
+
+def subset(parts: dict, idx) -> dict:
+    return {k: np.asarray(v)[idx].copy() for k, v in parts.items()}
