@@ -1,0 +1,195 @@
+/*
+ * sph.h -- C ABI of the GB300-native adaptive-resolution weakly-compressible
+ * SPH library (Muta & Ramachandran, "Efficient and Accurate Adaptive
+ * Resolution for Weakly-Compressible SPH", arXiv 2107.01276).
+ *
+ * The library advances one 2-D particle simulation per context on one GPU.
+ * Every numerical step runs in the library's own CUDA kernels (sm_103a);
+ * there is no CPU fallback.  Paper references are to its sections and its
+ * equation labels.
+ *
+ * Conventions
+ *  - Ownership: the library allocates and owns all device memory of a
+ *    context (sized by sph_params.capacity at sph_create).  Callers own
+ *    every host buffer they pass; every transfer is a copy.
+ *  - Streams: all device work of a context is enqueued on the stream given
+ *    to sph_create (a cudaStream_t; NULL = the legacy default stream).
+ *    sph_load_particles, sph_rhs, sph_step and sph_adapt return once their
+ *    work is enqueued, except where stated; sph_read synchronises.
+ *  - Errors: every call returns an sph_status and never throws or aborts.
+ *    After any status other than SPH_ECUDA the context stays usable;
+ *    sph_last_error() gives a one-line message.  A NULL context gives
+ *    SPH_EINVAL.
+ *  - Particle order: the library keeps particles sorted by cell key and
+ *    re-sorts them whenever it rebuilds the neighbour structure.  sph_read
+ *    returns every field of one state in the same (current) order;
+ *    SPH_F_ID gives each particle's persistent identity.
+ *  - Precision: SPH_FP64 computes everything in double.  SPH_MIXED keeps
+ *    positions, time integration, masses, split/merge bookkeeping and the
+ *    time-step reduction in double and does the pair arithmetic of the
+ *    right-hand side in float with float accumulation.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_EINVAL = 1,      /* bad argument; nothing was changed */
+    SPH_ENOMEM = 2,      /* device allocation failed */
+    SPH_ECUDA = 3,       /* CUDA runtime error; the context must be destroyed */
+    SPH_ECAPACITY = 4,   /* particle count would exceed sph_params.capacity */
+    SPH_ENONFINITE = 5,  /* a rate or state value became NaN/Inf */
+    SPH_ETIMEOUT = 6,    /* a bounded device wait gave up */
+    SPH_ESTATE = 7       /* call not valid in the current state (e.g. no fluid loaded) */
+} sph_status;
+
+typedef enum { SPH_FLUID = 0, SPH_WALL = 1, SPH_BACKGROUND = 2 } sph_kind;
+typedef enum { SPH_FP64 = 0, SPH_MIXED = 1 } sph_precision;
+
+/* Problem parameters (SI units).  sph_default_params fills the paper's
+ * values; the reading switches take the defaults stated beside them. */
+typedef struct {
+    int dim;                 /* must be 2 (the paper is two-dimensional) */
+    double lo[2], hi[2];     /* domain box; positions stay in it */
+    int periodic[2];         /* 1: periodic axis, minimum-image pairs */
+    double rho0;             /* reference density */
+    double cs;               /* artificial speed of sound (section 2) */
+    double nu;               /* kinematic viscosity */
+    double U_ref;            /* speed U of the time-step rule (section 2.4) */
+    double hdx;              /* C of h = C (m/rho)^(1/d) (section 3.1) */
+    double alpha_e;          /* EDAC viscosity factor, Eq. edac-alpha: 1.5 */
+    double split_alpha;      /* child smoothing-length factor (section 3.1): 0.9 */
+    double split_eps;        /* child ring radius / h (section 3.1): 0.4 */
+    double Cr;               /* layer size ratio (section 3.3): 1.08 */
+    double ds_min, ds_max;   /* finest / coarsest particle spacing (section 3.3) */
+    int merge_iters;         /* merge rounds after splitting (section 3.2): 3 */
+    int shift_iters;         /* shift + Taylor rounds (section 3.2): 3 */
+    int precision;           /* sph_precision */
+    long long capacity;      /* maximum fluid particles held on the device */
+    int pavg_mode;           /* 0 (default): P_j = (p_j - p_avg,i)/(rho_j^2 beta_j);
+                                1: literal Eq. mom:pre with p_avg,j */
+    int edac_diff_denominator; /* 1 (default): EDAC diffusion sum divided by r^2+eta */
+    int edac_rho_factor;     /* 1 (default): third EDAC sum multiplied by rho_i */
+    double cell_c0;          /* level-0 cell side of the neighbour grid;
+                                <= 0: 3*hdx*ds_min if ds_min > 0, else 3*min(h)
+                                of the fluid at load time */
+} sph_params;
+
+/* Host arrays of one particle set, n entries each.  Unused members may be
+ * NULL: u, v, p, rho default to 0, 0, 0, rho0; id defaults to 0..n-1 and
+ * ds (background only) to ds_max; mmin/mmax default to 0. */
+typedef struct {
+    const double *x, *y, *u, *v, *p, *rho, *m, *h;
+    const double *mmin, *mmax, *ds;
+    const int64_t *id;
+} sph_particles;
+
+/* Fields sph_read can copy out.  Doubles unless noted. */
+typedef enum {
+    SPH_F_X = 0, SPH_F_Y, SPH_F_U, SPH_F_V, SPH_F_P, SPH_F_RHO, SPH_F_M,
+    SPH_F_H, SPH_F_MMIN, SPH_F_MMAX,
+    SPH_F_ID,          /* int64 */
+    SPH_F_BETA, SPH_F_PAVG, SPH_F_DRX, SPH_F_DRY,   /* last pass A */
+    SPH_F_DPDT, SPH_F_DUDT, SPH_F_DVDT,             /* last pass B */
+    SPH_F_NNB,         /* int32: |N(i)| of the last pass A, i included */
+    /* The next three describe the current positions.  If particles moved
+     * since the last rebuild, reading one rebuilds first, which re-sorts
+     * the particles (read SPH_F_ID after them) and drops the last
+     * right-hand side. */
+    SPH_F_CELLKEY,     /* uint64: level << 58 | morton(ix, iy) */
+    SPH_F_NEIGH_OFF,   /* int64[n+1]: CSR offsets of N(i) */
+    SPH_F_NEIGH_ID,    /* int64[total]: ids of N(i), any order within a list */
+    SPH_F_COUNT
+} sph_field;
+
+typedef struct {
+    long long n;          /* fluid particles */
+    long long n_wall;     /* wall (dummy) particles */
+    long long n_bg;       /* background particles */
+    double t;             /* simulated time advanced by sph_step */
+    double dt;            /* time step of the last sph_step (Eq. timestep) */
+    double c0;            /* level-0 cell side in use */
+    int levels;           /* number of cell levels (top level spans the domain) */
+    long long steps;      /* PEC steps taken */
+    long long launches;   /* kernels launched by this context so far */
+} sph_info;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Fill *p with the paper's values: alpha_e 1.5, split_alpha 0.9,
+ * split_eps 0.4, Cr 1.08, 3 merge and 3 shift rounds, hdx 1.0, and the
+ * default readings; domain [0,1]^2 non-periodic, rho0 1, cs 10, nu 0,
+ * U_ref 1, precision FP64, capacity 0 (must be set). */
+void sph_default_params(sph_params *p);
+
+/* Validate *p and allocate a context with device storage for
+ * p->capacity fluid particles.  stream: cudaStream_t (may be NULL).
+ * Errors: SPH_EINVAL (dim != 2, empty box, capacity <= 0, non-positive
+ * rho0/cs/hdx, negative nu), SPH_ENOMEM, SPH_ECUDA.  *out is NULL on error. */
+sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out);
+
+/* Replace the particle set of the given kind by n particles copied from
+ * host arrays (x, y, m, h required; see sph_particles for defaults).
+ * Fluid positions must lie in the box (periodic axes: [lo, hi)).
+ * Synchronous with respect to the host buffers (they may be reused on
+ * return).  Errors: SPH_EINVAL (NULL required array, n < 0, h or m not
+ * positive and finite, position outside the box), SPH_ECAPACITY
+ * (n > capacity), SPH_ECUDA. */
+sph_status sph_load_particles(sph_ctx *ctx, sph_kind kind, long long n,
+                              const sph_particles *src);
+
+/* One right-hand-side evaluation at the current state (section 2): rebuild
+ * the cell structure, pass A (summation density Eq. sd-gather, beta Eq.
+ * beta, p_avg Eq. pavg, limited shift Eqs. shift-deltar / shift-limit),
+ * pass B (EDAC pressure rate Eq. edac:sph, momentum rate Eq. mom-sph),
+ * with dt from Eq. timestep for u~ - u = dr/dt.  Results are read with
+ * sph_read (SPH_F_RHO ... SPH_F_DVDT).  Errors: SPH_ESTATE (no fluid). */
+sph_status sph_rhs(sph_ctx *ctx);
+
+/* nsteps predict-evaluate-correct steps (section 2.4, Eqs. int-pre and
+ * int-cor; two right-hand sides per step; dt from Eq. timestep).  If
+ * t_out is not NULL it receives the simulated time after the steps, which
+ * requires one synchronisation.  Errors: SPH_ESTATE, SPH_EINVAL
+ * (nsteps < 0), SPH_ENONFINITE (checked once at the end when t_out is
+ * given). */
+sph_status sph_step(sph_ctx *ctx, int nsteps, double *t_out);
+
+/* Copy one field of the fluid set to the host buffer dst holding cap
+ * elements of the field's type; *n_out (if not NULL) receives the element
+ * count.  Synchronises the context's stream.  Errors: SPH_EINVAL (bad
+ * field, dst NULL), SPH_ECAPACITY (cap too small; *n_out still set),
+ * SPH_ESTATE (field not computed yet). */
+sph_status sph_read(sph_ctx *ctx, sph_field field, void *dst, long long cap,
+                    long long *n_out);
+
+/* Counts, time and time step of the context (synchronises). */
+sph_status sph_get_info(sph_ctx *ctx, sph_info *out);
+
+/* Kernel timing: when enabled the context records CUDA events around the
+ * launches of each timed kernel family on its stream.  sph_kernel_time
+ * returns the accumulated device milliseconds and launch count of one
+ * family (0: pass B, 1: pass A, 2: cell rebuild (keys, sort, gather,
+ * table), 3: PEC stages, 4: adaptation kernels) and resets them if reset
+ * is non-zero.  Synchronises. */
+sph_status sph_set_timing(sph_ctx *ctx, int enable);
+sph_status sph_kernel_time(sph_ctx *ctx, int family, double *ms,
+                           long long *launches, int reset);
+
+/* Free all device and host storage of the context (synchronises). */
+sph_status sph_destroy(sph_ctx *ctx);
+
+/* Message of the last error on this context ("" if none); valid until the
+ * next call on the context.  NULL ctx: message of the last failed
+ * sph_create in this thread. */
+const char *sph_last_error(const sph_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,399 @@
+// Cell keys, stable LSD radix sort, exclusive scan, permutation gather and
+// the cell hash table: the neighbour-structure rebuild that the paper runs
+// before every iteration (section 3.4, step iii: "update the nearest
+// neighbor search").  All HBM-bound; no tensor cores.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ------------------------------------------------------------------ keys --
+// Level l_i: smallest l >= 0 with c0 2^l >= t, t = (3 h_i) / c0 in FP64,
+// capped at lmax.  Cell index floor((x - lo) / w_l) clamped to the level's
+// cell count.  skey = l << (2 mbits) | morton(ix, iy), ix on even bits.
+__device__ __forceinline__ int level_of(double h, double c0, int lmax) {
+    double t = __ddiv_rn(__dmul_rn(3.0, h), c0);
+    int l = 0;
+    if (t > 1.0) {
+        int e;
+        double f = frexp(t, &e);
+        l = (f == 0.5) ? e - 1 : e;
+    }
+    return l > lmax ? lmax : l;
+}
+
+__device__ __forceinline__ int cell_coord(double x, double lo, double w,
+                                          int ncell) {
+    double q = floor(__ddiv_rn(__dsub_rn(x, lo), w));
+    int c;
+    if (q < 0.0)
+        c = 0;
+    else if (q > (double)(ncell - 1))
+        c = ncell - 1;
+    else
+        c = (int)q;
+    return c;
+}
+
+struct KeysArgs {
+    Domain dom;
+    double c0;
+    int lmax, mbits;
+    Level lev[MAX_LEVELS];
+};
+
+__global__ void k_keys(int n, KeysArgs a, const double *__restrict__ x,
+                       const double *__restrict__ y,
+                       const double *__restrict__ h,
+                       uint64_t *__restrict__ skey,
+                       uint32_t *__restrict__ perm, uint32_t *level_mask,
+                       int *bbox) {
+    __shared__ int sb[MAX_LEVELS * 4];
+    __shared__ uint32_t smask;
+    for (int t = threadIdx.x; t < MAX_LEVELS * 4; t += blockDim.x)
+        sb[t] = (t & 1) ? -1 : 0x7fffffff;
+    if (threadIdx.x == 0) smask = 0;
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        int l = level_of(h[i], a.c0, a.lmax);
+        const Level &L = a.lev[l];
+        int ix = cell_coord(x[i], a.dom.lo[0], L.w[0], L.n[0]);
+        int iy = cell_coord(y[i], a.dom.lo[1], L.w[1], L.n[1]);
+        uint64_t m = spread2((uint64_t)ix) | (spread2((uint64_t)iy) << 1);
+        skey[i] = ((uint64_t)l << (2 * a.mbits)) | m;
+        perm[i] = (uint32_t)i;
+        atomicOr(&smask, 1u << l);
+        atomicMin(&sb[l * 4 + 0], ix);
+        atomicMax(&sb[l * 4 + 1], ix);
+        atomicMin(&sb[l * 4 + 2], iy);
+        atomicMax(&sb[l * 4 + 3], iy);
+    }
+    __syncthreads();
+    uint32_t msk = smask;
+    for (int t = threadIdx.x; t < MAX_LEVELS * 4; t += blockDim.x) {
+        int l = t >> 2;
+        if (!(msk & (1u << l))) continue;
+        if (t & 1)
+            atomicMax(&bbox[t], sb[t]);
+        else
+            atomicMin(&bbox[t], sb[t]);
+    }
+    if (threadIdx.x == 0 && msk) atomicOr(level_mask, msk);
+}
+
+void compute_levels(const Domain &dom, double c0, Level *lev) {
+    for (int l = 0; l < MAX_LEVELS; ++l) {
+        double c = ldexp(c0, l);
+        lev[l].c = c;
+        for (int ax = 0; ax < 2; ++ax) {
+            double Lx = dom.L[ax];
+            long long nc;
+            double w;
+            if (dom.periodic[ax]) {
+                nc = (long long)floor(Lx / c);
+                if (nc < 1) nc = 1;
+                w = Lx / (double)nc;
+            } else {
+                nc = (long long)ceil(Lx / c);
+                if (nc < 1) nc = 1;
+                w = c;
+            }
+            if (nc > (1ll << MAX_MORTON_BITS)) nc = 1ll << MAX_MORTON_BITS;
+            lev[l].n[ax] = (int)nc;
+            lev[l].w[ax] = w;
+        }
+    }
+}
+
+void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
+                 int lmax, int mbits, const Level *lev, const double *x,
+                 const double *y, const double *h, uint64_t *skey,
+                 uint32_t *perm, uint32_t *level_mask, int *bbox) {
+    KeysArgs a;
+    a.dom = dom;
+    a.c0 = c0;
+    a.lmax = lmax;
+    a.mbits = mbits;
+    for (int l = 0; l < MAX_LEVELS; ++l) a.lev[l] = lev[l];
+    if (n <= 0) return;
+    int bs = 256;
+    k_keys<<<(n + bs - 1) / bs, bs, 0, s>>>(n, a, x, y, h, skey, perm,
+                                            level_mask, bbox);
+}
+
+// ------------------------------------------------------------ radix sort --
+// 8-bit digits, 256 threads (8 warps) per tile of 8 * 32 * ITEMS keys.
+// Warp w ranks its contiguous sub-tile step by step with __match_any_sync;
+// the per-(warp, digit) running counts in shared memory make the rank
+// stable.  Tile counts are scanned digit-major, so the scatter keeps the
+// input order among equal digits across tiles as well.
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+template <bool SCATTER>
+__global__ void __launch_bounds__(RS_THREADS)
+    k_radix(int n, int shift, int ntiles, const uint64_t *__restrict__ kin,
+            const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+            uint32_t *__restrict__ vout, uint32_t *__restrict__ counts) {
+    __shared__ uint32_t cnt[RS_WARPS][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_THREADS)
+        (&cnt[0][0])[t] = 0;
+    __syncthreads();
+    const int tile = blockIdx.x;
+    const long long base = (long long)tile * RS_TILE + (long long)w * 32 * RS_ITEMS;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t rank[RS_ITEMS];
+    uint64_t key[RS_ITEMS];
+    int dig[RS_ITEMS];
+#pragma unroll
+    for (int s = 0; s < RS_ITEMS; ++s) {
+        long long e = base + s * 32 + lane;
+        bool ok = e < n;
+        uint64_t k = ok ? kin[e] : 0;
+        int d = ok ? (int)((k >> shift) & 255u) : 256;
+        key[s] = k;
+        dig[s] = d;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (ok) before = cnt[w][d];
+        __syncwarp();
+        if (ok && lane == leader) cnt[w][d] = before + __popc(peers);
+        __syncwarp();
+        rank[s] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    if (!SCATTER) {
+        int d = threadIdx.x;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) tot += cnt[ww][d];
+        counts[(size_t)d * ntiles + tile] = tot;
+        return;
+    }
+    {
+        int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) {
+            uint32_t c = cnt[ww][d];
+            cnt[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < RS_ITEMS; ++s) {
+        long long e = base + s * 32 + lane;
+        if (e >= n) continue;
+        int d = dig[s];
+        uint32_t pos = counts[(size_t)d * ntiles + tile] + cnt[w][d] + rank[s];
+        kout[pos] = key[s];
+        vout[pos] = vin[e];
+    }
+}
+
+void radix_sort(cudaStream_t s, int n, int bits, uint64_t *key,
+                uint32_t *val, SortScratch &sc, int *launches) {
+    if (n <= 1 || bits <= 0) return;
+    int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    uint64_t *ka = key, *kb = sc.key_alt;
+    uint32_t *va = val, *vb = sc.val_alt;
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_radix<false><<<ntiles, RS_THREADS, 0, s>>>(n, shift, ntiles, ka, va,
+                                                     kb, vb, sc.counts);
+        exclusive_scan(s, sc.counts, sc.counts, 256 * ntiles, nullptr, sc,
+                       launches);
+        k_radix<true><<<ntiles, RS_THREADS, 0, s>>>(n, shift, ntiles, ka, va,
+                                                    kb, vb, sc.counts);
+        *launches += 2;
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    if (ka != key) {
+        cudaMemcpyAsync(key, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(val, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+    }
+}
+
+// ------------------------------------------------------------------ scan --
+constexpr int SC_THREADS = 256;
+constexpr int SC_ITEMS = 8;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v,
+                                                    uint32_t *total) {
+    __shared__ uint32_t ws[SC_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < SC_THREADS / 32 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < SC_THREADS / 32) ws[lane] = t;
+    }
+    __syncthreads();
+    uint32_t pre = (w > 0 ? ws[w - 1] : 0) + x - v;
+    if (total) *total = ws[SC_THREADS / 32 - 1];
+    __syncthreads();
+    return pre;
+}
+
+__global__ void k_scan_reduce(const uint32_t *__restrict__ in, int n,
+                              uint32_t *__restrict__ sums) {
+    long long b0 = (long long)blockIdx.x * SC_TILE;
+    uint32_t acc = 0;
+    for (int s = 0; s < SC_ITEMS; ++s) {
+        long long e = b0 + s * SC_THREADS + threadIdx.x;
+        if (e < n) acc += in[e];
+    }
+    uint32_t tot;
+    block_excl_scan(acc, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_down(const uint32_t *in, uint32_t *out, int n,
+                            const uint32_t *__restrict__ offs,
+                            uint32_t *total_dev) {
+    long long b0 = (long long)blockIdx.x * SC_TILE +
+                   (long long)threadIdx.x * SC_ITEMS;
+    uint32_t v[SC_ITEMS];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int s = 0; s < SC_ITEMS; ++s) {
+        long long e = b0 + s;
+        v[s] = e < n ? in[e] : 0;
+        acc += v[s];
+    }
+    uint32_t tot;
+    uint32_t pre = block_excl_scan(acc, &tot);
+    pre += offs ? offs[blockIdx.x] : 0;
+#pragma unroll
+    for (int s = 0; s < SC_ITEMS; ++s) {
+        long long e = b0 + s;
+        if (e < n) out[e] = pre;
+        pre += v[s];
+    }
+    if (total_dev && blockIdx.x == gridDim.x - 1 && threadIdx.x == SC_THREADS - 1)
+        *total_dev = pre;
+}
+
+size_t scan_scratch_elems(size_t n) {
+    size_t tot = 0;
+    while (n > (size_t)SC_TILE) {
+        n = (n + SC_TILE - 1) / SC_TILE;
+        tot += n;
+    }
+    return tot + 1;
+}
+
+static void scan_rec(cudaStream_t s, const uint32_t *in, uint32_t *out, int n,
+                     uint32_t *total_dev, uint32_t *tmp, int *launches) {
+    int nb = (n + SC_TILE - 1) / SC_TILE;
+    if (nb <= 1) {
+        k_scan_down<<<1, SC_THREADS, 0, s>>>(in, out, n, nullptr, total_dev);
+        *launches += 1;
+        return;
+    }
+    uint32_t *sums = tmp;
+    k_scan_reduce<<<nb, SC_THREADS, 0, s>>>(in, n, sums);
+    scan_rec(s, sums, sums, nb, nullptr, tmp + nb, launches);
+    k_scan_down<<<nb, SC_THREADS, 0, s>>>(in, out, n, sums, total_dev);
+    *launches += 2;
+}
+
+void exclusive_scan(cudaStream_t s, const uint32_t *in, uint32_t *out, int n,
+                    uint32_t *total_dev, SortScratch &sc, int *launches) {
+    if (n <= 0) {
+        if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
+        return;
+    }
+    scan_rec(s, in, out, n, total_dev, sc.scan_tmp, launches);
+}
+
+// ---------------------------------------------------------------- gather --
+__global__ void k_gather(int n, const uint32_t *__restrict__ perm, GatherList g) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t src = perm[i];
+    for (int k = 0; k < g.nd; ++k) g.dst[k][i] = g.src[k][src];
+    for (int k = 0; k < g.ni; ++k) g.idst[k][i] = g.isrc[k][src];
+}
+
+void gather_by_perm(cudaStream_t s, int n, const uint32_t *perm,
+                    const GatherList &g, int *launches) {
+    if (n <= 0) return;
+    int bs = 256;
+    k_gather<<<(n + bs - 1) / bs, bs, 0, s>>>(n, perm, g);
+    *launches += 1;
+}
+
+// ------------------------------------------------------------ cell table --
+__global__ void k_table_insert(int n, const uint64_t *__restrict__ skey,
+                               uint64_t *tkey, uint32_t *tstart,
+                               uint32_t tmask) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t k = skey[i];
+    if (i > 0 && skey[i - 1] == k) return;
+    uint32_t slot = hash_slot(k, tmask);
+    // The table holds at most n keys in 2n slots, so a free slot exists and
+    // the probe ends within tmask + 1 steps.
+    for (uint32_t it = 0; it <= tmask; ++it) {
+        unsigned long long prev = atomicCAS((unsigned long long *)&tkey[slot],
+                                            (unsigned long long)EMPTY_KEY,
+                                            (unsigned long long)k);
+        if (prev == EMPTY_KEY || prev == k) {
+            tstart[slot] = (uint32_t)i;
+            return;
+        }
+        slot = (slot + 1) & tmask;
+    }
+}
+
+__global__ void k_table_end(int n, const uint64_t *__restrict__ skey,
+                            const uint64_t *__restrict__ tkey, uint32_t *tend,
+                            uint32_t tmask) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t k = skey[i];
+    if (i + 1 < n && skey[i + 1] == k) return;
+    uint32_t slot = hash_slot(k, tmask);
+    for (uint32_t it = 0; it <= tmask; ++it) {
+        uint64_t t = tkey[slot];
+        if (t == k) {
+            tend[slot] = (uint32_t)(i + 1);
+            return;
+        }
+        if (t == EMPTY_KEY) return;
+        slot = (slot + 1) & tmask;
+    }
+}
+
+void build_cell_table(cudaStream_t s, int n, const uint64_t *skey,
+                      uint64_t *tkey, uint32_t *tstart, uint32_t *tend,
+                      uint32_t tmask, int *launches) {
+    cudaMemsetAsync(tkey, 0xff, sizeof(uint64_t) * ((size_t)tmask + 1), s);
+    if (n <= 0) return;
+    int bs = 256;
+    k_table_insert<<<(n + bs - 1) / bs, bs, 0, s>>>(n, skey, tkey, tstart, tmask);
+    k_table_end<<<(n + bs - 1) / bs, bs, 0, s>>>(n, skey, tkey, tend, tmask);
+    *launches += 2;
+}
+
+}  // namespace sph

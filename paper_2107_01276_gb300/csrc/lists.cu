@@ -1,0 +1,233 @@
+// Per-rebuild packing (levels, FP32 anchor coordinates, float mirrors) and
+// the CSR neighbour lists N(i) (definition and search in neighbors.cuh).
+//
+// List build: count (own + reverse) -> exclusive scan -> fill -> sort the
+// reverse segment of each list, so lists are deterministic: own entries in
+// traversal order, then the finer-level entries in ascending index.
+#include "lists.cuh"
+#include "neighbors.cuh"
+
+namespace sph {
+
+// ------------------------------------------------------------------ pack --
+__global__ void k_pack(PackArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    a.lev[i] = (uint8_t)(a.skey[i] >> a.lshift);
+    if (!a.mixed) return;
+    const double x = a.x[i], y = a.y[i];
+    int g[2];
+    float xl[2];
+    const double q[2] = {x, y};
+    for (int ax = 0; ax < 2; ++ax) {
+        double t = __dsub_rn(q[ax], a.lo[ax]);
+        double c = floor(__ddiv_rn(t, a.Ad[ax]));
+        int gi = c < 0.0 ? 0 : (c > (double)(a.an.n[ax] - 1) ? a.an.n[ax] - 1 : (int)c);
+        g[ax] = gi;
+        xl[ax] = (float)__dsub_rn(t, __dmul_rn((double)gi, a.Ad[ax]));
+    }
+    a.pk[i] = make_float4(xl[0], xl[1], (float)a.h[i],
+                          __uint_as_float((unsigned)g[0] | ((unsigned)g[1] << 16)));
+    a.mf[i] = (float)a.m[i];
+    a.pf[i] = (float)a.p[i];
+    a.uf[i] = (float)a.u[i];
+    a.vf[i] = (float)a.v[i];
+}
+
+// ------------------------------------------------------------ list build --
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_list_count(ListArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int li = a.lev[i];
+    const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
+    float4 pi;
+    if (MIXED) pi = a.pk[i];
+    uint32_t cnt = 0;
+    for_each_candidate(a.g, a.d, li, xi, yi, hi, [&](int j) {
+        bool in;
+        if (MIXED) {
+            float dx, dy, r2;
+            in = pred_mixed(a.d, a.an, pi, __ldg(&a.pk[j]), xi, yi, hi, a.x,
+                            a.y, a.h, j, dx, dy, r2);
+        } else {
+            in = pred_fp64(a.d, xi, yi, hi, __ldg(&a.x[j]), __ldg(&a.y[j]),
+                           __ldg(&a.h[j]));
+        }
+        if (in) {
+            ++cnt;
+            if (__ldg(&a.lev[j]) > li) atomicAdd(&a.rev[j], 1u);
+        }
+    });
+    a.own[i] = cnt;
+}
+
+__global__ void k_list_total(int n, const uint32_t *own, const uint32_t *rev,
+                             uint32_t *tot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) tot[i] = own[i] + rev[i];
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_list_fill(ListArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int li = a.lev[i];
+    const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
+    float4 pi;
+    if (MIXED) pi = a.pk[i];
+    uint32_t k = a.off[i];
+    const uint32_t cap = a.cap;
+    for_each_candidate(a.g, a.d, li, xi, yi, hi, [&](int j) {
+        bool in;
+        if (MIXED) {
+            float dx, dy, r2;
+            in = pred_mixed(a.d, a.an, pi, __ldg(&a.pk[j]), xi, yi, hi, a.x,
+                            a.y, a.h, j, dx, dy, r2);
+        } else {
+            in = pred_fp64(a.d, xi, yi, hi, __ldg(&a.x[j]), __ldg(&a.y[j]),
+                           __ldg(&a.h[j]));
+        }
+        if (in) {
+            if (k < cap) a.list[k] = (uint32_t)j;
+            ++k;
+            if (__ldg(&a.lev[j]) > li) {
+                uint32_t pos = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
+                if (pos < cap) a.list[pos] = (uint32_t)i;
+            }
+        }
+    });
+    if (i == a.n - 1 && a.off[a.n] > cap) atomicOr(a.overflow, 1);
+}
+
+// Sort of each reverse segment (ascending index).  Segments of at most 16
+// entries (the common case: only particles next to a finer level have
+// any) are sorted in registers by the particle's thread; longer ones are
+// queued for a warp-wide bitonic sort in shared memory.
+constexpr int SORT_REG = 16;
+constexpr int SORT_SMEM = 1024;
+
+__global__ void k_list_sort_rev(int n, const uint32_t *off, const uint32_t *own,
+                                uint32_t *list, uint32_t cap, uint32_t *longq,
+                                uint32_t *nlong) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t b = off[i] + own[i], e = off[i + 1];
+    if (e > cap || e <= b + 1) return;
+    const uint32_t len = e - b;
+    if (len > SORT_REG) {
+        longq[atomicAdd(nlong, 1u)] = (uint32_t)i;
+        return;
+    }
+    uint32_t r[SORT_REG];
+#pragma unroll
+    for (int t = 0; t < SORT_REG; ++t) r[t] = t < (int)len ? list[b + t] : 0xffffffffu;
+    // odd-even transposition sort, fixed indices (stays in registers)
+#pragma unroll
+    for (int round = 0; round < SORT_REG; ++round) {
+#pragma unroll
+        for (int t = round & 1; t + 1 < SORT_REG; t += 2) {
+            uint32_t lo = min(r[t], r[t + 1]), hi = max(r[t], r[t + 1]);
+            r[t] = lo;
+            r[t + 1] = hi;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < SORT_REG; ++t)
+        if (t < (int)len) list[b + t] = r[t];
+}
+
+__global__ void k_list_sort_long(const uint32_t *off, const uint32_t *own,
+                                 uint32_t *list, const uint32_t *longq,
+                                 const uint32_t *nlong) {
+    __shared__ uint32_t buf[4][SORT_SMEM];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *s = buf[w];
+    const uint32_t nq = *nlong;
+    const uint32_t gw = blockIdx.x * 4 + w, nw = gridDim.x * 4;
+    for (uint32_t q = gw; q < nq; q += nw) {
+        const uint32_t i = longq[q];
+        const uint32_t b = off[i] + own[i], e = off[i + 1];
+        const uint32_t len = e - b;
+        if (len > SORT_SMEM) {
+            // rare: plain insertion sort by one lane
+            if (lane == 0) {
+                for (uint32_t k = b + 1; k < e; ++k) {
+                    uint32_t v = list[k], m = k;
+                    while (m > b && list[m - 1] > v) {
+                        list[m] = list[m - 1];
+                        --m;
+                    }
+                    list[m] = v;
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        uint32_t P = 32;
+        while (P < len) P <<= 1;
+        for (uint32_t t = lane; t < P; t += 32) s[t] = t < len ? list[b + t] : 0xffffffffu;
+        __syncwarp();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t t = lane; t < P; t += 32) {
+                    uint32_t ixj = t ^ j;
+                    if (ixj > t) {
+                        uint32_t x0 = s[t], x1 = s[ixj];
+                        bool asc = (t & k) == 0;
+                        if ((x0 > x1) == asc) {
+                            s[t] = x1;
+                            s[ixj] = x0;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (uint32_t t = lane; t < len; t += 32) list[b + t] = s[t];
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------- launchers --
+static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
+
+void launch_pack(cudaStream_t s, const PackArgs &a) {
+    if (a.n > 0) k_pack<<<nblk(a.n, 256), 256, 0, s>>>(a);
+}
+
+void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
+                       SortScratch &sc, uint32_t *tot_tmp, int *launches) {
+    const int n = a.n;
+    if (n <= 0) {
+        cudaMemsetAsync(a.off, 0, sizeof(uint32_t), s);
+        return;
+    }
+    cudaMemsetAsync(a.rev, 0, sizeof(uint32_t) * n, s);
+    if (mixed)
+        k_list_count<true><<<nblk(n, 128), 128, 0, s>>>(a);
+    else
+        k_list_count<false><<<nblk(n, 128), 128, 0, s>>>(a);
+    k_list_total<<<nblk(n, 256), 256, 0, s>>>(n, a.own, a.rev, tot_tmp);
+    // off has n + 1 entries: scan n + 1 values with a trailing zero
+    cudaMemsetAsync(tot_tmp + n, 0, sizeof(uint32_t), s);
+    exclusive_scan(s, tot_tmp, a.off, n + 1, nullptr, sc, launches);
+    *launches += 2;
+}
+
+void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, int *launches) {
+    const int n = a.n;
+    if (n <= 0) return;
+    cudaMemsetAsync(a.rev, 0, sizeof(uint32_t) * n, s);
+    if (mixed)
+        k_list_fill<true><<<nblk(n, 128), 128, 0, s>>>(a);
+    else
+        k_list_fill<false><<<nblk(n, 128), 128, 0, s>>>(a);
+    cudaMemsetAsync(a.nlong, 0, sizeof(uint32_t), s);
+    k_list_sort_rev<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.own, a.list, a.cap,
+                                                  a.longq, a.nlong);
+    k_list_sort_long<<<152, 128, 0, s>>>(a.off, a.own, a.list, a.longq, a.nlong);
+    *launches += 3;
+}
+
+}  // namespace sph

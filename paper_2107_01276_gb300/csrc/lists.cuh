@@ -1,0 +1,46 @@
+// Argument blocks of the packing kernel and the neighbour-list build.
+#pragma once
+
+#include "neighbors.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+struct PackArgs {
+    int n;
+    int lshift;                 // 2 * mbits: level = skey >> lshift
+    int mixed;
+    const uint64_t *skey;
+    const double *x, *y, *h, *m, *p, *u, *v;
+    double lo[2], Ad[2];        // anchor origin and side (FP64)
+    Anchor an;
+    uint8_t *lev;
+    float4 *pk;                 // {xl, yl, h, gx | gy << 16}
+    float *mf, *pf, *uf, *vf;
+};
+
+struct ListArgs {
+    int n;
+    Grid g;
+    Domain d;
+    Anchor an;
+    const double *x, *y, *h;
+    const float4 *pk;
+    const uint8_t *lev;
+    uint32_t *own;              // entries found by i itself
+    uint32_t *rev;              // reverse-entry counters / cursors
+    uint32_t *off;              // n + 1 offsets
+    uint32_t *list;             // neighbour indices
+    uint32_t cap;               // list capacity (entries)
+    int *overflow;
+    uint32_t *longq, *nlong;    // particles with long reverse segments
+};
+
+void launch_pack(cudaStream_t s, const PackArgs &a);
+// Count and scan into off (n + 1 entries; tot_tmp needs n + 1), then fill
+// the lists; entries past a.cap are dropped and flag a.overflow.
+void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
+                       SortScratch &sc, uint32_t *tot_tmp, int *launches);
+void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, int *launches);
+
+}  // namespace sph

@@ -1,0 +1,382 @@
+// Gather pair loops of one right-hand-side evaluation (section 2), the PEC
+// stages (section 2.4) and the time-step reduction (Eq. timestep).
+//
+// Thread per particle over the key-sorted order: neighbouring lanes sit in
+// the same or adjacent cells, so a warp's candidate loads hit the same
+// lines.  Templated on the pair-arithmetic type R (double: FP64 path,
+// float: mixed path); positions and the neighbour predicate stay FP64.
+#include <float.h>
+
+#include "neighbors.cuh"
+#include "pair_passes.cuh"
+
+namespace sph {
+
+// Quintic spline in q (section 2, Eq. kernel) without sigma2, and its
+// q-derivative.  sigma2 = 7 / (478 pi h^2); dW/dr = sigma2 / h * dw(q).
+template <typename R>
+__device__ __forceinline__ R qs_w(R q) {
+    if (q >= R(3)) return R(0);
+    R a = R(3) - q, a2 = a * a;
+    R w = a2 * a2 * a;
+    if (q < R(2)) {
+        R b = R(2) - q, b2 = b * b;
+        w -= R(6) * (b2 * b2 * b);
+        if (q < R(1)) {
+            R c = R(1) - q, c2 = c * c;
+            w += R(15) * (c2 * c2 * c);
+        }
+    }
+    return w;
+}
+
+template <typename R>
+__device__ __forceinline__ R qs_dw(R q) {
+    if (q >= R(3)) return R(0);
+    R a = R(3) - q, a2 = a * a;
+    R w = R(-5) * (a2 * a2);
+    if (q < R(2)) {
+        R b = R(2) - q, b2 = b * b;
+        w += R(30) * (b2 * b2);
+        if (q < R(1)) {
+            R c = R(1) - q, c2 = c * c;
+            w -= R(75) * (c2 * c2);
+        }
+    }
+    return w;
+}
+
+template <typename R>
+__device__ __forceinline__ R sigma_norm() {
+    return R(7.0 / (478.0 * PI));
+}
+
+// Separation r_i - r_j of list entry j: FP64 minimum image on the FP64
+// path; on the mixed path rebuilt in FP32 from the anchor coordinates.
+template <typename R> struct Sep;
+template <> struct Sep<double> {
+    double xi, yi;
+    __device__ __forceinline__ void init(const Domain &, const double *x,
+                                         const double *y, const float4 *, int i) {
+        xi = x[i];
+        yi = y[i];
+    }
+    __device__ __forceinline__ void get(const Domain &d, const Anchor &,
+                                        const double *x, const double *y,
+                                        const float4 *, int j, double &dx,
+                                        double &dy, double &r2) const {
+        dx = min_image(d, 0, __dsub_rn(xi, __ldg(&x[j])));
+        dy = min_image(d, 1, __dsub_rn(yi, __ldg(&y[j])));
+        r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    }
+};
+template <> struct Sep<float> {
+    float4 pi;
+    __device__ __forceinline__ void init(const Domain &, const double *,
+                                         const double *, const float4 *pk, int i) {
+        pi = pk[i];
+    }
+    __device__ __forceinline__ void get(const Domain &, const Anchor &an,
+                                        const double *, const double *,
+                                        const float4 *pk, int j, float &dx,
+                                        float &dy, float &r2) const {
+        anchor_sep(an, pi, __ldg(&pk[j]), dx, dy);
+        r2 = fmaf(dx, dx, dy * dy);
+    }
+};
+
+// ---------------------------------------------------------------- pass A --
+// Summation density (Eq. sd-gather), beta (Eq. beta), p_avg (Eq. pavg,
+// N_i counts i), shift dr (Eq. shift-deltar, volume m_j / rho0, W ratio
+// against the kernel at its inflection point for h_ij = (h_i + h_j)/2),
+// limited to 0.25 h_i (Eq. shift-limit).  Also stores V_i = m_i / rho_i and
+// 1 / (rho_i^2 beta_i) for pass B.
+template <typename R>
+__global__ void __launch_bounds__(128)
+    k_pass_a(PassAArgs<R> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    Sep<R> sp;
+    sp.init(a.d, a.x, a.y, a.pk, i);
+    const R hi = (R)a.h[i];
+    const R hinv = R(1) / hi;
+    const R inv_wxi = R(1) / qs_w<R>(R(XI_INFLECTION));
+    R rho = 0, srw = 0, psum = 0, ax = 0, ay = 0;
+    const uint32_t b = a.off[i], e = a.off[i + 1];
+    for (uint32_t k = b; k < e; ++k) {
+        const int j = (int)__ldg(&a.list[k]);
+        R dx, dy, r2;
+        sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+        const R r = sqrt(r2);
+        const R mj = a.m[j];
+        const R q = r * hinv;
+        rho += mj * qs_w<R>(q);
+        srw += mj * r * qs_dw<R>(q);
+        psum += a.p[j];
+        if (j != i && r > R(0)) {
+            const R hb = R(0.5) * (hi + (R)a.h[j]);
+            const R hbinv = R(1) / hb;
+            const R qb = r * hbinv;
+            R ratio = qs_w<R>(qb) * inv_wxi;
+            ratio *= ratio;
+            const R f = mj * (R(1) + R(0.24) * ratio * ratio) *
+                        (sigma_norm<R>() * hbinv * hbinv * hbinv) *
+                        qs_dw<R>(qb) / r;
+            ax += f * dx;
+            ay += f * dy;
+        }
+    }
+    const int cnt = (int)(e - b);
+    const R sig = sigma_norm<R>() * hinv * hinv;
+    rho *= sig;
+    const R beta = -(sig * hinv * srw) / (rho * R(2));
+    R drx = R(0), dry = R(0);
+    if (beta != R(0)) {
+        const R c = R(-0.5) * hi * hi / (R)a.rho0;
+        drx = c * ax;
+        dry = c * ay;
+    }
+    const R mag = sqrt(drx * drx + dry * dry);
+    const R lim = R(0.25) * hi;
+    if (mag > lim) {
+        const R th = lim / mag;
+        drx *= th;
+        dry *= th;
+    }
+    a.rho[i] = rho;
+    a.beta[i] = beta;
+    a.pavg[i] = psum / (R)cnt;
+    a.nnb[i] = cnt;
+    a.drx[i] = drx;
+    a.dry[i] = dry;
+    a.V[i] = a.m[i] / rho;
+    a.rb2[i] = beta != R(0) ? R(1) / (rho * rho * beta) : R(0);
+}
+
+// ---------------------------------------------------------------- pass B --
+// EDAC pressure rate (Eq. edac:sph) and momentum rate (Eq. mom-sph without
+// the A_i/A_j stresses and third line, unused per the paper's remark):
+//   dp/dt = rho0 c^2/beta_i sum V_j u_ij.gW_i
+//         + 1/beta_i sum V_j nu_ij (p_i - p_j) r_ij.gW_ij / (r^2 + eta)
+//         + rho_i sum m_j (dr_i/dt).(P_i gW_i + P_j gW_j)
+//   du/dt = -sum m_j (P_i gW_i + P_j gW_j)
+//         + 1/beta_i sum m_j 4 nu/(rho_i + rho_j) r_ij.gW_ij/(r^2 + eta) u_ij
+// gW_i = grad W(r_ij, h_i), gW_ij the mean of gW_i and gW_j (Eq. dw-avg),
+// nu_ij the Cleary mean of nu_e = alpha_e c h / 8 (Eqs. edac-alpha,
+// nu-cleary), eta = 0.001 h_i^2, P_j = (p_j - p_avg,i) / (rho_j^2 beta_j).
+template <typename R>
+__global__ void __launch_bounds__(128)
+    k_pass_b(PassBArgs<R> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const R rb2i = a.rb2[i];
+    const R beta_i = a.beta[i];
+    if (beta_i == R(0)) {
+        a.dpdt[i] = R(0);
+        a.dudt[i] = R(0);
+        a.dvdt[i] = R(0);
+        return;
+    }
+    Sep<R> sp;
+    sp.init(a.d, a.x, a.y, a.pk, i);
+    const R hi = (R)a.h[i], hinv = R(1) / hi;
+    const R dsig_i = sigma_norm<R>() * hinv * hinv * hinv;
+    const R rho_i = a.rho[i], pi = a.p[i], ui = a.u[i], vi = a.v[i];
+    const R pavg_i = a.pavg[i];
+    const R Pi = (pi - pavg_i) * rb2i;
+    const R nu_i = (R)a.alpha_e * (R)a.cs * hi / R(8);
+    const R eta = R(0.001) * hi * hi;
+    const double dt = *a.dt;
+    const R dux = (R)((double)a.drx[i] / dt), duy = (R)((double)a.dry[i] / dt);
+    const R four_nu = R(4) * (R)a.nu;
+    R div = 0, diff = 0, tvf = 0, fax = 0, fay = 0, vx = 0, vy = 0;
+    const uint32_t b = a.off[i], e = a.off[i + 1];
+    for (uint32_t k = b; k < e; ++k) {
+        const int j = (int)__ldg(&a.list[k]);
+        if (j == i) continue;
+        R dx, dy, r2;
+        sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+        const R r = sqrt(r2);
+        const R hj = (R)a.h[j];
+        R gi = 0, gj = 0;
+        if (r > R(0)) {
+            const R hjinv = R(1) / hj;
+            const R rinv = R(1) / r;
+            gi = dsig_i * qs_dw<R>(r * hinv) * rinv;
+            gj = sigma_norm<R>() * hjinv * hjinv * hjinv *
+                 qs_dw<R>(r * hjinv) * rinv;
+        }
+        const R rdg = R(0.5) * (gi + gj) * r2;
+        const R mj = a.m[j], Vj = a.V[j], rho_j = a.rho[j];
+        const R uij = ui - a.u[j], vij = vi - a.v[j];
+        const R pj = a.p[j];
+        const R pref = a.pavg_mode == 0 ? pavg_i : a.pavg[j];
+        const R Pj = (pj - pref) * a.rb2[j];
+        const R nu_j = (R)a.alpha_e * (R)a.cs * hj / R(8);
+        const R nu_ij = R(4) * nu_i * nu_j / (nu_i + nu_j);
+        const R dden = a.diff_denominator ? (r2 + eta) : R(1);
+        div += Vj * (uij * gi * dx + vij * gi * dy);
+        diff += Vj * nu_ij * (pi - pj) * rdg / dden;
+        const R fx = (Pi * gi + Pj * gj) * dx;
+        const R fy = (Pi * gi + Pj * gj) * dy;
+        tvf += mj * (dux * fx + duy * fy);
+        fax -= mj * fx;
+        fay -= mj * fy;
+        const R visc = mj * (four_nu / (rho_i + rho_j)) * rdg / (r2 + eta);
+        vx += visc * uij;
+        vy += visc * vij;
+    }
+    const R rf = a.rho_factor ? rho_i : R(1);
+    const R dpdt = ((R)a.rho0 * (R)a.cs * (R)a.cs / beta_i) * div +
+                   diff / beta_i + rf * tvf;
+    const R dudt = fax + vx / beta_i;
+    const R dvdt = fay + vy / beta_i;
+    a.dpdt[i] = dpdt;
+    a.dudt[i] = dudt;
+    a.dvdt[i] = dvdt;
+    if (!isfinite((double)dpdt) || !isfinite((double)dudt) ||
+        !isfinite((double)dvdt))
+        atomicOr(a.nonfinite, 1);
+}
+
+// ---------------------------------------------------- neighbour CSR dump --
+__global__ void k_nbr_ids(int n, const uint32_t *off, const uint32_t *list,
+                          const int64_t *id, int64_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (uint32_t k = off[i]; k < off[i + 1]; ++k) out[k] = id[list[k]];
+}
+
+// ------------------------------------------------------------ PEC stages --
+// Section 2.4: u' = u0 + f dt du/dt; u~' = u' + dr/dt; r' = r0 + f dt u~';
+// p' = p0 + f dt dp/dt, with f = 1/2 (predict) or 1 (correct); FP64,
+// explicitly rounded; periodic axes wrapped back into the box.
+template <typename R>
+__global__ void k_pec(PecArgs<R> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double dt = *a.dt;
+    const double fdt = __dmul_rn(a.f, dt);
+    const double un = __dadd_rn(a.u0[i], __dmul_rn(fdt, (double)a.dudt[i]));
+    const double vn = __dadd_rn(a.v0[i], __dmul_rn(fdt, (double)a.dvdt[i]));
+    const double utx = __dadd_rn(un, __ddiv_rn((double)a.drx[i], dt));
+    const double uty = __dadd_rn(vn, __ddiv_rn((double)a.dry[i], dt));
+    double xn = __dadd_rn(a.x0[i], __dmul_rn(fdt, utx));
+    double yn = __dadd_rn(a.y0[i], __dmul_rn(fdt, uty));
+    if (a.d.periodic[0]) {
+        if (xn >= a.d.hi[0])
+            xn = __dsub_rn(xn, a.d.L[0]);
+        else if (xn < a.d.lo[0])
+            xn = __dadd_rn(xn, a.d.L[0]);
+    }
+    if (a.d.periodic[1]) {
+        if (yn >= a.d.hi[1])
+            yn = __dsub_rn(yn, a.d.L[1]);
+        else if (yn < a.d.lo[1])
+            yn = __dadd_rn(yn, a.d.L[1]);
+    }
+    a.x[i] = xn;
+    a.y[i] = yn;
+    a.u[i] = un;
+    a.v[i] = vn;
+    a.p[i] = __dadd_rn(a.p0[i], __dmul_rn(fdt, (double)a.dpdt[i]));
+}
+
+// ---------------------------------------------------------- time step ----
+// h > 0, so the IEEE bit patterns of h order like the values.
+__global__ void k_min_h(int n, const double *__restrict__ h,
+                        unsigned long long *out) {
+    unsigned long long m = ~0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += gridDim.x * blockDim.x) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(h[i]);
+        m = b < m ? b : m;
+    }
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t < m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMin(out, m);
+}
+
+// Eq. timestep: dt = min(0.25 h_min/(U + c_s), 0.125 h_min^2/nu).
+__global__ void k_dt(const unsigned long long *hmin_bits, double U, double cs,
+                     double nu, double *dt, double *tacc, int nsteps) {
+    const double hmin = __longlong_as_double((long long)*hmin_bits);
+    double v = __dmul_rn(0.25, __ddiv_rn(hmin, __dadd_rn(U, cs)));
+    if (nu > 0.0) {
+        double w = __dmul_rn(0.125, __ddiv_rn(__dmul_rn(hmin, hmin), nu));
+        if (w < v) v = w;
+    }
+    *dt = v;
+    if (tacc) {
+        for (int s = 0; s < nsteps; ++s) *tacc = __dadd_rn(*tacc, v);
+    }
+}
+
+// ---------------------------------------------------------- small utils --
+__global__ void k_reset_bbox(int *bbox, uint32_t *level_mask) {
+    int t = threadIdx.x;
+    if (t < MAX_LEVELS * 4) bbox[t] = (t & 1) ? -1 : 0x7fffffff;
+    if (t == 0) *level_mask = 0;
+}
+
+__global__ void k_to_float(int n, ConvList c) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = 0; a < c.k; ++a) c.dst[a][i] = (float)c.src[a][i];
+}
+
+__global__ void k_float_to_double(int n, const float *src, double *dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+
+// ------------------------------------------------------------- launchers --
+static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
+
+template <typename R>
+void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a) {
+    if (a.n > 0) k_pass_a<R><<<nblk(a.n, 128), 128, 0, s>>>(a);
+}
+template <typename R>
+void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a) {
+    if (a.n > 0) k_pass_b<R><<<nblk(a.n, 128), 128, 0, s>>>(a);
+}
+template <typename R>
+void launch_pec(cudaStream_t s, const PecArgs<R> &a) {
+    if (a.n > 0) k_pec<R><<<nblk(a.n, 256), 256, 0, s>>>(a);
+}
+template void launch_pass_a<double>(cudaStream_t, const PassAArgs<double> &);
+template void launch_pass_a<float>(cudaStream_t, const PassAArgs<float> &);
+template void launch_pass_b<double>(cudaStream_t, const PassBArgs<double> &);
+template void launch_pass_b<float>(cudaStream_t, const PassBArgs<float> &);
+template void launch_pec<double>(cudaStream_t, const PecArgs<double> &);
+template void launch_pec<float>(cudaStream_t, const PecArgs<float> &);
+
+void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,
+                    const uint32_t *list, const int64_t *id, int64_t *out) {
+    if (n > 0) k_nbr_ids<<<nblk(n, 128), 128, 0, s>>>(n, off, list, id, out);
+}
+void launch_dt(cudaStream_t s, int n, const double *h,
+               unsigned long long *hmin_bits, double U, double cs, double nu,
+               double *dt, double *tacc, int nsteps) {
+    cudaMemsetAsync(hmin_bits, 0xff, sizeof(unsigned long long), s);
+    int blocks = nblk(n, 256);
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    k_min_h<<<blocks, 256, 0, s>>>(n, h, hmin_bits);
+    k_dt<<<1, 1, 0, s>>>(hmin_bits, U, cs, nu, dt, tacc, nsteps);
+}
+void launch_reset_bbox(cudaStream_t s, int *bbox, uint32_t *level_mask) {
+    k_reset_bbox<<<1, MAX_LEVELS * 4, 0, s>>>(bbox, level_mask);
+}
+void launch_to_float(cudaStream_t s, int n, const ConvList &c) {
+    if (n > 0 && c.k > 0) k_to_float<<<nblk(n, 256), 256, 0, s>>>(n, c);
+}
+void launch_float_to_double(cudaStream_t s, int n, const float *src,
+                            double *dst) {
+    if (n > 0) k_float_to_double<<<nblk(n, 256), 256, 0, s>>>(n, src, dst);
+}
+
+}  // namespace sph

@@ -1,0 +1,71 @@
+// Argument blocks and launchers of the pair passes, PEC stages and
+// time-step reduction (pair_passes.cu).
+#pragma once
+
+#include "neighbors.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+template <typename R>
+struct PassAArgs {
+    int n;
+    Domain d;
+    Anchor an;
+    const uint32_t *off, *list;  // CSR neighbour lists
+    const float4 *pk;          // anchor coordinates (mixed path)
+    const double *x, *y, *h;   // FP64 positions and smoothing lengths
+    const R *m, *p;            // pair-arithmetic copies
+    double rho0;
+    R *rho, *beta, *pavg, *drx, *dry, *V, *rb2;
+    int *nnb;
+};
+
+template <typename R>
+struct PassBArgs {
+    int n;
+    Domain d;
+    Anchor an;
+    const uint32_t *off, *list;
+    const float4 *pk;
+    const double *x, *y, *h;
+    const R *m, *p, *u, *v;
+    const R *rho, *beta, *pavg, *drx, *dry, *V, *rb2;
+    const double *dt;          // device scalar
+    double rho0, cs, nu, alpha_e;
+    int pavg_mode, diff_denominator, rho_factor;
+    R *dpdt, *dudt, *dvdt;
+    int *nonfinite;
+};
+
+template <typename R>
+struct PecArgs {
+    int n;
+    Domain d;
+    double f;                  // 0.5 predict, 1.0 correct
+    const double *dt;
+    const double *x0, *y0, *u0, *v0, *p0;
+    const R *dudt, *dvdt, *dpdt, *drx, *dry;
+    double *x, *y, *u, *v, *p;
+};
+
+struct ConvList {
+    const double *src[8];
+    float *dst[8];
+    int k;
+};
+
+template <typename R> void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a);
+template <typename R> void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a);
+template <typename R> void launch_pec(cudaStream_t s, const PecArgs<R> &a);
+void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,
+                    const uint32_t *list, const int64_t *id, int64_t *out);
+void launch_dt(cudaStream_t s, int n, const double *h,
+               unsigned long long *hmin_bits, double U, double cs, double nu,
+               double *dt, double *tacc, int nsteps);
+void launch_reset_bbox(cudaStream_t s, int *bbox, uint32_t *level_mask);
+void launch_to_float(cudaStream_t s, int n, const ConvList &c);
+void launch_float_to_double(cudaStream_t s, int n, const float *src,
+                            double *dst);
+
+}  // namespace sph

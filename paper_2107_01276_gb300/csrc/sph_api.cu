@@ -1,0 +1,900 @@
+// Host orchestration and C ABI (include/sph.h) of the GB300 adaptive WCSPH
+// library.  Everything numerical is enqueued on the context's stream as
+// the library's own kernels; the host only validates, sizes launches and
+// moves buffers.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lists.cuh"
+#include "pair_passes.cuh"
+#include "sph_internal.cuh"
+
+using namespace sph;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Timer {
+    std::vector<cudaEvent_t> pool;       // free events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> open[5];
+    double ms[5] = {0, 0, 0, 0, 0};
+    long long count[5] = {0, 0, 0, 0, 0};
+};
+
+}  // namespace
+
+// Fields gathered by a rebuild (index into sph_ctx::f / ::falt).
+enum {
+    F_X = 0, F_Y, F_U, F_V, F_P, F_RHO, F_M, F_H, F_MMIN, F_MMAX,
+    F_X0, F_Y0, F_U0, F_V0, F_P0, NF
+};
+
+struct sph_ctx {
+    sph_params prm;
+    cudaStream_t s = nullptr;
+    std::string err;
+    long long cap = 0;
+    int n = 0;
+    Domain dom;
+    double c0 = 0.0;
+    int lmax = 0, mbits = 1, lbits = 0;
+    Level lev[MAX_LEVELS];
+
+    double *f[NF] = {};      // FP64 state, current (sorted) order
+    double *falt[NF] = {};   // gather targets, swapped with f
+    int64_t *id = nullptr, *id_alt = nullptr;
+
+    // pair-pass outputs and mirrors, sized for doubles (floats use half)
+    void *rhoR = nullptr, *beta = nullptr, *pavg = nullptr, *drx = nullptr,
+         *dry = nullptr, *V = nullptr, *rb2 = nullptr, *dpdt = nullptr,
+         *dudt = nullptr, *dvdt = nullptr;
+    float *mf = nullptr, *pf = nullptr, *uf = nullptr, *vf = nullptr;
+    int *nnb = nullptr;
+
+    // neighbour structure
+    uint64_t *skey = nullptr;
+    uint32_t *perm = nullptr;
+    SortScratch sc;
+    uint64_t *tkey = nullptr;
+    uint32_t *tstart = nullptr, *tend = nullptr;
+    uint32_t tcap = 0, tmask = 0;
+    int *bbox = nullptr;
+    uint32_t *level_mask = nullptr;
+    uint32_t *cnt_tmp = nullptr;   // n + 1 scratch (list totals)
+    // neighbour lists and packed per-particle data
+    uint8_t *lvl = nullptr;       // level of each particle (sorted order)
+    float4 *pk = nullptr;
+    uint32_t *own = nullptr, *rev = nullptr, *off = nullptr, *list = nullptr;
+    size_t list_cap = 0;
+    int *d_overflow = nullptr;
+    uint32_t *longq = nullptr, *d_nlong = nullptr;
+    Anchor an;
+    double anchor_A[2] = {0, 0};
+
+    // device scalars
+    double *d_dt = nullptr, *d_t = nullptr;
+    unsigned long long *d_hmin = nullptr;
+    int *d_nonfinite = nullptr;
+    uint32_t *d_total = nullptr;
+
+    bool grid_valid = false, rhs_valid = false, have_dt = false;
+    long long steps = 0;
+    int launches = 0;
+    bool timing = false;
+    Timer tm;
+};
+
+// ------------------------------------------------------------- helpers --
+static sph_status fail(sph_ctx *c, sph_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+static sph_status cuda_check(sph_ctx *c, const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(c, SPH_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return SPH_OK;
+}
+
+template <typename T>
+static bool dalloc(T **p, size_t elems) {
+    if (elems == 0) elems = 1;
+    return cudaMalloc((void **)p, elems * sizeof(T)) == cudaSuccess;
+}
+
+static bool is_mixed(const sph_ctx *c) { return c->prm.precision == SPH_MIXED; }
+
+static void t_begin(sph_ctx *c, int fam, cudaEvent_t *ev) {
+    *ev = nullptr;
+    if (!c->timing) return;
+    if (c->tm.pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->tm.pool.push_back(e);
+    }
+    *ev = c->tm.pool.back();
+    c->tm.pool.pop_back();
+    cudaEventRecord(*ev, c->s);
+    (void)fam;
+}
+
+static void t_end(sph_ctx *c, int fam, cudaEvent_t ev0) {
+    if (!c->timing || !ev0) return;
+    cudaEvent_t e1;
+    if (c->tm.pool.empty()) {
+        cudaEventCreate(&e1);
+    } else {
+        e1 = c->tm.pool.back();
+        c->tm.pool.pop_back();
+    }
+    cudaEventRecord(e1, c->s);
+    c->tm.open[fam].push_back({ev0, e1});
+}
+
+static void t_collect(sph_ctx *c) {
+    for (int f = 0; f < 5; ++f) {
+        for (auto &pr : c->tm.open[f]) {
+            float ms = 0.f;
+            cudaEventSynchronize(pr.second);
+            cudaEventElapsedTime(&ms, pr.first, pr.second);
+            c->tm.ms[f] += ms;
+            c->tm.count[f] += 1;
+            c->tm.pool.push_back(pr.first);
+            c->tm.pool.push_back(pr.second);
+        }
+        c->tm.open[f].clear();
+    }
+}
+
+static int bits_for(long long v) {   // bits to represent 0..v
+    int b = 0;
+    while ((1ll << b) <= v) ++b;
+    return b;
+}
+
+static Grid make_grid(const sph_ctx *c) {
+    Grid g;
+    g.tkey = c->tkey;
+    g.tstart = c->tstart;
+    g.tend = c->tend;
+    g.tmask = c->tmask;
+    g.level_mask = 0;   // filled by caller from device copy? (see rebuild)
+    g.mbits = c->mbits;
+    g.nlev = c->lmax + 1;
+    g.bbox = c->bbox;
+    for (int l = 0; l < MAX_LEVELS; ++l) g.lev[l] = c->lev[l];
+    return g;
+}
+
+// The occupied-level mask lives on the device; pair kernels read it
+// through the Grid by value, so the host fetches it once per rebuild.
+// To avoid that synchronisation every level up to lmax is queried; empty
+// levels cost one bounding-box test (their box is empty).
+static Grid grid_for_kernels(const sph_ctx *c) {
+    Grid g = make_grid(c);
+    g.level_mask = (c->lmax >= 31) ? 0xffffffffu : ((1u << (c->lmax + 1)) - 1u);
+    return g;
+}
+
+// ---------------------------------------------------------- the rebuild --
+// Keys, stable sort, gather of the state in sorted order, cell table and
+// (mixed path) float mirrors.  mid_step: also carry the PEC stage-start
+// copies x0..p0.
+static ListArgs list_args(sph_ctx *c) {
+    ListArgs la;
+    la.n = c->n;
+    la.g = grid_for_kernels(c);
+    la.d = c->dom;
+    la.an = c->an;
+    la.x = c->f[F_X];
+    la.y = c->f[F_Y];
+    la.h = c->f[F_H];
+    la.pk = c->pk;
+    la.lev = c->lvl;
+    la.own = c->own;
+    la.rev = c->rev;
+    la.off = c->off;
+    la.list = c->list;
+    la.cap = (uint32_t)std::min<size_t>(c->list_cap, 0xffffffffu);
+    la.overflow = c->d_overflow;
+    la.longq = c->longq;
+    la.nlong = c->d_nlong;
+    return la;
+}
+
+// exact: read the list total back (one synchronisation) and grow the list
+// buffer before filling; otherwise entries past the capacity are dropped
+// and flagged, and the flag is checked at the next synchronising call.
+static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
+    const int n = c->n;
+    cudaEvent_t ev;
+    t_begin(c, 2, &ev);
+    launch_reset_bbox(c->s, c->bbox, c->level_mask);
+    launch_keys(c->s, n, c->dom, c->c0, c->lmax, c->mbits, c->lev, c->f[F_X],
+                c->f[F_Y], c->f[F_H], c->skey, c->perm, c->level_mask, c->bbox);
+    c->launches += 2;
+    radix_sort(c->s, n, 2 * c->mbits + c->lbits, c->skey, c->perm, c->sc,
+               &c->launches);
+    GatherList gl;
+    memset(&gl, 0, sizeof(gl));
+    int last = mid_step ? NF : F_X0;
+    for (int k = 0; k < last; ++k) {
+        gl.src[gl.nd] = c->f[k];
+        gl.dst[gl.nd] = c->falt[k];
+        gl.nd++;
+    }
+    gl.isrc[0] = c->id;
+    gl.idst[0] = c->id_alt;
+    gl.ni = 1;
+    gather_by_perm(c->s, n, c->perm, gl, &c->launches);
+    for (int k = 0; k < last; ++k) std::swap(c->f[k], c->falt[k]);
+    std::swap(c->id, c->id_alt);
+    // table of 2n..4n slots (power of two)
+    uint32_t t = 1;
+    while (t < 2u * (uint32_t)std::max(n, 1)) t <<= 1;
+    c->tmask = t - 1;
+    build_cell_table(c->s, n, c->skey, c->tkey, c->tstart, c->tend, c->tmask,
+                     &c->launches);
+    PackArgs pa;
+    pa.n = n;
+    pa.lshift = 2 * c->mbits;
+    pa.mixed = is_mixed(c) ? 1 : 0;
+    pa.skey = c->skey;
+    pa.x = c->f[F_X];
+    pa.y = c->f[F_Y];
+    pa.h = c->f[F_H];
+    pa.m = c->f[F_M];
+    pa.p = c->f[F_P];
+    pa.u = c->f[F_U];
+    pa.v = c->f[F_V];
+    for (int ax = 0; ax < 2; ++ax) {
+        pa.lo[ax] = c->dom.lo[ax];
+        pa.Ad[ax] = c->anchor_A[ax];
+    }
+    pa.an = c->an;
+    pa.lev = c->lvl;
+    pa.pk = c->pk;
+    pa.mf = c->mf;
+    pa.pf = c->pf;
+    pa.uf = c->uf;
+    pa.vf = c->vf;
+    launch_pack(c->s, pa);
+    c->launches += 1;
+    ListArgs la = list_args(c);
+    build_lists_count(c->s, la, is_mixed(c), c->sc, c->cnt_tmp, &c->launches);
+    if (exact && n > 0) {
+        uint32_t total = 0;
+        cudaMemcpyAsync(&total, c->off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "rebuild sync");
+        if ((size_t)total > c->list_cap) {
+            size_t want = (size_t)total + total / 2 + 1024;
+            if (want > 0xffffffffull) want = 0xffffffffull;
+            if ((size_t)total > want)
+                return fail(c, SPH_ECAPACITY, "neighbour lists exceed 2^32 entries");
+            cudaFree(c->list);
+            c->list = nullptr;
+            if (!dalloc(&c->list, want)) {
+                cudaGetLastError();
+                c->list_cap = 0;
+                return fail(c, SPH_ENOMEM, "neighbour list allocation failed");
+            }
+            c->list_cap = want;
+            la = list_args(c);
+        }
+    }
+    build_lists_fill(c->s, la, is_mixed(c), &c->launches);
+    t_end(c, 2, ev);
+    c->grid_valid = true;
+    c->rhs_valid = false;
+    return cuda_check(c, "rebuild");
+}
+
+// Mixed path: refresh float mirrors of the fields PEC changed without a
+// rebuild in between (not needed: every RHS follows a rebuild).
+
+template <typename R>
+static void passes(sph_ctx *c) {
+    PassAArgs<R> a;
+    a.n = c->n;
+    a.d = c->dom;
+    a.an = c->an;
+    a.off = c->off;
+    a.list = c->list;
+    a.pk = c->pk;
+    a.x = c->f[F_X];
+    a.y = c->f[F_Y];
+    a.h = c->f[F_H];
+    if (sizeof(R) == sizeof(double)) {
+        a.m = (const R *)c->f[F_M];
+        a.p = (const R *)c->f[F_P];
+    } else {
+        a.m = (const R *)c->mf;
+        a.p = (const R *)c->pf;
+    }
+    a.rho0 = c->prm.rho0;
+    a.rho = (R *)c->rhoR;
+    a.beta = (R *)c->beta;
+    a.pavg = (R *)c->pavg;
+    a.drx = (R *)c->drx;
+    a.dry = (R *)c->dry;
+    a.V = (R *)c->V;
+    a.rb2 = (R *)c->rb2;
+    a.nnb = c->nnb;
+    cudaEvent_t ev;
+    t_begin(c, 1, &ev);
+    launch_pass_a<R>(c->s, a);
+    t_end(c, 1, ev);
+
+    PassBArgs<R> b;
+    b.n = c->n;
+    b.d = c->dom;
+    b.an = c->an;
+    b.off = c->off;
+    b.list = c->list;
+    b.pk = c->pk;
+    b.x = a.x;
+    b.y = a.y;
+    b.h = a.h;
+    b.m = a.m;
+    b.p = a.p;
+    if (sizeof(R) == sizeof(double)) {
+        b.u = (const R *)c->f[F_U];
+        b.v = (const R *)c->f[F_V];
+    } else {
+        b.u = (const R *)c->uf;
+        b.v = (const R *)c->vf;
+    }
+    b.rho = a.rho;
+    b.beta = a.beta;
+    b.pavg = a.pavg;
+    b.drx = a.drx;
+    b.dry = a.dry;
+    b.V = a.V;
+    b.rb2 = a.rb2;
+    b.dt = c->d_dt;
+    b.rho0 = c->prm.rho0;
+    b.cs = c->prm.cs;
+    b.nu = c->prm.nu;
+    b.alpha_e = c->prm.alpha_e;
+    b.pavg_mode = c->prm.pavg_mode;
+    b.diff_denominator = c->prm.edac_diff_denominator;
+    b.rho_factor = c->prm.edac_rho_factor;
+    b.dpdt = (R *)c->dpdt;
+    b.dudt = (R *)c->dudt;
+    b.dvdt = (R *)c->dvdt;
+    b.nonfinite = c->d_nonfinite;
+    t_begin(c, 0, &ev);
+    launch_pass_b<R>(c->s, b);
+    t_end(c, 0, ev);
+    c->launches += 2;
+}
+
+static void run_passes(sph_ctx *c) {
+    if (is_mixed(c))
+        passes<float>(c);
+    else
+        passes<double>(c);
+}
+
+template <typename R>
+static void pec(sph_ctx *c, double f) {
+    PecArgs<R> a;
+    a.n = c->n;
+    a.d = c->dom;
+    a.f = f;
+    a.dt = c->d_dt;
+    a.x0 = c->f[F_X0];
+    a.y0 = c->f[F_Y0];
+    a.u0 = c->f[F_U0];
+    a.v0 = c->f[F_V0];
+    a.p0 = c->f[F_P0];
+    a.dudt = (const R *)c->dudt;
+    a.dvdt = (const R *)c->dvdt;
+    a.dpdt = (const R *)c->dpdt;
+    a.drx = (const R *)c->drx;
+    a.dry = (const R *)c->dry;
+    a.x = c->f[F_X];
+    a.y = c->f[F_Y];
+    a.u = c->f[F_U];
+    a.v = c->f[F_V];
+    a.p = c->f[F_P];
+    cudaEvent_t ev;
+    t_begin(c, 3, &ev);
+    launch_pec<R>(c->s, a);
+    t_end(c, 3, ev);
+    c->launches += 1;
+}
+
+static void run_pec(sph_ctx *c, double f) {
+    if (is_mixed(c))
+        pec<float>(c, f);
+    else
+        pec<double>(c, f);
+}
+
+// Latest summation density into the FP64 state (density is recomputed,
+// never integrated).
+static void store_rho(sph_ctx *c) {
+    if (is_mixed(c)) {
+        launch_float_to_double(c->s, c->n, (const float *)c->rhoR, c->f[F_RHO]);
+        c->launches += 1;
+    } else {
+        cudaMemcpyAsync(c->f[F_RHO], c->rhoR, sizeof(double) * c->n,
+                        cudaMemcpyDeviceToDevice, c->s);
+    }
+}
+
+static void compute_dt(sph_ctx *c, double *tacc, int nsteps) {
+    launch_dt(c->s, c->n, c->f[F_H], c->d_hmin, c->prm.U_ref, c->prm.cs,
+              c->prm.nu, c->d_dt, tacc, nsteps);
+    c->launches += 2;
+    c->have_dt = true;
+}
+
+static void free_ctx(sph_ctx *c) {
+    for (int k = 0; k < NF; ++k) {
+        cudaFree(c->f[k]);
+        cudaFree(c->falt[k]);
+    }
+    void *ps[] = {c->id, c->id_alt, c->rhoR, c->beta, c->pavg, c->drx,
+                  c->dry, c->V, c->rb2, c->dpdt, c->dudt, c->dvdt, c->mf,
+                  c->pf, c->uf, c->vf, c->nnb, c->skey, c->perm,
+                  c->sc.key_alt, c->sc.val_alt, c->sc.counts, c->sc.scan_tmp,
+                  c->tkey, c->tstart, c->tend, c->bbox, c->level_mask,
+                  c->cnt_tmp, c->d_dt, c->d_t, c->d_hmin, c->d_nonfinite,
+                  c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
+                  c->d_overflow, c->longq, c->d_nlong};
+    for (void *p : ps) cudaFree(p);
+    for (auto e : c->tm.pool) cudaEventDestroy(e);
+    for (int f = 0; f < 5; ++f)
+        for (auto &pr : c->tm.open[f]) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+}
+
+// ================================================================ C ABI ==
+extern "C" {
+
+void sph_default_params(sph_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->dim = 2;
+    p->lo[0] = p->lo[1] = 0.0;
+    p->hi[0] = p->hi[1] = 1.0;
+    p->rho0 = 1.0;
+    p->cs = 10.0;
+    p->nu = 0.0;
+    p->U_ref = 1.0;
+    p->hdx = 1.0;
+    p->alpha_e = 1.5;
+    p->split_alpha = 0.9;
+    p->split_eps = 0.4;
+    p->Cr = 1.08;
+    p->merge_iters = 3;
+    p->shift_iters = 3;
+    p->precision = SPH_FP64;
+    p->capacity = 0;
+    p->pavg_mode = 0;
+    p->edac_diff_denominator = 1;
+    p->edac_rho_factor = 1;
+    p->cell_c0 = 0.0;
+}
+
+sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
+    if (out) *out = nullptr;
+    if (!p || !out) {
+        g_create_error = "sph_create: NULL argument";
+        return SPH_EINVAL;
+    }
+    std::string why;
+    if (p->dim != 2) why = "dim must be 2";
+    else if (!(p->hi[0] > p->lo[0]) || !(p->hi[1] > p->lo[1])) why = "empty domain box";
+    else if (p->capacity <= 0 || p->capacity > (1ll << 30)) why = "capacity must be in 1..2^30";
+    else if (!(p->rho0 > 0) || !(p->cs > 0) || !(p->hdx > 0)) why = "rho0, cs, hdx must be positive";
+    else if (!(p->nu >= 0)) why = "nu must be >= 0";
+    else if (!(p->U_ref >= 0)) why = "U_ref must be >= 0";
+    else if (p->precision != SPH_FP64 && p->precision != SPH_MIXED) why = "bad precision";
+    else if (p->pavg_mode < 0 || p->pavg_mode > 1) why = "bad pavg_mode";
+    if (!why.empty()) {
+        g_create_error = "sph_create: " + why;
+        return SPH_EINVAL;
+    }
+    sph_ctx *c = new sph_ctx();
+    c->prm = *p;
+    c->s = (cudaStream_t)stream;
+    c->cap = p->capacity;
+    for (int a = 0; a < 2; ++a) {
+        c->dom.lo[a] = p->lo[a];
+        c->dom.hi[a] = p->hi[a];
+        c->dom.L[a] = p->hi[a] - p->lo[a];
+        c->dom.half[a] = 0.5 * c->dom.L[a];
+        c->dom.periodic[a] = p->periodic[a] ? 1 : 0;
+    }
+    const size_t N = (size_t)c->cap;
+    bool ok = true;
+    for (int k = 0; k < NF; ++k) ok = ok && dalloc(&c->f[k], N) && dalloc(&c->falt[k], N);
+    ok = ok && dalloc(&c->id, N) && dalloc(&c->id_alt, N);
+    double **rs[] = {(double **)&c->rhoR, (double **)&c->beta, (double **)&c->pavg,
+                     (double **)&c->drx, (double **)&c->dry, (double **)&c->V,
+                     (double **)&c->rb2, (double **)&c->dpdt, (double **)&c->dudt,
+                     (double **)&c->dvdt};
+    for (auto pp : rs) ok = ok && dalloc(pp, N);
+    ok = ok && dalloc(&c->mf, N) && dalloc(&c->pf, N) && dalloc(&c->uf, N) &&
+         dalloc(&c->vf, N) && dalloc(&c->nnb, N);
+    ok = ok && dalloc(&c->skey, N) && dalloc(&c->perm, N) &&
+         dalloc(&c->sc.key_alt, N) && dalloc(&c->sc.val_alt, N);
+    size_t tiles = (N + 2047) / 2048;
+    c->sc.counts_cap = 256 * tiles;
+    c->sc.scan_cap = scan_scratch_elems(std::max(c->sc.counts_cap, N + 1));
+    ok = ok && dalloc(&c->sc.counts, c->sc.counts_cap) &&
+         dalloc(&c->sc.scan_tmp, c->sc.scan_cap);
+    uint32_t t = 1;
+    while (t < 2u * (uint32_t)N) t <<= 1;
+    c->tcap = t;
+    ok = ok && dalloc(&c->tkey, t) && dalloc(&c->tstart, t) && dalloc(&c->tend, t);
+    ok = ok && dalloc(&c->bbox, MAX_LEVELS * 4) && dalloc(&c->level_mask, 1) &&
+         dalloc(&c->cnt_tmp, N + 1);
+    ok = ok && dalloc(&c->d_dt, 1) && dalloc(&c->d_t, 1) && dalloc(&c->d_hmin, 1) &&
+         dalloc(&c->d_nonfinite, 1) && dalloc(&c->d_total, 1) &&
+         dalloc(&c->d_overflow, 1);
+    ok = ok && dalloc(&c->lvl, N) && dalloc(&c->pk, N) && dalloc(&c->own, N) &&
+         dalloc(&c->rev, N) && dalloc(&c->off, N + 1) &&
+         dalloc(&c->longq, N) && dalloc(&c->d_nlong, 1);
+    c->list_cap = std::min<size_t>(N * 48, 0xffffffffull);
+    ok = ok && dalloc(&c->list, c->list_cap);
+    if (!ok) {
+        cudaGetLastError();
+        free_ctx(c);
+        delete c;
+        g_create_error = "sph_create: device allocation failed";
+        return SPH_ENOMEM;
+    }
+    cudaMemsetAsync(c->d_t, 0, sizeof(double), c->s);
+    cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->s);
+    cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
+    if (cudaGetLastError() != cudaSuccess) {
+        free_ctx(c);
+        delete c;
+        g_create_error = "sph_create: CUDA error";
+        return SPH_ECUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
+                              const sph_particles *src) {
+    if (!c) return SPH_EINVAL;
+    c->err.clear();
+    if (kind != SPH_FLUID)
+        return fail(c, SPH_EINVAL, "sph_load_particles: only SPH_FLUID is supported");
+    if (n < 0 || (n > 0 && !src)) return fail(c, SPH_EINVAL, "sph_load_particles: bad n or src");
+    if (n > c->cap) return fail(c, SPH_ECAPACITY, "sph_load_particles: n exceeds capacity");
+    if (n > 0 && (!src->x || !src->y || !src->m || !src->h))
+        return fail(c, SPH_EINVAL, "sph_load_particles: x, y, m, h are required");
+    double hmin = INFINITY;
+    for (long long i = 0; i < n; ++i) {
+        double h = src->h[i], m = src->m[i];
+        if (!(h > 0) || !isfinite(h) || !(m > 0) || !isfinite(m))
+            return fail(c, SPH_EINVAL, "sph_load_particles: h and m must be positive and finite");
+        hmin = std::min(hmin, h);
+        for (int a = 0; a < 2; ++a) {
+            double q = a == 0 ? src->x[i] : src->y[i];
+            bool in = c->dom.periodic[a] ? (q >= c->dom.lo[a] && q < c->dom.hi[a])
+                                         : (q >= c->dom.lo[a] && q <= c->dom.hi[a]);
+            if (!in || !isfinite(q))
+                return fail(c, SPH_EINVAL, "sph_load_particles: position outside the box");
+        }
+    }
+    // level-0 cell side
+    double c0 = c->prm.cell_c0;
+    if (!(c0 > 0)) c0 = c->prm.ds_min > 0 ? 3.0 * c->prm.hdx * c->prm.ds_min : 3.0 * hmin;
+    if (n == 0 && !(c0 > 0)) c0 = std::max(c->dom.L[0], c->dom.L[1]);
+    double Lmax = std::max(c->dom.L[0], c->dom.L[1]);
+    int lmax = 0;
+    while (ldexp(c0, lmax) < Lmax) ++lmax;
+    if (lmax >= MAX_LEVELS)
+        return fail(c, SPH_EINVAL, "sph_load_particles: domain spans too many cell levels");
+    Level lev[MAX_LEVELS];
+    compute_levels(c->dom, c0, lev);
+    long long nmax = std::max(lev[0].n[0], lev[0].n[1]);
+    if (nmax >= (1ll << MAX_MORTON_BITS))
+        return fail(c, SPH_EINVAL, "sph_load_particles: level-0 grid too fine for the domain");
+    double hmax = 0.0;
+    for (long long i = 0; i < n; ++i) hmax = std::max(hmax, src->h[i]);
+    for (int a = 0; a < 2; ++a)
+        if (c->dom.periodic[a] && !(3.0 * hmax < 0.5 * c->dom.L[a]))
+            return fail(c, SPH_EINVAL,
+                        "sph_load_particles: 3 h_max must be below half a periodic period");
+    // anchor lattice of the FP32 separations: side ~ c0, at most 65535 cells
+    Anchor an;
+    double Ad[2];
+    for (int a = 0; a < 2; ++a) {
+        double L = c->dom.L[a];
+        long long na;
+        if (c->dom.periodic[a]) {
+            na = std::max(1ll, (long long)floor(L / c0));
+            if (na > 65535) na = 65535;
+            Ad[a] = L / (double)na;
+        } else {
+            Ad[a] = std::max(c0, L / 65535.0);
+            na = std::max(1ll, (long long)ceil(L / Ad[a]));
+            if (na > 65535) na = 65535;
+        }
+        an.A[a] = (float)Ad[a];
+        an.n[a] = (int)na;
+        an.periodic[a] = c->dom.periodic[a];
+    }
+    c->an = an;
+    c->anchor_A[0] = Ad[0];
+    c->anchor_A[1] = Ad[1];
+    c->c0 = c0;
+    c->lmax = lmax;
+    memcpy(c->lev, lev, sizeof(lev));
+    c->mbits = std::max(1, bits_for(nmax - 1));
+    c->lbits = bits_for(lmax);
+    c->n = (int)n;
+
+    std::vector<double> tmp;
+    auto put = [&](double *dst, const double *s, double dflt) {
+        if (n == 0) return;
+        if (s) {
+            cudaMemcpyAsync(dst, s, sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
+        } else {
+            tmp.assign((size_t)n, dflt);
+            cudaMemcpyAsync(dst, tmp.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
+            cudaStreamSynchronize(c->s);
+        }
+    };
+    put(c->f[F_X], src ? src->x : nullptr, 0);
+    put(c->f[F_Y], src ? src->y : nullptr, 0);
+    put(c->f[F_U], src ? src->u : nullptr, 0);
+    put(c->f[F_V], src ? src->v : nullptr, 0);
+    put(c->f[F_P], src ? src->p : nullptr, 0);
+    put(c->f[F_RHO], src ? src->rho : nullptr, c->prm.rho0);
+    put(c->f[F_M], src ? src->m : nullptr, 0);
+    put(c->f[F_H], src ? src->h : nullptr, 0);
+    put(c->f[F_MMIN], src ? src->mmin : nullptr, 0);
+    put(c->f[F_MMAX], src ? src->mmax : nullptr, 0);
+    if (n > 0) {
+        if (src->id) {
+            cudaMemcpyAsync(c->id, src->id, sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
+        } else {
+            std::vector<int64_t> ids((size_t)n);
+            for (long long i = 0; i < n; ++i) ids[i] = i;
+            cudaMemcpyAsync(c->id, ids.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
+            cudaStreamSynchronize(c->s);
+        }
+    }
+    cudaStreamSynchronize(c->s);
+    c->grid_valid = c->rhs_valid = c->have_dt = false;
+    return cuda_check(c, "sph_load_particles");
+}
+
+sph_status sph_rhs(sph_ctx *c) {
+    if (!c) return SPH_EINVAL;
+    c->err.clear();
+    if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_rhs: no fluid particles loaded");
+    compute_dt(c, nullptr, 0);
+    sph_status st = rebuild(c, false);
+    if (st != SPH_OK) return st;
+    run_passes(c);
+    store_rho(c);
+    c->rhs_valid = true;
+    return cuda_check(c, "sph_rhs");
+}
+
+sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
+    if (!c) return SPH_EINVAL;
+    c->err.clear();
+    if (nsteps < 0) return fail(c, SPH_EINVAL, "sph_step: nsteps < 0");
+    if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_step: no fluid particles loaded");
+    const size_t bytes = sizeof(double) * c->n;
+    for (int s = 0; s < nsteps; ++s) {
+        compute_dt(c, c->d_t, 1);
+        sph_status st = rebuild(c, false, s == 0);
+        if (st != SPH_OK) return st;
+        cudaMemcpyAsync(c->f[F_X0], c->f[F_X], bytes, cudaMemcpyDeviceToDevice, c->s);
+        cudaMemcpyAsync(c->f[F_Y0], c->f[F_Y], bytes, cudaMemcpyDeviceToDevice, c->s);
+        cudaMemcpyAsync(c->f[F_U0], c->f[F_U], bytes, cudaMemcpyDeviceToDevice, c->s);
+        cudaMemcpyAsync(c->f[F_V0], c->f[F_V], bytes, cudaMemcpyDeviceToDevice, c->s);
+        cudaMemcpyAsync(c->f[F_P0], c->f[F_P], bytes, cudaMemcpyDeviceToDevice, c->s);
+        run_passes(c);
+        run_pec(c, 0.5);
+        st = rebuild(c, true, false);
+        if (st != SPH_OK) return st;
+        run_passes(c);
+        run_pec(c, 1.0);
+        store_rho(c);
+        c->grid_valid = false;   // positions moved since the last rebuild
+        c->rhs_valid = true;     // rates of the n+1/2 evaluation, current order
+        c->steps += 1;
+    }
+    sph_status st = cuda_check(c, "sph_step");
+    if (st != SPH_OK) return st;
+    if (t_out) {
+        double t = 0;
+        int bad = 0, ovf = 0;
+        cudaMemcpyAsync(&t, c->d_t, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+        cudaMemcpyAsync(&bad, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+        cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_step sync");
+        *t_out = t;
+        if (ovf) {
+            cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
+            return fail(c, SPH_ECAPACITY, "sph_step: neighbour list overflow during the steps");
+        }
+        if (bad) return fail(c, SPH_ENONFINITE, "sph_step: non-finite rate");
+    }
+    return SPH_OK;
+}
+
+static sph_status read_R(sph_ctx *c, const void *src, double *dst, long long n) {
+    if (is_mixed(c)) {
+        std::vector<float> tmp((size_t)n);
+        cudaMemcpyAsync(tmp.data(), src, sizeof(float) * n, cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
+        for (long long i = 0; i < n; ++i) dst[i] = tmp[i];
+    } else {
+        cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
+    }
+    return SPH_OK;
+}
+
+sph_status sph_read(sph_ctx *c, sph_field field, void *dst, long long cap,
+                    long long *n_out) {
+    if (!c) return SPH_EINVAL;
+    c->err.clear();
+    if (!dst && cap > 0) return fail(c, SPH_EINVAL, "sph_read: dst is NULL");
+    const long long n = c->n;
+    auto need = [&](long long k) -> sph_status {
+        if (n_out) *n_out = k;
+        if (cap < k) return fail(c, SPH_ECAPACITY, "sph_read: buffer too small");
+        return SPH_OK;
+    };
+    sph_status st;
+    switch (field) {
+    case SPH_F_X: case SPH_F_Y: case SPH_F_U: case SPH_F_V: case SPH_F_P:
+    case SPH_F_RHO: case SPH_F_M: case SPH_F_H: case SPH_F_MMIN:
+    case SPH_F_MMAX: {
+        static const int map[] = {F_X, F_Y, F_U, F_V, F_P, F_RHO, F_M, F_H, F_MMIN, F_MMAX};
+        if ((st = need(n)) != SPH_OK) return st;
+        cudaMemcpyAsync(dst, c->f[map[field]], sizeof(double) * n, cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
+        return SPH_OK;
+    }
+    case SPH_F_ID:
+        if ((st = need(n)) != SPH_OK) return st;
+        cudaMemcpyAsync(dst, c->id, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
+        return SPH_OK;
+    case SPH_F_BETA: case SPH_F_PAVG: case SPH_F_DRX: case SPH_F_DRY:
+    case SPH_F_DPDT: case SPH_F_DUDT: case SPH_F_DVDT: {
+        if (!c->rhs_valid) return fail(c, SPH_ESTATE, "sph_read: no right-hand side at this state");
+        if ((st = need(n)) != SPH_OK) return st;
+        const void *srcs[] = {c->beta, c->pavg, c->drx, c->dry, c->dpdt, c->dudt, c->dvdt};
+        return read_R(c, srcs[field - SPH_F_BETA], (double *)dst, n);
+    }
+    case SPH_F_NNB:
+        if (!c->rhs_valid) return fail(c, SPH_ESTATE, "sph_read: no right-hand side at this state");
+        if ((st = need(n)) != SPH_OK) return st;
+        cudaMemcpyAsync(dst, c->nnb, sizeof(int) * n, cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
+        return SPH_OK;
+    case SPH_F_CELLKEY: {
+        if (!c->grid_valid) {
+            if ((st = rebuild(c, false)) != SPH_OK) return st;
+        }
+        if ((st = need(n)) != SPH_OK) return st;
+        uint64_t *o = (uint64_t *)dst;
+        cudaMemcpyAsync(o, c->skey, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
+        const int sh = 2 * c->mbits;
+        const uint64_t mask = (sh >= 64) ? ~0ull : ((1ull << sh) - 1ull);
+        for (long long i = 0; i < n; ++i) o[i] = ((o[i] >> sh) << 58) | (o[i] & mask);
+        return SPH_OK;
+    }
+    case SPH_F_NEIGH_OFF: case SPH_F_NEIGH_ID: {
+        if (n == 0) {
+            if (field == SPH_F_NEIGH_OFF) {
+                if ((st = need(1)) != SPH_OK) return st;
+                ((int64_t *)dst)[0] = 0;
+            } else if (n_out) {
+                *n_out = 0;
+            }
+            return SPH_OK;
+        }
+        if (!c->grid_valid) {
+            if ((st = rebuild(c, false)) != SPH_OK) return st;
+        }
+        std::vector<uint32_t> off((size_t)n + 1);
+        int ovf = 0;
+        cudaMemcpyAsync(off.data(), c->off, sizeof(uint32_t) * (n + 1), cudaMemcpyDeviceToHost, c->s);
+        cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
+        if (ovf) return fail(c, SPH_ECAPACITY, "sph_read: neighbour list overflow");
+        const uint32_t total = off[n];
+        if (field == SPH_F_NEIGH_OFF) {
+            if ((st = need(n + 1)) != SPH_OK) return st;
+            int64_t *o = (int64_t *)dst;
+            for (long long i = 0; i <= n; ++i) o[i] = off[i];
+            return SPH_OK;
+        }
+        if ((st = need(total)) != SPH_OK) return st;
+        int64_t *dev = nullptr;
+        if (cudaMalloc((void **)&dev, sizeof(int64_t) * std::max<uint32_t>(total, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, SPH_ENOMEM, "sph_read: neighbour list allocation failed");
+        }
+        launch_nbr_ids(c->s, c->n, c->off, c->list, c->id, dev);
+        c->launches += 1;
+        cudaMemcpyAsync(dst, dev, sizeof(int64_t) * total, cudaMemcpyDeviceToHost, c->s);
+        cudaError_t e = cudaStreamSynchronize(c->s);
+        cudaFree(dev);
+        if (e != cudaSuccess) return cuda_check(c, "sph_read");
+        return SPH_OK;
+    }
+    default:
+        return fail(c, SPH_EINVAL, "sph_read: unknown field");
+    }
+}
+
+sph_status sph_get_info(sph_ctx *c, sph_info *out) {
+    if (!c || !out) return SPH_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->n = c->n;
+    double t = 0, dt = 0;
+    cudaMemcpyAsync(&t, c->d_t, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    if (c->have_dt) cudaMemcpyAsync(&dt, c->d_dt, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_get_info");
+    out->t = t;
+    out->dt = dt;
+    out->c0 = c->c0;
+    out->levels = c->lmax + 1;
+    out->steps = c->steps;
+    out->launches = c->launches;
+    return SPH_OK;
+}
+
+sph_status sph_set_timing(sph_ctx *c, int enable) {
+    if (!c) return SPH_EINVAL;
+    c->timing = enable != 0;
+    return SPH_OK;
+}
+
+sph_status sph_kernel_time(sph_ctx *c, int family, double *ms,
+                           long long *launches, int reset) {
+    if (!c || family < 0 || family > 4) return SPH_EINVAL;
+    t_collect(c);
+    if (ms) *ms = c->tm.ms[family];
+    if (launches) *launches = c->tm.count[family];
+    if (reset) {
+        c->tm.ms[family] = 0;
+        c->tm.count[family] = 0;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_destroy(sph_ctx *c) {
+    if (!c) return SPH_EINVAL;
+    cudaStreamSynchronize(c->s);
+    free_ctx(c);
+    delete c;
+    return SPH_OK;
+}
+
+const char *sph_last_error(const sph_ctx *c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Internal declarations shared by the library's CUDA translation units.
+// Adaptive-resolution WCSPH (Muta & Ramachandran, arXiv 2107.01276) on
+// sm_103a.  Nothing here is part of the public C ABI (include/sph.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+constexpr int MAX_LEVELS = 32;      // cell levels c0 * 2^l, l < MAX_LEVELS
+constexpr int MAX_MORTON_BITS = 29; // per axis
+constexpr double PI = 3.14159265358979323846;
+// Point of inflection of the quintic spline in q (section 2.1).
+constexpr double XI_INFLECTION = 0.759298480738450;
+
+// ---------------------------------------------------------------- domain --
+struct Domain {
+    double lo[2], hi[2], L[2], half[2];
+    int periodic[2];
+};
+
+// One level of the multi-level cell grid.
+struct Level {
+    double c;      // nominal cell side c0 * 2^l (>= 3h of its particles)
+    double w[2];   // cell width per axis (L / count on periodic axes)
+    int n[2];      // cell count per axis
+};
+
+// Device view of the cell structure built by a rebuild.  Particles are
+// sorted by skey = level << (2*mbits) | morton(ix, iy); every occupied cell
+// has one entry in an open-addressing hash table (key -> [start, end)).
+struct Grid {
+    const uint64_t *tkey;   // hash slots, EMPTY = ~0
+    const uint32_t *tstart;
+    const uint32_t *tend;
+    uint32_t tmask;         // table size - 1 (power of two)
+    uint32_t level_mask;    // bit l set if level l is occupied
+    int mbits;              // morton bits per axis
+    int nlev;               // levels in use (top level = nlev - 1)
+    const int *bbox;        // per level: min ix, max ix, min iy, max iy
+    Level lev[MAX_LEVELS];
+};
+
+constexpr uint64_t EMPTY_KEY = ~0ull;
+
+__host__ __device__ inline uint64_t spread2(uint64_t v) {
+    v &= 0x1fffffffull;
+    v = (v | (v << 16)) & 0x0000ffff0000ffffull;
+    v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
+    v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+
+__host__ __device__ inline uint32_t hash_slot(uint64_t k, uint32_t mask) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return (uint32_t)k & mask;
+}
+
+// Minimum-image separation component, FP64, no contraction.
+__device__ __forceinline__ double min_image(const Domain &d, int a,
+                                            double s) {
+    if (d.periodic[a]) {
+        if (s > d.half[a])
+            s = __dsub_rn(s, d.L[a]);
+        else if (s < -d.half[a])
+            s = __dadd_rn(s, d.L[a]);
+    }
+    return s;
+}
+
+// ------------------------------------------------------------- context --
+struct DeviceState;  // defined in sph_api.cu
+
+// Radix sort + scan scratch owned by the context.
+struct SortScratch {
+    uint64_t *key_alt = nullptr;
+    uint32_t *val_alt = nullptr;
+    uint32_t *counts = nullptr;   // 256 * tiles
+    uint32_t *scan_tmp = nullptr; // recursive scan block sums
+    size_t counts_cap = 0, scan_cap = 0;
+};
+
+// Launch helpers implemented in keys_sort.cu
+// Cell widths and counts of every level (host, FP64; same expressions as
+// the level definition in the keys kernel).
+void compute_levels(const Domain &dom, double c0, Level *lev);
+void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
+                 int lmax, int mbits, const Level *lev, const double *x,
+                 const double *y, const double *h, uint64_t *skey,
+                 uint32_t *perm, uint32_t *level_mask, int *bbox);
+// Stable LSD radix sort of (skey, perm) over the low `bits` bits.
+void radix_sort(cudaStream_t s, int n, int bits, uint64_t *key,
+                uint32_t *val, SortScratch &sc, int *launches);
+// Exclusive scan of n uint32 values (in may equal out); *total_dev (if not
+// NULL) receives the sum.
+void exclusive_scan(cudaStream_t s, const uint32_t *in, uint32_t *out,
+                    int n, uint32_t *total_dev, SortScratch &sc,
+                    int *launches);
+size_t scan_scratch_elems(size_t n);
+void build_cell_table(cudaStream_t s, int n, const uint64_t *skey,
+                      uint64_t *tkey, uint32_t *tstart, uint32_t *tend,
+                      uint32_t tmask, int *launches);
+// out[k][i] = in[k][perm[i]] for up to 16 double arrays and 2 int64 arrays.
+struct GatherList {
+    const double *src[16];
+    double *dst[16];
+    int nd;
+    const int64_t *isrc[2];
+    int64_t *idst[2];
+    int ni;
+};
+void gather_by_perm(cudaStream_t s, int n, const uint32_t *perm,
+                    const GatherList &g, int *launches);
+
+}  // namespace sph

@@ -1,0 +1,257 @@
+"""Python binding of the C ABI in include/sph.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``libsph_gb300.so``; this
+module converts numpy arrays to pointers, calls the C functions by the same
+names, and turns status codes into exceptions.  There is no fallback: if
+the library is missing or cannot load, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_ECAPACITY, SPH_ENONFINITE, \
+    SPH_ETIMEOUT, SPH_ESTATE = range(8)
+STATUS_NAMES = ["SPH_OK", "SPH_EINVAL", "SPH_ENOMEM", "SPH_ECUDA",
+                "SPH_ECAPACITY", "SPH_ENONFINITE", "SPH_ETIMEOUT",
+                "SPH_ESTATE"]
+SPH_FLUID, SPH_WALL, SPH_BACKGROUND = 0, 1, 2
+SPH_FP64, SPH_MIXED = 0, 1
+
+FIELDS = ["x", "y", "u", "v", "p", "rho", "m", "h", "mmin", "mmax", "id",
+          "beta", "pavg", "drx", "dry", "dpdt", "dudt", "dvdt", "nnb",
+          "cellkey", "neigh_off", "neigh_id"]
+FIELD = {k: i for i, k in enumerate(FIELDS)}
+_FIELD_DTYPE = {"id": np.int64, "nnb": np.int32, "cellkey": np.uint64,
+                "neigh_off": np.int64, "neigh_id": np.int64}
+
+TIMER_PASS_B, TIMER_PASS_A, TIMER_REBUILD, TIMER_PEC, TIMER_ADAPT = range(5)
+
+
+class SphError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8
+                                     else status, msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2),
+        ("periodic", ctypes.c_int * 2),
+        ("rho0", ctypes.c_double), ("cs", ctypes.c_double),
+        ("nu", ctypes.c_double), ("U_ref", ctypes.c_double),
+        ("hdx", ctypes.c_double), ("alpha_e", ctypes.c_double),
+        ("split_alpha", ctypes.c_double), ("split_eps", ctypes.c_double),
+        ("Cr", ctypes.c_double), ("ds_min", ctypes.c_double),
+        ("ds_max", ctypes.c_double),
+        ("merge_iters", ctypes.c_int), ("shift_iters", ctypes.c_int),
+        ("precision", ctypes.c_int), ("capacity", ctypes.c_longlong),
+        ("pavg_mode", ctypes.c_int), ("edac_diff_denominator", ctypes.c_int),
+        ("edac_rho_factor", ctypes.c_int), ("cell_c0", ctypes.c_double),
+    ]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+class Particles(ctypes.Structure):
+    _fields_ = [(k, _D) for k in ("x", "y", "u", "v", "p", "rho", "m", "h",
+                                  "mmin", "mmax", "ds")] + [
+        ("id", ctypes.POINTER(ctypes.c_int64))]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_longlong), ("n_wall", ctypes.c_longlong),
+                ("n_bg", ctypes.c_longlong), ("t", ctypes.c_double),
+                ("dt", ctypes.c_double), ("c0", ctypes.c_double),
+                ("levels", ctypes.c_int), ("steps", ctypes.c_longlong),
+                ("launches", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Load libsph_gb300.so (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise OSError("libsph_gb300.so not built: %s" % path)
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    ctx = ctypes.c_void_p
+    L.sph_default_params.restype = None
+    L.sph_default_params.argtypes = [P(Params)]
+    L.sph_create.restype = ctypes.c_int
+    L.sph_create.argtypes = [P(Params), ctypes.c_void_p, P(ctx)]
+    L.sph_load_particles.restype = ctypes.c_int
+    L.sph_load_particles.argtypes = [ctx, ctypes.c_int, ctypes.c_longlong,
+                                     P(Particles)]
+    L.sph_rhs.restype = ctypes.c_int
+    L.sph_rhs.argtypes = [ctx]
+    L.sph_step.restype = ctypes.c_int
+    L.sph_step.argtypes = [ctx, ctypes.c_int, _D]
+    L.sph_read.restype = ctypes.c_int
+    L.sph_read.argtypes = [ctx, ctypes.c_int, ctypes.c_void_p,
+                           ctypes.c_longlong, P(ctypes.c_longlong)]
+    L.sph_get_info.restype = ctypes.c_int
+    L.sph_get_info.argtypes = [ctx, P(Info)]
+    L.sph_set_timing.restype = ctypes.c_int
+    L.sph_set_timing.argtypes = [ctx, ctypes.c_int]
+    L.sph_kernel_time.restype = ctypes.c_int
+    L.sph_kernel_time.argtypes = [ctx, ctypes.c_int, _D,
+                                  P(ctypes.c_longlong), ctypes.c_int]
+    L.sph_destroy.restype = ctypes.c_int
+    L.sph_destroy.argtypes = [ctx]
+    L.sph_last_error.restype = ctypes.c_char_p
+    L.sph_last_error.argtypes = [ctx]
+    _lib = L
+    return L
+
+
+def declared_functions():
+    """Names of the functions include/sph.h declares."""
+    txt = open(os.path.join(_build.INCLUDE, "sph.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sph_[a-z_0-9]+)\s*\(", txt)))
+
+
+def make_params(d: dict, precision: int = SPH_FP64, capacity: int = 0,
+                **over) -> Params:
+    """sph_params from a workload's parameter dict (unknown keys ignored)."""
+    P = Params()
+    lib().sph_default_params(ctypes.byref(P))
+    d = dict(d)
+    d.update(over)
+    for k, v in d.items():
+        if k in ("lo", "hi"):
+            getattr(P, k)[:] = [float(a) for a in v]
+        elif k == "periodic":
+            P.periodic[:] = [int(a) for a in v]
+        elif k in dict(Params._fields_):
+            t = dict(Params._fields_)[k]
+            setattr(P, k, int(v) if t in (ctypes.c_int, ctypes.c_longlong)
+                    else float(v))
+    P.precision = int(precision)
+    P.capacity = int(capacity)
+    return P
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Simulation:
+    """One sph_ctx.  ``stream`` is a cudaStream_t handle (int), 0 for the
+    legacy default stream."""
+
+    def __init__(self, params: Params, stream: int = 0):
+        self._L = lib()
+        self._ctx = ctypes.c_void_p()
+        st = self._L.sph_create(ctypes.byref(params),
+                                ctypes.c_void_p(int(stream)),
+                                ctypes.byref(self._ctx))
+        if st != SPH_OK:
+            raise SphError(st, self._L.sph_last_error(None).decode())
+        self.params = params
+        self._keep = []
+
+    def _check(self, st):
+        if st != SPH_OK:
+            raise SphError(st, self._L.sph_last_error(self._ctx).decode())
+
+    def load(self, particles: dict, kind: int = SPH_FLUID):
+        n = len(particles["x"])
+        src = Particles()
+        keep = []
+        for k in ("x", "y", "u", "v", "p", "rho", "m", "h", "mmin", "mmax",
+                  "ds"):
+            if k in particles and particles[k] is not None:
+                a = _f64(particles[k])
+                keep.append(a)
+                setattr(src, k, a.ctypes.data_as(_D))
+        if "id" in particles and particles["id"] is not None:
+            a = np.ascontiguousarray(particles["id"], dtype=np.int64)
+            keep.append(a)
+            src.id = a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        self._check(self._L.sph_load_particles(self._ctx, int(kind), n,
+                                               ctypes.byref(src)))
+
+    def load_raw(self, kind: int, n: int, src: Particles):
+        """sph_load_particles with a caller-built Particles block (pinned
+        host buffers for end-to-end timing)."""
+        self._check(self._L.sph_load_particles(self._ctx, int(kind), int(n),
+                                               ctypes.byref(src)))
+
+    def rhs(self):
+        self._check(self._L.sph_rhs(self._ctx))
+
+    def step(self, nsteps: int = 1, want_time: bool = True):
+        t = ctypes.c_double(0.0)
+        self._check(self._L.sph_step(self._ctx, int(nsteps),
+                                     ctypes.byref(t) if want_time else None))
+        return t.value if want_time else None
+
+    def read(self, field: str) -> np.ndarray:
+        f = FIELD[field]
+        dt = _FIELD_DTYPE.get(field, np.float64)
+        n = ctypes.c_longlong(0)
+        st = self._L.sph_read(self._ctx, f, None, 0, ctypes.byref(n))
+        if st not in (SPH_OK, SPH_ECAPACITY):
+            self._check(st)
+        out = np.zeros(max(n.value, 1), dtype=dt)
+        self._check(self._L.sph_read(self._ctx, f,
+                                     out.ctypes.data_as(ctypes.c_void_p),
+                                     out.size, ctypes.byref(n)))
+        return out[:n.value]
+
+    def read_into(self, field: str, out: np.ndarray) -> int:
+        n = ctypes.c_longlong(0)
+        self._check(self._L.sph_read(self._ctx, FIELD[field],
+                                     out.ctypes.data_as(ctypes.c_void_p),
+                                     out.size, ctypes.byref(n)))
+        return n.value
+
+    def info(self) -> dict:
+        i = Info()
+        self._check(self._L.sph_get_info(self._ctx, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def set_timing(self, on: bool):
+        self._check(self._L.sph_set_timing(self._ctx, 1 if on else 0))
+
+    def kernel_time(self, family: int, reset: bool = False):
+        ms = ctypes.c_double(0)
+        cnt = ctypes.c_longlong(0)
+        self._check(self._L.sph_kernel_time(self._ctx, family,
+                                            ctypes.byref(ms),
+                                            ctypes.byref(cnt), int(reset)))
+        return ms.value, cnt.value
+
+    def close(self):
+        if self._ctx:
+            self._L.sph_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -11,9 +11,10 @@ Workloads (all synthetic; the paper's runs use no external data set):
                     initial condition of section 4.1 (Eq. tgv_sol at t = 0).
   perturbed      -- lattice with position jitter and a smooth h variation,
                     for parity at sizes the oracle finishes in seconds.
-  graded_strip   -- periodic strip whose spacing varies geometrically over
-                    a 1:ratio range (the pair-kernel sweep), tent-shaped so
-                    the spacing is continuous across the periodic wrap.
+  graded_strip   -- periodic square whose column spacing grows by the
+                    paper's layer ratio C_r from a fine core to 1:ratio (the
+                    pair-kernel sweep), symmetric so the spacing is
+                    continuous across the periodic wrap.
 """
 from __future__ import annotations
 
@@ -93,41 +94,66 @@ def perturbed(nx: int = 40, ny: int = 32, L: float = 1.0, hdx: float = 1.2,
     return dict(particles=parts, params=params, dx=dx)
 
 
+def _graded_columns(d_min, ratio, Cr, L):
+    """Column spacings of a symmetric graded strip: spacing d_min in a core
+    of 8 columns at x = L/2, growing by Cr per column to ratio*d_min, then
+    constant out to both (periodic) ends."""
+    d_max = ratio * d_min
+    half = [d_min] * 4
+    d = d_min
+    while d < d_max:
+        d = min(d * Cr, d_max)
+        half.append(d)
+    width = sum(half)
+    if width > 0.5 * L:
+        raise ValueError("grading does not fit the domain")
+    n_out = max(1, int(round((0.5 * L - width) / d_max)))
+    half += [d_max] * n_out
+    cols = half[::-1] + half            # coarse ... fine fine ... coarse
+    x = np.cumsum([0.0] + cols[:-1])
+    x = x * (L / sum(cols))
+    w = np.array(cols) * (L / sum(cols))
+    return x, w
+
+
 def graded_strip(n_target: int = 1 << 20, ratio: float = 250.0,
-                 hdx: float = 1.2, rho0: float = 1.0, cs: float = 10.0,
-                 nu: float = 0.0, seed: int = 4):
-    """Periodic square [0, L)^2 of columns whose spacing grows
-    geometrically from dx_min at x = L/2 to ratio*dx_min at x = 0 and L
-    (a tent, continuous across the wrap).  Column k holds round(L/dx_k)
-    particles at spacing L/ny_k.  h = hdx*dx, m = rho0*dx*dy; u, v ~
-    N(0, 0.1); rho = rho0 (1 + U(-0.01, 0.01)); p = rho0 cs^2 (rho/rho0 - 1).
-    L is chosen so the particle count is close to n_target."""
+                 Cr: float = 1.08, hdx: float = 1.2, rho0: float = 1.0,
+                 cs: float = 10.0, nu: float = 0.0, seed: int = 4):
+    """Periodic unit square of columns whose spacing grows geometrically,
+    by Cr from one column to the next (the paper's layer ratio, section
+    3.3), from dx_min in a core at x = L/2 to ratio*dx_min, then stays
+    constant to x = 0 and L.  Column k holds round(L/dx_k) particles at
+    spacing L/ny_k.  h = hdx*sqrt(dx dy), m = rho0*dx*dy; u, v ~ N(0, 0.1);
+    rho = rho0 (1 + U(-0.01, 0.01)); p = rho0 cs^2 (rho/rho0 - 1).  dx_min
+    is chosen so the particle count is close to n_target."""
     rng = np.random.default_rng(seed)
     L = 1.0
-    # particle count for dx_min = 1: N(L) ~ 2 * int_0^{L/2} L / dx(x)^2 dx
-    # with dx(x) = ratio^(1 - 2x/L); solve for the scale that gives n_target
-    lr = math.log(ratio)
-    # int_0^{L/2} ratio^(-2(1-2x/L)) dx = L/(4 lr) (1 - ratio^-2)
-    est = 2.0 * L * L / (4.0 * lr) * (1.0 - ratio ** -2)
-    dx_min = math.sqrt(est / n_target)
-    xs, dxs = [], []
-    xpos = 0.0
-    while xpos < L:
-        t = abs(2.0 * xpos / L - 1.0)      # 1 at the ends, 0 at the middle
-        d = dx_min * ratio ** t
-        xs.append(xpos)
-        dxs.append(d)
-        xpos += d
-    # stretch column positions so the last gap closes the period exactly
-    xs = np.array(xs) * (L / xpos)
-    dxs = np.array(dxs) * (L / xpos)
+
+    def count(dmin):
+        try:
+            x, w = _graded_columns(dmin, ratio, Cr, L)
+        except ValueError:
+            return None
+        return int(sum(max(1, int(round(L / d))) for d in w))
+
+    lo, hi = 1e-7, 1.0 / (2.0 * ratio)
+    while count(hi) is None:
+        hi *= 0.7
+    for _ in range(60):
+        mid = math.sqrt(lo * hi)
+        c = count(mid)
+        if c is None or c < n_target:
+            hi = mid
+        else:
+            lo = mid
+    dx_min = lo if count(lo) is not None else hi
+    xs, ws = _graded_columns(dx_min, ratio, Cr, L)
     cx, cy, cdx, cdy = [], [], [], []
-    for xc, d in zip(xs, dxs):
+    for xc, d in zip(xs, ws):
         ny = max(1, int(round(L / d)))
         dy = L / ny
-        yy = (np.arange(ny) + 0.5) * dy
         cx.append(np.full(ny, xc + 0.5 * d))
-        cy.append(yy)
+        cy.append((np.arange(ny) + 0.5) * dy)
         cdx.append(np.full(ny, d))
         cdy.append(np.full(ny, dy))
     x = np.concatenate(cx) % L
@@ -144,7 +170,7 @@ def graded_strip(n_target: int = 1 << 20, ratio: float = 250.0,
                  h=hdx * s)
     params = _base_params(lo=(0.0, 0.0), hi=(L, L), periodic=(1, 1),
                           rho0=rho0, cs=cs, nu=nu, U_ref=1.0, hdx=hdx,
-                          ds_min=float(s.min()))
+                          ds_min=float(s.min()), Cr=Cr)
     return dict(particles=parts, params=params, dx_min=float(s.min()))
 
 

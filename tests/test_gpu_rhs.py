@@ -1,0 +1,197 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle for the
+neighbour structure, one right-hand side and PEC steps."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_01276_gb300 import sph
+from paper_2107_01276_gb300 import workloads as wl
+from tests.helpers import (FP64_TOL, MIXED_TOL, by_id, cuda_ok, norm,
+                           neighbour_sets_by_id, stream_handle)
+
+pytestmark = pytest.mark.gpu
+
+RHS_FIELDS = ("rho", "beta", "pavg", "drx", "dry", "dpdt", "dudt", "dvdt")
+
+
+def _sim(d, precision, cap=None, **over):
+    n = len(d["particles"]["x"])
+    P = sph.make_params(d["params"], precision=precision,
+                        capacity=cap or max(n, 1), **over)
+    sim = sph.Simulation(P, stream_handle())
+    sim.load(d["particles"])
+    return sim
+
+
+def _oracle_rhs(d, dt):
+    P = oracle.params(**d["params"])
+    st = oracle.make_state(d["particles"])
+    return oracle.rhs(P, dt, st)
+
+
+CASES = {
+    "tgv_jitter": lambda: wl.taylor_green(nx=40, jitter=0.2, seed=3),
+    "perturbed_periodic": lambda: wl.perturbed(nx=44, ny=37, h_ratio=3.0,
+                                               seed=5),
+    "perturbed_open": lambda: wl.perturbed(nx=41, ny=29, h_ratio=6.0,
+                                           periodic=(0, 0), seed=6),
+    "perturbed_mixed_bc": lambda: wl.perturbed(nx=35, ny=31, h_ratio=2.0,
+                                               periodic=(1, 0), seed=7),
+    "graded_1_16": lambda: wl.graded_strip(n_target=6000, ratio=16.0),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not cuda_ok():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_cell_keys_bit_exact(case):
+    d = CASES[case]()
+    sim = _sim(d, sph.SPH_FP64)
+    sim.rhs()                       # rebuild now, so later reads keep order
+    got = by_id(sim, ["cellkey"])
+    c0 = sim.info()["c0"]
+    P = oracle.params(**d["params"])
+    key, lev = oracle.cell_keys(P, c0, d["particles"]["x"],
+                                d["particles"]["y"], d["particles"]["h"])
+    assert np.array_equal(got["cellkey"], key)
+    # stored order is sorted by key
+    raw = sim.read("cellkey")
+    assert np.all(raw[1:] >= raw[:-1])
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_neighbour_sets_bit_exact(case):
+    d = CASES[case]()
+    sim = _sim(d, sph.SPH_FP64)
+    sim.rhs()
+    sets = neighbour_sets_by_id(sim)
+    pt = d["particles"]
+    P = oracle.params(**d["params"])
+    off, nbr = oracle.neighbors(P, pt["x"], pt["y"], pt["h"])
+    assert len(sets) == len(pt["x"])
+    for i in range(len(pt["x"])):
+        assert np.array_equal(sets[i], nbr[off[i]:off[i + 1]]), i
+
+
+@pytest.mark.parametrize("precision,tol", [(sph.SPH_FP64, FP64_TOL),
+                                           (sph.SPH_MIXED, MIXED_TOL)])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_rhs_parity(case, precision, tol):
+    d = CASES[case]()
+    sim = _sim(d, precision)
+    sim.rhs()
+    got = by_id(sim, list(RHS_FIELDS) + ["nnb"])
+    dt = oracle.dt(oracle.params(**d["params"]), d["particles"]["h"])
+    ref = _oracle_rhs(d, dt)
+    assert np.array_equal(got["nnb"], ref["nnb"])
+    for f in RHS_FIELDS:
+        e = norm(got[f], ref[f], ref["s_" + f])
+        assert e <= tol, (f, e)
+
+
+def test_rhs_parity_literal_pavg_and_switches():
+    d = wl.perturbed(nx=30, ny=30, h_ratio=2.0, seed=9)
+    for over in (dict(pavg_mode=1), dict(edac_diff_denominator=0),
+                 dict(edac_rho_factor=0)):
+        dd = dict(d, params=dict(d["params"], **over))
+        sim = _sim(dd, sph.SPH_FP64)
+        sim.rhs()
+        got = by_id(sim, list(RHS_FIELDS))
+        dt = oracle.dt(oracle.params(**dd["params"]), d["particles"]["h"])
+        ref = _oracle_rhs(dd, dt)
+        for f in RHS_FIELDS:
+            assert norm(got[f], ref[f], ref["s_" + f]) <= FP64_TOL, (over, f)
+
+
+@pytest.mark.parametrize("precision,tol", [(sph.SPH_FP64, 1e-10),
+                                           (sph.SPH_MIXED, 1e-4)])
+def test_pec_steps_parity(precision, tol):
+    """Ten PEC steps of the jittered Taylor-Green vortex: state after the
+    steps against the oracle's, relative to each field's magnitude."""
+    d = wl.taylor_green(nx=32, jitter=0.1, seed=2, Re=100)
+    sim = _sim(d, precision)
+    t = sim.step(10)
+    got = by_id(sim, ["x", "y", "u", "v", "p", "rho"])
+    P = oracle.params(**d["params"])
+    st = oracle.make_state(d["particles"])
+    tr = oracle.step(P, st, 10)
+    assert abs(t - tr) <= 1e-15 * tr
+    n = st["n"]
+    L = 1.0
+    for f in ("x", "y"):
+        dxy = got[f] - st[f][:n]
+        dxy -= L * np.round(dxy / L)
+        assert np.abs(dxy).max() <= tol * d["dx"], f
+    for f in ("u", "v", "p", "rho"):
+        scale = max(np.abs(st[f][:n]).max(), 1e-30)
+        assert np.abs(got[f] - st[f][:n]).max() <= tol * scale, f
+
+
+@pytest.mark.parametrize("precision", [sph.SPH_FP64, sph.SPH_MIXED])
+def test_taylor_green_decay_on_gpu(precision):
+    """50x50 Taylor-Green vortex at Re 100, 200 PEC steps: max |u| follows
+    exp(-8 pi^2 t / Re) within 1 % (section 4.1, Eq. tgv_sol)."""
+    d = wl.taylor_green(nx=50, Re=100)
+    sim = _sim(d, precision)
+    u0 = np.hypot(d["particles"]["u"], d["particles"]["v"]).max()
+    t = sim.step(200)
+    u = np.hypot(sim.read("u"), sim.read("v")).max()
+    assert abs((u / u0) / math.exp(-8 * math.pi ** 2 * t / 100.0) - 1) < 0.01
+
+
+def test_edge_cases():
+    d = wl.taylor_green(nx=10)
+    P = sph.make_params(d["params"], capacity=100)
+    sim = sph.Simulation(P, stream_handle())
+    # empty set: valid load, but no right-hand side
+    sim.load({k: v[:0] for k, v in d["particles"].items()})
+    with pytest.raises(sph.SphError) as e:
+        sim.rhs()
+    assert e.value.status == sph.SPH_ESTATE
+    assert len(sim.read("x")) == 0
+    assert list(sim.read("neigh_off")) == [0]
+    # over capacity
+    big = wl.taylor_green(nx=11)["particles"]
+    with pytest.raises(sph.SphError) as e:
+        sim.load(big)
+    assert e.value.status == sph.SPH_ECAPACITY
+    # outside the box
+    bad = dict(d["particles"], x=d["particles"]["x"] + 2.0)
+    with pytest.raises(sph.SphError) as e:
+        sim.load(bad)
+    assert e.value.status == sph.SPH_EINVAL
+    # a lone particle: density m W(0, h), beta 0, no shift, zero rates
+    one = {k: v[:1].copy() for k, v in d["particles"].items()}
+    sim.load(one)
+    sim.rhs()
+    rho = sim.read("rho")[0]
+    assert rho == pytest.approx(one["m"][0] * float(oracle.W(0.0, one["h"][0])),
+                                rel=1e-14)
+    assert sim.read("beta")[0] == 0.0
+    for f in ("drx", "dry", "dpdt", "dudt", "dvdt"):
+        assert sim.read(f)[0] == 0.0
+    sim.close()
+
+
+def test_ragged_sizes_and_repeat_determinism():
+    """Sizes that leave partial tiles in every kernel; two evaluations of
+    the same state give bit-identical results."""
+    for nx, ny in ((23, 21), (33, 31), (47, 45)):
+        d = wl.perturbed(nx=nx, ny=ny, h_ratio=2.0, seed=nx)
+        sim = _sim(d, sph.SPH_FP64)
+        sim.rhs()
+        a = by_id(sim, list(RHS_FIELDS))
+        sim.rhs()
+        b = by_id(sim, list(RHS_FIELDS))
+        for f in RHS_FIELDS:
+            assert np.array_equal(a[f], b[f])
+        dt = oracle.dt(oracle.params(**d["params"]), d["particles"]["h"])
+        ref = _oracle_rhs(d, dt)
+        for f in RHS_FIELDS:
+            assert norm(a[f], ref[f], ref["s_" + f]) <= FP64_TOL
