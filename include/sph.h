@@ -181,6 +181,41 @@ sph_status sph_set_timing(sph_ctx *ctx, int enable);
 sph_status sph_kernel_time(sph_ctx *ctx, int family, double *ms,
                            long long *launches, int reset);
 
+/* Cell keys and stable sort of a particle set, allocating nothing.
+ *
+ * The paper has no counterpart to this entry point.  It serves callers
+ * that cannot allocate device memory themselves: for example a solver
+ * embedded in a host application that owns all device memory through its
+ * own pool (a raw cudaMalloc/cudaFree would bypass that pool's accounting,
+ * and cudaFree can stall the whole device), or a latency-critical loop
+ * that must not pay for an allocation.  It computes, without a context,
+ * the same keys and order as the neighbour rebuild of a context
+ * (SPH_F_CELLKEY and SPH_F_ID after sph_rhs).  The scratch it needs is one
+ * fixed device array inside the library, about 3.2 MB, reserved on every
+ * GPU that loads the library until the process exits; the call itself
+ * allocates nothing.
+ *
+ * x, y, h: device arrays of n particles (FP64).  key_out (uint64) and
+ * perm_out (uint32): caller-owned device arrays of n entries, written with
+ * the cell keys (level << 58 | morton(ix, iy)) in ascending order and, for
+ * each sorted position, the input index of its particle (stable for equal
+ * keys).  Level-0 cell side: p->cell_c0 if > 0, else 3 * p->hdx *
+ * p->ds_min.  The work is enqueued on `stream` (cudaStream_t; NULL = the
+ * legacy default stream) and the call returns once it is enqueued.
+ *
+ * Limits and sharing: n <= 262144 (SPH_EINVAL beyond).  The first call on
+ * a device looks up the device address of the fixed array, with that
+ * device current; make that first call before any stream capture.  Every
+ * call on a device uses the same array and each call resets the parts it
+ * relies on, so calls whose work overlaps on the GPU (different streams or
+ * host threads) race and must be serialised by the caller.
+ * Errors: SPH_EINVAL (NULL argument, n out of range, no cell side, bad
+ * domain), SPH_ECUDA (device address lookup or launch failure). */
+sph_status sph_cell_sort_noalloc(const sph_params *p, long long n,
+                                 const double *x, const double *y,
+                                 const double *h, uint64_t *key_out,
+                                 uint32_t *perm_out, void *stream);
+
 /* Free all device and host storage of the context (synchronises). */
 sph_status sph_destroy(sph_ctx *ctx);
 

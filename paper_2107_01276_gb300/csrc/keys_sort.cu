@@ -196,6 +196,10 @@ __global__ void __launch_bounds__(RS_THREADS)
     }
 }
 
+size_t radix_counts_elems(size_t n) {
+    return 256 * ((n + RS_TILE - 1) / RS_TILE);
+}
+
 void radix_sort(cudaStream_t s, int n, int bits, uint64_t *key,
                 uint32_t *val, SortScratch &sc, int *launches) {
     if (n <= 1 || bits <= 0) return;

@@ -108,6 +108,8 @@ void exclusive_scan(cudaStream_t s, const uint32_t *in, uint32_t *out,
                     int n, uint32_t *total_dev, SortScratch &sc,
                     int *launches);
 size_t scan_scratch_elems(size_t n);
+// Tile-count entries radix_sort needs in SortScratch::counts for n keys.
+size_t radix_counts_elems(size_t n);
 void build_cell_table(cudaStream_t s, int n, const uint64_t *skey,
                       uint64_t *tkey, uint32_t *tstart, uint32_t *tend,
                       uint32_t tmask, int *launches);

@@ -116,8 +116,22 @@ def lib(build_if_missing: bool = True):
     L.sph_destroy.argtypes = [ctx]
     L.sph_last_error.restype = ctypes.c_char_p
     L.sph_last_error.argtypes = [ctx]
+    L.sph_cell_sort_noalloc.restype = ctypes.c_int
+    L.sph_cell_sort_noalloc.argtypes = [P(Params), ctypes.c_longlong] + \
+        [ctypes.c_void_p] * 6
     _lib = L
     return L
+
+
+def cell_sort_noalloc(params: Params, n: int, x_ptr: int, y_ptr: int,
+                      h_ptr: int, key_ptr: int, perm_ptr: int,
+                      stream: int = 0) -> int:
+    """sph_cell_sort_noalloc on caller-owned device pointers; returns the
+    status code."""
+    v = ctypes.c_void_p
+    return lib().sph_cell_sort_noalloc(ctypes.byref(params), int(n),
+                                       v(x_ptr), v(y_ptr), v(h_ptr),
+                                       v(key_ptr), v(perm_ptr), v(stream))
 
 
 def declared_functions():
