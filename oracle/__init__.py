@@ -75,6 +75,13 @@ class _RhsOut(ctypes.Structure):
         (k, ctypes.POINTER(ctypes.c_double)) for k in _RHS_S]
 
 
+class _AdaptStats(ctypes.Structure):
+    _fields_ = [("n_before", ctypes.c_longlong), ("n_split", ctypes.c_longlong),
+                ("n_merged", ctypes.c_longlong), ("n_after", ctypes.c_longlong),
+                ("mass_before", ctypes.c_double),
+                ("mass_after", ctypes.c_double)]
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 _U64 = ctypes.POINTER(ctypes.c_uint64)
@@ -125,6 +132,26 @@ def lib():
             for f in (L.orc_pec_predict, L.orc_pec_correct):
                 f.restype = None
                 f.argtypes = [_P, ctypes.c_double, ctypes.c_int] + [_D] * 15
+            L.orc_bg_resolution.restype = None
+            L.orc_bg_resolution.argtypes = [_P, ctypes.POINTER(_State),
+                                            ctypes.c_int, _D, _D, _D, _D]
+            L.orc_split.restype = ctypes.c_int
+            L.orc_split.argtypes = [_P, ctypes.POINTER(_State),
+                                    ctypes.POINTER(ctypes.c_longlong)]
+            L.orc_merge_round.restype = ctypes.c_int
+            L.orc_merge_round.argtypes = [_P, ctypes.POINTER(_State)]
+            L.orc_shift_compute.restype = None
+            L.orc_shift_compute.argtypes = [_P, ctypes.POINTER(_State)] + \
+                [_D] * 9
+            L.orc_shift_round.restype = None
+            L.orc_shift_round.argtypes = [_P, ctypes.POINTER(_State)]
+            L.orc_h_update.restype = None
+            L.orc_h_update.argtypes = [_P, ctypes.POINTER(_State)]
+            L.orc_adapt.restype = ctypes.c_int
+            L.orc_adapt.argtypes = [_P, ctypes.POINTER(_State), ctypes.c_int,
+                                    _D, _D, _D, _D,
+                                    ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(_AdaptStats)]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
             _lib = L
@@ -343,3 +370,74 @@ def pec_stage(P, which, dt_, x0, y0, u0, v0, p0, dudt, dvdt, dpdt, drx,
     f(ctypes.byref(P), float(dt_), n, *[_d(a) for a in arrs],
       *[_d(a) for a in out])
     return dict(zip(("x", "y", "u", "v", "p"), out))
+
+
+# ---------------------------------------------------------- adaptation --
+def _bg(bg):
+    if bg is None:
+        z = np.zeros(1)
+        return 0, z, z, z, z
+    arrs = [_f64(bg[k]) for k in ("x", "y", "h", "ds")]
+    return len(arrs[0]), arrs[0], arrs[1], arrs[2], arrs[3]
+
+
+def bg_resolution(P, st, bg):
+    """Fluid m_min, m_max from background particles (dict x, y, h, ds)."""
+    nb, bx, by, bh, bd = _bg(bg)
+    s = _cstate(st)
+    lib().orc_bg_resolution(ctypes.byref(P), ctypes.byref(s), nb, _d(bx),
+                            _d(by), _d(bh), _d(bd))
+
+
+def split(P, st, next_id):
+    """One split pass; returns (parents split or -1, new next_id)."""
+    s = _cstate(st)
+    nid = ctypes.c_longlong(int(next_id))
+    r = lib().orc_split(ctypes.byref(P), ctypes.byref(s), ctypes.byref(nid))
+    st["n"] = s.n
+    return r, nid.value
+
+
+def merge_round(P, st):
+    s = _cstate(st)
+    r = lib().orc_merge_round(ctypes.byref(P), ctypes.byref(s))
+    st["n"] = s.n
+    return r
+
+
+def shift_compute(P, st):
+    n = st["n"]
+    out = {k: np.zeros(max(n, 1)) for k in ("rho", "drx", "dry", "gux",
+                                             "guy", "gvx", "gvy", "gpx",
+                                             "gpy")}
+    s = _cstate(st)
+    lib().orc_shift_compute(ctypes.byref(P), ctypes.byref(s),
+                            *[_d(out[k]) for k in ("rho", "drx", "dry", "gux",
+                                                   "guy", "gvx", "gvy", "gpx",
+                                                   "gpy")])
+    return {k: v[:n] for k, v in out.items()}
+
+
+def shift_round(P, st):
+    s = _cstate(st)
+    lib().orc_shift_round(ctypes.byref(P), ctypes.byref(s))
+
+
+def h_update(P, st):
+    s = _cstate(st)
+    lib().orc_h_update(ctypes.byref(P), ctypes.byref(s))
+
+
+def adapt(P, st, bg=None, next_id=None):
+    """One adaptation (background resolution, split, merge rounds, shift
+    rounds, h update) in place; returns (status, stats dict, next_id)."""
+    nb, bx, by, bh, bd = _bg(bg)
+    if next_id is None:
+        next_id = int(st["id"][:st["n"]].max()) + 1 if st["n"] else 0
+    s = _cstate(st)
+    nid = ctypes.c_longlong(int(next_id))
+    z = _AdaptStats()
+    r = lib().orc_adapt(ctypes.byref(P), ctypes.byref(s), nb, _d(bx), _d(by),
+                        _d(bh), _d(bd), ctypes.byref(nid), ctypes.byref(z))
+    st["n"] = s.n
+    return r, {k: getattr(z, k) for k, _ in _AdaptStats._fields_}, nid.value

@@ -700,3 +700,329 @@ int orc_step(const orc_params *P, orc_state *s, int nsteps, double *t) {
     rhs_bufs_free(&b);
     return 0;
 }
+
+/* ========================================================================
+ * Adaptive refinement, section 3.
+ * ====================================================================== */
+
+/* m_ref from the background (section 3.3): a fluid particle takes the
+ * smallest background reference mass rho0 ds_b^2 over background particles
+ * b with r_ib < 3 max(h_i, h_b); with none in range, the nearest background
+ * particle's (ties to the lower index).  m_max = 1.05 m_ref,
+ * m_min = 0.5 m_ref. */
+void orc_bg_resolution(const orc_params *P, orc_state *s, int nb,
+                       const double *bx, const double *by, const double *bh,
+                       const double *bds) {
+    if (nb <= 0) return;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < s->n; ++i) {
+        double best = -1.0;
+        double nr2 = DBL_MAX;
+        int nearest = -1;
+        for (int b = 0; b < nb; ++b) {
+            double dx, dy;
+            separation(P, s->x[i], s->y[i], bx[b], by[b], &dx, &dy);
+            double r2 = dx * dx + dy * dy;
+            double R = 3.0 * (s->h[i] > bh[b] ? s->h[i] : bh[b]);
+            double mref = P->rho0 * bds[b] * bds[b];
+            if (r2 < R * R && (best < 0.0 || mref < best)) best = mref;
+            if (r2 < nr2) {
+                nr2 = r2;
+                nearest = b;
+            }
+        }
+        if (best < 0.0) best = P->rho0 * bds[nearest] * bds[nearest];
+        s->mmax[i] = 1.05 * best;
+        s->mmin[i] = 0.5 * best;
+    }
+}
+
+/* Hexagon directions k pi / 3, k = 0..5 (cosines and sines written out). */
+static const double HEX_C[6] = {1.0, 0.5, -0.5, -1.0, -0.5, 0.5};
+static const double HEX_S[6] = {0.0, 0.8660254037844386, 0.8660254037844386,
+                                0.0, -0.8660254037844386, -0.8660254037844386};
+
+typedef struct {
+    long long id;
+    int idx;
+} id_idx;
+
+static int cmp_id_idx(const void *a, const void *b) {
+    long long x = ((const id_idx *)a)->id, y = ((const id_idx *)b)->id;
+    return (x > y) - (x < y);
+}
+
+/* Split (section 3.1): a particle with m > m_max becomes 7 children, one
+ * (m_max <= 0 means no limit: such a particle is never split or merged)
+ * at the centre and six on the circle of radius eps h at angles k pi/3,
+ * each with smoothing length alpha h and mass m/7 (the centre child takes
+ * m - 6 (m/7) so the masses add up to m); rho, u, v, p, m_min, m_max are
+ * copied.  The centre child keeps the parent's id and slot; the six others
+ * are appended, and parent number r (counting parents in id order) gives
+ * them ids next_id + 6 r + k. */
+int orc_split(const orc_params *P, orc_state *s, long long *next_id) {
+    int n = s->n;
+    id_idx *par = (id_idx *)malloc((size_t)(n > 0 ? n : 1) * sizeof(id_idx));
+    int np = 0;
+    for (int i = 0; i < n; ++i)
+        if (s->mmax[i] > 0.0 && s->m[i] > s->mmax[i]) {
+            par[np].id = s->id[i];
+            par[np].idx = i;
+            ++np;
+        }
+    if ((long long)n + 6LL * np > s->cap) {
+        free(par);
+        return -1;
+    }
+    qsort(par, (size_t)np, sizeof(id_idx), cmp_id_idx);
+    for (int r = 0; r < np; ++r) {
+        int i = par[r].idx;
+        double m = s->m[i], h = s->h[i];
+        double mc = m / 7.0;
+        double rad = P->split_eps * h;
+        for (int k = 0; k < 6; ++k) {
+            int c = n + 6 * r + k;
+            s->x[c] = wrap(P, 0, s->x[i] + rad * HEX_C[k]);
+            s->y[c] = wrap(P, 1, s->y[i] + rad * HEX_S[k]);
+            s->u[c] = s->u[i];
+            s->v[c] = s->v[i];
+            s->p[c] = s->p[i];
+            s->rho[c] = s->rho[i];
+            s->m[c] = mc;
+            s->h[c] = P->split_alpha * h;
+            s->mmin[c] = s->mmin[i];
+            s->mmax[c] = s->mmax[i];
+            s->id[c] = *next_id + 6LL * r + k;
+        }
+        s->m[i] = m - 6.0 * mc;
+        s->h[i] = P->split_alpha * h;
+    }
+    s->n = n + 6 * np;
+    *next_id += 6LL * np;
+    free(par);
+    return np;
+}
+
+/* Merge round (section 3.2).  i may merge with j != i in N(i) when neither
+ * is to be split (m > m_max), r_ij < (h_i + h_j)/2 (tested as r^2 <
+ * ((h_i + h_j)/2)^2) and m_i + m_j < max(m_max,i, m_max,j); closest_i is
+ * the admissible j of least (r_ij^2, id_j).  Mutually closest pairs merge
+ * into the one with the smaller id: mass m_a + m_b; position, velocity,
+ * pressure and density mass-weighted (Eqs. merged-pos, merged-prop, with
+ * b's periodic image nearest a); h from Eq. merged-h with d = 2; the kept
+ * particle keeps its m_min, m_max.  The other particle is removed and the
+ * survivors keep their relative order. */
+int orc_merge_round(const orc_params *P, orc_state *s) {
+    int n = s->n;
+    if (n <= 1) return 0;
+    neighbors_auto(P, n, s->x, s->y, s->h);
+    int *closest = (int *)malloc((size_t)n * sizeof(int));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        closest[i] = -1;
+        if (!(s->mmax[i] > 0.0) || s->m[i] > s->mmax[i]) continue;
+        double br2 = 0.0;
+        long long bid = 0;
+        for (int k = g_off[i]; k < g_off[i + 1]; ++k) {
+            int j = g_nbr[k];
+            if (j == i || !(s->mmax[j] > 0.0) || s->m[j] > s->mmax[j]) continue;
+            double dx, dy;
+            separation(P, s->x[i], s->y[i], s->x[j], s->y[j], &dx, &dy);
+            double r2 = dx * dx + dy * dy;
+            double hh = 0.5 * (s->h[i] + s->h[j]);
+            if (!(r2 < hh * hh)) continue;
+            double mx = s->mmax[i] > s->mmax[j] ? s->mmax[i] : s->mmax[j];
+            if (!(s->m[i] + s->m[j] < mx)) continue;
+            if (closest[i] < 0 || r2 < br2 || (r2 == br2 && s->id[j] < bid)) {
+                closest[i] = j;
+                br2 = r2;
+                bid = s->id[j];
+            }
+        }
+    }
+    const double W01 = orc_W(0.0, 1.0);
+    char *dead = (char *)calloc((size_t)n, 1);
+    int pairs = 0;
+    for (int i = 0; i < n; ++i) {
+        int j = closest[i];
+        if (j < 0 || closest[j] != i || s->id[i] > s->id[j]) continue;
+        /* i kept (smaller id), j removed */
+        double ma = s->m[i], mb = s->m[j], mm = ma + mb;
+        double xa = s->x[i], ya = s->y[i];
+        double xb = xa + min_image(P, 0, s->x[j] - xa);
+        double yb = ya + min_image(P, 1, s->y[j] - ya);
+        double xm = (ma * xa + mb * xb) / mm;
+        double ym = (ma * ya + mb * yb) / mm;
+        double ra = sqrt((xm - xa) * (xm - xa) + (ym - ya) * (ym - ya));
+        double rb = sqrt((xm - xb) * (xm - xb) + (ym - yb) * (ym - yb));
+        double den = ma * orc_W(ra, s->h[i]) + mb * orc_W(rb, s->h[j]);
+        double hm = sqrt(mm * W01 / den);
+        s->u[i] = (ma * s->u[i] + mb * s->u[j]) / mm;
+        s->v[i] = (ma * s->v[i] + mb * s->v[j]) / mm;
+        s->p[i] = (ma * s->p[i] + mb * s->p[j]) / mm;
+        s->rho[i] = (ma * s->rho[i] + mb * s->rho[j]) / mm;
+        s->x[i] = wrap(P, 0, xm);
+        s->y[i] = wrap(P, 1, ym);
+        s->m[i] = mm;
+        s->h[i] = hm;
+        dead[j] = 1;
+        ++pairs;
+    }
+    int w = 0;
+    for (int i = 0; i < n; ++i) {
+        if (dead[i]) continue;
+        if (w != i) {
+            s->x[w] = s->x[i]; s->y[w] = s->y[i]; s->u[w] = s->u[i];
+            s->v[w] = s->v[i]; s->p[w] = s->p[i]; s->rho[w] = s->rho[i];
+            s->m[w] = s->m[i]; s->h[w] = s->h[i]; s->mmin[w] = s->mmin[i];
+            s->mmax[w] = s->mmax[i]; s->id[w] = s->id[i];
+        }
+        ++w;
+    }
+    s->n = w;
+    free(dead);
+    free(closest);
+    return pairs;
+}
+
+/* Summation density, limited shift (Eqs. shift-deltar, shift-limit, same
+ * readings as pass A) and the gradients of the Taylor correction:
+ * grad phi_i = sum_{j != i} V_j (phi_j - phi_i) grad_i W(r_ij, h_i) with
+ * V_j = m_j / rho_j (the paper names no gradient operator; this is the
+ * first-order form consistent with its gather sums). */
+void orc_shift_compute(const orc_params *P, const orc_state *s, double *rho,
+                       double *drx, double *dry, double *gux, double *guy,
+                       double *gvx, double *gvy, double *gpx, double *gpy) {
+    const double w_xi = w_of_q(XI_INFLECTION);
+    int n = s->n;
+    neighbors_auto(P, n, s->x, s->y, s->h);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        double r_ = 0.0;
+        for (int k = g_off[i]; k < g_off[i + 1]; ++k) {
+            int j = g_nbr[k];
+            double dx, dy;
+            separation(P, s->x[i], s->y[i], s->x[j], s->y[j], &dx, &dy);
+            r_ += s->m[j] * orc_W(sqrt(dx * dx + dy * dy), s->h[i]);
+        }
+        rho[i] = r_;
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        double ax = 0, ay = 0, ux = 0, uy = 0, vx = 0, vy = 0, px = 0, py = 0;
+        for (int k = g_off[i]; k < g_off[i + 1]; ++k) {
+            int j = g_nbr[k];
+            if (j == i) continue;
+            double dx, dy;
+            separation(P, s->x[i], s->y[i], s->x[j], s->y[j], &dx, &dy);
+            double r = sqrt(dx * dx + dy * dy);
+            if (!(r > 0.0)) continue;
+            double hb = 0.5 * (s->h[i] + s->h[j]);
+            double ratio = w_of_q(r / hb) / w_xi;
+            double f = (s->m[j] / P->rho0) * (1.0 + 0.24 * p4(ratio)) *
+                       orc_dWdr(r, hb) / r;
+            ax += f * dx;
+            ay += f * dy;
+            double g = orc_dWdr(r, s->h[i]) / r;
+            double Vj = s->m[j] / rho[j];
+            double du = s->u[j] - s->u[i], dv = s->v[j] - s->v[i],
+                   dp = s->p[j] - s->p[i];
+            ux += Vj * du * g * dx;
+            uy += Vj * du * g * dy;
+            vx += Vj * dv * g * dx;
+            vy += Vj * dv * g * dy;
+            px += Vj * dp * g * dx;
+            py += Vj * dp * g * dy;
+        }
+        double c = -0.5 * s->h[i] * s->h[i];
+        double sx = c * ax, sy = c * ay;
+        double mag = sqrt(sx * sx + sy * sy);
+        double lim = 0.25 * s->h[i];
+        if (mag > lim) {
+            double th = lim / mag;
+            sx *= th;
+            sy *= th;
+        }
+        drx[i] = sx;
+        dry[i] = sy;
+        gux[i] = ux; guy[i] = uy;
+        gvx[i] = vx; gvy[i] = vy;
+        gpx[i] = px; gpy[i] = py;
+    }
+}
+
+void orc_shift_round(const orc_params *P, orc_state *s) {
+    int n = s->n;
+    int nn = n > 0 ? n : 1;
+    double *b = (double *)malloc((size_t)nn * 9 * sizeof(double));
+    double *rho = b, *drx = b + nn, *dry = b + 2 * nn, *gux = b + 3 * nn,
+           *guy = b + 4 * nn, *gvx = b + 5 * nn, *gvy = b + 6 * nn,
+           *gpx = b + 7 * nn, *gpy = b + 8 * nn;
+    orc_shift_compute(P, s, rho, drx, dry, gux, guy, gvx, gvy, gpx, gpy);
+    for (int i = 0; i < n; ++i) {
+        s->x[i] = wrap(P, 0, s->x[i] + drx[i]);
+        s->y[i] = wrap(P, 1, s->y[i] + dry[i]);
+        s->u[i] = s->u[i] + (gux[i] * drx[i] + guy[i] * dry[i]);
+        s->v[i] = s->v[i] + (gvx[i] * drx[i] + gvy[i] * dry[i]);
+        s->p[i] = s->p[i] + (gpx[i] * drx[i] + gpy[i] * dry[i]);
+        s->rho[i] = rho[i];
+    }
+    free(b);
+}
+
+/* h_i = hdx (mbar_i / rho_i)^(1/2): mbar_i the mean mass over N(i) (i
+ * included), rho_i the summation density (section 3.1, "h = C
+ * (m/rho)^(1/d)" with the neighbourhood-average mass).  One evaluation. */
+void orc_h_update(const orc_params *P, orc_state *s) {
+    int n = s->n;
+    int nn = n > 0 ? n : 1;
+    double *hn = (double *)malloc((size_t)nn * 2 * sizeof(double));
+    double *rn = hn + nn;
+    neighbors_auto(P, n, s->x, s->y, s->h);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        double rho = 0.0, msum = 0.0;
+        int cnt = 0;
+        for (int k = g_off[i]; k < g_off[i + 1]; ++k) {
+            int j = g_nbr[k];
+            double dx, dy;
+            separation(P, s->x[i], s->y[i], s->x[j], s->y[j], &dx, &dy);
+            rho += s->m[j] * orc_W(sqrt(dx * dx + dy * dy), s->h[i]);
+            msum += s->m[j];
+            cnt += 1;
+        }
+        rn[i] = rho;
+        hn[i] = P->hdx * sqrt((msum / cnt) / rho);
+    }
+    for (int i = 0; i < n; ++i) {
+        s->h[i] = hn[i];
+        s->rho[i] = rn[i];
+    }
+    free(hn);
+}
+
+/* One adaptation (section 3.4, steps ii-iii): resolution from the
+ * background, one split pass, merge_iters merge rounds, shift_iters shift
+ * rounds with Taylor correction, then the h update. */
+int orc_adapt(const orc_params *P, orc_state *s, int nb, const double *bx,
+              const double *by, const double *bh, const double *bds,
+              long long *next_id, orc_adapt_stats *st) {
+    orc_adapt_stats z;
+    memset(&z, 0, sizeof(z));
+    z.n_before = s->n;
+    for (int i = 0; i < s->n; ++i) z.mass_before += s->m[i];
+    orc_bg_resolution(P, s, nb, bx, by, bh, bds);
+    int ns = orc_split(P, s, next_id);
+    if (ns < 0) {
+        if (st) *st = z;
+        return -1;
+    }
+    z.n_split = ns;
+    for (int r = 0; r < P->merge_iters; ++r) z.n_merged += orc_merge_round(P, s);
+    for (int r = 0; r < P->shift_iters; ++r) orc_shift_round(P, s);
+    orc_h_update(P, s);
+    z.n_after = s->n;
+    for (int i = 0; i < s->n; ++i) z.mass_after += s->m[i];
+    if (st) *st = z;
+    return 0;
+}

@@ -115,6 +115,36 @@ void orc_pec_correct(const orc_params *P, double dt, int n, const double *x0,
                      const double *drx, const double *dry, double *x,
                      double *y, double *u, double *v, double *p);
 
+/* ---- adaptive refinement (section 3) ---- */
+typedef struct {
+    long long n_before, n_split, n_merged, n_after;
+    double mass_before, mass_after;
+} orc_adapt_stats;
+
+/* Fluid m_ref from background particles (section 3.3): m_min, m_max. */
+void orc_bg_resolution(const orc_params *P, orc_state *s, int nb,
+                       const double *bx, const double *by, const double *bh,
+                       const double *bds);
+/* One split pass (section 3.1); returns the number of parents split, or
+ * -1 if the children would exceed the capacity (state unchanged). */
+int orc_split(const orc_params *P, orc_state *s, long long *next_id);
+/* One parallel mutual-closest merge round (section 3.2); returns pairs. */
+int orc_merge_round(const orc_params *P, orc_state *s);
+/* Shift displacement and Taylor gradients at the current state (no
+ * update); g* hold the x and y components of grad u, grad v, grad p. */
+void orc_shift_compute(const orc_params *P, const orc_state *s, double *rho,
+                       double *drx, double *dry, double *gux, double *guy,
+                       double *gvx, double *gvy, double *gpx, double *gpy);
+/* One shift round: shift by dr and Taylor-correct u, v, p (Eqs. shift,
+ * shift-correct). */
+void orc_shift_round(const orc_params *P, orc_state *s);
+/* Smoothing length from the neighbourhood-average mass (section 3.1). */
+void orc_h_update(const orc_params *P, orc_state *s);
+/* The whole adaptation of one iteration (section 3.4, ii-iii). */
+int orc_adapt(const orc_params *P, orc_state *s, int nb, const double *bx,
+              const double *by, const double *bh, const double *bds,
+              long long *next_id, orc_adapt_stats *st);
+
 int orc_num_threads(void);
 
 #ifdef __cplusplus
