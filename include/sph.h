@@ -120,6 +120,15 @@ typedef struct {
     long long launches;   /* kernels launched by this context so far */
 } sph_info;
 
+/* Counts and masses of one sph_adapt call. */
+typedef struct {
+    long long n_before;   /* fluid particles before */
+    long long n_split;    /* parents split (each became 7 particles) */
+    long long n_merged;   /* particles removed by merging, over all rounds */
+    long long n_after;    /* fluid particles after */
+    double mass_before, mass_after;   /* total fluid mass (FP64 sums) */
+} sph_adapt_stats;
+
 typedef struct sph_ctx sph_ctx;
 
 /* Fill *p with the paper's values: alpha_e 1.5, split_alpha 0.9,
@@ -135,7 +144,10 @@ void sph_default_params(sph_params *p);
 sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out);
 
 /* Replace the particle set of the given kind by n particles copied from
- * host arrays (x, y, m, h required; see sph_particles for defaults).
+ * host arrays.  SPH_FLUID: x, y, m, h required (see sph_particles for
+ * defaults).  SPH_BACKGROUND (section 3.3): x, y, h and ds (the particle
+ * size; NULL takes ds_max) required, any count; they only set the fluid's
+ * m_min/m_max in sph_adapt.
  * Fluid positions must lie in the box (periodic axes: [lo, hi)).
  * Synchronous with respect to the host buffers (they may be reused on
  * return).  Errors: SPH_EINVAL (NULL required array, n < 0, h or m not
@@ -159,6 +171,27 @@ sph_status sph_rhs(sph_ctx *ctx);
  * (nsteps < 0), SPH_ENONFINITE (checked once at the end when t_out is
  * given). */
 sph_status sph_step(sph_ctx *ctx, int nsteps, double *t_out);
+
+/* One adaptation of the fluid particles (section 3, steps ii-iii of the
+ * time loop in section 3.4), in FP64 for both precisions:
+ *  1. if a background set is loaded, m_ref of each fluid particle is the
+ *     smallest rho0 ds_b^2 over background particles b with r_ib <
+ *     3 max(h_i, h_b), else that of the nearest one; m_max = 1.05 m_ref,
+ *     m_min = 0.5 m_ref (section 3.3).  Without a background the loaded
+ *     m_min/m_max stay; m_max <= 0 means no limit (never split or merged);
+ *  2. one split pass: m > m_max -> 7 children (centre + hexagon at
+ *     split_eps*h, h = split_alpha*h, mass m/7), children ids assigned from
+ *     a counter in parent-id order (section 3.1);
+ *  3. merge_iters rounds of mutual-closest merging (section 3.2,
+ *     Eqs. merged-pos, merged-prop, merged-h);
+ *  4. shift_iters rounds of limited shifting with Taylor correction of u,
+ *     v, p (Eqs. shift, shift-deltar, shift-limit, shift-correct);
+ *  5. h = hdx (mbar/rho)^(1/2) with the neighbourhood-average mass.
+ * Synchronises (it reads back the particle counts).  out (may be NULL)
+ * receives counts and total masses.  Errors: SPH_ESTATE (no fluid),
+ * SPH_ECAPACITY (the children would exceed the capacity; nothing is split,
+ * m_min/m_max are already refreshed). */
+sph_status sph_adapt(sph_ctx *ctx, sph_adapt_stats *out);
 
 /* Copy one field of the fluid set to the host buffer dst holding cap
  * elements of the field's type; *n_out (if not NULL) receives the element

@@ -1,0 +1,445 @@
+// Adaptive refinement (section 3): resolution from the background,
+// split, mutual-closest merge, shift with Taylor correction, h update.
+// FP64 throughout, with explicitly rounded operations wherever a result
+// feeds a decision (split test, merge admissibility and closest partner),
+// so the decisions match the definition bit for bit.
+#include "adapt.cuh"
+#include "neighbors.cuh"
+
+namespace sph {
+
+// Quintic spline in FP64 with the operation order of its definition
+// (section 2, Eq. kernel): sigma2 = 7 / (478 pi h^2), q = r / h.
+__device__ __forceinline__ double p5_rn(double a) {
+    return __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(a, a), a), a), a);
+}
+__device__ __forceinline__ double w_rn(double q) {
+    if (q >= 3.0) return 0.0;
+    double w = p5_rn(__dsub_rn(3.0, q));
+    if (q < 2.0) w = __dsub_rn(w, __dmul_rn(6.0, p5_rn(__dsub_rn(2.0, q))));
+    if (q < 1.0) w = __dadd_rn(w, __dmul_rn(15.0, p5_rn(__dsub_rn(1.0, q))));
+    return w;
+}
+__device__ __forceinline__ double W_rn(double r, double h) {
+    double s = __ddiv_rn(7.0, __dmul_rn(__dmul_rn(__dmul_rn(478.0, PI), h), h));
+    return __dmul_rn(s, w_rn(__ddiv_rn(r, h)));
+}
+__device__ __forceinline__ double wrap_rn(const Domain &d, int a, double x) {
+    if (d.periodic[a]) {
+        if (x >= d.hi[a])
+            x = __dsub_rn(x, d.L[a]);
+        else if (x < d.lo[a])
+            x = __dadd_rn(x, d.L[a]);
+    }
+    return x;
+}
+
+// Quintic kernel and derivative for the sums (ordinary FP64).
+__device__ __forceinline__ double qw(double q) {
+    if (q >= 3.0) return 0.0;
+    double a = 3.0 - q, a2 = a * a, w = a2 * a2 * a;
+    if (q < 2.0) {
+        double b = 2.0 - q, b2 = b * b;
+        w -= 6.0 * b2 * b2 * b;
+        if (q < 1.0) {
+            double c = 1.0 - q, c2 = c * c;
+            w += 15.0 * c2 * c2 * c;
+        }
+    }
+    return w;
+}
+__device__ __forceinline__ double qdw(double q) {
+    if (q >= 3.0) return 0.0;
+    double a = 3.0 - q, a2 = a * a, w = -5.0 * a2 * a2;
+    if (q < 2.0) {
+        double b = 2.0 - q, b2 = b * b;
+        w += 30.0 * b2 * b2;
+        if (q < 1.0) {
+            double c = 1.0 - q, c2 = c * c;
+            w -= 75.0 * c2 * c2;
+        }
+    }
+    return w;
+}
+constexpr double SIGMA_N = 7.0 / (478.0 * PI);
+
+__device__ __forceinline__ void sep_rn(const Domain &d, double xi, double yi,
+                                       double xj, double yj, double &dx,
+                                       double &dy, double &r2) {
+    dx = min_image(d, 0, __dsub_rn(xi, xj));
+    dy = min_image(d, 1, __dsub_rn(yi, yj));
+    r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+// ------------------------------------------- resolution from background --
+// m_ref,i = min rho0 ds_b^2 over background b with r_ib < 3 max(h_i, h_b)
+// (section 3.3); particles with none in range are queued for the nearest
+// background particle.  m_max = 1.05 m_ref, m_min = 0.5 m_ref.
+__global__ void k_bg_mref(BgArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
+    double best = -1.0;
+    for_each_candidate(a.g, a.d, 0, xi, yi, hi, [&](int b) {
+        if (pred_fp64(a.d, xi, yi, hi, __ldg(&a.bx[b]), __ldg(&a.by[b]),
+                      __ldg(&a.bh[b]))) {
+            const double ds = __ldg(&a.bds[b]);
+            const double mref = __dmul_rn(__dmul_rn(a.rho0, ds), ds);
+            if (best < 0.0 || mref < best) best = mref;
+        }
+    });
+    if (best < 0.0) {
+        a.queue[atomicAdd(a.nqueue, 1u)] = (uint32_t)i;
+        return;
+    }
+    a.mmax[i] = __dmul_rn(1.05, best);
+    a.mmin[i] = __dmul_rn(0.5, best);
+}
+
+// Nearest background particle (least r^2, then least load index) for the
+// queued fluid particles; a warp per particle.
+__global__ void k_bg_nearest(BgArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nq = *a.nqueue;
+    for (uint32_t q = w; q < nq; q += nw) {
+        const int i = (int)a.queue[q];
+        const double xi = a.x[i], yi = a.y[i];
+        double br2 = 1e308;
+        long long bidx = -1;
+        int bb = -1;
+        for (int b = lane; b < a.nb; b += 32) {
+            double dx, dy, r2;
+            sep_rn(a.d, xi, yi, a.bx[b], a.by[b], dx, dy, r2);
+            long long id = a.bid[b];
+            if (r2 < br2 || (r2 == br2 && id < bidx)) {
+                br2 = r2;
+                bidx = id;
+                bb = b;
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            double r2o = __shfl_xor_sync(0xffffffffu, br2, o);
+            long long ido = __shfl_xor_sync(0xffffffffu, bidx, o);
+            int bo = __shfl_xor_sync(0xffffffffu, bb, o);
+            if (bo >= 0 && (bb < 0 || r2o < br2 || (r2o == br2 && ido < bidx))) {
+                br2 = r2o;
+                bidx = ido;
+                bb = bo;
+            }
+        }
+        if (lane == 0 && bb >= 0) {
+            const double ds = a.bds[bb];
+            const double mref = __dmul_rn(__dmul_rn(a.rho0, ds), ds);
+            a.mmax[i] = __dmul_rn(1.05, mref);
+            a.mmin[i] = __dmul_rn(0.5, mref);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ split --
+__global__ void k_split_flag(int n, const double *m, const double *mmax,
+                             uint32_t *flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double mx = mmax[i];
+    flag[i] = (mx > 0.0 && m[i] > mx) ? 1u : 0u;
+}
+
+__global__ void k_split_collect(int n, const uint32_t *flag,
+                                const uint32_t *pos, const int64_t *id,
+                                uint64_t *key, uint32_t *val) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag[i]) return;
+    key[pos[i]] = (uint64_t)id[i];
+    val[pos[i]] = (uint32_t)i;
+}
+
+// Parent number r (in id order) writes its six ring children to slots
+// n + 6r + k with ids next_id + 6r + k; the centre child stays in place.
+__global__ void k_split_emit(SplitArgs a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.count) return;
+    const double C[6] = {1.0, 0.5, -0.5, -1.0, -0.5, 0.5};
+    const double S[6] = {0.0, 0.8660254037844386, 0.8660254037844386, 0.0,
+                         -0.8660254037844386, -0.8660254037844386};
+    const int i = (int)a.parent[r];
+    double *f[NSTATE];
+    for (int k = 0; k < NSTATE; ++k) f[k] = a.f[k];
+    const double m = f[S_M][i], h = f[S_H][i];
+    const double mc = __ddiv_rn(m, 7.0);
+    const double rad = __dmul_rn(a.eps, h);
+    const double hc = __dmul_rn(a.alpha, h);
+    for (int k = 0; k < 6; ++k) {
+        const int c = a.n + 6 * r + k;
+        f[S_X][c] = wrap_rn(a.d, 0, __dadd_rn(f[S_X][i], __dmul_rn(rad, C[k])));
+        f[S_Y][c] = wrap_rn(a.d, 1, __dadd_rn(f[S_Y][i], __dmul_rn(rad, S[k])));
+        f[S_U][c] = f[S_U][i];
+        f[S_V][c] = f[S_V][i];
+        f[S_P][c] = f[S_P][i];
+        f[S_RHO][c] = f[S_RHO][i];
+        f[S_M][c] = mc;
+        f[S_H][c] = hc;
+        f[S_MMIN][c] = f[S_MMIN][i];
+        f[S_MMAX][c] = f[S_MMAX][i];
+        a.id[c] = a.next_id + 6ll * r + k;
+    }
+    f[S_M][i] = __dsub_rn(m, __dmul_rn(6.0, mc));
+    f[S_H][i] = hc;
+}
+
+// ------------------------------------------------------------------ merge --
+// closest_i: admissible j in N(i) of least (r^2, id_j); admissible: j != i,
+// neither to be split, r^2 < ((h_i + h_j)/2)^2, m_i + m_j < max(m_max).
+__global__ void k_merge_closest(MergeArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double *x = a.f[S_X], *y = a.f[S_Y], *h = a.f[S_H], *m = a.f[S_M],
+                 *mmax = a.f[S_MMAX];
+    int best = -1;
+    const double mi = m[i], mxi = mmax[i];
+    if (mxi > 0.0 && !(mi > mxi)) {
+        const double xi = x[i], yi = y[i], hi = h[i];
+        double br2 = 0.0;
+        long long bid = 0;
+        for (uint32_t k = a.off[i]; k < a.off[i + 1]; ++k) {
+            const int j = (int)a.list[k];
+            if (j == i) continue;
+            const double mxj = mmax[j], mj = m[j];
+            if (!(mxj > 0.0) || mj > mxj) continue;
+            double dx, dy, r2;
+            sep_rn(a.d, xi, yi, x[j], y[j], dx, dy, r2);
+            const double hh = __dmul_rn(0.5, __dadd_rn(hi, h[j]));
+            if (!(r2 < __dmul_rn(hh, hh))) continue;
+            const double mx = mxi > mxj ? mxi : mxj;
+            if (!(__dadd_rn(mi, mj) < mx)) continue;
+            const long long idj = a.id[j];
+            if (best < 0 || r2 < br2 || (r2 == br2 && idj < bid)) {
+                best = j;
+                br2 = r2;
+                bid = idj;
+            }
+        }
+    }
+    a.closest[i] = best;
+}
+
+// Mutually closest pairs merge into the particle with the smaller id
+// (Eqs. merged-pos, merged-prop, merged-h with d = 2); alive marks the
+// survivors.
+__global__ void k_merge_apply(MergeArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int j = a.closest[i];
+    uint32_t alive = 1;
+    if (j >= 0 && a.closest[j] == i) {
+        if (a.id[i] > a.id[j]) {
+            alive = 0;
+        } else {
+            double *f[NSTATE];
+            for (int k = 0; k < NSTATE; ++k) f[k] = a.f[k];
+            const double ma = f[S_M][i], mb = f[S_M][j];
+            const double mm = __dadd_rn(ma, mb);
+            const double xa = f[S_X][i], ya = f[S_Y][i];
+            const double xb = __dadd_rn(xa, min_image(a.d, 0, __dsub_rn(f[S_X][j], xa)));
+            const double yb = __dadd_rn(ya, min_image(a.d, 1, __dsub_rn(f[S_Y][j], ya)));
+            const double xm = __ddiv_rn(__dadd_rn(__dmul_rn(ma, xa), __dmul_rn(mb, xb)), mm);
+            const double ym = __ddiv_rn(__dadd_rn(__dmul_rn(ma, ya), __dmul_rn(mb, yb)), mm);
+            const double ax = __dsub_rn(xm, xa), ay = __dsub_rn(ym, ya);
+            const double bx = __dsub_rn(xm, xb), by = __dsub_rn(ym, yb);
+            const double ra = __dsqrt_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)));
+            const double rb = __dsqrt_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)));
+            const double den = __dadd_rn(__dmul_rn(ma, W_rn(ra, f[S_H][i])),
+                                         __dmul_rn(mb, W_rn(rb, f[S_H][j])));
+            const double hm = __dsqrt_rn(__ddiv_rn(__dmul_rn(mm, W_rn(0.0, 1.0)), den));
+            auto mw = [&](int k) {
+                return __ddiv_rn(__dadd_rn(__dmul_rn(ma, f[k][i]), __dmul_rn(mb, f[k][j])), mm);
+            };
+            const double un = mw(S_U), vn = mw(S_V), pn = mw(S_P), rn = mw(S_RHO);
+            f[S_U][i] = un;
+            f[S_V][i] = vn;
+            f[S_P][i] = pn;
+            f[S_RHO][i] = rn;
+            f[S_X][i] = wrap_rn(a.d, 0, xm);
+            f[S_Y][i] = wrap_rn(a.d, 1, ym);
+            f[S_M][i] = mm;
+            f[S_H][i] = hm;
+        }
+    }
+    a.alive[i] = alive;
+}
+
+// Stream compaction: survivors move to pos[i] in the alternate arrays.
+__global__ void k_compact(int n, const uint32_t *alive, const uint32_t *pos,
+                          CompactArgs c) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !alive[i]) return;
+    const uint32_t d = pos[i];
+    for (int k = 0; k < NSTATE; ++k) c.dst[k][d] = c.src[k][i];
+    c.idst[d] = c.isrc[i];
+}
+
+// ------------------------------------------------------- shift and Taylor --
+// Summation density of every particle (Eq. sd-gather) and, for the h
+// update, the mean neighbour mass.
+__global__ void k_density_mbar(ShiftArgs a, int want_h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double *x = a.f[S_X], *y = a.f[S_Y], *h = a.f[S_H], *m = a.f[S_M];
+    const double xi = x[i], yi = y[i], hi = h[i], hinv = 1.0 / hi;
+    double rho = 0.0, msum = 0.0;
+    const uint32_t b = a.off[i], e = a.off[i + 1];
+    for (uint32_t k = b; k < e; ++k) {
+        const int j = (int)a.list[k];
+        double dx, dy, r2;
+        sep_rn(a.d, xi, yi, x[j], y[j], dx, dy, r2);
+        rho += m[j] * qw(sqrt(r2) * hinv);
+        msum += m[j];
+    }
+    rho *= SIGMA_N * hinv * hinv;
+    a.rho[i] = rho;
+    if (want_h) a.hnew[i] = a.hdx * sqrt((msum / (double)(e - b)) / rho);
+}
+
+// Limited shift (Eqs. shift-deltar, shift-limit) and the Taylor gradients
+// grad phi_i = sum_{j != i} V_j (phi_j - phi_i) grad_i W(r_ij, h_i).
+__global__ void k_shift_compute(ShiftArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double *x = a.f[S_X], *y = a.f[S_Y], *h = a.f[S_H], *m = a.f[S_M],
+                 *u = a.f[S_U], *v = a.f[S_V], *p = a.f[S_P];
+    const double xi = x[i], yi = y[i], hi = h[i], hinv = 1.0 / hi;
+    const double inv_wxi = 1.0 / qw(XI_INFLECTION);
+    const double ui = u[i], vi = v[i], pi = p[i];
+    double ax = 0, ay = 0, gux = 0, guy = 0, gvx = 0, gvy = 0, gpx = 0, gpy = 0;
+    for (uint32_t k = a.off[i]; k < a.off[i + 1]; ++k) {
+        const int j = (int)a.list[k];
+        if (j == i) continue;
+        double dx, dy, r2;
+        sep_rn(a.d, xi, yi, x[j], y[j], dx, dy, r2);
+        const double r = sqrt(r2);
+        if (!(r > 0.0)) continue;
+        const double hb = 0.5 * (hi + h[j]), hbinv = 1.0 / hb;
+        double ratio = qw(r * hbinv) * inv_wxi;
+        ratio *= ratio;
+        const double f = (m[j] / a.rho0) * (1.0 + 0.24 * ratio * ratio) *
+                         (SIGMA_N * hbinv * hbinv * hbinv) * qdw(r * hbinv) / r;
+        ax += f * dx;
+        ay += f * dy;
+        const double g = SIGMA_N * hinv * hinv * hinv * qdw(r * hinv) / r;
+        const double Vg = (m[j] / a.rho[j]) * g;
+        const double du = u[j] - ui, dv = v[j] - vi, dp = p[j] - pi;
+        gux += Vg * du * dx;
+        guy += Vg * du * dy;
+        gvx += Vg * dv * dx;
+        gvy += Vg * dv * dy;
+        gpx += Vg * dp * dx;
+        gpy += Vg * dp * dy;
+    }
+    const double c = -0.5 * hi * hi;
+    double sx = c * ax, sy = c * ay;
+    const double mag = sqrt(sx * sx + sy * sy), lim = 0.25 * hi;
+    if (mag > lim) {
+        const double th = lim / mag;
+        sx *= th;
+        sy *= th;
+    }
+    a.drx[i] = sx;
+    a.dry[i] = sy;
+    a.du[i] = gux * sx + guy * sy;
+    a.dv[i] = gvx * sx + gvy * sy;
+    a.dp[i] = gpx * sx + gpy * sy;
+}
+
+__global__ void k_shift_apply(ShiftArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    a.f[S_X][i] = wrap_rn(a.d, 0, a.f[S_X][i] + a.drx[i]);
+    a.f[S_Y][i] = wrap_rn(a.d, 1, a.f[S_Y][i] + a.dry[i]);
+    a.f[S_U][i] += a.du[i];
+    a.f[S_V][i] += a.dv[i];
+    a.f[S_P][i] += a.dp[i];
+    a.f[S_RHO][i] = a.rho[i];
+}
+
+__global__ void k_h_apply(ShiftArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    a.f[S_H][i] = a.hnew[i];
+    a.f[S_RHO][i] = a.rho[i];
+}
+
+// Deterministic two-stage sum of the masses.
+__global__ void k_mass_partial(int n, const double *m, double *part) {
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256)
+        acc += m[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_mass_final(int nb, const double *part, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += part[b];
+        *out = acc;
+    }
+}
+
+// ------------------------------------------------------------- launchers --
+static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
+
+void launch_bg_mref(cudaStream_t s, const BgArgs &a) {
+    if (a.n <= 0) return;
+    cudaMemsetAsync(a.nqueue, 0, sizeof(uint32_t), s);
+    k_bg_mref<<<nblk(a.n, 128), 128, 0, s>>>(a);
+    k_bg_nearest<<<152, 256, 0, s>>>(a);
+}
+void launch_split_flag(cudaStream_t s, int n, const double *m,
+                       const double *mmax, uint32_t *flag) {
+    if (n > 0) k_split_flag<<<nblk(n, 256), 256, 0, s>>>(n, m, mmax, flag);
+}
+void launch_split_collect(cudaStream_t s, int n, const uint32_t *flag,
+                          const uint32_t *pos, const int64_t *id,
+                          uint64_t *key, uint32_t *val) {
+    if (n > 0)
+        k_split_collect<<<nblk(n, 256), 256, 0, s>>>(n, flag, pos, id, key, val);
+}
+void launch_split_emit(cudaStream_t s, const SplitArgs &a) {
+    if (a.count > 0) k_split_emit<<<nblk(a.count, 128), 128, 0, s>>>(a);
+}
+void launch_merge(cudaStream_t s, const MergeArgs &a) {
+    if (a.n <= 0) return;
+    k_merge_closest<<<nblk(a.n, 128), 128, 0, s>>>(a);
+    k_merge_apply<<<nblk(a.n, 128), 128, 0, s>>>(a);
+}
+void launch_compact(cudaStream_t s, int n, const uint32_t *alive,
+                    const uint32_t *pos, const CompactArgs &c) {
+    if (n > 0) k_compact<<<nblk(n, 256), 256, 0, s>>>(n, alive, pos, c);
+}
+void launch_shift_round(cudaStream_t s, const ShiftArgs &a) {
+    if (a.n <= 0) return;
+    k_density_mbar<<<nblk(a.n, 128), 128, 0, s>>>(a, 0);
+    k_shift_compute<<<nblk(a.n, 128), 128, 0, s>>>(a);
+    k_shift_apply<<<nblk(a.n, 256), 256, 0, s>>>(a);
+}
+void launch_h_update(cudaStream_t s, const ShiftArgs &a) {
+    if (a.n <= 0) return;
+    k_density_mbar<<<nblk(a.n, 128), 128, 0, s>>>(a, 1);
+    k_h_apply<<<nblk(a.n, 256), 256, 0, s>>>(a);
+}
+void launch_mass_sum(cudaStream_t s, int n, const double *m, double *part,
+                     double *out) {
+    int nb = std::max(1, std::min(nblk(n, 256), 256));
+    k_mass_partial<<<nb, 256, 0, s>>>(n, m, part);
+    k_mass_final<<<1, 32, 0, s>>>(nb, part, out);
+}
+
+}  // namespace sph

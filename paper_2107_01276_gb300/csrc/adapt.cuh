@@ -1,0 +1,76 @@
+// Argument blocks and launchers of the adaptive-refinement kernels
+// (adapt.cu).
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// The FP64 state arrays, in the order the context stores them.
+enum { S_X = 0, S_Y, S_U, S_V, S_P, S_RHO, S_M, S_H, S_MMIN, S_MMAX, NSTATE };
+
+struct BgArgs {
+    int n;                      // fluid particles
+    Domain d;
+    Grid g;                     // cell structure of the background
+    const double *x, *y, *h;    // fluid
+    double *mmin, *mmax;
+    int nb;
+    const double *bx, *by, *bh, *bds;   // background, sorted by its keys
+    const int64_t *bid;         // background load index
+    double rho0;
+    uint32_t *queue, *nqueue;   // fluid particles with no background in range
+};
+
+struct SplitArgs {
+    int n, count;               // particles before the split, parents
+    Domain d;
+    double *f[NSTATE];
+    int64_t *id;
+    const uint32_t *parent;     // parent slot by rank (id order)
+    long long next_id;
+    double alpha, eps;
+};
+
+struct MergeArgs {
+    int n;
+    Domain d;
+    double *f[NSTATE];
+    const int64_t *id;
+    const uint32_t *off, *list;
+    int *closest;
+    uint32_t *alive;
+};
+
+struct CompactArgs {
+    const double *src[NSTATE];
+    double *dst[NSTATE];
+    const int64_t *isrc;
+    int64_t *idst;
+};
+
+struct ShiftArgs {
+    int n;
+    Domain d;
+    double *f[NSTATE];
+    const uint32_t *off, *list;
+    double rho0, hdx;
+    double *rho, *drx, *dry, *du, *dv, *dp, *hnew;   // scratch
+};
+
+void launch_bg_mref(cudaStream_t s, const BgArgs &a);
+void launch_split_flag(cudaStream_t s, int n, const double *m,
+                       const double *mmax, uint32_t *flag);
+void launch_split_collect(cudaStream_t s, int n, const uint32_t *flag,
+                          const uint32_t *pos, const int64_t *id,
+                          uint64_t *key, uint32_t *val);
+void launch_split_emit(cudaStream_t s, const SplitArgs &a);
+void launch_merge(cudaStream_t s, const MergeArgs &a);
+void launch_compact(cudaStream_t s, int n, const uint32_t *alive,
+                    const uint32_t *pos, const CompactArgs &c);
+void launch_shift_round(cudaStream_t s, const ShiftArgs &a);
+void launch_h_update(cudaStream_t s, const ShiftArgs &a);
+void launch_mass_sum(cudaStream_t s, int n, const double *m, double *part,
+                     double *out);
+
+}  // namespace sph

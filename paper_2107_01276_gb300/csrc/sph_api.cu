@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "adapt.cuh"
 #include "lists.cuh"
 #include "pair_passes.cuh"
 #include "sph_internal.cuh"
@@ -76,6 +77,25 @@ struct sph_ctx {
     uint32_t *longq = nullptr, *d_nlong = nullptr;
     Anchor an;
     double anchor_A[2] = {0, 0};
+
+    // adaptation
+    long long next_id = 0;
+    uint32_t *tmp_a = nullptr, *tmp_b = nullptr;   // N + 1 each
+    int *closest = nullptr;
+    double *d_mass = nullptr, *d_mass_part = nullptr;  // [2], [256]
+    // background set (section 3.3), sorted by its own cell keys
+    int n_bg = 0, bg_cap = 0;
+    double *bx = nullptr, *by = nullptr, *bh = nullptr, *bds = nullptr;
+    int64_t *bid = nullptr;
+    uint64_t *bkey = nullptr, *btkey = nullptr;
+    uint32_t *bperm = nullptr, *btstart = nullptr, *btend = nullptr;
+    int *bbbox = nullptr;
+    uint32_t *bmask = nullptr;
+    uint32_t btmask = 0;
+    double bc0 = 0.0;
+    int blmax = 0, bmbits = 1, blbits = 0;
+    Level blev[MAX_LEVELS];
+    SortScratch bsc;
 
     // device scalars
     double *d_dt = nullptr, *d_t = nullptr;
@@ -450,7 +470,11 @@ static void free_ctx(sph_ctx *c) {
                   c->tkey, c->tstart, c->tend, c->bbox, c->level_mask,
                   c->cnt_tmp, c->d_dt, c->d_t, c->d_hmin, c->d_nonfinite,
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
-                  c->d_overflow, c->longq, c->d_nlong};
+                  c->d_overflow, c->longq, c->d_nlong, c->tmp_a, c->tmp_b,
+                  c->closest, c->d_mass, c->d_mass_part, c->bx, c->by, c->bh,
+                  c->bds, c->bid, c->bkey, c->btkey, c->bperm, c->btstart,
+                  c->btend, c->bbbox, c->bmask, c->bsc.key_alt, c->bsc.val_alt,
+                  c->bsc.counts, c->bsc.scan_tmp};
     for (void *p : ps) cudaFree(p);
     for (auto e : c->tm.pool) cudaEventDestroy(e);
     for (int f = 0; f < 5; ++f)
@@ -458,6 +482,152 @@ static void free_ctx(sph_ctx *c) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
         }
+}
+
+// ---------------------------------------------------------- background --
+static void free_bg(sph_ctx *c) {
+    void *ps[] = {c->bx, c->by, c->bh, c->bds, c->bid, c->bkey, c->btkey,
+                  c->bperm, c->btstart, c->btend, c->bbbox, c->bmask,
+                  c->bsc.key_alt, c->bsc.val_alt, c->bsc.counts, c->bsc.scan_tmp};
+    for (void *p : ps) cudaFree(p);
+    c->bx = c->by = c->bh = c->bds = nullptr;
+    c->bid = nullptr;
+    c->bkey = c->btkey = nullptr;
+    c->bperm = c->btstart = c->btend = nullptr;
+    c->bbbox = nullptr;
+    c->bmask = nullptr;
+    c->bsc = SortScratch();
+    c->bg_cap = 0;
+    c->n_bg = 0;
+}
+
+// Background particles (section 3.3): x, y, h and size ds, kept sorted by
+// their own multi-level cell keys so fluid particles can query them.
+static sph_status load_background(sph_ctx *c, long long n,
+                                  const sph_particles *src) {
+    if (n > 0 && (!src->x || !src->y || !src->h))
+        return fail(c, SPH_EINVAL, "sph_load_particles: background needs x, y, h");
+    if (n > 0 && !src->ds && !(c->prm.ds_max > 0))
+        return fail(c, SPH_EINVAL, "sph_load_particles: background needs ds (or ds_max > 0)");
+    double hmin = INFINITY;
+    for (long long i = 0; i < n; ++i) {
+        double h = src->h[i], ds = src->ds ? src->ds[i] : c->prm.ds_max;
+        if (!(h > 0) || !isfinite(h) || !(ds > 0) || !isfinite(ds) ||
+            !isfinite(src->x[i]) || !isfinite(src->y[i]))
+            return fail(c, SPH_EINVAL, "sph_load_particles: background h, ds must be positive");
+        hmin = std::min(hmin, h);
+    }
+    if (n > (1ll << 30)) return fail(c, SPH_ECAPACITY, "sph_load_particles: background too large");
+    c->n_bg = 0;
+    if (n == 0) return SPH_OK;
+    double c0 = 3.0 * hmin;
+    double Lmax = std::max(c->dom.L[0], c->dom.L[1]);
+    int lmax = 0;
+    while (ldexp(c0, lmax) < Lmax) ++lmax;
+    if (lmax >= MAX_LEVELS) return fail(c, SPH_EINVAL, "background spans too many levels");
+    Level lev[MAX_LEVELS];
+    compute_levels(c->dom, c0, lev);
+    long long nmax = std::max(lev[0].n[0], lev[0].n[1]);
+    if (nmax >= (1ll << MAX_MORTON_BITS)) return fail(c, SPH_EINVAL, "background grid too fine");
+    if (n > c->bg_cap) {
+        free_bg(c);
+        size_t N = (size_t)n;
+        bool ok = dalloc(&c->bx, N) && dalloc(&c->by, N) && dalloc(&c->bh, N) &&
+                  dalloc(&c->bds, N) && dalloc(&c->bid, N) && dalloc(&c->bkey, N) &&
+                  dalloc(&c->bperm, N) && dalloc(&c->bbbox, MAX_LEVELS * 4) &&
+                  dalloc(&c->bmask, 1) && dalloc(&c->bsc.key_alt, N) &&
+                  dalloc(&c->bsc.val_alt, N);
+        size_t tiles = (N + 2047) / 2048;
+        c->bsc.counts_cap = 256 * tiles;
+        c->bsc.scan_cap = scan_scratch_elems(c->bsc.counts_cap);
+        ok = ok && dalloc(&c->bsc.counts, c->bsc.counts_cap) &&
+             dalloc(&c->bsc.scan_tmp, c->bsc.scan_cap);
+        uint32_t t = 1;
+        while (t < 2u * (uint32_t)N) t <<= 1;
+        ok = ok && dalloc(&c->btkey, t) && dalloc(&c->btstart, t) && dalloc(&c->btend, t);
+        if (!ok) {
+            cudaGetLastError();
+            free_bg(c);
+            return fail(c, SPH_ENOMEM, "background allocation failed");
+        }
+        c->bg_cap = (int)n;
+    }
+    // upload unsorted into temporaries, then sort into place
+    double *tmp = nullptr;
+    int64_t *tid = nullptr;
+    if (!dalloc(&tmp, 4 * (size_t)n) || !dalloc(&tid, (size_t)n)) {
+        cudaGetLastError();
+        cudaFree(tmp);
+        return fail(c, SPH_ENOMEM, "background staging allocation failed");
+    }
+    std::vector<double> dsv;
+    const double *ds = src->ds;
+    if (!ds) {
+        dsv.assign((size_t)n, c->prm.ds_max);
+        ds = dsv.data();
+    }
+    std::vector<int64_t> ids((size_t)n);
+    for (long long i = 0; i < n; ++i) ids[i] = i;
+    cudaMemcpyAsync(tmp, src->x, sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(tmp + n, src->y, sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(tmp + 2 * n, src->h, sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(tmp + 3 * n, ds, sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(tid, ids.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
+    c->bc0 = c0;
+    c->blmax = lmax;
+    memcpy(c->blev, lev, sizeof(lev));
+    c->bmbits = std::max(1, bits_for(nmax - 1));
+    c->blbits = bits_for(lmax);
+    launch_reset_bbox(c->s, c->bbbox, c->bmask);
+    launch_keys(c->s, (int)n, c->dom, c0, lmax, c->bmbits, c->blev, tmp, tmp + n,
+                tmp + 2 * n, c->bkey, c->bperm, c->bmask, c->bbbox);
+    radix_sort(c->s, (int)n, 2 * c->bmbits + c->blbits, c->bkey, c->bperm,
+               c->bsc, &c->launches);
+    GatherList gl;
+    memset(&gl, 0, sizeof(gl));
+    double *dst[4] = {c->bx, c->by, c->bh, c->bds};
+    for (int k = 0; k < 4; ++k) {
+        gl.src[k] = tmp + k * n;
+        gl.dst[k] = dst[k];
+    }
+    gl.nd = 4;
+    gl.isrc[0] = tid;
+    gl.idst[0] = c->bid;
+    gl.ni = 1;
+    gather_by_perm(c->s, (int)n, c->bperm, gl, &c->launches);
+    uint32_t t = 1;
+    while (t < 2u * (uint32_t)n) t <<= 1;
+    c->btmask = t - 1;
+    build_cell_table(c->s, (int)n, c->bkey, c->btkey, c->btstart, c->btend,
+                     c->btmask, &c->launches);
+    c->launches += 2;
+    cudaError_t e = cudaStreamSynchronize(c->s);
+    cudaFree(tmp);
+    cudaFree(tid);
+    if (e != cudaSuccess) return cuda_check(c, "load_background");
+    c->n_bg = (int)n;
+    return cuda_check(c, "load_background");
+}
+
+static Grid bg_grid(const sph_ctx *c) {
+    Grid g;
+    g.tkey = c->btkey;
+    g.tstart = c->btstart;
+    g.tend = c->btend;
+    g.tmask = c->btmask;
+    g.level_mask = (c->blmax >= 31) ? 0xffffffffu : ((1u << (c->blmax + 1)) - 1u);
+    g.mbits = c->bmbits;
+    g.nlev = c->blmax + 1;
+    g.bbox = c->bbbox;
+    for (int l = 0; l < MAX_LEVELS; ++l) g.lev[l] = c->blev[l];
+    return g;
+}
+
+static uint32_t read_u32(sph_ctx *c, const uint32_t *dev, sph_status *st) {
+    uint32_t v = 0;
+    cudaMemcpyAsync(&v, dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) *st = cuda_check(c, "sync");
+    return v;
 }
 
 // ================================================================ C ABI ==
@@ -548,6 +718,9 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
     ok = ok && dalloc(&c->lvl, N) && dalloc(&c->pk, N) && dalloc(&c->own, N) &&
          dalloc(&c->rev, N) && dalloc(&c->off, N + 1) &&
          dalloc(&c->longq, N) && dalloc(&c->d_nlong, 1);
+    ok = ok && dalloc(&c->tmp_a, N + 1) && dalloc(&c->tmp_b, N + 1) &&
+         dalloc(&c->closest, N) && dalloc(&c->d_mass, 2) &&
+         dalloc(&c->d_mass_part, 256);
     c->list_cap = std::min<size_t>(N * 48, 0xffffffffull);
     ok = ok && dalloc(&c->list, c->list_cap);
     if (!ok) {
@@ -574,9 +747,14 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
                               const sph_particles *src) {
     if (!c) return SPH_EINVAL;
     c->err.clear();
-    if (kind != SPH_FLUID)
-        return fail(c, SPH_EINVAL, "sph_load_particles: only SPH_FLUID is supported");
     if (n < 0 || (n > 0 && !src)) return fail(c, SPH_EINVAL, "sph_load_particles: bad n or src");
+    if (kind == SPH_BACKGROUND) {
+        sph_status st = load_background(c, n, src);
+        cudaStreamSynchronize(c->s);
+        return st;
+    }
+    if (kind != SPH_FLUID)
+        return fail(c, SPH_EINVAL, "sph_load_particles: unknown kind");
     if (n > c->cap) return fail(c, SPH_ECAPACITY, "sph_load_particles: n exceeds capacity");
     if (n > 0 && (!src->x || !src->y || !src->m || !src->h))
         return fail(c, SPH_EINVAL, "sph_load_particles: x, y, m, h are required");
@@ -664,6 +842,12 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
     put(c->f[F_H], src ? src->h : nullptr, 0);
     put(c->f[F_MMIN], src ? src->mmin : nullptr, 0);
     put(c->f[F_MMAX], src ? src->mmax : nullptr, 0);
+    c->next_id = n;
+    if (n > 0 && src->id) {
+        long long mx = -1;
+        for (long long i = 0; i < n; ++i) mx = std::max<long long>(mx, src->id[i]);
+        c->next_id = mx + 1;
+    }
     if (n > 0) {
         if (src->id) {
             cudaMemcpyAsync(c->id, src->id, sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
@@ -735,6 +919,146 @@ sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
         if (bad) return fail(c, SPH_ENONFINITE, "sph_step: non-finite rate");
     }
     return SPH_OK;
+}
+
+sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
+    if (!c) return SPH_EINVAL;
+    c->err.clear();
+    if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_adapt: no fluid particles loaded");
+    sph_adapt_stats z;
+    memset(&z, 0, sizeof(z));
+    z.n_before = c->n;
+    sph_status st = SPH_OK;
+    cudaEvent_t ev;
+    t_begin(c, 4, &ev);
+    launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass);
+    // resolution from the background (section 3.3)
+    if (c->n_bg > 0) {
+        BgArgs a;
+        a.n = c->n;
+        a.d = c->dom;
+        a.g = bg_grid(c);
+        a.x = c->f[F_X];
+        a.y = c->f[F_Y];
+        a.h = c->f[F_H];
+        a.mmin = c->f[F_MMIN];
+        a.mmax = c->f[F_MMAX];
+        a.nb = c->n_bg;
+        a.bx = c->bx;
+        a.by = c->by;
+        a.bh = c->bh;
+        a.bds = c->bds;
+        a.bid = c->bid;
+        a.rho0 = c->prm.rho0;
+        a.queue = c->tmp_b;
+        a.nqueue = c->d_total;
+        launch_bg_mref(c->s, a);
+        c->launches += 2;
+    }
+    // split pass (section 3.1): flag, scan, rank parents by id, emit
+    launch_split_flag(c->s, c->n, c->f[F_M], c->f[F_MMAX], c->tmp_a);
+    exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
+    c->launches += 1;
+    uint32_t count = read_u32(c, c->d_total, &st);
+    if (st != SPH_OK) return st;
+    if ((long long)c->n + 6ll * count > c->cap) {
+        t_end(c, 4, ev);
+        return fail(c, SPH_ECAPACITY, "sph_adapt: split children exceed the capacity");
+    }
+    if (count > 0) {
+        launch_split_collect(c->s, c->n, c->tmp_a, c->tmp_b, c->id, c->skey, c->perm);
+        radix_sort(c->s, (int)count, std::max(1, bits_for(c->next_id)), c->skey,
+                   c->perm, c->sc, &c->launches);
+        SplitArgs a;
+        a.n = c->n;
+        a.count = (int)count;
+        a.d = c->dom;
+        for (int k = 0; k < NSTATE; ++k) a.f[k] = c->f[k];
+        a.id = c->id;
+        a.parent = c->perm;
+        a.next_id = c->next_id;
+        a.alpha = c->prm.split_alpha;
+        a.eps = c->prm.split_eps;
+        launch_split_emit(c->s, a);
+        c->launches += 2;
+        c->n += 6 * (int)count;
+        c->next_id += 6ll * count;
+    }
+    z.n_split = count;
+    // merge rounds (section 3.2)
+    for (int r = 0; r < c->prm.merge_iters; ++r) {
+        if ((st = rebuild(c, false)) != SPH_OK) return st;
+        MergeArgs a;
+        a.n = c->n;
+        a.d = c->dom;
+        for (int k = 0; k < NSTATE; ++k) a.f[k] = c->f[k];
+        a.id = c->id;
+        a.off = c->off;
+        a.list = c->list;
+        a.closest = c->closest;
+        a.alive = c->tmp_a;
+        launch_merge(c->s, a);
+        exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
+        c->launches += 2;
+        uint32_t keep = read_u32(c, c->d_total, &st);
+        if (st != SPH_OK) return st;
+        if ((int)keep < c->n) {
+            CompactArgs ca;
+            for (int k = 0; k < NSTATE; ++k) {
+                ca.src[k] = c->f[k];
+                ca.dst[k] = c->falt[k];
+            }
+            ca.isrc = c->id;
+            ca.idst = c->id_alt;
+            launch_compact(c->s, c->n, c->tmp_a, c->tmp_b, ca);
+            c->launches += 1;
+            for (int k = 0; k < NSTATE; ++k) std::swap(c->f[k], c->falt[k]);
+            std::swap(c->id, c->id_alt);
+            z.n_merged += c->n - (int)keep;
+            c->n = (int)keep;
+        }
+    }
+    // shift rounds with Taylor correction, then the h update (3.2, 3.4)
+    ShiftArgs sa;
+    auto shift_args = [&]() {
+        sa.n = c->n;
+        sa.d = c->dom;
+        for (int k = 0; k < NSTATE; ++k) sa.f[k] = c->f[k];
+        sa.off = c->off;
+        sa.list = c->list;
+        sa.rho0 = c->prm.rho0;
+        sa.hdx = c->prm.hdx;
+        sa.rho = (double *)c->rhoR;
+        sa.drx = (double *)c->drx;
+        sa.dry = (double *)c->dry;
+        sa.du = (double *)c->dudt;
+        sa.dv = (double *)c->dvdt;
+        sa.dp = (double *)c->dpdt;
+        sa.hnew = (double *)c->V;
+    };
+    for (int r = 0; r < c->prm.shift_iters; ++r) {
+        if ((st = rebuild(c, false)) != SPH_OK) return st;
+        shift_args();
+        launch_shift_round(c->s, sa);
+        c->launches += 3;
+    }
+    if ((st = rebuild(c, false)) != SPH_OK) return st;
+    shift_args();
+    launch_h_update(c->s, sa);
+    c->launches += 2;
+    launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass + 1);
+    c->launches += 4;
+    t_end(c, 4, ev);
+    c->grid_valid = false;   // h changed since the last rebuild
+    c->rhs_valid = false;
+    double mass[2] = {0, 0};
+    cudaMemcpyAsync(mass, c->d_mass, sizeof(mass), cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_adapt");
+    z.mass_before = mass[0];
+    z.mass_after = mass[1];
+    z.n_after = c->n;
+    if (out) *out = z;
+    return cuda_check(c, "sph_adapt");
 }
 
 static sph_status read_R(sph_ctx *c, const void *src, double *dst, long long n) {
@@ -852,6 +1176,7 @@ sph_status sph_get_info(sph_ctx *c, sph_info *out) {
     if (!c || !out) return SPH_EINVAL;
     memset(out, 0, sizeof(*out));
     out->n = c->n;
+    out->n_bg = c->n_bg;
     double t = 0, dt = 0;
     cudaMemcpyAsync(&t, c->d_t, sizeof(double), cudaMemcpyDeviceToHost, c->s);
     if (c->have_dt) cudaMemcpyAsync(&dt, c->d_dt, sizeof(double), cudaMemcpyDeviceToHost, c->s);

@@ -67,6 +67,13 @@ class Particles(ctypes.Structure):
         ("id", ctypes.POINTER(ctypes.c_int64))]
 
 
+class AdaptStats(ctypes.Structure):
+    _fields_ = [("n_before", ctypes.c_longlong), ("n_split", ctypes.c_longlong),
+                ("n_merged", ctypes.c_longlong), ("n_after", ctypes.c_longlong),
+                ("mass_before", ctypes.c_double),
+                ("mass_after", ctypes.c_double)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_longlong), ("n_wall", ctypes.c_longlong),
                 ("n_bg", ctypes.c_longlong), ("t", ctypes.c_double),
@@ -102,6 +109,8 @@ def lib(build_if_missing: bool = True):
     L.sph_rhs.argtypes = [ctx]
     L.sph_step.restype = ctypes.c_int
     L.sph_step.argtypes = [ctx, ctypes.c_int, _D]
+    L.sph_adapt.restype = ctypes.c_int
+    L.sph_adapt.argtypes = [ctx, P(AdaptStats)]
     L.sph_read.restype = ctypes.c_int
     L.sph_read.argtypes = [ctx, ctypes.c_int, ctypes.c_void_p,
                            ctypes.c_longlong, P(ctypes.c_longlong)]
@@ -216,6 +225,11 @@ class Simulation:
         self._check(self._L.sph_step(self._ctx, int(nsteps),
                                      ctypes.byref(t) if want_time else None))
         return t.value if want_time else None
+
+    def adapt(self) -> dict:
+        z = AdaptStats()
+        self._check(self._L.sph_adapt(self._ctx, ctypes.byref(z)))
+        return {k: getattr(z, k) for k, _ in AdaptStats._fields_}
 
     def read(self, field: str) -> np.ndarray:
         f = FIELD[field]
