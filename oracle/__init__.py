@@ -152,6 +152,10 @@ def lib():
                                     _D, _D, _D, _D,
                                     ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(_AdaptStats)]
+            L.orc_set_walls.restype = None
+            L.orc_set_walls.argtypes = [ctypes.c_int] + [_D] * 6
+            L.orc_wall_bc.restype = None
+            L.orc_wall_bc.argtypes = [_P, ctypes.POINTER(_State), _D, _D, _D]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
             _lib = L
@@ -441,3 +445,25 @@ def adapt(P, st, bg=None, next_id=None):
                         _d(bh), _d(bd), ctypes.byref(nid), ctypes.byref(z))
     st["n"] = s.n
     return r, {k: getattr(z, k) for k, _ in _AdaptStats._fields_}, nid.value
+
+
+# --------------------------------------------------------------- walls --
+def set_walls(walls):
+    """Register dummy wall particles (dict x, y, h, m, optional u, v) for
+    rhs/step/adapt; None clears them."""
+    if walls is None or len(walls["x"]) == 0:
+        lib().orc_set_walls(0, None, None, None, None, None, None)
+        return
+    n = len(walls["x"])
+    arrs = [_f64(walls[k]) for k in ("x", "y", "h", "m")]
+    arrs.append(_f64(walls.get("u", np.zeros(n))))
+    arrs.append(_f64(walls.get("v", np.zeros(n))))
+    lib().orc_set_walls(n, *[_d(a) for a in arrs])
+
+
+def wall_bc(P, st, nw):
+    """Wall pressure and extrapolated velocity of the registered walls."""
+    out = [np.zeros(max(nw, 1)) for _ in range(3)]
+    s = _cstate(st)
+    lib().orc_wall_bc(ctypes.byref(P), ctypes.byref(s), *[_d(a) for a in out])
+    return {"p": out[0][:nw], "ugx": out[1][:nw], "ugy": out[2][:nw]}

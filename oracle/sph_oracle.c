@@ -352,6 +352,95 @@ void orc_cell_keys(const orc_params *P, double c0, int n, const double *x,
     }
 }
 
+
+/* ------------------------------------------------------------------------
+ * Dummy wall particles (section 2.2, Adami et al.).  For wall particle w,
+ * over fluid neighbours f (r_wf < 3 max(h_w, h_f)), with
+ * W_wf = W(r_wf, (h_w + h_f)/2):
+ *   u^_w = sum u_f W_wf / sum W_wf                        (Eq. shepard)
+ *   u_w  = 2 u_wall - u^_w                                (Eq. bc-wall)
+ *   p_w  = sum p_f W_wf / sum W_wf                        (Eq. bc-pre, g = a_w = 0)
+ * and p_w = 0, u^ = 0 without fluid neighbours.  Walls join the fluid's
+ * sums as neighbours: mass m_w in the density, beta, p_avg and shifting
+ * sums; in pass B, the prescribed wall velocity in the divergence term
+ * (no penetration), the extrapolated velocity in the viscous term
+ * (no slip), p_w in the pressure terms, with rho_w = rho0 and beta_w = 1.
+ * Walls have no rates of their own.
+ * ---------------------------------------------------------------------- */
+static int g_nw = 0;
+static double *g_w = NULL;   /* x, y, h, m, uw, vw, pw, ugx, ugy */
+
+void orc_set_walls(int n, const double *x, const double *y, const double *h,
+                   const double *m, const double *uw, const double *vw) {
+    free(g_w);
+    g_w = NULL;
+    g_nw = n > 0 ? n : 0;
+    if (g_nw == 0) return;
+    g_w = (double *)calloc((size_t)g_nw * 9, sizeof(double));
+    memcpy(g_w, x, sizeof(double) * n);
+    memcpy(g_w + n, y, sizeof(double) * n);
+    memcpy(g_w + 2 * n, h, sizeof(double) * n);
+    memcpy(g_w + 3 * n, m, sizeof(double) * n);
+    if (uw) memcpy(g_w + 4 * n, uw, sizeof(double) * n);
+    if (vw) memcpy(g_w + 5 * n, vw, sizeof(double) * n);
+}
+
+#define WX(k) g_w[(k)]
+#define WY(k) g_w[g_nw + (k)]
+#define WH(k) g_w[2 * g_nw + (k)]
+#define WM(k) g_w[3 * g_nw + (k)]
+#define WU(k) g_w[4 * g_nw + (k)]
+#define WV(k) g_w[5 * g_nw + (k)]
+#define WP(k) g_w[6 * g_nw + (k)]
+#define WGX(k) g_w[7 * g_nw + (k)]
+#define WGY(k) g_w[8 * g_nw + (k)]
+
+void orc_wall_bc(const orc_params *P, const orc_state *s, double *pw,
+                 double *ugx, double *ugy) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int w = 0; w < g_nw; ++w) {
+        double sw = 0.0, su = 0.0, sv = 0.0, sp = 0.0;
+        for (int f = 0; f < s->n; ++f) {
+            if (!orc_is_neighbor(P, WX(w), WY(w), WH(w), s->x[f], s->y[f],
+                                 s->h[f]))
+                continue;
+            double dx, dy;
+            separation(P, WX(w), WY(w), s->x[f], s->y[f], &dx, &dy);
+            double W = orc_W(sqrt(dx * dx + dy * dy), 0.5 * (WH(w) + s->h[f]));
+            sw += W;
+            su += s->u[f] * W;
+            sv += s->v[f] * W;
+            sp += s->p[f] * W;
+        }
+        double uh = 0.0, vh = 0.0, p = 0.0;
+        if (sw > 0.0) {
+            uh = su / sw;
+            vh = sv / sw;
+            p = sp / sw;
+        }
+        pw[w] = p;
+        ugx[w] = 2.0 * WU(w) - uh;
+        ugy[w] = 2.0 * WV(w) - vh;
+    }
+}
+
+static void wall_bc_update(const orc_params *P, const orc_state *s) {
+    if (g_nw > 0)
+        orc_wall_bc(P, s, &WP(0), &WGX(0), &WGY(0));
+}
+
+/* Wall neighbours of fluid particle i, ascending wall index. */
+static int wall_nbrs(const orc_params *P, double xi, double yi, double hi,
+                     int *out, int cap) {
+    int c = 0;
+    for (int w = 0; w < g_nw; ++w)
+        if (orc_is_neighbor(P, xi, yi, hi, WX(w), WY(w), WH(w))) {
+            if (c < cap) out[c] = w;
+            ++c;
+        }
+    return c;
+}
+
 /* ------------------------------------------------------------------------
  * Pass A: summation density (section 2, Eq. sd-gather), variable-h
  * correction beta (Eq. beta), average pressure (Eq. pavg, N_i counts i
@@ -394,6 +483,32 @@ int orc_pass_a(const orc_params *P, int n, const double *x, const double *y,
                 ay += f * dy;
                 sax += fabs(f * dx);
                 say += fabs(f * dy);
+            }
+        }
+        if (g_nw > 0) {
+            int wl[2048];
+            int nwl = wall_nbrs(P, x[i], y[i], h[i], wl, 2048);
+            if (nwl > 2048) nwl = 2048;
+            for (int k = 0; k < nwl; ++k) {
+                int w = wl[k];
+                double dx, dy;
+                separation(P, x[i], y[i], WX(w), WY(w), &dx, &dy);
+                double r = sqrt(dx * dx + dy * dy);
+                rho += WM(w) * orc_W(r, h[i]);
+                srw += WM(w) * r * orc_dWdr(r, h[i]);
+                psum += WP(w);
+                spabs += fabs(WP(w));
+                cnt += 1;
+                if (r > 0.0) {
+                    double hb = 0.5 * (h[i] + WH(w));
+                    double ratio = w_of_q(r / hb) / w_xi;
+                    double f = (WM(w) / P->rho0) * (1.0 + 0.24 * p4(ratio)) *
+                               orc_dWdr(r, hb) / r;
+                    ax += f * dx;
+                    ay += f * dy;
+                    sax += fabs(f * dx);
+                    say += fabs(f * dy);
+                }
             }
         }
         double beta = -srw / (rho * DIM);
@@ -521,6 +636,59 @@ void orc_pass_b(const orc_params *P, double dt, int n, const double *x,
             s_vx += fabs(visc) * au;
             s_vy += fabs(visc) * av;
         }
+        if (g_nw > 0) {
+            int wl[2048];
+            int nwl = wall_nbrs(P, x[i], y[i], h[i], wl, 2048);
+            if (nwl > 2048) nwl = 2048;
+            for (int k = 0; k < nwl; ++k) {
+                int w = wl[k];
+                double dx, dy;
+                separation(P, x[i], y[i], WX(w), WY(w), &dx, &dy);
+                double r2 = dx * dx + dy * dy;
+                double r = sqrt(r2);
+                double gi = 0.0, gj = 0.0;
+                if (r > 0.0) {
+                    gi = orc_dWdr(r, h[i]) / r;
+                    gj = orc_dWdr(r, WH(w)) / r;
+                }
+                double gWix = gi * dx, gWiy = gi * dy;
+                double gWjx = gj * dx, gWjy = gj * dy;
+                double rdotgbar = 0.5 * (gi + gj) * r2;
+                double Vj = WM(w) / P->rho0;
+                /* prescribed wall velocity: no penetration */
+                double uij = u[i] - WU(w), vij = v[i] - WV(w);
+                double pref = (P->pavg_mode == 0) ? pavg_i : 0.0;
+                double Pj = (WP(w) - pref) / (P->rho0 * P->rho0);
+                double Pj_abs = (fabs(WP(w)) + fabs(pref)) / (P->rho0 * P->rho0);
+                double nu_j = P->alpha_e * P->cs * WH(w) / 8.0;
+                double nu_ij = 4.0 * nu_i * nu_j / (nu_i + nu_j);
+                double dden = P->edac_diff_denominator ? (r2 + eta) : 1.0;
+                div += Vj * (uij * gWix + vij * gWiy);
+                diff += Vj * nu_ij * (p[i] - WP(w)) * rdotgbar / dden;
+                double fx = Pi * gWix + Pj * gWjx;
+                double fy = Pi * gWiy + Pj * gWjy;
+                tvf += WM(w) * (dux * fx + duy * fy);
+                ax -= WM(w) * fx;
+                ay -= WM(w) * fy;
+                /* extrapolated wall velocity: no slip */
+                double ug = u[i] - WGX(w), vg = v[i] - WGY(w);
+                double visc = WM(w) * (4.0 * P->nu / (rho_i + P->rho0)) *
+                              rdotgbar / (r2 + eta);
+                vx += visc * ug;
+                vy += visc * vg;
+                double au = fabs(u[i]) + fabs(WU(w)), av = fabs(v[i]) + fabs(WV(w));
+                s_div += Vj * (au * fabs(gWix) + av * fabs(gWiy));
+                s_diff += Vj * nu_ij * (fabs(p[i]) + fabs(WP(w))) *
+                          fabs(rdotgbar) / dden;
+                double afx = Pi_abs * fabs(gWix) + Pj_abs * fabs(gWjx);
+                double afy = Pi_abs * fabs(gWiy) + Pj_abs * fabs(gWjy);
+                s_tvf += WM(w) * (fabs(dux) * afx + fabs(duy) * afy);
+                s_ax += WM(w) * afx;
+                s_ay += WM(w) * afy;
+                s_vx += fabs(visc) * (fabs(u[i]) + fabs(WGX(w)));
+                s_vy += fabs(visc) * (fabs(v[i]) + fabs(WGY(w)));
+            }
+        }
         double rf = P->edac_rho_factor ? rho_i : 1.0;
         o->dpdt[i] = (P->rho0 * c2 / beta_i) * div + diff / beta_i + rf * tvf;
         o->dudt[i] = ax + vx / beta_i;
@@ -568,6 +736,7 @@ static long long neighbors_auto(const orc_params *P, int n, const double *x,
 
 int orc_rhs(const orc_params *P, double dt, const orc_state *s,
             orc_rhs_out *o) {
+    wall_bc_update(P, s);
     neighbors_auto(P, s->n, s->x, s->y, s->h);
     int deg = orc_pass_a(P, s->n, s->x, s->y, s->h, s->m, s->p, g_off, g_nbr,
                          o);
@@ -885,8 +1054,9 @@ int orc_merge_round(const orc_params *P, orc_state *s) {
     return pairs;
 }
 
-/* Summation density, limited shift (Eqs. shift-deltar, shift-limit, same
- * readings as pass A) and the gradients of the Taylor correction:
+/* Summation density (walls included), limited shift (Eqs. shift-deltar,
+ * shift-limit, same readings as pass A, walls included) and the gradients
+ * of the Taylor correction over fluid neighbours:
  * grad phi_i = sum_{j != i} V_j (phi_j - phi_i) grad_i W(r_ij, h_i) with
  * V_j = m_j / rho_j (the paper names no gradient operator; this is the
  * first-order form consistent with its gather sums). */
@@ -904,6 +1074,16 @@ void orc_shift_compute(const orc_params *P, const orc_state *s, double *rho,
             double dx, dy;
             separation(P, s->x[i], s->y[i], s->x[j], s->y[j], &dx, &dy);
             r_ += s->m[j] * orc_W(sqrt(dx * dx + dy * dy), s->h[i]);
+        }
+        if (g_nw > 0) {
+            int wl[2048];
+            int nwl = wall_nbrs(P, s->x[i], s->y[i], s->h[i], wl, 2048);
+            if (nwl > 2048) nwl = 2048;
+            for (int k = 0; k < nwl; ++k) {
+                double dx, dy;
+                separation(P, s->x[i], s->y[i], WX(wl[k]), WY(wl[k]), &dx, &dy);
+                r_ += WM(wl[k]) * orc_W(sqrt(dx * dx + dy * dy), s->h[i]);
+            }
         }
         rho[i] = r_;
     }
@@ -933,6 +1113,24 @@ void orc_shift_compute(const orc_params *P, const orc_state *s, double *rho,
             vy += Vj * dv * g * dy;
             px += Vj * dp * g * dx;
             py += Vj * dp * g * dy;
+        }
+        if (g_nw > 0) {
+            int wl[2048];
+            int nwl = wall_nbrs(P, s->x[i], s->y[i], s->h[i], wl, 2048);
+            if (nwl > 2048) nwl = 2048;
+            for (int k = 0; k < nwl; ++k) {
+                int w = wl[k];
+                double dx, dy;
+                separation(P, s->x[i], s->y[i], WX(w), WY(w), &dx, &dy);
+                double r = sqrt(dx * dx + dy * dy);
+                if (!(r > 0.0)) continue;
+                double hb = 0.5 * (s->h[i] + WH(w));
+                double ratio = w_of_q(r / hb) / w_xi;
+                double f = (WM(w) / P->rho0) * (1.0 + 0.24 * p4(ratio)) *
+                           orc_dWdr(r, hb) / r;
+                ax += f * dx;
+                ay += f * dy;
+            }
         }
         double c = -0.5 * s->h[i] * s->h[i];
         double sx = c * ax, sy = c * ay;
@@ -970,8 +1168,8 @@ void orc_shift_round(const orc_params *P, orc_state *s) {
     free(b);
 }
 
-/* h_i = hdx (mbar_i / rho_i)^(1/2): mbar_i the mean mass over N(i) (i
- * included), rho_i the summation density (section 3.1, "h = C
+/* h_i = hdx (mbar_i / rho_i)^(1/2): mbar_i the mean mass over the fluid
+ * N(i) (i included), rho_i the summation density with walls (section 3.1, "h = C
  * (m/rho)^(1/d)" with the neighbourhood-average mass).  One evaluation. */
 void orc_h_update(const orc_params *P, orc_state *s) {
     int n = s->n;
@@ -990,6 +1188,16 @@ void orc_h_update(const orc_params *P, orc_state *s) {
             rho += s->m[j] * orc_W(sqrt(dx * dx + dy * dy), s->h[i]);
             msum += s->m[j];
             cnt += 1;
+        }
+        if (g_nw > 0) {
+            int wl[2048];
+            int nwl = wall_nbrs(P, s->x[i], s->y[i], s->h[i], wl, 2048);
+            if (nwl > 2048) nwl = 2048;
+            for (int k = 0; k < nwl; ++k) {
+                double dx, dy;
+                separation(P, s->x[i], s->y[i], WX(wl[k]), WY(wl[k]), &dx, &dy);
+                rho += WM(wl[k]) * orc_W(sqrt(dx * dx + dy * dy), s->h[i]);
+            }
         }
         rn[i] = rho;
         hn[i] = P->hdx * sqrt((msum / cnt) / rho);

@@ -115,6 +115,16 @@ void orc_pec_correct(const orc_params *P, double dt, int n, const double *x0,
                      const double *drx, const double *dry, double *x,
                      double *y, double *u, double *v, double *p);
 
+/* ---- dummy wall particles (section 2.2) ---- */
+/* Register the wall set used by orc_rhs / orc_step (copied; n = 0 clears
+ * it): positions, smoothing lengths, masses and prescribed velocities. */
+void orc_set_walls(int n, const double *x, const double *y, const double *h,
+                   const double *m, const double *uw, const double *vw);
+/* Wall pressure and extrapolated velocity from the fluid (Eqs. bc-wall,
+ * shepard, bc-pre with g = a_w = 0) for the registered walls. */
+void orc_wall_bc(const orc_params *P, const orc_state *s, double *pw,
+                 double *ugx, double *ugy);
+
 /* ---- adaptive refinement (section 3) ---- */
 typedef struct {
     long long n_before, n_split, n_merged, n_after;
