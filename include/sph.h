@@ -118,6 +118,7 @@ typedef struct {
     int levels;           /* number of cell levels (top level spans the domain) */
     long long steps;      /* PEC steps taken */
     long long launches;   /* kernels launched by this context so far */
+    long long next_id;    /* id the next split child will receive */
 } sph_info;
 
 /* Counts and masses of one sph_adapt call. */

@@ -297,6 +297,11 @@ __global__ void k_density_mbar(ShiftArgs a, int want_h) {
         rho += m[j] * qw(sqrt(r2) * hinv);
         msum += m[j];
     }
+    if (a.w.n > 0) {
+        for_each_wall(a.w, a.d, xi, yi, hi, [&](int k, double, double, double r2) {
+            rho += a.w.m[k] * qw(sqrt(r2) * hinv);
+        });
+    }
     rho *= SIGMA_N * hinv * hinv;
     a.rho[i] = rho;
     if (want_h) a.hnew[i] = a.hdx * sqrt((msum / (double)(e - b)) / rho);
@@ -336,6 +341,20 @@ __global__ void k_shift_compute(ShiftArgs a) {
         gvy += Vg * dv * dy;
         gpx += Vg * dp * dx;
         gpy += Vg * dp * dy;
+    }
+    if (a.w.n > 0) {
+        for_each_wall(a.w, a.d, xi, yi, hi, [&](int k, double dx, double dy,
+                                               double r2) {
+            const double r = sqrt(r2);
+            if (!(r > 0.0)) return;
+            const double hb = 0.5 * (hi + a.w.h[k]), hbinv = 1.0 / hb;
+            double ratio = qw(r * hbinv) * inv_wxi;
+            ratio *= ratio;
+            const double f = (a.w.m[k] / a.rho0) * (1.0 + 0.24 * ratio * ratio) *
+                             (SIGMA_N * hbinv * hbinv * hbinv) * qdw(r * hbinv) / r;
+            ax += f * dx;
+            ay += f * dy;
+        });
     }
     const double c = -0.5 * hi * hi;
     double sx = c * ax, sy = c * ay;

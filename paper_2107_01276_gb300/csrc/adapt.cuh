@@ -3,6 +3,7 @@
 #pragma once
 
 #include "sph_internal.cuh"
+#include "walls.cuh"
 
 namespace sph {
 
@@ -56,6 +57,7 @@ struct ShiftArgs {
     const uint32_t *off, *list;
     double rho0, hdx;
     double *rho, *drx, *dry, *du, *dv, *dp, *hnew;   // scratch
+    WallView w;                 // walls join the densities and the shift
 };
 
 void launch_bg_mref(cudaStream_t s, const BgArgs &a);

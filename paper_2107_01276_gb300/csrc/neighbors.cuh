@@ -41,33 +41,52 @@ __device__ __forceinline__ bool table_lookup(const Grid &g, uint64_t key,
     return false;
 }
 
-// Cell index range [a0, a1] on one axis of one level for the query square
-// [x - Q, x + Q]; on a periodic axis `wrap` is set and indices are taken
-// modulo n (the whole axis if the range covers it).  Non-periodic ranges
-// are clipped to the level's occupied bounding box.
-__device__ __forceinline__ void axis_range(const Domain &d, const Level &L,
-                                           const int *bb, int ax, double x,
-                                           double Q, int &a0, int &a1,
-                                           bool &wrap) {
+// Cell index ranges on one axis of one level for the query interval
+// [x - Q, x + Q], clipped to the level's occupied bounding box [b0, b1].
+// On a periodic axis the interval is cut into pieces that each map into
+// [b0, b1] by one shift of the period; r[k] = {first, last, shift} with
+// cell index = c + shift.  Returns the number of pieces (0..3).
+struct AxisPieces {
+    int first[3], last[3], shift[3];
+    int n;
+};
+
+__device__ __forceinline__ void axis_pieces(const Domain &d, const Level &L,
+                                            const int *bb, int ax, double x,
+                                            double Q, AxisPieces &r) {
     const int nc = L.n[ax];
+    const int b0 = __ldg(&bb[2 * ax]), b1 = __ldg(&bb[2 * ax + 1]);
     double lo = __ddiv_rn(__dsub_rn(__dsub_rn(x, Q), d.lo[ax]), L.w[ax]);
     double hi = __ddiv_rn(__dsub_rn(__dadd_rn(x, Q), d.lo[ax]), L.w[ax]);
     double flo = floor(lo), fhi = floor(hi);
+    r.n = 0;
     if (d.periodic[ax]) {
         if (fhi - flo + 1.0 >= (double)nc) {
-            a0 = 0;
-            a1 = nc - 1;
-            wrap = false;
-        } else {
-            a0 = (int)flo;
-            a1 = (int)fhi;
-            wrap = true;
+            r.first[0] = b0;
+            r.last[0] = b1;
+            r.shift[0] = 0;
+            r.n = 1;
+            return;
+        }
+        const int a0 = (int)flo, a1 = (int)fhi;
+        for (int k = -1; k <= 1; ++k) {
+            const int lo_k = max(a0, b0 + k * nc), hi_k = min(a1, b1 + k * nc);
+            if (lo_k <= hi_k) {
+                r.first[r.n] = lo_k;
+                r.last[r.n] = hi_k;
+                r.shift[r.n] = -k * nc;
+                r.n++;
+            }
         }
     } else {
-        int b0 = bb[2 * ax], b1 = bb[2 * ax + 1];
-        a0 = flo < (double)b0 ? b0 : (int)flo;
-        a1 = fhi > (double)b1 ? b1 : (int)fhi;
-        wrap = false;
+        const int a0 = flo < (double)b0 ? b0 : (int)flo;
+        const int a1 = fhi > (double)b1 ? b1 : (int)fhi;
+        if (a0 <= a1) {
+            r.first[0] = a0;
+            r.last[0] = a1;
+            r.shift[0] = 0;
+            r.n = 1;
+        }
     }
 }
 
@@ -87,22 +106,24 @@ __device__ __forceinline__ void for_each_candidate(const Grid &g,
         const Level &L = g.lev[l];
         // margin covers rounding in level and cell assignment
         const double Q = fmax(Ri, L.c) * (1.0 + 1e-7);
-        int x0, x1, y0, y1;
-        bool wx, wy;
-        axis_range(d, L, bb, 0, xi, Q, x0, x1, wx);
-        axis_range(d, L, bb, 1, yi, Q, y0, y1, wy);
+        AxisPieces px, py;
+        axis_pieces(d, L, bb, 0, xi, Q, px);
+        if (px.n == 0) continue;
+        axis_pieces(d, L, bb, 1, yi, Q, py);
         const uint64_t lbits = (uint64_t)l << (2 * g.mbits);
-        for (int cy = y0; cy <= y1; ++cy) {
-            int ry = cy;
-            if (wy) ry = ((cy % L.n[1]) + L.n[1]) % L.n[1];
-            const uint64_t my = spread2((uint64_t)ry) << 1;
-            for (int cx = x0; cx <= x1; ++cx) {
-                int rx = cx;
-                if (wx) rx = ((cx % L.n[0]) + L.n[0]) % L.n[0];
-                uint32_t s, e;
-                if (!table_lookup(g, lbits | my | spread2((uint64_t)rx), s, e))
-                    continue;
-                for (uint32_t j = s; j < e; ++j) f((int)j);
+        for (int ky = 0; ky < py.n; ++ky) {
+            for (int cy = py.first[ky]; cy <= py.last[ky]; ++cy) {
+                const uint64_t my = spread2((uint64_t)(cy + py.shift[ky])) << 1;
+                for (int kx = 0; kx < px.n; ++kx) {
+                    for (int cx = px.first[kx]; cx <= px.last[kx]; ++cx) {
+                        uint32_t s, e;
+                        if (!table_lookup(g, lbits | my |
+                                                 spread2((uint64_t)(cx + px.shift[kx])),
+                                          s, e))
+                            continue;
+                        for (uint32_t j = s; j < e; ++j) f((int)j);
+                    }
+                }
             }
         }
     }

@@ -126,7 +126,33 @@ __global__ void __launch_bounds__(128)
             ay += f * dy;
         }
     }
-    const int cnt = (int)(e - b);
+    int cnt = (int)(e - b);
+    if (a.w.n > 0) {
+        const double xi = a.x[i], yi = a.y[i], hid = a.h[i];
+        for_each_wall(a.w, a.d, xi, yi, hid, [&](int k, double dxd, double dyd,
+                                                double r2d) {
+            const R dx = (R)dxd, dy = (R)dyd;
+            const R r = sqrt((R)r2d);
+            const R mk = (R)a.w.m[k];
+            const R q = r * hinv;
+            rho += mk * qs_w<R>(q);
+            srw += mk * r * qs_dw<R>(q);
+            psum += (R)a.w.p[k];
+            cnt += 1;
+            if (r > R(0)) {
+                const R hb = R(0.5) * (hi + (R)a.w.h[k]);
+                const R hbinv = R(1) / hb;
+                const R qb = r * hbinv;
+                R ratio = qs_w<R>(qb) * inv_wxi;
+                ratio *= ratio;
+                const R f = mk * (R(1) + R(0.24) * ratio * ratio) *
+                            (sigma_norm<R>() * hbinv * hbinv * hbinv) *
+                            qs_dw<R>(qb) / r;
+                ax += f * dx;
+                ay += f * dy;
+            }
+        });
+    }
     const R sig = sigma_norm<R>() * hinv * hinv;
     rho *= sig;
     const R beta = -(sig * hinv * srw) / (rho * R(2));
@@ -226,6 +252,46 @@ __global__ void __launch_bounds__(128)
         vx += visc * uij;
         vy += visc * vij;
     }
+    if (a.w.n > 0) {
+        const double xi = a.x[i], yi = a.y[i];
+        const R rho0 = (R)a.rho0;
+        for_each_wall(a.w, a.d, xi, yi, (double)a.h[i], [&](int k, double dxd,
+                                                           double dyd, double r2d) {
+            const R dx = (R)dxd, dy = (R)dyd, r2 = (R)r2d;
+            const R r = sqrt(r2);
+            const R hk = (R)a.w.h[k];
+            R gi = 0, gj = 0;
+            if (r > R(0)) {
+                const R hkinv = R(1) / hk;
+                const R rinv = R(1) / r;
+                gi = dsig_i * qs_dw<R>(r * hinv) * rinv;
+                gj = sigma_norm<R>() * hkinv * hkinv * hkinv *
+                     qs_dw<R>(r * hkinv) * rinv;
+            }
+            const R rdg = R(0.5) * (gi + gj) * r2;
+            const R mk = (R)a.w.m[k];
+            const R Vk = mk / rho0;
+            // prescribed wall velocity (no penetration) in the divergence
+            const R uij = ui - (R)a.w.uw[k], vij = vi - (R)a.w.vw[k];
+            const R pk = (R)a.w.p[k];
+            const R pref = a.pavg_mode == 0 ? pavg_i : R(0);
+            const R Pk = (pk - pref) / (rho0 * rho0);
+            const R nu_k = (R)a.alpha_e * (R)a.cs * hk / R(8);
+            const R nu_ik = R(4) * nu_i * nu_k / (nu_i + nu_k);
+            const R dden = a.diff_denominator ? (r2 + eta) : R(1);
+            div += Vk * (uij * gi * dx + vij * gi * dy);
+            diff += Vk * nu_ik * (pi - pk) * rdg / dden;
+            const R fx = (Pi * gi + Pk * gj) * dx;
+            const R fy = (Pi * gi + Pk * gj) * dy;
+            tvf += mk * (dux * fx + duy * fy);
+            fax -= mk * fx;
+            fay -= mk * fy;
+            // extrapolated wall velocity (no slip) in the viscous term
+            const R visc = mk * (four_nu / (rho_i + rho0)) * rdg / (r2 + eta);
+            vx += visc * (ui - (R)a.w.ugx[k]);
+            vy += visc * (vi - (R)a.w.ugy[k]);
+        });
+    }
     const R rf = a.rho_factor ? rho_i : R(1);
     const R dpdt = ((R)a.rho0 * (R)a.cs * (R)a.cs / beta_i) * div +
                    diff / beta_i + rf * tvf;
@@ -237,6 +303,40 @@ __global__ void __launch_bounds__(128)
     if (!isfinite((double)dpdt) || !isfinite((double)dudt) ||
         !isfinite((double)dvdt))
         atomicOr(a.nonfinite, 1);
+}
+
+// --------------------------------------------------------- wall BC -----
+// Section 2.2 (Adami dummy walls), per wall particle w over fluid f with
+// W_wf = W(r_wf, (h_w + h_f)/2): u^ = sum u_f W / sum W (Eq. shepard),
+// u_ghost = 2 u_wall - u^ (Eq. bc-wall), p_w = sum p_f W / sum W (Eq.
+// bc-pre with g = a_w = 0); p_w = 0 and u^ = 0 without fluid in range.
+__global__ void k_wall_bc(WallBcArgs a) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.w.n) return;
+    const double xw = a.w.x[k], yw = a.w.y[k], hw = a.w.h[k];
+    double sw = 0, su = 0, sv = 0, sp = 0;
+    for_each_candidate(a.g, a.d, 0, xw, yw, hw, [&](int f) {
+        const double xf = __ldg(&a.x[f]), yf = __ldg(&a.y[f]), hf = __ldg(&a.h[f]);
+        if (!pred_fp64(a.d, xw, yw, hw, xf, yf, hf)) return;
+        double dx = min_image(a.d, 0, xw - xf), dy = min_image(a.d, 1, yw - yf);
+        const double hb = 0.5 * (hw + hf);
+        const double hbinv = 1.0 / hb;
+        const double W = sigma_norm<double>() * hbinv * hbinv *
+                         qs_w<double>(sqrt(dx * dx + dy * dy) * hbinv);
+        sw += W;
+        su += a.u[f] * W;
+        sv += a.v[f] * W;
+        sp += a.p[f] * W;
+    });
+    double uh = 0, vh = 0, p = 0;
+    if (sw > 0) {
+        uh = su / sw;
+        vh = sv / sw;
+        p = sp / sw;
+    }
+    a.pw[k] = p;
+    a.ugx[k] = 2.0 * a.w.uw[k] - uh;
+    a.ugy[k] = 2.0 * a.w.vw[k] - vh;
 }
 
 // ---------------------------------------------------- neighbour CSR dump --
@@ -354,6 +454,9 @@ template void launch_pass_b<float>(cudaStream_t, const PassBArgs<float> &);
 template void launch_pec<double>(cudaStream_t, const PecArgs<double> &);
 template void launch_pec<float>(cudaStream_t, const PecArgs<float> &);
 
+void launch_wall_bc(cudaStream_t s, const WallBcArgs &a) {
+    if (a.w.n > 0) k_wall_bc<<<nblk(a.w.n, 128), 128, 0, s>>>(a);
+}
 void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,
                     const uint32_t *list, const int64_t *id, int64_t *out) {
     if (n > 0) k_nbr_ids<<<nblk(n, 128), 128, 0, s>>>(n, off, list, id, out);

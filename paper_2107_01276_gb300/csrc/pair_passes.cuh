@@ -4,6 +4,7 @@
 
 #include "neighbors.cuh"
 #include "sph_internal.cuh"
+#include "walls.cuh"
 
 namespace sph {
 
@@ -16,6 +17,7 @@ struct PassAArgs {
     const float4 *pk;          // anchor coordinates (mixed path)
     const double *x, *y, *h;   // FP64 positions and smoothing lengths
     const R *m, *p;            // pair-arithmetic copies
+    WallView w;
     double rho0;
     R *rho, *beta, *pavg, *drx, *dry, *V, *rb2;
     int *nnb;
@@ -30,6 +32,7 @@ struct PassBArgs {
     const float4 *pk;
     const double *x, *y, *h;
     const R *m, *p, *u, *v;
+    WallView w;
     const R *rho, *beta, *pavg, *drx, *dry, *V, *rb2;
     const double *dt;          // device scalar
     double rho0, cs, nu, alpha_e;

@@ -36,6 +36,34 @@ enum {
     F_X0, F_Y0, F_U0, F_V0, F_P0, NF
 };
 
+// A particle set that does not move between loads (background, walls),
+// kept sorted by its own multi-level cell keys with its own cell table.
+struct StaticSet {
+    int n = 0, cap = 0;
+    double *x = nullptr, *y = nullptr, *h = nullptr;
+    double *ex[3] = {nullptr, nullptr, nullptr};   // extra per-particle fields
+    int nex = 0;
+    int64_t *id = nullptr;                         // load index
+    uint64_t *key = nullptr, *tkey = nullptr;
+    uint32_t *perm = nullptr, *tstart = nullptr, *tend = nullptr;
+    int *bbox = nullptr;
+    uint32_t *mask = nullptr;
+    uint32_t tmask = 0;
+    double c0 = 0.0;
+    int lmax = 0, mbits = 1, lbits = 0;
+    Level lev[MAX_LEVELS];
+    SortScratch sc;
+};
+
+static void free_set(StaticSet *S) {
+    void *ps[] = {S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2], S->id,
+                  S->key, S->tkey, S->perm, S->tstart, S->tend, S->bbox,
+                  S->mask, S->sc.key_alt, S->sc.val_alt, S->sc.counts,
+                  S->sc.scan_tmp};
+    for (void *p : ps) cudaFree(p);
+    *S = StaticSet();
+}
+
 struct sph_ctx {
     sph_params prm;
     cudaStream_t s = nullptr;
@@ -83,19 +111,9 @@ struct sph_ctx {
     uint32_t *tmp_a = nullptr, *tmp_b = nullptr;   // N + 1 each
     int *closest = nullptr;
     double *d_mass = nullptr, *d_mass_part = nullptr;  // [2], [256]
-    // background set (section 3.3), sorted by its own cell keys
-    int n_bg = 0, bg_cap = 0;
-    double *bx = nullptr, *by = nullptr, *bh = nullptr, *bds = nullptr;
-    int64_t *bid = nullptr;
-    uint64_t *bkey = nullptr, *btkey = nullptr;
-    uint32_t *bperm = nullptr, *btstart = nullptr, *btend = nullptr;
-    int *bbbox = nullptr;
-    uint32_t *bmask = nullptr;
-    uint32_t btmask = 0;
-    double bc0 = 0.0;
-    int blmax = 0, bmbits = 1, blbits = 0;
-    Level blev[MAX_LEVELS];
-    SortScratch bsc;
+    StaticSet bg;     // background particles (section 3.3); extra: ds
+    StaticSet wall;   // dummy wall particles (section 2.2); extra: m, u, v
+    double *wp = nullptr, *wugx = nullptr, *wugy = nullptr;   // wall BC
 
     // device scalars
     double *d_dt = nullptr, *d_t = nullptr;
@@ -109,6 +127,9 @@ struct sph_ctx {
     bool timing = false;
     Timer tm;
 };
+
+static Grid set_grid(const StaticSet &S);
+static WallView wall_view(const sph_ctx *c);
 
 // ------------------------------------------------------------- helpers --
 static sph_status fail(sph_ctx *c, sph_status st, const std::string &msg) {
@@ -339,6 +360,7 @@ static void passes(sph_ctx *c) {
         a.p = (const R *)c->pf;
     }
     a.rho0 = c->prm.rho0;
+    a.w = wall_view(c);
     a.rho = (R *)c->rhoR;
     a.beta = (R *)c->beta;
     a.pavg = (R *)c->pavg;
@@ -371,6 +393,7 @@ static void passes(sph_ctx *c) {
         b.u = (const R *)c->uf;
         b.v = (const R *)c->vf;
     }
+    b.w = a.w;
     b.rho = a.rho;
     b.beta = a.beta;
     b.pavg = a.pavg;
@@ -397,6 +420,23 @@ static void passes(sph_ctx *c) {
 }
 
 static void run_passes(sph_ctx *c) {
+    if (c->wall.n > 0) {
+        WallBcArgs wb;
+        wb.w = wall_view(c);
+        wb.g = grid_for_kernels(c);
+        wb.d = c->dom;
+        wb.x = c->f[F_X];
+        wb.y = c->f[F_Y];
+        wb.h = c->f[F_H];
+        wb.u = c->f[F_U];
+        wb.v = c->f[F_V];
+        wb.p = c->f[F_P];
+        wb.pw = c->wp;
+        wb.ugx = c->wugx;
+        wb.ugy = c->wugy;
+        launch_wall_bc(c->s, wb);
+        c->launches += 1;
+    }
     if (is_mixed(c))
         passes<float>(c);
     else
@@ -471,11 +511,11 @@ static void free_ctx(sph_ctx *c) {
                   c->cnt_tmp, c->d_dt, c->d_t, c->d_hmin, c->d_nonfinite,
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
                   c->d_overflow, c->longq, c->d_nlong, c->tmp_a, c->tmp_b,
-                  c->closest, c->d_mass, c->d_mass_part, c->bx, c->by, c->bh,
-                  c->bds, c->bid, c->bkey, c->btkey, c->bperm, c->btstart,
-                  c->btend, c->bbbox, c->bmask, c->bsc.key_alt, c->bsc.val_alt,
-                  c->bsc.counts, c->bsc.scan_tmp};
+                  c->closest, c->d_mass, c->d_mass_part, c->wp, c->wugx,
+                  c->wugy};
     for (void *p : ps) cudaFree(p);
+    free_set(&c->bg);
+    free_set(&c->wall);
     for (auto e : c->tm.pool) cudaEventDestroy(e);
     for (int f = 0; f < 5; ++f)
         for (auto &pr : c->tm.open[f]) {
@@ -484,143 +524,178 @@ static void free_ctx(sph_ctx *c) {
         }
 }
 
-// ---------------------------------------------------------- background --
-static void free_bg(sph_ctx *c) {
-    void *ps[] = {c->bx, c->by, c->bh, c->bds, c->bid, c->bkey, c->btkey,
-                  c->bperm, c->btstart, c->btend, c->bbbox, c->bmask,
-                  c->bsc.key_alt, c->bsc.val_alt, c->bsc.counts, c->bsc.scan_tmp};
-    for (void *p : ps) cudaFree(p);
-    c->bx = c->by = c->bh = c->bds = nullptr;
-    c->bid = nullptr;
-    c->bkey = c->btkey = nullptr;
-    c->bperm = c->btstart = c->btend = nullptr;
-    c->bbbox = nullptr;
-    c->bmask = nullptr;
-    c->bsc = SortScratch();
-    c->bg_cap = 0;
-    c->n_bg = 0;
-}
-
-// Background particles (section 3.3): x, y, h and size ds, kept sorted by
-// their own multi-level cell keys so fluid particles can query them.
-static sph_status load_background(sph_ctx *c, long long n,
-                                  const sph_particles *src) {
-    if (n > 0 && (!src->x || !src->y || !src->h))
-        return fail(c, SPH_EINVAL, "sph_load_particles: background needs x, y, h");
-    if (n > 0 && !src->ds && !(c->prm.ds_max > 0))
-        return fail(c, SPH_EINVAL, "sph_load_particles: background needs ds (or ds_max > 0)");
+// ------------------------------------------------------ static sets --
+// Background (section 3.3) and dummy walls (section 2.2): uploaded once,
+// sorted by their own cell keys, queried by fluid particles.
+static sph_status build_set(sph_ctx *c, StaticSet *S, long long n,
+                            const double *x, const double *y, const double *h,
+                            const double *const *extra, int nex) {
     double hmin = INFINITY;
     for (long long i = 0; i < n; ++i) {
-        double h = src->h[i], ds = src->ds ? src->ds[i] : c->prm.ds_max;
-        if (!(h > 0) || !isfinite(h) || !(ds > 0) || !isfinite(ds) ||
-            !isfinite(src->x[i]) || !isfinite(src->y[i]))
-            return fail(c, SPH_EINVAL, "sph_load_particles: background h, ds must be positive");
-        hmin = std::min(hmin, h);
+        if (!(h[i] > 0) || !isfinite(h[i]) || !isfinite(x[i]) || !isfinite(y[i]))
+            return fail(c, SPH_EINVAL, "sph_load_particles: h must be positive, positions finite");
+        hmin = std::min(hmin, h[i]);
     }
-    if (n > (1ll << 30)) return fail(c, SPH_ECAPACITY, "sph_load_particles: background too large");
-    c->n_bg = 0;
+    if (n > (1ll << 30)) return fail(c, SPH_ECAPACITY, "sph_load_particles: set too large");
+    S->n = 0;
     if (n == 0) return SPH_OK;
     double c0 = 3.0 * hmin;
     double Lmax = std::max(c->dom.L[0], c->dom.L[1]);
     int lmax = 0;
     while (ldexp(c0, lmax) < Lmax) ++lmax;
-    if (lmax >= MAX_LEVELS) return fail(c, SPH_EINVAL, "background spans too many levels");
+    if (lmax >= MAX_LEVELS) return fail(c, SPH_EINVAL, "set spans too many cell levels");
     Level lev[MAX_LEVELS];
     compute_levels(c->dom, c0, lev);
     long long nmax = std::max(lev[0].n[0], lev[0].n[1]);
-    if (nmax >= (1ll << MAX_MORTON_BITS)) return fail(c, SPH_EINVAL, "background grid too fine");
-    if (n > c->bg_cap) {
-        free_bg(c);
+    if (nmax >= (1ll << MAX_MORTON_BITS)) return fail(c, SPH_EINVAL, "set grid too fine");
+    if (n > S->cap || nex != S->nex) {
+        free_set(S);
         size_t N = (size_t)n;
-        bool ok = dalloc(&c->bx, N) && dalloc(&c->by, N) && dalloc(&c->bh, N) &&
-                  dalloc(&c->bds, N) && dalloc(&c->bid, N) && dalloc(&c->bkey, N) &&
-                  dalloc(&c->bperm, N) && dalloc(&c->bbbox, MAX_LEVELS * 4) &&
-                  dalloc(&c->bmask, 1) && dalloc(&c->bsc.key_alt, N) &&
-                  dalloc(&c->bsc.val_alt, N);
+        bool ok = dalloc(&S->x, N) && dalloc(&S->y, N) && dalloc(&S->h, N) &&
+                  dalloc(&S->id, N) && dalloc(&S->key, N) && dalloc(&S->perm, N) &&
+                  dalloc(&S->bbox, MAX_LEVELS * 4) && dalloc(&S->mask, 1) &&
+                  dalloc(&S->sc.key_alt, N) && dalloc(&S->sc.val_alt, N);
+        for (int k = 0; k < nex; ++k) ok = ok && dalloc(&S->ex[k], N);
         size_t tiles = (N + 2047) / 2048;
-        c->bsc.counts_cap = 256 * tiles;
-        c->bsc.scan_cap = scan_scratch_elems(c->bsc.counts_cap);
-        ok = ok && dalloc(&c->bsc.counts, c->bsc.counts_cap) &&
-             dalloc(&c->bsc.scan_tmp, c->bsc.scan_cap);
+        S->sc.counts_cap = 256 * tiles;
+        S->sc.scan_cap = scan_scratch_elems(S->sc.counts_cap);
+        ok = ok && dalloc(&S->sc.counts, S->sc.counts_cap) &&
+             dalloc(&S->sc.scan_tmp, S->sc.scan_cap);
         uint32_t t = 1;
         while (t < 2u * (uint32_t)N) t <<= 1;
-        ok = ok && dalloc(&c->btkey, t) && dalloc(&c->btstart, t) && dalloc(&c->btend, t);
+        ok = ok && dalloc(&S->tkey, t) && dalloc(&S->tstart, t) && dalloc(&S->tend, t);
         if (!ok) {
             cudaGetLastError();
-            free_bg(c);
-            return fail(c, SPH_ENOMEM, "background allocation failed");
+            free_set(S);
+            return fail(c, SPH_ENOMEM, "particle set allocation failed");
         }
-        c->bg_cap = (int)n;
+        S->cap = (int)n;
+        S->nex = nex;
     }
-    // upload unsorted into temporaries, then sort into place
+    const int nf = 3 + nex;
     double *tmp = nullptr;
     int64_t *tid = nullptr;
-    if (!dalloc(&tmp, 4 * (size_t)n) || !dalloc(&tid, (size_t)n)) {
+    if (!dalloc(&tmp, (size_t)nf * n) || !dalloc(&tid, (size_t)n)) {
         cudaGetLastError();
         cudaFree(tmp);
-        return fail(c, SPH_ENOMEM, "background staging allocation failed");
-    }
-    std::vector<double> dsv;
-    const double *ds = src->ds;
-    if (!ds) {
-        dsv.assign((size_t)n, c->prm.ds_max);
-        ds = dsv.data();
+        return fail(c, SPH_ENOMEM, "particle set staging allocation failed");
     }
     std::vector<int64_t> ids((size_t)n);
     for (long long i = 0; i < n; ++i) ids[i] = i;
-    cudaMemcpyAsync(tmp, src->x, sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
-    cudaMemcpyAsync(tmp + n, src->y, sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
-    cudaMemcpyAsync(tmp + 2 * n, src->h, sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
-    cudaMemcpyAsync(tmp + 3 * n, ds, sizeof(double) * n, cudaMemcpyHostToDevice, c->s);
+    const double *srcs[6] = {x, y, h, nullptr, nullptr, nullptr};
+    for (int k = 0; k < nex; ++k) srcs[3 + k] = extra[k];
+    for (int k = 0; k < nf; ++k)
+        cudaMemcpyAsync(tmp + (size_t)k * n, srcs[k], sizeof(double) * n,
+                        cudaMemcpyHostToDevice, c->s);
     cudaMemcpyAsync(tid, ids.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
-    c->bc0 = c0;
-    c->blmax = lmax;
-    memcpy(c->blev, lev, sizeof(lev));
-    c->bmbits = std::max(1, bits_for(nmax - 1));
-    c->blbits = bits_for(lmax);
-    launch_reset_bbox(c->s, c->bbbox, c->bmask);
-    launch_keys(c->s, (int)n, c->dom, c0, lmax, c->bmbits, c->blev, tmp, tmp + n,
-                tmp + 2 * n, c->bkey, c->bperm, c->bmask, c->bbbox);
-    radix_sort(c->s, (int)n, 2 * c->bmbits + c->blbits, c->bkey, c->bperm,
-               c->bsc, &c->launches);
+    S->c0 = c0;
+    S->lmax = lmax;
+    memcpy(S->lev, lev, sizeof(lev));
+    S->mbits = std::max(1, bits_for(nmax - 1));
+    S->lbits = bits_for(lmax);
+    launch_reset_bbox(c->s, S->bbox, S->mask);
+    launch_keys(c->s, (int)n, c->dom, c0, lmax, S->mbits, S->lev, tmp, tmp + n,
+                tmp + 2 * n, S->key, S->perm, S->mask, S->bbox);
+    radix_sort(c->s, (int)n, 2 * S->mbits + S->lbits, S->key, S->perm, S->sc,
+               &c->launches);
     GatherList gl;
     memset(&gl, 0, sizeof(gl));
-    double *dst[4] = {c->bx, c->by, c->bh, c->bds};
-    for (int k = 0; k < 4; ++k) {
-        gl.src[k] = tmp + k * n;
+    double *dst[6] = {S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2]};
+    for (int k = 0; k < nf; ++k) {
+        gl.src[k] = tmp + (size_t)k * n;
         gl.dst[k] = dst[k];
     }
-    gl.nd = 4;
+    gl.nd = nf;
     gl.isrc[0] = tid;
-    gl.idst[0] = c->bid;
+    gl.idst[0] = S->id;
     gl.ni = 1;
-    gather_by_perm(c->s, (int)n, c->bperm, gl, &c->launches);
+    gather_by_perm(c->s, (int)n, S->perm, gl, &c->launches);
     uint32_t t = 1;
     while (t < 2u * (uint32_t)n) t <<= 1;
-    c->btmask = t - 1;
-    build_cell_table(c->s, (int)n, c->bkey, c->btkey, c->btstart, c->btend,
-                     c->btmask, &c->launches);
+    S->tmask = t - 1;
+    build_cell_table(c->s, (int)n, S->key, S->tkey, S->tstart, S->tend, S->tmask,
+                     &c->launches);
     c->launches += 2;
     cudaError_t e = cudaStreamSynchronize(c->s);
     cudaFree(tmp);
     cudaFree(tid);
-    if (e != cudaSuccess) return cuda_check(c, "load_background");
-    c->n_bg = (int)n;
-    return cuda_check(c, "load_background");
+    if (e != cudaSuccess) return cuda_check(c, "build_set");
+    S->n = (int)n;
+    return cuda_check(c, "build_set");
 }
 
-static Grid bg_grid(const sph_ctx *c) {
+static Grid set_grid(const StaticSet &S) {
     Grid g;
-    g.tkey = c->btkey;
-    g.tstart = c->btstart;
-    g.tend = c->btend;
-    g.tmask = c->btmask;
-    g.level_mask = (c->blmax >= 31) ? 0xffffffffu : ((1u << (c->blmax + 1)) - 1u);
-    g.mbits = c->bmbits;
-    g.nlev = c->blmax + 1;
-    g.bbox = c->bbbox;
-    for (int l = 0; l < MAX_LEVELS; ++l) g.lev[l] = c->blev[l];
+    g.tkey = S.tkey;
+    g.tstart = S.tstart;
+    g.tend = S.tend;
+    g.tmask = S.tmask;
+    g.level_mask = (S.lmax >= 31) ? 0xffffffffu : ((1u << (S.lmax + 1)) - 1u);
+    g.mbits = S.mbits;
+    g.nlev = S.lmax + 1;
+    g.bbox = S.bbox;
+    for (int l = 0; l < MAX_LEVELS; ++l) g.lev[l] = S.lev[l];
     return g;
+}
+
+static WallView wall_view(const sph_ctx *c) {
+    WallView w;
+    w.n = c->wall.n;
+    w.g = set_grid(c->wall);
+    w.x = c->wall.x;
+    w.y = c->wall.y;
+    w.h = c->wall.h;
+    w.m = c->wall.ex[0];
+    w.uw = c->wall.ex[1];
+    w.vw = c->wall.ex[2];
+    w.p = c->wp;
+    w.ugx = c->wugx;
+    w.ugy = c->wugy;
+    return w;
+}
+
+static sph_status load_background(sph_ctx *c, long long n, const sph_particles *src) {
+    if (n > 0 && (!src->x || !src->y || !src->h))
+        return fail(c, SPH_EINVAL, "sph_load_particles: background needs x, y, h");
+    if (n > 0 && !src->ds && !(c->prm.ds_max > 0))
+        return fail(c, SPH_EINVAL, "sph_load_particles: background needs ds (or ds_max > 0)");
+    std::vector<double> dsv;
+    const double *ds = n > 0 ? src->ds : nullptr;
+    if (n > 0 && !ds) {
+        dsv.assign((size_t)n, c->prm.ds_max);
+        ds = dsv.data();
+    }
+    for (long long i = 0; i < n; ++i)
+        if (!(ds[i] > 0) || !isfinite(ds[i]))
+            return fail(c, SPH_EINVAL, "sph_load_particles: background ds must be positive");
+    const double *ex[1] = {ds};
+    return build_set(c, &c->bg, n, n ? src->x : nullptr, n ? src->y : nullptr,
+                     n ? src->h : nullptr, ex, 1);
+}
+
+static sph_status load_walls(sph_ctx *c, long long n, const sph_particles *src) {
+    if (n > 0 && (!src->x || !src->y || !src->h || !src->m))
+        return fail(c, SPH_EINVAL, "sph_load_particles: walls need x, y, h, m");
+    for (long long i = 0; i < n; ++i)
+        if (!(src->m[i] > 0) || !isfinite(src->m[i]))
+            return fail(c, SPH_EINVAL, "sph_load_particles: wall masses must be positive");
+    std::vector<double> zero((size_t)std::max(n, 1ll), 0.0);
+    const double *ex[3] = {n ? src->m : nullptr, (n && src->u) ? src->u : zero.data(),
+                           (n && src->v) ? src->v : zero.data()};
+    sph_status st = build_set(c, &c->wall, n, n ? src->x : nullptr,
+                              n ? src->y : nullptr, n ? src->h : nullptr, ex, 3);
+    if (st != SPH_OK) return st;
+    cudaFree(c->wp);
+    cudaFree(c->wugx);
+    cudaFree(c->wugy);
+    c->wp = c->wugx = c->wugy = nullptr;
+    if (n > 0 && !(dalloc(&c->wp, n) && dalloc(&c->wugx, n) && dalloc(&c->wugy, n))) {
+        cudaGetLastError();
+        c->wall.n = 0;
+        return fail(c, SPH_ENOMEM, "wall allocation failed");
+    }
+    c->rhs_valid = false;
+    return SPH_OK;
 }
 
 static uint32_t read_u32(sph_ctx *c, const uint32_t *dev, sph_status *st) {
@@ -748,11 +823,8 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
     if (!c) return SPH_EINVAL;
     c->err.clear();
     if (n < 0 || (n > 0 && !src)) return fail(c, SPH_EINVAL, "sph_load_particles: bad n or src");
-    if (kind == SPH_BACKGROUND) {
-        sph_status st = load_background(c, n, src);
-        cudaStreamSynchronize(c->s);
-        return st;
-    }
+    if (kind == SPH_BACKGROUND) return load_background(c, n, src);
+    if (kind == SPH_WALL) return load_walls(c, n, src);
     if (kind != SPH_FLUID)
         return fail(c, SPH_EINVAL, "sph_load_particles: unknown kind");
     if (n > c->cap) return fail(c, SPH_ECAPACITY, "sph_load_particles: n exceeds capacity");
@@ -933,22 +1005,22 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     t_begin(c, 4, &ev);
     launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass);
     // resolution from the background (section 3.3)
-    if (c->n_bg > 0) {
+    if (c->bg.n > 0) {
         BgArgs a;
         a.n = c->n;
         a.d = c->dom;
-        a.g = bg_grid(c);
+        a.g = set_grid(c->bg);
         a.x = c->f[F_X];
         a.y = c->f[F_Y];
         a.h = c->f[F_H];
         a.mmin = c->f[F_MMIN];
         a.mmax = c->f[F_MMAX];
-        a.nb = c->n_bg;
-        a.bx = c->bx;
-        a.by = c->by;
-        a.bh = c->bh;
-        a.bds = c->bds;
-        a.bid = c->bid;
+        a.nb = c->bg.n;
+        a.bx = c->bg.x;
+        a.by = c->bg.y;
+        a.bh = c->bg.h;
+        a.bds = c->bg.ex[0];
+        a.bid = c->bg.id;
         a.rho0 = c->prm.rho0;
         a.queue = c->tmp_b;
         a.nqueue = c->d_total;
@@ -1035,6 +1107,7 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         sa.dv = (double *)c->dvdt;
         sa.dp = (double *)c->dpdt;
         sa.hnew = (double *)c->V;
+        sa.w = wall_view(c);
     };
     for (int r = 0; r < c->prm.shift_iters; ++r) {
         if ((st = rebuild(c, false)) != SPH_OK) return st;
@@ -1176,7 +1249,8 @@ sph_status sph_get_info(sph_ctx *c, sph_info *out) {
     if (!c || !out) return SPH_EINVAL;
     memset(out, 0, sizeof(*out));
     out->n = c->n;
-    out->n_bg = c->n_bg;
+    out->n_bg = c->bg.n;
+    out->n_wall = c->wall.n;
     double t = 0, dt = 0;
     cudaMemcpyAsync(&t, c->d_t, sizeof(double), cudaMemcpyDeviceToHost, c->s);
     if (c->have_dt) cudaMemcpyAsync(&dt, c->d_dt, sizeof(double), cudaMemcpyDeviceToHost, c->s);
@@ -1187,6 +1261,7 @@ sph_status sph_get_info(sph_ctx *c, sph_info *out) {
     out->levels = c->lmax + 1;
     out->steps = c->steps;
     out->launches = c->launches;
+    out->next_id = c->next_id;
     return SPH_OK;
 }
 

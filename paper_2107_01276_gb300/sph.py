@@ -79,7 +79,8 @@ class Info(ctypes.Structure):
                 ("n_bg", ctypes.c_longlong), ("t", ctypes.c_double),
                 ("dt", ctypes.c_double), ("c0", ctypes.c_double),
                 ("levels", ctypes.c_int), ("steps", ctypes.c_longlong),
-                ("launches", ctypes.c_longlong)]
+                ("launches", ctypes.c_longlong),
+                ("next_id", ctypes.c_longlong)]
 
 
 _lib = None

@@ -11,6 +11,11 @@ Workloads (all synthetic; the paper's runs use no external data set):
                     initial condition of section 4.1 (Eq. tgv_sol at t = 0).
   perturbed      -- lattice with position jitter and a smooth h variation,
                     for parity at sizes the oracle finishes in seconds.
+  half_plane_walls -- fluid above rows of dummy wall particles (parity of
+                    the wall boundary condition).
+  cylinder       -- flow past a circular cylinder (section 4.4) with wall
+                    rings, a background graded by C_r per ring, and a coarse
+                    fluid lattice that sph_adapt refines.
   graded_strip   -- periodic square whose column spacing grows by the
                     paper's layer ratio C_r from a fine core to 1:ratio (the
                     pair-kernel sweep), symmetric so the spacing is
@@ -172,6 +177,107 @@ def graded_strip(n_target: int = 1 << 20, ratio: float = 250.0,
                           rho0=rho0, cs=cs, nu=nu, U_ref=1.0, hdx=hdx,
                           ds_min=float(s.min()), Cr=Cr)
     return dict(particles=parts, params=params, dx_min=float(s.min()))
+
+
+def half_plane_walls(nx: int = 30, ny: int = 20, layers: int = 4,
+                     dx: float = 0.02, hdx: float = 1.2, rho0: float = 1.0,
+                     cs: float = 10.0, nu: float = 0.01, jitter: float = 0.1,
+                     seed: int = 21):
+    """Fluid lattice y > 0 above `layers` rows of wall particles (y < 0) on
+    an x-periodic strip; jittered fluid, random u, v, p."""
+    rng = np.random.default_rng(seed)
+    gx = (np.arange(nx) + 0.5) * dx
+    gy = (np.arange(ny) + 0.5) * dx
+    X, Y = np.meshgrid(gx, gy, indexing="xy")
+    n = X.size
+    x = (X.ravel() + jitter * dx * rng.uniform(-1, 1, n)) % (nx * dx)
+    y = Y.ravel() + jitter * dx * rng.uniform(-0.5, 1, n)
+    fl = dict(x=x, y=y, u=rng.normal(0, 0.1, n), v=rng.normal(0, 0.1, n),
+              p=rng.normal(0, 0.3, n), rho=np.full(n, rho0),
+              m=np.full(n, rho0 * dx * dx), h=np.full(n, hdx * dx))
+    wy = -(np.arange(layers) + 0.5) * dx
+    WX, WY = np.meshgrid(gx, wy, indexing="xy")
+    nw = WX.size
+    walls = dict(x=WX.ravel(), y=WY.ravel(), h=np.full(nw, hdx * dx),
+                 m=np.full(nw, rho0 * dx * dx), u=np.full(nw, 0.05),
+                 v=np.zeros(nw))
+    params = _base_params(lo=(0.0, -1.0), hi=(nx * dx, 1.0), periodic=(1, 0),
+                          rho0=rho0, cs=cs, nu=nu, U_ref=1.0, hdx=hdx)
+    return dict(particles=fl, walls=walls, params=params, dx=dx)
+
+
+def cylinder(D: float = 2.0, Re: float = 40.0, ds_min_over_D: float = 1 / 50,
+             ds_max_over_D: float = 0.5, Lx_over_D: float = 25.0,
+             Ly_over_D: float = 15.0, center_over_D=(7.5, 7.5),
+             rho0: float = 1000.0, cs: float = 10.0, U: float = 1.0,
+             hdx: float = 1.2, Cr: float = 1.08, jitter: float = 1e-3,
+             wall_layers: int = 4, seed: int = 2):
+    """Flow past a circular cylinder (section 4.4, Table fpc-params: D = 2,
+    rho0 = 1000, c_s = 10, h/dx = 1.2, C_r = 1.08), periodic box of
+    25D x 15D, impulsive start u = U.
+
+    - walls: `wall_layers` rings of dummy particles inside the cylinder at
+      spacing ds_min (section 2.2);
+    - background: rings around the cylinder whose size grows by C_r per
+      ring from ds_min at the wall to ds_max, then a ds_max lattice (the
+      geometry-based resolution of section 3.3 given as input);
+    - fluid: a ds_max lattice outside the cylinder with 1e-3 ds_max
+      position jitter; sph_adapt refines it to the background's sizes.
+    """
+    rng = np.random.default_rng(seed)
+    R = 0.5 * D
+    cx, cy = center_over_D[0] * D, center_over_D[1] * D
+    Lx, Ly = Lx_over_D * D, Ly_over_D * D
+    ds_min, ds_max = ds_min_over_D * D, ds_max_over_D * D
+    # walls
+    wx, wy = [], []
+    for k in range(wall_layers):
+        r = R - (k + 0.5) * ds_min
+        nk = max(3, int(round(2 * math.pi * r / ds_min)))
+        th = (np.arange(nk) + 0.5 * (k % 2)) * 2 * math.pi / nk
+        wx.append(cx + r * np.cos(th))
+        wy.append(cy + r * np.sin(th))
+    wx, wy = np.concatenate(wx), np.concatenate(wy)
+    nw = wx.size
+    walls = dict(x=wx, y=wy, h=np.full(nw, hdx * ds_min),
+                 m=np.full(nw, rho0 * ds_min * ds_min), u=np.zeros(nw),
+                 v=np.zeros(nw))
+    # background rings, sizes growing by Cr per ring
+    bx, by, bds = [], [], []
+    r, ds = R + 0.5 * ds_min, ds_min
+    while ds < ds_max:
+        nk = max(6, int(round(2 * math.pi * r / ds)))
+        th = np.arange(nk) * 2 * math.pi / nk
+        bx.append(cx + r * np.cos(th))
+        by.append(cy + r * np.sin(th))
+        bds.append(np.full(nk, ds))
+        r += ds
+        ds = min(ds * Cr, ds_max)
+    r_ring = r
+    gxs = (np.arange(int(round(Lx / ds_max))) + 0.5) * ds_max
+    gys = (np.arange(int(round(Ly / ds_max))) + 0.5) * ds_max
+    GX, GY = np.meshgrid(gxs, gys, indexing="xy")
+    far = np.hypot(GX - cx, GY - cy) >= r_ring
+    bx.append(GX[far])
+    by.append(GY[far])
+    bds.append(np.full(int(far.sum()), ds_max))
+    bg = dict(x=np.concatenate(bx) % Lx, y=np.concatenate(by) % Ly,
+              ds=np.concatenate(bds))
+    bg["h"] = hdx * bg["ds"]
+    # fluid: coarse lattice outside the cylinder
+    inside = np.hypot(GX - cx, GY - cy) < R + 0.5 * ds_max
+    fx, fy = GX[~inside].ravel(), GY[~inside].ravel()
+    n = fx.size
+    fx = (fx + jitter * ds_max * rng.uniform(-1, 1, n)) % Lx
+    fy = (fy + jitter * ds_max * rng.uniform(-1, 1, n)) % Ly
+    fl = dict(x=fx, y=fy, u=np.full(n, U), v=np.zeros(n), p=np.zeros(n),
+              rho=np.full(n, rho0), m=np.full(n, rho0 * ds_max * ds_max),
+              h=np.full(n, hdx * ds_max))
+    params = _base_params(lo=(0.0, 0.0), hi=(Lx, Ly), periodic=(1, 1),
+                          rho0=rho0, cs=cs, nu=U * D / Re, U_ref=U, hdx=hdx,
+                          ds_min=ds_min, ds_max=ds_max, Cr=Cr)
+    return dict(particles=fl, walls=walls, background=bg, params=params,
+                D=D, Re=Re, U=U)
 
 
 def subset(parts: dict, idx) -> dict:
