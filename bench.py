@@ -36,16 +36,28 @@ PASS_B_FLOP_PER_PAIR = 90
 PASS_A_FLOP_PER_PAIR = 60
 
 WORKLOADS = {
+    # configs[1]: flow past a cylinder at Re 40, spacing graded from D/50 at
+    # the wall to D/2 (1:25), split/merge every step
+    "cylinder-re40": dict(kind="cylinder", Re=40.0, refine_calls=12),
     # pair-kernel sweep shape at N ~ 1M: 2-D periodic square, spacing
     # graded over 1:250 by C_r per column, u,v ~ N(0, 0.1),
-    # rho = 1 + U(-0.01, 0.01)
+    # rho = 1 + U(-0.01, 0.01); PEC steps, no adaptation
     "graded-1M": dict(kind="graded", n_target=1 << 20, ratio=250.0),
 }
-DEFAULT_WORKLOAD = "graded-1M"
+DEFAULT_WORKLOAD = "cylinder-re40"
 
 
 def make_workload(name):
     w = WORKLOADS[name]
+    if w["kind"] == "cylinder":
+        d = wl.cylinder(Re=w["Re"])
+        desc = ("flow past a cylinder, Re %g, D=2, rho0=1000, c_s=10, "
+                "h/dx=1.2, C_r=1.08, spacing D/50 at the wall to D/2 (1:25), "
+                "25D x 15D periodic box, impulsive start; coarse lattice "
+                "refined by %d sph_adapt calls before timing; a step is "
+                "sph_adapt (split/merge/shift/h) + one PEC step"
+                % (w["Re"], w["refine_calls"]))
+        return d, desc
     if w["kind"] == "graded":
         d = wl.graded_strip(n_target=w["n_target"], ratio=w["ratio"])
         desc = ("2-D periodic square, column spacing graded by C_r=1.08 per "
@@ -128,9 +140,9 @@ def fp32_alu_peak_tflops(sm_mhz):
 
 # ------------------------------------------------------------ reference --
 def cpu_sample(d, frac=0.08, seed=0):
-    """A spatial window of the workload (x in a band of width frac*L around
-    the middle of the strip) as a standalone non-periodic set: bounded CPU
-    work with the same particle shapes."""
+    """A spatial window of the graded workload (x in a band of width
+    frac*L around the middle) as a standalone set, non-periodic in x:
+    bounded CPU work with the same particle shapes."""
     pt = d["particles"]
     L = d["params"]["hi"][0] - d["params"]["lo"][0]
     c = 0.5 * L
@@ -140,15 +152,50 @@ def cpu_sample(d, frac=0.08, seed=0):
     return {"particles": sub, "params": prm}, int(sel.sum())
 
 
-def run_oracle_sample(d, steps, frac):
+def oracle_steps(d, state, steps, adaptive):
+    """Time `steps` steps of the oracle (adaptation + PEC step when
+    adaptive) from `state`; returns (particle-steps, seconds, threads)."""
     import oracle
-    sd, n = cpu_sample(d, frac)
-    P = oracle.params(**sd["params"])
-    st = oracle.make_state(sd["particles"])
-    t0 = time.perf_counter()
-    oracle.step(P, st, steps)
-    el = time.perf_counter() - t0
-    return n, el, oracle.num_threads()
+    P = oracle.params(**d["params"])
+    st = oracle.make_state(state, cap=max(4 * len(state["x"]), 1000))
+    oracle.set_walls(d.get("walls"))
+    nid = int(np.max(state["id"])) + 1 if "id" in state else None
+    ps, el = 0, 0.0
+    try:
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            if adaptive:
+                _, _, nid = oracle.adapt(P, st, bg=d.get("background"),
+                                         next_id=nid)
+            oracle.step(P, st, 1)
+            el += time.perf_counter() - t0
+            ps += st["n"]
+    finally:
+        oracle.set_walls(None)
+    return ps, el, oracle.num_threads()
+
+
+def reference_state(d, kind):
+    """The state the oracle starts from: for the cylinder, the coarse set
+    refined by the oracle's own adaptation (as the GPU setup does)."""
+    if kind != "cylinder":
+        sd, n = cpu_sample(d, 0.1)
+        return sd, sd["particles"], "window |x-L/2|<0.05L of the workload " \
+            "(%d particles, non-periodic in x)" % n
+    import oracle
+    P = oracle.params(**d["params"])
+    st = oracle.make_state(d["particles"], cap=400000)
+    oracle.set_walls(d["walls"])
+    nid = None
+    try:
+        for _ in range(WORKLOADS["cylinder-re40"]["refine_calls"]):
+            _, _, nid = oracle.adapt(P, st, bg=d["background"], next_id=nid)
+    finally:
+        oracle.set_walls(None)
+    n = st["n"]
+    state = {k: st[k][:n].copy() for k in oracle.STATE_FIELDS}
+    state["id"] = st["id"][:n].copy()
+    return d, state, "the whole workload (%d particles after refinement)" % n
 
 
 def reference_arm(args):
@@ -156,27 +203,22 @@ def reference_arm(args):
     if rank != 0:
         return 0
     d, desc = make_workload(args.workload)
-    frac = 0.1
-    for _ in range(max(args.warmup, 0)):
-        run_oracle_sample(d, 1, frac)
-    tot_el, tot_ps = 0.0, 0
-    for _ in range(args.steps):
-        n, el, cores = run_oracle_sample(d, 1, frac)
-        tot_el += el
-        tot_ps += n
-    v = tot_ps / tot_el
+    kind = WORKLOADS[args.workload]["kind"]
+    dd, state, sample = reference_state(d, kind)
+    adaptive = kind == "cylinder"
+    oracle_steps(dd, state, max(args.warmup, 0) and 1, adaptive)
+    ps, el, cores = oracle_steps(dd, state, args.steps, adaptive)
+    v = ps / el
     line = {"impl": "reference", "metric": "particle-steps/s", "value": v,
             "unit": "particle-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * tot_el / args.steps,
+            "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc},
             "cpu_baseline": {"value": v, "unit": "particle-steps/s",
                              "cores": cores, "kind": "oracle",
-                             "sample": "window |x-L/2|<%.3gL of the workload "
-                                       "(%d particles), 1 PEC step per "
-                                       "timed step" % (frac / 2, n)},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -187,8 +229,8 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(WORKLOADS))
@@ -198,6 +240,8 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return reference_arm(args)
+
+    import ctypes
 
     import torch
     from paper_2107_01276_gb300 import sph
@@ -213,113 +257,142 @@ def main():
     sph.lib()
     stream = torch.cuda.current_stream().cuda_stream
 
+    wdef = WORKLOADS[args.workload]
+    kind = wdef["kind"]
+    adaptive = kind == "cylinder"
     d, desc = make_workload(args.workload)
     pt = d["particles"]
-    n = len(pt["x"])
 
     def new_sim(precision):
-        P = sph.make_params(d["params"], precision=precision,
-                            capacity=int(n * 1.1) + 16)
+        cap = 400000 if adaptive else int(len(pt["x"]) * 1.1) + 16
+        P = sph.make_params(d["params"], precision=precision, capacity=cap)
         s = sph.Simulation(P, stream)
         s.load(pt)
+        if "walls" in d:
+            s.load(d["walls"], kind=sph.SPH_WALL)
+        if "background" in d:
+            s.load(d["background"], kind=sph.SPH_BACKGROUND)
+        for _ in range(wdef.get("refine_calls", 0)):
+            s.adapt()
         return s
+
+    def one_step(s):
+        n = None
+        if adaptive:
+            n = s.adapt()["n_after"]
+        s.step(1, want_time=False)
+        return n
 
     # L2 flush buffer (> 129 MB L2), written between timed steps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def timed_steps(sim, K, W):
+    def timed_steps(s, K, W):
         for _ in range(W):
-            sim.step(1, want_time=False)
+            one_step(s)
         torch.cuda.synchronize()
+        n_fixed = s.info()["n"]
         evs = [(torch.cuda.Event(enable_timing=True),
                 torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        sim.set_timing(True)
+        s.set_timing(True)
         for fam in range(5):
-            sim.kernel_time(fam, reset=True)
-        l0 = sim.info()["launches"]
+            s.kernel_time(fam, reset=True)
+        l0 = s.info()["launches"]
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        ns = []
         for k in range(K):
             flush.zero_()
             evs[k][0].record()
-            sim.step(1, want_time=False)
+            n = one_step(s)
             evs[k][1].record()
+            ns.append(n if n is not None else n_fixed)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        sim.set_timing(False)
+        s.set_timing(False)
         ms = [a.elapsed_time(b) for a, b in evs]
-        fams = [sim.kernel_time(f) for f in range(5)]
-        return ms, fams, sim.info()["launches"] - l0
+        fams = [s.kernel_time(f) for f in range(5)]
+        return ms, ns, fams, s.info()["launches"] - l0
 
     sim = new_sim(sph.SPH_MIXED)
     clk = ClockSampler(local)
     clk.start()
-    ms, fams, nlaunch = timed_steps(sim, args.steps, args.warmup)
+    ms, ns, fams, nlaunch = timed_steps(sim, args.steps, args.warmup)
     clocks = clk.stop()
+    tot_ms = float(np.sum(ms))
+    my = torch.tensor([tot_ms, float(np.sum(ns))], dtype=torch.float64,
+                      device="cuda")
+    if dist:
+        t_all = [torch.zeros_like(my) for _ in range(world)]
+        dist.all_gather(t_all, my)
+        tmax = max(float(t[0]) for t in t_all)
+        units = sum(float(t[1]) for t in t_all)
+    else:
+        tmax, units = tot_ms, float(np.sum(ns))
+    value = units / (tmax / 1e3)
+
+    # pass-B pairs of the final state (rate of the pair loop)
     sim.rhs()
     nnb = sim.read("nnb")
-    pairs = int(nnb.sum()) - n            # ordered pairs j != i per pass
-    info = sim.info()
-    launches_per_step = None
-    tot_ms = float(np.sum(ms))
-    my_time = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(my_time, op=dist.ReduceOp.MAX)
-    tmax = float(my_time.item())
-    value = world * n * args.steps / (tmax / 1e3)
-
+    n_now = len(nnb)
+    pairs = int(nnb.sum()) - n_now
     passb_ms, passb_cnt = fams[0]
-    passa_ms, passa_cnt = fams[1]
     avg_b = passb_ms / max(passb_cnt, 1)
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak_alu = fp32_alu_peak_tflops(2070.0)
     ach_b = PASS_B_FLOP_PER_PAIR * pairs / (avg_b / 1e3) / 1e12
-    # launches per step: count of this context's launches over the region
-    info2 = sim.info()
 
-    # e2e through the C ABI with pinned host buffers: H2D load of the
-    # step's particle state, one PEC step, D2H read of x, y, u, v, p.
-    fields_in = ("x", "y", "u", "v", "p", "rho", "m", "h")
-    pinned = {k: torch.from_numpy(np.ascontiguousarray(pt[k], np.float64)
+    # e2e through the C ABI with pinned host buffers: H2D of the step's
+    # fluid state, the step (adaptation + PEC), D2H of x, y, u, v, p
+    state = {k: sim.read(k) for k in ("x", "y", "u", "v", "p", "rho", "m",
+                                      "h", "mmin", "mmax")}
+    state["id"] = sim.read("id")
+    n_e = len(state["x"])
+    fields_in = ("x", "y", "u", "v", "p", "rho", "m", "h", "mmin", "mmax")
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(state[k], np.float64)
                                   ).pin_memory() for k in fields_in}
+    pid = torch.from_numpy(state["id"].astype(np.int64)).pin_memory()
     src = sph.Particles()
     for k in fields_in:
-        setattr(src, k, __import__("ctypes").cast(
-            pinned[k].data_ptr(), sph._D))
-    outs = {k: torch.empty(n, dtype=torch.float64).pin_memory()
+        setattr(src, k, ctypes.cast(pinned[k].data_ptr(), sph._D))
+    src.id = ctypes.cast(pid.data_ptr(), ctypes.POINTER(ctypes.c_int64))
+    cap_out = (400000 if adaptive else 0) + 2 * n_e
+    outs = {k: torch.empty(cap_out, dtype=torch.float64).pin_memory()
             for k in ("x", "y", "u", "v", "p")}
     out_np = {k: v.numpy() for k, v in outs.items()}
-    for _ in range(2):
-        sim.load_raw(sph.SPH_FLUID, n, src)
-        sim.step(1, want_time=False)
+    d2h = 0
+
+    def e2e_step():
+        sim.load_raw(sph.SPH_FLUID, n_e, src)
+        one_step(sim)
+        nb = 0
         for k in out_np:
-            sim.read_into(k, out_np[k])
+            nb += 8 * sim.read_into(k, out_np[k])
+        return nb
+
+    for _ in range(2):
+        e2e_step()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     ke = max(3, args.steps // 2)
+    t0 = time.perf_counter()
     for _ in range(ke):
-        sim.load_raw(sph.SPH_FLUID, n, src)
-        sim.step(1, want_time=False)
-        for k in out_np:
-            sim.read_into(k, out_np[k])
+        d2h = e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_val = world * n * ke / float(e2e_t.item())
+    e2e_val = world * n_e * ke / float(e2e_t.item())
     sim.close()
 
-    # plain FP64 GPU form on the same workload (spec: mixed vs FP64)
+    # the plain FP64 GPU form on the same workload
     fp64 = None
     if not args.no_fp64:
         s64 = new_sim(sph.SPH_FP64)
-        ms64, f64, _ = timed_steps(s64, max(3, args.steps // 4), 3)
-        fp64 = n / (float(np.mean(ms64)) / 1e3)
+        ms64, ns64, _, _ = timed_steps(s64, max(4, args.steps // 4), 3)
+        fp64 = float(np.sum(ns64)) / (float(np.sum(ms64)) / 1e3)
         s64.close()
 
     if rank != 0:
@@ -329,32 +402,37 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        frac = 0.1
-        run_oracle_sample(d, 1, 0.01)           # warm (build, caches)
-        nn, el, cores = run_oracle_sample(d, 2, frac)
-        el /= 2
-        cpu = {"value": nn / el, "unit": "particle-steps/s", "cores": cores,
+        dd, st0, sample = reference_state(d, kind) if kind != "cylinder" \
+            else (d, state, "the GPU's refined state (%d particles)" % n_e)
+        steps_cpu = 2
+        ps, el, cores = oracle_steps(dd, st0, steps_cpu, adaptive)
+        cpu = {"value": ps / el, "unit": "particle-steps/s", "cores": cores,
                "kind": "oracle",
-               "sample": "window |x-L/2|<%.3gL of the workload (%d particles,"
-                         " non-periodic in x), 2 PEC steps" % (frac / 2, nn)}
+               "sample": "%s, %d oracle steps (%s)" % (
+                   sample, steps_cpu,
+                   "adaptation + PEC step each" if adaptive else "PEC")}
 
     peaks, pk_kind = measured_peaks()
+    fam_names = ["pass_b", "pass_a", "rebuild", "pec", "adapt"]
     line = {
         "metric": "particle-steps/s", "value": value,
         "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32-pair/f64-state", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": desc, "n": n,
-                   "precision": "mixed", "l2": "flushed between steps "
-                   "(256 MiB write)"},
-        "pair_interactions_per_s": pairs * 2 / (tmax / 1e3 / args.steps),
+        "config": {"workload": args.workload, "desc": desc,
+                   "n_particles": int(np.mean(ns)),
+                   "n_walls": len(d["walls"]["x"]) if "walls" in d else 0,
+                   "n_background": len(d["background"]["x"])
+                   if "background" in d else 0,
+                   "precision": "mixed",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "pair_interactions_per_s": 4 * pairs / (tmax / 1e3 / args.steps),
         "pass_b_pair_interactions_per_s": pairs / (avg_b / 1e3),
         "fp64_particle_steps_per_s": fp64,
         "mixed_over_fp64": (value / world / fp64) if fp64 else None,
-        "kernel_ms_per_step": {
-            "pass_b": passb_ms / args.steps, "pass_a": passa_ms / args.steps,
-            "rebuild": fams[2][0] / args.steps, "pec": fams[3][0] / args.steps},
+        "kernel_ms_per_step": {fam_names[f]: fams[f][0] / args.steps
+                               for f in range(5)},
         "roofline": {"bound": "alu", "kernel": "k_pass_b<float>",
                      "achieved": ach_b, "peak": peak_alu, "unit": "TFLOP/s",
                      "frac": ach_b / peak_alu, "traffic": None,
@@ -362,14 +440,13 @@ def main():
                                   "(152 SM x 128 lanes x 2)"},
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "particle-steps/s",
-                "h2d_bytes_per_step": 8 * len(fields_in) * n,
-                "d2h_bytes_per_step": 8 * len(outs) * n},
-        "gpu_launches": None,
+                "h2d_bytes_per_step": 8 * len(fields_in) * n_e + 8 * n_e,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(nlaunch),
         "cpu_baseline": cpu,
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "kind": pk_kind},
         "neighbours_mean": float(nnb.mean()),
     }
-    line["gpu_launches"] = int(nlaunch)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
