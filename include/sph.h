@@ -128,6 +128,8 @@ typedef struct {
     long long n_merged;   /* particles removed by merging, over all rounds */
     long long n_after;    /* fluid particles after */
     double mass_before, mass_after;   /* total fluid mass (FP64 sums) */
+    long long n_bg_nearest;   /* fluid particles with no background particle
+                                 in range (took the nearest one's size) */
 } sph_adapt_stats;
 
 typedef struct sph_ctx sph_ctx;

@@ -4,7 +4,9 @@
 // feeds a decision (split test, merge admissibility and closest partner),
 // so the decisions match the definition bit for bit.
 #include "adapt.cuh"
+#include "kernels.cuh"
 #include "neighbors.cuh"
+#include "team.cuh"
 
 namespace sph {
 
@@ -34,35 +36,6 @@ __device__ __forceinline__ double wrap_rn(const Domain &d, int a, double x) {
     return x;
 }
 
-// Quintic kernel and derivative for the sums (ordinary FP64).
-__device__ __forceinline__ double qw(double q) {
-    if (q >= 3.0) return 0.0;
-    double a = 3.0 - q, a2 = a * a, w = a2 * a2 * a;
-    if (q < 2.0) {
-        double b = 2.0 - q, b2 = b * b;
-        w -= 6.0 * b2 * b2 * b;
-        if (q < 1.0) {
-            double c = 1.0 - q, c2 = c * c;
-            w += 15.0 * c2 * c2 * c;
-        }
-    }
-    return w;
-}
-__device__ __forceinline__ double qdw(double q) {
-    if (q >= 3.0) return 0.0;
-    double a = 3.0 - q, a2 = a * a, w = -5.0 * a2 * a2;
-    if (q < 2.0) {
-        double b = 2.0 - q, b2 = b * b;
-        w += 30.0 * b2 * b2;
-        if (q < 1.0) {
-            double c = 1.0 - q, c2 = c * c;
-            w -= 75.0 * c2 * c2;
-        }
-    }
-    return w;
-}
-constexpr double SIGMA_N = 7.0 / (478.0 * PI);
-
 __device__ __forceinline__ void sep_rn(const Domain &d, double xi, double yi,
                                        double xj, double yj, double &dx,
                                        double &dy, double &r2) {
@@ -75,20 +48,29 @@ __device__ __forceinline__ void sep_rn(const Domain &d, double xi, double yi,
 // m_ref,i = min rho0 ds_b^2 over background b with r_ib < 3 max(h_i, h_b)
 // (section 3.3); particles with none in range are queued for the nearest
 // background particle.  m_max = 1.05 m_ref, m_min = 0.5 m_ref.
-__global__ void k_bg_mref(BgArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+template <int T>
+__global__ void __launch_bounds__(128) k_bg_mref(BgArgs a) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
     if (i >= a.n) return;
     const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
-    double best = -1.0;
-    for_each_candidate(a.g, a.d, 0, xi, yi, hi, [&](int b) {
-        if (pred_fp64(a.d, xi, yi, hi, __ldg(&a.bx[b]), __ldg(&a.by[b]),
-                      __ldg(&a.bh[b]))) {
-            const double ds = __ldg(&a.bds[b]);
-            const double mref = __dmul_rn(__dmul_rn(a.rho0, ds), ds);
-            if (best < 0.0 || mref < best) best = mref;
+    const float4 pi = a.pk[i];
+    const float2 q = anchor_rel(a.an, pi);
+    double best = 1e308;
+    for_each_cell(a.g, a.d, 0, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
+        for (uint32_t b = s + tm.lane; b < e; b += T) {
+            float fx, fy, fr2;
+            if (pred_mixed(a.d, a.an, pi, __ldg(&a.bpk[b]), xi, yi, hi, a.bx,
+                           a.by, a.bh, (int)b, fx, fy, fr2)) {
+                const double ds = __ldg(&a.bds[b]);
+                const double mref = __dmul_rn(__dmul_rn(a.rho0, ds), ds);
+                best = mref < best ? mref : best;
+            }
         }
     });
-    if (best < 0.0) {
+    best = team_min<T>(tm.mask, best);
+    if (tm.lane != 0) return;
+    if (best == 1e308) {
         a.queue[atomicAdd(a.nqueue, 1u)] = (uint32_t)i;
         return;
     }
@@ -192,18 +174,20 @@ __global__ void k_split_emit(SplitArgs a) {
 // ------------------------------------------------------------------ merge --
 // closest_i: admissible j in N(i) of least (r^2, id_j); admissible: j != i,
 // neither to be split, r^2 < ((h_i + h_j)/2)^2, m_i + m_j < max(m_max).
-__global__ void k_merge_closest(MergeArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+template <int T>
+__global__ void __launch_bounds__(128) k_merge_closest(MergeArgs a) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
     if (i >= a.n) return;
     const double *x = a.f[S_X], *y = a.f[S_Y], *h = a.f[S_H], *m = a.f[S_M],
                  *mmax = a.f[S_MMAX];
     int best = -1;
+    double br2 = 0.0;
+    long long bid = 0;
     const double mi = m[i], mxi = mmax[i];
     if (mxi > 0.0 && !(mi > mxi)) {
         const double xi = x[i], yi = y[i], hi = h[i];
-        double br2 = 0.0;
-        long long bid = 0;
-        for (uint32_t k = a.off[i]; k < a.off[i + 1]; ++k) {
+        for (uint32_t k = a.off[i] + tm.lane; k < a.off[i + 1]; k += T) {
             const int j = (int)a.list[k];
             if (j == i) continue;
             const double mxj = mmax[j], mj = m[j];
@@ -222,7 +206,19 @@ __global__ void k_merge_closest(MergeArgs a) {
             }
         }
     }
-    a.closest[i] = best;
+    // lexicographic (r^2, id) minimum over the team
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) {
+        const int ob = __shfl_xor_sync(tm.mask, best, o);
+        const double orr = __shfl_xor_sync(tm.mask, br2, o);
+        const long long oid = __shfl_xor_sync(tm.mask, bid, o);
+        if (ob >= 0 && (best < 0 || orr < br2 || (orr == br2 && oid < bid))) {
+            best = ob;
+            br2 = orr;
+            bid = oid;
+        }
+    }
+    if (tm.lane == 0) a.closest[i] = best;
 }
 
 // Mutually closest pairs merge into the particle with the smaller id
@@ -281,60 +277,97 @@ __global__ void k_compact(int n, const uint32_t *alive, const uint32_t *pos,
 }
 
 // ------------------------------------------------------- shift and Taylor --
-// Summation density of every particle (Eq. sd-gather) and, for the h
-// update, the mean neighbour mass.
-__global__ void k_density_mbar(ShiftArgs a, int want_h) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+template <typename R>
+struct ShiftIn {
+    const R *m, *u, *v, *p;
+    __device__ __forceinline__ ShiftIn(const ShiftArgs &a) {
+        if (sizeof(R) == sizeof(double)) {
+            m = (const R *)a.f[S_M];
+            u = (const R *)a.f[S_U];
+            v = (const R *)a.f[S_V];
+            p = (const R *)a.f[S_P];
+        } else {
+            m = (const R *)a.mf;
+            u = (const R *)a.uf;
+            v = (const R *)a.vf;
+            p = (const R *)a.pf;
+        }
+    }
+};
+
+// Summation density of every particle (Eq. sd-gather, walls included) and,
+// for the h update, the mean fluid-neighbour mass.
+template <typename R, int T>
+__global__ void __launch_bounds__(128) k_density_mbar(ShiftArgs a, int want_h) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
     if (i >= a.n) return;
-    const double *x = a.f[S_X], *y = a.f[S_Y], *h = a.f[S_H], *m = a.f[S_M];
-    const double xi = x[i], yi = y[i], hi = h[i], hinv = 1.0 / hi;
-    double rho = 0.0, msum = 0.0;
+    const ShiftIn<R> in(a);
+    Sep<R> sp;
+    sp.init(a.d, a.f[S_X], a.f[S_Y], a.pk, i);
+    const R hi = (R)a.f[S_H][i], hinv = R(1) / hi;
+    R rho = 0, msum = 0;
     const uint32_t b = a.off[i], e = a.off[i + 1];
-    for (uint32_t k = b; k < e; ++k) {
+    for (uint32_t k = b + tm.lane; k < e; k += T) {
         const int j = (int)a.list[k];
-        double dx, dy, r2;
-        sep_rn(a.d, xi, yi, x[j], y[j], dx, dy, r2);
-        rho += m[j] * qw(sqrt(r2) * hinv);
-        msum += m[j];
+        R dx, dy, r2;
+        sp.get(a.d, a.an, a.f[S_X], a.f[S_Y], a.pk, j, dx, dy, r2);
+        rho += in.m[j] * qs_w<R>(sqrt(r2) * hinv);
+        msum += in.m[j];
     }
     if (a.w.n > 0) {
-        for_each_wall(a.w, a.d, xi, yi, hi, [&](int k, double, double, double r2) {
-            rho += a.w.m[k] * qw(sqrt(r2) * hinv);
+        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane,
+                      [&](int k, double, double, double r2) {
+            rho += (R)a.w.m[k] * qs_w<R>(sqrt((R)r2) * hinv);
         });
     }
-    rho *= SIGMA_N * hinv * hinv;
-    a.rho[i] = rho;
-    if (want_h) a.hnew[i] = a.hdx * sqrt((msum / (double)(e - b)) / rho);
+    rho = team_sum<T>(tm.mask, rho);
+    msum = team_sum<T>(tm.mask, msum);
+    if (tm.lane != 0) return;
+    rho *= sigma_norm<R>() * hinv * hinv;
+    ((R *)a.rho)[i] = rho;
+    if (want_h)
+        ((R *)a.hnew)[i] = (R)a.hdx * sqrt((msum / (R)(e - b)) / rho);
 }
 
-// Limited shift (Eqs. shift-deltar, shift-limit) and the Taylor gradients
-// grad phi_i = sum_{j != i} V_j (phi_j - phi_i) grad_i W(r_ij, h_i).
-__global__ void k_shift_compute(ShiftArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Limited shift (Eqs. shift-deltar, shift-limit; walls included) and the
+// Taylor increments grad phi_i . dr_i with grad phi_i = sum_{j != i} V_j
+// (phi_j - phi_i) grad_i W(r_ij, h_i) over fluid neighbours.
+template <typename R, int T>
+__global__ void __launch_bounds__(128) k_shift_compute(ShiftArgs a) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
     if (i >= a.n) return;
-    const double *x = a.f[S_X], *y = a.f[S_Y], *h = a.f[S_H], *m = a.f[S_M],
-                 *u = a.f[S_U], *v = a.f[S_V], *p = a.f[S_P];
-    const double xi = x[i], yi = y[i], hi = h[i], hinv = 1.0 / hi;
-    const double inv_wxi = 1.0 / qw(XI_INFLECTION);
-    const double ui = u[i], vi = v[i], pi = p[i];
-    double ax = 0, ay = 0, gux = 0, guy = 0, gvx = 0, gvy = 0, gpx = 0, gpy = 0;
-    for (uint32_t k = a.off[i]; k < a.off[i + 1]; ++k) {
-        const int j = (int)a.list[k];
-        if (j == i) continue;
-        double dx, dy, r2;
-        sep_rn(a.d, xi, yi, x[j], y[j], dx, dy, r2);
-        const double r = sqrt(r2);
-        if (!(r > 0.0)) continue;
-        const double hb = 0.5 * (hi + h[j]), hbinv = 1.0 / hb;
-        double ratio = qw(r * hbinv) * inv_wxi;
+    const ShiftIn<R> in(a);
+    const R *rhoj = (const R *)a.rho;
+    Sep<R> sp;
+    sp.init(a.d, a.f[S_X], a.f[S_Y], a.pk, i);
+    const R hi = (R)a.f[S_H][i], hinv = R(1) / hi;
+    const R inv_wxi = R(1) / qs_w<R>(R(XI_INFLECTION));
+    const R ui = in.u[i], vi = in.v[i], pi = in.p[i];
+    const R rho0 = (R)a.rho0;
+    R ax = 0, ay = 0, gux = 0, guy = 0, gvx = 0, gvy = 0, gpx = 0, gpy = 0;
+    auto shift = [&](R mj, R hj, R dx, R dy, R r) {
+        const R hb = R(0.5) * (hi + hj), hbinv = R(1) / hb;
+        R ratio = qs_w<R>(r * hbinv) * inv_wxi;
         ratio *= ratio;
-        const double f = (m[j] / a.rho0) * (1.0 + 0.24 * ratio * ratio) *
-                         (SIGMA_N * hbinv * hbinv * hbinv) * qdw(r * hbinv) / r;
+        const R f = (mj / rho0) * (R(1) + R(0.24) * ratio * ratio) *
+                    (sigma_norm<R>() * hbinv * hbinv * hbinv) *
+                    qs_dw<R>(r * hbinv) / r;
         ax += f * dx;
         ay += f * dy;
-        const double g = SIGMA_N * hinv * hinv * hinv * qdw(r * hinv) / r;
-        const double Vg = (m[j] / a.rho[j]) * g;
-        const double du = u[j] - ui, dv = v[j] - vi, dp = p[j] - pi;
+    };
+    for (uint32_t k = a.off[i] + tm.lane; k < a.off[i + 1]; k += T) {
+        const int j = (int)a.list[k];
+        if (j == i) continue;
+        R dx, dy, r2;
+        sp.get(a.d, a.an, a.f[S_X], a.f[S_Y], a.pk, j, dx, dy, r2);
+        const R r = sqrt(r2);
+        if (!(r > R(0))) continue;
+        shift(in.m[j], (R)a.f[S_H][j], dx, dy, r);
+        const R g = sigma_norm<R>() * hinv * hinv * hinv * qs_dw<R>(r * hinv) / r;
+        const R Vg = (in.m[j] / rhoj[j]) * g;
+        const R du = in.u[j] - ui, dv = in.v[j] - vi, dp = in.p[j] - pi;
         gux += Vg * du * dx;
         guy += Vg * du * dy;
         gvx += Vg * dv * dx;
@@ -343,50 +376,55 @@ __global__ void k_shift_compute(ShiftArgs a) {
         gpy += Vg * dp * dy;
     }
     if (a.w.n > 0) {
-        for_each_wall(a.w, a.d, xi, yi, hi, [&](int k, double dx, double dy,
-                                               double r2) {
-            const double r = sqrt(r2);
-            if (!(r > 0.0)) return;
-            const double hb = 0.5 * (hi + a.w.h[k]), hbinv = 1.0 / hb;
-            double ratio = qw(r * hbinv) * inv_wxi;
-            ratio *= ratio;
-            const double f = (a.w.m[k] / a.rho0) * (1.0 + 0.24 * ratio * ratio) *
-                             (SIGMA_N * hbinv * hbinv * hbinv) * qdw(r * hbinv) / r;
-            ax += f * dx;
-            ay += f * dy;
+        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane,
+                      [&](int k, double dxd, double dyd, double r2) {
+            const R r = sqrt((R)r2);
+            if (!(r > R(0))) return;
+            shift((R)a.w.m[k], (R)a.w.h[k], (R)dxd, (R)dyd, r);
         });
     }
-    const double c = -0.5 * hi * hi;
-    double sx = c * ax, sy = c * ay;
-    const double mag = sqrt(sx * sx + sy * sy), lim = 0.25 * hi;
+    ax = team_sum<T>(tm.mask, ax);
+    ay = team_sum<T>(tm.mask, ay);
+    gux = team_sum<T>(tm.mask, gux);
+    guy = team_sum<T>(tm.mask, guy);
+    gvx = team_sum<T>(tm.mask, gvx);
+    gvy = team_sum<T>(tm.mask, gvy);
+    gpx = team_sum<T>(tm.mask, gpx);
+    gpy = team_sum<T>(tm.mask, gpy);
+    if (tm.lane != 0) return;
+    const R c = R(-0.5) * hi * hi;
+    R sx = c * ax, sy = c * ay;
+    const R mag = sqrt(sx * sx + sy * sy), lim = R(0.25) * hi;
     if (mag > lim) {
-        const double th = lim / mag;
+        const R th = lim / mag;
         sx *= th;
         sy *= th;
     }
-    a.drx[i] = sx;
-    a.dry[i] = sy;
-    a.du[i] = gux * sx + guy * sy;
-    a.dv[i] = gvx * sx + gvy * sy;
-    a.dp[i] = gpx * sx + gpy * sy;
+    ((R *)a.drx)[i] = sx;
+    ((R *)a.dry)[i] = sy;
+    ((R *)a.du)[i] = gux * sx + guy * sy;
+    ((R *)a.dv)[i] = gvx * sx + gvy * sy;
+    ((R *)a.dp)[i] = gpx * sx + gpy * sy;
 }
 
+template <typename R>
 __global__ void k_shift_apply(ShiftArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    a.f[S_X][i] = wrap_rn(a.d, 0, a.f[S_X][i] + a.drx[i]);
-    a.f[S_Y][i] = wrap_rn(a.d, 1, a.f[S_Y][i] + a.dry[i]);
-    a.f[S_U][i] += a.du[i];
-    a.f[S_V][i] += a.dv[i];
-    a.f[S_P][i] += a.dp[i];
-    a.f[S_RHO][i] = a.rho[i];
+    a.f[S_X][i] = wrap_rn(a.d, 0, a.f[S_X][i] + (double)((const R *)a.drx)[i]);
+    a.f[S_Y][i] = wrap_rn(a.d, 1, a.f[S_Y][i] + (double)((const R *)a.dry)[i]);
+    a.f[S_U][i] += (double)((const R *)a.du)[i];
+    a.f[S_V][i] += (double)((const R *)a.dv)[i];
+    a.f[S_P][i] += (double)((const R *)a.dp)[i];
+    a.f[S_RHO][i] = (double)((const R *)a.rho)[i];
 }
 
+template <typename R>
 __global__ void k_h_apply(ShiftArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    a.f[S_H][i] = a.hnew[i];
-    a.f[S_RHO][i] = a.rho[i];
+    a.f[S_H][i] = (double)((const R *)a.hnew)[i];
+    a.f[S_RHO][i] = (double)((const R *)a.rho)[i];
 }
 
 // Deterministic two-stage sum of the masses.
@@ -418,7 +456,11 @@ static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
 void launch_bg_mref(cudaStream_t s, const BgArgs &a) {
     if (a.n <= 0) return;
     cudaMemsetAsync(a.nqueue, 0, sizeof(uint32_t), s);
-    k_bg_mref<<<nblk(a.n, 128), 128, 0, s>>>(a);
+    switch (team_size(a.n)) {
+    case 16: k_bg_mref<16><<<nblk(a.n * 16, 128), 128, 0, s>>>(a); break;
+    case 4: k_bg_mref<4><<<nblk(a.n * 4, 128), 128, 0, s>>>(a); break;
+    default: k_bg_mref<1><<<nblk(a.n, 128), 128, 0, s>>>(a); break;
+    }
     k_bg_nearest<<<152, 256, 0, s>>>(a);
 }
 void launch_split_flag(cudaStream_t s, int n, const double *m,
@@ -436,23 +478,57 @@ void launch_split_emit(cudaStream_t s, const SplitArgs &a) {
 }
 void launch_merge(cudaStream_t s, const MergeArgs &a) {
     if (a.n <= 0) return;
-    k_merge_closest<<<nblk(a.n, 128), 128, 0, s>>>(a);
+    switch (team_size(a.n)) {
+    case 16: k_merge_closest<16><<<nblk(a.n * 16, 128), 128, 0, s>>>(a); break;
+    case 4: k_merge_closest<4><<<nblk(a.n * 4, 128), 128, 0, s>>>(a); break;
+    default: k_merge_closest<1><<<nblk(a.n, 128), 128, 0, s>>>(a); break;
+    }
     k_merge_apply<<<nblk(a.n, 128), 128, 0, s>>>(a);
 }
 void launch_compact(cudaStream_t s, int n, const uint32_t *alive,
                     const uint32_t *pos, const CompactArgs &c) {
     if (n > 0) k_compact<<<nblk(n, 256), 256, 0, s>>>(n, alive, pos, c);
 }
-void launch_shift_round(cudaStream_t s, const ShiftArgs &a) {
-    if (a.n <= 0) return;
-    k_density_mbar<<<nblk(a.n, 128), 128, 0, s>>>(a, 0);
-    k_shift_compute<<<nblk(a.n, 128), 128, 0, s>>>(a);
-    k_shift_apply<<<nblk(a.n, 256), 256, 0, s>>>(a);
+template <typename R, int T>
+static void shift_round_T(cudaStream_t s, const ShiftArgs &a) {
+    k_density_mbar<R, T><<<nblk(a.n * T, 128), 128, 0, s>>>(a, 0);
+    k_shift_compute<R, T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
+    k_shift_apply<R><<<nblk(a.n, 256), 256, 0, s>>>(a);
 }
-void launch_h_update(cudaStream_t s, const ShiftArgs &a) {
+template <typename R>
+static void shift_round_R(cudaStream_t s, const ShiftArgs &a) {
+    switch (team_size(a.n)) {
+    case 16: shift_round_T<R, 16>(s, a); break;
+    case 4: shift_round_T<R, 4>(s, a); break;
+    default: shift_round_T<R, 1>(s, a); break;
+    }
+}
+void launch_shift_round(cudaStream_t s, const ShiftArgs &a, bool mixed) {
     if (a.n <= 0) return;
-    k_density_mbar<<<nblk(a.n, 128), 128, 0, s>>>(a, 1);
-    k_h_apply<<<nblk(a.n, 256), 256, 0, s>>>(a);
+    if (mixed)
+        shift_round_R<float>(s, a);
+    else
+        shift_round_R<double>(s, a);
+}
+template <typename R, int T>
+static void h_update_T(cudaStream_t s, const ShiftArgs &a) {
+    k_density_mbar<R, T><<<nblk(a.n * T, 128), 128, 0, s>>>(a, 1);
+    k_h_apply<R><<<nblk(a.n, 256), 256, 0, s>>>(a);
+}
+template <typename R>
+static void h_update_R(cudaStream_t s, const ShiftArgs &a) {
+    switch (team_size(a.n)) {
+    case 16: h_update_T<R, 16>(s, a); break;
+    case 4: h_update_T<R, 4>(s, a); break;
+    default: h_update_T<R, 1>(s, a); break;
+    }
+}
+void launch_h_update(cudaStream_t s, const ShiftArgs &a, bool mixed) {
+    if (a.n <= 0) return;
+    if (mixed)
+        h_update_R<float>(s, a);
+    else
+        h_update_R<double>(s, a);
 }
 void launch_mass_sum(cudaStream_t s, int n, const double *m, double *part,
                      double *out) {

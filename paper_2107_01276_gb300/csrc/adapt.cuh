@@ -19,6 +19,8 @@ struct BgArgs {
     int nb;
     const double *bx, *by, *bh, *bds;   // background, sorted by its keys
     const int64_t *bid;         // background load index
+    Anchor an;
+    const float4 *pk, *bpk;     // anchor data of fluid and background
     double rho0;
     uint32_t *queue, *nqueue;   // fluid particles with no background in range
 };
@@ -56,8 +58,13 @@ struct ShiftArgs {
     double *f[NSTATE];
     const uint32_t *off, *list;
     double rho0, hdx;
-    double *rho, *drx, *dry, *du, *dv, *dp, *hnew;   // scratch
+    // scratch of the pair-arithmetic type (double or float)
+    void *rho, *drx, *dry, *du, *dv, *dp, *hnew;
     WallView w;                 // walls join the densities and the shift
+    // mixed path: FP32 anchor coordinates and mirrors of m, u, v, p
+    Anchor an;
+    const float4 *pk;
+    const float *mf, *uf, *vf, *pf;
 };
 
 void launch_bg_mref(cudaStream_t s, const BgArgs &a);
@@ -70,8 +77,8 @@ void launch_split_emit(cudaStream_t s, const SplitArgs &a);
 void launch_merge(cudaStream_t s, const MergeArgs &a);
 void launch_compact(cudaStream_t s, int n, const uint32_t *alive,
                     const uint32_t *pos, const CompactArgs &c);
-void launch_shift_round(cudaStream_t s, const ShiftArgs &a);
-void launch_h_update(cudaStream_t s, const ShiftArgs &a);
+void launch_shift_round(cudaStream_t s, const ShiftArgs &a, bool mixed);
+void launch_h_update(cudaStream_t s, const ShiftArgs &a, bool mixed);
 void launch_mass_sum(cudaStream_t s, int n, const double *m, double *part,
                      double *out);
 

@@ -85,6 +85,7 @@ void compute_levels(const Domain &dom, double c0, Level *lev) {
     for (int l = 0; l < MAX_LEVELS; ++l) {
         double c = ldexp(c0, l);
         lev[l].c = c;
+        lev[l].cf = (float)c;
         for (int ax = 0; ax < 2; ++ax) {
             double Lx = dom.L[ax];
             long long nc;
@@ -101,6 +102,7 @@ void compute_levels(const Domain &dom, double c0, Level *lev) {
             if (nc > (1ll << MAX_MORTON_BITS)) nc = 1ll << MAX_MORTON_BITS;
             lev[l].n[ax] = (int)nc;
             lev[l].w[ax] = w;
+            lev[l].invw[ax] = (float)(1.0 / w);
         }
     }
 }

@@ -6,6 +6,7 @@
 // traversal order, then the finer-level entries in ascending index.
 #include "lists.cuh"
 #include "neighbors.cuh"
+#include "team.cuh"
 
 namespace sph {
 
@@ -14,7 +15,6 @@ __global__ void k_pack(PackArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     a.lev[i] = (uint8_t)(a.skey[i] >> a.lshift);
-    if (!a.mixed) return;
     const double x = a.x[i], y = a.y[i];
     int g[2];
     float xl[2];
@@ -28,38 +28,66 @@ __global__ void k_pack(PackArgs a) {
     }
     a.pk[i] = make_float4(xl[0], xl[1], (float)a.h[i],
                           __uint_as_float((unsigned)g[0] | ((unsigned)g[1] << 16)));
+    if (!a.mixed) return;
     a.mf[i] = (float)a.m[i];
     a.pf[i] = (float)a.p[i];
     a.uf[i] = (float)a.u[i];
     a.vf[i] = (float)a.v[i];
 }
 
-// ------------------------------------------------------------ list build --
-template <bool MIXED>
-__global__ void __launch_bounds__(128) k_list_count(ListArgs a) {
+// Anchor coordinates of a particle set (static sets: walls, background).
+__global__ void k_anchor_pack(int n, const double *x, const double *y,
+                              const double *h, double lo0, double lo1,
+                              double A0, double A1, Anchor an, float4 *pk) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double q[2] = {x[i], y[i]}, lo[2] = {lo0, lo1}, A[2] = {A0, A1};
+    int g[2];
+    float xl[2];
+    for (int ax = 0; ax < 2; ++ax) {
+        double t = __dsub_rn(q[ax], lo[ax]);
+        double c = floor(__ddiv_rn(t, A[ax]));
+        int gi = c < 0.0 ? 0 : (c > (double)(an.n[ax] - 1) ? an.n[ax] - 1 : (int)c);
+        g[ax] = gi;
+        xl[ax] = (float)__dsub_rn(t, __dmul_rn((double)gi, A[ax]));
+    }
+    pk[i] = make_float4(xl[0], xl[1], (float)h[i],
+                        __uint_as_float((unsigned)g[0] | ((unsigned)g[1] << 16)));
+}
+
+// ------------------------------------------------------------ list build --
+// Membership of candidate j for particle i: FP32 anchor filter with the
+// FP64 predicate in its band (exact, for both precisions).
+__device__ __forceinline__ bool member(const ListArgs &a, const float4 &pi,
+                                       double xi, double yi, double hi,
+                                       int j) {
+    float dx, dy, r2;
+    return pred_mixed(a.d, a.an, pi, __ldg(&a.pk[j]), xi, yi, hi, a.x, a.y,
+                      a.h, j, dx, dy, r2);
+}
+
+// A team of T threads walks particle i's cells; each cell's candidates
+// are taken T at a time, one per lane.
+template <int T>
+__global__ void __launch_bounds__(128) k_list_count(ListArgs a) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
     if (i >= a.n) return;
     const int li = a.lev[i];
     const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
-    float4 pi;
-    if (MIXED) pi = a.pk[i];
+    const float4 pi = a.pk[i];
+    const float2 q = anchor_rel(a.an, pi);
     uint32_t cnt = 0;
-    for_each_candidate(a.g, a.d, li, xi, yi, hi, [&](int j) {
-        bool in;
-        if (MIXED) {
-            float dx, dy, r2;
-            in = pred_mixed(a.d, a.an, pi, __ldg(&a.pk[j]), xi, yi, hi, a.x,
-                            a.y, a.h, j, dx, dy, r2);
-        } else {
-            in = pred_fp64(a.d, xi, yi, hi, __ldg(&a.x[j]), __ldg(&a.y[j]),
-                           __ldg(&a.h[j]));
-        }
-        if (in) {
-            ++cnt;
-            if (__ldg(&a.lev[j]) > li) atomicAdd(&a.rev[j], 1u);
+    for_each_cell(a.g, a.d, li, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
+        for (uint32_t j = s + tm.lane; j < e; j += T) {
+            if (member(a, pi, xi, yi, hi, (int)j)) {
+                ++cnt;
+                if (__ldg(&a.lev[j]) > li) atomicAdd(&a.rev[j], 1u);
+            }
         }
     });
-    a.own[i] = cnt;
+    cnt = team_sum<T>(tm.mask, cnt);
+    if (tm.lane == 0) a.own[i] = cnt;
 }
 
 __global__ void k_list_total(int n, const uint32_t *own, const uint32_t *rev,
@@ -68,36 +96,38 @@ __global__ void k_list_total(int n, const uint32_t *own, const uint32_t *rev,
     if (i < n) tot[i] = own[i] + rev[i];
 }
 
-template <bool MIXED>
+// Same walk; the team's ballot orders each group of T candidates, so a
+// list's own entries come in (cell, index) order whatever T is.
+template <int T>
 __global__ void __launch_bounds__(128) k_list_fill(ListArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const Team<T> tm;
+    const int i = Team<T>::particle();
     if (i >= a.n) return;
     const int li = a.lev[i];
     const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
-    float4 pi;
-    if (MIXED) pi = a.pk[i];
+    const float4 pi = a.pk[i];
+    const float2 q = anchor_rel(a.an, pi);
     uint32_t k = a.off[i];
     const uint32_t cap = a.cap;
-    for_each_candidate(a.g, a.d, li, xi, yi, hi, [&](int j) {
-        bool in;
-        if (MIXED) {
-            float dx, dy, r2;
-            in = pred_mixed(a.d, a.an, pi, __ldg(&a.pk[j]), xi, yi, hi, a.x,
-                            a.y, a.h, j, dx, dy, r2);
-        } else {
-            in = pred_fp64(a.d, xi, yi, hi, __ldg(&a.x[j]), __ldg(&a.y[j]),
-                           __ldg(&a.h[j]));
-        }
-        if (in) {
-            if (k < cap) a.list[k] = (uint32_t)j;
-            ++k;
-            if (__ldg(&a.lev[j]) > li) {
-                uint32_t pos = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
-                if (pos < cap) a.list[pos] = (uint32_t)i;
+    const unsigned below = tm.mask & ((1u << (threadIdx.x & 31)) - 1u);
+    for_each_cell(a.g, a.d, li, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
+        for (uint32_t j0 = s; j0 < e; j0 += T) {
+            const uint32_t j = j0 + tm.lane;
+            const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);
+            const unsigned bal = T == 1 ? (in ? 1u : 0u)
+                                        : __ballot_sync(tm.mask, in);
+            if (in) {
+                const uint32_t pos = k + (T == 1 ? 0u : __popc(bal & below));
+                if (pos < cap) a.list[pos] = j;
+                if (__ldg(&a.lev[j]) > li) {
+                    uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
+                    if (rp < cap) a.list[rp] = (uint32_t)i;
+                }
             }
+            k += __popc(bal);
         }
     });
-    if (i == a.n - 1 && a.off[a.n] > cap) atomicOr(a.overflow, 1);
+    if (i == a.n - 1 && tm.lane == 0 && a.off[a.n] > cap) atomicOr(a.overflow, 1);
 }
 
 // Sort of each reverse segment (ascending index).  Segments of at most 16
@@ -195,6 +225,13 @@ static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
 void launch_pack(cudaStream_t s, const PackArgs &a) {
     if (a.n > 0) k_pack<<<nblk(a.n, 256), 256, 0, s>>>(a);
 }
+void launch_anchor_pack(cudaStream_t s, int n, const double *x,
+                        const double *y, const double *h, const double *lo,
+                        const double *A, const Anchor &an, float4 *pk) {
+    if (n > 0)
+        k_anchor_pack<<<nblk(n, 256), 256, 0, s>>>(n, x, y, h, lo[0], lo[1],
+                                                    A[0], A[1], an, pk);
+}
 
 void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
                        SortScratch &sc, uint32_t *tot_tmp, int *launches) {
@@ -204,10 +241,10 @@ void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
         return;
     }
     cudaMemsetAsync(a.rev, 0, sizeof(uint32_t) * n, s);
-    if (mixed)
-        k_list_count<true><<<nblk(n, 128), 128, 0, s>>>(a);
-    else
-        k_list_count<false><<<nblk(n, 128), 128, 0, s>>>(a);
+    const int T = team_size(n);
+    if (T == 16) k_list_count<16><<<nblk(n * 16, 128), 128, 0, s>>>(a);
+    else if (T == 4) k_list_count<4><<<nblk(n * 4, 128), 128, 0, s>>>(a);
+    else k_list_count<1><<<nblk(n, 128), 128, 0, s>>>(a);
     k_list_total<<<nblk(n, 256), 256, 0, s>>>(n, a.own, a.rev, tot_tmp);
     // off has n + 1 entries: scan n + 1 values with a trailing zero
     cudaMemsetAsync(tot_tmp + n, 0, sizeof(uint32_t), s);
@@ -219,10 +256,10 @@ void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, int *launches) {
     const int n = a.n;
     if (n <= 0) return;
     cudaMemsetAsync(a.rev, 0, sizeof(uint32_t) * n, s);
-    if (mixed)
-        k_list_fill<true><<<nblk(n, 128), 128, 0, s>>>(a);
-    else
-        k_list_fill<false><<<nblk(n, 128), 128, 0, s>>>(a);
+    const int T = team_size(n);
+    if (T == 16) k_list_fill<16><<<nblk(n * 16, 128), 128, 0, s>>>(a);
+    else if (T == 4) k_list_fill<4><<<nblk(n * 4, 128), 128, 0, s>>>(a);
+    else k_list_fill<1><<<nblk(n, 128), 128, 0, s>>>(a);
     cudaMemsetAsync(a.nlong, 0, sizeof(uint32_t), s);
     k_list_sort_rev<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.own, a.list, a.cap,
                                                   a.longq, a.nlong);

@@ -37,6 +37,9 @@ struct ListArgs {
 };
 
 void launch_pack(cudaStream_t s, const PackArgs &a);
+void launch_anchor_pack(cudaStream_t s, int n, const double *x,
+                        const double *y, const double *h, const double *lo,
+                        const double *A, const Anchor &an, float4 *pk);
 // Count and scan into off (n + 1 entries; tot_tmp needs n + 1), then fill
 // the lists; entries past a.cap are dropped and flag a.overflow.
 void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,

@@ -43,61 +43,64 @@ __device__ __forceinline__ bool table_lookup(const Grid &g, uint64_t key,
 
 // Cell index ranges on one axis of one level for the query interval
 // [x - Q, x + Q], clipped to the level's occupied bounding box [b0, b1].
-// On a periodic axis the interval is cut into pieces that each map into
-// [b0, b1] by one shift of the period; r[k] = {first, last, shift} with
-// cell index = c + shift.  Returns the number of pieces (0..3).
+// On a periodic axis the interval is cut into up to three pieces, one per
+// period shift k = -1, 0, 1, that each map into [b0, b1]; piece k covers
+// cells first[k]..last[k] (empty if first > last) with cell index c +
+// shift[k].  Fixed slots keep the arrays in registers.
 struct AxisPieces {
     int first[3], last[3], shift[3];
-    int n;
 };
 
-__device__ __forceinline__ void axis_pieces(const Domain &d, const Level &L,
-                                            const int *bb, int ax, double x,
-                                            double Q, AxisPieces &r) {
+__device__ __forceinline__ bool axis_pieces(const Domain &d, const Level &L,
+                                            const int *bb, int ax, float x,
+                                            float Q, AxisPieces &r) {
     const int nc = L.n[ax];
     const int b0 = __ldg(&bb[2 * ax]), b1 = __ldg(&bb[2 * ax + 1]);
-    double lo = __ddiv_rn(__dsub_rn(__dsub_rn(x, Q), d.lo[ax]), L.w[ax]);
-    double hi = __ddiv_rn(__dsub_rn(__dadd_rn(x, Q), d.lo[ax]), L.w[ax]);
-    double flo = floor(lo), fhi = floor(hi);
-    r.n = 0;
+    // FP32 with a margin far above its rounding ((|x| + Q) / w 2^-21 cells):
+    // the pieces only need to cover the exact cell range
+    const float s = L.invw[ax];
+    const float margin = (fabsf(x) + Q) * s * (1.0f / 1048576.0f) + (1.0f / 1024.0f);
+    const float flo = floorf((x - Q) * s - margin);
+    const float fhi = floorf((x + Q) * s + margin);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r.first[k] = 1;
+        r.last[k] = 0;
+        r.shift[k] = 0;
+    }
     if (d.periodic[ax]) {
-        if (fhi - flo + 1.0 >= (double)nc) {
-            r.first[0] = b0;
-            r.last[0] = b1;
-            r.shift[0] = 0;
-            r.n = 1;
-            return;
+        if (fhi - flo + 1.0f >= (float)nc) {
+            r.first[1] = b0;
+            r.last[1] = b1;
+            return b0 <= b1;
         }
         const int a0 = (int)flo, a1 = (int)fhi;
-        for (int k = -1; k <= 1; ++k) {
-            const int lo_k = max(a0, b0 + k * nc), hi_k = min(a1, b1 + k * nc);
-            if (lo_k <= hi_k) {
-                r.first[r.n] = lo_k;
-                r.last[r.n] = hi_k;
-                r.shift[r.n] = -k * nc;
-                r.n++;
-            }
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int off = (k - 1) * nc;
+            r.first[k] = max(a0, b0 + off);
+            r.last[k] = min(a1, b1 + off);
+            r.shift[k] = -off;
+            any |= r.first[k] <= r.last[k];
         }
-    } else {
-        const int a0 = flo < (double)b0 ? b0 : (int)flo;
-        const int a1 = fhi > (double)b1 ? b1 : (int)fhi;
-        if (a0 <= a1) {
-            r.first[0] = a0;
-            r.last[0] = a1;
-            r.shift[0] = 0;
-            r.n = 1;
-        }
+        return any;
     }
+    r.first[1] = flo < (float)b0 ? b0 : (int)flo;
+    r.last[1] = fhi > (float)b1 ? b1 : (int)fhi;
+    return r.first[1] <= r.last[1];
 }
 
-// Calls f(j) for every particle j in the cells of levels >= li that
-// intersect the square of half side max(3 h_i, c_l) around (xi, yi).
+// Calls f(s, e) for the particle range [s, e) of every occupied cell of
+// levels >= li that intersects the square of half side max(3 h_i, c_l)
+// around (xi, yi).  Cells come in a fixed order (level, then row, then
+// column), so traversal order is deterministic.
+// (xr, yr): position relative to the domain's lower corner, FP32.
 template <class F>
-__device__ __forceinline__ void for_each_candidate(const Grid &g,
-                                                   const Domain &d, int li,
-                                                   double xi, double yi,
-                                                   double hi, F &&f) {
-    const double Ri = __dmul_rn(3.0, hi);
+__device__ __forceinline__ void for_each_cell(const Grid &g, const Domain &d,
+                                              int li, float xr, float yr,
+                                              float hi, F &&f) {
+    const float Ri = 3.0f * hi;
     const uint32_t mask = g.level_mask & ~((1u << li) - 1u);
     for (uint32_t mm = mask; mm; mm &= mm - 1) {
         const int l = __ffs(mm) - 1;
@@ -105,28 +108,41 @@ __device__ __forceinline__ void for_each_candidate(const Grid &g,
         if (__ldg(&bb[0]) > __ldg(&bb[1])) continue;   // level holds no particle
         const Level &L = g.lev[l];
         // margin covers rounding in level and cell assignment
-        const double Q = fmax(Ri, L.c) * (1.0 + 1e-7);
+        const float Q = fmaxf(Ri, L.cf) * (1.0f + 1e-5f);
         AxisPieces px, py;
-        axis_pieces(d, L, bb, 0, xi, Q, px);
-        if (px.n == 0) continue;
-        axis_pieces(d, L, bb, 1, yi, Q, py);
+        if (!axis_pieces(d, L, bb, 0, xr, Q, px)) continue;
+        if (!axis_pieces(d, L, bb, 1, yr, Q, py)) continue;
         const uint64_t lbits = (uint64_t)l << (2 * g.mbits);
-        for (int ky = 0; ky < py.n; ++ky) {
+        // piece loops unrolled so the piece arrays stay in registers
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
             for (int cy = py.first[ky]; cy <= py.last[ky]; ++cy) {
                 const uint64_t my = spread2((uint64_t)(cy + py.shift[ky])) << 1;
-                for (int kx = 0; kx < px.n; ++kx) {
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
                     for (int cx = px.first[kx]; cx <= px.last[kx]; ++cx) {
                         uint32_t s, e;
                         if (!table_lookup(g, lbits | my |
                                                  spread2((uint64_t)(cx + px.shift[kx])),
                                           s, e))
                             continue;
-                        for (uint32_t j = s; j < e; ++j) f((int)j);
+                        f(s, e);
                     }
                 }
             }
         }
     }
+}
+
+// Calls f(j) for every particle j of the cells for_each_cell visits.
+template <class F>
+__device__ __forceinline__ void for_each_candidate(const Grid &g,
+                                                   const Domain &d, int li,
+                                                   float xr, float yr,
+                                                   float hi, F &&f) {
+    for_each_cell(g, d, li, xr, yr, hi, [&](uint32_t s, uint32_t e) {
+        for (uint32_t j = s; j < e; ++j) f((int)j);
+    });
 }
 
 // The FP64 neighbour predicate (definition above).
@@ -164,6 +180,14 @@ __device__ __forceinline__ void anchor_sep(const Anchor &an, const float4 &pi,
     }
     dx = fmaf((float)kx, an.A[0], pi.x - pj.x);
     dy = fmaf((float)ky, an.A[1], pi.y - pj.y);
+}
+
+// Position relative to the domain's lower corner in FP32, from the anchor
+// data p = {xl, yl, h, gx | gy << 16}.
+__device__ __forceinline__ float2 anchor_rel(const Anchor &an, const float4 &p) {
+    const unsigned g = __float_as_uint(p.w);
+    return make_float2(fmaf((float)(g & 0xffffu), an.A[0], p.x),
+                       fmaf((float)(g >> 16), an.A[1], p.y));
 }
 
 // Mixed-path predicate: FP32 test on anchor separations, FP64 predicate

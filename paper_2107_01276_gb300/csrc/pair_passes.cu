@@ -7,94 +7,24 @@
 // float: mixed path); positions and the neighbour predicate stay FP64.
 #include <float.h>
 
+#include "kernels.cuh"
 #include "neighbors.cuh"
 #include "pair_passes.cuh"
+#include "team.cuh"
 
 namespace sph {
-
-// Quintic spline in q (section 2, Eq. kernel) without sigma2, and its
-// q-derivative.  sigma2 = 7 / (478 pi h^2); dW/dr = sigma2 / h * dw(q).
-template <typename R>
-__device__ __forceinline__ R qs_w(R q) {
-    if (q >= R(3)) return R(0);
-    R a = R(3) - q, a2 = a * a;
-    R w = a2 * a2 * a;
-    if (q < R(2)) {
-        R b = R(2) - q, b2 = b * b;
-        w -= R(6) * (b2 * b2 * b);
-        if (q < R(1)) {
-            R c = R(1) - q, c2 = c * c;
-            w += R(15) * (c2 * c2 * c);
-        }
-    }
-    return w;
-}
-
-template <typename R>
-__device__ __forceinline__ R qs_dw(R q) {
-    if (q >= R(3)) return R(0);
-    R a = R(3) - q, a2 = a * a;
-    R w = R(-5) * (a2 * a2);
-    if (q < R(2)) {
-        R b = R(2) - q, b2 = b * b;
-        w += R(30) * (b2 * b2);
-        if (q < R(1)) {
-            R c = R(1) - q, c2 = c * c;
-            w -= R(75) * (c2 * c2);
-        }
-    }
-    return w;
-}
-
-template <typename R>
-__device__ __forceinline__ R sigma_norm() {
-    return R(7.0 / (478.0 * PI));
-}
-
-// Separation r_i - r_j of list entry j: FP64 minimum image on the FP64
-// path; on the mixed path rebuilt in FP32 from the anchor coordinates.
-template <typename R> struct Sep;
-template <> struct Sep<double> {
-    double xi, yi;
-    __device__ __forceinline__ void init(const Domain &, const double *x,
-                                         const double *y, const float4 *, int i) {
-        xi = x[i];
-        yi = y[i];
-    }
-    __device__ __forceinline__ void get(const Domain &d, const Anchor &,
-                                        const double *x, const double *y,
-                                        const float4 *, int j, double &dx,
-                                        double &dy, double &r2) const {
-        dx = min_image(d, 0, __dsub_rn(xi, __ldg(&x[j])));
-        dy = min_image(d, 1, __dsub_rn(yi, __ldg(&y[j])));
-        r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-    }
-};
-template <> struct Sep<float> {
-    float4 pi;
-    __device__ __forceinline__ void init(const Domain &, const double *,
-                                         const double *, const float4 *pk, int i) {
-        pi = pk[i];
-    }
-    __device__ __forceinline__ void get(const Domain &, const Anchor &an,
-                                        const double *, const double *,
-                                        const float4 *pk, int j, float &dx,
-                                        float &dy, float &r2) const {
-        anchor_sep(an, pi, __ldg(&pk[j]), dx, dy);
-        r2 = fmaf(dx, dx, dy * dy);
-    }
-};
 
 // ---------------------------------------------------------------- pass A --
 // Summation density (Eq. sd-gather), beta (Eq. beta), p_avg (Eq. pavg,
 // N_i counts i), shift dr (Eq. shift-deltar, volume m_j / rho0, W ratio
 // against the kernel at its inflection point for h_ij = (h_i + h_j)/2),
 // limited to 0.25 h_i (Eq. shift-limit).  Also stores V_i = m_i / rho_i and
-// 1 / (rho_i^2 beta_i) for pass B.
-template <typename R>
+// 1 / (rho_i^2 beta_i) for pass B.  A team of T threads shares particle i.
+template <typename R, int T>
 __global__ void __launch_bounds__(128)
     k_pass_a(PassAArgs<R> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const Team<T> tm;
+    const int i = Team<T>::particle();
     if (i >= a.n) return;
     Sep<R> sp;
     sp.init(a.d, a.x, a.y, a.pk, i);
@@ -102,19 +32,16 @@ __global__ void __launch_bounds__(128)
     const R hinv = R(1) / hi;
     const R inv_wxi = R(1) / qs_w<R>(R(XI_INFLECTION));
     R rho = 0, srw = 0, psum = 0, ax = 0, ay = 0;
-    const uint32_t b = a.off[i], e = a.off[i + 1];
-    for (uint32_t k = b; k < e; ++k) {
-        const int j = (int)__ldg(&a.list[k]);
-        R dx, dy, r2;
-        sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+    int cnt = 0;
+    auto pair = [&](R mj, R hj, R pj, bool self, R dx, R dy, R r2) {
         const R r = sqrt(r2);
-        const R mj = a.m[j];
         const R q = r * hinv;
         rho += mj * qs_w<R>(q);
         srw += mj * r * qs_dw<R>(q);
-        psum += a.p[j];
-        if (j != i && r > R(0)) {
-            const R hb = R(0.5) * (hi + (R)a.h[j]);
+        psum += pj;
+        cnt += 1;
+        if (!self && r > R(0)) {
+            const R hb = R(0.5) * (hi + hj);
             const R hbinv = R(1) / hb;
             const R qb = r * hbinv;
             R ratio = qs_w<R>(qb) * inv_wxi;
@@ -125,34 +52,28 @@ __global__ void __launch_bounds__(128)
             ax += f * dx;
             ay += f * dy;
         }
+    };
+    const uint32_t b = a.off[i], e = a.off[i + 1];
+    for (uint32_t k = b + tm.lane; k < e; k += T) {
+        const int j = (int)__ldg(&a.list[k]);
+        R dx, dy, r2;
+        sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+        pair(a.m[j], (R)a.h[j], a.p[j], j == i, dx, dy, r2);
     }
-    int cnt = (int)(e - b);
     if (a.w.n > 0) {
-        const double xi = a.x[i], yi = a.y[i], hid = a.h[i];
-        for_each_wall(a.w, a.d, xi, yi, hid, [&](int k, double dxd, double dyd,
-                                                double r2d) {
-            const R dx = (R)dxd, dy = (R)dyd;
-            const R r = sqrt((R)r2d);
-            const R mk = (R)a.w.m[k];
-            const R q = r * hinv;
-            rho += mk * qs_w<R>(q);
-            srw += mk * r * qs_dw<R>(q);
-            psum += (R)a.w.p[k];
-            cnt += 1;
-            if (r > R(0)) {
-                const R hb = R(0.5) * (hi + (R)a.w.h[k]);
-                const R hbinv = R(1) / hb;
-                const R qb = r * hbinv;
-                R ratio = qs_w<R>(qb) * inv_wxi;
-                ratio *= ratio;
-                const R f = mk * (R(1) + R(0.24) * ratio * ratio) *
-                            (sigma_norm<R>() * hbinv * hbinv * hbinv) *
-                            qs_dw<R>(qb) / r;
-                ax += f * dx;
-                ay += f * dy;
-            }
+        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane,
+                      [&](int k, double dxd, double dyd, double r2d) {
+            pair((R)a.w.m[k], (R)a.w.h[k], (R)a.w.p[k], false, (R)dxd,
+                 (R)dyd, (R)r2d);
         });
     }
+    rho = team_sum<T>(tm.mask, rho);
+    srw = team_sum<T>(tm.mask, srw);
+    psum = team_sum<T>(tm.mask, psum);
+    ax = team_sum<T>(tm.mask, ax);
+    ay = team_sum<T>(tm.mask, ay);
+    cnt = team_sum<T>(tm.mask, cnt);
+    if (tm.lane != 0) return;
     const R sig = sigma_norm<R>() * hinv * hinv;
     rho *= sig;
     const R beta = -(sig * hinv * srw) / (rho * R(2));
@@ -190,17 +111,22 @@ __global__ void __launch_bounds__(128)
 // gW_i = grad W(r_ij, h_i), gW_ij the mean of gW_i and gW_j (Eq. dw-avg),
 // nu_ij the Cleary mean of nu_e = alpha_e c h / 8 (Eqs. edac-alpha,
 // nu-cleary), eta = 0.001 h_i^2, P_j = (p_j - p_avg,i) / (rho_j^2 beta_j).
-template <typename R>
+// Wall neighbours (section 2.2): prescribed wall velocity in the divergence
+// sum, extrapolated velocity in the viscous sum, rho_w = rho0, beta_w = 1.
+template <typename R, int T>
 __global__ void __launch_bounds__(128)
     k_pass_b(PassBArgs<R> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const Team<T> tm;
+    const int i = Team<T>::particle();
     if (i >= a.n) return;
     const R rb2i = a.rb2[i];
     const R beta_i = a.beta[i];
     if (beta_i == R(0)) {
-        a.dpdt[i] = R(0);
-        a.dudt[i] = R(0);
-        a.dvdt[i] = R(0);
+        if (tm.lane == 0) {
+            a.dpdt[i] = R(0);
+            a.dudt[i] = R(0);
+            a.dvdt[i] = R(0);
+        }
         return;
     }
     Sep<R> sp;
@@ -216,14 +142,11 @@ __global__ void __launch_bounds__(128)
     const R dux = (R)((double)a.drx[i] / dt), duy = (R)((double)a.dry[i] / dt);
     const R four_nu = R(4) * (R)a.nu;
     R div = 0, diff = 0, tvf = 0, fax = 0, fay = 0, vx = 0, vy = 0;
-    const uint32_t b = a.off[i], e = a.off[i + 1];
-    for (uint32_t k = b; k < e; ++k) {
-        const int j = (int)__ldg(&a.list[k]);
-        if (j == i) continue;
-        R dx, dy, r2;
-        sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+    // one neighbour's contributions; uj: velocity in the divergence sum,
+    // ugj: velocity in the viscous sum
+    auto pair = [&](R dx, R dy, R r2, R hj, R mj, R Vj, R rho_j, R Pj, R pj,
+                    R ujx, R ujy, R ugx, R ugy) {
         const R r = sqrt(r2);
-        const R hj = (R)a.h[j];
         R gi = 0, gj = 0;
         if (r > R(0)) {
             const R hjinv = R(1) / hj;
@@ -233,65 +156,52 @@ __global__ void __launch_bounds__(128)
                  qs_dw<R>(r * hjinv) * rinv;
         }
         const R rdg = R(0.5) * (gi + gj) * r2;
-        const R mj = a.m[j], Vj = a.V[j], rho_j = a.rho[j];
-        const R uij = ui - a.u[j], vij = vi - a.v[j];
-        const R pj = a.p[j];
-        const R pref = a.pavg_mode == 0 ? pavg_i : a.pavg[j];
-        const R Pj = (pj - pref) * a.rb2[j];
+        const R uij = ui - ujx, vij = vi - ujy;
         const R nu_j = (R)a.alpha_e * (R)a.cs * hj / R(8);
         const R nu_ij = R(4) * nu_i * nu_j / (nu_i + nu_j);
         const R dden = a.diff_denominator ? (r2 + eta) : R(1);
         div += Vj * (uij * gi * dx + vij * gi * dy);
         diff += Vj * nu_ij * (pi - pj) * rdg / dden;
-        const R fx = (Pi * gi + Pj * gj) * dx;
-        const R fy = (Pi * gi + Pj * gj) * dy;
+        const R fp = Pi * gi + Pj * gj;
+        const R fx = fp * dx, fy = fp * dy;
         tvf += mj * (dux * fx + duy * fy);
         fax -= mj * fx;
         fay -= mj * fy;
         const R visc = mj * (four_nu / (rho_i + rho_j)) * rdg / (r2 + eta);
-        vx += visc * uij;
-        vy += visc * vij;
+        vx += visc * (ui - ugx);
+        vy += visc * (vi - ugy);
+    };
+    const uint32_t b = a.off[i], e = a.off[i + 1];
+    for (uint32_t k = b + tm.lane; k < e; k += T) {
+        const int j = (int)__ldg(&a.list[k]);
+        if (j == i) continue;
+        R dx, dy, r2;
+        sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+        const R pj = a.p[j];
+        const R pref = a.pavg_mode == 0 ? pavg_i : a.pavg[j];
+        const R uj = a.u[j], vj = a.v[j];
+        pair(dx, dy, r2, (R)a.h[j], a.m[j], a.V[j], a.rho[j],
+             (pj - pref) * a.rb2[j], pj, uj, vj, uj, vj);
     }
     if (a.w.n > 0) {
-        const double xi = a.x[i], yi = a.y[i];
         const R rho0 = (R)a.rho0;
-        for_each_wall(a.w, a.d, xi, yi, (double)a.h[i], [&](int k, double dxd,
-                                                           double dyd, double r2d) {
-            const R dx = (R)dxd, dy = (R)dyd, r2 = (R)r2d;
-            const R r = sqrt(r2);
-            const R hk = (R)a.w.h[k];
-            R gi = 0, gj = 0;
-            if (r > R(0)) {
-                const R hkinv = R(1) / hk;
-                const R rinv = R(1) / r;
-                gi = dsig_i * qs_dw<R>(r * hinv) * rinv;
-                gj = sigma_norm<R>() * hkinv * hkinv * hkinv *
-                     qs_dw<R>(r * hkinv) * rinv;
-            }
-            const R rdg = R(0.5) * (gi + gj) * r2;
-            const R mk = (R)a.w.m[k];
-            const R Vk = mk / rho0;
-            // prescribed wall velocity (no penetration) in the divergence
-            const R uij = ui - (R)a.w.uw[k], vij = vi - (R)a.w.vw[k];
-            const R pk = (R)a.w.p[k];
+        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane,
+                      [&](int k, double dxd, double dyd, double r2d) {
+            const R mk = (R)a.w.m[k], pk = (R)a.w.p[k];
             const R pref = a.pavg_mode == 0 ? pavg_i : R(0);
-            const R Pk = (pk - pref) / (rho0 * rho0);
-            const R nu_k = (R)a.alpha_e * (R)a.cs * hk / R(8);
-            const R nu_ik = R(4) * nu_i * nu_k / (nu_i + nu_k);
-            const R dden = a.diff_denominator ? (r2 + eta) : R(1);
-            div += Vk * (uij * gi * dx + vij * gi * dy);
-            diff += Vk * nu_ik * (pi - pk) * rdg / dden;
-            const R fx = (Pi * gi + Pk * gj) * dx;
-            const R fy = (Pi * gi + Pk * gj) * dy;
-            tvf += mk * (dux * fx + duy * fy);
-            fax -= mk * fx;
-            fay -= mk * fy;
-            // extrapolated wall velocity (no slip) in the viscous term
-            const R visc = mk * (four_nu / (rho_i + rho0)) * rdg / (r2 + eta);
-            vx += visc * (ui - (R)a.w.ugx[k]);
-            vy += visc * (vi - (R)a.w.ugy[k]);
+            pair((R)dxd, (R)dyd, (R)r2d, (R)a.w.h[k], mk, mk / rho0, rho0,
+                 (pk - pref) / (rho0 * rho0), pk, (R)a.w.uw[k], (R)a.w.vw[k],
+                 (R)a.w.ugx[k], (R)a.w.ugy[k]);
         });
     }
+    div = team_sum<T>(tm.mask, div);
+    diff = team_sum<T>(tm.mask, diff);
+    tvf = team_sum<T>(tm.mask, tvf);
+    fax = team_sum<T>(tm.mask, fax);
+    fay = team_sum<T>(tm.mask, fay);
+    vx = team_sum<T>(tm.mask, vx);
+    vy = team_sum<T>(tm.mask, vy);
+    if (tm.lane != 0) return;
     const R rf = a.rho_factor ? rho_i : R(1);
     const R dpdt = ((R)a.rho0 * (R)a.cs * (R)a.cs / beta_i) * div +
                    diff / beta_i + rf * tvf;
@@ -310,24 +220,39 @@ __global__ void __launch_bounds__(128)
 // W_wf = W(r_wf, (h_w + h_f)/2): u^ = sum u_f W / sum W (Eq. shepard),
 // u_ghost = 2 u_wall - u^ (Eq. bc-wall), p_w = sum p_f W / sum W (Eq.
 // bc-pre with g = a_w = 0); p_w = 0 and u^ = 0 without fluid in range.
-__global__ void k_wall_bc(WallBcArgs a) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+template <int T>
+__global__ void __launch_bounds__(128) k_wall_bc(WallBcArgs a) {
+    const Team<T> tm;
+    const int k = Team<T>::particle();
     if (k >= a.w.n) return;
     const double xw = a.w.x[k], yw = a.w.y[k], hw = a.w.h[k];
+    const float4 pw = a.w.pk[k];
+    const float2 q = anchor_rel(a.an, pw);
     double sw = 0, su = 0, sv = 0, sp = 0;
-    for_each_candidate(a.g, a.d, 0, xw, yw, hw, [&](int f) {
-        const double xf = __ldg(&a.x[f]), yf = __ldg(&a.y[f]), hf = __ldg(&a.h[f]);
-        if (!pred_fp64(a.d, xw, yw, hw, xf, yf, hf)) return;
-        double dx = min_image(a.d, 0, xw - xf), dy = min_image(a.d, 1, yw - yf);
-        const double hb = 0.5 * (hw + hf);
-        const double hbinv = 1.0 / hb;
-        const double W = sigma_norm<double>() * hbinv * hbinv *
-                         qs_w<double>(sqrt(dx * dx + dy * dy) * hbinv);
-        sw += W;
-        su += a.u[f] * W;
-        sv += a.v[f] * W;
-        sp += a.p[f] * W;
+    for_each_cell(a.g, a.d, 0, q.x, q.y, pw.z, [&](uint32_t s, uint32_t e) {
+        for (uint32_t f = s + tm.lane; f < e; f += T) {
+            float fx, fy, fr2;
+            if (!pred_mixed(a.d, a.an, pw, __ldg(&a.pk[f]), xw, yw, hw, a.x,
+                            a.y, a.h, (int)f, fx, fy, fr2))
+                continue;
+            const double xf = __ldg(&a.x[f]), yf = __ldg(&a.y[f]),
+                         hf = __ldg(&a.h[f]);
+            const double dx = min_image(a.d, 0, xw - xf);
+            const double dy = min_image(a.d, 1, yw - yf);
+            const double hbinv = 1.0 / (0.5 * (hw + hf));
+            const double W = sigma_norm<double>() * hbinv * hbinv *
+                             qs_w<double>(sqrt(dx * dx + dy * dy) * hbinv);
+            sw += W;
+            su += a.u[f] * W;
+            sv += a.v[f] * W;
+            sp += a.p[f] * W;
+        }
     });
+    sw = team_sum<T>(tm.mask, sw);
+    su = team_sum<T>(tm.mask, su);
+    sv = team_sum<T>(tm.mask, sv);
+    sp = team_sum<T>(tm.mask, sp);
+    if (tm.lane != 0) return;
     double uh = 0, vh = 0, p = 0;
     if (sw > 0) {
         uh = su / sw;
@@ -437,11 +362,21 @@ static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
 
 template <typename R>
 void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a) {
-    if (a.n > 0) k_pass_a<R><<<nblk(a.n, 128), 128, 0, s>>>(a);
+    if (a.n <= 0) return;
+    switch (team_size(a.n)) {
+    case 16: k_pass_a<R, 16><<<nblk(a.n * 16, 128), 128, 0, s>>>(a); break;
+    case 4: k_pass_a<R, 4><<<nblk(a.n * 4, 128), 128, 0, s>>>(a); break;
+    default: k_pass_a<R, 1><<<nblk(a.n, 128), 128, 0, s>>>(a); break;
+    }
 }
 template <typename R>
 void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a) {
-    if (a.n > 0) k_pass_b<R><<<nblk(a.n, 128), 128, 0, s>>>(a);
+    if (a.n <= 0) return;
+    switch (team_size(a.n)) {
+    case 16: k_pass_b<R, 16><<<nblk(a.n * 16, 128), 128, 0, s>>>(a); break;
+    case 4: k_pass_b<R, 4><<<nblk(a.n * 4, 128), 128, 0, s>>>(a); break;
+    default: k_pass_b<R, 1><<<nblk(a.n, 128), 128, 0, s>>>(a); break;
+    }
 }
 template <typename R>
 void launch_pec(cudaStream_t s, const PecArgs<R> &a) {
@@ -455,7 +390,7 @@ template void launch_pec<double>(cudaStream_t, const PecArgs<double> &);
 template void launch_pec<float>(cudaStream_t, const PecArgs<float> &);
 
 void launch_wall_bc(cudaStream_t s, const WallBcArgs &a) {
-    if (a.w.n > 0) k_wall_bc<<<nblk(a.w.n, 128), 128, 0, s>>>(a);
+    if (a.w.n > 0) k_wall_bc<16><<<nblk(a.w.n * 16, 128), 128, 0, s>>>(a);
 }
 void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,
                     const uint32_t *list, const int64_t *id, int64_t *out) {

@@ -43,6 +43,8 @@ struct StaticSet {
     double *x = nullptr, *y = nullptr, *h = nullptr;
     double *ex[3] = {nullptr, nullptr, nullptr};   // extra per-particle fields
     int nex = 0;
+    float4 *pk = nullptr;       // anchor data (context anchor lattice)
+    int pk_version = -1;        // anchor version pk was computed for
     int64_t *id = nullptr;                         // load index
     uint64_t *key = nullptr, *tkey = nullptr;
     uint32_t *perm = nullptr, *tstart = nullptr, *tend = nullptr;
@@ -56,7 +58,7 @@ struct StaticSet {
 };
 
 static void free_set(StaticSet *S) {
-    void *ps[] = {S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2], S->id,
+    void *ps[] = {S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2], S->id, S->pk,
                   S->key, S->tkey, S->perm, S->tstart, S->tend, S->bbox,
                   S->mask, S->sc.key_alt, S->sc.val_alt, S->sc.counts,
                   S->sc.scan_tmp};
@@ -105,12 +107,14 @@ struct sph_ctx {
     uint32_t *longq = nullptr, *d_nlong = nullptr;
     Anchor an;
     double anchor_A[2] = {0, 0};
+    int anchor_version = 0;     // bumped whenever the anchor lattice is set
 
     // adaptation
     long long next_id = 0;
     uint32_t *tmp_a = nullptr, *tmp_b = nullptr;   // N + 1 each
     int *closest = nullptr;
     double *d_mass = nullptr, *d_mass_part = nullptr;  // [2], [256]
+    uint32_t *d_aux = nullptr;                         // [4] adapt counters
     StaticSet bg;     // background particles (section 3.3); extra: ds
     StaticSet wall;   // dummy wall particles (section 2.2); extra: m, u, v
     double *wp = nullptr, *wugx = nullptr, *wugy = nullptr;   // wall BC
@@ -130,6 +134,7 @@ struct sph_ctx {
 
 static Grid set_grid(const StaticSet &S);
 static WallView wall_view(const sph_ctx *c);
+static void ensure_set_pk(sph_ctx *c, StaticSet *S);
 
 // ------------------------------------------------------------- helpers --
 static sph_status fail(sph_ctx *c, sph_status st, const std::string &msg) {
@@ -420,8 +425,11 @@ static void passes(sph_ctx *c) {
 }
 
 static void run_passes(sph_ctx *c) {
+    ensure_set_pk(c, &c->wall);
     if (c->wall.n > 0) {
         WallBcArgs wb;
+        wb.an = c->an;
+        wb.pk = c->pk;
         wb.w = wall_view(c);
         wb.g = grid_for_kernels(c);
         wb.d = c->dom;
@@ -512,7 +520,7 @@ static void free_ctx(sph_ctx *c) {
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
                   c->d_overflow, c->longq, c->d_nlong, c->tmp_a, c->tmp_b,
                   c->closest, c->d_mass, c->d_mass_part, c->wp, c->wugx,
-                  c->wugy};
+                  c->wugy, c->d_aux};
     for (void *p : ps) cudaFree(p);
     free_set(&c->bg);
     free_set(&c->wall);
@@ -553,6 +561,7 @@ static sph_status build_set(sph_ctx *c, StaticSet *S, long long n,
         size_t N = (size_t)n;
         bool ok = dalloc(&S->x, N) && dalloc(&S->y, N) && dalloc(&S->h, N) &&
                   dalloc(&S->id, N) && dalloc(&S->key, N) && dalloc(&S->perm, N) &&
+                  dalloc(&S->pk, N) &&
                   dalloc(&S->bbox, MAX_LEVELS * 4) && dalloc(&S->mask, 1) &&
                   dalloc(&S->sc.key_alt, N) && dalloc(&S->sc.val_alt, N);
         for (int k = 0; k < nex; ++k) ok = ok && dalloc(&S->ex[k], N);
@@ -621,7 +630,18 @@ static sph_status build_set(sph_ctx *c, StaticSet *S, long long n,
     cudaFree(tid);
     if (e != cudaSuccess) return cuda_check(c, "build_set");
     S->n = (int)n;
+    S->pk_version = -1;
     return cuda_check(c, "build_set");
+}
+
+// Anchor data of a static set for the context's current anchor lattice.
+static void ensure_set_pk(sph_ctx *c, StaticSet *S) {
+    if (S->n <= 0 || c->anchor_version == 0 || S->pk_version == c->anchor_version)
+        return;
+    launch_anchor_pack(c->s, S->n, S->x, S->y, S->h, c->dom.lo, c->anchor_A,
+                       c->an, S->pk);
+    c->launches += 1;
+    S->pk_version = c->anchor_version;
 }
 
 static Grid set_grid(const StaticSet &S) {
@@ -648,6 +668,7 @@ static WallView wall_view(const sph_ctx *c) {
     w.m = c->wall.ex[0];
     w.uw = c->wall.ex[1];
     w.vw = c->wall.ex[2];
+    w.pk = c->wall.pk;
     w.p = c->wp;
     w.ugx = c->wugx;
     w.ugy = c->wugy;
@@ -795,7 +816,7 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
          dalloc(&c->longq, N) && dalloc(&c->d_nlong, 1);
     ok = ok && dalloc(&c->tmp_a, N + 1) && dalloc(&c->tmp_b, N + 1) &&
          dalloc(&c->closest, N) && dalloc(&c->d_mass, 2) &&
-         dalloc(&c->d_mass_part, 256);
+         dalloc(&c->d_mass_part, 256) && dalloc(&c->d_aux, 4);
     c->list_cap = std::min<size_t>(N * 48, 0xffffffffull);
     ok = ok && dalloc(&c->list, c->list_cap);
     if (!ok) {
@@ -886,6 +907,7 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
     c->an = an;
     c->anchor_A[0] = Ad[0];
     c->anchor_A[1] = Ad[1];
+    c->anchor_version += 1;
     c->c0 = c0;
     c->lmax = lmax;
     memcpy(c->lev, lev, sizeof(lev));
@@ -1005,11 +1027,20 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     t_begin(c, 4, &ev);
     launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass);
     // resolution from the background (section 3.3)
+    ensure_set_pk(c, &c->wall);
     if (c->bg.n > 0) {
+        ensure_set_pk(c, &c->bg);
+        // fluid anchor data at the current positions (moved since the last
+        // rebuild)
+        launch_anchor_pack(c->s, c->n, c->f[F_X], c->f[F_Y], c->f[F_H],
+                           c->dom.lo, c->anchor_A, c->an, c->pk);
         BgArgs a;
         a.n = c->n;
         a.d = c->dom;
         a.g = set_grid(c->bg);
+        a.an = c->an;
+        a.pk = c->pk;
+        a.bpk = c->bg.pk;
         a.x = c->f[F_X];
         a.y = c->f[F_Y];
         a.h = c->f[F_H];
@@ -1023,9 +1054,11 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         a.bid = c->bg.id;
         a.rho0 = c->prm.rho0;
         a.queue = c->tmp_b;
-        a.nqueue = c->d_total;
+        a.nqueue = c->d_aux;
         launch_bg_mref(c->s, a);
         c->launches += 2;
+    } else {
+        cudaMemsetAsync(c->d_aux, 0, sizeof(uint32_t), c->s);
     }
     // split pass (section 3.1): flag, scan, rank parents by id, emit
     launch_split_flag(c->s, c->n, c->f[F_M], c->f[F_MMAX], c->tmp_a);
@@ -1100,24 +1133,30 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         sa.list = c->list;
         sa.rho0 = c->prm.rho0;
         sa.hdx = c->prm.hdx;
-        sa.rho = (double *)c->rhoR;
-        sa.drx = (double *)c->drx;
-        sa.dry = (double *)c->dry;
-        sa.du = (double *)c->dudt;
-        sa.dv = (double *)c->dvdt;
-        sa.dp = (double *)c->dpdt;
-        sa.hnew = (double *)c->V;
+        sa.rho = c->rhoR;
+        sa.drx = c->drx;
+        sa.dry = c->dry;
+        sa.du = c->dudt;
+        sa.dv = c->dvdt;
+        sa.dp = c->dpdt;
+        sa.hnew = c->V;
         sa.w = wall_view(c);
+        sa.an = c->an;
+        sa.pk = c->pk;
+        sa.mf = c->mf;
+        sa.uf = c->uf;
+        sa.vf = c->vf;
+        sa.pf = c->pf;
     };
     for (int r = 0; r < c->prm.shift_iters; ++r) {
         if ((st = rebuild(c, false)) != SPH_OK) return st;
         shift_args();
-        launch_shift_round(c->s, sa);
+        launch_shift_round(c->s, sa, is_mixed(c));
         c->launches += 3;
     }
     if ((st = rebuild(c, false)) != SPH_OK) return st;
     shift_args();
-    launch_h_update(c->s, sa);
+    launch_h_update(c->s, sa, is_mixed(c));
     c->launches += 2;
     launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass + 1);
     c->launches += 4;
@@ -1125,10 +1164,13 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     c->grid_valid = false;   // h changed since the last rebuild
     c->rhs_valid = false;
     double mass[2] = {0, 0};
+    uint32_t nfb = 0;
     cudaMemcpyAsync(mass, c->d_mass, sizeof(mass), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(&nfb, c->d_aux, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
     if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_adapt");
     z.mass_before = mass[0];
     z.mass_after = mass[1];
+    z.n_bg_nearest = nfb;
     z.n_after = c->n;
     if (out) *out = z;
     return cuda_check(c, "sph_adapt");

@@ -29,6 +29,8 @@ struct Level {
     double c;      // nominal cell side c0 * 2^l (>= 3h of its particles)
     double w[2];   // cell width per axis (L / count on periodic axes)
     int n[2];      // cell count per axis
+    float cf;      // c in FP32
+    float invw[2]; // 1 / w in FP32 (cell ranges of queries)
 };
 
 // Device view of the cell structure built by a rebuild.  Particles are

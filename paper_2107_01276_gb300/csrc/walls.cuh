@@ -11,24 +11,36 @@ struct WallView {
     int n;
     Grid g;
     const double *x, *y, *h, *m, *uw, *vw;
+    const float4 *pk;             // anchor coordinates of the walls
     const double *p, *ugx, *ugy;
 };
 
 // Calls f(k, dx, dy, r2) for every wall particle k with r_ik < 3 max(h_i,
-// h_k) (the FP64 predicate), (dx, dy) = r_i - r_k by minimum image.
-template <class F>
+// h_k) (membership by the FP32 anchor filter with the FP64 predicate in
+// its band), (dx, dy) = r_i - r_k by FP64 minimum image.  With a team of T
+// threads, lane `lane` takes every T-th wall cell.  pi: particle i's
+// anchor data.
+template <int T, class F>
 __device__ __forceinline__ void for_each_wall(const WallView &w,
-                                              const Domain &d, double xi,
-                                              double yi, double hi, F &&f) {
+                                              const Domain &d,
+                                              const Anchor &an,
+                                              const float4 &pi, double xi,
+                                              double yi, double hi, int lane,
+                                              F &&f) {
     if (w.n <= 0) return;
-    for_each_candidate(w.g, d, 0, xi, yi, hi, [&](int k) {
-        const double xk = __ldg(&w.x[k]), yk = __ldg(&w.y[k]);
-        const double hk = __ldg(&w.h[k]);
-        double dx = min_image(d, 0, __dsub_rn(xi, xk));
-        double dy = min_image(d, 1, __dsub_rn(yi, yk));
-        double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-        double R = __dmul_rn(3.0, hi > hk ? hi : hk);
-        if (r2 < __dmul_rn(R, R)) f(k, dx, dy, r2);
+    const float2 q = anchor_rel(an, pi);
+    int c = 0;
+    for_each_cell(w.g, d, 0, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
+        if ((c++ & (T - 1)) != lane) return;
+        for (uint32_t k = s; k < e; ++k) {
+            float fx, fy, fr2;
+            if (!pred_mixed(d, an, pi, __ldg(&w.pk[k]), xi, yi, hi, w.x, w.y,
+                            w.h, (int)k, fx, fy, fr2))
+                continue;
+            const double dx = min_image(d, 0, __dsub_rn(xi, __ldg(&w.x[k])));
+            const double dy = min_image(d, 1, __dsub_rn(yi, __ldg(&w.y[k])));
+            f((int)k, dx, dy, __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        }
     });
 }
 
@@ -36,6 +48,8 @@ struct WallBcArgs {
     WallView w;
     Grid g;                       // fluid cell structure
     Domain d;
+    Anchor an;
+    const float4 *pk;             // fluid anchor data
     const double *x, *y, *h, *u, *v, *p;   // fluid
     double *pw, *ugx, *ugy;
 };

@@ -71,7 +71,8 @@ class AdaptStats(ctypes.Structure):
     _fields_ = [("n_before", ctypes.c_longlong), ("n_split", ctypes.c_longlong),
                 ("n_merged", ctypes.c_longlong), ("n_after", ctypes.c_longlong),
                 ("mass_before", ctypes.c_double),
-                ("mass_after", ctypes.c_double)]
+                ("mass_after", ctypes.c_double),
+                ("n_bg_nearest", ctypes.c_longlong)]
 
 
 class Info(ctypes.Structure):

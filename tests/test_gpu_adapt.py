@@ -73,10 +73,13 @@ def test_split_merge_bit_exact_without_shift():
     sim.close()
 
 
-@pytest.mark.parametrize("precision", [sph.SPH_FP64, sph.SPH_MIXED])
-def test_full_adapt_parity(precision):
+@pytest.mark.parametrize("precision,tol", [(sph.SPH_FP64, 1e-11),
+                                           (sph.SPH_MIXED, 2e-5)])
+def test_full_adapt_parity(precision, tol):
     """Whole adaptation (3 merge and 3 shift rounds): counts equal, ids
-    equal, masses exact, the rest within sum-order rounding."""
+    equal, masses exact (split and merge decisions are FP64 on both paths);
+    positions, h, u, v, p within sum-order rounding (FP64) or the FP32
+    shift and density sums of the mixed path."""
     d, bg = _refine_case(seed=13)
     sim, gst, ost, got, ref = _run_both(d, bg, precision=precision)
     for k in ("n_split", "n_merged", "n_after"):
@@ -88,11 +91,11 @@ def test_full_adapt_parity(precision):
     for k in ("x", "y"):
         dd = got[k] - ref[k]
         dd -= np.round(dd)                   # periodic unit box
-        assert np.abs(dd / h).max() < 1e-11, k
-    assert np.abs(got["h"] / h - 1).max() < 1e-11
+        assert np.abs(dd / h).max() < tol, k
+    assert np.abs(got["h"] / h - 1).max() < tol
     for k in ("u", "v", "p"):
         sc = max(np.abs(ref[k]).max(), 1e-30)
-        assert np.abs(got[k] - ref[k]).max() < 1e-11 * sc, k
+        assert np.abs(got[k] - ref[k]).max() < tol * sc, k
     m0 = gst[0]["mass_before"]
     assert abs(gst[0]["mass_after"] - m0) <= 1e-13 * m0
     assert abs(math.fsum(got["m"]) - math.fsum(d["particles"]["m"])) <= \
