@@ -8,6 +8,8 @@
 #include "neighbors.cuh"
 #include "team.cuh"
 
+#include <algorithm>
+
 namespace sph {
 
 // ------------------------------------------------------------------ pack --
@@ -90,6 +92,66 @@ __global__ void __launch_bounds__(128) k_list_count(ListArgs a) {
     if (tm.lane == 0) a.own[i] = cnt;
 }
 
+// Single-walk list build: each team writes its own entries, in the same
+// (cell, index) order as k_list_fill, into a fixed-stride staging row of
+// STAGE entries; particles with more own entries go to a queue that
+// k_list_fill_queue handles with a second walk.
+constexpr int STAGE = 64;
+
+template <int T>
+__global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
+    if (i >= a.n) return;
+    const int li = a.lev[i];
+    const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
+    const float4 pi = a.pk[i];
+    const float2 q = anchor_rel(a.an, pi);
+    uint32_t k = 0;
+    uint32_t *row = a.stage + (size_t)i * STAGE;
+    const unsigned below = tm.mask & ((1u << (threadIdx.x & 31)) - 1u);
+    for_each_cell(a.g, a.d, li, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
+        for (uint32_t j0 = s; j0 < e; j0 += T) {
+            const uint32_t j = j0 + tm.lane;
+            const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);
+            const unsigned bal = T == 1 ? (in ? 1u : 0u)
+                                        : __ballot_sync(tm.mask, in);
+            if (in) {
+                const uint32_t pos = k + (T == 1 ? 0u : __popc(bal & below));
+                if (pos < STAGE) row[pos] = j;
+                if (__ldg(&a.lev[j]) > li) atomicAdd(&a.rev[j], 1u);
+            }
+            k += __popc(bal);
+        }
+    });
+    if (tm.lane == 0) {
+        a.own[i] = k;
+        if (k > STAGE) a.queue[atomicAdd(a.nqueue, 1u)] = (uint32_t)i;
+    }
+}
+
+// Copies the staged own entries into place and writes the reverse entries
+// (i into the list of each coarser neighbour j).
+__global__ void k_list_place(ListArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const uint32_t own = a.own[i];
+    if (own > STAGE) return;              // handled by k_list_fill_queue
+    const int li = a.lev[i];
+    const uint32_t base = a.off[i];
+    const uint32_t *row = a.stage + (size_t)i * STAGE;
+    const uint32_t cap = a.cap;
+    for (uint32_t k = 0; k < own; ++k) {
+        const uint32_t j = row[k];
+        if (base + k < cap) a.list[base + k] = j;
+        if (__ldg(&a.lev[j]) > li) {
+            const uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
+            if (rp < cap) a.list[rp] = (uint32_t)i;
+        }
+    }
+    if (i == a.n - 1 && a.off[a.n] > cap) atomicOr(a.overflow, 1);
+}
+
 __global__ void k_list_total(int n, const uint32_t *own, const uint32_t *rev,
                              uint32_t *tot) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -130,11 +192,47 @@ __global__ void __launch_bounds__(128) k_list_fill(ListArgs a) {
     if (i == a.n - 1 && tm.lane == 0 && a.off[a.n] > cap) atomicOr(a.overflow, 1);
 }
 
-// Sort of each reverse segment (ascending index).  Segments of at most 16
+// Second walk for the queued particles (more than STAGE own entries):
+// same order as k_list_fill; teams take queue entries in turn.
+template <int T>
+__global__ void __launch_bounds__(128) k_list_fill_queue(ListArgs a) {
+    const Team<T> tm;
+    const uint32_t nq = *a.nqueue;
+    const uint32_t team = (blockIdx.x * blockDim.x + threadIdx.x) / T;
+    const uint32_t nteam = (gridDim.x * blockDim.x) / T;
+    const unsigned below = tm.mask & ((1u << (threadIdx.x & 31)) - 1u);
+    for (uint32_t qi = team; qi < nq; qi += nteam) {
+        const int i = (int)a.queue[qi];
+        const int li = a.lev[i];
+        const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
+        const float4 pi = a.pk[i];
+        const float2 q = anchor_rel(a.an, pi);
+        uint32_t k = a.off[i];
+        const uint32_t cap = a.cap;
+        for_each_cell(a.g, a.d, li, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
+            for (uint32_t j0 = s; j0 < e; j0 += T) {
+                const uint32_t j = j0 + tm.lane;
+                const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);
+                const unsigned bal = __ballot_sync(tm.mask, in);
+                if (in) {
+                    const uint32_t pos = k + __popc(bal & below);
+                    if (pos < cap) a.list[pos] = j;
+                    if (__ldg(&a.lev[j]) > li) {
+                        uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
+                        if (rp < cap) a.list[rp] = (uint32_t)i;
+                    }
+                }
+                k += __popc(bal);
+            }
+        });
+    }
+}
+
+// Sort of each reverse segment (ascending index).  Segments of at most 32
 // entries (the common case: only particles next to a finer level have
 // any) are sorted in registers by the particle's thread; longer ones are
 // queued for a warp-wide bitonic sort in shared memory.
-constexpr int SORT_REG = 16;
+constexpr int SORT_REG = 32;
 constexpr int SORT_SMEM = 1024;
 
 __global__ void k_list_sort_rev(int n, const uint32_t *off, const uint32_t *own,
@@ -235,16 +333,18 @@ void launch_anchor_pack(cudaStream_t s, int n, const double *x,
 
 void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
                        SortScratch &sc, uint32_t *tot_tmp, int *launches) {
+    (void)mixed;
     const int n = a.n;
     if (n <= 0) {
         cudaMemsetAsync(a.off, 0, sizeof(uint32_t), s);
         return;
     }
     cudaMemsetAsync(a.rev, 0, sizeof(uint32_t) * n, s);
+    cudaMemsetAsync(a.nqueue, 0, sizeof(uint32_t), s);
     const int T = team_size(n);
-    if (T == 16) k_list_count<16><<<nblk(n * 16, 128), 128, 0, s>>>(a);
-    else if (T == 4) k_list_count<4><<<nblk(n * 4, 128), 128, 0, s>>>(a);
-    else k_list_count<1><<<nblk(n, 128), 128, 0, s>>>(a);
+    if (T == 16) k_list_gather<16><<<nblk(n * 16, 128), 128, 0, s>>>(a);
+    else if (T == 4) k_list_gather<4><<<nblk(n * 4, 128), 128, 0, s>>>(a);
+    else k_list_gather<1><<<nblk(n, 128), 128, 0, s>>>(a);
     k_list_total<<<nblk(n, 256), 256, 0, s>>>(n, a.own, a.rev, tot_tmp);
     // off has n + 1 entries: scan n + 1 values with a trailing zero
     cudaMemsetAsync(tot_tmp + n, 0, sizeof(uint32_t), s);
@@ -253,18 +353,18 @@ void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
 }
 
 void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, int *launches) {
+    (void)mixed;
     const int n = a.n;
     if (n <= 0) return;
     cudaMemsetAsync(a.rev, 0, sizeof(uint32_t) * n, s);
-    const int T = team_size(n);
-    if (T == 16) k_list_fill<16><<<nblk(n * 16, 128), 128, 0, s>>>(a);
-    else if (T == 4) k_list_fill<4><<<nblk(n * 4, 128), 128, 0, s>>>(a);
-    else k_list_fill<1><<<nblk(n, 128), 128, 0, s>>>(a);
+    k_list_place<<<nblk(n, 128), 128, 0, s>>>(a);
+    k_list_fill_queue<16><<<152 * 4, 128, 0, s>>>(a);
     cudaMemsetAsync(a.nlong, 0, sizeof(uint32_t), s);
     k_list_sort_rev<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.own, a.list, a.cap,
                                                   a.longq, a.nlong);
-    k_list_sort_long<<<152, 128, 0, s>>>(a.off, a.own, a.list, a.longq, a.nlong);
-    *launches += 3;
+    k_list_sort_long<<<std::max(1, std::min(152 * 16, nblk(n, 512))), 128, 0, s>>>(
+        a.off, a.own, a.list, a.longq, a.nlong);
+    *launches += 4;
 }
 
 }  // namespace sph

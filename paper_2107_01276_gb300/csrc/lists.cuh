@@ -34,6 +34,8 @@ struct ListArgs {
     uint32_t cap;               // list capacity (entries)
     int *overflow;
     uint32_t *longq, *nlong;    // particles with long reverse segments
+    uint32_t *stage;            // n x STAGE staging rows of own entries
+    uint32_t *queue, *nqueue;   // particles whose own entries overflow a row
 };
 
 void launch_pack(cudaStream_t s, const PackArgs &a);

@@ -18,8 +18,9 @@ namespace sph {
 // Summation density (Eq. sd-gather), beta (Eq. beta), p_avg (Eq. pavg,
 // N_i counts i), shift dr (Eq. shift-deltar, volume m_j / rho0, W ratio
 // against the kernel at its inflection point for h_ij = (h_i + h_j)/2),
-// limited to 0.25 h_i (Eq. shift-limit).  Also stores V_i = m_i / rho_i and
-// 1 / (rho_i^2 beta_i) for pass B.  A team of T threads shares particle i.
+// limited to 0.25 h_i (Eq. shift-limit).  Also writes the two per-particle
+// records pass B gathers: {m, V = m/rho, rho, 1/(rho^2 beta)} and
+// {p, u, v, 1/h}.  A team of T threads shares particle i.
 template <typename R, int T>
 __global__ void __launch_bounds__(128)
     k_pass_a(PassAArgs<R> a) {
@@ -34,21 +35,21 @@ __global__ void __launch_bounds__(128)
     R rho = 0, srw = 0, psum = 0, ax = 0, ay = 0;
     int cnt = 0;
     auto pair = [&](R mj, R hj, R pj, bool self, R dx, R dy, R r2) {
-        const R r = sqrt(r2);
+        const R rinv = r2 > R(0) ? frsqrt(r2) : R(0);
+        const R r = r2 * rinv;
         const R q = r * hinv;
         rho += mj * qs_w<R>(q);
         srw += mj * r * qs_dw<R>(q);
         psum += pj;
         cnt += 1;
         if (!self && r > R(0)) {
-            const R hb = R(0.5) * (hi + hj);
-            const R hbinv = R(1) / hb;
+            const R hbinv = fdiv(R(2), hi + hj);
             const R qb = r * hbinv;
             R ratio = qs_w<R>(qb) * inv_wxi;
             ratio *= ratio;
             const R f = mj * (R(1) + R(0.24) * ratio * ratio) *
                         (sigma_norm<R>() * hbinv * hbinv * hbinv) *
-                        qs_dw<R>(qb) / r;
+                        qs_dw<R>(qb) * rinv;
             ax += f * dx;
             ay += f * dy;
         }
@@ -56,9 +57,9 @@ __global__ void __launch_bounds__(128)
     const uint32_t b = a.off[i], e = a.off[i + 1];
     for (uint32_t k = b + tm.lane; k < e; k += T) {
         const int j = (int)__ldg(&a.list[k]);
-        R dx, dy, r2;
-        sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
-        pair(a.m[j], (R)a.h[j], a.p[j], j == i, dx, dy, r2);
+        R dx, dy, r2, hj;
+        sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
+        pair(a.m[j], hj, a.p[j], j == i, dx, dy, r2);
     }
     if (a.w.n > 0) {
         for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane,
@@ -90,14 +91,22 @@ __global__ void __launch_bounds__(128)
         drx *= th;
         dry *= th;
     }
+    const R mi = a.m[i];
+    const R V = mi / rho;
+    const R rb2 = beta != R(0) ? R(1) / (rho * rho * beta) : R(0);
     a.rho[i] = rho;
     a.beta[i] = beta;
     a.pavg[i] = psum / (R)cnt;
     a.nnb[i] = cnt;
     a.drx[i] = drx;
     a.dry[i] = dry;
-    a.V[i] = a.m[i] / rho;
-    a.rb2[i] = beta != R(0) ? R(1) / (rho * rho * beta) : R(0);
+    a.V[i] = V;
+    a.rb2[i] = rb2;
+    typename V4<R>::T A, B;
+    A.x = mi; A.y = V; A.z = rho; A.w = rb2;
+    B.x = a.p[i]; B.y = a.u[i]; B.z = a.v[i]; B.w = hinv;
+    a.nbA[i] = A;
+    a.nbB[i] = B;
 }
 
 // ---------------------------------------------------------------- pass B --
@@ -109,8 +118,9 @@ __global__ void __launch_bounds__(128)
 //   du/dt = -sum m_j (P_i gW_i + P_j gW_j)
 //         + 1/beta_i sum m_j 4 nu/(rho_i + rho_j) r_ij.gW_ij/(r^2 + eta) u_ij
 // gW_i = grad W(r_ij, h_i), gW_ij the mean of gW_i and gW_j (Eq. dw-avg),
-// nu_ij the Cleary mean of nu_e = alpha_e c h / 8 (Eqs. edac-alpha,
-// nu-cleary), eta = 0.001 h_i^2, P_j = (p_j - p_avg,i) / (rho_j^2 beta_j).
+// nu_ij the Cleary mean 4 nu_i nu_j/(nu_i + nu_j) of nu_e = alpha_e c h / 8
+// (Eqs. edac-alpha, nu-cleary), which equals (alpha_e c / 2) / (1/h_i +
+// 1/h_j); eta = 0.001 h_i^2, P_j = (p_j - p_avg,i) / (rho_j^2 beta_j).
 // Wall neighbours (section 2.2): prescribed wall velocity in the divergence
 // sum, extrapolated velocity in the viscous sum, rho_w = rho0, beta_w = 1.
 template <typename R, int T>
@@ -131,67 +141,68 @@ __global__ void __launch_bounds__(128)
     }
     Sep<R> sp;
     sp.init(a.d, a.x, a.y, a.pk, i);
-    const R hi = (R)a.h[i], hinv = R(1) / hi;
+    const typename V4<R>::T Bi = a.nbB[i];
+    const R hinv = Bi.w;
     const R dsig_i = sigma_norm<R>() * hinv * hinv * hinv;
-    const R rho_i = a.rho[i], pi = a.p[i], ui = a.u[i], vi = a.v[i];
+    const R rho_i = a.rho[i], pi = Bi.x, ui = Bi.y, vi = Bi.z;
     const R pavg_i = a.pavg[i];
     const R Pi = (pi - pavg_i) * rb2i;
-    const R nu_i = (R)a.alpha_e * (R)a.cs * hi / R(8);
+    const R half_ac = R(0.5) * (R)a.alpha_e * (R)a.cs;   // 4 nu_e,i nu_e,j / (..) numerator
+    const R hi = R(1) / hinv;
     const R eta = R(0.001) * hi * hi;
     const double dt = *a.dt;
     const R dux = (R)((double)a.drx[i] / dt), duy = (R)((double)a.dry[i] / dt);
     const R four_nu = R(4) * (R)a.nu;
+    const bool dden_on = a.diff_denominator != 0;
     R div = 0, diff = 0, tvf = 0, fax = 0, fay = 0, vx = 0, vy = 0;
-    // one neighbour's contributions; uj: velocity in the divergence sum,
-    // ugj: velocity in the viscous sum
-    auto pair = [&](R dx, R dy, R r2, R hj, R mj, R Vj, R rho_j, R Pj, R pj,
-                    R ujx, R ujy, R ugx, R ugy) {
-        const R r = sqrt(r2);
+    // one neighbour's contributions; (ujx, ujy): velocity in the divergence
+    // sum, (ugx, ugy): velocity in the viscous sum
+    auto pair = [&](R dx, R dy, R r2, R hjinv, R mj, R Vj, R rho_j, R Pj,
+                    R pj, R ujx, R ujy, R ugx, R ugy) {
         R gi = 0, gj = 0;
-        if (r > R(0)) {
-            const R hjinv = R(1) / hj;
-            const R rinv = R(1) / r;
+        if (r2 > R(0)) {
+            const R rinv = frsqrt(r2);
+            const R r = r2 * rinv;
             gi = dsig_i * qs_dw<R>(r * hinv) * rinv;
             gj = sigma_norm<R>() * hjinv * hjinv * hjinv *
                  qs_dw<R>(r * hjinv) * rinv;
         }
         const R rdg = R(0.5) * (gi + gj) * r2;
+        const R nu_ij = fdiv(half_ac, hinv + hjinv);
+        const R inv_reta = fdiv(R(1), r2 + eta);
         const R uij = ui - ujx, vij = vi - ujy;
-        const R nu_j = (R)a.alpha_e * (R)a.cs * hj / R(8);
-        const R nu_ij = R(4) * nu_i * nu_j / (nu_i + nu_j);
-        const R dden = a.diff_denominator ? (r2 + eta) : R(1);
-        div += Vj * (uij * gi * dx + vij * gi * dy);
-        diff += Vj * nu_ij * (pi - pj) * rdg / dden;
+        div += Vj * gi * (uij * dx + vij * dy);
+        diff += Vj * nu_ij * (pi - pj) * rdg * (dden_on ? inv_reta : R(1));
         const R fp = Pi * gi + Pj * gj;
         const R fx = fp * dx, fy = fp * dy;
         tvf += mj * (dux * fx + duy * fy);
         fax -= mj * fx;
         fay -= mj * fy;
-        const R visc = mj * (four_nu / (rho_i + rho_j)) * rdg / (r2 + eta);
+        const R visc = fdiv(mj * four_nu * rdg * inv_reta, rho_i + rho_j);
         vx += visc * (ui - ugx);
         vy += visc * (vi - ugy);
     };
     const uint32_t b = a.off[i], e = a.off[i + 1];
+    const bool literal = a.pavg_mode != 0;
     for (uint32_t k = b + tm.lane; k < e; k += T) {
         const int j = (int)__ldg(&a.list[k]);
         if (j == i) continue;
         R dx, dy, r2;
         sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
-        const R pj = a.p[j];
-        const R pref = a.pavg_mode == 0 ? pavg_i : a.pavg[j];
-        const R uj = a.u[j], vj = a.v[j];
-        pair(dx, dy, r2, (R)a.h[j], a.m[j], a.V[j], a.rho[j],
-             (pj - pref) * a.rb2[j], pj, uj, vj, uj, vj);
+        const typename V4<R>::T A = a.nbA[j], B = a.nbB[j];
+        const R pref = literal ? a.pavg[j] : pavg_i;
+        pair(dx, dy, r2, B.w, A.x, A.y, A.z, (B.x - pref) * A.w, B.x, B.y,
+             B.z, B.y, B.z);
     }
     if (a.w.n > 0) {
         const R rho0 = (R)a.rho0;
         for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane,
                       [&](int k, double dxd, double dyd, double r2d) {
             const R mk = (R)a.w.m[k], pk = (R)a.w.p[k];
-            const R pref = a.pavg_mode == 0 ? pavg_i : R(0);
-            pair((R)dxd, (R)dyd, (R)r2d, (R)a.w.h[k], mk, mk / rho0, rho0,
-                 (pk - pref) / (rho0 * rho0), pk, (R)a.w.uw[k], (R)a.w.vw[k],
-                 (R)a.w.ugx[k], (R)a.w.ugy[k]);
+            const R pref = literal ? R(0) : pavg_i;
+            pair((R)dxd, (R)dyd, (R)r2d, R(1) / (R)a.w.h[k], mk, mk / rho0,
+                 rho0, (pk - pref) / (rho0 * rho0), pk, (R)a.w.uw[k],
+                 (R)a.w.vw[k], (R)a.w.ugx[k], (R)a.w.ugy[k]);
         });
     }
     div = team_sum<T>(tm.mask, div);

@@ -2,6 +2,7 @@
 // time-step reduction (pair_passes.cu).
 #pragma once
 
+#include "kernels.cuh"
 #include "neighbors.cuh"
 #include "sph_internal.cuh"
 #include "walls.cuh"
@@ -16,11 +17,14 @@ struct PassAArgs {
     const uint32_t *off, *list;  // CSR neighbour lists
     const float4 *pk;          // anchor coordinates (mixed path)
     const double *x, *y, *h;   // FP64 positions and smoothing lengths
-    const R *m, *p;            // pair-arithmetic copies
+    const R *m, *p, *u, *v;    // pair-arithmetic copies
     WallView w;
     double rho0;
     R *rho, *beta, *pavg, *drx, *dry, *V, *rb2;
     int *nnb;
+    // per-particle records for pass B: {m, V, rho, 1/(rho^2 beta)} and
+    // {p, u, v, 1/h}
+    typename V4<R>::T *nbA, *nbB;
 };
 
 template <typename R>
@@ -34,6 +38,7 @@ struct PassBArgs {
     const R *m, *p, *u, *v;
     WallView w;
     const R *rho, *beta, *pavg, *drx, *dry, *V, *rb2;
+    const typename V4<R>::T *nbA, *nbB;
     const double *dt;          // device scalar
     double rho0, cs, nu, alpha_e;
     int pavg_mode, diff_denominator, rho_factor;

@@ -82,6 +82,7 @@ struct sph_ctx {
     int64_t *id = nullptr, *id_alt = nullptr;
 
     // pair-pass outputs and mirrors, sized for doubles (floats use half)
+    void *nbA = nullptr, *nbB = nullptr;   // pass-B records (double4 sized)
     void *rhoR = nullptr, *beta = nullptr, *pavg = nullptr, *drx = nullptr,
          *dry = nullptr, *V = nullptr, *rb2 = nullptr, *dpdt = nullptr,
          *dudt = nullptr, *dvdt = nullptr;
@@ -105,6 +106,7 @@ struct sph_ctx {
     size_t list_cap = 0;
     int *d_overflow = nullptr;
     uint32_t *longq = nullptr, *d_nlong = nullptr;
+    uint32_t *stage = nullptr, *lqueue = nullptr, *d_nlq = nullptr;
     Anchor an;
     double anchor_A[2] = {0, 0};
     int anchor_version = 0;     // bumped whenever the anchor lattice is set
@@ -252,6 +254,9 @@ static ListArgs list_args(sph_ctx *c) {
     la.overflow = c->d_overflow;
     la.longq = c->longq;
     la.nlong = c->d_nlong;
+    la.stage = c->stage;
+    la.queue = c->lqueue;
+    la.nqueue = c->d_nlq;
     return la;
 }
 
@@ -360,10 +365,16 @@ static void passes(sph_ctx *c) {
     if (sizeof(R) == sizeof(double)) {
         a.m = (const R *)c->f[F_M];
         a.p = (const R *)c->f[F_P];
+        a.u = (const R *)c->f[F_U];
+        a.v = (const R *)c->f[F_V];
     } else {
         a.m = (const R *)c->mf;
         a.p = (const R *)c->pf;
+        a.u = (const R *)c->uf;
+        a.v = (const R *)c->vf;
     }
+    a.nbA = (typename V4<R>::T *)c->nbA;
+    a.nbB = (typename V4<R>::T *)c->nbB;
     a.rho0 = c->prm.rho0;
     a.w = wall_view(c);
     a.rho = (R *)c->rhoR;
@@ -406,6 +417,8 @@ static void passes(sph_ctx *c) {
     b.dry = a.dry;
     b.V = a.V;
     b.rb2 = a.rb2;
+    b.nbA = a.nbA;
+    b.nbB = a.nbB;
     b.dt = c->d_dt;
     b.rho0 = c->prm.rho0;
     b.cs = c->prm.cs;
@@ -511,14 +524,15 @@ static void free_ctx(sph_ctx *c) {
         cudaFree(c->f[k]);
         cudaFree(c->falt[k]);
     }
-    void *ps[] = {c->id, c->id_alt, c->rhoR, c->beta, c->pavg, c->drx,
+    void *ps[] = {c->nbA, c->nbB, c->id, c->id_alt, c->rhoR, c->beta, c->pavg, c->drx,
                   c->dry, c->V, c->rb2, c->dpdt, c->dudt, c->dvdt, c->mf,
                   c->pf, c->uf, c->vf, c->nnb, c->skey, c->perm,
                   c->sc.key_alt, c->sc.val_alt, c->sc.counts, c->sc.scan_tmp,
                   c->tkey, c->tstart, c->tend, c->bbox, c->level_mask,
                   c->cnt_tmp, c->d_dt, c->d_t, c->d_hmin, c->d_nonfinite,
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
-                  c->d_overflow, c->longq, c->d_nlong, c->tmp_a, c->tmp_b,
+                  c->d_overflow, c->longq, c->d_nlong, c->stage, c->lqueue,
+                  c->d_nlq, c->tmp_a, c->tmp_b,
                   c->closest, c->d_mass, c->d_mass_part, c->wp, c->wugx,
                   c->wugy, c->d_aux};
     for (void *p : ps) cudaFree(p);
@@ -793,6 +807,7 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
                      (double **)&c->rb2, (double **)&c->dpdt, (double **)&c->dudt,
                      (double **)&c->dvdt};
     for (auto pp : rs) ok = ok && dalloc(pp, N);
+    ok = ok && dalloc((double4_32a **)&c->nbA, N) && dalloc((double4_32a **)&c->nbB, N);
     ok = ok && dalloc(&c->mf, N) && dalloc(&c->pf, N) && dalloc(&c->uf, N) &&
          dalloc(&c->vf, N) && dalloc(&c->nnb, N);
     ok = ok && dalloc(&c->skey, N) && dalloc(&c->perm, N) &&
@@ -813,7 +828,8 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
          dalloc(&c->d_overflow, 1);
     ok = ok && dalloc(&c->lvl, N) && dalloc(&c->pk, N) && dalloc(&c->own, N) &&
          dalloc(&c->rev, N) && dalloc(&c->off, N + 1) &&
-         dalloc(&c->longq, N) && dalloc(&c->d_nlong, 1);
+         dalloc(&c->longq, N) && dalloc(&c->d_nlong, 1) &&
+         dalloc(&c->stage, N * 64) && dalloc(&c->lqueue, N) && dalloc(&c->d_nlq, 1);
     ok = ok && dalloc(&c->tmp_a, N + 1) && dalloc(&c->tmp_b, N + 1) &&
          dalloc(&c->closest, N) && dalloc(&c->d_mass, 2) &&
          dalloc(&c->d_mass_part, 256) && dalloc(&c->d_aux, 4);
