@@ -82,6 +82,23 @@ class _AdaptStats(ctypes.Structure):
                 ("mass_after", ctypes.c_double)]
 
 
+class _BgSet(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("cap", ctypes.c_int)] + [
+        (k, ctypes.POINTER(ctypes.c_double)) for k in ("x", "y", "h", "m", "ds")
+    ] + [("id", ctypes.POINTER(ctypes.c_longlong))]
+
+
+class BgParams(ctypes.Structure):
+    _fields_ = [("ds_min", ctypes.c_double), ("ds_max", ctypes.c_double),
+                ("Cr", ctypes.c_double), ("Nr", ctypes.c_double),
+                ("smooth_iters", ctypes.c_int), ("vort_k", ctypes.c_double)]
+
+
+class _BgStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in
+                ("n_before", "n_marked", "n_vort", "n_split", "n_after")]
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 _U64 = ctypes.POINTER(ctypes.c_uint64)
@@ -158,6 +175,33 @@ def lib():
             L.orc_wall_bc.argtypes = [_P, ctypes.POINTER(_State), _D, _D, _D]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
+            L.orc_neighbors_classes.restype = ctypes.c_longlong
+            L.orc_neighbors_classes.argtypes = [_P, ctypes.c_int, _D, _D, _D,
+                                                _I, _I, ctypes.c_longlong]
+            _BG = ctypes.POINTER(_BgSet)
+            _BP = ctypes.POINTER(BgParams)
+            _LL = ctypes.POINTER(ctypes.c_longlong)
+            _U8 = ctypes.POINTER(ctypes.c_uint8)
+            L.orc_bg_iterations.restype = ctypes.c_int
+            L.orc_bg_iterations.argtypes = [_BP]
+            L.orc_vorticity.restype = None
+            L.orc_vorticity.argtypes = [_P, ctypes.POINTER(_State), _D]
+            L.orc_bg_mark.restype = ctypes.c_int
+            L.orc_bg_mark.argtypes = [_P, _BP, _BG, ctypes.c_int, _D, _D, _D,
+                                      ctypes.c_int, _D, _D, _D, _D, _U8]
+            L.orc_bg_size.restype = None
+            L.orc_bg_size.argtypes = [_P, _BP, _BG, _U8]
+            L.orc_bg_split.restype = ctypes.c_int
+            L.orc_bg_split.argtypes = [_P, _BG, _LL]
+            L.orc_bg_hsmooth.restype = None
+            L.orc_bg_hsmooth.argtypes = [_P, _BP, _BG]
+            L.orc_bg_shift.restype = None
+            L.orc_bg_shift.argtypes = [_P, _BG]
+            L.orc_bg_iteration.restype = ctypes.c_int
+            L.orc_bg_iteration.argtypes = [_P, _BP, _BG, _LL, ctypes.c_int,
+                                           _D, _D, _D, ctypes.c_int, _D, _D,
+                                           _D, _D,
+                                           ctypes.POINTER(_BgStats)]
             _lib = L
     return _lib
 
@@ -467,3 +511,159 @@ def wall_bc(P, st, nw):
     s = _cstate(st)
     lib().orc_wall_bc(ctypes.byref(P), ctypes.byref(s), *[_d(a) for a in out])
     return {"p": out[0][:nw], "ugx": out[1][:nw], "ugy": out[2][:nw]}
+
+
+# ---------------------------------------------------------- background --
+BG_FIELDS = ("x", "y", "h", "m", "ds")
+
+
+def bg_params(ds_min, ds_max, Cr=1.08, Nr=48.0, smooth_iters=3, vort_k=0.0):
+    """Background construction parameters (section 3.3; N_r = 48 and three
+    smoothing repetitions are the paper's)."""
+    B = BgParams()
+    B.ds_min, B.ds_max, B.Cr, B.Nr = float(ds_min), float(ds_max), float(Cr), \
+        float(Nr)
+    B.smooth_iters, B.vort_k = int(smooth_iters), float(vort_k)
+    return B
+
+
+def make_bgset(fields: dict, cap: int | None = None) -> dict:
+    """Background set arrays (x, y, h, m, ds, id) with capacity ``cap``."""
+    n = len(fields["x"])
+    cap = max(n, cap or n, 1)
+    b = {"n": n, "cap": cap}
+    for k in BG_FIELDS:
+        a = np.zeros(cap)
+        a[:n] = fields[k]
+        b[k] = a
+    ida = np.zeros(cap, np.int64)
+    ida[:n] = fields.get("id", np.arange(n))
+    b["id"] = ida
+    return b
+
+
+def _cbg(b):
+    s = _BgSet()
+    s.n, s.cap = b["n"], b["cap"]
+    for k in BG_FIELDS:
+        setattr(s, k, _d(b[k]))
+    s.id = b["id"].ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+    return s
+
+
+def _sync_bg(b, s):
+    b["n"] = s.n
+
+
+def neighbors_classes(P, x, y, h):
+    """Same sets as ``neighbors`` by the h-class bucket search."""
+    x, y, h = _f64(x), _f64(y), _f64(h)
+    n = len(x)
+    off = np.zeros(n + 1, np.int32)
+    cap = max(64, 48 * n)
+    while True:
+        nbr = np.zeros(cap, np.int32)
+        tot = lib().orc_neighbors_classes(ctypes.byref(P), n, _d(x), _d(y),
+                                          _d(h), _i(off), _i(nbr), cap)
+        if tot <= cap:
+            return off, nbr[:tot].copy()
+        cap = int(tot)
+
+
+def bg_iterations(B) -> int:
+    return int(lib().orc_bg_iterations(ctypes.byref(B)))
+
+
+def vorticity(P, st):
+    """omega_i of the fluid state (gradient operator of the Taylor
+    correction)."""
+    n = st["n"]
+    out = np.zeros(max(n, 1))
+    s = _cstate(st)
+    lib().orc_vorticity(ctypes.byref(P), ctypes.byref(s), _d(out))
+    return out[:n]
+
+
+def _solid_fluid(solid, fluid):
+    z = np.zeros(1)
+    if solid is None or len(solid["x"]) == 0:
+        sw = (0, z, z, z)
+    else:
+        sw = (len(solid["x"]),) + tuple(_f64(solid[k]) for k in ("x", "y", "h"))
+    if fluid is None or len(fluid["x"]) == 0:
+        fl = (0, z, z, z, None)
+    else:
+        fl = (len(fluid["x"]),) + tuple(_f64(fluid[k]) for k in ("x", "y", "h")) \
+            + (_f64(fluid["phi"]),)
+    return sw, fl
+
+
+def bg_mark(P, B, b, solid, fluid=None):
+    """Step 1 in place; returns the mark array (0, 1 solid, 2 vorticity).
+    ``fluid``: dict x, y, h, phi (= |omega|) or None."""
+    (nw, wx, wy, wh), (nf, fx, fy, fh, phi) = _solid_fluid(solid, fluid)
+    mark = np.zeros(max(b["n"], 1), np.uint8)
+    s = _cbg(b)
+    lib().orc_bg_mark(ctypes.byref(P), ctypes.byref(B), ctypes.byref(s), nw,
+                      _d(wx), _d(wy), _d(wh), nf, _d(fx), _d(fy), _d(fh),
+                      _d(phi) if phi is not None else None,
+                      mark.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return mark[:b["n"]]
+
+
+def bg_size(P, B, b, mark):
+    mark = np.ascontiguousarray(mark, np.uint8)
+    s = _cbg(b)
+    lib().orc_bg_size(ctypes.byref(P), ctypes.byref(B), ctypes.byref(s),
+                      mark.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+
+
+def bg_split(P, b, next_id):
+    s = _cbg(b)
+    nid = ctypes.c_longlong(int(next_id))
+    r = lib().orc_bg_split(ctypes.byref(P), ctypes.byref(s), ctypes.byref(nid))
+    _sync_bg(b, s)
+    return r, nid.value
+
+
+def bg_hsmooth(P, B, b):
+    s = _cbg(b)
+    lib().orc_bg_hsmooth(ctypes.byref(P), ctypes.byref(B), ctypes.byref(s))
+
+
+def bg_shift(P, b):
+    s = _cbg(b)
+    lib().orc_bg_shift(ctypes.byref(P), ctypes.byref(s))
+
+
+def bg_iteration(P, B, b, next_id, solid, fluid=None):
+    """One construction iteration in place; returns (status, stats,
+    next_id)."""
+    (nw, wx, wy, wh), (nf, fx, fy, fh, phi) = _solid_fluid(solid, fluid)
+    s = _cbg(b)
+    nid = ctypes.c_longlong(int(next_id))
+    z = _BgStats()
+    r = lib().orc_bg_iteration(ctypes.byref(P), ctypes.byref(B), ctypes.byref(s),
+                               ctypes.byref(nid), nw, _d(wx), _d(wy), _d(wh),
+                               nf, _d(fx), _d(fy), _d(fh),
+                               _d(phi) if phi is not None else None,
+                               ctypes.byref(z))
+    _sync_bg(b, s)
+    return r, {k: getattr(z, k) for k, _ in _BgStats._fields_}, nid.value
+
+
+def bg_build(P, B, b, solid, iterations=None, next_id=None, fluid=None):
+    """The whole construction: ``iterations`` (default 3 ceil(log(ds_max /
+    ds_min) / log Cr)) iterations in place; returns (status, list of
+    per-iteration stats, next_id)."""
+    if iterations is None:
+        iterations = bg_iterations(B)
+    if next_id is None:
+        next_id = int(b["id"][:b["n"]].max()) + 1 if b["n"] else 0
+    stats = []
+    for _ in range(iterations):
+        r, z, next_id = bg_iteration(P, B, b, next_id, solid, fluid)
+        stats.append(z)
+        if r != 0:
+            return r, stats, next_id
+    return 0, stats, next_id

@@ -1234,3 +1234,418 @@ int orc_adapt(const orc_params *P, orc_state *s, int nb, const double *bx,
     if (st) *st = z;
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Background particles, section 3.3.
+ *
+ * The background set defines the resolution field: each background
+ * particle carries a size ds (its m_ref = rho0 ds^2), a mass m, a smoothing
+ * length h and a persistent id.  One iteration of the construction:
+ *   1. boundary marking: a background particle with a solid particle in
+ *      range (r < 3 max(h_b, h_s)) takes ds = ds_min; with solution
+ *      adaptivity also one whose phi (max |omega| over the fluid particles
+ *      in range) exceeds vort_k max|omega|;
+ *   2. size rule for the others over their background neighbours j != i
+ *      (sizes after step 1): with lo, hi, g the least, largest and
+ *      geometric-mean size, ds = Cr lo if hi / lo < Cr^3, else g; kept in
+ *      [ds_min, ds_max]; no neighbour leaves ds unchanged.  Every particle
+ *      reads the sizes of the same (previous) sweep;
+ *   3. split of particles with m > 1.05 rho0 ds^2 into seven children as
+ *      for the fluid (section 3.1), children copy ds;
+ *   4. smooth_iters times: h-smoothing (Eq. h-smoothing, N_i and the sum
+ *      of h_j over N(i) including i) and one shifting step (Eqs.
+ *      shift-deltar, shift-limit with volumes m_j / rho0), both over the
+ *      background set alone.
+ * The whole construction repeats the iteration 3 ceil(log(ds_max/ds_min) /
+ * log Cr) times (section 3.3).
+ * ---------------------------------------------------------------------- */
+
+/* Variable-h neighbour search for sets whose h spans a wide range: the
+ * particles are grouped into classes of h (h / h_min in [2^k, 2^(k+1))),
+ * each class bucketed with side >= 3 h_max of the class, and particle i
+ * scans, per class, the buckets within 3 max(h_i, h_max of the class).
+ * Same predicate and ascending order as orc_neighbors_brute. */
+long long orc_neighbors_classes(const orc_params *P, int n, const double *x,
+                                const double *y, const double *h, int *off,
+                                int *nbr, long long cap) {
+    if (n <= 0) {
+        off[0] = 0;
+        return 0;
+    }
+    double hmin = DBL_MAX;
+    for (int i = 0; i < n; ++i)
+        if (h[i] < hmin) hmin = h[i];
+    enum { MAXC = 24 };
+    int *cls = (int *)malloc((size_t)n * sizeof(int));
+    int ncls = 0;
+    for (int i = 0; i < n; ++i) {
+        int e;
+        frexp(h[i] / hmin, &e);   /* h/hmin in [2^(e-1), 2^e) */
+        int k = e - 1;
+        if (k < 0) k = 0;
+        if (k > MAXC - 1) k = MAXC - 1;
+        cls[i] = k;
+        if (k + 1 > ncls) ncls = k + 1;
+    }
+    double chmax[MAXC];
+    int nc[MAXC][2];
+    double w[MAXC][2];
+    int *head[MAXC];
+    for (int k = 0; k < ncls; ++k) chmax[k] = 0.0;
+    for (int i = 0; i < n; ++i)
+        if (h[i] > chmax[cls[i]]) chmax[cls[i]] = h[i];
+    int *next = (int *)malloc((size_t)n * sizeof(int));
+    int *bx = (int *)malloc((size_t)n * sizeof(int));
+    int *by = (int *)malloc((size_t)n * sizeof(int));
+    for (int k = 0; k < ncls; ++k) {
+        head[k] = NULL;
+        if (chmax[k] <= 0.0) continue;
+        double side = 3.0 * chmax[k];
+        for (int a = 0; a < 2; ++a) {
+            double L = P->hi[a] - P->lo[a];
+            if (P->periodic[a]) {
+                nc[k][a] = (int)floor(L / side);
+                if (nc[k][a] < 1) nc[k][a] = 1;
+                w[k][a] = L / nc[k][a];
+            } else {
+                nc[k][a] = (int)ceil(L / side);
+                if (nc[k][a] < 1) nc[k][a] = 1;
+                w[k][a] = side;
+            }
+        }
+        long long ncell = (long long)nc[k][0] * nc[k][1];
+        head[k] = (int *)malloc((size_t)ncell * sizeof(int));
+        for (long long c = 0; c < ncell; ++c) head[k][c] = -1;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        int k = cls[i];
+        int ix = (int)floor((x[i] - P->lo[0]) / w[k][0]);
+        int iy = (int)floor((y[i] - P->lo[1]) / w[k][1]);
+        if (ix < 0) ix = 0;
+        if (ix > nc[k][0] - 1) ix = nc[k][0] - 1;
+        if (iy < 0) iy = 0;
+        if (iy > nc[k][1] - 1) iy = nc[k][1] - 1;
+        bx[i] = ix;
+        by[i] = iy;
+        long long c = (long long)iy * nc[k][0] + ix;
+        next[i] = head[k][c];
+        head[k][c] = i;
+    }
+    int *cnt = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            long long tot = 0;
+            for (int i = 0; i < n; ++i) {
+                off[i] = (int)tot;
+                tot += cnt[i];
+            }
+            off[n] = (int)tot;
+            if (tot > cap) break;
+        }
+#pragma omp parallel for schedule(dynamic, 32)
+        for (int i = 0; i < n; ++i) {
+            int kbase = (pass == 1) ? off[i] : 0;
+            int c = 0;
+            for (int k = 0; k < ncls; ++k) {
+                if (!head[k]) continue;
+                double R = 3.0 * (h[i] > chmax[k] ? h[i] : chmax[k]);
+                /* bucket of i in class k's grid */
+                int ix = (int)floor((x[i] - P->lo[0]) / w[k][0]);
+                int iy = (int)floor((y[i] - P->lo[1]) / w[k][1]);
+                int sx = (int)ceil(R / w[k][0]) + 1, sy = (int)ceil(R / w[k][1]) + 1;
+                int x0 = ix - sx, x1 = ix + sx, y0 = iy - sy, y1 = iy + sy;
+                if (P->periodic[0] && x1 - x0 + 1 >= nc[k][0]) {
+                    x0 = 0;
+                    x1 = nc[k][0] - 1;
+                }
+                if (P->periodic[1] && y1 - y0 + 1 >= nc[k][1]) {
+                    y0 = 0;
+                    y1 = nc[k][1] - 1;
+                }
+                for (int b = y0; b <= y1; ++b) {
+                    int bb = b;
+                    if (P->periodic[1]) bb = ((b % nc[k][1]) + nc[k][1]) % nc[k][1];
+                    else if (b < 0 || b >= nc[k][1]) continue;
+                    for (int a = x0; a <= x1; ++a) {
+                        int aa = a;
+                        if (P->periodic[0]) aa = ((a % nc[k][0]) + nc[k][0]) % nc[k][0];
+                        else if (a < 0 || a >= nc[k][0]) continue;
+                        for (int j = head[k][(long long)bb * nc[k][0] + aa]; j >= 0;
+                             j = next[j])
+                            if (orc_is_neighbor(P, x[i], y[i], h[i], x[j], y[j], h[j])) {
+                                if (pass == 1) nbr[kbase + c] = j;
+                                ++c;
+                            }
+                    }
+                }
+            }
+            if (pass == 0)
+                cnt[i] = c;
+            else
+                qsort(nbr + kbase, (size_t)c, sizeof(int), cmp_int);
+        }
+    }
+    long long tot = off[n];
+    for (int k = 0; k < ncls; ++k) free(head[k]);
+    free(cnt); free(next); free(bx); free(by); free(cls);
+    return tot;
+}
+
+static int *g_boff = NULL, *g_bnbr = NULL;
+static long long g_bcap = 0;
+static int g_boffn = 0;
+
+static void bg_neighbors(const orc_params *P, const orc_bgset *b) {
+    int n = b->n;
+    if (g_boffn < n + 1) {
+        free(g_boff);
+        g_boff = (int *)malloc((size_t)(n + 1) * sizeof(int));
+        g_boffn = n + 1;
+    }
+    for (;;) {
+        long long tot = orc_neighbors_classes(P, n, b->x, b->y, b->h, g_boff,
+                                              g_bnbr, g_bcap);
+        if (tot <= g_bcap) return;
+        free(g_bnbr);
+        g_bcap = tot + tot / 4 + 64;
+        g_bnbr = (int *)malloc((size_t)g_bcap * sizeof(int));
+    }
+}
+
+int orc_bg_iterations(const orc_bg_params *B) {
+    return 3 * (int)ceil(log(B->ds_max / B->ds_min) / log(B->Cr));
+}
+
+/* Vorticity of the fluid, omega = dv/dx - du/dy, with the gradient operator
+ * of the Taylor correction: omega_i = sum_{j != i} V_j ((v_j - v_i) dW/dx -
+ * (u_j - u_i) dW/dy), grad W = grad_i W(r_ij, h_i), V_j = m_j / rho_j (the
+ * paper names vorticity as its adaptivity measure without an operator). */
+void orc_vorticity(const orc_params *P, const orc_state *s, double *omega) {
+    int n = s->n;
+    neighbors_auto(P, n, s->x, s->y, s->h);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        double w = 0.0;
+        for (int k = g_off[i]; k < g_off[i + 1]; ++k) {
+            int j = g_nbr[k];
+            if (j == i) continue;
+            double dx, dy;
+            separation(P, s->x[i], s->y[i], s->x[j], s->y[j], &dx, &dy);
+            double r = sqrt(dx * dx + dy * dy);
+            if (!(r > 0.0)) continue;
+            double g = orc_dWdr(r, s->h[i]) / r;
+            double Vj = s->m[j] / s->rho[j];
+            w += Vj * ((s->v[j] - s->v[i]) * (g * dx) - (s->u[j] - s->u[i]) * (g * dy));
+        }
+        omega[i] = w;
+    }
+}
+
+/* Step 1.  mark[b] = 1: a solid particle in range; 2: otherwise phi_b >
+ * vort_k max|omega| (when vort_k > 0 and phi is given: phi_f = |omega_f| of
+ * fluid particle f, phi_b the largest phi_f over fluid particles in range);
+ * 0: neither.  Marked particles take ds = ds_min.  Returns the marked count. */
+int orc_bg_mark(const orc_params *P, const orc_bg_params *B, orc_bgset *b,
+                int nw, const double *wx, const double *wy, const double *wh,
+                int nf, const double *fx, const double *fy, const double *fh,
+                const double *phi, unsigned char *mark) {
+    double pmax = 0.0;
+    int use_phi = B->vort_k > 0.0 && nf > 0 && phi;
+    if (use_phi)
+        for (int f = 0; f < nf; ++f)
+            if (phi[f] > pmax) pmax = phi[f];
+    double thr = B->vort_k * pmax;
+    int count = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : count)
+    for (int i = 0; i < b->n; ++i) {
+        unsigned char mk = 0;
+        for (int s = 0; s < nw && !mk; ++s)
+            if (orc_is_neighbor(P, b->x[i], b->y[i], b->h[i], wx[s], wy[s], wh[s]))
+                mk = 1;
+        if (!mk && use_phi && pmax > 0.0) {
+            double pb = 0.0;
+            for (int f = 0; f < nf; ++f)
+                if (orc_is_neighbor(P, b->x[i], b->y[i], b->h[i], fx[f], fy[f], fh[f]) &&
+                    phi[f] > pb)
+                    pb = phi[f];
+            if (pb > thr) mk = 2;
+        }
+        mark[i] = mk;
+        if (mk) {
+            b->ds[i] = B->ds_min;
+            ++count;
+        }
+    }
+    return count;
+}
+
+/* Step 2 (Jacobi over the unmarked particles). */
+void orc_bg_size(const orc_params *P, const orc_bg_params *B, orc_bgset *b,
+                 const unsigned char *mark) {
+    int n = b->n;
+    bg_neighbors(P, b);
+    double *nds = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    const double cr3 = B->Cr * B->Cr * B->Cr;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        if (mark[i]) {
+            nds[i] = b->ds[i];
+            continue;
+        }
+        double lo = DBL_MAX, hi = 0.0, slog = 0.0;
+        int c = 0;
+        for (int k = g_boff[i]; k < g_boff[i + 1]; ++k) {
+            int j = g_bnbr[k];
+            if (j == i) continue;
+            double s = b->ds[j];
+            if (s < lo) lo = s;
+            if (s > hi) hi = s;
+            slog += log(s);
+            ++c;
+        }
+        double d = b->ds[i];
+        if (c > 0) d = (hi / lo < cr3) ? B->Cr * lo : exp(slog / c);
+        if (d > B->ds_max) d = B->ds_max;
+        if (d < B->ds_min) d = B->ds_min;
+        nds[i] = d;
+    }
+    memcpy(b->ds, nds, sizeof(double) * (size_t)n);
+    free(nds);
+}
+
+/* Step 3: parents are the particles with m > 1.05 rho0 ds^2; children as
+ * in orc_split (ring at eps h, angles k pi/3, h = alpha h, m / 7, centre
+ * keeps the id, ring ids next_id + 6 r + k with r the parent's rank in id
+ * order) and copy ds.  Returns the parents, or -1 over capacity. */
+int orc_bg_split(const orc_params *P, orc_bgset *b, long long *next_id) {
+    int n = b->n;
+    id_idx *par = (id_idx *)malloc((size_t)(n > 0 ? n : 1) * sizeof(id_idx));
+    int np = 0;
+    for (int i = 0; i < n; ++i) {
+        double mref = P->rho0 * b->ds[i] * b->ds[i];
+        if (b->m[i] > 1.05 * mref) {
+            par[np].id = b->id[i];
+            par[np].idx = i;
+            ++np;
+        }
+    }
+    if ((long long)n + 6LL * np > b->cap) {
+        free(par);
+        return -1;
+    }
+    qsort(par, (size_t)np, sizeof(id_idx), cmp_id_idx);
+    for (int r = 0; r < np; ++r) {
+        int i = par[r].idx;
+        double m = b->m[i], h = b->h[i];
+        double mc = m / 7.0;
+        double rad = P->split_eps * h;
+        for (int k = 0; k < 6; ++k) {
+            int c = n + 6 * r + k;
+            b->x[c] = wrap(P, 0, b->x[i] + rad * HEX_C[k]);
+            b->y[c] = wrap(P, 1, b->y[i] + rad * HEX_S[k]);
+            b->m[c] = mc;
+            b->h[c] = P->split_alpha * h;
+            b->ds[c] = b->ds[i];
+            b->id[c] = *next_id + 6LL * r + k;
+        }
+        b->m[i] = m - 6.0 * mc;
+        b->h[i] = P->split_alpha * h;
+    }
+    b->n = n + 6 * np;
+    *next_id += 6LL * np;
+    free(par);
+    return np;
+}
+
+/* Eq. h-smoothing (Jacobi): h_i <- (1/2) ((h_i/2)(1 + sqrt(N_r / N_i)) +
+ * sum_j h_j / N_i) over the background N(i), i included. */
+void orc_bg_hsmooth(const orc_params *P, const orc_bg_params *B, orc_bgset *b) {
+    int n = b->n;
+    bg_neighbors(P, b);
+    double *nh = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        double sh = 0.0;
+        int c = 0;
+        for (int k = g_boff[i]; k < g_boff[i + 1]; ++k) {
+            sh += b->h[g_bnbr[k]];
+            ++c;
+        }
+        double Ni = (double)c;
+        nh[i] = 0.5 * (0.5 * b->h[i] * (1.0 + sqrt(B->Nr / Ni)) + sh / Ni);
+    }
+    memcpy(b->h, nh, sizeof(double) * (size_t)n);
+    free(nh);
+}
+
+/* One shifting step of the background alone: Eqs. shift-deltar and
+ * shift-limit with the readings of pass A (h_ij = mean h, denominator the
+ * kernel at its inflection point, volume m_j / rho0). */
+void orc_bg_shift(const orc_params *P, orc_bgset *b) {
+    const double w_xi = w_of_q(XI_INFLECTION);
+    int n = b->n;
+    bg_neighbors(P, b);
+    double *d = (double *)malloc((size_t)(n > 0 ? n : 1) * 2 * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        double ax = 0.0, ay = 0.0;
+        for (int k = g_boff[i]; k < g_boff[i + 1]; ++k) {
+            int j = g_bnbr[k];
+            if (j == i) continue;
+            double dx, dy;
+            separation(P, b->x[i], b->y[i], b->x[j], b->y[j], &dx, &dy);
+            double r = sqrt(dx * dx + dy * dy);
+            if (!(r > 0.0)) continue;
+            double hb = 0.5 * (b->h[i] + b->h[j]);
+            double ratio = w_of_q(r / hb) / w_xi;
+            double f = (b->m[j] / P->rho0) * (1.0 + 0.24 * p4(ratio)) *
+                       orc_dWdr(r, hb) / r;
+            ax += f * dx;
+            ay += f * dy;
+        }
+        double c = -0.5 * b->h[i] * b->h[i];
+        double sx = c * ax, sy = c * ay;
+        double mag = sqrt(sx * sx + sy * sy);
+        double lim = 0.25 * b->h[i];
+        if (mag > lim) {
+            double th = lim / mag;
+            sx *= th;
+            sy *= th;
+        }
+        d[2 * i] = sx;
+        d[2 * i + 1] = sy;
+    }
+    for (int i = 0; i < n; ++i) {
+        b->x[i] = wrap(P, 0, b->x[i] + d[2 * i]);
+        b->y[i] = wrap(P, 1, b->y[i] + d[2 * i + 1]);
+    }
+    free(d);
+}
+
+int orc_bg_iteration(const orc_params *P, const orc_bg_params *B,
+                     orc_bgset *b, long long *next_id, int nw,
+                     const double *wx, const double *wy, const double *wh,
+                     int nf, const double *fx, const double *fy,
+                     const double *fh, const double *phi, orc_bg_stats *st) {
+    orc_bg_stats z;
+    memset(&z, 0, sizeof(z));
+    z.n_before = b->n;
+    unsigned char *mark = (unsigned char *)malloc((size_t)(b->n > 0 ? b->n : 1));
+    z.n_marked = orc_bg_mark(P, B, b, nw, wx, wy, wh, nf, fx, fy, fh, phi, mark);
+    for (int i = 0; i < b->n; ++i) z.n_vort += mark[i] == 2;
+    orc_bg_size(P, B, b, mark);
+    free(mark);
+    int ns = orc_bg_split(P, b, next_id);
+    if (ns < 0) {
+        if (st) *st = z;
+        return -1;
+    }
+    z.n_split = ns;
+    for (int r = 0; r < B->smooth_iters; ++r) {
+        orc_bg_hsmooth(P, B, b);
+        orc_bg_shift(P, b);
+    }
+    z.n_after = b->n;
+    if (st) *st = z;
+    return 0;
+}

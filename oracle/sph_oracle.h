@@ -155,6 +155,46 @@ int orc_adapt(const orc_params *P, orc_state *s, int nb, const double *bx,
               const double *by, const double *bh, const double *bds,
               long long *next_id, orc_adapt_stats *st);
 
+/* ---- background particles (section 3.3) ---- */
+typedef struct {
+    int n, cap;
+    double *x, *y, *h, *m, *ds;   /* ds: particle size, m_ref = rho0 ds^2 */
+    long long *id;
+} orc_bgset;
+typedef struct {
+    double ds_min, ds_max;   /* finest and coarsest size */
+    double Cr;               /* size ratio of adjacent layers */
+    double Nr;               /* reference neighbour count, Eq. h-smoothing (48) */
+    int smooth_iters;        /* h-smoothing + shifting repetitions (3) */
+    double vort_k;           /* > 0: vorticity marking threshold factor */
+} orc_bg_params;
+typedef struct {
+    long long n_before, n_marked, n_vort, n_split, n_after;
+} orc_bg_stats;
+/* Same sets as orc_neighbors_brute, for sets whose h spans a wide range. */
+long long orc_neighbors_classes(const orc_params *P, int n, const double *x,
+                                const double *y, const double *h, int *off,
+                                int *nbr, long long cap);
+/* 3 ceil(log(ds_max / ds_min) / log Cr). */
+int orc_bg_iterations(const orc_bg_params *B);
+/* omega_i = sum_{j != i} V_j ((v_j - v_i) dW/dx - (u_j - u_i) dW/dy). */
+void orc_vorticity(const orc_params *P, const orc_state *s, double *omega);
+/* The steps of one construction iteration, and the iteration itself
+ * (phi: |omega| of the nf fluid particles, or NULL). */
+int orc_bg_mark(const orc_params *P, const orc_bg_params *B, orc_bgset *b,
+                int nw, const double *wx, const double *wy, const double *wh,
+                int nf, const double *fx, const double *fy, const double *fh,
+                const double *phi, unsigned char *mark);
+void orc_bg_size(const orc_params *P, const orc_bg_params *B, orc_bgset *b,
+                 const unsigned char *mark);
+int orc_bg_split(const orc_params *P, orc_bgset *b, long long *next_id);
+void orc_bg_hsmooth(const orc_params *P, const orc_bg_params *B, orc_bgset *b);
+void orc_bg_shift(const orc_params *P, orc_bgset *b);
+int orc_bg_iteration(const orc_params *P, const orc_bg_params *B,
+                     orc_bgset *b, long long *next_id, int nw,
+                     const double *wx, const double *wy, const double *wh,
+                     int nf, const double *fx, const double *fy,
+                     const double *fh, const double *phi, orc_bg_stats *st);
 int orc_num_threads(void);
 
 #ifdef __cplusplus
