@@ -79,6 +79,20 @@ typedef struct {
     double cell_c0;          /* level-0 cell side of the neighbour grid;
                                 <= 0: 3*hdx*ds_min if ds_min > 0, else 3*min(h)
                                 of the fluid at load time */
+    /* background construction (section 3.3, sph_background) */
+    double bg_Nr;            /* reference neighbour count N_r of Eq.
+                                h-smoothing: 48 */
+    int bg_smooth_iters;     /* h-smoothing + shifting repetitions per
+                                iteration: 3 */
+    double vort_k;           /* > 0: solution adaptivity, background particles
+                                near fluid with |omega| > vort_k max|omega|
+                                take ds_min (0.05 in the paper's runs);
+                                <= 0 (default): off */
+    int n_bg;                /* > 0: every n_bg-th sph_adapt call first runs
+                                one background iteration; 0 (default): never */
+    long long bg_capacity;   /* maximum background particles during the
+                                construction; <= 0: max(100 x the loaded
+                                count, 2^18) */
 } sph_params;
 
 /* Host arrays of one particle set, n entries each.  Unused members may be
@@ -105,6 +119,13 @@ typedef enum {
     SPH_F_CELLKEY,     /* uint64: level << 58 | morton(ix, iy) */
     SPH_F_NEIGH_OFF,   /* int64[n+1]: CSR offsets of N(i) */
     SPH_F_NEIGH_ID,    /* int64[total]: ids of N(i), any order within a list */
+    SPH_F_OMEGA,       /* vorticity of the fluid at the current positions
+                          (rebuilds first like SPH_F_CELLKEY) */
+    /* The background set (section 3.3), n_bg entries in the library's
+     * order; SPH_F_BG_ID gives each particle's identity (load index, or
+     * assigned by splitting during sph_background). */
+    SPH_F_BG_X, SPH_F_BG_Y, SPH_F_BG_H, SPH_F_BG_M, SPH_F_BG_DS,
+    SPH_F_BG_ID,       /* int64 */
     SPH_F_COUNT
 } sph_field;
 
@@ -132,6 +153,16 @@ typedef struct {
                                  in range (took the nearest one's size) */
 } sph_adapt_stats;
 
+/* Counts of one sph_background call. */
+typedef struct {
+    long long n_before;   /* background particles before */
+    long long n_marked;   /* last iteration: particles set to ds_min */
+    long long n_vort;     /* ... of them by the vorticity criterion */
+    long long n_split;    /* parents split, over all iterations */
+    long long n_after;    /* background particles after */
+    int iterations;       /* iterations run */
+} sph_bg_stats;
+
 typedef struct sph_ctx sph_ctx;
 
 /* Fill *p with the paper's values: alpha_e 1.5, split_alpha 0.9,
@@ -148,9 +179,13 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out);
 
 /* Replace the particle set of the given kind by n particles copied from
  * host arrays.  SPH_FLUID: x, y, m, h required (see sph_particles for
- * defaults).  SPH_BACKGROUND (section 3.3): x, y, h and ds (the particle
- * size; NULL takes ds_max) required, any count; they only set the fluid's
- * m_min/m_max in sph_adapt.
+ * defaults).  SPH_BACKGROUND (section 3.3): x, y, h required; ds (the
+ * particle size; NULL takes ds_max), m (NULL: rho0 ds^2, used only by
+ * sph_background) and id (NULL: 0..n-1) optional, any count; the set only
+ * sets the fluid's m_min/m_max in sph_adapt and is refined by
+ * sph_background.  SPH_WALL (section 2.2): x, y, h, m required, u, v the
+ * prescribed wall velocity (NULL: 0); the walls also serve as the solid of
+ * the background construction.
  * Fluid positions must lie in the box (periodic axes: [lo, hi)).
  * Synchronous with respect to the host buffers (they may be reused on
  * return).  Errors: SPH_EINVAL (NULL required array, n < 0, h or m not
@@ -195,6 +230,31 @@ sph_status sph_step(sph_ctx *ctx, int nsteps, double *t_out);
  * SPH_ECAPACITY (the children would exceed the capacity; nothing is split,
  * m_min/m_max are already refreshed). */
 sph_status sph_adapt(sph_ctx *ctx, sph_adapt_stats *out);
+
+/* Background construction (section 3.3): `iterations` iterations over the
+ * loaded background (iterations <= 0: 3 ceil(log(ds_max / ds_min) /
+ * log Cr), the paper's count for the initial construction), each:
+ *  1. a background particle with a wall particle s in range (r_bs <
+ *     3 max(h_b, h_s)) takes ds_min; with vort_k > 0 and fluid loaded, so
+ *     does one whose largest |omega| over fluid particles in range exceeds
+ *     vort_k max|omega| (omega from the fluid's current state);
+ *  2. every other particle takes, over its background neighbours j != i
+ *     (same range rule, sizes after step 1, all read before any is
+ *     written): Cr min_j ds_j if max_j ds_j / min_j ds_j < Cr^3, else the
+ *     geometric mean of the ds_j; clamped to [ds_min, ds_max]; unchanged
+ *     without neighbours;
+ *  3. particles with m > 1.05 rho0 ds^2 split into seven as in sph_adapt
+ *     (children copy ds; ids continue from the largest background id);
+ *  4. bg_smooth_iters times: Eq. h-smoothing with N_r = bg_Nr over N(i)
+ *     (i included), then one limited shifting step (Eqs. shift-deltar,
+ *     shift-limit, volumes m_j / rho0) of the background alone.
+ * FP64 throughout, both precisions.  The refined set replaces the loaded
+ * background (read it with SPH_F_BG_*).  Synchronises (split counts).
+ * out (may be NULL) receives counts.  Errors: SPH_ESTATE (no background),
+ * SPH_EINVAL (ds_min, ds_max, Cr, bg_Nr not usable: need 0 < ds_min <=
+ * ds_max, Cr > 1, bg_Nr > 0), SPH_ECAPACITY (the background would exceed
+ * bg_capacity; the iterations before that are kept), SPH_ENOMEM. */
+sph_status sph_background(sph_ctx *ctx, int iterations, sph_bg_stats *out);
 
 /* Copy one field of the fluid set to the host buffer dst holding cap
  * elements of the field's type; *n_out (if not NULL) receives the element

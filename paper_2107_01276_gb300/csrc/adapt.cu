@@ -165,6 +165,7 @@ __global__ void k_split_emit(SplitArgs a) {
         f[S_H][c] = hc;
         f[S_MMIN][c] = f[S_MMIN][i];
         f[S_MMAX][c] = f[S_MMAX][i];
+        if (f[S_DS]) f[S_DS][c] = f[S_DS][i];
         a.id[c] = a.next_id + 6ll * r + k;
     }
     f[S_M][i] = __dsub_rn(m, __dmul_rn(6.0, mc));
@@ -272,7 +273,8 @@ __global__ void k_compact(int n, const uint32_t *alive, const uint32_t *pos,
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !alive[i]) return;
     const uint32_t d = pos[i];
-    for (int k = 0; k < NSTATE; ++k) c.dst[k][d] = c.src[k][i];
+    for (int k = 0; k < NSTATE; ++k)
+        if (c.dst[k]) c.dst[k][d] = c.src[k][i];
     c.idst[d] = c.isrc[i];
 }
 

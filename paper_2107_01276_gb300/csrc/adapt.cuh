@@ -7,8 +7,10 @@
 
 namespace sph {
 
-// The FP64 state arrays, in the order the context stores them.
-enum { S_X = 0, S_Y, S_U, S_V, S_P, S_RHO, S_M, S_H, S_MMIN, S_MMAX, NSTATE };
+// The FP64 state arrays, in the order the context stores them.  S_DS (the
+// size of a background particle, section 3.3) exists only in a context
+// that holds the background under construction; elsewhere it is NULL.
+enum { S_X = 0, S_Y, S_U, S_V, S_P, S_RHO, S_M, S_H, S_MMIN, S_MMAX, S_DS, NSTATE };
 
 struct BgArgs {
     int n;                      // fluid particles

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "adapt.cuh"
+#include "background.cuh"
 #include "lists.cuh"
 #include "pair_passes.cuh"
 #include "sph_internal.cuh"
@@ -30,11 +31,15 @@ struct Timer {
 
 }  // namespace
 
-// Fields gathered by a rebuild (index into sph_ctx::f / ::falt).
+// Fields gathered by a rebuild (index into sph_ctx::f / ::falt).  F_DS is
+// allocated only in the context that holds the background under
+// construction (section 3.3); F_X0..F_P0 only travel within a PEC step.
 enum {
-    F_X = 0, F_Y, F_U, F_V, F_P, F_RHO, F_M, F_H, F_MMIN, F_MMAX,
+    F_X = 0, F_Y, F_U, F_V, F_P, F_RHO, F_M, F_H, F_MMIN, F_MMAX, F_DS,
     F_X0, F_Y0, F_U0, F_V0, F_P0, NF
 };
+static_assert((int)F_DS == (int)S_DS && (int)F_X0 == (int)NSTATE,
+              "state field order shared with the adaptation kernels");
 
 // A particle set that does not move between loads (background, walls),
 // kept sorted by its own multi-level cell keys with its own cell table.
@@ -117,7 +122,17 @@ struct sph_ctx {
     int *closest = nullptr;
     double *d_mass = nullptr, *d_mass_part = nullptr;  // [2], [256]
     uint32_t *d_aux = nullptr;                         // [4] adapt counters
-    StaticSet bg;     // background particles (section 3.3); extra: ds
+    StaticSet bg;     // background particles (section 3.3); extra: ds, m
+    // background construction: the background as a particle context of its
+    // own (ds carried in F_DS), created on the first sph_background call
+    sph_ctx *bgc = nullptr;
+    bool bgc_valid = false;   // bgc holds the same set as bg
+    bool has_ds = false;      // this context is such a background context
+    long long bg_next_id = 0; // id the next background split child receives
+    long long adapt_calls = 0;
+    double *omega = nullptr;                 // fluid vorticity
+    unsigned long long *d_wmax = nullptr;    // max |omega| (bits)
+    unsigned long long *d_minmax = nullptr;  // [2] min / max (bits)
     StaticSet wall;   // dummy wall particles (section 2.2); extra: m, u, v
     double *wp = nullptr, *wugx = nullptr, *wugy = nullptr;   // wall BC
 
@@ -277,6 +292,7 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
     memset(&gl, 0, sizeof(gl));
     int last = mid_step ? NF : F_X0;
     for (int k = 0; k < last; ++k) {
+        if (!c->f[k]) continue;
         gl.src[gl.nd] = c->f[k];
         gl.dst[gl.nd] = c->falt[k];
         gl.nd++;
@@ -536,6 +552,14 @@ static void free_ctx(sph_ctx *c) {
                   c->closest, c->d_mass, c->d_mass_part, c->wp, c->wugx,
                   c->wugy, c->d_aux};
     for (void *p : ps) cudaFree(p);
+    cudaFree(c->omega);
+    cudaFree(c->d_wmax);
+    cudaFree(c->d_minmax);
+    if (c->bgc) {
+        free_ctx(c->bgc);
+        delete c->bgc;
+        c->bgc = nullptr;
+    }
     free_set(&c->bg);
     free_set(&c->wall);
     for (auto e : c->tm.pool) cudaEventDestroy(e);
@@ -547,29 +571,32 @@ static void free_ctx(sph_ctx *c) {
 }
 
 // ------------------------------------------------------ static sets --
-// Background (section 3.3) and dummy walls (section 2.2): uploaded once,
-// sorted by their own cell keys, queried by fluid particles.
-static sph_status build_set(sph_ctx *c, StaticSet *S, long long n,
-                            const double *x, const double *y, const double *h,
-                            const double *const *extra, int nex) {
-    double hmin = INFINITY;
-    for (long long i = 0; i < n; ++i) {
-        if (!(h[i] > 0) || !isfinite(h[i]) || !isfinite(x[i]) || !isfinite(y[i]))
-            return fail(c, SPH_EINVAL, "sph_load_particles: h must be positive, positions finite");
-        hmin = std::min(hmin, h[i]);
-    }
-    if (n > (1ll << 30)) return fail(c, SPH_ECAPACITY, "sph_load_particles: set too large");
+// Background (section 3.3) and dummy walls (section 2.2): sorted by their
+// own cell keys, queried by fluid particles.
+//
+// build_set_sorted: tmp holds nf = 3 + nex device arrays of n doubles (x,
+// y, h, extras) and tid the n ids; both are freed here.  hmin: least h.
+static sph_status build_set_sorted(sph_ctx *c, StaticSet *S, long long n,
+                                   double hmin, int nex, double *tmp,
+                                   int64_t *tid) {
+    auto done = [&](sph_status st) {
+        cudaStreamSynchronize(c->s);
+        cudaFree(tmp);
+        cudaFree(tid);
+        return st;
+    };
+    if (n > (1ll << 30)) return done(fail(c, SPH_ECAPACITY, "sph_load_particles: set too large"));
     S->n = 0;
-    if (n == 0) return SPH_OK;
+    if (n == 0) return done(SPH_OK);
     double c0 = 3.0 * hmin;
     double Lmax = std::max(c->dom.L[0], c->dom.L[1]);
     int lmax = 0;
     while (ldexp(c0, lmax) < Lmax) ++lmax;
-    if (lmax >= MAX_LEVELS) return fail(c, SPH_EINVAL, "set spans too many cell levels");
+    if (lmax >= MAX_LEVELS) return done(fail(c, SPH_EINVAL, "set spans too many cell levels"));
     Level lev[MAX_LEVELS];
     compute_levels(c->dom, c0, lev);
     long long nmax = std::max(lev[0].n[0], lev[0].n[1]);
-    if (nmax >= (1ll << MAX_MORTON_BITS)) return fail(c, SPH_EINVAL, "set grid too fine");
+    if (nmax >= (1ll << MAX_MORTON_BITS)) return done(fail(c, SPH_EINVAL, "set grid too fine"));
     if (n > S->cap || nex != S->nex) {
         free_set(S);
         size_t N = (size_t)n;
@@ -590,27 +617,12 @@ static sph_status build_set(sph_ctx *c, StaticSet *S, long long n,
         if (!ok) {
             cudaGetLastError();
             free_set(S);
-            return fail(c, SPH_ENOMEM, "particle set allocation failed");
+            return done(fail(c, SPH_ENOMEM, "particle set allocation failed"));
         }
         S->cap = (int)n;
         S->nex = nex;
     }
     const int nf = 3 + nex;
-    double *tmp = nullptr;
-    int64_t *tid = nullptr;
-    if (!dalloc(&tmp, (size_t)nf * n) || !dalloc(&tid, (size_t)n)) {
-        cudaGetLastError();
-        cudaFree(tmp);
-        return fail(c, SPH_ENOMEM, "particle set staging allocation failed");
-    }
-    std::vector<int64_t> ids((size_t)n);
-    for (long long i = 0; i < n; ++i) ids[i] = i;
-    const double *srcs[6] = {x, y, h, nullptr, nullptr, nullptr};
-    for (int k = 0; k < nex; ++k) srcs[3 + k] = extra[k];
-    for (int k = 0; k < nf; ++k)
-        cudaMemcpyAsync(tmp + (size_t)k * n, srcs[k], sizeof(double) * n,
-                        cudaMemcpyHostToDevice, c->s);
-    cudaMemcpyAsync(tid, ids.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
     S->c0 = c0;
     S->lmax = lmax;
     memcpy(S->lev, lev, sizeof(lev));
@@ -639,13 +651,82 @@ static sph_status build_set(sph_ctx *c, StaticSet *S, long long n,
     build_cell_table(c->s, (int)n, S->key, S->tkey, S->tstart, S->tend, S->tmask,
                      &c->launches);
     c->launches += 2;
-    cudaError_t e = cudaStreamSynchronize(c->s);
-    cudaFree(tmp);
-    cudaFree(tid);
-    if (e != cudaSuccess) return cuda_check(c, "build_set");
+    done(SPH_OK);
     S->n = (int)n;
     S->pk_version = -1;
     return cuda_check(c, "build_set");
+}
+
+// From host arrays (validated here); ids NULL: 0..n-1.
+static sph_status build_set(sph_ctx *c, StaticSet *S, long long n,
+                            const double *x, const double *y, const double *h,
+                            const double *const *extra, int nex,
+                            const int64_t *ids) {
+    double hmin = INFINITY;
+    for (long long i = 0; i < n; ++i) {
+        if (!(h[i] > 0) || !isfinite(h[i]) || !isfinite(x[i]) || !isfinite(y[i]))
+            return fail(c, SPH_EINVAL, "sph_load_particles: h must be positive, positions finite");
+        hmin = std::min(hmin, h[i]);
+    }
+    if (n == 0) {
+        S->n = 0;
+        return SPH_OK;
+    }
+    const int nf = 3 + nex;
+    double *tmp = nullptr;
+    int64_t *tid = nullptr;
+    if (!dalloc(&tmp, (size_t)nf * n) || !dalloc(&tid, (size_t)n)) {
+        cudaGetLastError();
+        cudaFree(tmp);
+        return fail(c, SPH_ENOMEM, "particle set staging allocation failed");
+    }
+    std::vector<int64_t> idv;
+    if (!ids) {
+        idv.resize((size_t)n);
+        for (long long i = 0; i < n; ++i) idv[i] = i;
+        ids = idv.data();
+    }
+    const double *srcs[6] = {x, y, h, nullptr, nullptr, nullptr};
+    for (int k = 0; k < nex; ++k) srcs[3 + k] = extra[k];
+    for (int k = 0; k < nf; ++k)
+        cudaMemcpyAsync(tmp + (size_t)k * n, srcs[k], sizeof(double) * n,
+                        cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(tid, ids, sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
+    return build_set_sorted(c, S, n, hmin, nex, tmp, tid);
+}
+
+// From device arrays of another context (x, y, h, extras, ids).
+static sph_status build_set_device(sph_ctx *c, StaticSet *S, long long n,
+                                   const double *const *src, int nex,
+                                   const int64_t *ids) {
+    if (n == 0) {
+        S->n = 0;
+        return SPH_OK;
+    }
+    const int nf = 3 + nex;
+    double *tmp = nullptr;
+    int64_t *tid = nullptr;
+    if (!dalloc(&tmp, (size_t)nf * n) || !dalloc(&tid, (size_t)n)) {
+        cudaGetLastError();
+        cudaFree(tmp);
+        return fail(c, SPH_ENOMEM, "particle set staging allocation failed");
+    }
+    for (int k = 0; k < nf; ++k)
+        cudaMemcpyAsync(tmp + (size_t)k * n, src[k], sizeof(double) * n,
+                        cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(tid, ids, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, c->s);
+    launch_minmax_pos(c->s, (int)n, tmp + 2 * n, c->d_minmax);
+    c->launches += 1;
+    unsigned long long mm[2] = {0, 0};
+    cudaMemcpyAsync(mm, c->d_minmax, sizeof(mm), cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) {
+        cudaFree(tmp);
+        cudaFree(tid);
+        return cuda_check(c, "build_set_device");
+    }
+    double hmin;
+    memcpy(&hmin, &mm[0], sizeof(double));
+    return build_set_sorted(c, S, n, hmin, nex, tmp, tid);
 }
 
 // Anchor data of a static set for the context's current anchor lattice.
@@ -703,9 +784,26 @@ static sph_status load_background(sph_ctx *c, long long n, const sph_particles *
     for (long long i = 0; i < n; ++i)
         if (!(ds[i] > 0) || !isfinite(ds[i]))
             return fail(c, SPH_EINVAL, "sph_load_particles: background ds must be positive");
-    const double *ex[1] = {ds};
+    std::vector<double> mv;
+    const double *m = n > 0 ? src->m : nullptr;
+    if (n > 0 && !m) {
+        mv.resize((size_t)n);
+        for (long long i = 0; i < n; ++i) mv[i] = c->prm.rho0 * ds[i] * ds[i];
+        m = mv.data();
+    }
+    for (long long i = 0; i < n; ++i)
+        if (!(m[i] > 0) || !isfinite(m[i]))
+            return fail(c, SPH_EINVAL, "sph_load_particles: background m must be positive");
+    const double *ex[2] = {ds, m};
+    c->bgc_valid = false;
+    c->bg_next_id = n;
+    if (n > 0 && src->id) {
+        long long mx = -1;
+        for (long long i = 0; i < n; ++i) mx = std::max<long long>(mx, src->id[i]);
+        c->bg_next_id = mx + 1;
+    }
     return build_set(c, &c->bg, n, n ? src->x : nullptr, n ? src->y : nullptr,
-                     n ? src->h : nullptr, ex, 1);
+                     n ? src->h : nullptr, ex, 2, n ? src->id : nullptr);
 }
 
 static sph_status load_walls(sph_ctx *c, long long n, const sph_particles *src) {
@@ -718,7 +816,8 @@ static sph_status load_walls(sph_ctx *c, long long n, const sph_particles *src) 
     const double *ex[3] = {n ? src->m : nullptr, (n && src->u) ? src->u : zero.data(),
                            (n && src->v) ? src->v : zero.data()};
     sph_status st = build_set(c, &c->wall, n, n ? src->x : nullptr,
-                              n ? src->y : nullptr, n ? src->h : nullptr, ex, 3);
+                              n ? src->y : nullptr, n ? src->h : nullptr, ex, 3,
+                              nullptr);
     if (st != SPH_OK) return st;
     cudaFree(c->wp);
     cudaFree(c->wugx);
@@ -740,56 +839,14 @@ static uint32_t read_u32(sph_ctx *c, const uint32_t *dev, sph_status *st) {
     return v;
 }
 
-// ================================================================ C ABI ==
-extern "C" {
-
-void sph_default_params(sph_params *p) {
-    if (!p) return;
-    memset(p, 0, sizeof(*p));
-    p->dim = 2;
-    p->lo[0] = p->lo[1] = 0.0;
-    p->hi[0] = p->hi[1] = 1.0;
-    p->rho0 = 1.0;
-    p->cs = 10.0;
-    p->nu = 0.0;
-    p->U_ref = 1.0;
-    p->hdx = 1.0;
-    p->alpha_e = 1.5;
-    p->split_alpha = 0.9;
-    p->split_eps = 0.4;
-    p->Cr = 1.08;
-    p->merge_iters = 3;
-    p->shift_iters = 3;
-    p->precision = SPH_FP64;
-    p->capacity = 0;
-    p->pavg_mode = 0;
-    p->edac_diff_denominator = 1;
-    p->edac_rho_factor = 1;
-    p->cell_c0 = 0.0;
-}
-
-sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
-    if (out) *out = nullptr;
-    if (!p || !out) {
-        g_create_error = "sph_create: NULL argument";
-        return SPH_EINVAL;
-    }
-    std::string why;
-    if (p->dim != 2) why = "dim must be 2";
-    else if (!(p->hi[0] > p->lo[0]) || !(p->hi[1] > p->lo[1])) why = "empty domain box";
-    else if (p->capacity <= 0 || p->capacity > (1ll << 30)) why = "capacity must be in 1..2^30";
-    else if (!(p->rho0 > 0) || !(p->cs > 0) || !(p->hdx > 0)) why = "rho0, cs, hdx must be positive";
-    else if (!(p->nu >= 0)) why = "nu must be >= 0";
-    else if (!(p->U_ref >= 0)) why = "U_ref must be >= 0";
-    else if (p->precision != SPH_FP64 && p->precision != SPH_MIXED) why = "bad precision";
-    else if (p->pavg_mode < 0 || p->pavg_mode > 1) why = "bad pavg_mode";
-    if (!why.empty()) {
-        g_create_error = "sph_create: " + why;
-        return SPH_EINVAL;
-    }
+// Allocate a context for p->capacity particles (parameters already
+// validated).  has_ds: the context holds a background under construction.
+static sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
+                          sph_ctx **out, std::string *why) {
     sph_ctx *c = new sph_ctx();
     c->prm = *p;
-    c->s = (cudaStream_t)stream;
+    c->has_ds = has_ds;
+    c->s = stream;
     c->cap = p->capacity;
     for (int a = 0; a < 2; ++a) {
         c->dom.lo[a] = p->lo[a];
@@ -800,7 +857,9 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
     }
     const size_t N = (size_t)c->cap;
     bool ok = true;
-    for (int k = 0; k < NF; ++k) ok = ok && dalloc(&c->f[k], N) && dalloc(&c->falt[k], N);
+    for (int k = 0; k < NF; ++k)
+        if (k != F_DS || has_ds) ok = ok && dalloc(&c->f[k], N) && dalloc(&c->falt[k], N);
+    ok = ok && dalloc(&c->omega, N) && dalloc(&c->d_wmax, 1) && dalloc(&c->d_minmax, 2);
     ok = ok && dalloc(&c->id, N) && dalloc(&c->id_alt, N);
     double **rs[] = {(double **)&c->rhoR, (double **)&c->beta, (double **)&c->pavg,
                      (double **)&c->drx, (double **)&c->dry, (double **)&c->V,
@@ -839,7 +898,7 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
         cudaGetLastError();
         free_ctx(c);
         delete c;
-        g_create_error = "sph_create: device allocation failed";
+        *why = "device allocation failed";
         return SPH_ENOMEM;
     }
     cudaMemsetAsync(c->d_t, 0, sizeof(double), c->s);
@@ -848,39 +907,17 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
     if (cudaGetLastError() != cudaSuccess) {
         free_ctx(c);
         delete c;
-        g_create_error = "sph_create: CUDA error";
+        *why = "CUDA error";
         return SPH_ECUDA;
     }
     *out = c;
     return SPH_OK;
 }
 
-sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
-                              const sph_particles *src) {
-    if (!c) return SPH_EINVAL;
-    c->err.clear();
-    if (n < 0 || (n > 0 && !src)) return fail(c, SPH_EINVAL, "sph_load_particles: bad n or src");
-    if (kind == SPH_BACKGROUND) return load_background(c, n, src);
-    if (kind == SPH_WALL) return load_walls(c, n, src);
-    if (kind != SPH_FLUID)
-        return fail(c, SPH_EINVAL, "sph_load_particles: unknown kind");
-    if (n > c->cap) return fail(c, SPH_ECAPACITY, "sph_load_particles: n exceeds capacity");
-    if (n > 0 && (!src->x || !src->y || !src->m || !src->h))
-        return fail(c, SPH_EINVAL, "sph_load_particles: x, y, m, h are required");
-    double hmin = INFINITY;
-    for (long long i = 0; i < n; ++i) {
-        double h = src->h[i], m = src->m[i];
-        if (!(h > 0) || !isfinite(h) || !(m > 0) || !isfinite(m))
-            return fail(c, SPH_EINVAL, "sph_load_particles: h and m must be positive and finite");
-        hmin = std::min(hmin, h);
-        for (int a = 0; a < 2; ++a) {
-            double q = a == 0 ? src->x[i] : src->y[i];
-            bool in = c->dom.periodic[a] ? (q >= c->dom.lo[a] && q < c->dom.hi[a])
-                                         : (q >= c->dom.lo[a] && q <= c->dom.hi[a]);
-            if (!in || !isfinite(q))
-                return fail(c, SPH_EINVAL, "sph_load_particles: position outside the box");
-        }
-    }
+// Level-0 cell side, cell levels and the FP32 anchor lattice for a fluid
+// set whose smoothing lengths span [hmin, hmax] (n may be 0).
+static sph_status setup_fluid_grid(sph_ctx *c, long long n, double hmin,
+                                   double hmax) {
     // level-0 cell side
     double c0 = c->prm.cell_c0;
     if (!(c0 > 0)) c0 = c->prm.ds_min > 0 ? 3.0 * c->prm.hdx * c->prm.ds_min : 3.0 * hmin;
@@ -895,8 +932,6 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
     long long nmax = std::max(lev[0].n[0], lev[0].n[1]);
     if (nmax >= (1ll << MAX_MORTON_BITS))
         return fail(c, SPH_EINVAL, "sph_load_particles: level-0 grid too fine for the domain");
-    double hmax = 0.0;
-    for (long long i = 0; i < n; ++i) hmax = std::max(hmax, src->h[i]);
     for (int a = 0; a < 2; ++a)
         if (c->dom.periodic[a] && !(3.0 * hmax < 0.5 * c->dom.L[a]))
             return fail(c, SPH_EINVAL,
@@ -929,6 +964,312 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
     memcpy(c->lev, lev, sizeof(lev));
     c->mbits = std::max(1, bits_for(nmax - 1));
     c->lbits = bits_for(lmax);
+    return SPH_OK;
+}
+
+// One split pass (section 3.1): flag m > m_max, scan, rank the parents by
+// id, emit the children.  One synchronisation (the parent count).
+static sph_status split_pass(sph_ctx *c, uint32_t *count_out) {
+    sph_status st = SPH_OK;
+    *count_out = 0;
+    launch_split_flag(c->s, c->n, c->f[F_M], c->f[F_MMAX], c->tmp_a);
+    exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
+    c->launches += 1;
+    uint32_t count = read_u32(c, c->d_total, &st);
+    if (st != SPH_OK) return st;
+    if ((long long)c->n + 6ll * count > c->cap)
+        return fail(c, SPH_ECAPACITY, c->has_ds
+                        ? "sph_background: split children exceed bg_capacity"
+                        : "sph_adapt: split children exceed the capacity");
+    if (count > 0) {
+        launch_split_collect(c->s, c->n, c->tmp_a, c->tmp_b, c->id, c->skey, c->perm);
+        radix_sort(c->s, (int)count, std::max(1, bits_for(c->next_id)), c->skey,
+                   c->perm, c->sc, &c->launches);
+        SplitArgs a;
+        a.n = c->n;
+        a.count = (int)count;
+        a.d = c->dom;
+        for (int k = 0; k < NSTATE; ++k) a.f[k] = c->f[k];
+        a.id = c->id;
+        a.parent = c->perm;
+        a.next_id = c->next_id;
+        a.alpha = c->prm.split_alpha;
+        a.eps = c->prm.split_eps;
+        launch_split_emit(c->s, a);
+        c->launches += 2;
+        c->n += 6 * (int)count;
+        c->next_id += 6ll * count;
+        c->grid_valid = false;
+    }
+    *count_out = count;
+    return SPH_OK;
+}
+
+// Arguments of the shift and h-update kernels over the current lists.
+static ShiftArgs shift_args(sph_ctx *c) {
+    ShiftArgs sa;
+    sa.n = c->n;
+    sa.d = c->dom;
+    for (int k = 0; k < NSTATE; ++k) sa.f[k] = c->f[k];
+    sa.off = c->off;
+    sa.list = c->list;
+    sa.rho0 = c->prm.rho0;
+    sa.hdx = c->prm.hdx;
+    sa.rho = c->rhoR;
+    sa.drx = c->drx;
+    sa.dry = c->dry;
+    sa.du = c->dudt;
+    sa.dv = c->dvdt;
+    sa.dp = c->dpdt;
+    sa.hnew = c->V;
+    sa.w = wall_view(c);
+    sa.an = c->an;
+    sa.pk = c->pk;
+    sa.mf = c->mf;
+    sa.uf = c->uf;
+    sa.vf = c->vf;
+    sa.pf = c->pf;
+    return sa;
+}
+
+// ------------------------------------------------ background construction --
+// The background under construction (section 3.3) lives in a context of
+// its own (FP64, ds in F_DS), so the fluid's rebuild, split and shift
+// machinery serves it unchanged.  It is loaded from the context's
+// background set and written back into it after the iterations.
+static sph_status ensure_bgc(sph_ctx *c) {
+    const long long n = c->bg.n;
+    long long cap = c->prm.bg_capacity > 0 ? c->prm.bg_capacity
+                                           : std::max(100ll * n, 1ll << 18);
+    cap = std::min(std::max(cap, n), 1ll << 30);
+    if (c->bgc && c->bgc_valid) return SPH_OK;
+    if (c->bgc && c->bgc->cap < cap) {
+        free_ctx(c->bgc);
+        delete c->bgc;
+        c->bgc = nullptr;
+    }
+    if (!c->bgc) {
+        sph_params p = c->prm;
+        p.precision = SPH_FP64;
+        p.capacity = cap;
+        p.cell_c0 = 0.0;
+        p.n_bg = 0;
+        std::string why;
+        sph_status st = new_ctx(&p, c->s, true, &c->bgc, &why);
+        if (st != SPH_OK) return fail(c, st, "sph_background: " + why);
+    }
+    sph_ctx *b = c->bgc;
+    launch_minmax_pos(c->s, (int)n, c->bg.h, c->d_minmax);
+    c->launches += 1;
+    unsigned long long mm[2] = {0, 0};
+    cudaMemcpyAsync(mm, c->d_minmax, sizeof(mm), cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_background");
+    double hmin, hmax;
+    memcpy(&hmin, &mm[0], sizeof(double));
+    memcpy(&hmax, &mm[1], sizeof(double));
+    sph_status st = setup_fluid_grid(b, n, hmin, hmax);
+    if (st != SPH_OK) return fail(c, st, b->err);
+    b->n = (int)n;
+    const size_t bytes = sizeof(double) * n;
+    cudaMemcpyAsync(b->f[F_X], c->bg.x, bytes, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(b->f[F_Y], c->bg.y, bytes, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(b->f[F_H], c->bg.h, bytes, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(b->f[F_DS], c->bg.ex[0], bytes, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(b->f[F_M], c->bg.ex[1], bytes, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(b->id, c->bg.id, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, c->s);
+    for (int k : {F_U, F_V, F_P, F_RHO, F_MMIN, F_MMAX})
+        cudaMemsetAsync(b->f[k], 0, bytes, c->s);
+    b->next_id = c->bg_next_id;
+    b->grid_valid = b->rhs_valid = b->have_dt = false;
+    c->bgc_valid = true;
+    return cuda_check(c, "sph_background load");
+}
+
+// Fluid vorticity at the current state into c->omega (lists rebuilt).
+static sph_status compute_vorticity(sph_ctx *c) {
+    sph_status st = rebuild(c, false);
+    if (st != SPH_OK) return st;
+    VortArgs v;
+    v.n = c->n;
+    v.d = c->dom;
+    v.x = c->f[F_X];
+    v.y = c->f[F_Y];
+    v.u = c->f[F_U];
+    v.v = c->f[F_V];
+    v.m = c->f[F_M];
+    v.rho = c->f[F_RHO];
+    v.h = c->f[F_H];
+    v.off = c->off;
+    v.list = c->list;
+    v.omega = c->omega;
+    v.wmax = c->d_wmax;
+    launch_vorticity(c->s, v);
+    c->launches += 1;
+    return SPH_OK;
+}
+
+// One construction iteration on the background context b (see
+// sph_background in sph.h).  vort: c->omega / c->d_wmax hold the fluid
+// vorticity and c's cell structure matches the fluid positions.
+static sph_status bg_iteration(sph_ctx *c, sph_ctx *b, bool vort,
+                               sph_bg_stats *z) {
+    const sph_params &P = c->prm;
+    sph_status st;
+    if ((st = rebuild(b, false)) != SPH_OK) return fail(c, st, b->err);
+    BgMarkArgs ma;
+    ma.n = b->n;
+    ma.d = b->dom;
+    ma.x = b->f[F_X];
+    ma.y = b->f[F_Y];
+    ma.h = b->f[F_H];
+    ma.ds = b->f[F_DS];
+    ma.mark = b->tmp_a;
+    ma.ds_min = P.ds_min;
+    ma.nw = c->wall.n;
+    ma.wg = set_grid(c->wall);
+    ma.wx = c->wall.x;
+    ma.wy = c->wall.y;
+    ma.wh = c->wall.h;
+    ma.nf = vort ? c->n : 0;
+    ma.fg = grid_for_kernels(c);
+    ma.fx = c->f[F_X];
+    ma.fy = c->f[F_Y];
+    ma.fh = c->f[F_H];
+    ma.omega = c->omega;
+    ma.wmax = c->d_wmax;
+    ma.vort_k = P.vort_k;
+    ma.counts = b->d_aux;
+    launch_bg_mark(b->s, ma);
+    BgSizeArgs sa;
+    sa.n = b->n;
+    sa.off = b->off;
+    sa.list = b->list;
+    sa.mark = b->tmp_a;
+    sa.ds = b->f[F_DS];
+    sa.ds_out = b->falt[F_DS];
+    sa.mmin = b->f[F_MMIN];
+    sa.mmax = b->f[F_MMAX];
+    sa.Cr = P.Cr;
+    sa.cr3 = P.Cr * P.Cr * P.Cr;
+    sa.ds_min = P.ds_min;
+    sa.ds_max = P.ds_max;
+    sa.rho0 = P.rho0;
+    launch_bg_size(b->s, sa);
+    std::swap(b->f[F_DS], b->falt[F_DS]);
+    c->launches += 2;
+    uint32_t count = 0;
+    if ((st = split_pass(b, &count)) != SPH_OK) return fail(c, st, b->err);
+    z->n_split += count;
+    for (int r = 0; r < P.bg_smooth_iters; ++r) {
+        if ((st = rebuild(b, false)) != SPH_OK) return fail(c, st, b->err);
+        BgSmoothArgs ha;
+        ha.n = b->n;
+        ha.off = b->off;
+        ha.list = b->list;
+        ha.h = b->f[F_H];
+        ha.h_out = b->falt[F_H];
+        ha.Nr = P.bg_Nr;
+        launch_bg_hsmooth(b->s, ha);
+        std::swap(b->f[F_H], b->falt[F_H]);
+        b->grid_valid = false;
+        if ((st = rebuild(b, false)) != SPH_OK) return fail(c, st, b->err);
+        launch_shift_round(b->s, shift_args(b), false);
+        b->grid_valid = false;
+        c->launches += 4;
+    }
+    return SPH_OK;
+}
+
+// ================================================================ C ABI ==
+extern "C" {
+
+void sph_default_params(sph_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->dim = 2;
+    p->lo[0] = p->lo[1] = 0.0;
+    p->hi[0] = p->hi[1] = 1.0;
+    p->rho0 = 1.0;
+    p->cs = 10.0;
+    p->nu = 0.0;
+    p->U_ref = 1.0;
+    p->hdx = 1.0;
+    p->alpha_e = 1.5;
+    p->split_alpha = 0.9;
+    p->split_eps = 0.4;
+    p->Cr = 1.08;
+    p->merge_iters = 3;
+    p->shift_iters = 3;
+    p->precision = SPH_FP64;
+    p->capacity = 0;
+    p->pavg_mode = 0;
+    p->edac_diff_denominator = 1;
+    p->edac_rho_factor = 1;
+    p->cell_c0 = 0.0;
+    p->bg_Nr = 48.0;
+    p->bg_smooth_iters = 3;
+    p->vort_k = 0.0;
+    p->n_bg = 0;
+    p->bg_capacity = 0;
+}
+
+sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
+    if (out) *out = nullptr;
+    if (!p || !out) {
+        g_create_error = "sph_create: NULL argument";
+        return SPH_EINVAL;
+    }
+    std::string why;
+    if (p->dim != 2) why = "dim must be 2";
+    else if (!(p->hi[0] > p->lo[0]) || !(p->hi[1] > p->lo[1])) why = "empty domain box";
+    else if (p->capacity <= 0 || p->capacity > (1ll << 30)) why = "capacity must be in 1..2^30";
+    else if (!(p->rho0 > 0) || !(p->cs > 0) || !(p->hdx > 0)) why = "rho0, cs, hdx must be positive";
+    else if (!(p->nu >= 0)) why = "nu must be >= 0";
+    else if (!(p->U_ref >= 0)) why = "U_ref must be >= 0";
+    else if (p->precision != SPH_FP64 && p->precision != SPH_MIXED) why = "bad precision";
+    else if (p->pavg_mode < 0 || p->pavg_mode > 1) why = "bad pavg_mode";
+    else if (p->n_bg < 0 || p->bg_smooth_iters < 0) why = "n_bg, bg_smooth_iters must be >= 0";
+    else if (p->bg_capacity > (1ll << 30)) why = "bg_capacity must be at most 2^30";
+    if (!why.empty()) {
+        g_create_error = "sph_create: " + why;
+        return SPH_EINVAL;
+    }
+    std::string why2;
+    sph_status st = new_ctx(p, (cudaStream_t)stream, false, out, &why2);
+    if (st != SPH_OK) g_create_error = "sph_create: " + why2;
+    return st;
+}
+
+sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
+                              const sph_particles *src) {
+    if (!c) return SPH_EINVAL;
+    c->err.clear();
+    if (n < 0 || (n > 0 && !src)) return fail(c, SPH_EINVAL, "sph_load_particles: bad n or src");
+    if (kind == SPH_BACKGROUND) return load_background(c, n, src);
+    if (kind == SPH_WALL) return load_walls(c, n, src);
+    if (kind != SPH_FLUID)
+        return fail(c, SPH_EINVAL, "sph_load_particles: unknown kind");
+    if (n > c->cap) return fail(c, SPH_ECAPACITY, "sph_load_particles: n exceeds capacity");
+    if (n > 0 && (!src->x || !src->y || !src->m || !src->h))
+        return fail(c, SPH_EINVAL, "sph_load_particles: x, y, m, h are required");
+    double hmin = INFINITY;
+    for (long long i = 0; i < n; ++i) {
+        double h = src->h[i], m = src->m[i];
+        if (!(h > 0) || !isfinite(h) || !(m > 0) || !isfinite(m))
+            return fail(c, SPH_EINVAL, "sph_load_particles: h and m must be positive and finite");
+        hmin = std::min(hmin, h);
+        for (int a = 0; a < 2; ++a) {
+            double q = a == 0 ? src->x[i] : src->y[i];
+            bool in = c->dom.periodic[a] ? (q >= c->dom.lo[a] && q < c->dom.hi[a])
+                                         : (q >= c->dom.lo[a] && q <= c->dom.hi[a]);
+            if (!in || !isfinite(q))
+                return fail(c, SPH_EINVAL, "sph_load_particles: position outside the box");
+        }
+    }
+    double hmax = 0.0;
+    for (long long i = 0; i < n; ++i) hmax = std::max(hmax, src->h[i]);
+    sph_status gst = setup_fluid_grid(c, n, hmin, hmax);
+    if (gst != SPH_OK) return gst;
     c->n = (int)n;
 
     std::vector<double> tmp;
@@ -952,6 +1293,7 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
     put(c->f[F_H], src ? src->h : nullptr, 0);
     put(c->f[F_MMIN], src ? src->mmin : nullptr, 0);
     put(c->f[F_MMAX], src ? src->mmax : nullptr, 0);
+    if (c->f[F_DS]) put(c->f[F_DS], src ? src->ds : nullptr, c->prm.ds_max);
     c->next_id = n;
     if (n > 0 && src->id) {
         long long mx = -1;
@@ -1035,6 +1377,10 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     if (!c) return SPH_EINVAL;
     c->err.clear();
     if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_adapt: no fluid particles loaded");
+    if (c->prm.n_bg > 0 && c->bg.n > 0 && ++c->adapt_calls % c->prm.n_bg == 0) {
+        sph_status bs = sph_background(c, 1, nullptr);
+        if (bs != SPH_OK) return bs;
+    }
     sph_adapt_stats z;
     memset(&z, 0, sizeof(z));
     z.n_before = c->n;
@@ -1076,34 +1422,11 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     } else {
         cudaMemsetAsync(c->d_aux, 0, sizeof(uint32_t), c->s);
     }
-    // split pass (section 3.1): flag, scan, rank parents by id, emit
-    launch_split_flag(c->s, c->n, c->f[F_M], c->f[F_MMAX], c->tmp_a);
-    exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
-    c->launches += 1;
-    uint32_t count = read_u32(c, c->d_total, &st);
-    if (st != SPH_OK) return st;
-    if ((long long)c->n + 6ll * count > c->cap) {
+    // split pass (section 3.1)
+    uint32_t count = 0;
+    if ((st = split_pass(c, &count)) != SPH_OK) {
         t_end(c, 4, ev);
-        return fail(c, SPH_ECAPACITY, "sph_adapt: split children exceed the capacity");
-    }
-    if (count > 0) {
-        launch_split_collect(c->s, c->n, c->tmp_a, c->tmp_b, c->id, c->skey, c->perm);
-        radix_sort(c->s, (int)count, std::max(1, bits_for(c->next_id)), c->skey,
-                   c->perm, c->sc, &c->launches);
-        SplitArgs a;
-        a.n = c->n;
-        a.count = (int)count;
-        a.d = c->dom;
-        for (int k = 0; k < NSTATE; ++k) a.f[k] = c->f[k];
-        a.id = c->id;
-        a.parent = c->perm;
-        a.next_id = c->next_id;
-        a.alpha = c->prm.split_alpha;
-        a.eps = c->prm.split_eps;
-        launch_split_emit(c->s, a);
-        c->launches += 2;
-        c->n += 6 * (int)count;
-        c->next_id += 6ll * count;
+        return st;
     }
     z.n_split = count;
     // merge rounds (section 3.2)
@@ -1140,39 +1463,13 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         }
     }
     // shift rounds with Taylor correction, then the h update (3.2, 3.4)
-    ShiftArgs sa;
-    auto shift_args = [&]() {
-        sa.n = c->n;
-        sa.d = c->dom;
-        for (int k = 0; k < NSTATE; ++k) sa.f[k] = c->f[k];
-        sa.off = c->off;
-        sa.list = c->list;
-        sa.rho0 = c->prm.rho0;
-        sa.hdx = c->prm.hdx;
-        sa.rho = c->rhoR;
-        sa.drx = c->drx;
-        sa.dry = c->dry;
-        sa.du = c->dudt;
-        sa.dv = c->dvdt;
-        sa.dp = c->dpdt;
-        sa.hnew = c->V;
-        sa.w = wall_view(c);
-        sa.an = c->an;
-        sa.pk = c->pk;
-        sa.mf = c->mf;
-        sa.uf = c->uf;
-        sa.vf = c->vf;
-        sa.pf = c->pf;
-    };
     for (int r = 0; r < c->prm.shift_iters; ++r) {
         if ((st = rebuild(c, false)) != SPH_OK) return st;
-        shift_args();
-        launch_shift_round(c->s, sa, is_mixed(c));
+        launch_shift_round(c->s, shift_args(c), is_mixed(c));
         c->launches += 3;
     }
     if ((st = rebuild(c, false)) != SPH_OK) return st;
-    shift_args();
-    launch_h_update(c->s, sa, is_mixed(c));
+    launch_h_update(c->s, shift_args(c), is_mixed(c));
     c->launches += 2;
     launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass + 1);
     c->launches += 4;
@@ -1190,6 +1487,56 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     z.n_after = c->n;
     if (out) *out = z;
     return cuda_check(c, "sph_adapt");
+}
+
+sph_status sph_background(sph_ctx *c, int iterations, sph_bg_stats *out) {
+    if (!c) return SPH_EINVAL;
+    c->err.clear();
+    if (c->bg.n <= 0) return fail(c, SPH_ESTATE, "sph_background: no background particles loaded");
+    const sph_params &P = c->prm;
+    if (!(P.ds_min > 0) || !(P.ds_max >= P.ds_min) || !isfinite(P.ds_max) ||
+        !(P.Cr > 1) || !isfinite(P.Cr) || !(P.bg_Nr > 0) || !isfinite(P.bg_Nr))
+        return fail(c, SPH_EINVAL,
+                    "sph_background: need 0 < ds_min <= ds_max, Cr > 1, bg_Nr > 0");
+    if (iterations <= 0)
+        iterations = 3 * (int)ceil(log(P.ds_max / P.ds_min) / log(P.Cr));
+    sph_bg_stats z;
+    memset(&z, 0, sizeof(z));
+    z.n_before = c->bg.n;
+    sph_status st = ensure_bgc(c);
+    if (st != SPH_OK) return st;
+    sph_ctx *b = c->bgc;
+    cudaEvent_t ev;
+    t_begin(c, 4, &ev);
+    const bool vort = P.vort_k > 0 && c->n > 0;
+    if (vort && (st = compute_vorticity(c)) != SPH_OK) {
+        t_end(c, 4, ev);
+        return st;
+    }
+    sph_status ist = SPH_OK;
+    int it = 0;
+    for (; it < iterations && ist == SPH_OK; ++it) ist = bg_iteration(c, b, vort, &z);
+    std::string ierr = c->err;
+    // the refined set replaces the background (also after a failed
+    // iteration: the completed ones are kept)
+    const double *src[5] = {b->f[F_X], b->f[F_Y], b->f[F_H], b->f[F_DS], b->f[F_M]};
+    st = build_set_device(c, &c->bg, b->n, src, 2, b->id);
+    t_end(c, 4, ev);
+    if (st != SPH_OK) {
+        c->bgc_valid = false;
+        return st;
+    }
+    c->bg_next_id = b->next_id;
+    uint32_t cnt[2] = {0, 0};
+    cudaMemcpyAsync(cnt, b->d_aux, sizeof(cnt), cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_background");
+    z.n_marked = cnt[0];
+    z.n_vort = cnt[1];
+    z.n_after = c->bg.n;
+    z.iterations = ist == SPH_OK ? it : it - 1;
+    if (out) *out = z;
+    if (ist != SPH_OK) return fail(c, ist, ierr);
+    return cuda_check(c, "sph_background");
 }
 
 static sph_status read_R(sph_ctx *c, const void *src, double *dst, long long n) {
@@ -1296,6 +1643,23 @@ sph_status sph_read(sph_ctx *c, sph_field field, void *dst, long long cap,
         cudaError_t e = cudaStreamSynchronize(c->s);
         cudaFree(dev);
         if (e != cudaSuccess) return cuda_check(c, "sph_read");
+        return SPH_OK;
+    }
+    case SPH_F_OMEGA:
+        if ((st = need(n)) != SPH_OK) return st;
+        if (n > 0 && (st = compute_vorticity(c)) != SPH_OK) return st;
+        cudaMemcpyAsync(dst, c->omega, sizeof(double) * n, cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
+        return SPH_OK;
+    case SPH_F_BG_X: case SPH_F_BG_Y: case SPH_F_BG_H: case SPH_F_BG_M:
+    case SPH_F_BG_DS: case SPH_F_BG_ID: {
+        const long long nb = c->bg.n;
+        if (n_out) *n_out = nb;
+        if (cap < nb) return fail(c, SPH_ECAPACITY, "sph_read: buffer too small");
+        if (nb == 0) return SPH_OK;
+        const void *srcs[] = {c->bg.x, c->bg.y, c->bg.h, c->bg.ex[1], c->bg.ex[0], c->bg.id};
+        cudaMemcpyAsync(dst, srcs[field - SPH_F_BG_X], 8 * nb, cudaMemcpyDeviceToHost, c->s);
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
         return SPH_OK;
     }
     default:

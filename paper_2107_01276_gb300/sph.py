@@ -25,10 +25,12 @@ SPH_FP64, SPH_MIXED = 0, 1
 
 FIELDS = ["x", "y", "u", "v", "p", "rho", "m", "h", "mmin", "mmax", "id",
           "beta", "pavg", "drx", "dry", "dpdt", "dudt", "dvdt", "nnb",
-          "cellkey", "neigh_off", "neigh_id"]
+          "cellkey", "neigh_off", "neigh_id", "omega",
+          "bg_x", "bg_y", "bg_h", "bg_m", "bg_ds", "bg_id"]
 FIELD = {k: i for i, k in enumerate(FIELDS)}
 _FIELD_DTYPE = {"id": np.int64, "nnb": np.int32, "cellkey": np.uint64,
-                "neigh_off": np.int64, "neigh_id": np.int64}
+                "neigh_off": np.int64, "neigh_id": np.int64,
+                "bg_id": np.int64}
 
 TIMER_PASS_B, TIMER_PASS_A, TIMER_REBUILD, TIMER_PEC, TIMER_ADAPT = range(5)
 
@@ -55,6 +57,9 @@ class Params(ctypes.Structure):
         ("precision", ctypes.c_int), ("capacity", ctypes.c_longlong),
         ("pavg_mode", ctypes.c_int), ("edac_diff_denominator", ctypes.c_int),
         ("edac_rho_factor", ctypes.c_int), ("cell_c0", ctypes.c_double),
+        ("bg_Nr", ctypes.c_double), ("bg_smooth_iters", ctypes.c_int),
+        ("vort_k", ctypes.c_double), ("n_bg", ctypes.c_int),
+        ("bg_capacity", ctypes.c_longlong),
     ]
 
 
@@ -73,6 +78,12 @@ class AdaptStats(ctypes.Structure):
                 ("mass_before", ctypes.c_double),
                 ("mass_after", ctypes.c_double),
                 ("n_bg_nearest", ctypes.c_longlong)]
+
+
+class BgStats(ctypes.Structure):
+    _fields_ = [("n_before", ctypes.c_longlong), ("n_marked", ctypes.c_longlong),
+                ("n_vort", ctypes.c_longlong), ("n_split", ctypes.c_longlong),
+                ("n_after", ctypes.c_longlong), ("iterations", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -113,6 +124,8 @@ def lib(build_if_missing: bool = True):
     L.sph_step.argtypes = [ctx, ctypes.c_int, _D]
     L.sph_adapt.restype = ctypes.c_int
     L.sph_adapt.argtypes = [ctx, P(AdaptStats)]
+    L.sph_background.restype = ctypes.c_int
+    L.sph_background.argtypes = [ctx, ctypes.c_int, P(BgStats)]
     L.sph_read.restype = ctypes.c_int
     L.sph_read.argtypes = [ctx, ctypes.c_int, ctypes.c_void_p,
                            ctypes.c_longlong, P(ctypes.c_longlong)]
@@ -232,6 +245,18 @@ class Simulation:
         z = AdaptStats()
         self._check(self._L.sph_adapt(self._ctx, ctypes.byref(z)))
         return {k: getattr(z, k) for k, _ in AdaptStats._fields_}
+
+    def background(self, iterations: int = 0) -> dict:
+        """sph_background: ``iterations`` construction iterations (0: the
+        paper's count for the initial construction)."""
+        z = BgStats()
+        self._check(self._L.sph_background(self._ctx, int(iterations),
+                                           ctypes.byref(z)))
+        return {k: getattr(z, k) for k, _ in BgStats._fields_}
+
+    def read_background(self) -> dict:
+        """The background set (x, y, h, m, ds, id) in the library's order."""
+        return {k: self.read("bg_" + k) for k in ("x", "y", "h", "m", "ds", "id")}
 
     def read(self, field: str) -> np.ndarray:
         f = FIELD[field]

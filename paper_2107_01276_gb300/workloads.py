@@ -211,16 +211,22 @@ def cylinder(D: float = 2.0, Re: float = 40.0, ds_min_over_D: float = 1 / 50,
              Ly_over_D: float = 15.0, center_over_D=(7.5, 7.5),
              rho0: float = 1000.0, cs: float = 10.0, U: float = 1.0,
              hdx: float = 1.2, Cr: float = 1.08, jitter: float = 1e-3,
-             wall_layers: int = 4, seed: int = 2):
+             wall_layers: int = 4, seed: int = 2,
+             background: str = "construct"):
     """Flow past a circular cylinder (section 4.4, Table fpc-params: D = 2,
     rho0 = 1000, c_s = 10, h/dx = 1.2, C_r = 1.08), periodic box of
     25D x 15D, impulsive start u = U.
 
     - walls: `wall_layers` rings of dummy particles inside the cylinder at
       spacing ds_min (section 2.2);
-    - background: rings around the cylinder whose size grows by C_r per
-      ring from ds_min at the wall to ds_max, then a ds_max lattice (the
-      geometry-based resolution of section 3.3 given as input);
+    - background, `background="construct"` (default): a ds_max lattice
+      over the whole box (h = hdx ds_max, m = rho0 ds_max^2) to be refined
+      by the construction of section 3.3 (sph_background) before use; the
+      dict then has construct_background = True.  `background="rings"`:
+      rings around the cylinder whose size grows by C_r per ring from
+      ds_min at the wall to ds_max, then a ds_max lattice -- the graded
+      layers the construction aims at, given directly;
+    - background_rings: the ring background in either case;
     - fluid: a ds_max lattice outside the cylinder with 1e-3 ds_max
       position jitter; sph_adapt refines it to the background's sizes.
     """
@@ -261,9 +267,13 @@ def cylinder(D: float = 2.0, Re: float = 40.0, ds_min_over_D: float = 1 / 50,
     bx.append(GX[far])
     by.append(GY[far])
     bds.append(np.full(int(far.sum()), ds_max))
-    bg = dict(x=np.concatenate(bx) % Lx, y=np.concatenate(by) % Ly,
-              ds=np.concatenate(bds))
-    bg["h"] = hdx * bg["ds"]
+    rings = dict(x=np.concatenate(bx) % Lx, y=np.concatenate(by) % Ly,
+                 ds=np.concatenate(bds))
+    rings["h"] = hdx * rings["ds"]
+    nb = GX.size
+    lattice = dict(x=GX.ravel().copy(), y=GY.ravel().copy(),
+                   h=np.full(nb, hdx * ds_max), ds=np.full(nb, ds_max),
+                   m=np.full(nb, rho0 * ds_max * ds_max))
     # fluid: coarse lattice outside the cylinder
     inside = np.hypot(GX - cx, GY - cy) < R + 0.5 * ds_max
     fx, fy = GX[~inside].ravel(), GY[~inside].ravel()
@@ -276,8 +286,16 @@ def cylinder(D: float = 2.0, Re: float = 40.0, ds_min_over_D: float = 1 / 50,
     params = _base_params(lo=(0.0, 0.0), hi=(Lx, Ly), periodic=(1, 1),
                           rho0=rho0, cs=cs, nu=U * D / Re, U_ref=U, hdx=hdx,
                           ds_min=ds_min, ds_max=ds_max, Cr=Cr)
-    return dict(particles=fl, walls=walls, background=bg, params=params,
-                D=D, Re=Re, U=U)
+    if background not in ("construct", "rings"):
+        raise ValueError("background must be 'construct' or 'rings'")
+    out = dict(particles=fl, walls=walls, params=params, D=D, Re=Re, U=U,
+               background_rings=rings)
+    if background == "construct":
+        out["background"] = lattice
+        out["construct_background"] = True
+    else:
+        out["background"] = rings
+    return out
 
 
 def subset(parts: dict, idx) -> dict:

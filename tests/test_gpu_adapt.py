@@ -115,29 +115,40 @@ def test_nearest_background_fallback_and_open_box():
 
 
 def test_repeated_adaptation_then_steps():
-    """Three adaptation calls, each compared with the oracle on the same
-    input (the GPU state before the call): counts, ids and masses equal.
-    Then PEC steps: the state stays finite and mass is conserved."""
+    """Three adaptation calls: the oracle runs its own sequence, and each of
+    its states before a call is loaded into a fresh context for one
+    sph_adapt call: counts, ids and masses equal.  Then the GPU's own three
+    calls followed by PEC steps: the state stays finite and mass is
+    conserved."""
     d, bg = _refine_case(seed=14)
     pr = dict(d["params"])
     P = sph.make_params(pr, precision=sph.SPH_FP64, capacity=20000)
-    sim = sph.Simulation(P, stream_handle())
-    sim.load(d["particles"])
-    sim.load(bg, kind=sph.SPH_BACKGROUND)
     OP = oracle.params(**pr)
+    st = oracle.make_state(d["particles"], cap=20000)
     nid = len(d["particles"]["x"])
     for call in range(3):
-        before = by_id(sim, list(FIELDS))
-        st = oracle.make_state(before, cap=20000)
-        r, o, nid = oracle.adapt(OP, st, bg=bg, next_id=nid)
+        n = st["n"]
+        before = {k: st[k][:n].copy() for k in FIELDS}
+        before["id"] = st["id"][:n].copy()
+        sim = sph.Simulation(P, stream_handle())
+        sim.load(before)
+        sim.load(bg, kind=sph.SPH_BACKGROUND)
         g = sim.adapt()
+        after = by_id(sim, ["m"])
+        sim.close()
+        assert nid == int(before["id"].max()) + 1
+        r, o, nid = oracle.adapt(OP, st, bg=bg, next_id=nid)
         assert (g["n_split"], g["n_merged"], g["n_after"]) == \
             (o["n_split"], o["n_merged"], o["n_after"]), call
-        after = by_id(sim, ["m"])
         n = st["n"]
         order = np.argsort(st["id"][:n])
         assert np.array_equal(after["id"], st["id"][:n][order])
         assert np.array_equal(after["m"], st["m"][:n][order])
+    sim = sph.Simulation(P, stream_handle())
+    sim.load(d["particles"])
+    sim.load(bg, kind=sph.SPH_BACKGROUND)
+    for _ in range(3):
+        sim.adapt()
     sim.step(5)
     for k in ("x", "y", "u", "v", "p"):
         assert np.all(np.isfinite(sim.read(k)))

@@ -1,6 +1,7 @@
 """Parity of the dummy-wall boundary (section 2.2) on the GPU with the
 oracle: right-hand sides and PEC steps next to a wall, and the cylinder
-workload (walls, background, adaptation) at the size of configs[1]."""
+workload (walls, background, adaptation) at the size of configs[1].  Every
+oracle input comes from the seeded generators or from the oracle itself."""
 import math
 
 import numpy as np
@@ -86,33 +87,73 @@ def test_pec_steps_next_to_a_wall():
     sim.close()
 
 
+def _snapshot(st):
+    n = st["n"]
+    out = {k: st[k][:n].copy() for k in STATE}
+    out["id"] = st["id"][:n].copy()
+    return out
+
+
+@pytest.fixture(scope="module")
+def cyl_oracle():
+    """The oracle's own refinement of the cylinder's coarse lattice against
+    the C_r-graded ring background: its states before adaptation calls 0
+    and 6 and after call 6."""
+    d = wl.cylinder(background="rings")
+    P = oracle.params(**d["params"])
+    st = oracle.make_state(d["particles"], cap=200000)
+    nid = st["n"]
+    states = {}
+    oracle.set_walls(d["walls"])
+    try:
+        for call in range(7):
+            if call in (0, 6):
+                states[call] = _snapshot(st)
+            r, _, nid = oracle.adapt(P, st, bg=d["background"], next_id=nid)
+            assert r == 0
+    finally:
+        oracle.set_walls(None)
+    states["final"] = _snapshot(st)
+    return d, states
+
+
+@pytest.mark.parametrize("call", [0, 6])
+def test_cylinder_adapt_parity(cyl_oracle, call):
+    """One sph_adapt call from the oracle's state before call `call`:
+    counts, ids and masses equal the oracle's (FP64 decisions)."""
+    d, states = cyl_oracle
+    state = states[call]
+    sim = _sim(dict(d, particles=state), sph.SPH_FP64, cap=200000, bg=True)
+    g = sim.adapt()
+    got = by_id(sim, ["m", "mmax"])
+    sim.close()
+    P = oracle.params(**d["params"])
+    st = oracle.make_state(state, cap=200000)
+    oracle.set_walls(d["walls"])
+    try:
+        r, o, _ = oracle.adapt(P, st, bg=d["background"],
+                               next_id=int(state["id"].max()) + 1)
+    finally:
+        oracle.set_walls(None)
+    assert r == 0
+    assert (g["n_split"], g["n_merged"], g["n_after"]) == \
+        (o["n_split"], o["n_merged"], o["n_after"])
+    n = st["n"]
+    order = np.argsort(st["id"][:n])
+    assert np.array_equal(got["id"], st["id"][:n][order])
+    assert np.array_equal(got["m"], st["m"][:n][order])
+    assert np.array_equal(got["mmax"], st["mmax"][:n][order])
+
+
 @pytest.fixture(scope="module")
 def cyl_refined():
-    """configs[1]-shaped cylinder: coarse fluid refined by repeated
-    sph_adapt against the graded background, with the oracle checking one
-    adaptation call on identical inputs."""
+    """configs[1]-shaped cylinder refined on the GPU alone: the coarse
+    lattice through 12 sph_adapt calls against the ring background."""
     if not cuda_ok():
         pytest.skip("no CUDA device")
-    d = wl.cylinder()
+    d = wl.cylinder(background="rings")
     sim = _sim(d, sph.SPH_FP64, cap=200000, bg=True)
-    P = oracle.params(**d["params"])
-    stats = []
-    for call in range(12):
-        before = by_id(sim, list(STATE))
-        nid = sim.info()["next_id"]
-        g = sim.adapt()
-        stats.append(g)
-        if call in (0, 6):
-            st = oracle.make_state(before, cap=200000)
-            oracle.set_walls(d["walls"])
-            try:
-                r, o, _ = oracle.adapt(P, st, bg=d["background"],
-                                       next_id=nid)
-            finally:
-                oracle.set_walls(None)
-            assert r == 0
-            assert (g["n_split"], g["n_merged"], g["n_after"]) == \
-                (o["n_split"], o["n_merged"], o["n_after"]), call
+    stats = [sim.adapt() for _ in range(12)]
     return d, sim, stats
 
 
@@ -133,9 +174,10 @@ def test_cylinder_refines_and_conserves_mass(cyl_refined):
 
 @pytest.mark.parametrize("precision,tol", [(sph.SPH_FP64, FP64_TOL),
                                            (sph.SPH_MIXED, MIXED_TOL)])
-def test_cylinder_rhs_parity(cyl_refined, precision, tol):
-    d, sim, _ = cyl_refined
-    state = by_id(sim, list(STATE))
+def test_cylinder_rhs_parity(cyl_oracle, precision, tol):
+    """Right-hand side at the oracle's refined cylinder state."""
+    d, states = cyl_oracle
+    state = states["final"]
     P = sph.make_params(d["params"], precision=precision, capacity=200000)
     s2 = sph.Simulation(P, stream_handle())
     s2.load(state)
@@ -147,3 +189,26 @@ def test_cylinder_rhs_parity(cyl_refined, precision, tol):
     for f in RHS_FIELDS:
         assert norm(got[f], ref[f], ref["s_" + f]) <= tol, f
     s2.close()
+
+
+def test_cylinder_constructed_background():
+    """configs[1] set-up as the bench runs it: the ds_max lattice refined by
+    the full construction (3 ceil(log 25 / log 1.08) = 126 iterations) on
+    the GPU: ds_min next to the cylinder, ds_max far away, sizes growing
+    outward, mass of the background conserved."""
+    d = wl.cylinder()
+    assert d["construct_background"]
+    sim = _sim(d, sph.SPH_MIXED, cap=200000, bg=True)
+    g = sim.background()
+    assert g["iterations"] == 126
+    b = sim.read_background()
+    sim.close()
+    m0 = math.fsum(d["background"]["m"])
+    assert abs(math.fsum(b["m"]) - m0) <= 1e-12 * m0
+    pr = d["params"]
+    assert b["ds"].min() >= pr["ds_min"] and b["ds"].max() <= pr["ds_max"]
+    r = np.hypot(b["x"] - 15.0, b["y"] - 15.0)
+    edges = [1.0, 1.2, 1.5, 2.0, 3.0, 5.0, 8.0, 12.0]
+    med = [np.median(b["ds"][(r >= a) & (r < c)]) for a, c in zip(edges, edges[1:])]
+    assert all(y >= x for x, y in zip(med, med[1:]))
+    assert med[0] == pr["ds_min"] and med[-1] == pr["ds_max"]
