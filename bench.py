@@ -246,6 +246,10 @@ def main():
                     choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed steps of the mixed run with "
+                         "cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -298,7 +302,7 @@ def main():
     # L2 flush buffer (> 129 MB L2), written between timed steps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def timed_steps(s, K, W):
+    def timed_steps(s, K, W, profile=False):
         for _ in range(W):
             one_step(s)
         torch.cuda.synchronize()
@@ -312,6 +316,8 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        if profile:
+            torch.cuda.cudart().cudaProfilerStart()
         ns = []
         for k in range(K):
             flush.zero_()
@@ -320,6 +326,8 @@ def main():
             evs[k][1].record()
             ns.append(n if n is not None else n_fixed)
         torch.cuda.synchronize()
+        if profile:
+            torch.cuda.cudart().cudaProfilerStop()
         if dist:
             dist.barrier()
         s.set_timing(False)
@@ -331,7 +339,8 @@ def main():
     n_bg = sim.info()["n_bg"]
     clk = ClockSampler(local)
     clk.start()
-    ms, ns, fams, nlaunch = timed_steps(sim, args.steps, args.warmup)
+    ms, ns, fams, nlaunch = timed_steps(sim, args.steps, args.warmup,
+                                        profile=args.profile_region)
     clocks = clk.stop()
     tot_ms = float(np.sum(ms))
     my = torch.tensor([tot_ms, float(np.sum(ns))], dtype=torch.float64,

@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(128) k_bg_mref(BgArgs a) {
     const float4 pi = a.pk[i];
     const float2 q = anchor_rel(a.an, pi);
     double best = 1e308;
-    for_each_cell(a.g, a.d, 0, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
+    for_each_cell_team<T>(a.g, a.d, 0, q.x, q.y, pi.z, tm.lane, tm.mask,
+                          [&](uint32_t s, uint32_t e) {
         for (uint32_t b = s + tm.lane; b < e; b += T) {
             float fx, fy, fr2;
             if (pred_mixed(a.d, a.an, pi, __ldg(&a.bpk[b]), xi, yi, hi, a.bx,
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(128) k_density_mbar(ShiftArgs a, int want_h) {
         msum += in.m[j];
     }
     if (a.w.n > 0) {
-        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane,
+        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane, tm.mask,
                       [&](int k, double, double, double r2) {
             rho += (R)a.w.m[k] * qs_w<R>(sqrt((R)r2) * hinv);
         });
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(128) k_shift_compute(ShiftArgs a) {
         gpy += Vg * dp * dy;
     }
     if (a.w.n > 0) {
-        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane,
+        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane, tm.mask,
                       [&](int k, double dxd, double dyd, double r2) {
             const R r = sqrt((R)r2);
             if (!(r > R(0))) return;

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(128) k_bg_mark(BgMarkArgs a) {
     const float xr = (float)(xi - a.d.lo[0]), yr = (float)(yi - a.d.lo[1]);
     int hit = 0;
     if (a.nw > 0) {
-        for_each_cell(a.wg, a.d, 0, xr, yr, (float)hi, [&](uint32_t s, uint32_t e) {
+        for_each_cell_team<T>(a.wg, a.d, 0, xr, yr, (float)hi, tm.lane, tm.mask,
+                              [&](uint32_t s, uint32_t e) {
             for (uint32_t j = s + tm.lane; j < e && !hit; j += T)
                 if (pred_fp64(a.d, xi, yi, hi, a.wx[j], a.wy[j], a.wh[j])) hit = 1;
         });
@@ -77,7 +78,8 @@ __global__ void __launch_bounds__(128) k_bg_mark(BgMarkArgs a) {
         const double wmax = __longlong_as_double((long long)*a.wmax);
         if (wmax > 0.0) {
             double pb = 0.0;
-            for_each_cell(a.fg, a.d, 0, xr, yr, (float)hi, [&](uint32_t s, uint32_t e) {
+            for_each_cell_team<T>(a.fg, a.d, 0, xr, yr, (float)hi, tm.lane, tm.mask,
+                                  [&](uint32_t s, uint32_t e) {
                 for (uint32_t j = s + tm.lane; j < e; j += T)
                     if (pred_fp64(a.d, xi, yi, hi, a.fx[j], a.fy[j], a.fh[j]))
                         pb = fmax(pb, fabs(a.omega[j]));

@@ -2,6 +2,8 @@
 // the cell hash table: the neighbour-structure rebuild that the paper runs
 // before every iteration (section 3.4, step iii: "update the nearest
 // neighbor search").  All HBM-bound; no tensor cores.
+#include <algorithm>
+
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -46,7 +48,7 @@ __global__ void k_keys(int n, KeysArgs a, const double *__restrict__ x,
                        const double *__restrict__ h,
                        uint64_t *__restrict__ skey,
                        uint32_t *__restrict__ perm, uint32_t *level_mask,
-                       int *bbox) {
+                       int *bbox, uint32_t *__restrict__ zero) {
     __shared__ int sb[MAX_LEVELS * 4];
     __shared__ uint32_t smask;
     for (int t = threadIdx.x; t < MAX_LEVELS * 4; t += blockDim.x)
@@ -62,6 +64,7 @@ __global__ void k_keys(int n, KeysArgs a, const double *__restrict__ x,
         uint64_t m = spread2((uint64_t)ix) | (spread2((uint64_t)iy) << 1);
         skey[i] = ((uint64_t)l << (2 * a.mbits)) | m;
         perm[i] = (uint32_t)i;
+        if (zero) zero[i] = 0;
         atomicOr(&smask, 1u << l);
         atomicMin(&sb[l * 4 + 0], ix);
         atomicMax(&sb[l * 4 + 1], ix);
@@ -110,7 +113,8 @@ void compute_levels(const Domain &dom, double c0, Level *lev) {
 void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
                  int lmax, int mbits, const Level *lev, const double *x,
                  const double *y, const double *h, uint64_t *skey,
-                 uint32_t *perm, uint32_t *level_mask, int *bbox) {
+                 uint32_t *perm, uint32_t *level_mask, int *bbox,
+                 uint32_t *zero) {
     KeysArgs a;
     a.dom = dom;
     a.c0 = c0;
@@ -120,7 +124,7 @@ void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
     if (n <= 0) return;
     int bs = 256;
     k_keys<<<(n + bs - 1) / bs, bs, 0, s>>>(n, a, x, y, h, skey, perm,
-                                            level_mask, bbox);
+                                            level_mask, bbox, zero);
 }
 
 // ------------------------------------------------------------ radix sort --
@@ -198,6 +202,108 @@ __global__ void __launch_bounds__(RS_THREADS)
     }
 }
 
+// Small sets (n <= RSS_MAX): every pass in one block of 32 warps.  Warp w
+// owns a contiguous chunk of the input; the per-(warp, digit) counts,
+// scanned digit-major, give each warp's scatter base, and the warp ranks
+// its chunk 32 keys at a time with __match_any_sync, so the sort is stable
+// exactly like the tiled form.  Ends with the result in (ka, va).
+constexpr int RSS_THREADS = 1024;
+constexpr int RSS_WARPS = RSS_THREADS / 32;
+constexpr int RSS_MAX = 32768;
+
+__global__ void __launch_bounds__(RSS_THREADS)
+    k_radix_small(int n, int passes, uint64_t *ka, uint32_t *va, uint64_t *kb,
+                  uint32_t *vb) {
+    __shared__ uint32_t cnt[RSS_WARPS][256];
+    __shared__ uint32_t dtot[256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int chunk = (((n + RSS_WARPS - 1) / RSS_WARPS) + 31) & ~31;
+    const int wb = w * chunk, we = min(n, wb + chunk);
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        const uint64_t *kin = (p & 1) ? kb : ka;
+        const uint32_t *vin = (p & 1) ? vb : va;
+        uint64_t *kout = (p & 1) ? ka : kb;
+        uint32_t *vout = (p & 1) ? va : vb;
+        for (int t = threadIdx.x; t < RSS_WARPS * 256; t += RSS_THREADS)
+            (&cnt[0][0])[t] = 0;
+        __syncthreads();
+        for (int b = wb; b < we; b += 32) {
+            const int e = b + lane;
+            const bool ok = e < we;
+            const int d = ok ? (int)((kin[e] >> shift) & 255u) : 256;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            uint32_t before = 0;
+            if (ok) before = cnt[w][d];
+            __syncwarp();
+            if (ok && lane == __ffs(peers) - 1) cnt[w][d] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {            // per digit: prefix over warps
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+            for (int ww = 0; ww < RSS_WARPS; ++ww) {
+                const uint32_t c = cnt[ww][d];
+                cnt[ww][d] = run;
+                run += c;
+            }
+            dtot[d] = run;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {             // digit bases (exclusive scan of 256)
+            uint32_t v[8], sum = 0;
+            for (int k = 0; k < 8; ++k) {
+                v[k] = dtot[lane * 8 + k];
+                sum += v[k];
+            }
+            uint32_t x = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            uint32_t pre = x - sum;
+            for (int k = 0; k < 8; ++k) {
+                dtot[lane * 8 + k] = pre;
+                pre += v[k];
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < RSS_WARPS * 256; t += RSS_THREADS)
+            (&cnt[0][0])[t] += dtot[t & 255];
+        __syncthreads();
+        for (int b = wb; b < we; b += 32) {
+            const int e = b + lane;
+            const bool ok = e < we;
+            uint64_t k = 0;
+            int d = 256;
+            if (ok) {
+                k = kin[e];
+                d = (int)((k >> shift) & 255u);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            uint32_t before = 0;
+            if (ok) before = cnt[w][d];
+            __syncwarp();
+            if (ok && lane == __ffs(peers) - 1) cnt[w][d] = before + __popc(peers);
+            __syncwarp();
+            if (ok) {
+                const uint32_t pos = before + __popc(peers & lt);
+                kout[pos] = k;
+                vout[pos] = vin[e];
+            }
+        }
+        __syncthreads();
+    }
+    if (passes & 1) {                       // result is in (kb, vb)
+        for (int e = threadIdx.x; e < n; e += RSS_THREADS) {
+            ka[e] = kb[e];
+            va[e] = vb[e];
+        }
+    }
+}
+
 size_t radix_counts_elems(size_t n) {
     return 256 * ((n + RS_TILE - 1) / RS_TILE);
 }
@@ -205,6 +311,12 @@ size_t radix_counts_elems(size_t n) {
 void radix_sort(cudaStream_t s, int n, int bits, uint64_t *key,
                 uint32_t *val, SortScratch &sc, int *launches) {
     if (n <= 1 || bits <= 0) return;
+    if (n <= RSS_MAX) {
+        k_radix_small<<<1, RSS_THREADS, 0, s>>>(n, (bits + 7) / 8, key, val,
+                                               sc.key_alt, sc.val_alt);
+        *launches += 1;
+        return;
+    }
     int ntiles = (n + RS_TILE - 1) / RS_TILE;
     uint64_t *ka = key, *kb = sc.key_alt;
     uint32_t *va = val, *vb = sc.val_alt;
@@ -323,13 +435,71 @@ static void scan_rec(cudaStream_t s, const uint32_t *in, uint32_t *out, int n,
     *launches += 2;
 }
 
+// Small scans (n <= 1024 * 32): one block of 1024 threads, thread t owns
+// a contiguous chunk; two passes over the chunk (sum, then write), so in
+// may equal out.  With `rev`, the values are in[i] + rev[i] and rev is
+// zeroed (the neighbour-list totals), and out[n] receives the total.
+constexpr int SS_THREADS = 1024;
+constexpr int SS_MAX = SS_THREADS * 32;
+
+__global__ void __launch_bounds__(SS_THREADS)
+    k_scan_small(const uint32_t *in, uint32_t *rev, uint32_t *out, int n,
+                 uint32_t *total_dev, int write_total_at_n) {
+    __shared__ uint32_t ws[SS_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int chunk = (n + SS_THREADS - 1) / SS_THREADS;
+    const int b = threadIdx.x * chunk, e = min(n, b + chunk);
+    uint32_t sum = 0;
+    for (int i = b; i < e; ++i) sum += in[i] + (rev ? rev[i] : 0u);
+    uint32_t x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    uint32_t pre = (w > 0 ? ws[w - 1] : 0u) + x - sum;
+    for (int i = b; i < e; ++i) {
+        const uint32_t v = in[i] + (rev ? rev[i] : 0u);
+        if (rev) rev[i] = 0;
+        out[i] = pre;
+        pre += v;
+    }
+    if (threadIdx.x == SS_THREADS - 1) {
+        if (total_dev) *total_dev = ws[SS_THREADS / 32 - 1];
+        if (write_total_at_n) out[n] = ws[SS_THREADS / 32 - 1];
+    }
+}
+
 void exclusive_scan(cudaStream_t s, const uint32_t *in, uint32_t *out, int n,
                     uint32_t *total_dev, SortScratch &sc, int *launches) {
     if (n <= 0) {
         if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
         return;
     }
+    if (n <= SS_MAX) {
+        k_scan_small<<<1, SS_THREADS, 0, s>>>(in, nullptr, out, n, total_dev, 0);
+        *launches += 1;
+        return;
+    }
     scan_rec(s, in, out, n, total_dev, sc.scan_tmp, launches);
+}
+
+bool list_offsets_small(cudaStream_t s, const uint32_t *own, uint32_t *rev,
+                        uint32_t *off, int n, int *launches) {
+    if (n <= 0 || n > SS_MAX) return false;
+    k_scan_small<<<1, SS_THREADS, 0, s>>>(own, rev, off, n, nullptr, 1);
+    *launches += 1;
+    return true;
 }
 
 // ---------------------------------------------------------------- gather --
@@ -377,18 +547,59 @@ __global__ void k_table_end(int n, const uint64_t *__restrict__ skey,
                             uint32_t tmask) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    table_mark_end(i, n, skey, tkey, tend, tmask);
+}
+
+// Gather in sorted order fused with the insertion of each cell's start.
+__global__ void k_gather_insert(int n, const uint32_t *__restrict__ perm,
+                                GatherList g, const uint64_t *__restrict__ skey,
+                                uint64_t *tkey, uint32_t *tstart,
+                                uint32_t tmask) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t src = perm[i];
+    for (int k = 0; k < g.nd; ++k) g.dst[k][i] = g.src[k][src];
+    for (int k = 0; k < g.ni; ++k) g.idst[k][i] = g.isrc[k][src];
     uint64_t k = skey[i];
-    if (i + 1 < n && skey[i + 1] == k) return;
+    if (i > 0 && skey[i - 1] == k) return;
     uint32_t slot = hash_slot(k, tmask);
     for (uint32_t it = 0; it <= tmask; ++it) {
-        uint64_t t = tkey[slot];
-        if (t == k) {
-            tend[slot] = (uint32_t)(i + 1);
+        unsigned long long prev = atomicCAS((unsigned long long *)&tkey[slot],
+                                            (unsigned long long)EMPTY_KEY,
+                                            (unsigned long long)k);
+        if (prev == EMPTY_KEY || prev == k) {
+            tstart[slot] = (uint32_t)i;
             return;
         }
-        if (t == EMPTY_KEY) return;
         slot = (slot + 1) & tmask;
     }
+}
+
+void gather_insert(cudaStream_t s, int n, const uint32_t *perm,
+                   const GatherList &g, const uint64_t *skey, uint64_t *tkey,
+                   uint32_t *tstart, uint32_t tmask, int *launches) {
+    if (n <= 0) return;
+    k_gather_insert<<<(n + 255) / 256, 256, 0, s>>>(n, perm, g, skey, tkey,
+                                                     tstart, tmask);
+    *launches += 1;
+}
+
+// Reset before a rebuild: level bounding boxes and mask, every table key,
+// and up to four counters.
+__global__ void k_rebuild_reset(RebuildReset r) {
+    const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t st = gridDim.x * blockDim.x;
+    if (t0 < MAX_LEVELS * 4) r.bbox[t0] = (t0 & 1) ? -1 : 0x7fffffff;
+    if (t0 == 0) *r.level_mask = 0;
+    if (t0 < 4 && r.zero[t0]) *r.zero[t0] = 0;
+    for (uint32_t k = t0; k < r.tslots; k += st) r.tkey[k] = EMPTY_KEY;
+}
+
+void launch_rebuild_reset(cudaStream_t s, const RebuildReset &r, int *launches) {
+    int nb = (int)std::min<uint32_t>((r.tslots + 255) / 256, 608u);
+    if (nb < 1) nb = 1;
+    k_rebuild_reset<<<nb, 256, 0, s>>>(r);
+    *launches += 1;
 }
 
 void build_cell_table(cudaStream_t s, int n, const uint64_t *skey,

@@ -1,8 +1,10 @@
 // Per-rebuild packing (levels, FP32 anchor coordinates, float mirrors) and
 // the CSR neighbour lists N(i) (definition and search in neighbors.cuh).
 //
-// List build: count (own + reverse) -> exclusive scan -> fill -> sort the
-// reverse segment of each list, so lists are deterministic: own entries in
+// List build: one walk per particle stages its own entries and counts the
+// reverse ones -> exclusive scan -> place (own entries copied, reverse
+// entries written into the coarser neighbours' lists) -> sort the reverse
+// segment of each list, so lists are deterministic: own entries in
 // traversal order, then the finer-level entries in ascending index.
 #include "lists.cuh"
 #include "neighbors.cuh"
@@ -30,6 +32,7 @@ __global__ void k_pack(PackArgs a) {
     }
     a.pk[i] = make_float4(xl[0], xl[1], (float)a.h[i],
                           __uint_as_float((unsigned)g[0] | ((unsigned)g[1] << 16)));
+    if (a.tend) table_mark_end(i, a.n, a.skey, a.tkey, a.tend, a.tmask);
     if (!a.mixed) return;
     a.mf[i] = (float)a.m[i];
     a.pf[i] = (float)a.p[i];
@@ -68,35 +71,12 @@ __device__ __forceinline__ bool member(const ListArgs &a, const float4 &pi,
                       a.h, j, dx, dy, r2);
 }
 
-// A team of T threads walks particle i's cells; each cell's candidates
-// are taken T at a time, one per lane.
-template <int T>
-__global__ void __launch_bounds__(128) k_list_count(ListArgs a) {
-    const Team<T> tm;
-    const int i = Team<T>::particle();
-    if (i >= a.n) return;
-    const int li = a.lev[i];
-    const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
-    const float4 pi = a.pk[i];
-    const float2 q = anchor_rel(a.an, pi);
-    uint32_t cnt = 0;
-    for_each_cell(a.g, a.d, li, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
-        for (uint32_t j = s + tm.lane; j < e; j += T) {
-            if (member(a, pi, xi, yi, hi, (int)j)) {
-                ++cnt;
-                if (__ldg(&a.lev[j]) > li) atomicAdd(&a.rev[j], 1u);
-            }
-        }
-    });
-    cnt = team_sum<T>(tm.mask, cnt);
-    if (tm.lane == 0) a.own[i] = cnt;
-}
-
-// Single-walk list build: each team writes its own entries, in the same
-// (cell, index) order as k_list_fill, into a fixed-stride staging row of
-// STAGE entries; particles with more own entries go to a queue that
-// k_list_fill_queue handles with a second walk.
-constexpr int STAGE = 64;
+// Single-walk list build: a team of T lanes walks particle i's own and
+// coarser levels (cells looked up in parallel, each cell's candidates
+// taken T at a time, one per lane); the team's ballot orders each group,
+// so own entries come in (cell, index) order whatever T is.  They go into
+// a fixed-stride staging row of stage_w entries; particles with more own
+// entries go to a queue that k_list_fill_queue handles with a second walk.
 
 template <int T>
 __global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
@@ -108,9 +88,11 @@ __global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
     const float4 pi = a.pk[i];
     const float2 q = anchor_rel(a.an, pi);
     uint32_t k = 0;
-    uint32_t *row = a.stage + (size_t)i * STAGE;
+    const uint32_t W = a.stage_w;
+    uint32_t *row = a.stage + (size_t)i * W;
     const unsigned below = tm.mask & ((1u << (threadIdx.x & 31)) - 1u);
-    for_each_cell(a.g, a.d, li, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
+    for_each_cell_team<T>(a.g, a.d, li, q.x, q.y, pi.z, tm.lane, tm.mask,
+                          [&](uint32_t s, uint32_t e) {
         for (uint32_t j0 = s; j0 < e; j0 += T) {
             const uint32_t j = j0 + tm.lane;
             const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);
@@ -118,7 +100,7 @@ __global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
                                         : __ballot_sync(tm.mask, in);
             if (in) {
                 const uint32_t pos = k + (T == 1 ? 0u : __popc(bal & below));
-                if (pos < STAGE) row[pos] = j;
+                if (pos < W) row[pos] = j;
                 if (__ldg(&a.lev[j]) > li) atomicAdd(&a.rev[j], 1u);
             }
             k += __popc(bal);
@@ -126,30 +108,34 @@ __global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
     });
     if (tm.lane == 0) {
         a.own[i] = k;
-        if (k > STAGE) a.queue[atomicAdd(a.nqueue, 1u)] = (uint32_t)i;
+        atomicMax(a.max_own, k);
+        if (k > W) a.queue[atomicAdd(a.nqueue, 1u)] = (uint32_t)i;
     }
 }
 
 // Copies the staged own entries into place and writes the reverse entries
-// (i into the list of each coarser neighbour j).
-__global__ void k_list_place(ListArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// (i into the list of each coarser neighbour j); T lanes per particle.
+template <int T>
+__global__ void __launch_bounds__(128) k_list_place(ListArgs a) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
     if (i >= a.n) return;
     const uint32_t own = a.own[i];
-    if (own > STAGE) return;              // handled by k_list_fill_queue
-    const int li = a.lev[i];
-    const uint32_t base = a.off[i];
-    const uint32_t *row = a.stage + (size_t)i * STAGE;
-    const uint32_t cap = a.cap;
-    for (uint32_t k = 0; k < own; ++k) {
-        const uint32_t j = row[k];
-        if (base + k < cap) a.list[base + k] = j;
-        if (__ldg(&a.lev[j]) > li) {
-            const uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
-            if (rp < cap) a.list[rp] = (uint32_t)i;
+    if (own <= a.stage_w) {               // else handled by k_list_fill_queue
+        const int li = a.lev[i];
+        const uint32_t base = a.off[i];
+        const uint32_t *row = a.stage + (size_t)i * a.stage_w;
+        const uint32_t cap = a.cap;
+        for (uint32_t k = tm.lane; k < own; k += T) {
+            const uint32_t j = row[k];
+            if (base + k < cap) a.list[base + k] = j;
+            if (__ldg(&a.lev[j]) > li) {
+                const uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
+                if (rp < cap) a.list[rp] = (uint32_t)i;
+            }
         }
     }
-    if (i == a.n - 1 && a.off[a.n] > cap) atomicOr(a.overflow, 1);
+    if (i == a.n - 1 && tm.lane == 0 && a.off[a.n] > a.cap) atomicOr(a.overflow, 1);
 }
 
 __global__ void k_list_total(int n, const uint32_t *own, const uint32_t *rev,
@@ -158,42 +144,8 @@ __global__ void k_list_total(int n, const uint32_t *own, const uint32_t *rev,
     if (i < n) tot[i] = own[i] + rev[i];
 }
 
-// Same walk; the team's ballot orders each group of T candidates, so a
-// list's own entries come in (cell, index) order whatever T is.
-template <int T>
-__global__ void __launch_bounds__(128) k_list_fill(ListArgs a) {
-    const Team<T> tm;
-    const int i = Team<T>::particle();
-    if (i >= a.n) return;
-    const int li = a.lev[i];
-    const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
-    const float4 pi = a.pk[i];
-    const float2 q = anchor_rel(a.an, pi);
-    uint32_t k = a.off[i];
-    const uint32_t cap = a.cap;
-    const unsigned below = tm.mask & ((1u << (threadIdx.x & 31)) - 1u);
-    for_each_cell(a.g, a.d, li, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
-        for (uint32_t j0 = s; j0 < e; j0 += T) {
-            const uint32_t j = j0 + tm.lane;
-            const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);
-            const unsigned bal = T == 1 ? (in ? 1u : 0u)
-                                        : __ballot_sync(tm.mask, in);
-            if (in) {
-                const uint32_t pos = k + (T == 1 ? 0u : __popc(bal & below));
-                if (pos < cap) a.list[pos] = j;
-                if (__ldg(&a.lev[j]) > li) {
-                    uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
-                    if (rp < cap) a.list[rp] = (uint32_t)i;
-                }
-            }
-            k += __popc(bal);
-        }
-    });
-    if (i == a.n - 1 && tm.lane == 0 && a.off[a.n] > cap) atomicOr(a.overflow, 1);
-}
-
-// Second walk for the queued particles (more than STAGE own entries):
-// same order as k_list_fill; teams take queue entries in turn.
+// Second walk for the queued particles (more than stage_w own entries):
+// same order as k_list_gather; teams take queue entries in turn.
 template <int T>
 __global__ void __launch_bounds__(128) k_list_fill_queue(ListArgs a) {
     const Team<T> tm;
@@ -209,7 +161,8 @@ __global__ void __launch_bounds__(128) k_list_fill_queue(ListArgs a) {
         const float2 q = anchor_rel(a.an, pi);
         uint32_t k = a.off[i];
         const uint32_t cap = a.cap;
-        for_each_cell(a.g, a.d, li, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
+        for_each_cell_team<T>(a.g, a.d, li, q.x, q.y, pi.z, tm.lane, tm.mask,
+                              [&](uint32_t s, uint32_t e) {
             for (uint32_t j0 = s; j0 < e; j0 += T) {
                 const uint32_t j = j0 + tm.lane;
                 const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);
@@ -339,27 +292,31 @@ void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
         cudaMemsetAsync(a.off, 0, sizeof(uint32_t), s);
         return;
     }
-    cudaMemsetAsync(a.rev, 0, sizeof(uint32_t) * n, s);
-    cudaMemsetAsync(a.nqueue, 0, sizeof(uint32_t), s);
     const int T = team_size(n);
     if (T == 16) k_list_gather<16><<<nblk(n * 16, 128), 128, 0, s>>>(a);
     else if (T == 4) k_list_gather<4><<<nblk(n * 4, 128), 128, 0, s>>>(a);
     else k_list_gather<1><<<nblk(n, 128), 128, 0, s>>>(a);
+    *launches += 1;
+    if (list_offsets_small(s, a.own, a.rev, a.off, n, launches)) return;
     k_list_total<<<nblk(n, 256), 256, 0, s>>>(n, a.own, a.rev, tot_tmp);
     // off has n + 1 entries: scan n + 1 values with a trailing zero
     cudaMemsetAsync(tot_tmp + n, 0, sizeof(uint32_t), s);
     exclusive_scan(s, tot_tmp, a.off, n + 1, nullptr, sc, launches);
-    *launches += 2;
+    cudaMemsetAsync(a.rev, 0, sizeof(uint32_t) * n, s);
+    *launches += 1;
 }
 
-void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, int *launches) {
+void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,
+                      int *launches) {
     (void)mixed;
     const int n = a.n;
     if (n <= 0) return;
-    cudaMemsetAsync(a.rev, 0, sizeof(uint32_t) * n, s);
-    k_list_place<<<nblk(n, 128), 128, 0, s>>>(a);
-    k_list_fill_queue<16><<<152 * 4, 128, 0, s>>>(a);
-    cudaMemsetAsync(a.nlong, 0, sizeof(uint32_t), s);
+    switch (team_size(n)) {
+    case 16: k_list_place<16><<<nblk(n * 16, 128), 128, 0, s>>>(a); break;
+    case 4: k_list_place<4><<<nblk(n * 4, 128), 128, 0, s>>>(a); break;
+    default: k_list_place<1><<<nblk(n, 128), 128, 0, s>>>(a); break;
+    }
+    if (queue) k_list_fill_queue<16><<<152 * 4, 128, 0, s>>>(a);
     k_list_sort_rev<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.own, a.list, a.cap,
                                                   a.longq, a.nlong);
     k_list_sort_long<<<std::max(1, std::min(152 * 16, nblk(n, 512))), 128, 0, s>>>(

@@ -17,6 +17,10 @@ struct PackArgs {
     uint8_t *lev;
     float4 *pk;                 // {xl, yl, h, gx | gy << 16}
     float *mf, *pf, *uf, *vf;
+    // cell table: the last particle of each cell records its end
+    const uint64_t *tkey;
+    uint32_t *tend;
+    uint32_t tmask;
 };
 
 struct ListArgs {
@@ -34,7 +38,9 @@ struct ListArgs {
     uint32_t cap;               // list capacity (entries)
     int *overflow;
     uint32_t *longq, *nlong;    // particles with long reverse segments
-    uint32_t *stage;            // n x STAGE staging rows of own entries
+    uint32_t *stage;            // n x stage_w staging rows of own entries
+    uint32_t stage_w;           // row width (entries)
+    uint32_t *max_own;          // largest own-entry count of the build
     uint32_t *queue, *nqueue;   // particles whose own entries overflow a row
 };
 
@@ -43,9 +49,14 @@ void launch_anchor_pack(cudaStream_t s, int n, const double *x,
                         const double *y, const double *h, const double *lo,
                         const double *A, const Anchor &an, float4 *pk);
 // Count and scan into off (n + 1 entries; tot_tmp needs n + 1), then fill
-// the lists; entries past a.cap are dropped and flag a.overflow.
+// the lists; entries past a.cap are dropped and flag a.overflow.  Before
+// the count, rev[0..n) and the counters nqueue, max_own and nlong must be
+// zero (the rebuild's reset and key kernels do that).
 void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
                        SortScratch &sc, uint32_t *tot_tmp, int *launches);
-void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, int *launches);
+// queue: launch the second walk for rows that overflowed (false when the
+// caller knows none did).
+void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,
+                      int *launches);
 
 }  // namespace sph

@@ -134,6 +134,69 @@ __device__ __forceinline__ void for_each_cell(const Grid &g, const Domain &d,
     }
 }
 
+// Team form of for_each_cell: the T lanes of a team (mask: the team's
+// lanes) look up the cells of a level in parallel, lane t taking cells t,
+// t + T, ..., and then every lane calls f(s, e) for the occupied cells in
+// the same order as for_each_cell (level, then row, then column).  The
+// hash lookups and cell arithmetic are thus done once per cell instead of
+// once per lane; f may use team-wide shuffles and ballots.
+template <int T, class F>
+__device__ __forceinline__ void for_each_cell_team(const Grid &g,
+                                                   const Domain &d, int li,
+                                                   float xr, float yr,
+                                                   float hi, int lane,
+                                                   unsigned mask, F &&f) {
+    if constexpr (T == 1) {
+        (void)lane;
+        (void)mask;
+        for_each_cell(g, d, li, xr, yr, hi, f);
+        return;
+    }
+    const float Ri = 3.0f * hi;
+    const uint32_t lmask = g.level_mask & ~((1u << li) - 1u);
+    for (uint32_t mm = lmask; mm; mm &= mm - 1) {
+        const int l = __ffs(mm) - 1;
+        const int *bb = g.bbox + 4 * l;
+        if (__ldg(&bb[0]) > __ldg(&bb[1])) continue;   // level holds no particle
+        const Level &L = g.lev[l];
+        const float Q = fmaxf(Ri, L.cf) * (1.0f + 1e-5f);
+        AxisPieces px, py;
+        if (!axis_pieces(d, L, bb, 0, xr, Q, px)) continue;
+        if (!axis_pieces(d, L, bb, 1, yr, Q, py)) continue;
+        const int nx0 = max(0, px.last[0] - px.first[0] + 1);
+        const int nx1 = max(0, px.last[1] - px.first[1] + 1);
+        const int nx2 = max(0, px.last[2] - px.first[2] + 1);
+        const int ny0 = max(0, py.last[0] - py.first[0] + 1);
+        const int ny1 = max(0, py.last[1] - py.first[1] + 1);
+        const int ny2 = max(0, py.last[2] - py.first[2] + 1);
+        const int nx = nx0 + nx1 + nx2, ny = ny0 + ny1 + ny2;
+        const int ncell = nx * ny;
+        const uint64_t lbits = (uint64_t)l << (2 * g.mbits);
+        for (int base = 0; base < ncell; base += T) {
+            const int idx = base + lane;
+            uint32_t s = 0, e = 0;
+            if (idx < ncell) {
+                const int iy = idx / nx, ix = idx - iy * nx;
+                const int cx = ix < nx0 ? px.first[0] + ix + px.shift[0]
+                             : ix < nx0 + nx1 ? px.first[1] + (ix - nx0) + px.shift[1]
+                                              : px.first[2] + (ix - nx0 - nx1) + px.shift[2];
+                const int cy = iy < ny0 ? py.first[0] + iy + py.shift[0]
+                             : iy < ny0 + ny1 ? py.first[1] + (iy - ny0) + py.shift[1]
+                                              : py.first[2] + (iy - ny0 - ny1) + py.shift[2];
+                if (!table_lookup(g, lbits | (spread2((uint64_t)cy) << 1) |
+                                         spread2((uint64_t)cx), s, e))
+                    s = e = 0;
+            }
+            const int cnt = min(T, ncell - base);
+            for (int t = 0; t < cnt; ++t) {
+                const uint32_t ss = T == 1 ? s : __shfl_sync(mask, s, t, T);
+                const uint32_t ee = T == 1 ? e : __shfl_sync(mask, e, t, T);
+                if (ee > ss) f(ss, ee);
+            }
+        }
+    }
+}
+
 // Calls f(j) for every particle j of the cells for_each_cell visits.
 template <class F>
 __device__ __forceinline__ void for_each_candidate(const Grid &g,

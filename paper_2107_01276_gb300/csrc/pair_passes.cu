@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128)
         pair(a.m[j], hj, a.p[j], j == i, dx, dy, r2);
     }
     if (a.w.n > 0) {
-        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane,
+        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane, tm.mask,
                       [&](int k, double dxd, double dyd, double r2d) {
             pair((R)a.w.m[k], (R)a.w.h[k], (R)a.w.p[k], false, (R)dxd,
                  (R)dyd, (R)r2d);
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(128)
     }
     if (a.w.n > 0) {
         const R rho0 = (R)a.rho0;
-        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane,
+        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane, tm.mask,
                       [&](int k, double dxd, double dyd, double r2d) {
             const R mk = (R)a.w.m[k], pk = (R)a.w.p[k];
             const R pref = literal ? R(0) : pavg_i;
@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(128) k_wall_bc(WallBcArgs a) {
     const float4 pw = a.w.pk[k];
     const float2 q = anchor_rel(a.an, pw);
     double sw = 0, su = 0, sv = 0, sp = 0;
-    for_each_cell(a.g, a.d, 0, q.x, q.y, pw.z, [&](uint32_t s, uint32_t e) {
+    for_each_cell_team<T>(a.g, a.d, 0, q.x, q.y, pw.z, tm.lane, tm.mask,
+                          [&](uint32_t s, uint32_t e) {
         for (uint32_t f = s + tm.lane; f < e; f += T) {
             float fx, fy, fr2;
             if (!pred_mixed(a.d, a.an, pw, __ldg(&a.pk[f]), xw, yw, hw, a.x,

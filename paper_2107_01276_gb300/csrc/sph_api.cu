@@ -112,6 +112,9 @@ struct sph_ctx {
     int *d_overflow = nullptr;
     uint32_t *longq = nullptr, *d_nlong = nullptr;
     uint32_t *stage = nullptr, *lqueue = nullptr, *d_nlq = nullptr;
+    uint32_t stage_w = 64;          // staging row width (entries)
+    uint32_t stage_want = 0;        // width to switch to at the next build
+    uint32_t *d_max_own = nullptr;  // largest own-entry count of a build
     Anchor an;
     double anchor_A[2] = {0, 0};
     int anchor_version = 0;     // bumped whenever the anchor lattice is set
@@ -270,6 +273,8 @@ static ListArgs list_args(sph_ctx *c) {
     la.longq = c->longq;
     la.nlong = c->d_nlong;
     la.stage = c->stage;
+    la.stage_w = c->stage_w;
+    la.max_own = c->d_max_own;
     la.queue = c->lqueue;
     la.nqueue = c->d_nlq;
     return la;
@@ -280,12 +285,37 @@ static ListArgs list_args(sph_ctx *c) {
 // and flagged, and the flag is checked at the next synchronising call.
 static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
     const int n = c->n;
+    if (c->stage_want > c->stage_w) {
+        uint32_t *ns = nullptr;
+        if (dalloc(&ns, (size_t)c->cap * c->stage_want)) {
+            cudaFree(c->stage);   // waits for the last build's use of it
+            c->stage = ns;
+            c->stage_w = c->stage_want;
+        } else {
+            cudaGetLastError();   // keep the narrower rows
+        }
+        c->stage_want = 0;
+    }
     cudaEvent_t ev;
     t_begin(c, 2, &ev);
-    launch_reset_bbox(c->s, c->bbox, c->level_mask);
+    // table of 2n..4n slots (power of two)
+    uint32_t t = 1;
+    while (t < 2u * (uint32_t)std::max(n, 1)) t <<= 1;
+    c->tmask = t - 1;
+    RebuildReset rr;
+    rr.bbox = c->bbox;
+    rr.level_mask = c->level_mask;
+    rr.tkey = c->tkey;
+    rr.tslots = t;
+    rr.zero[0] = c->d_nlq;
+    rr.zero[1] = c->d_max_own;
+    rr.zero[2] = c->d_nlong;
+    rr.zero[3] = nullptr;
+    launch_rebuild_reset(c->s, rr, &c->launches);
     launch_keys(c->s, n, c->dom, c->c0, c->lmax, c->mbits, c->lev, c->f[F_X],
-                c->f[F_Y], c->f[F_H], c->skey, c->perm, c->level_mask, c->bbox);
-    c->launches += 2;
+                c->f[F_Y], c->f[F_H], c->skey, c->perm, c->level_mask, c->bbox,
+                c->rev);
+    c->launches += 1;
     radix_sort(c->s, n, 2 * c->mbits + c->lbits, c->skey, c->perm, c->sc,
                &c->launches);
     GatherList gl;
@@ -300,15 +330,10 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
     gl.isrc[0] = c->id;
     gl.idst[0] = c->id_alt;
     gl.ni = 1;
-    gather_by_perm(c->s, n, c->perm, gl, &c->launches);
+    gather_insert(c->s, n, c->perm, gl, c->skey, c->tkey, c->tstart, c->tmask,
+                  &c->launches);
     for (int k = 0; k < last; ++k) std::swap(c->f[k], c->falt[k]);
     std::swap(c->id, c->id_alt);
-    // table of 2n..4n slots (power of two)
-    uint32_t t = 1;
-    while (t < 2u * (uint32_t)std::max(n, 1)) t <<= 1;
-    c->tmask = t - 1;
-    build_cell_table(c->s, n, c->skey, c->tkey, c->tstart, c->tend, c->tmask,
-                     &c->launches);
     PackArgs pa;
     pa.n = n;
     pa.lshift = 2 * c->mbits;
@@ -332,14 +357,24 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
     pa.pf = c->pf;
     pa.uf = c->uf;
     pa.vf = c->vf;
+    pa.tkey = c->tkey;
+    pa.tend = c->tend;
+    pa.tmask = c->tmask;
     launch_pack(c->s, pa);
     c->launches += 1;
     ListArgs la = list_args(c);
     build_lists_count(c->s, la, is_mixed(c), c->sc, c->cnt_tmp, &c->launches);
+    bool queue = true;
     if (exact && n > 0) {
-        uint32_t total = 0;
+        uint32_t total = 0, max_own = 0;
         cudaMemcpyAsync(&total, c->off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
+        cudaMemcpyAsync(&max_own, c->d_max_own, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
         if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "rebuild sync");
+        // widen the staging rows from the next build on, so that particles
+        // rarely take the second walk (at most 256 entries a row)
+        queue = max_own > c->stage_w;
+        if (max_own > c->stage_w && c->stage_w < 256)
+            c->stage_want = std::min<uint32_t>(256, (max_own + max_own / 4 + 15) & ~15u);
         if ((size_t)total > c->list_cap) {
             size_t want = (size_t)total + total / 2 + 1024;
             if (want > 0xffffffffull) want = 0xffffffffull;
@@ -356,7 +391,7 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
             la = list_args(c);
         }
     }
-    build_lists_fill(c->s, la, is_mixed(c), &c->launches);
+    build_lists_fill(c->s, la, is_mixed(c), queue, &c->launches);
     t_end(c, 2, ev);
     c->grid_valid = true;
     c->rhs_valid = false;
@@ -547,7 +582,7 @@ static void free_ctx(sph_ctx *c) {
                   c->tkey, c->tstart, c->tend, c->bbox, c->level_mask,
                   c->cnt_tmp, c->d_dt, c->d_t, c->d_hmin, c->d_nonfinite,
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
-                  c->d_overflow, c->longq, c->d_nlong, c->stage, c->lqueue,
+                  c->d_overflow, c->longq, c->d_nlong, c->stage, c->lqueue, c->d_max_own,
                   c->d_nlq, c->tmp_a, c->tmp_b,
                   c->closest, c->d_mass, c->d_mass_part, c->wp, c->wugx,
                   c->wugy, c->d_aux};
@@ -888,7 +923,8 @@ static sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
     ok = ok && dalloc(&c->lvl, N) && dalloc(&c->pk, N) && dalloc(&c->own, N) &&
          dalloc(&c->rev, N) && dalloc(&c->off, N + 1) &&
          dalloc(&c->longq, N) && dalloc(&c->d_nlong, 1) &&
-         dalloc(&c->stage, N * 64) && dalloc(&c->lqueue, N) && dalloc(&c->d_nlq, 1);
+         dalloc(&c->stage, N * c->stage_w) && dalloc(&c->lqueue, N) &&
+         dalloc(&c->d_nlq, 1) && dalloc(&c->d_max_own, 1);
     ok = ok && dalloc(&c->tmp_a, N + 1) && dalloc(&c->tmp_b, N + 1) &&
          dalloc(&c->closest, N) && dalloc(&c->d_mass, 2) &&
          dalloc(&c->d_mass_part, 256) && dalloc(&c->d_aux, 4);

@@ -100,7 +100,8 @@ void compute_levels(const Domain &dom, double c0, Level *lev);
 void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
                  int lmax, int mbits, const Level *lev, const double *x,
                  const double *y, const double *h, uint64_t *skey,
-                 uint32_t *perm, uint32_t *level_mask, int *bbox);
+                 uint32_t *perm, uint32_t *level_mask, int *bbox,
+                 uint32_t *zero = nullptr);   // zero[i] = 0 for i < n
 // Stable LSD radix sort of (skey, perm) over the low `bits` bits.
 void radix_sort(cudaStream_t s, int n, int bits, uint64_t *key,
                 uint32_t *val, SortScratch &sc, int *launches);
@@ -110,6 +111,10 @@ void exclusive_scan(cudaStream_t s, const uint32_t *in, uint32_t *out,
                     int n, uint32_t *total_dev, SortScratch &sc,
                     int *launches);
 size_t scan_scratch_elems(size_t n);
+// off[i] = exclusive scan of own[i] + rev[i], off[n] = total, rev zeroed,
+// in one launch; false (nothing done) if n is too large for one block.
+bool list_offsets_small(cudaStream_t s, const uint32_t *own, uint32_t *rev,
+                        uint32_t *off, int n, int *launches);
 // Tile-count entries radix_sort needs in SortScratch::counts for n keys.
 size_t radix_counts_elems(size_t n);
 void build_cell_table(cudaStream_t s, int n, const uint64_t *skey,
@@ -126,5 +131,38 @@ struct GatherList {
 };
 void gather_by_perm(cudaStream_t s, int n, const uint32_t *perm,
                     const GatherList &g, int *launches);
+// gather_by_perm fused with the insertion of each cell's start into the
+// table (keys reset to EMPTY_KEY beforehand).
+void gather_insert(cudaStream_t s, int n, const uint32_t *perm,
+                   const GatherList &g, const uint64_t *skey, uint64_t *tkey,
+                   uint32_t *tstart, uint32_t tmask, int *launches);
+struct RebuildReset {
+    int *bbox;
+    uint32_t *level_mask;
+    uint64_t *tkey;
+    uint32_t tslots;
+    uint32_t *zero[4];
+};
+void launch_rebuild_reset(cudaStream_t s, const RebuildReset &r, int *launches);
+
+// End of the cell of sorted particle i, if i is its last particle: the
+// cell's table slot receives i + 1.
+__device__ __forceinline__ void table_mark_end(int i, int n,
+                                               const uint64_t *skey,
+                                               const uint64_t *tkey,
+                                               uint32_t *tend, uint32_t tmask) {
+    const uint64_t k = skey[i];
+    if (i + 1 < n && skey[i + 1] == k) return;
+    uint32_t slot = hash_slot(k, tmask);
+    for (uint32_t it = 0; it <= tmask; ++it) {
+        const uint64_t t = tkey[slot];
+        if (t == k) {
+            tend[slot] = (uint32_t)(i + 1);
+            return;
+        }
+        if (t == EMPTY_KEY) return;
+        slot = (slot + 1) & tmask;
+    }
+}
 
 }  // namespace sph

@@ -18,21 +18,21 @@ struct WallView {
 // Calls f(k, dx, dy, r2) for every wall particle k with r_ik < 3 max(h_i,
 // h_k) (membership by the FP32 anchor filter with the FP64 predicate in
 // its band), (dx, dy) = r_i - r_k by FP64 minimum image.  With a team of T
-// threads, lane `lane` takes every T-th wall cell.  pi: particle i's
-// anchor data.
+// threads (lanes `mask`), the team looks the wall cells up together and
+// lane `lane` takes every T-th wall of each cell.  pi: particle i's anchor
+// data.
 template <int T, class F>
 __device__ __forceinline__ void for_each_wall(const WallView &w,
                                               const Domain &d,
                                               const Anchor &an,
                                               const float4 &pi, double xi,
                                               double yi, double hi, int lane,
-                                              F &&f) {
+                                              unsigned mask, F &&f) {
     if (w.n <= 0) return;
     const float2 q = anchor_rel(an, pi);
-    int c = 0;
-    for_each_cell(w.g, d, 0, q.x, q.y, pi.z, [&](uint32_t s, uint32_t e) {
-        if ((c++ & (T - 1)) != lane) return;
-        for (uint32_t k = s; k < e; ++k) {
+    for_each_cell_team<T>(w.g, d, 0, q.x, q.y, pi.z, lane, mask,
+                          [&](uint32_t s, uint32_t e) {
+        for (uint32_t k = s + lane; k < e; k += T) {
             float fx, fy, fr2;
             if (!pred_mixed(d, an, pi, __ldg(&w.pk[k]), xi, yi, hi, w.x, w.y,
                             w.h, (int)k, fx, fy, fr2))
