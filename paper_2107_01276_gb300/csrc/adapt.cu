@@ -459,11 +459,10 @@ static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
 void launch_bg_mref(cudaStream_t s, const BgArgs &a) {
     if (a.n <= 0) return;
     cudaMemsetAsync(a.nqueue, 0, sizeof(uint32_t), s);
-    switch (team_size(a.n)) {
-    case 16: k_bg_mref<16><<<nblk(a.n * 16, 128), 128, 0, s>>>(a); break;
-    case 4: k_bg_mref<4><<<nblk(a.n * 4, 128), 128, 0, s>>>(a); break;
-    default: k_bg_mref<1><<<nblk(a.n, 128), 128, 0, s>>>(a); break;
-    }
+    with_team(a.n, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        k_bg_mref<T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
+    });
     k_bg_nearest<<<152, 256, 0, s>>>(a);
 }
 void launch_split_flag(cudaStream_t s, int n, const double *m,
@@ -481,11 +480,10 @@ void launch_split_emit(cudaStream_t s, const SplitArgs &a) {
 }
 void launch_merge(cudaStream_t s, const MergeArgs &a) {
     if (a.n <= 0) return;
-    switch (team_size(a.n)) {
-    case 16: k_merge_closest<16><<<nblk(a.n * 16, 128), 128, 0, s>>>(a); break;
-    case 4: k_merge_closest<4><<<nblk(a.n * 4, 128), 128, 0, s>>>(a); break;
-    default: k_merge_closest<1><<<nblk(a.n, 128), 128, 0, s>>>(a); break;
-    }
+    with_team(a.n, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        k_merge_closest<T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
+    });
     k_merge_apply<<<nblk(a.n, 128), 128, 0, s>>>(a);
 }
 void launch_compact(cudaStream_t s, int n, const uint32_t *alive,
@@ -500,11 +498,7 @@ static void shift_round_T(cudaStream_t s, const ShiftArgs &a) {
 }
 template <typename R>
 static void shift_round_R(cudaStream_t s, const ShiftArgs &a) {
-    switch (team_size(a.n)) {
-    case 16: shift_round_T<R, 16>(s, a); break;
-    case 4: shift_round_T<R, 4>(s, a); break;
-    default: shift_round_T<R, 1>(s, a); break;
-    }
+    with_team(a.n, [&](auto t) { shift_round_T<R, decltype(t)::value>(s, a); });
 }
 void launch_shift_round(cudaStream_t s, const ShiftArgs &a, bool mixed) {
     if (a.n <= 0) return;
@@ -520,11 +514,7 @@ static void h_update_T(cudaStream_t s, const ShiftArgs &a) {
 }
 template <typename R>
 static void h_update_R(cudaStream_t s, const ShiftArgs &a) {
-    switch (team_size(a.n)) {
-    case 16: h_update_T<R, 16>(s, a); break;
-    case 4: h_update_T<R, 4>(s, a); break;
-    default: h_update_T<R, 1>(s, a); break;
-    }
+    with_team(a.n, [&](auto t) { h_update_T<R, decltype(t)::value>(s, a); });
 }
 void launch_h_update(cudaStream_t s, const ShiftArgs &a, bool mixed) {
     if (a.n <= 0) return;

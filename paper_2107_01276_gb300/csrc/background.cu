@@ -181,11 +181,10 @@ __global__ void k_minmax_pos(int n, const double *v, unsigned long long *out) {
 static inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 
 #define SPH_TEAM_LAUNCH(KER, n, args, s)                                      \
-    switch (team_size(n)) {                                                   \
-    case 16: KER<16><<<nblk((long long)(n) * 16, 128), 128, 0, s>>>(args); break; \
-    case 4: KER<4><<<nblk((long long)(n) * 4, 128), 128, 0, s>>>(args); break;    \
-    default: KER<1><<<nblk((n), 128), 128, 0, s>>>(args); break;              \
-    }
+    with_team(n, [&](auto t_) {                                               \
+        constexpr int T_ = decltype(t_)::value;                               \
+        KER<T_><<<nblk((long long)(n) * T_, 128), 128, 0, s>>>(args);         \
+    });
 
 void launch_vorticity(cudaStream_t s, const VortArgs &a) {
     cudaMemsetAsync(a.wmax, 0, sizeof(unsigned long long), s);

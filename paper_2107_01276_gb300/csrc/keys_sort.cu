@@ -202,37 +202,44 @@ __global__ void __launch_bounds__(RS_THREADS)
     }
 }
 
-// Small sets (n <= RSS_MAX): every pass in one block of 32 warps.  Warp w
-// owns a contiguous chunk of the input; the per-(warp, digit) counts,
-// scanned digit-major, give each warp's scatter base, and the warp ranks
-// its chunk 32 keys at a time with __match_any_sync, so the sort is stable
-// exactly like the tiled form.  Ends with the result in (ka, va).
+// Small sets (n <= RSS_MAX): every pass in one block of 32 warps, keys
+// and values staged in shared memory.  Warp w owns a contiguous chunk; the
+// per-(warp, digit) counts, scanned digit-major, give each warp's scatter
+// base, and the warp ranks its chunk 32 keys at a time with
+// __match_any_sync, so the sort is stable exactly like the tiled form.
+// Intermediate passes scatter into (kb, vb) and reload; the last pass
+// scatters into (ka, va).
 constexpr int RSS_THREADS = 1024;
 constexpr int RSS_WARPS = RSS_THREADS / 32;
-constexpr int RSS_MAX = 32768;
+constexpr int RSS_MAX = 16384;
 
 __global__ void __launch_bounds__(RSS_THREADS)
     k_radix_small(int n, int passes, uint64_t *ka, uint32_t *va, uint64_t *kb,
                   uint32_t *vb) {
+    extern __shared__ uint64_t sk[];          // n keys, then n values
+    uint32_t *sv = (uint32_t *)(sk + n);
     __shared__ uint32_t cnt[RSS_WARPS][256];
     __shared__ uint32_t dtot[256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int chunk = (((n + RSS_WARPS - 1) / RSS_WARPS) + 31) & ~31;
     const int wb = w * chunk, we = min(n, wb + chunk);
+    for (int e = threadIdx.x; e < n; e += RSS_THREADS) {
+        sk[e] = ka[e];
+        sv[e] = va[e];
+    }
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
-        const uint64_t *kin = (p & 1) ? kb : ka;
-        const uint32_t *vin = (p & 1) ? vb : va;
-        uint64_t *kout = (p & 1) ? ka : kb;
-        uint32_t *vout = (p & 1) ? va : vb;
+        const bool last = p == passes - 1;
+        uint64_t *kout = last ? ka : kb;
+        uint32_t *vout = last ? va : vb;
         for (int t = threadIdx.x; t < RSS_WARPS * 256; t += RSS_THREADS)
             (&cnt[0][0])[t] = 0;
         __syncthreads();
         for (int b = wb; b < we; b += 32) {
             const int e = b + lane;
             const bool ok = e < we;
-            const int d = ok ? (int)((kin[e] >> shift) & 255u) : 256;
+            const int d = ok ? (int)((sk[e] >> shift) & 255u) : 256;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             uint32_t before = 0;
             if (ok) before = cnt[w][d];
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(RSS_THREADS)
             uint64_t k = 0;
             int d = 256;
             if (ok) {
-                k = kin[e];
+                k = sk[e];
                 d = (int)((k >> shift) & 255u);
             }
             const unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -291,17 +298,35 @@ __global__ void __launch_bounds__(RSS_THREADS)
             if (ok) {
                 const uint32_t pos = before + __popc(peers & lt);
                 kout[pos] = k;
-                vout[pos] = vin[e];
+                vout[pos] = sv[e];
             }
         }
         __syncthreads();
-    }
-    if (passes & 1) {                       // result is in (kb, vb)
-        for (int e = threadIdx.x; e < n; e += RSS_THREADS) {
-            ka[e] = kb[e];
-            va[e] = vb[e];
+        if (!last) {
+            for (int e = threadIdx.x; e < n; e += RSS_THREADS) {
+                sk[e] = kb[e];
+                sv[e] = vb[e];
+            }
+            __syncthreads();
         }
     }
+}
+
+// The dynamic shared-memory limit of k_radix_small, raised once per device.
+static bool radix_small_ready() {
+    static signed char ok[64];   // 0 unknown, 1 ready, -1 unavailable
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return false;
+    }
+    if (ok[dev] == 0) {
+        ok[dev] = cudaFuncSetAttribute(k_radix_small,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       RSS_MAX * 12) == cudaSuccess ? 1 : -1;
+        if (ok[dev] < 0) cudaGetLastError();
+    }
+    return ok[dev] == 1;
 }
 
 size_t radix_counts_elems(size_t n) {
@@ -311,9 +336,9 @@ size_t radix_counts_elems(size_t n) {
 void radix_sort(cudaStream_t s, int n, int bits, uint64_t *key,
                 uint32_t *val, SortScratch &sc, int *launches) {
     if (n <= 1 || bits <= 0) return;
-    if (n <= RSS_MAX) {
-        k_radix_small<<<1, RSS_THREADS, 0, s>>>(n, (bits + 7) / 8, key, val,
-                                               sc.key_alt, sc.val_alt);
+    if (n <= RSS_MAX && radix_small_ready()) {
+        k_radix_small<<<1, RSS_THREADS, (size_t)n * 12, s>>>(
+            n, (bits + 7) / 8, key, val, sc.key_alt, sc.val_alt);
         *launches += 1;
         return;
     }
@@ -447,10 +472,16 @@ __global__ void __launch_bounds__(SS_THREADS)
                  uint32_t *total_dev, int write_total_at_n) {
     __shared__ uint32_t ws[SS_THREADS / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int chunk = (n + SS_THREADS - 1) / SS_THREADS;
-    const int b = threadIdx.x * chunk, e = min(n, b + chunk);
+    const int chunk = (n + SS_THREADS - 1) / SS_THREADS;   // <= 32
+    const int b = threadIdx.x * chunk;
+    uint32_t v[32];
     uint32_t sum = 0;
-    for (int i = b; i < e; ++i) sum += in[i] + (rev ? rev[i] : 0u);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const int i = b + k;
+        v[k] = (k < chunk && i < n) ? in[i] + (rev ? rev[i] : 0u) : 0u;
+        sum += v[k];
+    }
     uint32_t x = sum;
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -468,11 +499,14 @@ __global__ void __launch_bounds__(SS_THREADS)
     }
     __syncthreads();
     uint32_t pre = (w > 0 ? ws[w - 1] : 0u) + x - sum;
-    for (int i = b; i < e; ++i) {
-        const uint32_t v = in[i] + (rev ? rev[i] : 0u);
-        if (rev) rev[i] = 0;
-        out[i] = pre;
-        pre += v;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const int i = b + k;
+        if (k < chunk && i < n) {
+            if (rev) rev[i] = 0;
+            out[i] = pre;
+            pre += v[k];
+        }
     }
     if (threadIdx.x == SS_THREADS - 1) {
         if (total_dev) *total_dev = ws[SS_THREADS / 32 - 1];

@@ -292,10 +292,10 @@ void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
         cudaMemsetAsync(a.off, 0, sizeof(uint32_t), s);
         return;
     }
-    const int T = team_size(n);
-    if (T == 16) k_list_gather<16><<<nblk(n * 16, 128), 128, 0, s>>>(a);
-    else if (T == 4) k_list_gather<4><<<nblk(n * 4, 128), 128, 0, s>>>(a);
-    else k_list_gather<1><<<nblk(n, 128), 128, 0, s>>>(a);
+    with_team(n, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        k_list_gather<T><<<nblk(n * T, 128), 128, 0, s>>>(a);
+    });
     *launches += 1;
     if (list_offsets_small(s, a.own, a.rev, a.off, n, launches)) return;
     k_list_total<<<nblk(n, 256), 256, 0, s>>>(n, a.own, a.rev, tot_tmp);
@@ -311,11 +311,10 @@ void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,
     (void)mixed;
     const int n = a.n;
     if (n <= 0) return;
-    switch (team_size(n)) {
-    case 16: k_list_place<16><<<nblk(n * 16, 128), 128, 0, s>>>(a); break;
-    case 4: k_list_place<4><<<nblk(n * 4, 128), 128, 0, s>>>(a); break;
-    default: k_list_place<1><<<nblk(n, 128), 128, 0, s>>>(a); break;
-    }
+    with_team(n, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        k_list_place<T><<<nblk(n * T, 128), 128, 0, s>>>(a);
+    });
     if (queue) k_list_fill_queue<16><<<152 * 4, 128, 0, s>>>(a);
     k_list_sort_rev<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.own, a.list, a.cap,
                                                   a.longq, a.nlong);

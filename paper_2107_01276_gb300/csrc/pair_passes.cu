@@ -375,20 +375,18 @@ static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
 template <typename R>
 void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a) {
     if (a.n <= 0) return;
-    switch (team_size(a.n)) {
-    case 16: k_pass_a<R, 16><<<nblk(a.n * 16, 128), 128, 0, s>>>(a); break;
-    case 4: k_pass_a<R, 4><<<nblk(a.n * 4, 128), 128, 0, s>>>(a); break;
-    default: k_pass_a<R, 1><<<nblk(a.n, 128), 128, 0, s>>>(a); break;
-    }
+    with_team(a.n, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        k_pass_a<R, T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
+    });
 }
 template <typename R>
 void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a) {
     if (a.n <= 0) return;
-    switch (team_size(a.n)) {
-    case 16: k_pass_b<R, 16><<<nblk(a.n * 16, 128), 128, 0, s>>>(a); break;
-    case 4: k_pass_b<R, 4><<<nblk(a.n * 4, 128), 128, 0, s>>>(a); break;
-    default: k_pass_b<R, 1><<<nblk(a.n, 128), 128, 0, s>>>(a); break;
-    }
+    with_team(a.n, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        k_pass_b<R, T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
+    });
 }
 template <typename R>
 void launch_pec(cudaStream_t s, const PecArgs<R> &a) {

@@ -146,6 +146,10 @@ struct sph_ctx {
     uint32_t *d_total = nullptr;
 
     bool grid_valid = false, rhs_valid = false, have_dt = false;
+    // list sizing: entry total and particle count of the last build that
+    // read its total back
+    uint32_t last_total = 0;
+    int last_total_n = 0;
     long long steps = 0;
     int launches = 0;
     bool timing = false;
@@ -281,10 +285,18 @@ static ListArgs list_args(sph_ctx *c) {
 }
 
 // exact: read the list total back (one synchronisation) and grow the list
-// buffer before filling; otherwise entries past the capacity are dropped
-// and flagged, and the flag is checked at the next synchronising call.
+// buffer before filling -- unless the last total read back was at most
+// half the buffer and the particle count is within 10 % of the one it was
+// read at, where the build runs without the synchronisation.  Without it,
+// entries past the capacity are dropped and flagged, and the flag is
+// checked at the next synchronising call (which then reports
+// SPH_ECAPACITY and forces an exact build).
 static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
     const int n = c->n;
+    if (exact && c->last_total > 0 && (size_t)c->last_total * 2 <= c->list_cap &&
+        (long long)n * 10 <= (long long)c->last_total_n * 11 &&
+        (long long)n * 10 >= (long long)c->last_total_n * 9)
+        exact = false;
     if (c->stage_want > c->stage_w) {
         uint32_t *ns = nullptr;
         if (dalloc(&ns, (size_t)c->cap * c->stage_want)) {
@@ -370,6 +382,8 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
         cudaMemcpyAsync(&total, c->off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
         cudaMemcpyAsync(&max_own, c->d_max_own, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
         if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "rebuild sync");
+        c->last_total = total;
+        c->last_total_n = n;
         // widen the staging rows from the next build on, so that particles
         // rarely take the second walk (at most 256 entries a row)
         queue = max_own > c->stage_w;
@@ -1216,6 +1230,18 @@ static sph_status bg_iteration(sph_ctx *c, sph_ctx *b, bool vort,
     return SPH_OK;
 }
 
+// Reports (and clears) a neighbour-list overflow of a build that ran
+// without its sizing synchronisation; synchronises.
+static sph_status check_overflow(sph_ctx *c, const char *who) {
+    int ovf = 0;
+    cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, who);
+    if (!ovf) return SPH_OK;
+    cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
+    c->last_total = 0;   // the next build sizes its lists exactly
+    return fail(c, SPH_ECAPACITY, std::string(who) + ": neighbour list overflow");
+}
+
 // ================================================================ C ABI ==
 extern "C" {
 
@@ -1402,6 +1428,7 @@ sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
         *t_out = t;
         if (ovf) {
             cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
+            c->last_total = 0;   // the next build sizes its lists exactly
             return fail(c, SPH_ECAPACITY, "sph_step: neighbour list overflow during the steps");
         }
         if (bad) return fail(c, SPH_ENONFINITE, "sph_step: non-finite rate");
@@ -1514,9 +1541,16 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     c->rhs_valid = false;
     double mass[2] = {0, 0};
     uint32_t nfb = 0;
+    int ovf = 0;
     cudaMemcpyAsync(mass, c->d_mass, sizeof(mass), cudaMemcpyDeviceToHost, c->s);
     cudaMemcpyAsync(&nfb, c->d_aux, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
     if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_adapt");
+    if (ovf) {
+        cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
+        c->last_total = 0;   // the next build sizes its lists exactly
+        return fail(c, SPH_ECAPACITY, "sph_adapt: neighbour list overflow during the call");
+    }
     z.mass_before = mass[0];
     z.mass_after = mass[1];
     z.n_bg_nearest = nfb;
@@ -1563,6 +1597,7 @@ sph_status sph_background(sph_ctx *c, int iterations, sph_bg_stats *out) {
         return st;
     }
     c->bg_next_id = b->next_id;
+    if ((st = check_overflow(b, "sph_background")) != SPH_OK) return fail(c, st, b->err);
     uint32_t cnt[2] = {0, 0};
     cudaMemcpyAsync(cnt, b->d_aux, sizeof(cnt), cudaMemcpyDeviceToHost, c->s);
     if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_background");
@@ -1618,6 +1653,7 @@ sph_status sph_read(sph_ctx *c, sph_field field, void *dst, long long cap,
     case SPH_F_BETA: case SPH_F_PAVG: case SPH_F_DRX: case SPH_F_DRY:
     case SPH_F_DPDT: case SPH_F_DUDT: case SPH_F_DVDT: {
         if (!c->rhs_valid) return fail(c, SPH_ESTATE, "sph_read: no right-hand side at this state");
+        if ((st = check_overflow(c, "sph_read")) != SPH_OK) return st;
         if ((st = need(n)) != SPH_OK) return st;
         const void *srcs[] = {c->beta, c->pavg, c->drx, c->dry, c->dpdt, c->dudt, c->dvdt};
         return read_R(c, srcs[field - SPH_F_BETA], (double *)dst, n);
@@ -1659,7 +1695,10 @@ sph_status sph_read(sph_ctx *c, sph_field field, void *dst, long long cap,
         cudaMemcpyAsync(off.data(), c->off, sizeof(uint32_t) * (n + 1), cudaMemcpyDeviceToHost, c->s);
         cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
         if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
-        if (ovf) return fail(c, SPH_ECAPACITY, "sph_read: neighbour list overflow");
+        if (ovf) {
+            c->last_total = 0;
+            return fail(c, SPH_ECAPACITY, "sph_read: neighbour list overflow");
+        }
         const uint32_t total = off[n];
         if (field == SPH_F_NEIGH_OFF) {
             if ((st = need(n + 1)) != SPH_OK) return st;

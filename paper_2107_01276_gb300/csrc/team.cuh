@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace sph {
 
 template <int T>
@@ -41,12 +43,26 @@ __device__ __forceinline__ V team_min(unsigned mask, V v) {
     return v;
 }
 
-// Team size for n particles: enough threads to fill the GPU's 152 SMs a
-// few times over, at most 16 lanes per particle.
+// Team size for n particles: a whole warp per particle while that still
+// fits the GPU once (152 SMs x 64 resident warps), then 16 lanes while a
+// team still fills it a few times over, 4 up to 300k, 1 beyond.
 inline int team_size(int n) {
+    if (n <= 152 * 64) return 32;
     if (n <= 40000) return 16;
     if (n <= 300000) return 4;
     return 1;
+}
+
+// Host-side dispatch: f(std::integral_constant<int, T>()) with T =
+// team_size(n).
+template <class F>
+inline void with_team(int n, F &&f) {
+    switch (team_size(n)) {
+    case 32: f(std::integral_constant<int, 32>()); break;
+    case 16: f(std::integral_constant<int, 16>()); break;
+    case 4: f(std::integral_constant<int, 4>()); break;
+    default: f(std::integral_constant<int, 1>()); break;
+    }
 }
 
 }  // namespace sph
