@@ -57,8 +57,14 @@ __global__ void __launch_bounds__(128) k_bg_mref(BgArgs a) {
     const float4 pi = a.pk[i];
     const float2 q = anchor_rel(a.an, pi);
     double best = 1e308;
+    // Levels come finest first, so the running minimum soon exceeds no
+    // coarse cell's least m_ref: a lane skips its share of a cell whose
+    // least rho0 ds^2 is not below its own running minimum (those
+    // candidates cannot lower the minimum; rounding is monotone in ds).
     for_each_cell_team<T>(a.g, a.d, 0, q.x, q.y, pi.z, tm.lane, tm.mask,
                           [&](uint32_t s, uint32_t e) {
+        const double dmin = __ldg(&a.bcmin[s]);
+        if (__dmul_rn(__dmul_rn(a.rho0, dmin), dmin) >= best) return;
         for (uint32_t b = s + tm.lane; b < e; b += T) {
             float fx, fy, fr2;
             if (pred_mixed(a.d, a.an, pi, __ldg(&a.bpk[b]), xi, yi, hi, a.bx,
@@ -189,11 +195,21 @@ __global__ void __launch_bounds__(128) k_merge_closest(MergeArgs a) {
     const double mi = m[i], mxi = mmax[i];
     if (mxi > 0.0 && !(mi > mxi)) {
         const double xi = x[i], yi = y[i], hi = h[i];
+        const float4 pi = a.pk[i];
         for (uint32_t k = a.off[i] + tm.lane; k < a.off[i + 1]; k += T) {
             const int j = (int)a.list[k];
             if (j == i) continue;
             const double mxj = mmax[j], mj = m[j];
             if (!(mxj > 0.0) || mj > mxj) continue;
+            {   // FP32 pre-test on the anchor separation: its error is
+                // far below the 1e-4 relative margin, so no admissible
+                // pair is dropped; the FP64 test below decides
+                const float4 pj = __ldg(&a.pk[j]);
+                float fx, fy;
+                anchor_sep(a.an, pi, pj, fx, fy);
+                const float hhf = 0.5f * (pi.z + pj.z);
+                if (fmaf(fx, fx, fy * fy) > 1.0001f * hhf * hhf) continue;
+            }
             double dx, dy, r2;
             sep_rn(a.d, xi, yi, x[j], y[j], dx, dy, r2);
             const double hh = __dmul_rn(0.5, __dadd_rn(hi, h[j]));
@@ -523,11 +539,16 @@ void launch_h_update(cudaStream_t s, const ShiftArgs &a, bool mixed) {
     else
         h_update_R<double>(s, a);
 }
-void launch_mass_sum(cudaStream_t s, int n, const double *m, double *part,
-                     double *out) {
+int launch_mass_sum(cudaStream_t s, int n, const double *m, double *part,
+                    double *out) {
     int nb = std::max(1, std::min(nblk(n, 256), 256));
+    if (nb == 1) {   // small sets: the block's sum is the total
+        k_mass_partial<<<1, 256, 0, s>>>(n, m, out);
+        return 1;
+    }
     k_mass_partial<<<nb, 256, 0, s>>>(n, m, part);
     k_mass_final<<<1, 32, 0, s>>>(nb, part, out);
+    return 2;
 }
 
 }  // namespace sph

@@ -20,6 +20,8 @@ struct BgArgs {
     double *mmin, *mmax;
     int nb;
     const double *bx, *by, *bh, *bds;   // background, sorted by its keys
+    const double *bcmin;        // per background cell (at its first
+                                // particle): least ds of the cell
     const int64_t *bid;         // background load index
     Anchor an;
     const float4 *pk, *bpk;     // anchor data of fluid and background
@@ -43,6 +45,8 @@ struct MergeArgs {
     double *f[NSTATE];
     const int64_t *id;
     const uint32_t *off, *list;
+    Anchor an;
+    const float4 *pk;           // anchor data at the current positions
     int *closest;
     uint32_t *alive;
 };
@@ -81,7 +85,8 @@ void launch_compact(cudaStream_t s, int n, const uint32_t *alive,
                     const uint32_t *pos, const CompactArgs &c);
 void launch_shift_round(cudaStream_t s, const ShiftArgs &a, bool mixed);
 void launch_h_update(cudaStream_t s, const ShiftArgs &a, bool mixed);
-void launch_mass_sum(cudaStream_t s, int n, const double *m, double *part,
+// Returns the number of kernels launched.
+int launch_mass_sum(cudaStream_t s, int n, const double *m, double *part,
                      double *out);
 
 }  // namespace sph

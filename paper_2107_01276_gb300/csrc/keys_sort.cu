@@ -629,6 +629,26 @@ __global__ void k_rebuild_reset(RebuildReset r) {
     for (uint32_t k = t0; k < r.tslots; k += st) r.tkey[k] = EMPTY_KEY;
 }
 
+// Smallest value of v over each cell of a sorted set, stored at the cell's
+// first particle (other entries are left as they are).
+__global__ void k_cell_min(int n, const uint64_t *__restrict__ skey,
+                           const double *__restrict__ v, double *cmin) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t k = skey[i];
+    if (i > 0 && skey[i - 1] == k) return;
+    double m = v[i];
+    for (int j = i + 1; j < n && skey[j] == k; ++j) m = fmin(m, v[j]);
+    cmin[i] = m;
+}
+
+void launch_cell_min(cudaStream_t s, int n, const uint64_t *skey,
+                     const double *v, double *cmin, int *launches) {
+    if (n <= 0) return;
+    k_cell_min<<<(n + 255) / 256, 256, 0, s>>>(n, skey, v, cmin);
+    *launches += 1;
+}
+
 void launch_rebuild_reset(cudaStream_t s, const RebuildReset &r, int *launches) {
     int nb = (int)std::min<uint32_t>((r.tslots + 255) / 256, 608u);
     if (nb < 1) nb = 1;

@@ -294,12 +294,31 @@ __global__ void k_pec(PecArgs<R> a) {
     if (i >= a.n) return;
     const double dt = *a.dt;
     const double fdt = __dmul_rn(a.f, dt);
-    const double un = __dadd_rn(a.u0[i], __dmul_rn(fdt, (double)a.dudt[i]));
-    const double vn = __dadd_rn(a.v0[i], __dmul_rn(fdt, (double)a.dvdt[i]));
+    double x0, y0, u0, v0, p0;
+    if (a.save) {
+        x0 = a.x[i];
+        y0 = a.y[i];
+        u0 = a.u[i];
+        v0 = a.v[i];
+        p0 = a.p[i];
+        ((double *)a.x0)[i] = x0;
+        ((double *)a.y0)[i] = y0;
+        ((double *)a.u0)[i] = u0;
+        ((double *)a.v0)[i] = v0;
+        ((double *)a.p0)[i] = p0;
+    } else {
+        x0 = a.x0[i];
+        y0 = a.y0[i];
+        u0 = a.u0[i];
+        v0 = a.v0[i];
+        p0 = a.p0[i];
+    }
+    const double un = __dadd_rn(u0, __dmul_rn(fdt, (double)a.dudt[i]));
+    const double vn = __dadd_rn(v0, __dmul_rn(fdt, (double)a.dvdt[i]));
     const double utx = __dadd_rn(un, __ddiv_rn((double)a.drx[i], dt));
     const double uty = __dadd_rn(vn, __ddiv_rn((double)a.dry[i], dt));
-    double xn = __dadd_rn(a.x0[i], __dmul_rn(fdt, utx));
-    double yn = __dadd_rn(a.y0[i], __dmul_rn(fdt, uty));
+    double xn = __dadd_rn(x0, __dmul_rn(fdt, utx));
+    double yn = __dadd_rn(y0, __dmul_rn(fdt, uty));
     if (a.d.periodic[0]) {
         if (xn >= a.d.hi[0])
             xn = __dsub_rn(xn, a.d.L[0]);
@@ -316,7 +335,7 @@ __global__ void k_pec(PecArgs<R> a) {
     a.y[i] = yn;
     a.u[i] = un;
     a.v[i] = vn;
-    a.p[i] = __dadd_rn(a.p0[i], __dmul_rn(fdt, (double)a.dpdt[i]));
+    a.p[i] = __dadd_rn(p0, __dmul_rn(fdt, (double)a.dpdt[i]));
 }
 
 // ---------------------------------------------------------- time step ----
@@ -337,8 +356,9 @@ __global__ void k_min_h(int n, const double *__restrict__ h,
 }
 
 // Eq. timestep: dt = min(0.25 h_min/(U + c_s), 0.125 h_min^2/nu).
-__global__ void k_dt(const unsigned long long *hmin_bits, double U, double cs,
-                     double nu, double *dt, double *tacc, int nsteps) {
+__device__ __forceinline__ void k_dt_body(const unsigned long long *hmin_bits,
+                                          double U, double cs, double nu,
+                                          double *dt, double *tacc, int nsteps) {
     const double hmin = __longlong_as_double((long long)*hmin_bits);
     double v = __dmul_rn(0.25, __ddiv_rn(hmin, __dadd_rn(U, cs)));
     if (nu > 0.0) {
@@ -349,6 +369,11 @@ __global__ void k_dt(const unsigned long long *hmin_bits, double U, double cs,
     if (tacc) {
         for (int s = 0; s < nsteps; ++s) *tacc = __dadd_rn(*tacc, v);
     }
+}
+
+__global__ void k_dt(const unsigned long long *hmin_bits, double U, double cs,
+                     double nu, double *dt, double *tacc, int nsteps) {
+    k_dt_body(hmin_bits, U, cs, nu, dt, tacc, nsteps);
 }
 
 // ---------------------------------------------------------- small utils --
@@ -400,21 +425,55 @@ template void launch_pec<double>(cudaStream_t, const PecArgs<double> &);
 template void launch_pec<float>(cudaStream_t, const PecArgs<float> &);
 
 void launch_wall_bc(cudaStream_t s, const WallBcArgs &a) {
-    if (a.w.n > 0) k_wall_bc<16><<<nblk(a.w.n * 16, 128), 128, 0, s>>>(a);
+    if (a.w.n <= 0) return;
+    with_team(a.w.n, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        k_wall_bc<T><<<nblk(a.w.n * T, 128), 128, 0, s>>>(a);
+    });
 }
 void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,
                     const uint32_t *list, const int64_t *id, int64_t *out) {
     if (n > 0) k_nbr_ids<<<nblk(n, 128), 128, 0, s>>>(n, off, list, id, out);
 }
-void launch_dt(cudaStream_t s, int n, const double *h,
-               unsigned long long *hmin_bits, double U, double cs, double nu,
-               double *dt, double *tacc, int nsteps) {
+// One block: h_min and the time step together (small sets).
+__global__ void __launch_bounds__(1024)
+    k_dt_small(int n, const double *__restrict__ h, double U, double cs,
+               double nu, unsigned long long *hmin_bits, double *dt,
+               double *tacc, int nsteps) {
+    __shared__ unsigned long long wm[32];
+    unsigned long long m = ~0ull;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(h[i]);
+        m = b < m ? b : m;
+    }
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t < m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wm[w] < m ? wm[w] : m;
+        *hmin_bits = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) k_dt_body(hmin_bits, U, cs, nu, dt, tacc, nsteps);
+}
+
+int launch_dt(cudaStream_t s, int n, const double *h,
+              unsigned long long *hmin_bits, double U, double cs, double nu,
+              double *dt, double *tacc, int nsteps) {
+    if (n <= 65536) {
+        k_dt_small<<<1, 1024, 0, s>>>(n, h, U, cs, nu, hmin_bits, dt, tacc, nsteps);
+        return 1;
+    }
     cudaMemsetAsync(hmin_bits, 0xff, sizeof(unsigned long long), s);
     int blocks = nblk(n, 256);
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
     k_min_h<<<blocks, 256, 0, s>>>(n, h, hmin_bits);
     k_dt<<<1, 1, 0, s>>>(hmin_bits, U, cs, nu, dt, tacc, nsteps);
+    return 2;
 }
 void launch_reset_bbox(cudaStream_t s, int *bbox, uint32_t *level_mask) {
     k_reset_bbox<<<1, MAX_LEVELS * 4, 0, s>>>(bbox, level_mask);

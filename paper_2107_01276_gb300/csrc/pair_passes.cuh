@@ -51,6 +51,8 @@ struct PecArgs {
     int n;
     Domain d;
     double f;                  // 0.5 predict, 1.0 correct
+    int save;                  // 1: the current x, y, u, v, p are the stage
+                               // start; copy them into x0..p0 first
     const double *dt;
     const double *x0, *y0, *u0, *v0, *p0;
     const R *dudt, *dvdt, *dpdt, *drx, *dry;
@@ -68,7 +70,8 @@ template <typename R> void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a);
 template <typename R> void launch_pec(cudaStream_t s, const PecArgs<R> &a);
 void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,
                     const uint32_t *list, const int64_t *id, int64_t *out);
-void launch_dt(cudaStream_t s, int n, const double *h,
+// Returns the number of kernels launched.
+int launch_dt(cudaStream_t s, int n, const double *h,
                unsigned long long *hmin_bits, double U, double cs, double nu,
                double *dt, double *tacc, int nsteps);
 void launch_reset_bbox(cudaStream_t s, int *bbox, uint32_t *level_mask);

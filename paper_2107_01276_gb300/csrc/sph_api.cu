@@ -51,6 +51,8 @@ struct StaticSet {
     float4 *pk = nullptr;       // anchor data (context anchor lattice)
     int pk_version = -1;        // anchor version pk was computed for
     int64_t *id = nullptr;                         // load index
+    double *cmin = nullptr;     // background: least ds of each cell, at the
+                                // cell's first particle
     uint64_t *key = nullptr, *tkey = nullptr;
     uint32_t *perm = nullptr, *tstart = nullptr, *tend = nullptr;
     int *bbox = nullptr;
@@ -63,7 +65,7 @@ struct StaticSet {
 };
 
 static void free_set(StaticSet *S) {
-    void *ps[] = {S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2], S->id, S->pk,
+    void *ps[] = {S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2], S->id, S->pk, S->cmin,
                   S->key, S->tkey, S->perm, S->tstart, S->tend, S->bbox,
                   S->mask, S->sc.key_alt, S->sc.val_alt, S->sc.counts,
                   S->sc.scan_tmp};
@@ -535,6 +537,7 @@ static void pec(sph_ctx *c, double f) {
     a.n = c->n;
     a.d = c->dom;
     a.f = f;
+    a.save = f < 1.0 ? 1 : 0;   // the predictor starts the step: keep x0..p0
     a.dt = c->d_dt;
     a.x0 = c->f[F_X0];
     a.y0 = c->f[F_Y0];
@@ -578,9 +581,8 @@ static void store_rho(sph_ctx *c) {
 }
 
 static void compute_dt(sph_ctx *c, double *tacc, int nsteps) {
-    launch_dt(c->s, c->n, c->f[F_H], c->d_hmin, c->prm.U_ref, c->prm.cs,
+    c->launches += launch_dt(c->s, c->n, c->f[F_H], c->d_hmin, c->prm.U_ref, c->prm.cs,
               c->prm.nu, c->d_dt, tacc, nsteps);
-    c->launches += 2;
     c->have_dt = true;
 }
 
@@ -655,6 +657,7 @@ static sph_status build_set_sorted(sph_ctx *c, StaticSet *S, long long n,
                   dalloc(&S->bbox, MAX_LEVELS * 4) && dalloc(&S->mask, 1) &&
                   dalloc(&S->sc.key_alt, N) && dalloc(&S->sc.val_alt, N);
         for (int k = 0; k < nex; ++k) ok = ok && dalloc(&S->ex[k], N);
+        ok = ok && dalloc(&S->cmin, N);
         size_t tiles = (N + 2047) / 2048;
         S->sc.counts_cap = 256 * tiles;
         S->sc.scan_cap = scan_scratch_elems(S->sc.counts_cap);
@@ -699,6 +702,7 @@ static sph_status build_set_sorted(sph_ctx *c, StaticSet *S, long long n,
     S->tmask = t - 1;
     build_cell_table(c->s, (int)n, S->key, S->tkey, S->tstart, S->tend, S->tmask,
                      &c->launches);
+    if (nex > 0) launch_cell_min(c->s, (int)n, S->key, S->ex[0], S->cmin, &c->launches);
     c->launches += 2;
     done(SPH_OK);
     S->n = (int)n;
@@ -1395,16 +1399,10 @@ sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
     c->err.clear();
     if (nsteps < 0) return fail(c, SPH_EINVAL, "sph_step: nsteps < 0");
     if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_step: no fluid particles loaded");
-    const size_t bytes = sizeof(double) * c->n;
     for (int s = 0; s < nsteps; ++s) {
         compute_dt(c, c->d_t, 1);
         sph_status st = rebuild(c, false, s == 0);
         if (st != SPH_OK) return st;
-        cudaMemcpyAsync(c->f[F_X0], c->f[F_X], bytes, cudaMemcpyDeviceToDevice, c->s);
-        cudaMemcpyAsync(c->f[F_Y0], c->f[F_Y], bytes, cudaMemcpyDeviceToDevice, c->s);
-        cudaMemcpyAsync(c->f[F_U0], c->f[F_U], bytes, cudaMemcpyDeviceToDevice, c->s);
-        cudaMemcpyAsync(c->f[F_V0], c->f[F_V], bytes, cudaMemcpyDeviceToDevice, c->s);
-        cudaMemcpyAsync(c->f[F_P0], c->f[F_P], bytes, cudaMemcpyDeviceToDevice, c->s);
         run_passes(c);
         run_pec(c, 0.5);
         st = rebuild(c, true, false);
@@ -1450,7 +1448,7 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     sph_status st = SPH_OK;
     cudaEvent_t ev;
     t_begin(c, 4, &ev);
-    launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass);
+    c->launches += launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass);
     // resolution from the background (section 3.3)
     ensure_set_pk(c, &c->wall);
     if (c->bg.n > 0) {
@@ -1476,6 +1474,7 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         a.by = c->bg.y;
         a.bh = c->bg.h;
         a.bds = c->bg.ex[0];
+        a.bcmin = c->bg.cmin;
         a.bid = c->bg.id;
         a.rho0 = c->prm.rho0;
         a.queue = c->tmp_b;
@@ -1504,6 +1503,8 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         a.list = c->list;
         a.closest = c->closest;
         a.alive = c->tmp_a;
+        a.an = c->an;
+        a.pk = c->pk;
         launch_merge(c->s, a);
         exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
         c->launches += 2;
@@ -1534,8 +1535,7 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     if ((st = rebuild(c, false)) != SPH_OK) return st;
     launch_h_update(c->s, shift_args(c), is_mixed(c));
     c->launches += 2;
-    launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass + 1);
-    c->launches += 4;
+    c->launches += launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass + 1);
     t_end(c, 4, ev);
     c->grid_valid = false;   // h changed since the last rebuild
     c->rhs_valid = false;

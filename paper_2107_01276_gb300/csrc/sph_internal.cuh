@@ -144,6 +144,9 @@ struct RebuildReset {
     uint32_t *zero[4];
 };
 void launch_rebuild_reset(cudaStream_t s, const RebuildReset &r, int *launches);
+// cmin[start of each cell] = min of v over the cell (sorted set).
+void launch_cell_min(cudaStream_t s, int n, const uint64_t *skey,
+                     const double *v, double *cmin, int *launches);
 
 // End of the cell of sorted particle i, if i is its last particle: the
 // cell's table slot receives i + 1.
