@@ -326,13 +326,24 @@ __global__ void __launch_bounds__(128) k_density_mbar(ShiftArgs a, int want_h) {
     sp.init(a.d, a.f[S_X], a.f[S_Y], a.pk, i);
     const R hi = (R)a.f[S_H][i], hinv = R(1) / hi;
     R rho = 0, msum = 0;
+    uint32_t cnt = 0;
     const uint32_t b = a.off[i], e = a.off[i + 1];
+    const bool check = want_h && a.filter;
+    const float4 pki = check ? a.pk[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const double xi = a.f[S_X][i], yi = a.f[S_Y][i], hid = a.f[S_H][i];
     for (uint32_t k = b + tm.lane; k < e; k += T) {
         const int j = (int)a.list[k];
         R dx, dy, r2;
         sp.get(a.d, a.an, a.f[S_X], a.f[S_Y], a.pk, j, dx, dy, r2);
-        rho += in.m[j] * qs_w<R>(sqrt(r2) * hinv);
+        rho += in.m[j] * qs_w<R>(sqrt(r2) * hinv);   // zero beyond 3 h_i
+        if (check) {
+            float fx, fy, fr2;
+            if (!pred_mixed(a.d, a.an, pki, __ldg(&a.pk[j]), xi, yi, hid,
+                            a.f[S_X], a.f[S_Y], a.f[S_H], j, fx, fy, fr2))
+                continue;
+        }
         msum += in.m[j];
+        ++cnt;
     }
     if (a.w.n > 0) {
         for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane, tm.mask,
@@ -342,11 +353,12 @@ __global__ void __launch_bounds__(128) k_density_mbar(ShiftArgs a, int want_h) {
     }
     rho = team_sum<T>(tm.mask, rho);
     msum = team_sum<T>(tm.mask, msum);
+    cnt = team_sum<T>(tm.mask, cnt);
     if (tm.lane != 0) return;
     rho *= sigma_norm<R>() * hinv * hinv;
     ((R *)a.rho)[i] = rho;
     if (want_h)
-        ((R *)a.hnew)[i] = (R)a.hdx * sqrt((msum / (R)(e - b)) / rho);
+        ((R *)a.hnew)[i] = (R)a.hdx * sqrt((msum / (R)cnt) / rho);
 }
 
 // Limited shift (Eqs. shift-deltar, shift-limit; walls included) and the

@@ -71,6 +71,9 @@ struct ShiftArgs {
     Anchor an;
     const float4 *pk;
     const float *mf, *uf, *vf, *pf;
+    // 1: the lists are a superset of N(i) (built with a skin); the mean
+    // mass of the h update then counts only members
+    int filter;
 };
 
 void launch_bg_mref(cudaStream_t s, const BgArgs &a);

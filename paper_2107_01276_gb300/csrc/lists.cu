@@ -67,6 +67,14 @@ __device__ __forceinline__ bool member(const ListArgs &a, const float4 &pi,
                                        double xi, double yi, double hi,
                                        int j) {
     float dx, dy, r2;
+    if (a.skin > 1.0f) {
+        // skin lists: a superset is all that is needed, and the skin is far
+        // wider than the FP32 error of the separation
+        const float4 pj = __ldg(&a.pk[j]);
+        anchor_sep(a.an, pi, pj, dx, dy);
+        const float R = a.skin * 3.0f * fmaxf(pi.z, pj.z);
+        return fmaf(dx, dx, dy * dy) < R * R;
+    }
     return pred_mixed(a.d, a.an, pi, __ldg(&a.pk[j]), xi, yi, hi, a.x, a.y,
                       a.h, j, dx, dy, r2);
 }
@@ -91,8 +99,8 @@ __global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
     const uint32_t W = a.stage_w;
     uint32_t *row = a.stage + (size_t)i * W;
     const unsigned below = tm.mask & ((1u << (threadIdx.x & 31)) - 1u);
-    for_each_cell_team<T>(a.g, a.d, li, q.x, q.y, pi.z, tm.lane, tm.mask,
-                          [&](uint32_t s, uint32_t e) {
+    for_each_cell_team_scaled<T>(a.g, a.d, li, q.x, q.y, pi.z, a.skin, tm.lane,
+                                 tm.mask, [&](uint32_t s, uint32_t e) {
         for (uint32_t j0 = s; j0 < e; j0 += T) {
             const uint32_t j = j0 + tm.lane;
             const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);
@@ -161,8 +169,9 @@ __global__ void __launch_bounds__(128) k_list_fill_queue(ListArgs a) {
         const float2 q = anchor_rel(a.an, pi);
         uint32_t k = a.off[i];
         const uint32_t cap = a.cap;
-        for_each_cell_team<T>(a.g, a.d, li, q.x, q.y, pi.z, tm.lane, tm.mask,
-                              [&](uint32_t s, uint32_t e) {
+        for_each_cell_team_scaled<T>(a.g, a.d, li, q.x, q.y, pi.z, a.skin,
+                                     tm.lane, tm.mask,
+                                     [&](uint32_t s, uint32_t e) {
             for (uint32_t j0 = s; j0 < e; j0 += T) {
                 const uint32_t j = j0 + tm.lane;
                 const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);

@@ -42,6 +42,10 @@ struct ListArgs {
     uint32_t stage_w;           // row width (entries)
     uint32_t *max_own;          // largest own-entry count of the build
     uint32_t *queue, *nqueue;   // particles whose own entries overflow a row
+    // skin >= 1: lists hold every pair with r_ij < skin * 3 max(h_i, h_j)
+    // (a superset of N(i) for particles that move less than the skin
+    // allows); 1: exactly N(i)
+    float skin;
 };
 
 void launch_pack(cudaStream_t s, const PackArgs &a);

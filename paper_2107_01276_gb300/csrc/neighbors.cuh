@@ -96,10 +96,16 @@ __device__ __forceinline__ bool axis_pieces(const Domain &d, const Level &L,
 // around (xi, yi).  Cells come in a fixed order (level, then row, then
 // column), so traversal order is deterministic.
 // (xr, yr): position relative to the domain's lower corner, FP32.
+//
+// for_each_cell_scaled widens the square by qscale >= 1 (every pair with
+// r_ij < qscale * 3 max(h_i, h_j) is then in the cells visited): the walk
+// of lists with a skin.
 template <class F>
-__device__ __forceinline__ void for_each_cell(const Grid &g, const Domain &d,
-                                              int li, float xr, float yr,
-                                              float hi, F &&f) {
+__device__ __forceinline__ void for_each_cell_scaled(const Grid &g,
+                                                     const Domain &d, int li,
+                                                     float xr, float yr,
+                                                     float hi, float qscale,
+                                                     F &&f) {
     const float Ri = 3.0f * hi;
     const uint32_t mask = g.level_mask & ~((1u << li) - 1u);
     for (uint32_t mm = mask; mm; mm &= mm - 1) {
@@ -108,7 +114,7 @@ __device__ __forceinline__ void for_each_cell(const Grid &g, const Domain &d,
         if (__ldg(&bb[0]) > __ldg(&bb[1])) continue;   // level holds no particle
         const Level &L = g.lev[l];
         // margin covers rounding in level and cell assignment
-        const float Q = fmaxf(Ri, L.cf) * (1.0f + 1e-5f);
+        const float Q = qscale * fmaxf(Ri, L.cf) * (1.0f + 1e-5f);
         AxisPieces px, py;
         if (!axis_pieces(d, L, bb, 0, xr, Q, px)) continue;
         if (!axis_pieces(d, L, bb, 1, yr, Q, py)) continue;
@@ -134,6 +140,13 @@ __device__ __forceinline__ void for_each_cell(const Grid &g, const Domain &d,
     }
 }
 
+template <class F>
+__device__ __forceinline__ void for_each_cell(const Grid &g, const Domain &d,
+                                              int li, float xr, float yr,
+                                              float hi, F &&f) {
+    for_each_cell_scaled(g, d, li, xr, yr, hi, 1.0f, f);
+}
+
 // Team form of for_each_cell: the T lanes of a team (mask: the team's
 // lanes) look up the cells of a level in parallel, lane t taking cells t,
 // t + T, ..., and then every lane calls f(s, e) for the occupied cells in
@@ -141,15 +154,13 @@ __device__ __forceinline__ void for_each_cell(const Grid &g, const Domain &d,
 // hash lookups and cell arithmetic are thus done once per cell instead of
 // once per lane; f may use team-wide shuffles and ballots.
 template <int T, class F>
-__device__ __forceinline__ void for_each_cell_team(const Grid &g,
-                                                   const Domain &d, int li,
-                                                   float xr, float yr,
-                                                   float hi, int lane,
-                                                   unsigned mask, F &&f) {
+__device__ __forceinline__ void for_each_cell_team_scaled(
+    const Grid &g, const Domain &d, int li, float xr, float yr, float hi,
+    float qscale, int lane, unsigned mask, F &&f) {
     if constexpr (T == 1) {
         (void)lane;
         (void)mask;
-        for_each_cell(g, d, li, xr, yr, hi, f);
+        for_each_cell_scaled(g, d, li, xr, yr, hi, qscale, f);
         return;
     }
     const float Ri = 3.0f * hi;
@@ -159,7 +170,7 @@ __device__ __forceinline__ void for_each_cell_team(const Grid &g,
         const int *bb = g.bbox + 4 * l;
         if (__ldg(&bb[0]) > __ldg(&bb[1])) continue;   // level holds no particle
         const Level &L = g.lev[l];
-        const float Q = fmaxf(Ri, L.cf) * (1.0f + 1e-5f);
+        const float Q = qscale * fmaxf(Ri, L.cf) * (1.0f + 1e-5f);
         AxisPieces px, py;
         if (!axis_pieces(d, L, bb, 0, xr, Q, px)) continue;
         if (!axis_pieces(d, L, bb, 1, yr, Q, py)) continue;
@@ -195,6 +206,15 @@ __device__ __forceinline__ void for_each_cell_team(const Grid &g,
             }
         }
     }
+}
+
+template <int T, class F>
+__device__ __forceinline__ void for_each_cell_team(const Grid &g,
+                                                   const Domain &d, int li,
+                                                   float xr, float yr,
+                                                   float hi, int lane,
+                                                   unsigned mask, F &&f) {
+    for_each_cell_team_scaled<T>(g, d, li, xr, yr, hi, 1.0f, lane, mask, f);
 }
 
 // Calls f(j) for every particle j of the cells for_each_cell visits.

@@ -149,9 +149,9 @@ struct sph_ctx {
 
     bool grid_valid = false, rhs_valid = false, have_dt = false;
     // list sizing: entry total and particle count of the last build that
-    // read its total back
-    uint32_t last_total = 0;
-    int last_total_n = 0;
+    // read its total back, for exact lists and for lists with a skin
+    uint32_t last_total = 0, last_total_skin = 0;
+    int last_total_n = 0, last_total_skin_n = 0;
     long long steps = 0;
     int launches = 0;
     bool timing = false;
@@ -261,6 +261,7 @@ static Grid grid_for_kernels(const sph_ctx *c) {
 // copies x0..p0.
 static ListArgs list_args(sph_ctx *c) {
     ListArgs la;
+    la.skin = 1.0f;
     la.n = c->n;
     la.g = grid_for_kernels(c);
     la.d = c->dom;
@@ -286,6 +287,41 @@ static ListArgs list_args(sph_ctx *c) {
     return la;
 }
 
+// Per-particle anchor records (and the mixed path's float mirrors) at the
+// current positions; with table_end also the cell ends of the table (part
+// of a rebuild).
+static void pack(sph_ctx *c, bool table_end) {
+    const int n = c->n;
+    PackArgs pa;
+    pa.n = n;
+    pa.lshift = 2 * c->mbits;
+    pa.mixed = is_mixed(c) ? 1 : 0;
+    pa.skey = c->skey;
+    pa.x = c->f[F_X];
+    pa.y = c->f[F_Y];
+    pa.h = c->f[F_H];
+    pa.m = c->f[F_M];
+    pa.p = c->f[F_P];
+    pa.u = c->f[F_U];
+    pa.v = c->f[F_V];
+    for (int ax = 0; ax < 2; ++ax) {
+        pa.lo[ax] = c->dom.lo[ax];
+        pa.Ad[ax] = c->anchor_A[ax];
+    }
+    pa.an = c->an;
+    pa.lev = c->lvl;
+    pa.pk = c->pk;
+    pa.mf = c->mf;
+    pa.pf = c->pf;
+    pa.uf = c->uf;
+    pa.vf = c->vf;
+    pa.tkey = c->tkey;
+    pa.tend = table_end ? c->tend : nullptr;
+    pa.tmask = c->tmask;
+    launch_pack(c->s, pa);
+    c->launches += 1;
+}
+
 // exact: read the list total back (one synchronisation) and grow the list
 // buffer before filling -- unless the last total read back was at most
 // half the buffer and the particle count is within 10 % of the one it was
@@ -293,11 +329,19 @@ static ListArgs list_args(sph_ctx *c) {
 // entries past the capacity are dropped and flagged, and the flag is
 // checked at the next synchronising call (which then reports
 // SPH_ECAPACITY and forces an exact build).
-static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
+//
+// skin > 1: the lists hold every pair with r_ij < skin * 3 max(h_i, h_j), a
+// superset of N(i) that stays one while particles move less than
+// (skin - 1) 3 max(h) / 2 each.
+static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true,
+                          float skin = 1.0f) {
     const int n = c->n;
-    if (exact && c->last_total > 0 && (size_t)c->last_total * 2 <= c->list_cap &&
-        (long long)n * 10 <= (long long)c->last_total_n * 11 &&
-        (long long)n * 10 >= (long long)c->last_total_n * 9)
+    const bool sk = skin > 1.0f;
+    const uint32_t lt = sk ? c->last_total_skin : c->last_total;
+    const int ltn = sk ? c->last_total_skin_n : c->last_total_n;
+    if (exact && lt > 0 && (size_t)lt * 2 <= c->list_cap &&
+        (long long)n * 10 <= (long long)ltn * 11 &&
+        (long long)n * 10 >= (long long)ltn * 9)
         exact = false;
     if (c->stage_want > c->stage_w) {
         uint32_t *ns = nullptr;
@@ -348,35 +392,9 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
                   &c->launches);
     for (int k = 0; k < last; ++k) std::swap(c->f[k], c->falt[k]);
     std::swap(c->id, c->id_alt);
-    PackArgs pa;
-    pa.n = n;
-    pa.lshift = 2 * c->mbits;
-    pa.mixed = is_mixed(c) ? 1 : 0;
-    pa.skey = c->skey;
-    pa.x = c->f[F_X];
-    pa.y = c->f[F_Y];
-    pa.h = c->f[F_H];
-    pa.m = c->f[F_M];
-    pa.p = c->f[F_P];
-    pa.u = c->f[F_U];
-    pa.v = c->f[F_V];
-    for (int ax = 0; ax < 2; ++ax) {
-        pa.lo[ax] = c->dom.lo[ax];
-        pa.Ad[ax] = c->anchor_A[ax];
-    }
-    pa.an = c->an;
-    pa.lev = c->lvl;
-    pa.pk = c->pk;
-    pa.mf = c->mf;
-    pa.pf = c->pf;
-    pa.uf = c->uf;
-    pa.vf = c->vf;
-    pa.tkey = c->tkey;
-    pa.tend = c->tend;
-    pa.tmask = c->tmask;
-    launch_pack(c->s, pa);
-    c->launches += 1;
+    pack(c, true);
     ListArgs la = list_args(c);
+    la.skin = skin;
     build_lists_count(c->s, la, is_mixed(c), c->sc, c->cnt_tmp, &c->launches);
     bool queue = true;
     if (exact && n > 0) {
@@ -384,8 +402,13 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
         cudaMemcpyAsync(&total, c->off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
         cudaMemcpyAsync(&max_own, c->d_max_own, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
         if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "rebuild sync");
-        c->last_total = total;
-        c->last_total_n = n;
+        if (sk) {
+            c->last_total_skin = total;
+            c->last_total_skin_n = n;
+        } else {
+            c->last_total = total;
+            c->last_total_n = n;
+        }
         // widen the staging rows from the next build on, so that particles
         // rarely take the second walk (at most 256 entries a row)
         queue = max_own > c->stage_w;
@@ -405,6 +428,7 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true) {
             }
             c->list_cap = want;
             la = list_args(c);
+            la.skin = skin;
         }
     }
     build_lists_fill(c->s, la, is_mixed(c), queue, &c->launches);
@@ -1083,6 +1107,7 @@ static ShiftArgs shift_args(sph_ctx *c) {
     sa.uf = c->uf;
     sa.vf = c->vf;
     sa.pf = c->pf;
+    sa.filter = 0;
     return sa;
 }
 
@@ -1242,7 +1267,7 @@ static sph_status check_overflow(sph_ctx *c, const char *who) {
     if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, who);
     if (!ovf) return SPH_OK;
     cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
-    c->last_total = 0;   // the next build sizes its lists exactly
+    c->last_total = c->last_total_skin = 0;   // next builds size exactly
     return fail(c, SPH_ECAPACITY, std::string(who) + ": neighbour list overflow");
 }
 
@@ -1426,7 +1451,7 @@ sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
         *t_out = t;
         if (ovf) {
             cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
-            c->last_total = 0;   // the next build sizes its lists exactly
+            c->last_total = c->last_total_skin = 0;   // next builds size exactly
             return fail(c, SPH_ECAPACITY, "sph_step: neighbour list overflow during the steps");
         }
         if (bad) return fail(c, SPH_ENONFINITE, "sph_step: non-finite rate");
@@ -1527,13 +1552,34 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         }
     }
     // shift rounds with Taylor correction, then the h update (3.2, 3.4)
-    for (int r = 0; r < c->prm.shift_iters; ++r) {
+    // One list build serves every shift round and the h update: a round
+    // moves a particle by at most 0.25 h (Eq. shift-limit), so after k
+    // rounds a pair is at most k (h_i + h_j) / 4 <= k max(h) / 2 closer,
+    // and lists with skin 1 + k / 6 still hold N(i).  The shift sums vanish
+    // outside N(i) (kernel support); the h update counts members only.
+    // (mixed path only: on the FP64 path the wider lists cost more FP64
+    // pair work than the rebuilds they save)
+    const int ns = c->prm.shift_iters;
+    if (ns <= 4 && is_mixed(c)) {
+        if ((st = rebuild(c, false, true, 1.0f + ns / 6.0f + 0.01f)) != SPH_OK) return st;
+        for (int r = 0; r < ns; ++r) {
+            if (r > 0) pack(c, false);
+            launch_shift_round(c->s, shift_args(c), is_mixed(c));
+            c->launches += 3;
+        }
+        if (ns > 0) pack(c, false);
+        ShiftArgs ha = shift_args(c);
+        ha.filter = 1;
+        launch_h_update(c->s, ha, is_mixed(c));
+    } else {
+        for (int r = 0; r < ns; ++r) {
+            if ((st = rebuild(c, false)) != SPH_OK) return st;
+            launch_shift_round(c->s, shift_args(c), is_mixed(c));
+            c->launches += 3;
+        }
         if ((st = rebuild(c, false)) != SPH_OK) return st;
-        launch_shift_round(c->s, shift_args(c), is_mixed(c));
-        c->launches += 3;
+        launch_h_update(c->s, shift_args(c), is_mixed(c));
     }
-    if ((st = rebuild(c, false)) != SPH_OK) return st;
-    launch_h_update(c->s, shift_args(c), is_mixed(c));
     c->launches += 2;
     c->launches += launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass + 1);
     t_end(c, 4, ev);
@@ -1548,7 +1594,7 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_adapt");
     if (ovf) {
         cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
-        c->last_total = 0;   // the next build sizes its lists exactly
+        c->last_total = c->last_total_skin = 0;   // next builds size exactly
         return fail(c, SPH_ECAPACITY, "sph_adapt: neighbour list overflow during the call");
     }
     z.mass_before = mass[0];
@@ -1696,7 +1742,7 @@ sph_status sph_read(sph_ctx *c, sph_field field, void *dst, long long cap,
         cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
         if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_read");
         if (ovf) {
-            c->last_total = 0;
+            c->last_total = c->last_total_skin = 0;
             return fail(c, SPH_ECAPACITY, "sph_read: neighbour list overflow");
         }
         const uint32_t total = off[n];
