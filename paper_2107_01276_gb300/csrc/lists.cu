@@ -327,7 +327,9 @@ void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,
     if (queue) k_list_fill_queue<16><<<152 * 4, 128, 0, s>>>(a);
     k_list_sort_rev<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.own, a.list, a.cap,
                                                   a.longq, a.nlong);
-    k_list_sort_long<<<std::max(1, std::min(152 * 16, nblk(n, 512))), 128, 0, s>>>(
+    // up to one warp per particle (4 per block): the long segments are
+    // sorted in parallel whatever their number; idle warps exit at once
+    k_list_sort_long<<<std::max(1, std::min(152 * 16, nblk(n, 4))), 128, 0, s>>>(
         a.off, a.own, a.list, a.longq, a.nlong);
     *launches += 4;
 }
