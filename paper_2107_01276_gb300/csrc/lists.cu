@@ -320,10 +320,12 @@ void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,
     (void)mixed;
     const int n = a.n;
     if (n <= 0) return;
+    // at least 16 lanes per particle: a list's entries are then read from
+    // the staging row and written to the list in 64-byte runs
     with_team(n, [&](auto t) {
         constexpr int T = decltype(t)::value;
         k_list_place<T><<<nblk(n * T, 128), 128, 0, s>>>(a);
-    });
+    }, 16);
     if (queue) k_list_fill_queue<16><<<152 * 4, 128, 0, s>>>(a);
     k_list_sort_rev<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.own, a.list, a.cap,
                                                   a.longq, a.nlong);

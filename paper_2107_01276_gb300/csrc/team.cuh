@@ -54,10 +54,12 @@ inline int team_size(int n) {
 }
 
 // Host-side dispatch: f(std::integral_constant<int, T>()) with T =
-// team_size(n).
+// team_size(n), or at least min_t (a power of two up to 32).
 template <class F>
-inline void with_team(int n, F &&f) {
-    switch (team_size(n)) {
+inline void with_team(int n, F &&f, int min_t = 1) {
+    int t = team_size(n);
+    if (t < min_t) t = min_t;
+    switch (t) {
     case 32: f(std::integral_constant<int, 32>()); break;
     case 16: f(std::integral_constant<int, 16>()); break;
     case 4: f(std::integral_constant<int, 4>()); break;
