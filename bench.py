@@ -30,10 +30,47 @@ sys.path.insert(0, ROOT)
 
 from paper_2107_01276_gb300 import workloads as wl  # noqa: E402
 
-# FP32 flops of one pass-B pair evaluation (formula operation count, FMA = 2;
-# derivation in the design doc) and of one pass-A pair.
+# FP32 flops of one pass-B pair evaluation (formula operation count, FMA = 2)
+# and of one pass-A pair.
 PASS_B_FLOP_PER_PAIR = 90
 PASS_A_FLOP_PER_PAIR = 60
+# Compulsory bytes of the neighbour walk: per particle its x, y, h (FP64)
+# and anchor record read and its own-entry count written (44 B), per list
+# entry 4 B (the walk stages own entries and counts reverse ones).
+WALK_BYTES_PER_PARTICLE = 44
+WALK_BYTES_PER_ENTRY = 4
+NFAM = 6   # timed kernel families of the library (sph_kernel_time)
+FAM_NAMES = ["pass_b", "pass_a", "rebuild", "pec", "adapt", "walk"]
+# kernel sources a DRAM-traffic capture is tied to
+WALK_SOURCES = ["paper_2107_01276_gb300/csrc/lists.cu",
+                "paper_2107_01276_gb300/csrc/neighbors.cuh",
+                "paper_2107_01276_gb300/csrc/team.cuh"]
+
+
+def sources_sha(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), p),
+                  "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def walk_traffic(workload):
+    """DRAM bytes per launch of the neighbour walk from the committed ncu
+    summary, or None if there is none for this workload or the kernel
+    sources changed since it was taken."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "profiles", "walk_dram_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("sources_sha") != sources_sha(WALK_SOURCES):
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 WORKLOADS = {
     # configs[1]: flow past a cylinder at Re 40, spacing graded from D/50 at
@@ -310,7 +347,7 @@ def main():
         evs = [(torch.cuda.Event(enable_timing=True),
                 torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         s.set_timing(True)
-        for fam in range(5):
+        for fam in range(NFAM):
             s.kernel_time(fam, reset=True)
         l0 = s.info()["launches"]
         if dist:
@@ -332,7 +369,7 @@ def main():
             dist.barrier()
         s.set_timing(False)
         ms = [a.elapsed_time(b) for a, b in evs]
-        fams = [s.kernel_time(f) for f in range(5)]
+        fams = [s.kernel_time(f) for f in range(NFAM)]
         return ms, ns, fams, s.info()["launches"] - l0
 
     sim = new_sim(sph.SPH_MIXED)
@@ -363,6 +400,13 @@ def main():
     avg_b = passb_ms / max(passb_cnt, 1)
     peak_alu = fp32_alu_peak_tflops(2070.0)
     ach_b = PASS_B_FLOP_PER_PAIR * pairs / (avg_b / 1e3) / 1e12
+    # the dominant kernel of the step: the neighbour walk
+    walk_ms, walk_cnt = fams[5]
+    avg_w = walk_ms / max(walk_cnt, 1)
+    walk_bytes = WALK_BYTES_PER_PARTICLE * n_now + WALK_BYTES_PER_ENTRY * int(nnb.sum())
+    peaks0, _ = measured_peaks()
+    hbm_peak = peaks0.get("hbm_gbs") or 6800.0
+    ach_w = walk_bytes / (avg_w / 1e3) / 1e9
 
     # e2e through the C ABI with pinned host buffers: H2D of the step's
     # fluid state, the step (adaptation + PEC), D2H of x, y, u, v, p
@@ -434,7 +478,7 @@ def main():
                    "adaptation + PEC step each" if adaptive else "PEC")}
 
     peaks, pk_kind = measured_peaks()
-    fam_names = ["pass_b", "pass_a", "rebuild", "pec", "adapt"]
+    fam_names = FAM_NAMES
     line = {
         "metric": "particle-steps/s", "value": value,
         "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
@@ -452,8 +496,18 @@ def main():
         "fp64_particle_steps_per_s": fp64,
         "mixed_over_fp64": (value / world / fp64) if fp64 else None,
         "kernel_ms_per_step": {fam_names[f]: fams[f][0] / args.steps
-                               for f in range(5)},
-        "roofline": {"bound": "alu", "kernel": "k_pass_b<float>",
+                               for f in range(NFAM)},
+        "roofline": {"bound": "hbm", "kernel": "k_list_gather (neighbour walk)",
+                     "achieved": ach_w, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": ach_w / hbm_peak,
+                     "traffic": walk_traffic(args.workload),
+                     "bytes_per_launch": walk_bytes,
+                     "ms_per_launch": avg_w,
+                     "peak_kind": "measured copy bandwidth",
+                     "note": "instruction- and latency-bound, not "
+                             "bandwidth-bound: ncu shows high issue activity "
+                             "and a few % DRAM throughput for this kernel"},
+        "roofline_pass_b": {"bound": "alu", "kernel": "k_pass_b<float>",
                      "achieved": ach_b, "peak": peak_alu, "unit": "TFLOP/s",
                      "frac": ach_b / peak_alu, "traffic": None,
                      "peak_kind": "derived FP32 non-tensor peak at 2070 MHz "

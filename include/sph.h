@@ -270,9 +270,10 @@ sph_status sph_get_info(sph_ctx *ctx, sph_info *out);
 /* Kernel timing: when enabled the context records CUDA events around the
  * launches of each timed kernel family on its stream.  sph_kernel_time
  * returns the accumulated device milliseconds and launch count of one
- * family (0: pass B, 1: pass A, 2: cell rebuild (keys, sort, gather,
- * table), 3: PEC stages, 4: adaptation kernels) and resets them if reset
- * is non-zero.  Synchronises. */
+ * family (0: pass B, 1: pass A, 2: neighbour rebuild (keys, sort, gather,
+ * table, lists), 3: PEC stages, 4: adaptation (rebuilds inside it
+ * included), 5: the neighbour walk of each rebuild alone) and resets them
+ * if reset is non-zero.  Synchronises. */
 sph_status sph_set_timing(sph_ctx *ctx, int enable);
 sph_status sph_kernel_time(sph_ctx *ctx, int family, double *ms,
                            long long *launches, int reset);

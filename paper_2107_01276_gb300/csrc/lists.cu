@@ -293,19 +293,23 @@ void launch_anchor_pack(cudaStream_t s, int n, const double *x,
                                                     A[0], A[1], an, pk);
 }
 
-void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
-                       SortScratch &sc, uint32_t *tot_tmp, int *launches) {
-    (void)mixed;
+void launch_list_walk(cudaStream_t s, const ListArgs &a, int *launches) {
     const int n = a.n;
-    if (n <= 0) {
-        cudaMemsetAsync(a.off, 0, sizeof(uint32_t), s);
-        return;
-    }
+    if (n <= 0) return;
     with_team(n, [&](auto t) {
         constexpr int T = decltype(t)::value;
         k_list_gather<T><<<nblk(n * T, 128), 128, 0, s>>>(a);
     });
     *launches += 1;
+}
+
+void list_offsets(cudaStream_t s, const ListArgs &a, SortScratch &sc,
+                  uint32_t *tot_tmp, int *launches) {
+    const int n = a.n;
+    if (n <= 0) {
+        cudaMemsetAsync(a.off, 0, sizeof(uint32_t), s);
+        return;
+    }
     if (list_offsets_small(s, a.own, a.rev, a.off, n, launches)) return;
     k_list_total<<<nblk(n, 256), 256, 0, s>>>(n, a.own, a.rev, tot_tmp);
     // off has n + 1 entries: scan n + 1 values with a trailing zero

@@ -52,12 +52,14 @@ void launch_pack(cudaStream_t s, const PackArgs &a);
 void launch_anchor_pack(cudaStream_t s, int n, const double *x,
                         const double *y, const double *h, const double *lo,
                         const double *A, const Anchor &an, float4 *pk);
-// Count and scan into off (n + 1 entries; tot_tmp needs n + 1), then fill
-// the lists; entries past a.cap are dropped and flag a.overflow.  Before
-// the count, rev[0..n) and the counters nqueue, max_own and nlong must be
-// zero (the rebuild's reset and key kernels do that).
-void build_lists_count(cudaStream_t s, ListArgs a, bool mixed,
-                       SortScratch &sc, uint32_t *tot_tmp, int *launches);
+// The walk (own entries staged, reverse entries counted), then the
+// offsets (off has n + 1 entries; tot_tmp needs n + 1), then the fill;
+// entries past a.cap are dropped and flag a.overflow.  Before the walk,
+// rev[0..n) and the counters nqueue, max_own and nlong must be zero (the
+// rebuild's reset and key kernels do that).
+void launch_list_walk(cudaStream_t s, const ListArgs &a, int *launches);
+void list_offsets(cudaStream_t s, const ListArgs &a, SortScratch &sc,
+                  uint32_t *tot_tmp, int *launches);
 // queue: launch the second walk for rows that overflowed (false when the
 // caller knows none did).
 void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,

@@ -22,11 +22,15 @@ namespace {
 
 thread_local std::string g_create_error;
 
+// Timed kernel families: 0 pass B, 1 pass A, 2 rebuild, 3 PEC stages,
+// 4 adaptation, 5 the neighbour walk of the rebuild (k_list_gather).
+constexpr int NFAM = 6;
+
 struct Timer {
     std::vector<cudaEvent_t> pool;       // free events
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> open[5];
-    double ms[5] = {0, 0, 0, 0, 0};
-    long long count[5] = {0, 0, 0, 0, 0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> open[NFAM];
+    double ms[NFAM] = {0, 0, 0, 0, 0, 0};
+    long long count[NFAM] = {0, 0, 0, 0, 0, 0};
 };
 
 }  // namespace
@@ -211,7 +215,7 @@ static void t_end(sph_ctx *c, int fam, cudaEvent_t ev0) {
 }
 
 static void t_collect(sph_ctx *c) {
-    for (int f = 0; f < 5; ++f) {
+    for (int f = 0; f < NFAM; ++f) {
         for (auto &pr : c->tm.open[f]) {
             float ms = 0.f;
             cudaEventSynchronize(pr.second);
@@ -395,7 +399,13 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true,
     pack(c, true);
     ListArgs la = list_args(c);
     la.skin = skin;
-    build_lists_count(c->s, la, is_mixed(c), c->sc, c->cnt_tmp, &c->launches);
+    {
+        cudaEvent_t ew;
+        t_begin(c, 5, &ew);
+        launch_list_walk(c->s, la, &c->launches);
+        t_end(c, 5, ew);
+    }
+    list_offsets(c->s, la, c->sc, c->cnt_tmp, &c->launches);
     bool queue = true;
     if (exact && n > 0) {
         uint32_t total = 0, max_own = 0;
@@ -638,7 +648,7 @@ static void free_ctx(sph_ctx *c) {
     free_set(&c->bg);
     free_set(&c->wall);
     for (auto e : c->tm.pool) cudaEventDestroy(e);
-    for (int f = 0; f < 5; ++f)
+    for (int f = 0; f < NFAM; ++f)
         for (auto &pr : c->tm.open[f]) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
@@ -1816,7 +1826,7 @@ sph_status sph_set_timing(sph_ctx *c, int enable) {
 
 sph_status sph_kernel_time(sph_ctx *c, int family, double *ms,
                            long long *launches, int reset) {
-    if (!c || family < 0 || family > 4) return SPH_EINVAL;
+    if (!c || family < 0 || family >= NFAM) return SPH_EINVAL;
     t_collect(c);
     if (ms) *ms = c->tm.ms[family];
     if (launches) *launches = c->tm.count[family];

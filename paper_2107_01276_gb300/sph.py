@@ -32,7 +32,8 @@ _FIELD_DTYPE = {"id": np.int64, "nnb": np.int32, "cellkey": np.uint64,
                 "neigh_off": np.int64, "neigh_id": np.int64,
                 "bg_id": np.int64}
 
-TIMER_PASS_B, TIMER_PASS_A, TIMER_REBUILD, TIMER_PEC, TIMER_ADAPT = range(5)
+TIMER_PASS_B, TIMER_PASS_A, TIMER_REBUILD, TIMER_PEC, TIMER_ADAPT, \
+    TIMER_WALK = range(6)
 
 
 class SphError(RuntimeError):
