@@ -106,6 +106,8 @@ void compute_levels(const Domain &dom, double c0, Level *lev) {
             lev[l].n[ax] = (int)nc;
             lev[l].w[ax] = w;
             lev[l].invw[ax] = (float)(1.0 / w);
+            lev[l].wf[ax] = (float)w;
+            lev[l].invP[ax] = (float)(1.0 / ((double)nc * w));
         }
     }
 }
@@ -578,10 +580,10 @@ __global__ void k_table_insert(int n, const uint64_t *__restrict__ skey,
 
 __global__ void k_table_end(int n, const uint64_t *__restrict__ skey,
                             const uint64_t *__restrict__ tkey, uint32_t *tend,
-                            uint32_t tmask) {
+                            uint32_t tmask, const double *h, float *tmaxh) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    table_mark_end(i, n, skey, tkey, tend, tmask);
+    table_mark_end(i, n, skey, tkey, tend, tmask, h, tmaxh);
 }
 
 // Gather in sorted order fused with the insertion of each cell's start.
@@ -658,12 +660,14 @@ void launch_rebuild_reset(cudaStream_t s, const RebuildReset &r, int *launches) 
 
 void build_cell_table(cudaStream_t s, int n, const uint64_t *skey,
                       uint64_t *tkey, uint32_t *tstart, uint32_t *tend,
-                      uint32_t tmask, int *launches) {
+                      uint32_t tmask, int *launches, const double *h,
+                      float *tmaxh) {
     cudaMemsetAsync(tkey, 0xff, sizeof(uint64_t) * ((size_t)tmask + 1), s);
     if (n <= 0) return;
     int bs = 256;
     k_table_insert<<<(n + bs - 1) / bs, bs, 0, s>>>(n, skey, tkey, tstart, tmask);
-    k_table_end<<<(n + bs - 1) / bs, bs, 0, s>>>(n, skey, tkey, tend, tmask);
+    k_table_end<<<(n + bs - 1) / bs, bs, 0, s>>>(n, skey, tkey, tend, tmask, h,
+                                                 tmaxh);
     *launches += 2;
 }
 

@@ -32,7 +32,7 @@ __global__ void k_pack(PackArgs a) {
     }
     a.pk[i] = make_float4(xl[0], xl[1], (float)a.h[i],
                           __uint_as_float((unsigned)g[0] | ((unsigned)g[1] << 16)));
-    if (a.tend) table_mark_end(i, a.n, a.skey, a.tkey, a.tend, a.tmask);
+    if (a.tend) table_mark_end(i, a.n, a.skey, a.tkey, a.tend, a.tmask, a.h, a.tmaxh);
     if (!a.mixed) return;
     a.mf[i] = (float)a.m[i];
     a.pf[i] = (float)a.p[i];

@@ -21,6 +21,7 @@ struct PackArgs {
     const uint64_t *tkey;
     uint32_t *tend;
     uint32_t tmask;
+    float *tmaxh;               // per slot: the cell's largest h
 };
 
 struct ListArgs {

@@ -26,19 +26,78 @@
 namespace sph {
 
 __device__ __forceinline__ bool table_lookup(const Grid &g, uint64_t key,
-                                             uint32_t &s, uint32_t &e) {
+                                             uint32_t &s, uint32_t &e,
+                                             float *hmax = nullptr) {
     uint32_t slot = hash_slot(key, g.tmask);
     for (uint32_t it = 0; it <= g.tmask; ++it) {
         uint64_t t = __ldg(&g.tkey[slot]);
         if (t == key) {
             s = __ldg(&g.tstart[slot]);
             e = __ldg(&g.tend[slot]);
+            if (hmax) *hmax = g.tmaxh ? __ldg(&g.tmaxh[slot]) : 3.0e38f;
             return true;
         }
         if (t == EMPTY_KEY) return false;
         slot = (slot + 1) & g.tmask;
     }
     return false;
+}
+
+// Pruning of the cells of a query.  gap2: squared distance from (xr, yr)
+// to the rectangle of the cell (cx, cy) of level L, less a margin far
+// above FP32 rounding.  On a periodic axis the distance is to the nearest
+// periodic image of the cell (the indices may or may not be unwrapped);
+// the edge cells of a non-periodic axis reach to infinity (particles
+// outside the box are clamped into them).  A cell whose gap is at least the pair radius can hold no member:
+// before the lookup the radius is qscale * max(3 h_i, c_l) (no particle of
+// level l has 3h > c_l), after it qscale * 3 max(h_i, largest h of the
+// cell).
+__device__ __forceinline__ float cell_gap2(const Domain &d, const Level &L,
+                                           int cx, int cy, float xr,
+                                           float yr) {
+    const int c[2] = {cx, cy};
+    const float q[2] = {xr, yr};
+    float g2 = 0.0f;
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        const float w = L.wf[ax];
+        const float m = 1e-5f * (fabsf(q[ax]) + w);
+        float gap;
+        if (d.periodic[ax]) {
+            const float P = (float)L.n[ax] * w;          // the period
+            float t = q[ax] - ((float)c[ax] + 0.5f) * w;  // to the cell centre
+            t -= P * rintf(t * L.invP[ax]);
+            gap = fabsf(t) - 0.5f * w;
+        } else {
+            float lo = (float)c[ax] * w, hi = lo + w;
+            if (c[ax] <= 0) lo = -3.0e38f;
+            if (c[ax] >= L.n[ax] - 1) hi = 3.0e38f;
+            gap = fmaxf(lo - q[ax], q[ax] - hi);
+        }
+        gap = fmaxf(0.0f, gap - m);
+        g2 += gap * gap;
+    }
+    return g2;
+}
+
+// Lookup of cell (cx, cy) of level l (unwrapped indices, their periodic
+// shifts sx, sy) with the two prunings above; false: nothing to visit.
+__device__ __forceinline__ bool cell_visit(const Grid &g, const Domain &d,
+                                           const Level &L, uint64_t lbits,
+                                           int cx, int cy, int sx, int sy,
+                                           float xr, float yr, float hi,
+                                           float qscale, uint32_t &s,
+                                           uint32_t &e) {
+    const float g2 = cell_gap2(d, L, cx, cy, xr, yr);
+    const float Rl = qscale * fmaxf(3.0f * hi, L.cf);
+    if (g2 >= Rl * Rl) return false;
+    float hmax;
+    if (!table_lookup(g, lbits | (spread2((uint64_t)(cy + sy)) << 1) |
+                             spread2((uint64_t)(cx + sx)),
+                      s, e, &hmax))
+        return false;
+    const float Rc = qscale * 3.0f * fmaxf(hi, hmax);
+    return g2 < Rc * Rc;
 }
 
 // Cell index ranges on one axis of one level for the query interval
@@ -123,14 +182,12 @@ __device__ __forceinline__ void for_each_cell_scaled(const Grid &g,
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky) {
             for (int cy = py.first[ky]; cy <= py.last[ky]; ++cy) {
-                const uint64_t my = spread2((uint64_t)(cy + py.shift[ky])) << 1;
 #pragma unroll
                 for (int kx = 0; kx < 3; ++kx) {
                     for (int cx = px.first[kx]; cx <= px.last[kx]; ++cx) {
                         uint32_t s, e;
-                        if (!table_lookup(g, lbits | my |
-                                                 spread2((uint64_t)(cx + px.shift[kx])),
-                                          s, e))
+                        if (!cell_visit(g, d, L, lbits, cx, cy, px.shift[kx],
+                                        py.shift[ky], xr, yr, hi, qscale, s, e))
                             continue;
                         f(s, e);
                     }
@@ -188,14 +245,18 @@ __device__ __forceinline__ void for_each_cell_team_scaled(
             uint32_t s = 0, e = 0;
             if (idx < ncell) {
                 const int iy = idx / nx, ix = idx - iy * nx;
-                const int cx = ix < nx0 ? px.first[0] + ix + px.shift[0]
-                             : ix < nx0 + nx1 ? px.first[1] + (ix - nx0) + px.shift[1]
-                                              : px.first[2] + (ix - nx0 - nx1) + px.shift[2];
-                const int cy = iy < ny0 ? py.first[0] + iy + py.shift[0]
-                             : iy < ny0 + ny1 ? py.first[1] + (iy - ny0) + py.shift[1]
-                                              : py.first[2] + (iy - ny0 - ny1) + py.shift[2];
-                if (!table_lookup(g, lbits | (spread2((uint64_t)cy) << 1) |
-                                         spread2((uint64_t)cx), s, e))
+                const int kx = ix < nx0 ? 0 : ix < nx0 + nx1 ? 1 : 2;
+                const int ky = iy < ny0 ? 0 : iy < ny0 + ny1 ? 1 : 2;
+                const int cx = kx == 0 ? px.first[0] + ix
+                             : kx == 1 ? px.first[1] + (ix - nx0)
+                                       : px.first[2] + (ix - nx0 - nx1);
+                const int cy = ky == 0 ? py.first[0] + iy
+                             : ky == 1 ? py.first[1] + (iy - ny0)
+                                       : py.first[2] + (iy - ny0 - ny1);
+                const int sx = kx == 0 ? px.shift[0] : kx == 1 ? px.shift[1] : px.shift[2];
+                const int sy = ky == 0 ? py.shift[0] : ky == 1 ? py.shift[1] : py.shift[2];
+                if (!cell_visit(g, d, L, lbits, cx, cy, sx, sy, xr, yr, hi,
+                                qscale, s, e))
                     s = e = 0;
             }
             const int cnt = min(T, ncell - base);

@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(128)
 // 1/h_j); eta = 0.001 h_i^2, P_j = (p_j - p_avg,i) / (rho_j^2 beta_j).
 // Wall neighbours (section 2.2): prescribed wall velocity in the divergence
 // sum, extrapolated velocity in the viscous sum, rho_w = rho0, beta_w = 1.
+// (float: at most 72 registers, seven 128-thread blocks per SM)
 template <typename R, int T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 1)
     k_pass_b(PassBArgs<R> a) {
     const Team<T> tm;
     const int i = Team<T>::particle();

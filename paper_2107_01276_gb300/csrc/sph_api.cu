@@ -59,6 +59,7 @@ struct StaticSet {
                                 // cell's first particle
     uint64_t *key = nullptr, *tkey = nullptr;
     uint32_t *perm = nullptr, *tstart = nullptr, *tend = nullptr;
+    float *tmaxh = nullptr;
     int *bbox = nullptr;
     uint32_t *mask = nullptr;
     uint32_t tmask = 0;
@@ -70,7 +71,7 @@ struct StaticSet {
 
 static void free_set(StaticSet *S) {
     void *ps[] = {S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2], S->id, S->pk, S->cmin,
-                  S->key, S->tkey, S->perm, S->tstart, S->tend, S->bbox,
+                  S->key, S->tkey, S->perm, S->tstart, S->tend, S->tmaxh, S->bbox,
                   S->mask, S->sc.key_alt, S->sc.val_alt, S->sc.counts,
                   S->sc.scan_tmp};
     for (void *p : ps) cudaFree(p);
@@ -106,6 +107,7 @@ struct sph_ctx {
     SortScratch sc;
     uint64_t *tkey = nullptr;
     uint32_t *tstart = nullptr, *tend = nullptr;
+    float *tmaxh = nullptr;     // per slot: the cell's largest h
     uint32_t tcap = 0, tmask = 0;
     int *bbox = nullptr;
     uint32_t *level_mask = nullptr;
@@ -241,6 +243,7 @@ static Grid make_grid(const sph_ctx *c) {
     g.tstart = c->tstart;
     g.tend = c->tend;
     g.tmask = c->tmask;
+    g.tmaxh = c->tmaxh;
     g.level_mask = 0;   // filled by caller from device copy? (see rebuild)
     g.mbits = c->mbits;
     g.nlev = c->lmax + 1;
@@ -322,6 +325,7 @@ static void pack(sph_ctx *c, bool table_end) {
     pa.tkey = c->tkey;
     pa.tend = table_end ? c->tend : nullptr;
     pa.tmask = c->tmask;
+    pa.tmaxh = c->tmaxh;
     launch_pack(c->s, pa);
     c->launches += 1;
 }
@@ -629,7 +633,7 @@ static void free_ctx(sph_ctx *c) {
                   c->dry, c->V, c->rb2, c->dpdt, c->dudt, c->dvdt, c->mf,
                   c->pf, c->uf, c->vf, c->nnb, c->skey, c->perm,
                   c->sc.key_alt, c->sc.val_alt, c->sc.counts, c->sc.scan_tmp,
-                  c->tkey, c->tstart, c->tend, c->bbox, c->level_mask,
+                  c->tkey, c->tstart, c->tend, c->tmaxh, c->bbox, c->level_mask,
                   c->cnt_tmp, c->d_dt, c->d_t, c->d_hmin, c->d_nonfinite,
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
                   c->d_overflow, c->longq, c->d_nlong, c->stage, c->lqueue, c->d_max_own,
@@ -699,7 +703,8 @@ static sph_status build_set_sorted(sph_ctx *c, StaticSet *S, long long n,
              dalloc(&S->sc.scan_tmp, S->sc.scan_cap);
         uint32_t t = 1;
         while (t < 2u * (uint32_t)N) t <<= 1;
-        ok = ok && dalloc(&S->tkey, t) && dalloc(&S->tstart, t) && dalloc(&S->tend, t);
+        ok = ok && dalloc(&S->tkey, t) && dalloc(&S->tstart, t) && dalloc(&S->tend, t) &&
+             dalloc(&S->tmaxh, t);
         if (!ok) {
             cudaGetLastError();
             free_set(S);
@@ -735,7 +740,7 @@ static sph_status build_set_sorted(sph_ctx *c, StaticSet *S, long long n,
     while (t < 2u * (uint32_t)n) t <<= 1;
     S->tmask = t - 1;
     build_cell_table(c->s, (int)n, S->key, S->tkey, S->tstart, S->tend, S->tmask,
-                     &c->launches);
+                     &c->launches, S->h, S->tmaxh);
     if (nex > 0) launch_cell_min(c->s, (int)n, S->key, S->ex[0], S->cmin, &c->launches);
     c->launches += 2;
     done(SPH_OK);
@@ -832,6 +837,7 @@ static Grid set_grid(const StaticSet &S) {
     g.tstart = S.tstart;
     g.tend = S.tend;
     g.tmask = S.tmask;
+    g.tmaxh = S.tmaxh;
     g.level_mask = (S.lmax >= 31) ? 0xffffffffu : ((1u << (S.lmax + 1)) - 1u);
     g.mbits = S.mbits;
     g.nlev = S.lmax + 1;
@@ -966,7 +972,8 @@ static sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
     uint32_t t = 1;
     while (t < 2u * (uint32_t)N) t <<= 1;
     c->tcap = t;
-    ok = ok && dalloc(&c->tkey, t) && dalloc(&c->tstart, t) && dalloc(&c->tend, t);
+    ok = ok && dalloc(&c->tkey, t) && dalloc(&c->tstart, t) && dalloc(&c->tend, t) &&
+         dalloc(&c->tmaxh, t);
     ok = ok && dalloc(&c->bbox, MAX_LEVELS * 4) && dalloc(&c->level_mask, 1) &&
          dalloc(&c->cnt_tmp, N + 1);
     ok = ok && dalloc(&c->d_dt, 1) && dalloc(&c->d_t, 1) && dalloc(&c->d_hmin, 1) &&

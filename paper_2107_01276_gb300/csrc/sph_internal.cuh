@@ -31,6 +31,8 @@ struct Level {
     int n[2];      // cell count per axis
     float cf;      // c in FP32
     float invw[2]; // 1 / w in FP32 (cell ranges of queries)
+    float wf[2];   // w in FP32 (cell rectangles of queries)
+    float invP[2]; // 1 / (n w) in FP32 (periodic images of cells)
 };
 
 // Device view of the cell structure built by a rebuild.  Particles are
@@ -45,6 +47,8 @@ struct Grid {
     int mbits;              // morton bits per axis
     int nlev;               // levels in use (top level = nlev - 1)
     const int *bbox;        // per level: min ix, max ix, min iy, max iy
+    const float *tmaxh;     // per table slot: largest h of the cell (rounded
+                            // up to float), or NULL
     Level lev[MAX_LEVELS];
 };
 
@@ -117,9 +121,11 @@ bool list_offsets_small(cudaStream_t s, const uint32_t *own, uint32_t *rev,
                         uint32_t *off, int n, int *launches);
 // Tile-count entries radix_sort needs in SortScratch::counts for n keys.
 size_t radix_counts_elems(size_t n);
+// h, tmaxh (may be NULL): also record each cell's largest h.
 void build_cell_table(cudaStream_t s, int n, const uint64_t *skey,
                       uint64_t *tkey, uint32_t *tstart, uint32_t *tend,
-                      uint32_t tmask, int *launches);
+                      uint32_t tmask, int *launches,
+                      const double *h = nullptr, float *tmaxh = nullptr);
 // out[k][i] = in[k][perm[i]] for up to 16 double arrays and 2 int64 arrays.
 struct GatherList {
     const double *src[16];
@@ -149,11 +155,14 @@ void launch_cell_min(cudaStream_t s, int n, const uint64_t *skey,
                      const double *v, double *cmin, int *launches);
 
 // End of the cell of sorted particle i, if i is its last particle: the
-// cell's table slot receives i + 1.
+// cell's table slot receives i + 1 and, with tmaxh, the cell's largest h
+// rounded up to float.
 __device__ __forceinline__ void table_mark_end(int i, int n,
                                                const uint64_t *skey,
                                                const uint64_t *tkey,
-                                               uint32_t *tend, uint32_t tmask) {
+                                               uint32_t *tend, uint32_t tmask,
+                                               const double *h = nullptr,
+                                               float *tmaxh = nullptr) {
     const uint64_t k = skey[i];
     if (i + 1 < n && skey[i + 1] == k) return;
     uint32_t slot = hash_slot(k, tmask);
@@ -161,6 +170,11 @@ __device__ __forceinline__ void table_mark_end(int i, int n,
         const uint64_t t = tkey[slot];
         if (t == k) {
             tend[slot] = (uint32_t)(i + 1);
+            if (tmaxh) {
+                double m = h[i];
+                for (int j = i - 1; j >= 0 && skey[j] == k; --j) m = fmax(m, h[j]);
+                tmaxh[slot] = __double2float_ru(m);
+            }
             return;
         }
         if (t == EMPTY_KEY) return;
