@@ -49,7 +49,12 @@ typedef enum {
     SPH_ESTATE = 7       /* call not valid in the current state (e.g. no fluid loaded) */
 } sph_status;
 
-typedef enum { SPH_FLUID = 0, SPH_WALL = 1, SPH_BACKGROUND = 2 } sph_kind;
+typedef enum {
+    SPH_FLUID = 0,
+    SPH_WALL = 1,
+    SPH_BACKGROUND = 2,
+    SPH_REGION = 3   /* markers of a user-specified refinement region */
+} sph_kind;
 typedef enum { SPH_FP64 = 0, SPH_MIXED = 1 } sph_precision;
 
 /* Problem parameters (SI units).  sph_default_params fills the paper's
@@ -140,6 +145,7 @@ typedef struct {
     long long steps;      /* PEC steps taken */
     long long launches;   /* kernels launched by this context so far */
     long long next_id;    /* id the next split child will receive */
+    long long n_region;   /* refinement-region markers */
 } sph_info;
 
 /* Counts and masses of one sph_adapt call. */
@@ -185,7 +191,10 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out);
  * sets the fluid's m_min/m_max in sph_adapt and is refined by
  * sph_background.  SPH_WALL (section 2.2): x, y, h, m required, u, v the
  * prescribed wall velocity (NULL: 0); the walls also serve as the solid of
- * the background construction.
+ * the background construction.  SPH_REGION (section 3.3, user-specified
+ * regions): x, y, h of marker particles that act as a solid for the
+ * background construction's boundary marking only; they take no part in
+ * the flow.
  * Fluid positions must lie in the box (periodic axes: [lo, hi)).
  * Synchronous with respect to the host buffers (they may be reused on
  * return).  Errors: SPH_EINVAL (NULL required array, n < 0, h or m not
@@ -234,8 +243,9 @@ sph_status sph_adapt(sph_ctx *ctx, sph_adapt_stats *out);
 /* Background construction (section 3.3): `iterations` iterations over the
  * loaded background (iterations <= 0: 3 ceil(log(ds_max / ds_min) /
  * log Cr), the paper's count for the initial construction), each:
- *  1. a background particle with a wall particle s in range (r_bs <
- *     3 max(h_b, h_s)) takes ds_min; with vort_k > 0 and fluid loaded, so
+ *  1. a background particle with a wall or region-marker particle s in
+ *     range (r_bs < 3 max(h_b, h_s)) takes ds_min; with vort_k > 0 and
+ *     fluid loaded, so
  *     does one whose largest |omega| over fluid particles in range exceeds
  *     vort_k max|omega| (omega from the fluid's current state);
  *  2. every other particle takes, over its background neighbours j != i

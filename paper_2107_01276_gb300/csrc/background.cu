@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(128) k_vorticity(VortArgs a) {
 }
 
 // ---------------------------------------------------------------- mark --
-// mark = 1 if a solid particle s has r < 3 max(h_b, h_s); else 2 if the
+// mark = 1 if a solid particle s (wall or region marker) has r < 3
+// max(h_b, h_s); else 2 if the
 // largest |omega_f| over fluid particles f with r < 3 max(h_b, h_f) exceeds
 // vort_k max|omega|; else 0.  Candidates come from the cell grids of the
 // solid and fluid sets, membership from the FP64 predicate.
@@ -71,6 +72,13 @@ __global__ void __launch_bounds__(128) k_bg_mark(BgMarkArgs a) {
                               [&](uint32_t s, uint32_t e) {
             for (uint32_t j = s + tm.lane; j < e && !hit; j += T)
                 if (pred_fp64(a.d, xi, yi, hi, a.wx[j], a.wy[j], a.wh[j])) hit = 1;
+        });
+    }
+    if (a.nr > 0) {
+        for_each_cell_team<T>(a.rg, a.d, 0, xr, yr, (float)hi, tm.lane, tm.mask,
+                              [&](uint32_t s, uint32_t e) {
+            for (uint32_t j = s + tm.lane; j < e && !hit; j += T)
+                if (pred_fp64(a.d, xi, yi, hi, a.rx[j], a.ry[j], a.rh[j])) hit = 1;
         });
     }
     int mk = team_any<T>(tm.mask, hit);

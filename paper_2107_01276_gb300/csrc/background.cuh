@@ -30,6 +30,9 @@ struct BgMarkArgs {
     int nw;                         // solid (dummy wall) particles
     Grid wg;
     const double *wx, *wy, *wh;
+    int nr;                         // refinement-region markers
+    Grid rg;
+    const double *rx, *ry, *rh;
     int nf;                         // fluid particles (0: no vorticity marking)
     Grid fg;
     const double *fx, *fy, *fh, *omega;

@@ -145,6 +145,7 @@ struct sph_ctx {
     unsigned long long *d_wmax = nullptr;    // max |omega| (bits)
     unsigned long long *d_minmax = nullptr;  // [2] min / max (bits)
     StaticSet wall;   // dummy wall particles (section 2.2); extra: m, u, v
+    StaticSet region; // refinement-region markers (section 3.3)
     double *wp = nullptr, *wugx = nullptr, *wugy = nullptr;   // wall BC
 
     // device scalars
@@ -651,6 +652,7 @@ static void free_ctx(sph_ctx *c) {
     }
     free_set(&c->bg);
     free_set(&c->wall);
+    free_set(&c->region);
     for (auto e : c->tm.pool) cudaEventDestroy(e);
     for (int f = 0; f < NFAM; ++f)
         for (auto &pr : c->tm.open[f]) {
@@ -1226,6 +1228,11 @@ static sph_status bg_iteration(sph_ctx *c, sph_ctx *b, bool vort,
     ma.wx = c->wall.x;
     ma.wy = c->wall.y;
     ma.wh = c->wall.h;
+    ma.nr = c->region.n;
+    ma.rg = set_grid(c->region);
+    ma.rx = c->region.x;
+    ma.ry = c->region.y;
+    ma.rh = c->region.h;
     ma.nf = vort ? c->n : 0;
     ma.fg = grid_for_kernels(c);
     ma.fx = c->f[F_X];
@@ -1355,6 +1362,13 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
     if (n < 0 || (n > 0 && !src)) return fail(c, SPH_EINVAL, "sph_load_particles: bad n or src");
     if (kind == SPH_BACKGROUND) return load_background(c, n, src);
     if (kind == SPH_WALL) return load_walls(c, n, src);
+    if (kind == SPH_REGION) {
+        if (n > 0 && (!src->x || !src->y || !src->h))
+            return fail(c, SPH_EINVAL, "sph_load_particles: region markers need x, y, h");
+        return build_set(c, &c->region, n, n ? src->x : nullptr,
+                         n ? src->y : nullptr, n ? src->h : nullptr, nullptr, 0,
+                         nullptr);
+    }
     if (kind != SPH_FLUID)
         return fail(c, SPH_EINVAL, "sph_load_particles: unknown kind");
     if (n > c->cap) return fail(c, SPH_ECAPACITY, "sph_load_particles: n exceeds capacity");
@@ -1811,6 +1825,7 @@ sph_status sph_get_info(sph_ctx *c, sph_info *out) {
     out->n = c->n;
     out->n_bg = c->bg.n;
     out->n_wall = c->wall.n;
+    out->n_region = c->region.n;
     double t = 0, dt = 0;
     cudaMemcpyAsync(&t, c->d_t, sizeof(double), cudaMemcpyDeviceToHost, c->s);
     if (c->have_dt) cudaMemcpyAsync(&dt, c->d_dt, sizeof(double), cudaMemcpyDeviceToHost, c->s);

@@ -20,7 +20,7 @@ SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_ECAPACITY, SPH_ENONFINITE, \
 STATUS_NAMES = ["SPH_OK", "SPH_EINVAL", "SPH_ENOMEM", "SPH_ECUDA",
                 "SPH_ECAPACITY", "SPH_ENONFINITE", "SPH_ETIMEOUT",
                 "SPH_ESTATE"]
-SPH_FLUID, SPH_WALL, SPH_BACKGROUND = 0, 1, 2
+SPH_FLUID, SPH_WALL, SPH_BACKGROUND, SPH_REGION = 0, 1, 2, 3
 SPH_FP64, SPH_MIXED = 0, 1
 
 FIELDS = ["x", "y", "u", "v", "p", "rho", "m", "h", "mmin", "mmax", "id",
@@ -93,7 +93,8 @@ class Info(ctypes.Structure):
                 ("dt", ctypes.c_double), ("c0", ctypes.c_double),
                 ("levels", ctypes.c_int), ("steps", ctypes.c_longlong),
                 ("launches", ctypes.c_longlong),
-                ("next_id", ctypes.c_longlong)]
+                ("next_id", ctypes.c_longlong),
+                ("n_region", ctypes.c_longlong)]
 
 
 _lib = None

@@ -65,6 +65,110 @@ def taylor_green(nx: int = 50, Re: float = 100.0, L: float = 1.0,
     return dict(particles=parts, params=params, dx=dx, Re=Re, L=L, U=U)
 
 
+def _lattice(lo, hi, ds):
+    """Cell-centred lattice of spacing ~ds on the box [lo, hi)."""
+    nx = max(1, int(round((hi[0] - lo[0]) / ds)))
+    ny = max(1, int(round((hi[1] - lo[1]) / ds)))
+    gx = lo[0] + (np.arange(nx) + 0.5) * (hi[0] - lo[0]) / nx
+    gy = lo[1] + (np.arange(ny) + 0.5) * (hi[1] - lo[1]) / ny
+    X, Y = np.meshgrid(gx, gy, indexing="xy")
+    return X.ravel().copy(), Y.ravel().copy()
+
+
+def _background_lattice(lo, hi, ds_max, hdx, rho0):
+    """Background particles for the construction of section 3.3: a ds_max
+    lattice over the box with h = hdx ds_max and m = rho0 ds_max^2."""
+    x, y = _lattice(lo, hi, ds_max)
+    n = x.size
+    return dict(x=x, y=y, h=np.full(n, hdx * ds_max), ds=np.full(n, ds_max),
+                m=np.full(n, rho0 * ds_max * ds_max))
+
+
+def _markers(lo, hi, ds, hdx, inside):
+    """Refinement-region markers (section 3.3, user-specified regions): a
+    ds lattice over the box kept where inside(x, y)."""
+    x, y = _lattice(lo, hi, ds)
+    keep = inside(x, y)
+    n = int(keep.sum())
+    return dict(x=x[keep], y=y[keep], h=np.full(n, hdx * ds))
+
+
+def taylor_green_adaptive(nx: int = 50, Re: float = 100.0, L: float = 1.0,
+                          hdx: float = 1.0, rho0: float = 1.0,
+                          cs: float = 10.0, U: float = 1.0,
+                          zone=(0.1, 0.5), ratio: float = 2.0,
+                          Cr: float = 1.08):
+    """Taylor-Green vortex with an inner refinement zone [0.1 L, 0.5 L]^2 at
+    `ratio` times the outer resolution (section 4.1): fluid on the outer
+    nx*nx lattice with the closed-form fields, a background lattice at
+    ds_max = L/nx to be built by sph_background, and region markers filling
+    the zone at ds_min = ds_max / ratio."""
+    d = taylor_green(nx=nx, Re=Re, L=L, hdx=hdx, rho0=rho0, cs=cs, U=U)
+    ds_max = L / nx
+    ds_min = ds_max / ratio
+    z0, z1 = zone[0] * L, zone[1] * L
+    d["params"].update(ds_min=ds_min, ds_max=ds_max, Cr=Cr)
+    d["background"] = _background_lattice((0.0, 0.0), (L, L), ds_max, hdx, rho0)
+    d["region"] = _markers((z0, z0), (z1, z1), ds_min, hdx,
+                           lambda x, y: np.ones(x.size, bool))
+    d["construct_background"] = True
+    d["zone"] = (z0, z1)
+    return d
+
+
+def gresho_chan(nx: int = 50, hdx: float = 1.0, rho0: float = 1.0,
+                cs: float = 10.0, p0: float = 5.0, R: float = 0.2,
+                adaptive: bool = True, r_region: float = 0.45,
+                mass_ratio: float = 0.5, Cr: float = 1.08):
+    """Gresho-Chan vortex (section 4.2): inviscid, periodic unit box centred
+    on the vortex, Cartesian lattice, azimuthal velocity and pressure from
+    Eqs. gc-az and gc-p (p0 = 5, R = 0.2 L).  Beyond 2R the pressure is
+    p0 + 4 log 2 - 2, the value that keeps p continuous (dp/dr = u^2 / r);
+    the printed constant 4 log 2 - 4 would leave a jump of 2 at r = 2R.  Adaptive: region markers fill
+    the half disc y >= 0 of radius r_region around the centre at the size
+    whose reference mass is mass_ratio times the outer one, and a
+    background lattice at ds_max = L / nx is to be built."""
+    L = 1.0
+    dx = L / nx
+    x, y = _lattice((-0.5, -0.5), (0.5, 0.5), dx)
+    r = np.hypot(x, y)
+    q = r / R
+    uphi = np.where(q < 1, q, np.where(q < 2, 2 - q, 0.0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        p = np.where(r < R, 12.5 * r * r,
+                     np.where(r < 2 * R,
+                              4 - 4 * math.log(0.2) + 12.5 * r * r - 20 * r
+                              + 4 * np.log(np.maximum(r, 1e-300)),
+                              4 * math.log(2.0) - 2))
+    p = p0 + p
+    rs = np.where(r > 0, r, 1.0)
+    u = -uphi * y / rs
+    v = uphi * x / rs
+    n = x.size
+    parts = dict(x=x, y=y, u=u, v=v, p=rho0 * p, rho=np.full(n, rho0),
+                 m=np.full(n, rho0 * dx * dx), h=np.full(n, hdx * dx))
+    params = _base_params(lo=(-0.5, -0.5), hi=(0.5, 0.5), periodic=(1, 1),
+                          rho0=rho0, cs=cs, nu=0.0, U_ref=1.0, hdx=hdx)
+    d = dict(particles=parts, params=params, dx=dx, R=R, p0=p0)
+    if adaptive:
+        ds_max = dx
+        ds_min = dx * math.sqrt(mass_ratio)
+        params.update(ds_min=ds_min, ds_max=ds_max, Cr=Cr)
+        d["background"] = _background_lattice((-0.5, -0.5), (0.5, 0.5),
+                                              ds_max, hdx, rho0)
+        d["region"] = _markers((-0.5, -0.5), (0.5, 0.5), ds_min, hdx,
+                               lambda xx, yy: (np.hypot(xx, yy) < r_region)
+                               & (yy >= 0))
+        d["construct_background"] = True
+    return d
+
+
+def gresho_chan_exact(x, y, R: float = 0.2):
+    """Azimuthal speed of the Gresho-Chan vortex at (x, y) (Eq. gc-az)."""
+    q = np.hypot(x, y) / R
+    return np.where(q < 1, q, np.where(q < 2, 2 - q, 0.0))
+
+
 def perturbed(nx: int = 40, ny: int = 32, L: float = 1.0, hdx: float = 1.2,
               h_ratio: float = 2.0, jitter: float = 0.15,
               periodic=(1, 1), rho0: float = 1.0, cs: float = 10.0,
