@@ -178,17 +178,18 @@ def fp32_alu_peak_tflops(sm_mhz):
 
 
 # ------------------------------------------------------------ reference --
-def cpu_sample(d, frac=0.08, seed=0):
-    """A spatial window of the graded workload (x in a band of width
-    frac*L around the middle) as a standalone set, non-periodic in x:
+def cpu_sample(d, frac=0.1):
+    """A band 0 <= y - lo < frac * Ly of the graded workload (its columns
+    are graded along x, so the band holds every resolution in the
+    workload's proportions) as a standalone set, non-periodic in y:
     bounded CPU work with the same particle shapes."""
     pt = d["particles"]
-    L = d["params"]["hi"][0] - d["params"]["lo"][0]
-    c = 0.5 * L
-    sel = np.abs(pt["x"] - c) < 0.5 * frac * L
+    lo, hi = d["params"]["lo"][1], d["params"]["hi"][1]
+    sel = pt["y"] - lo < frac * (hi - lo)
     sub = {k: v[sel].copy() for k, v in pt.items()}
-    prm = dict(d["params"], periodic=(0, 1))
-    return {"particles": sub, "params": prm}, int(sel.sum())
+    per = d["params"]["periodic"]
+    prm = dict(d["params"], periodic=(per[0], 0))
+    return {"particles": sub, "params": prm}, int(sel.sum()), frac
 
 
 def oracle_steps(d, state, steps, adaptive):
@@ -222,9 +223,9 @@ def reference_state(d, kind):
     brute force over the background, so the smaller ring set makes the
     oracle's step faster, not slower)."""
     if kind != "cylinder":
-        sd, n = cpu_sample(d, 0.1)
-        return sd, sd["particles"], "window |x-L/2|<0.05L of the workload " \
-            "(%d particles, non-periodic in x)" % n
+        sd, n, frac = cpu_sample(d)
+        return sd, sd["particles"], "band 0 <= y < %.2f L of the workload " \
+            "(%d particles, all resolutions, non-periodic in y)" % (frac, n)
     import oracle
     P = oracle.params(**d["params"])
     st = oracle.make_state(d["particles"], cap=400000)
@@ -451,7 +452,42 @@ def main():
     if dist:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_val = world * n_e * ke / float(e2e_t.item())
+    bg_state = sim.read_background() if "background" in d else None
     sim.close()
+
+    # mixed-precision error report: the mixed and FP64 paths on one state
+    # (the mixed run's final one): right-hand sides field by field
+    # (max |mixed - fp64| / max |fp64|) and the counts of one adaptation
+    def error_report():
+        out = {"rhs_rel_err": {}, "adapt": {}}
+        res = {}
+        for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
+            cap = 400000 if adaptive else n_e + 16
+            P = sph.make_params(d["params"], precision=prec, capacity=cap,
+                                bg_capacity=400000)
+            sx = sph.Simulation(P, stream)
+            sx.load(dict(state))
+            if "walls" in d:
+                sx.load(d["walls"], kind=sph.SPH_WALL)
+            if bg_state is not None:
+                sx.load(bg_state, kind=sph.SPH_BACKGROUND)
+            sx.rhs()
+            ids = sx.read("id")
+            order = np.argsort(ids)
+            res[name] = {f: sx.read(f)[order] for f in
+                         ("rho", "beta", "pavg", "drx", "dry", "dpdt", "dudt",
+                          "dvdt")}
+            if adaptive:
+                g = sx.adapt()
+                out["adapt"][name] = {k: int(g[k]) for k in
+                                      ("n_split", "n_merged", "n_after")}
+            sx.close()
+        for f, ref in res["fp64"].items():
+            sc = float(np.abs(ref).max()) or 1.0
+            out["rhs_rel_err"][f] = float(np.abs(res["mixed"][f] - ref).max()) / sc
+        return out
+
+    err_rep = error_report() if world == 1 else None
 
     # the plain FP64 GPU form on the same workload
     fp64 = None
@@ -520,6 +556,7 @@ def main():
         "cpu_baseline": cpu,
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "kind": pk_kind},
         "neighbours_mean": float(nnb.mean()),
+        "mixed_vs_fp64": err_rep,
     }
     print(json.dumps(line))
     if dist:
