@@ -214,9 +214,15 @@ sph_status sph_rhs(sph_ctx *ctx);
 /* nsteps predict-evaluate-correct steps (section 2.4, Eqs. int-pre and
  * int-cor; two right-hand sides per step; dt from Eq. timestep).  If
  * t_out is not NULL it receives the simulated time after the steps, which
- * requires one synchronisation.  Errors: SPH_ESTATE, SPH_EINVAL
- * (nsteps < 0), SPH_ENONFINITE (checked once at the end when t_out is
- * given). */
+ * requires one synchronisation.  SPH_MIXED builds the neighbour lists once
+ * per step with a skin (radius 1.1 x 3 max(h_i, h_j)) and tests membership
+ * in the passes, so both evaluations see exactly N(i); a particle that
+ * moves more than 0.15 h in the predictor (far beyond the speeds the time
+ * step allows) invalidates that and is reported.  Errors: SPH_ESTATE,
+ * SPH_EINVAL (nsteps < 0), SPH_ENONFINITE (a non-finite rate, or a
+ * particle that outran the skin; checked at the end when t_out is given,
+ * else at the next synchronising call), SPH_ECAPACITY (neighbour-list
+ * overflow, likewise). */
 sph_status sph_step(sph_ctx *ctx, int nsteps, double *t_out);
 
 /* One adaptation of the fluid particles (section 3, steps ii-iii of the

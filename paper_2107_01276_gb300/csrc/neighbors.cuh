@@ -334,6 +334,25 @@ __device__ __forceinline__ float2 anchor_rel(const Anchor &an, const float4 &p) 
                        fmaf((float)(g >> 16), an.A[1], p.y));
 }
 
+// Membership of a candidate whose FP32 anchor separation r2 is already
+// known (hi, hj: the float h of the anchor records): the band test of
+// pred_mixed, then the FP64 predicate inside the band.
+__device__ __forceinline__ bool member_r2(const Domain &d, const Anchor &an,
+                                          float r2, float hi, float hj,
+                                          double xi, double yi, double hid,
+                                          const double *__restrict__ x,
+                                          const double *__restrict__ y,
+                                          const double *__restrict__ h,
+                                          int j) {
+    const float R = 3.0f * fmaxf(hi, hj);
+    const float R2 = R * R;
+    const float band = (R2 + 4.0f * fmaxf(an.A[0], an.A[1]) * R) *
+                       (1.0f / 65536.0f);
+    if (r2 < R2 - band) return true;
+    if (r2 > R2 + band) return false;
+    return pred_fp64(d, xi, yi, hid, __ldg(&x[j]), __ldg(&y[j]), __ldg(&h[j]));
+}
+
 // Mixed-path predicate: FP32 test on anchor separations, FP64 predicate
 // inside the uncertainty band.  The FP32 separation's absolute error is
 // below (4 A + 2 |dx|) 2^-24 per axis (anchor offsets rounded to FP32, one

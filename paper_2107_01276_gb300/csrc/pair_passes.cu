@@ -14,6 +14,23 @@
 
 namespace sph {
 
+// Membership test of a list entry when the lists carry a skin: the exact
+// predicate of N(i) on the separation the pass already has (FP32 band test
+// with the FP64 predicate inside the band on the mixed path; the FP64
+// predicate on the FP64 path).
+template <typename R>
+__device__ __forceinline__ bool skin_member(const Domain &d, const Anchor &an,
+                                            R r2, R hi, R hj, double xi,
+                                            double yi, double hid,
+                                            const double *x, const double *y,
+                                            const double *h, int j) {
+    if constexpr (sizeof(R) == 4) {
+        return member_r2(d, an, r2, hi, hj, xi, yi, hid, x, y, h, j);
+    } else {
+        return pred_fp64(d, xi, yi, hid, __ldg(&x[j]), __ldg(&y[j]), __ldg(&h[j]));
+    }
+}
+
 // ---------------------------------------------------------------- pass A --
 // Summation density (Eq. sd-gather), beta (Eq. beta), p_avg (Eq. pavg,
 // N_i counts i), shift dr (Eq. shift-deltar, volume m_j / rho0, W ratio
@@ -55,10 +72,14 @@ __global__ void __launch_bounds__(128)
         }
     };
     const uint32_t b = a.off[i], e = a.off[i + 1];
+    const double xid = a.x[i], yid = a.y[i], hid = a.h[i];
     for (uint32_t k = b + tm.lane; k < e; k += T) {
         const int j = (int)__ldg(&a.list[k]);
         R dx, dy, r2, hj;
         sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
+        if (a.filter && !skin_member<R>(a.d, a.an, r2, hi, hj, xid, yid, hid,
+                                        a.x, a.y, a.h, j))
+            continue;
         pair(a.m[j], hj, a.p[j], j == i, dx, dy, r2);
     }
     if (a.w.n > 0) {
@@ -185,11 +206,21 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 1)
     };
     const uint32_t b = a.off[i], e = a.off[i + 1];
     const bool literal = a.pavg_mode != 0;
+    const double xid = a.x[i], yid = a.y[i], hid = a.h[i];
+    const R hpk = (R)a.pk[i].z;   // h_i as the list builder saw it
     for (uint32_t k = b + tm.lane; k < e; k += T) {
         const int j = (int)__ldg(&a.list[k]);
         if (j == i) continue;
         R dx, dy, r2;
-        sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+        if (a.filter) {
+            R hj;
+            sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
+            if (!skin_member<R>(a.d, a.an, r2, hpk, hj, xid, yid, hid, a.x,
+                                a.y, a.h, j))
+                continue;
+        } else {
+            sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+        }
         const typename V4<R>::T A = a.nbA[j], B = a.nbB[j];
         const R pref = literal ? a.pavg[j] : pavg_i;
         pair(dx, dy, r2, B.w, A.x, A.y, A.z, (B.x - pref) * A.w, B.x, B.y,
@@ -241,8 +272,8 @@ __global__ void __launch_bounds__(128) k_wall_bc(WallBcArgs a) {
     const float4 pw = a.w.pk[k];
     const float2 q = anchor_rel(a.an, pw);
     double sw = 0, su = 0, sv = 0, sp = 0;
-    for_each_cell_team<T>(a.g, a.d, 0, q.x, q.y, pw.z, tm.lane, tm.mask,
-                          [&](uint32_t s, uint32_t e) {
+    for_each_cell_team_scaled<T>(a.g, a.d, 0, q.x, q.y, pw.z, a.qscale, tm.lane,
+                                 tm.mask, [&](uint32_t s, uint32_t e) {
         for (uint32_t f = s + tm.lane; f < e; f += T) {
             float fx, fy, fr2;
             if (!pred_mixed(a.d, a.an, pw, __ldg(&a.pk[f]), xw, yw, hw, a.x,
@@ -331,6 +362,12 @@ __global__ void k_pec(PecArgs<R> a) {
             yn = __dsub_rn(yn, a.d.L[1]);
         else if (yn < a.d.lo[1])
             yn = __dadd_rn(yn, a.d.L[1]);
+    }
+    if (a.skin_err) {
+        const double mx = min_image(a.d, 0, __dsub_rn(xn, x0));
+        const double my = min_image(a.d, 1, __dsub_rn(yn, y0));
+        const double lim = a.disp_lim * a.h[i];
+        if (mx * mx + my * my > lim * lim) atomicOr(a.skin_err, 1);
     }
     a.x[i] = xn;
     a.y[i] = yn;

@@ -25,6 +25,7 @@ struct PassAArgs {
     // per-particle records for pass B: {m, V, rho, 1/(rho^2 beta)} and
     // {p, u, v, 1/h}
     typename V4<R>::T *nbA, *nbB;
+    int filter;                // 1: lists with a skin, test membership
 };
 
 template <typename R>
@@ -44,6 +45,7 @@ struct PassBArgs {
     int pavg_mode, diff_denominator, rho_factor;
     R *dpdt, *dudt, *dvdt;
     int *nonfinite;
+    int filter;                // 1: lists with a skin, test membership
 };
 
 template <typename R>
@@ -53,6 +55,11 @@ struct PecArgs {
     double f;                  // 0.5 predict, 1.0 correct
     int save;                  // 1: the current x, y, u, v, p are the stage
                                // start; copy them into x0..p0 first
+    // with skin_err: a particle moving more than disp_lim h in this stage
+    // sets *skin_err (the neighbour lists of the step no longer hold N(i))
+    const double *h;
+    double disp_lim;
+    int *skin_err;
     const double *dt;
     const double *x0, *y0, *u0, *v0, *p0;
     const R *dudt, *dvdt, *dpdt, *drx, *dry;

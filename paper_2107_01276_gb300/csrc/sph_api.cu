@@ -158,6 +158,8 @@ struct sph_ctx {
     // list sizing: entry total and particle count of the last build that
     // read its total back, for exact lists and for lists with a skin
     uint32_t last_total = 0, last_total_skin = 0;
+    float skin = 1.0f;          // skin factor of the current lists (1: exact)
+    int *d_skin_err = nullptr;  // set when particles outran the skin
     int last_total_n = 0, last_total_skin_n = 0;
     long long steps = 0;
     int launches = 0;
@@ -404,6 +406,7 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true,
     pack(c, true);
     ListArgs la = list_args(c);
     la.skin = skin;
+    c->skin = skin;
     {
         cudaEvent_t ew;
         t_begin(c, 5, &ew);
@@ -453,9 +456,6 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true,
     return cuda_check(c, "rebuild");
 }
 
-// Mixed path: refresh float mirrors of the fields PEC changed without a
-// rebuild in between (not needed: every RHS follows a rebuild).
-
 template <typename R>
 static void passes(sph_ctx *c) {
     PassAArgs<R> a;
@@ -491,6 +491,7 @@ static void passes(sph_ctx *c) {
     a.V = (R *)c->V;
     a.rb2 = (R *)c->rb2;
     a.nnb = c->nnb;
+    a.filter = c->skin > 1.0f ? 1 : 0;
     cudaEvent_t ev;
     t_begin(c, 1, &ev);
     launch_pass_a<R>(c->s, a);
@@ -537,6 +538,7 @@ static void passes(sph_ctx *c) {
     b.dudt = (R *)c->dudt;
     b.dvdt = (R *)c->dvdt;
     b.nonfinite = c->d_nonfinite;
+    b.filter = a.filter;
     t_begin(c, 0, &ev);
     launch_pass_b<R>(c->s, b);
     t_end(c, 0, ev);
@@ -551,6 +553,7 @@ static void run_passes(sph_ctx *c) {
         wb.pk = c->pk;
         wb.w = wall_view(c);
         wb.g = grid_for_kernels(c);
+        wb.qscale = c->skin;
         wb.d = c->dom;
         wb.x = c->f[F_X];
         wb.y = c->f[F_Y];
@@ -577,6 +580,11 @@ static void pec(sph_ctx *c, double f) {
     a.d = c->dom;
     a.f = f;
     a.save = f < 1.0 ? 1 : 0;   // the predictor starts the step: keep x0..p0
+    a.h = c->f[F_H];
+    // with skin lists, the predictor's moves must stay within the skin: a
+    // pair approaches by at most 2 disp_lim max(h) <= (skin - 1) 3 max(h)
+    a.disp_lim = 1.5 * ((double)c->skin - 1.0);
+    a.skin_err = (a.save && c->skin > 1.0f) ? c->d_skin_err : nullptr;
     a.dt = c->d_dt;
     a.x0 = c->f[F_X0];
     a.y0 = c->f[F_Y0];
@@ -637,7 +645,7 @@ static void free_ctx(sph_ctx *c) {
                   c->tkey, c->tstart, c->tend, c->tmaxh, c->bbox, c->level_mask,
                   c->cnt_tmp, c->d_dt, c->d_t, c->d_hmin, c->d_nonfinite,
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
-                  c->d_overflow, c->longq, c->d_nlong, c->stage, c->lqueue, c->d_max_own,
+                  c->d_overflow, c->d_skin_err, c->longq, c->d_nlong, c->stage, c->lqueue, c->d_max_own,
                   c->d_nlq, c->tmp_a, c->tmp_b,
                   c->closest, c->d_mass, c->d_mass_part, c->wp, c->wugx,
                   c->wugy, c->d_aux};
@@ -980,6 +988,7 @@ static sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
          dalloc(&c->cnt_tmp, N + 1);
     ok = ok && dalloc(&c->d_dt, 1) && dalloc(&c->d_t, 1) && dalloc(&c->d_hmin, 1) &&
          dalloc(&c->d_nonfinite, 1) && dalloc(&c->d_total, 1) &&
+         dalloc(&c->d_skin_err, 1) &&
          dalloc(&c->d_overflow, 1);
     ok = ok && dalloc(&c->lvl, N) && dalloc(&c->pk, N) && dalloc(&c->own, N) &&
          dalloc(&c->rev, N) && dalloc(&c->off, N + 1) &&
@@ -1001,6 +1010,7 @@ static sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
     cudaMemsetAsync(c->d_t, 0, sizeof(double), c->s);
     cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->s);
     cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
+    cudaMemsetAsync(c->d_skin_err, 0, sizeof(int), c->s);
     if (cudaGetLastError() != cudaSuccess) {
         free_ctx(c);
         delete c;
@@ -1284,12 +1294,20 @@ static sph_status bg_iteration(sph_ctx *c, sph_ctx *b, bool vort,
 }
 
 // Reports (and clears) a neighbour-list overflow of a build that ran
-// without its sizing synchronisation; synchronises.
+// without its sizing synchronisation, and particles that outran the skin
+// of a step's lists; synchronises.
 static sph_status check_overflow(sph_ctx *c, const char *who) {
-    int ovf = 0;
-    cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    int flags[2] = {0, 0};
+    cudaMemcpyAsync(&flags[0], c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(&flags[1], c->d_skin_err, sizeof(int), cudaMemcpyDeviceToHost, c->s);
     if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, who);
-    if (!ovf) return SPH_OK;
+    if (flags[1]) {
+        cudaMemsetAsync(c->d_skin_err, 0, sizeof(int), c->s);
+        return fail(c, SPH_ENONFINITE,
+                    std::string(who) + ": particles moved farther than the neighbour-list "
+                    "skin within one step (flow speed far above U_ref + cs)");
+    }
+    if (!flags[0]) return SPH_OK;
     cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
     c->last_total = c->last_total_skin = 0;   // next builds size exactly
     return fail(c, SPH_ECAPACITY, std::string(who) + ": neighbour list overflow");
@@ -1455,14 +1473,24 @@ sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
     c->err.clear();
     if (nsteps < 0) return fail(c, SPH_EINVAL, "sph_step: nsteps < 0");
     if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_step: no fluid particles loaded");
+    // Mixed path: one neighbour build per step, with a skin that holds N(i)
+    // through the predictor's moves (checked on the device; a particle
+    // outrunning it is reported as an error at the next synchronisation).
+    // FP64 path: a fresh build before each evaluation (wider lists would
+    // cost more FP64 pair work than the build they save).
+    const float step_skin = is_mixed(c) ? 1.1f : 1.0f;
     for (int s = 0; s < nsteps; ++s) {
         compute_dt(c, c->d_t, 1);
-        sph_status st = rebuild(c, false, s == 0);
+        sph_status st = rebuild(c, false, s == 0, step_skin);
         if (st != SPH_OK) return st;
         run_passes(c);
         run_pec(c, 0.5);
-        st = rebuild(c, true, false);
-        if (st != SPH_OK) return st;
+        if (step_skin > 1.0f) {
+            pack(c, false);   // anchor records and mirrors at the predicted state
+        } else {
+            st = rebuild(c, true, false);
+            if (st != SPH_OK) return st;
+        }
         run_passes(c);
         run_pec(c, 1.0);
         store_rho(c);
@@ -1474,17 +1502,12 @@ sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
     if (st != SPH_OK) return st;
     if (t_out) {
         double t = 0;
-        int bad = 0, ovf = 0;
+        int bad = 0;
         cudaMemcpyAsync(&t, c->d_t, sizeof(double), cudaMemcpyDeviceToHost, c->s);
         cudaMemcpyAsync(&bad, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->s);
-        cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
         if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_step sync");
         *t_out = t;
-        if (ovf) {
-            cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
-            c->last_total = c->last_total_skin = 0;   // next builds size exactly
-            return fail(c, SPH_ECAPACITY, "sph_step: neighbour list overflow during the steps");
-        }
+        if ((st = check_overflow(c, "sph_step")) != SPH_OK) return st;
         if (bad) return fail(c, SPH_ENONFINITE, "sph_step: non-finite rate");
     }
     return SPH_OK;
@@ -1618,16 +1641,10 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     c->rhs_valid = false;
     double mass[2] = {0, 0};
     uint32_t nfb = 0;
-    int ovf = 0;
     cudaMemcpyAsync(mass, c->d_mass, sizeof(mass), cudaMemcpyDeviceToHost, c->s);
     cudaMemcpyAsync(&nfb, c->d_aux, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
-    cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, c->s);
     if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_adapt");
-    if (ovf) {
-        cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
-        c->last_total = c->last_total_skin = 0;   // next builds size exactly
-        return fail(c, SPH_ECAPACITY, "sph_adapt: neighbour list overflow during the call");
-    }
+    if ((st = check_overflow(c, "sph_adapt")) != SPH_OK) return st;
     z.mass_before = mass[0];
     z.mass_after = mass[1];
     z.n_bg_nearest = nfb;

@@ -47,6 +47,7 @@ __device__ __forceinline__ void for_each_wall(const WallView &w,
 struct WallBcArgs {
     WallView w;
     Grid g;                       // fluid cell structure
+    float qscale;                 // >= 1: the fluid moved since it was binned
     Domain d;
     Anchor an;
     const float4 *pk;             // fluid anchor data
