@@ -217,8 +217,9 @@ sph_status sph_rhs(sph_ctx *ctx);
  * requires one synchronisation.  SPH_MIXED builds the neighbour lists once
  * per step with a skin (radius 1.1 x 3 max(h_i, h_j)) and tests membership
  * in the passes, so both evaluations see exactly N(i); a particle that
- * moves more than 0.15 h in the predictor (far beyond the speeds the time
- * step allows) invalidates that and is reported.  Errors: SPH_ESTATE,
+ * moves more than 0.15 h in the predictor invalidates that and is
+ * reported (the time step and the shift limit keep moves below 0.15 h for
+ * speeds up to 0.2 (U_ref + cs), i.e. Mach 0.2).  Errors: SPH_ESTATE,
  * SPH_EINVAL (nsteps < 0), SPH_ENONFINITE (a non-finite rate, or a
  * particle that outran the skin; checked at the end when t_out is given,
  * else at the next synchronising call), SPH_ECAPACITY (neighbour-list
