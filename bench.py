@@ -80,6 +80,11 @@ WORKLOADS = {
     # graded over 1:250 by C_r per column, u,v ~ N(0, 0.1),
     # rho = 1 + U(-0.01, 0.01); PEC steps, no adaptation
     "graded-1M": dict(kind="graded", n_target=1 << 20, ratio=250.0),
+    # configs[4] shape: a stream of independent adaptive simulations (half
+    # cylinders at Re log-uniform in [20, 2000], half Taylor-Green vortices
+    # at Re in [50, 500]), Poisson arrivals at 20/s, served concurrently
+    "serving": dict(kind="serving", requests=32, rate=20.0, slots=8,
+                    steps=40, sizes=(5000, 50000)),
 }
 DEFAULT_WORKLOAD = "cylinder-re40"
 
@@ -250,6 +255,11 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if WORKLOADS[args.workload]["kind"] == "serving":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the oracle runs one simulation at a time; the "
+                          "serving workload has no reference arm"}))
+        return 0
     d, desc = make_workload(args.workload)
     kind = WORKLOADS[args.workload]["kind"]
     dd, state, sample = reference_state(d, kind)
@@ -273,6 +283,55 @@ def reference_arm(args):
     return 0
 
 
+# ------------------------------------------------------------- serving ----
+def serving_arm(args):
+    """The serving workload: requests admitted by free HBM and slots, each
+    simulation resident in its own context on its own stream; value is the
+    particle-steps of all requests over the wall time of the whole run
+    (set-up of each request included), with per-step latency percentiles."""
+    import torch
+    from paper_2107_01276_gb300 import serve, sph
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    sph.lib()
+    w = WORKLOADS[args.workload]
+    reqs = serve.c5_requests(n=w["requests"], rate=w["rate"],
+                             seed=7 + rank, steps=w["steps"], sizes=w["sizes"])
+    srv = serve.Server(slots=w["slots"])
+    clk = ClockSampler(local)
+    clk.start()
+    rep = srv.run(reqs)
+    clocks = clk.stop()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "particle-steps/s", "value": rep["particle_steps_per_s"] * world,
+        "unit": "particle-steps/s", "n_gpus": world, "steps": rep["steps"],
+        "warmup": 0, "ms_per_step": rep["step_ms_p50"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-pair/f64-state", "data": "synthetic",
+        "config": {"workload": "serving", "requests": w["requests"],
+                   "arrival_rate_per_s": w["rate"], "slots": w["slots"],
+                   "steps_per_request": w["steps"],
+                   "particles": list(w["sizes"]),
+                   "desc": "half flow past a cylinder (Re log-uniform "
+                           "[20, 2000], adapt every step), half Taylor-Green "
+                           "(Re uniform [50, 500]); Poisson arrivals; each "
+                           "request's set-up (background construction, "
+                           "refinement) inside the wall time"},
+        "latency_ms": {"p50": rep["step_ms_p50"], "p99": rep["step_ms_p99"]},
+        "serving": rep,
+        "clocks": clocks,
+        "e2e": {"value": rep["particle_steps_per_s"] * world,
+                "unit": "particle-steps/s", "h2d_bytes_per_step": None,
+                "d2h_bytes_per_step": None},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 # ---------------------------------------------------------------- ours ----
 def main():
     ap = argparse.ArgumentParser()
@@ -292,6 +351,8 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return reference_arm(args)
+    if WORKLOADS[args.workload]["kind"] == "serving":
+        return serving_arm(args)
 
     import ctypes
 

@@ -227,6 +227,7 @@ class Server:
             "step_ms_p99": float(np.percentile(lat, 99)) if lat.size else None,
             "queue_s_mean": float(np.mean([r.admitted - r.arrival for r in
                                            requests])) if requests else None,
+            "errors": sorted({r.error for r in requests if r.error}),
         }
 
 
@@ -252,8 +253,10 @@ def c5_requests(n: int = 256, rate: float = 20.0, seed: int = 7,
             inv = min(100.0, max(25.0, 50.0 * (target / 9000.0) ** (1 / 1.2)))
             d = wl.cylinder(Re=Re, ds_min_over_D=1.0 / inv)
             bgc = int(1.5 * 101268 * (inv / 50.0) ** 2) + 50000
+            # refined fluid: ~9k at D/50, growing about as (D/ds_min)^1.2
+            cap = int(4 * 9000 * (inv / 50.0) ** 1.2) + 20000
             reqs.append(Request(k, d, steps, adapt_every=1, refine=12,
-                                arrival=t, bg_capacity=bgc))
+                                arrival=t, capacity=cap, bg_capacity=bgc))
         else:
             Re = rng.uniform(50.0, 500.0)
             nx = int(round(math.sqrt(target)))
