@@ -73,14 +73,14 @@ def walk_traffic(workload):
     return rec.get("dram_bytes_per_launch")
 
 WORKLOADS = {
-    # configs[1]: flow past a cylinder at Re 40, spacing graded from D/50 at
+    # flow past a cylinder at Re 40, spacing graded from D/50 at
     # the wall to D/2 (1:25), split/merge every step
     "cylinder-re40": dict(kind="cylinder", Re=40.0, refine_calls=12),
     # pair-kernel sweep shape at N ~ 1M: 2-D periodic square, spacing
     # graded over 1:250 by C_r per column, u,v ~ N(0, 0.1),
     # rho = 1 + U(-0.01, 0.01); PEC steps, no adaptation
     "graded-1M": dict(kind="graded", n_target=1 << 20, ratio=250.0),
-    # configs[4] shape: a stream of independent adaptive simulations (half
+    # a stream of independent adaptive simulations (half
     # cylinders at Re log-uniform in [20, 2000], half Taylor-Green vortices
     # at Re in [50, 500]), Poisson arrivals at 20/s, served concurrently
     "serving": dict(kind="serving", requests=32, rate=20.0, slots=8,

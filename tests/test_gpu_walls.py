@@ -1,6 +1,6 @@
 """Parity of the dummy-wall boundary (section 2.2) on the GPU with the
 oracle: right-hand sides and PEC steps next to a wall, and the cylinder
-workload (walls, background, adaptation) at the size of configs[1].  Every
+workload (walls, background, adaptation) at the bench's size (D/50 to D/2).  Every
 oracle input comes from the seeded generators or from the oracle itself."""
 import math
 
@@ -147,7 +147,7 @@ def test_cylinder_adapt_parity(cyl_oracle, call):
 
 @pytest.fixture(scope="module")
 def cyl_refined():
-    """configs[1]-shaped cylinder refined on the GPU alone: the coarse
+    """The bench-sized cylinder (D/50 at the wall, D/2 far away) refined on the GPU alone: the coarse
     lattice through 12 sph_adapt calls against the ring background."""
     if not cuda_ok():
         pytest.skip("no CUDA device")
@@ -192,7 +192,7 @@ def test_cylinder_rhs_parity(cyl_oracle, precision, tol):
 
 
 def test_cylinder_constructed_background():
-    """configs[1] set-up as the bench runs it: the ds_max lattice refined by
+    """The cylinder set-up as the bench runs it: the ds_max lattice refined by
     the full construction (3 ceil(log 25 / log 1.08) = 126 iterations) on
     the GPU: ds_min next to the cylinder, ds_max far away, sizes growing
     outward, mass of the background conserved."""
