@@ -147,26 +147,30 @@ def test_taylor_green_decay_on_gpu(precision):
 
 def test_taylor_green_200_steps_parity():
     """The full 50x50 Taylor-Green run at Re 100: 200 FP64 PEC steps on the
-    GPU and in the oracle from the same state; the sum-order rounding
-    accumulated over the run stays far below the fields (the decay against
-    the closed form is tested below)."""
+    GPU and in the oracle from the same state.  Element by element the two
+    runs part after some tens of steps: on the unperturbed lattice many
+    pairs sit exactly at r = 3h, and rounding-level differences in the sums
+    flip their membership (and with it N_i in p_avg); a 1e-15 perturbation
+    of the oracle's own input spreads x by 1e-2 after 200 steps.  What the
+    run fixes is its flow statistics: max |u| and the kinetic energy, whose
+    spread under that perturbation is 3e-5 relative, and the mass (exact)."""
     d = wl.taylor_green(nx=50, Re=100)
     sim = _sim(d, sph.SPH_FP64)
     t = sim.step(200)
-    got = by_id(sim, ["x", "y", "u", "v", "p"])
+    got = by_id(sim, ["u", "v", "m"])
+    sim.close()
     P = oracle.params(**d["params"])
     st = oracle.make_state(d["particles"])
     tr = oracle.step(P, st, 200)
     assert abs(t - tr) <= 1e-13 * tr
     n = st["n"]
-    for f in ("x", "y"):
-        dxy = got[f] - st[f][:n]
-        dxy -= np.round(dxy)
-        assert np.abs(dxy).max() <= 1e-9 * d["dx"], f
-    for f in ("u", "v", "p"):
-        scale = np.abs(st[f][:n]).max()
-        assert np.abs(got[f] - st[f][:n]).max() <= 1e-9 * scale, f
-    sim.close()
+    ug = np.hypot(got["u"], got["v"])
+    uo = np.hypot(st["u"][:n], st["v"][:n])
+    assert abs(ug.max() / uo.max() - 1) < 2e-4
+    ke_g = 0.5 * np.sum(got["m"] * ug * ug)
+    ke_o = 0.5 * np.sum(st["m"][:n] * uo * uo)
+    assert abs(ke_g / ke_o - 1) < 2e-4
+    assert np.array_equal(got["m"], st["m"][:n])
 
 
 def test_edge_cases():
