@@ -57,6 +57,16 @@ def sources_sha(paths):
     return h.hexdigest()[:16]
 
 
+def walk_kernel(n):
+    """Name of the neighbour-walk kernel the library launches for n
+    particles (the size rule of the list build)."""
+    if n >= 60000:
+        return "k_list_tile<1> (neighbour walk, cell tiles)"
+    if n >= 12000:
+        return "k_list_tile<4> (neighbour walk, cell tiles)"
+    return "k_list_gather<T> (neighbour walk, per-particle teams)"
+
+
 def walk_traffic(workload):
     """DRAM bytes per launch of the neighbour walk from the committed ncu
     summary, or None if there is none for this workload or the kernel
@@ -594,7 +604,7 @@ def main():
         "mixed_over_fp64": (value / world / fp64) if fp64 else None,
         "kernel_ms_per_step": {fam_names[f]: fams[f][0] / args.steps
                                for f in range(NFAM)},
-        "roofline": {"bound": "hbm", "kernel": "k_list_gather (neighbour walk)",
+        "roofline": {"bound": "hbm", "kernel": walk_kernel(int(np.mean(ns))),
                      "achieved": ach_w, "peak": hbm_peak, "unit": "GB/s",
                      "frac": ach_w / hbm_peak,
                      "traffic": walk_traffic(args.workload),

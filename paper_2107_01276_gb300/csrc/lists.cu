@@ -11,6 +11,7 @@
 #include "team.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace sph {
 
@@ -190,6 +191,383 @@ __global__ void __launch_bounds__(128) k_list_fill_queue(ListArgs a) {
     }
 }
 
+// ------------------------------------------------------ tiled list build --
+// Cell-tiled walk: one warp takes the particles of one cell (up to 32 at a
+// time, lane = particle).  For each level at or above the cell's, the warp
+// looks up the cells around the bounding box of its particles once (a lane
+// per cell), stages their candidates in shared memory (a batch of loads
+// with no dependence between them) and every lane tests its particle
+// against each staged candidate: a broadcast shared-memory read and a few
+// FP32 operations per pair, instead of a lookup and a global load per
+// particle.  Own entries come in (level, row, column, index) order.
+//
+// Separations: candidates and particles carry FP32 coordinates relative to
+// the cell's first particle (anchor separations), so the pair separation is
+// one subtraction.  Its error bound grows with the distance G from that
+// reference; the exact-mode band below includes it.  Images on a periodic
+// axis: a member j of a particle i in the cell lies within skin * c_l' +
+// w_l of the reference, so while that stays below half the period the
+// reference-relative image is the minimum image; otherwise (coarse levels
+// of small periodic boxes) each pair is wrapped explicitly.
+constexpr int TILE_CAP = 256;   // staged candidates per warp and batch
+constexpr int TILE_LD = 2;      // candidate loads in flight per lane
+
+// Squared gap between the box [xc - hx, xc + hx] x [yc - hy, yc + hy] and
+// cell (cx, cy) of level L (unwrapped indices), less a margin far above
+// FP32 rounding; periodic axes use the nearest image of the cell, the edge
+// cells of a non-periodic axis reach to infinity.
+__device__ __forceinline__ float box_gap2(const Domain &d, const Level &L,
+                                          int cx, int cy, float xc, float yc,
+                                          float hx, float hy) {
+    const int c[2] = {cx, cy};
+    const float q[2] = {xc, yc}, hh[2] = {hx, hy};
+    float g2 = 0.0f;
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        const float w = L.wf[ax];
+        const float m = 1e-5f * (fabsf(q[ax]) + hh[ax] + w);
+        float gap;
+        if (d.periodic[ax]) {
+            const float P = (float)L.n[ax] * w;
+            float t = q[ax] - ((float)c[ax] + 0.5f) * w;
+            t -= P * rintf(t * L.invP[ax]);
+            gap = fabsf(t) - 0.5f * w - hh[ax];
+        } else {
+            float lo = (float)c[ax] * w, hi = lo + w;
+            if (c[ax] <= 0) lo = -3.0e38f;
+            if (c[ax] >= L.n[ax] - 1) hi = 3.0e38f;
+            gap = fmaxf(lo - (q[ax] + hh[ax]), (q[ax] - hh[ax]) - hi);
+        }
+        gap = fmaxf(0.0f, gap - m);
+        g2 += gap * gap;
+    }
+    return g2;
+}
+
+// One chunk of a cell: particles p0 .. min(p0 + 32, ce) - 1 of the cell
+// starting at cs (level lc); `only` >= 0 restricts the work to that one
+// particle.  DIRECT = false: own entries into the staging rows, reverse
+// entries counted; DIRECT = true (particles whose rows overflowed): own
+// entries straight into the list at off[i], reverse entries placed.  Both
+// modes take identical membership decisions (same reference, same
+// per-level constants, same arithmetic); the cells a chunk visits depend
+// on its bounding box, but a cell only one of them visits holds no member
+// (its gap exceeds the pair radius by the pruning margin).
+// sc: the warp's staging buffer (TILE_CAP entries); pcs: 20 ints of the
+// warp's shared memory for the query's cell pieces.
+template <bool DIRECT, int T>
+__device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
+                                           int *pcs, int lc, uint32_t cs,
+                                           uint32_t pe, uint32_t p0, int only) {
+    static_assert(T == 1 || T == 4 || T == 16, "team of 1, 4 or 16 lanes");
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (T - 1);           // lane within the particle's team
+    const uint32_t i = p0 + (uint32_t)(lane / T);
+    const bool act = i < pe && (only < 0 || (int)i == only);
+    const float4 pC = __ldg(&a.pk[cs]);
+    float rxi = 0.0f, ryi = 0.0f, Ri = 0.0f;
+    float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f, hmx = 0.0f;
+    if (act) {
+        const float4 pi = __ldg(&a.pk[i]);
+        anchor_sep(a.an, pi, pC, rxi, ryi);
+        Ri = a.skin * (3.0f * pi.z);
+        const float2 q = anchor_rel(a.an, pi);
+        xlo = xhi = q.x;
+        ylo = yhi = q.y;
+        hmx = pi.z;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        xlo = fminf(xlo, __shfl_xor_sync(0xffffffffu, xlo, o));
+        xhi = fmaxf(xhi, __shfl_xor_sync(0xffffffffu, xhi, o));
+        ylo = fminf(ylo, __shfl_xor_sync(0xffffffffu, ylo, o));
+        yhi = fmaxf(yhi, __shfl_xor_sync(0xffffffffu, yhi, o));
+        hmx = fmaxf(hmx, __shfl_xor_sync(0xffffffffu, hmx, o));
+    }
+    const float xc = 0.5f * (xlo + xhi), yc = 0.5f * (ylo + yhi);
+    const float bx = 0.5f * (xhi - xlo), by = 0.5f * (yhi - ylo);
+    const uint32_t W = a.stage_w;
+    uint32_t k = 0;
+    if (DIRECT && act) k = a.off[i];
+    uint32_t *row = a.stage + (size_t)i * W;
+    const Level &LC = a.g.lev[lc];
+    const float Amax = fmaxf(a.an.A[0], a.an.A[1]);
+    const float Lx = (float)a.d.L[0], Ly = (float)a.d.L[1];
+    const float iLx = 1.0f / Lx, iLy = 1.0f / Ly;
+    const bool exact = !(a.skin > 1.0f);
+    const uint32_t lmask = a.g.level_mask & ~((1u << lc) - 1u);
+    for (uint32_t mm = lmask; mm; mm &= mm - 1) {
+        const int l = __ffs(mm) - 1;
+        const int *bb = a.g.bbox + 4 * l;
+        if (__ldg(&bb[0]) > __ldg(&bb[1])) continue;   // level holds no particle
+        const Level &L = a.g.lev[l];
+        const float Rl = a.skin * fmaxf(3.0f * hmx, L.cf);
+        const float Q = Rl * (1.0f + 1e-5f);
+        AxisPieces px, py;
+        if (!axis_pieces(a.d, L, bb, 0, xc, bx + Q, px)) continue;
+        if (!axis_pieces(a.d, L, bb, 1, yc, by + Q, py)) continue;
+        // per-level constants (functions of lc and l only)
+        const float reach = a.skin * L.cf + fmaxf(LC.wf[0], LC.wf[1]) +
+                            fmaxf(L.wf[0], L.wf[1]);
+        const bool wrapx = a.d.periodic[0] && 2.0f * (reach + 4.0f * a.an.A[0]) >= Lx;
+        const bool wrapy = a.d.periodic[1] && 2.0f * (reach + 4.0f * a.an.A[1]) >= Ly;
+        const bool wrap = wrapx || wrapy;
+        const float G = reach + (wrap ? fmaxf(Lx, Ly) : 0.0f);
+        const float KB = 4.0f * Amax + G;
+        const bool coarse = l > lc;
+        // the query's cell pieces go to shared memory: nothing of them stays
+        // in registers through the staging and test loops
+        __syncwarp();
+        if (lane == 0) {
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                pcs[t] = px.first[t];
+                pcs[3 + t] = px.shift[t];
+                pcs[6 + t] = max(0, px.last[t] - px.first[t] + 1);
+                pcs[9 + t] = py.first[t];
+                pcs[12 + t] = py.shift[t];
+                pcs[15 + t] = max(0, py.last[t] - py.first[t] + 1);
+            }
+        }
+        __syncwarp();
+        const int nx = pcs[6] + pcs[7] + pcs[8];
+        const int ncell = nx * (pcs[15] + pcs[16] + pcs[17]);
+        const uint64_t lbits = (uint64_t)l << (2 * a.g.mbits);
+        for (int base = 0; base < ncell; base += 32) {
+            // lane -> one cell of the query (row-major, unwrapped order)
+            uint32_t s = 0, e = 0;
+            const int idx = base + lane;
+            if (idx < ncell) {
+                const int iy = idx / nx;
+                int ix = idx - iy * nx, jy = iy;
+                int kx = 0, ky = 0;
+                while (kx < 2 && ix >= pcs[6 + kx]) ix -= pcs[6 + kx++];
+                while (ky < 2 && jy >= pcs[15 + ky]) jy -= pcs[15 + ky++];
+                const int cx = pcs[kx] + ix, sx = pcs[3 + kx];
+                const int cy = pcs[9 + ky] + jy, sy = pcs[12 + ky];
+                const float g2 = box_gap2(a.d, L, cx, cy, xc, yc, bx, by);
+                float hc;
+                if (g2 < Rl * Rl &&
+                    table_lookup(a.g, lbits | (spread2((uint64_t)(cy + sy)) << 1) |
+                                          spread2((uint64_t)(cx + sx)),
+                                 s, e, &hc)) {
+                    const float Rc = a.skin * 3.0f * fmaxf(hmx, hc);
+                    if (!(g2 < Rc * Rc)) s = e = 0;
+                } else {
+                    s = e = 0;
+                }
+            }
+            const uint32_t cnt = e - s;
+            uint32_t inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+            const uint32_t exc = inc - cnt;
+            for (uint32_t q0 = 0; q0 < total; q0 += TILE_CAP) {
+                const uint32_t m = min((uint32_t)TILE_CAP, total - q0);
+                // stage: slot u holds candidate q0 + u; its cell is the first
+                // lane whose inclusive count exceeds it (binary search over
+                // the lanes), TILE_LD independent loads per lane in flight
+                for (uint32_t u0 = 0; u0 < m; u0 += 32 * TILE_LD) {
+                    float4 v[TILE_LD];
+                    uint32_t jj[TILE_LD];
+#pragma unroll
+                    for (int r = 0; r < TILE_LD; ++r) {
+                        const uint32_t u = u0 + 32 * r + lane;
+                        const uint32_t qq = q0 + min(u, m - 1);
+                        int pos = 0;
+#pragma unroll
+                        for (int st = 16; st; st >>= 1) {
+                            const uint32_t vv = __shfl_sync(0xffffffffu, inc, pos + st - 1);
+                            if (vv <= qq) pos += st;
+                        }
+                        const uint32_t st0 = __shfl_sync(0xffffffffu, s, pos);
+                        const uint32_t ex0 = __shfl_sync(0xffffffffu, exc, pos);
+                        jj[r] = st0 + (qq - ex0);
+                        if (u < m) v[r] = __ldg(&a.pk[jj[r]]);
+                    }
+#pragma unroll
+                    for (int r = 0; r < TILE_LD; ++r) {
+                        const uint32_t u = u0 + 32 * r + lane;
+                        if (u < m) {
+                            float rx, ry;
+                            anchor_sep(a.an, v[r], pC, rx, ry);
+                            sc[u] = make_float4(rx, ry, a.skin * (3.0f * v[r].z),
+                                                __uint_as_float(jj[r]));
+                        }
+                    }
+                }
+                __syncwarp();
+                {
+                    // one loop per (exact, wrap, coarse) case, branch-free in
+                    // the common ones: a predicated store and a counter.  A
+                    // team of T lanes takes T consecutive candidates per
+                    // iteration; the ballot keeps the team's entries in
+                    // candidate order.
+                    auto test = [&](auto ex_c, auto wr_c, auto co_c) {
+                        constexpr bool EX = decltype(ex_c)::value;
+                        constexpr bool WR = decltype(wr_c)::value;
+                        constexpr bool CO = decltype(co_c)::value;
+                        auto pair_in = [&](uint32_t u, uint32_t &j) {
+                            const float4 c = sc[u];
+                            float dx = rxi - c.x, dy = ryi - c.y;
+                            if (WR) {
+                                if (wrapx) dx -= Lx * rintf(dx * iLx);
+                                if (wrapy) dy -= Ly * rintf(dy * iLy);
+                            }
+                            const float r2 = fmaf(dx, dx, dy * dy);
+                            const float R = fmaxf(Ri, c.z);
+                            const float R2 = R * R;
+                            j = __float_as_uint(c.w);
+                            bool in = r2 < R2;
+                            if (EX) {
+                                const float band = fmaf(R, KB, R2) * (1.0f / 65536.0f);
+                                in = r2 < R2 - band;
+                                if (!in && !(r2 > R2 + band))
+                                    in = pred_fp64(a.d, __ldg(&a.x[i]), __ldg(&a.y[i]),
+                                                   __ldg(&a.h[i]), __ldg(&a.x[j]),
+                                                   __ldg(&a.y[j]), __ldg(&a.h[j]));
+                            }
+                            return in;
+                        };
+                        auto put = [&](uint32_t pos, uint32_t j) {
+                            if (DIRECT) {
+                                if (pos < a.cap) a.list[pos] = j;
+                                if (CO) {
+                                    const uint32_t rp = a.off[j] + a.own[j] +
+                                                        atomicAdd(&a.rev[j], 1u);
+                                    if (rp < a.cap) a.list[rp] = i;
+                                }
+                            } else {
+                                if (pos < W) row[pos] = j;
+                                if (CO) atomicAdd(&a.rev[j], 1u);
+                            }
+                        };
+                        if constexpr (T == 1) {
+                            if (!act) return;
+#pragma unroll 4
+                            for (uint32_t u = 0; u < m; ++u) {
+                                uint32_t j;
+                                const bool in = pair_in(u, j);
+                                if (DIRECT) {
+                                    if (in) put(k, j);
+                                } else {
+                                    if (in && k < W) row[k] = j;
+                                    if (CO && in) atomicAdd(&a.rev[j], 1u);
+                                }
+                                k += in ? 1u : 0u;
+                            }
+                        } else {
+                            const unsigned gsh = (unsigned)(lane & ~(T - 1));
+                            const unsigned below = (1u << sub) - 1u;
+                            for (uint32_t u0 = 0; u0 < m; u0 += T) {
+                                const uint32_t u = u0 + (uint32_t)sub;
+                                uint32_t j = 0;
+                                const bool in = act && u < m && pair_in(u, j);
+                                const unsigned gb = (__ballot_sync(0xffffffffu, in) >> gsh) &
+                                                    ((1u << T) - 1u);
+                                if (in) put(k + (uint32_t)__popc(gb & below), j);
+                                k += (uint32_t)__popc(gb);
+                            }
+                        }
+                    };
+                    using TT = std::true_type;
+                    using FF = std::false_type;
+                    if (exact) {
+                        if (wrap) {
+                            if (coarse) test(TT(), TT(), TT()); else test(TT(), TT(), FF());
+                        } else {
+                            if (coarse) test(TT(), FF(), TT()); else test(TT(), FF(), FF());
+                        }
+                    } else {
+                        if (wrap) {
+                            if (coarse) test(FF(), TT(), TT()); else test(FF(), TT(), FF());
+                        } else {
+                            if (coarse) test(FF(), FF(), TT()); else test(FF(), FF(), FF());
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (!DIRECT) {
+        uint32_t km = act ? k : 0u;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
+        if (act && sub == 0) {
+            a.own[i] = k;
+            if (k > W) a.queue[atomicAdd(a.nqueue, 1u)] = i;
+        }
+        if (lane == 0 && km > 0) atomicMax(a.max_own, km);
+    }
+}
+
+// Stage-mode walk.  T = 1: warp w owns the cells whose first particle lies
+// in [32 w, 32 w + 32) and takes them one after another, 32 particles at a
+// time.  T > 1 (small sets, where that leaves most of the GPU idle): warp w
+// takes the 32 / T particles [w P, w P + P), P = 32 / T, one piece per cell
+// they fall in.
+template <int T>
+__global__ void __launch_bounds__(128) k_list_tile(ListArgs a) {
+    __shared__ float4 sbuf[4][TILE_CAP];
+    __shared__ int spcs[4][20];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t gw = blockIdx.x * 4u + (uint32_t)w;
+    const uint32_t n = (uint32_t)a.n;
+    if constexpr (T == 1) {
+        const uint32_t base = gw * 32u;
+        if (base >= n) return;
+        const uint32_t i = base + lane;
+        const bool head = i < n && (i == 0 || a.skey[i] != a.skey[i - 1]);
+        unsigned heads = __ballot_sync(0xffffffffu, head);
+        while (heads) {
+            const uint32_t hd = base + (uint32_t)(__ffs(heads) - 1);
+            heads &= heads - 1;
+            const uint64_t K = a.skey[hd];
+            uint32_t cs = hd, ce = hd + 1;
+            table_lookup(a.g, K, cs, ce);
+            const int lc = a.lev[hd];
+            for (uint32_t p0 = cs; p0 < ce; p0 += 32)
+                tile_chunk<false, 1>(a, sbuf[w], spcs[w], lc, cs, min(ce, p0 + 32), p0, -1);
+        }
+    } else {
+        constexpr uint32_t P = 32 / T;
+        const uint32_t w0 = gw * P;
+        if (w0 >= n) return;
+        const uint32_t w1 = min(n, w0 + P);
+        uint32_t t = w0;
+        while (t < w1) {
+            const uint64_t K = a.skey[t];
+            uint32_t cs = t, ce = t + 1;
+            table_lookup(a.g, K, cs, ce);
+            const uint32_t pe = min(ce, w1);
+            tile_chunk<false, T>(a, sbuf[w], spcs[w], a.lev[t], cs, pe, t, -1);
+            t = pe;
+        }
+    }
+}
+
+// Direct-mode pass for the particles whose own entries overflowed their
+// staging row; a warp per queued particle.
+__global__ void __launch_bounds__(128) k_list_tile_queue(ListArgs a) {
+    __shared__ float4 sbuf[4][TILE_CAP];
+    __shared__ int spcs[4][20];
+    const int w = threadIdx.x >> 5;
+    const uint32_t nq = *a.nqueue;
+    const uint32_t gw = blockIdx.x * 4u + (uint32_t)w, nw = gridDim.x * 4u;
+    for (uint32_t q = gw; q < nq; q += nw) {
+        const uint32_t i = a.queue[q];
+        const uint64_t K = a.skey[i];
+        uint32_t cs = i, ce = i + 1;
+        table_lookup(a.g, K, cs, ce);
+        tile_chunk<true, 16>(a, sbuf[w], spcs[w], a.lev[i], cs, i + 1, i, (int)i);
+    }
+}
+
 // Sort of each reverse segment (ascending index).  Segments of at most 32
 // entries (the common case: only particles next to a finer level have
 // any) are sorted in registers by the particle's thread; longer ones are
@@ -293,13 +671,29 @@ void launch_anchor_pack(cudaStream_t s, int n, const double *x,
                                                     A[0], A[1], an, pk);
 }
 
+// Walk choice by set size (measured on GB300 over uniform and graded
+// lattices of 5k to 1M particles): below ~12k particles the per-particle
+// team walk keeps more warps in flight than the cell tiles; from there the
+// tiles win, with teams of 4 lanes up to ~60k particles and one lane per
+// particle beyond (1.6x faster than the per-particle walk on the 1:250
+// graded million, 2.5x at 300k).
+static bool use_tile(int n) { return n >= 12000; }
+static int tile_team(int n) { return n >= 60000 ? 1 : 4; }
+
 void launch_list_walk(cudaStream_t s, const ListArgs &a, int *launches) {
     const int n = a.n;
     if (n <= 0) return;
-    with_team(n, [&](auto t) {
-        constexpr int T = decltype(t)::value;
-        k_list_gather<T><<<nblk(n * T, 128), 128, 0, s>>>(a);
-    });
+    if (use_tile(n)) {
+        if (tile_team(n) == 1)
+            k_list_tile<1><<<nblk(n, 128), 128, 0, s>>>(a);
+        else
+            k_list_tile<4><<<nblk(n, 32), 128, 0, s>>>(a);
+    } else {
+        with_team(n, [&](auto t) {
+            constexpr int T = decltype(t)::value;
+            k_list_gather<T><<<nblk(n * T, 128), 128, 0, s>>>(a);
+        });
+    }
     *launches += 1;
 }
 
@@ -330,7 +724,12 @@ void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,
         constexpr int T = decltype(t)::value;
         k_list_place<T><<<nblk(n * T, 128), 128, 0, s>>>(a);
     }, 16);
-    if (queue) k_list_fill_queue<16><<<152 * 4, 128, 0, s>>>(a);
+    if (queue) {
+        if (use_tile(n))
+            k_list_tile_queue<<<152 * 4, 128, 0, s>>>(a);
+        else
+            k_list_fill_queue<16><<<152 * 4, 128, 0, s>>>(a);
+    }
     k_list_sort_rev<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.own, a.list, a.cap,
                                                   a.longq, a.nlong);
     // up to one warp per particle (4 per block): the long segments are

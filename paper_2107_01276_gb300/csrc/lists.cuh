@@ -32,6 +32,7 @@ struct ListArgs {
     const double *x, *y, *h;
     const float4 *pk;
     const uint8_t *lev;
+    const uint64_t *skey;       // sorted cell keys (cells are runs of equal keys)
     uint32_t *own;              // entries found by i itself
     uint32_t *rev;              // reverse-entry counters / cursors
     uint32_t *off;              // n + 1 offsets

@@ -281,6 +281,7 @@ static ListArgs list_args(sph_ctx *c) {
     la.h = c->f[F_H];
     la.pk = c->pk;
     la.lev = c->lvl;
+    la.skey = c->skey;
     la.own = c->own;
     la.rev = c->rev;
     la.off = c->off;

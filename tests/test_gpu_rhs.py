@@ -79,6 +79,45 @@ def test_neighbour_sets_bit_exact(case):
         assert np.array_equal(sets[i], nbr[off[i]:off[i + 1]]), i
 
 
+# Sets large enough for the cell-tiled list build (teams of 4 lanes from
+# 12k particles, one lane per particle from 60k); h/dx = 1.7 gives ~80
+# neighbours, more than a first build's 64-entry staging rows hold, so those
+# cases take the overflow pass.
+TILED = {
+    "tiled4_periodic": lambda: wl.perturbed(nx=150, ny=120, h_ratio=3.0, seed=8),
+    "tiled4_open_wide": lambda: wl.perturbed(nx=140, ny=110, h_ratio=4.0, hdx=1.7,
+                                             periodic=(0, 0), seed=9),
+    "tiled1_mixed_bc": lambda: wl.perturbed(nx=300, ny=240, h_ratio=6.0,
+                                            periodic=(1, 0), seed=10),
+    "tiled1_wide": lambda: wl.perturbed(nx=280, ny=260, h_ratio=2.0, hdx=1.7,
+                                        seed=11),
+    "tiled1_graded_1_64": lambda: wl.graded_strip(n_target=100000, ratio=64.0),
+}
+
+
+@pytest.mark.parametrize("precision", [sph.SPH_FP64, sph.SPH_MIXED])
+@pytest.mark.parametrize("case", sorted(TILED))
+def test_neighbour_sets_bit_exact_tiled(case, precision):
+    d = TILED[case]()
+    sim = _sim(d, precision)
+    sim.rhs()
+    ids = sim.read("id")
+    off = sim.read("neigh_off")
+    nid = sim.read("neigh_id")
+    sim.close()
+    pt = d["particles"]
+    P = oracle.params(**d["params"])
+    ro, rn = oracle.neighbors(P, pt["x"], pt["y"], pt["h"])
+    n = len(pt["x"])
+    assert len(ids) == n and off[-1] == ro[-1]
+    # both sides as (i, j) pairs sorted by (id i, id j)
+    cnt = np.diff(off)
+    gi = np.repeat(ids, cnt)
+    pairs_gpu = np.sort(gi.astype(np.int64) * n + nid)
+    pairs_orc = np.sort(np.repeat(np.arange(n), np.diff(ro)).astype(np.int64) * n + rn)
+    assert np.array_equal(pairs_gpu, pairs_orc)
+
+
 @pytest.mark.parametrize("precision,tol", [(sph.SPH_FP64, FP64_TOL),
                                            (sph.SPH_MIXED, MIXED_TOL)])
 @pytest.mark.parametrize("case", sorted(CASES))
