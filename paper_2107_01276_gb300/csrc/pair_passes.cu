@@ -14,6 +14,11 @@
 
 namespace sph {
 
+// List entries whose neighbour records a mixed-path pass loads ahead.
+constexpr int UNROLL_A = 2;
+constexpr int UNROLL_B = 2;
+constexpr int PASS_B_BLOCKS = 6;   // resident blocks of mixed pass B
+
 // Membership test of a list entry when the lists carry a skin: the exact
 // predicate of N(i) on the separation the pass already has (FP32 band test
 // with the FP64 predicate inside the band on the mixed path; the FP64
@@ -73,14 +78,49 @@ __global__ void __launch_bounds__(128)
     };
     const uint32_t b = a.off[i], e = a.off[i + 1];
     const double xid = a.x[i], yid = a.y[i], hid = a.h[i];
-    for (uint32_t k = b + tm.lane; k < e; k += T) {
-        const int j = (int)__ldg(&a.list[k]);
-        R dx, dy, r2, hj;
-        sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
-        if (a.filter && !skin_member<R>(a.d, a.an, r2, hi, hj, xid, yid, hid,
-                                        a.x, a.y, a.h, j))
-            continue;
-        pair(a.m[j], hj, a.p[j], j == i, dx, dy, r2);
+    if constexpr (sizeof(R) == 4) {
+        // U list entries per step, their records loaded before any is used
+        // (more loads in flight per warp)
+        auto body = [&](int j, const float4 &pj, R mj, R pjv) {
+            R dx, dy;
+            anchor_sep(a.an, sp.pi, pj, dx, dy);
+            const R r2 = fmaf(dx, dx, dy * dy);
+            if (a.filter && !skin_member<R>(a.d, a.an, r2, hi, pj.z, xid, yid,
+                                            hid, a.x, a.y, a.h, j))
+                return;
+            pair(mj, pj.z, pjv, j == i, dx, dy, r2);
+        };
+        constexpr int U = UNROLL_A;
+        uint32_t k = b + tm.lane;
+        for (; k + (U - 1) * T < e; k += U * T) {
+            int jj[U];
+            float4 pp[U];
+            R mm[U], qq[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) jj[u] = (int)__ldg(&a.list[k + u * T]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                pp[u] = __ldg(&a.pk[jj[u]]);
+                mm[u] = a.m[jj[u]];
+                qq[u] = a.p[jj[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) body(jj[u], pp[u], mm[u], qq[u]);
+        }
+        for (; k < e; k += T) {
+            const int j = (int)__ldg(&a.list[k]);
+            body(j, __ldg(&a.pk[j]), a.m[j], a.p[j]);
+        }
+    } else {
+        for (uint32_t k = b + tm.lane; k < e; k += T) {
+            const int j = (int)__ldg(&a.list[k]);
+            R dx, dy, r2, hj;
+            sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
+            if (a.filter && !skin_member<R>(a.d, a.an, r2, hi, hj, xid, yid, hid,
+                                            a.x, a.y, a.h, j))
+                continue;
+            pair(a.m[j], hj, a.p[j], j == i, dx, dy, r2);
+        }
     }
     if (a.w.n > 0) {
         for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane, tm.mask,
@@ -144,9 +184,9 @@ __global__ void __launch_bounds__(128)
 // 1/h_j); eta = 0.001 h_i^2, P_j = (p_j - p_avg,i) / (rho_j^2 beta_j).
 // Wall neighbours (section 2.2): prescribed wall velocity in the divergence
 // sum, extrapolated velocity in the viscous sum, rho_w = rho0, beta_w = 1.
-// (float: at most 72 registers, seven 128-thread blocks per SM)
+// (float: at most 80 registers, six 128-thread blocks per SM)
 template <typename R, int T>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 1)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_B_BLOCKS : 1)
     k_pass_b(PassBArgs<R> a) {
     const Team<T> tm;
     const int i = Team<T>::particle();
@@ -208,23 +248,61 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 1)
     const bool literal = a.pavg_mode != 0;
     const double xid = a.x[i], yid = a.y[i], hid = a.h[i];
     const R hpk = (R)a.pk[i].z;   // h_i as the list builder saw it
-    for (uint32_t k = b + tm.lane; k < e; k += T) {
-        const int j = (int)__ldg(&a.list[k]);
-        if (j == i) continue;
-        R dx, dy, r2;
-        if (a.filter) {
-            R hj;
-            sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
-            if (!skin_member<R>(a.d, a.an, r2, hpk, hj, xid, yid, hid, a.x,
-                                a.y, a.h, j))
-                continue;
-        } else {
-            sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+    if constexpr (sizeof(R) == 4) {
+        // U list entries per step, their records loaded before any is used
+        // (more loads in flight per warp)
+        auto body = [&](int j, const float4 &pj, const float4 &A,
+                        const float4 &B) {
+            if (j == i) return;
+            R dx, dy;
+            anchor_sep(a.an, sp.pi, pj, dx, dy);
+            const R r2 = fmaf(dx, dx, dy * dy);
+            if (a.filter && !skin_member<R>(a.d, a.an, r2, hpk, pj.z, xid, yid,
+                                            hid, a.x, a.y, a.h, j))
+                return;
+            const R pref = literal ? a.pavg[j] : pavg_i;
+            pair(dx, dy, r2, B.w, A.x, A.y, A.z, (B.x - pref) * A.w, B.x, B.y,
+                 B.z, B.y, B.z);
+        };
+        constexpr int U = UNROLL_B;
+        uint32_t k = b + tm.lane;
+        for (; k + (U - 1) * T < e; k += U * T) {
+            int jj[U];
+            float4 pp[U], AA[U], BB[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) jj[u] = (int)__ldg(&a.list[k + u * T]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                pp[u] = __ldg(&a.pk[jj[u]]);
+                AA[u] = a.nbA[jj[u]];
+                BB[u] = a.nbB[jj[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) body(jj[u], pp[u], AA[u], BB[u]);
         }
-        const typename V4<R>::T A = a.nbA[j], B = a.nbB[j];
-        const R pref = literal ? a.pavg[j] : pavg_i;
-        pair(dx, dy, r2, B.w, A.x, A.y, A.z, (B.x - pref) * A.w, B.x, B.y,
-             B.z, B.y, B.z);
+        for (; k < e; k += T) {
+            const int j = (int)__ldg(&a.list[k]);
+            body(j, __ldg(&a.pk[j]), a.nbA[j], a.nbB[j]);
+        }
+    } else {
+        for (uint32_t k = b + tm.lane; k < e; k += T) {
+            const int j = (int)__ldg(&a.list[k]);
+            if (j == i) continue;
+            R dx, dy, r2;
+            if (a.filter) {
+                R hj;
+                sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
+                if (!skin_member<R>(a.d, a.an, r2, hpk, hj, xid, yid, hid, a.x,
+                                    a.y, a.h, j))
+                    continue;
+            } else {
+                sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
+            }
+            const typename V4<R>::T A = a.nbA[j], B = a.nbB[j];
+            const R pref = literal ? a.pavg[j] : pavg_i;
+            pair(dx, dy, r2, B.w, A.x, A.y, A.z, (B.x - pref) * A.w, B.x, B.y,
+                 B.z, B.y, B.z);
+        }
     }
     if (a.w.n > 0) {
         const R rho0 = (R)a.rho0;

@@ -1590,7 +1590,10 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         c->launches += 2;
         uint32_t keep = read_u32(c, c->d_total, &st);
         if (st != SPH_OK) return st;
-        if ((int)keep < c->n) {
+        // a round that merges nothing leaves the state as it found it, so
+        // every later round would find the same pairs and merge nothing too
+        if ((int)keep == c->n) break;
+        {
             CompactArgs ca;
             for (int k = 0; k < NSTATE; ++k) {
                 ca.src[k] = c->f[k];
