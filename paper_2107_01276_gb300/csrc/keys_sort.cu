@@ -36,11 +36,48 @@ __device__ __forceinline__ int cell_coord(double x, double lo, double w,
     return c;
 }
 
+// Fast forms of the two quotients above: the product with a rounded
+// reciprocal is within 2^-51 relative of the correctly rounded quotient, so
+// where it lies farther than 1e-12 (relative) from every integer (cell
+// index) or power of two (level), it gives the same floor or exponent; the
+// rare cases closer than that take the correctly rounded division.  GB300's
+// FP64 division costs tens of FP64 operations at a small fraction of the
+// FP32 rate; a product costs one.
+__device__ __forceinline__ int level_of_fast(double h, double c0,
+                                             double inv_c0, int lmax) {
+    const double y = __dmul_rn(__dmul_rn(3.0, h), inv_c0);
+    if (y < 1.0 - 1e-12) return 0;
+    if (y > 1.0 + 1e-12) {
+        int e;
+        const double f = frexp(y, &e);
+        if (f > 0.5 + 1e-12 && f < 1.0 - 1e-12) return e > lmax ? lmax : e;
+    }
+    return level_of(h, c0, lmax);
+}
+
+__device__ __forceinline__ int cell_coord_fast(double x, double lo, double w,
+                                               double invw, int ncell) {
+    const double t = __dsub_rn(x, lo);
+    const double y = __dmul_rn(t, invw);
+    const double fy = floor(y);
+    const double tol = 1e-12 * fmax(1.0, fabs(y));
+    if (!(y - fy > tol && fy + 1.0 - y > tol)) return cell_coord(x, lo, w, ncell);
+    int c;
+    if (fy < 0.0)
+        c = 0;
+    else if (fy > (double)(ncell - 1))
+        c = ncell - 1;
+    else
+        c = (int)fy;
+    return c;
+}
+
 struct KeysArgs {
     Domain dom;
-    double c0;
+    double c0, inv_c0;
     int lmax, mbits;
     Level lev[MAX_LEVELS];
+    double invw[MAX_LEVELS][2];   // 1 / w per level and axis (FP64)
 };
 
 __global__ void k_keys(int n, KeysArgs a, const double *__restrict__ x,
@@ -57,10 +94,10 @@ __global__ void k_keys(int n, KeysArgs a, const double *__restrict__ x,
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        int l = level_of(h[i], a.c0, a.lmax);
+        int l = level_of_fast(h[i], a.c0, a.inv_c0, a.lmax);
         const Level &L = a.lev[l];
-        int ix = cell_coord(x[i], a.dom.lo[0], L.w[0], L.n[0]);
-        int iy = cell_coord(y[i], a.dom.lo[1], L.w[1], L.n[1]);
+        int ix = cell_coord_fast(x[i], a.dom.lo[0], L.w[0], a.invw[l][0], L.n[0]);
+        int iy = cell_coord_fast(y[i], a.dom.lo[1], L.w[1], a.invw[l][1], L.n[1]);
         uint64_t m = spread2((uint64_t)ix) | (spread2((uint64_t)iy) << 1);
         skey[i] = ((uint64_t)l << (2 * a.mbits)) | m;
         perm[i] = (uint32_t)i;
@@ -122,7 +159,12 @@ void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
     a.c0 = c0;
     a.lmax = lmax;
     a.mbits = mbits;
-    for (int l = 0; l < MAX_LEVELS; ++l) a.lev[l] = lev[l];
+    a.inv_c0 = 1.0 / c0;
+    for (int l = 0; l < MAX_LEVELS; ++l) {
+        a.lev[l] = lev[l];
+        a.invw[l][0] = 1.0 / lev[l].w[0];
+        a.invw[l][1] = 1.0 / lev[l].w[1];
+    }
     if (n <= 0) return;
     int bs = 256;
     k_keys<<<(n + bs - 1) / bs, bs, 0, s>>>(n, a, x, y, h, skey, perm,

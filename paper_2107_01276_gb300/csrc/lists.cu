@@ -25,8 +25,11 @@ __global__ void k_pack(PackArgs a) {
     float xl[2];
     const double q[2] = {x, y};
     for (int ax = 0; ax < 2; ++ax) {
+        // anchor index: any cell whose offset stays within about A will do
+        // (the separation error bound assumes |xl| <= A), so a product with
+        // the reciprocal replaces the FP64 division
         double t = __dsub_rn(q[ax], a.lo[ax]);
-        double c = floor(__ddiv_rn(t, a.Ad[ax]));
+        double c = floor(t * a.invAd[ax]);
         int gi = c < 0.0 ? 0 : (c > (double)(a.an.n[ax] - 1) ? a.an.n[ax] - 1 : (int)c);
         g[ax] = gi;
         xl[ax] = (float)__dsub_rn(t, __dmul_rn((double)gi, a.Ad[ax]));
@@ -48,11 +51,12 @@ __global__ void k_anchor_pack(int n, const double *x, const double *y,
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double q[2] = {x[i], y[i]}, lo[2] = {lo0, lo1}, A[2] = {A0, A1};
+    const double iA[2] = {1.0 / A0, 1.0 / A1};
     int g[2];
     float xl[2];
     for (int ax = 0; ax < 2; ++ax) {
         double t = __dsub_rn(q[ax], lo[ax]);
-        double c = floor(__ddiv_rn(t, A[ax]));
+        double c = floor(t * iA[ax]);
         int gi = c < 0.0 ? 0 : (c > (double)(an.n[ax] - 1) ? an.n[ax] - 1 : (int)c);
         g[ax] = gi;
         xl[ax] = (float)__dsub_rn(t, __dmul_rn((double)gi, A[ax]));
@@ -62,6 +66,11 @@ __global__ void k_anchor_pack(int n, const double *x, const double *y,
 }
 
 // ------------------------------------------------------------ list build --
+// A staged entry carries this bit when its particle lies on a coarser level
+// than the row's owner (the pair also needs a reverse entry).  Particle
+// indices stay below 2^31: a context holds far fewer particles.
+constexpr uint32_t STAGE_COARSE = 0x80000000u;
+
 // Membership of candidate j for particle i: FP32 anchor filter with the
 // FP64 predicate in its band (exact, for both precisions).
 __device__ __forceinline__ bool member(const ListArgs &a, const float4 &pi,
@@ -109,8 +118,9 @@ __global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
                                         : __ballot_sync(tm.mask, in);
             if (in) {
                 const uint32_t pos = k + (T == 1 ? 0u : __popc(bal & below));
-                if (pos < W) row[pos] = j;
-                if (__ldg(&a.lev[j]) > li) atomicAdd(&a.rev[j], 1u);
+                const bool co = __ldg(&a.lev[j]) > li;
+                if (pos < W) row[pos] = co ? (j | STAGE_COARSE) : j;
+                if (co) atomicAdd(&a.rev[j], 1u);
             }
             k += __popc(bal);
         }
@@ -131,14 +141,15 @@ __global__ void __launch_bounds__(128) k_list_place(ListArgs a) {
     if (i >= a.n) return;
     const uint32_t own = a.own[i];
     if (own <= a.stage_w) {               // else handled by k_list_fill_queue
-        const int li = a.lev[i];
         const uint32_t base = a.off[i];
         const uint32_t *row = a.stage + (size_t)i * a.stage_w;
         const uint32_t cap = a.cap;
+#pragma unroll 4
         for (uint32_t k = tm.lane; k < own; k += T) {
-            const uint32_t j = row[k];
+            const uint32_t ent = row[k];
+            const uint32_t j = ent & ~STAGE_COARSE;
             if (base + k < cap) a.list[base + k] = j;
-            if (__ldg(&a.lev[j]) > li) {
+            if (ent & STAGE_COARSE) {
                 const uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
                 if (rp < cap) a.list[rp] = (uint32_t)i;
             }
@@ -442,7 +453,7 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
                                     if (rp < a.cap) a.list[rp] = i;
                                 }
                             } else {
-                                if (pos < W) row[pos] = j;
+                                if (pos < W) row[pos] = CO ? (j | STAGE_COARSE) : j;
                                 if (CO) atomicAdd(&a.rev[j], 1u);
                             }
                         };
@@ -455,7 +466,7 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
                                 if (DIRECT) {
                                     if (in) put(k, j);
                                 } else {
-                                    if (in && k < W) row[k] = j;
+                                    if (in && k < W) row[k] = CO ? (j | STAGE_COARSE) : j;
                                     if (CO && in) atomicAdd(&a.rev[j], 1u);
                                 }
                                 k += in ? 1u : 0u;

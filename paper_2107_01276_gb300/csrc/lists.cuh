@@ -13,6 +13,7 @@ struct PackArgs {
     const uint64_t *skey;
     const double *x, *y, *h, *m, *p, *u, *v;
     double lo[2], Ad[2];        // anchor origin and side (FP64)
+    double invAd[2];            // 1 / Ad
     Anchor an;
     uint8_t *lev;
     float4 *pk;                 // {xl, yl, h, gx | gy << 16}

@@ -318,6 +318,7 @@ static void pack(sph_ctx *c, bool table_end) {
     for (int ax = 0; ax < 2; ++ax) {
         pa.lo[ax] = c->dom.lo[ax];
         pa.Ad[ax] = c->anchor_A[ax];
+        pa.invAd[ax] = 1.0 / c->anchor_A[ax];
     }
     pa.an = c->an;
     pa.lev = c->lvl;
