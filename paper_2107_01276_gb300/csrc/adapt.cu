@@ -193,12 +193,14 @@ __global__ void __launch_bounds__(128) k_merge_closest(MergeArgs a) {
     double br2 = 0.0;
     long long bid = 0;
     const double mi = m[i], mxi = mmax[i];
-    if (mxi > 0.0 && !(mi > mxi)) {
+    const bool alive_i = !a.alive_in || a.alive_in[i];
+    if (alive_i && mxi > 0.0 && !(mi > mxi)) {
         const double xi = x[i], yi = y[i], hi = h[i];
         const float4 pi = a.pk[i];
         for (uint32_t k = a.off[i] + tm.lane; k < a.off[i + 1]; k += T) {
             const int j = (int)a.list[k];
             if (j == i) continue;
+            if (a.alive_in && !a.alive_in[j]) continue;
             const double mxj = mmax[j], mj = m[j];
             if (!(mxj > 0.0) || mj > mxj) continue;
             {   // FP32 pre-test on the anchor separation: its error is
@@ -245,6 +247,12 @@ __global__ void __launch_bounds__(128) k_merge_closest(MergeArgs a) {
 __global__ void k_merge_apply(MergeArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    if (a.alive_in && !a.alive_in[i]) {
+        a.alive[i] = 0;
+        return;
+    }
+    const float h0 = a.alive_in ? a.h0[i] : (float)a.f[S_H][i];
+    float ds = a.alive_in ? a.dsum[i] : 0.0f;
     const int j = a.closest[i];
     uint32_t alive = 1;
     if (j >= 0 && a.closest[j] == i) {
@@ -279,8 +287,16 @@ __global__ void k_merge_apply(MergeArgs a) {
             f[S_Y][i] = wrap_rn(a.d, 1, ym);
             f[S_M][i] = mm;
             f[S_H][i] = hm;
+            // reach of the lists for the next round (rounded up)
+            ds = __fadd_ru(ds, __double2float_ru(ra));
+            if (__fadd_ru(0.5f * __double2float_ru(hm), ds) > a.budget * h0)
+                atomicOr(a.stale, 1);
+            a.pkw[i] = anchor_record(f[S_X][i], f[S_Y][i], hm, a.lo, a.Ad,
+                                     a.invAd, a.an);
         }
     }
+    a.h0[i] = h0;
+    a.dsum[i] = ds;
     a.alive[i] = alive;
 }
 

@@ -49,6 +49,20 @@ struct MergeArgs {
     const float4 *pk;           // anchor data at the current positions
     int *closest;
     uint32_t *alive;
+    // Rounds over one list build (merged-away particles stay in place,
+    // marked dead, until the rounds end): alive_in NULL in the first round
+    // after a build (all alive), else the alive flags of the last round.
+    // A merged particle that moved D since the build and now has smoothing
+    // length h keeps every later merge partner inside the lists while
+    // h / 2 + D <= budget h0 (h0: its h at the build; budget 1.5 times the
+    // lists' skin, less a margin); otherwise *stale is set and the next
+    // round rebuilds.
+    const uint32_t *alive_in;
+    float *h0, *dsum;
+    float budget;
+    int *stale;
+    float4 *pkw;                // anchor records, refreshed for merged particles
+    double lo[2], Ad[2], invAd[2];
 };
 
 struct CompactArgs {

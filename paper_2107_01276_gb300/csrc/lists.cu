@@ -20,22 +20,7 @@ __global__ void k_pack(PackArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     a.lev[i] = (uint8_t)(a.skey[i] >> a.lshift);
-    const double x = a.x[i], y = a.y[i];
-    int g[2];
-    float xl[2];
-    const double q[2] = {x, y};
-    for (int ax = 0; ax < 2; ++ax) {
-        // anchor index: any cell whose offset stays within about A will do
-        // (the separation error bound assumes |xl| <= A), so a product with
-        // the reciprocal replaces the FP64 division
-        double t = __dsub_rn(q[ax], a.lo[ax]);
-        double c = floor(t * a.invAd[ax]);
-        int gi = c < 0.0 ? 0 : (c > (double)(a.an.n[ax] - 1) ? a.an.n[ax] - 1 : (int)c);
-        g[ax] = gi;
-        xl[ax] = (float)__dsub_rn(t, __dmul_rn((double)gi, a.Ad[ax]));
-    }
-    a.pk[i] = make_float4(xl[0], xl[1], (float)a.h[i],
-                          __uint_as_float((unsigned)g[0] | ((unsigned)g[1] << 16)));
+    a.pk[i] = anchor_record(a.x[i], a.y[i], a.h[i], a.lo, a.Ad, a.invAd, a.an);
     if (a.tend) table_mark_end(i, a.n, a.skey, a.tkey, a.tend, a.tmask, a.h, a.tmaxh);
     if (!a.mixed) return;
     a.mf[i] = (float)a.m[i];
@@ -50,19 +35,8 @@ __global__ void k_anchor_pack(int n, const double *x, const double *y,
                               double A0, double A1, Anchor an, float4 *pk) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double q[2] = {x[i], y[i]}, lo[2] = {lo0, lo1}, A[2] = {A0, A1};
-    const double iA[2] = {1.0 / A0, 1.0 / A1};
-    int g[2];
-    float xl[2];
-    for (int ax = 0; ax < 2; ++ax) {
-        double t = __dsub_rn(q[ax], lo[ax]);
-        double c = floor(t * iA[ax]);
-        int gi = c < 0.0 ? 0 : (c > (double)(an.n[ax] - 1) ? an.n[ax] - 1 : (int)c);
-        g[ax] = gi;
-        xl[ax] = (float)__dsub_rn(t, __dmul_rn((double)gi, A[ax]));
-    }
-    pk[i] = make_float4(xl[0], xl[1], (float)h[i],
-                        __uint_as_float((unsigned)g[0] | ((unsigned)g[1] << 16)));
+    const double lo[2] = {lo0, lo1}, A[2] = {A0, A1}, iA[2] = {1.0 / A0, 1.0 / A1};
+    pk[i] = anchor_record(x[i], y[i], h[i], lo, A, iA, an);
 }
 
 // ------------------------------------------------------------ list build --

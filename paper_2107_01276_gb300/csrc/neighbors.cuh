@@ -326,6 +326,31 @@ __device__ __forceinline__ void anchor_sep(const Anchor &an, const float4 &pi,
     dy = fmaf((float)ky, an.A[1], pi.y - pj.y);
 }
 
+// Anchor record {xl, yl, h, gx | gy << 16} of a position: anchor cell g =
+// floor((x - lo) / A) (by a product with 1/A, clamped to the lattice; any
+// neighbouring cell would do, the offset then stays within about A, which is
+// all the separation error bound assumes) and the offset xl = x - lo - g A
+// rounded to FP32.
+__device__ __forceinline__ float4 anchor_record(double x, double y, double h,
+                                                const double *lo,
+                                                const double *A,
+                                                const double *invA,
+                                                const Anchor &an) {
+    const double q[2] = {x, y};
+    int g[2];
+    float xl[2];
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        const double t = __dsub_rn(q[ax], lo[ax]);
+        const double c = floor(t * invA[ax]);
+        const int gi = c < 0.0 ? 0 : (c > (double)(an.n[ax] - 1) ? an.n[ax] - 1 : (int)c);
+        g[ax] = gi;
+        xl[ax] = (float)__dsub_rn(t, __dmul_rn((double)gi, A[ax]));
+    }
+    return make_float4(xl[0], xl[1], (float)h,
+                       __uint_as_float((unsigned)g[0] | ((unsigned)g[1] << 16)));
+}
+
 // Position relative to the domain's lower corner in FP32, from the anchor
 // data p = {xl, yl, h, gx | gy << 16}.
 __device__ __forceinline__ float2 anchor_rel(const Anchor &an, const float4 &p) {

@@ -131,6 +131,7 @@ struct sph_ctx {
     long long next_id = 0;
     uint32_t *tmp_a = nullptr, *tmp_b = nullptr;   // N + 1 each
     int *closest = nullptr;
+    float *mh0 = nullptr, *mds = nullptr;   // merge rounds: h at the build, displacement
     double *d_mass = nullptr, *d_mass_part = nullptr;  // [2], [256]
     uint32_t *d_aux = nullptr;                         // [4] adapt counters
     StaticSet bg;     // background particles (section 3.3); extra: ds, m
@@ -649,7 +650,7 @@ static void free_ctx(sph_ctx *c) {
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
                   c->d_overflow, c->d_skin_err, c->longq, c->d_nlong, c->stage, c->lqueue, c->d_max_own,
                   c->d_nlq, c->tmp_a, c->tmp_b,
-                  c->closest, c->d_mass, c->d_mass_part, c->wp, c->wugx,
+                  c->closest, c->mh0, c->mds, c->d_mass, c->d_mass_part, c->wp, c->wugx,
                   c->wugy, c->d_aux};
     for (void *p : ps) cudaFree(p);
     cudaFree(c->omega);
@@ -998,7 +999,8 @@ static sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
          dalloc(&c->stage, N * c->stage_w) && dalloc(&c->lqueue, N) &&
          dalloc(&c->d_nlq, 1) && dalloc(&c->d_max_own, 1);
     ok = ok && dalloc(&c->tmp_a, N + 1) && dalloc(&c->tmp_b, N + 1) &&
-         dalloc(&c->closest, N) && dalloc(&c->d_mass, 2) &&
+         dalloc(&c->closest, N) && dalloc(&c->mh0, N) && dalloc(&c->mds, N) &&
+         dalloc(&c->d_mass, 2) &&
          dalloc(&c->d_mass_part, 256) && dalloc(&c->d_aux, 4);
     c->list_cap = std::min<size_t>(N * 48, 0xffffffffull);
     ok = ok && dalloc(&c->list, c->list_cap);
@@ -1572,29 +1574,19 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         return st;
     }
     z.n_split = count;
-    // merge rounds (section 3.2)
-    for (int r = 0; r < c->prm.merge_iters; ++r) {
-        if ((st = rebuild(c, false)) != SPH_OK) return st;
-        MergeArgs a;
-        a.n = c->n;
-        a.d = c->dom;
-        for (int k = 0; k < NSTATE; ++k) a.f[k] = c->f[k];
-        a.id = c->id;
-        a.off = c->off;
-        a.list = c->list;
-        a.closest = c->closest;
-        a.alive = c->tmp_a;
-        a.an = c->an;
-        a.pk = c->pk;
-        launch_merge(c->s, a);
-        exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
-        c->launches += 2;
-        uint32_t keep = read_u32(c, c->d_total, &st);
-        if (st != SPH_OK) return st;
-        // a round that merges nothing leaves the state as it found it, so
-        // every later round would find the same pairs and merge nothing too
-        if ((int)keep == c->n) break;
-        {
+    // merge rounds (section 3.2).  One list build serves several rounds:
+    // merged-away particles stay in place, marked dead, and the kept ones
+    // are updated in place, so the lists of the build still cover every
+    // later partner while each merged particle's h / 2 plus its move since
+    // the build stays within 1.5 h at the build (partners lie within
+    // (h_i + h_j) / 2, the lists reach 3 max(h_i, h_j) at the build); a
+    // merge beyond that flags the lists stale and the next round rebuilds
+    // after compacting.  A round that merges nothing ends the rounds: it
+    // left the state as it found it.
+    {
+        bool lists_ok = false, first = false, dead = false;
+        int n_alive = c->n;
+        auto compact_dead = [&]() {
             CompactArgs ca;
             for (int k = 0; k < NSTATE; ++k) {
                 ca.src[k] = c->f[k];
@@ -1606,9 +1598,58 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
             c->launches += 1;
             for (int k = 0; k < NSTATE; ++k) std::swap(c->f[k], c->falt[k]);
             std::swap(c->id, c->id_alt);
-            z.n_merged += c->n - (int)keep;
-            c->n = (int)keep;
+            c->n = n_alive;
+            c->grid_valid = false;
+            dead = false;
+        };
+        int *stale = (int *)(c->d_aux + 1);
+        for (int r = 0; r < c->prm.merge_iters; ++r) {
+            if (!lists_ok) {
+                if (dead) compact_dead();
+                if ((st = rebuild(c, false)) != SPH_OK) return st;
+                cudaMemsetAsync(stale, 0, sizeof(int), c->s);
+                lists_ok = true;
+                first = true;
+            }
+            MergeArgs a;
+            a.n = c->n;
+            a.d = c->dom;
+            for (int k = 0; k < NSTATE; ++k) a.f[k] = c->f[k];
+            a.id = c->id;
+            a.off = c->off;
+            a.list = c->list;
+            a.closest = c->closest;
+            a.alive = c->tmp_a;
+            a.an = c->an;
+            a.pk = c->pk;
+            a.alive_in = first ? nullptr : c->tmp_a;
+            a.h0 = c->mh0;
+            a.dsum = c->mds;
+            a.budget = 1.5f * c->skin * (1.0f - 1e-3f);
+            a.stale = stale;
+            a.pkw = c->pk;
+            for (int ax = 0; ax < 2; ++ax) {
+                a.lo[ax] = c->dom.lo[ax];
+                a.Ad[ax] = c->anchor_A[ax];
+                a.invAd[ax] = 1.0 / c->anchor_A[ax];
+            }
+            first = false;
+            launch_merge(c->s, a);
+            exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
+            c->launches += 2;
+            uint32_t keep = 0;
+            int is_stale = 0;
+            cudaMemcpyAsync(&keep, c->d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
+            cudaMemcpyAsync(&is_stale, stale, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+            if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_adapt merge");
+            if ((int)keep == n_alive) break;
+            z.n_merged += n_alive - (int)keep;
+            n_alive = (int)keep;
+            dead = true;
+            c->grid_valid = false;
+            if (is_stale) lists_ok = false;
         }
+        if (dead) compact_dead();
     }
     // shift rounds with Taylor correction, then the h update (3.2, 3.4)
     // One list build serves every shift round and the h update: a round

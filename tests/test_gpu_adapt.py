@@ -56,6 +56,35 @@ def _run_both(d, bg, precision=sph.SPH_FP64, calls=1, cap=20000, **over):
     return sim, gst, ost, got, ref
 
 
+@pytest.mark.parametrize("precision", [sph.SPH_FP64, sph.SPH_MIXED])
+@pytest.mark.parametrize("rounds", [3, 5])
+def test_merge_cascade_bit_exact_without_shift(rounds, precision):
+    """A lattice four times finer than its background (m_ref = 16 m): every
+    round merges, and particles merged in one round merge again in the
+    next.  The library runs later rounds on the lists of an earlier build
+    while the merged particles stay within their reach and rebuilds when
+    they leave it; counts, ids, positions and masses must equal the
+    oracle's, which rebuilds before every round."""
+    d = wl.perturbed(nx=48, ny=48, h_ratio=1.0, jitter=0.1, hdx=1.2, seed=21)
+    dx = d["dx"]
+    bgn = 12
+    g = (np.arange(bgn) + 0.5) / bgn
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    bg = {"x": X.ravel(), "y": Y.ravel(), "h": np.full(X.size, 1.2 / bgn),
+          "ds": np.full(X.size, 4.0 * dx)}
+    sim, gst, ost, got, ref = _run_both(d, bg, precision=precision,
+                                        shift_iters=0, merge_iters=rounds)
+    assert ost[0]["n_merged"] > d["particles"]["x"].size // 2
+    for k in ("n_before", "n_split", "n_merged", "n_after"):
+        assert gst[0][k] == ost[0][k], (k, gst[0], ost[0])
+    assert np.array_equal(got["id"], ref["id"])
+    for k in ("x", "y", "m", "mmin", "mmax", "u", "v", "p"):
+        assert np.array_equal(got[k], ref[k]), k
+    tol = 1e-13 if precision == sph.SPH_FP64 else 2e-5
+    assert np.abs(got["h"] / ref["h"] - 1).max() < tol
+    sim.close()
+
+
 def test_split_merge_bit_exact_without_shift():
     """With no shift rounds every position, mass and bound comes from the
     same FP64 expressions on both sides: identical after split + merges."""
