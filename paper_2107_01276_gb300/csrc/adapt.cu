@@ -58,21 +58,22 @@ __global__ void __launch_bounds__(128) k_bg_mref(BgArgs a) {
     const float2 q = anchor_rel(a.an, pi);
     double best = 1e308;
     // Levels come finest first, so the running minimum soon exceeds no
-    // coarse cell's least m_ref: a lane skips its share of a cell whose
-    // least rho0 ds^2 is not below its own running minimum (those
-    // candidates cannot lower the minimum; rounding is monotone in ds).
-    for_each_cell_team<T>(a.g, a.d, 0, q.x, q.y, pi.z, tm.lane, tm.mask,
-                          [&](uint32_t s, uint32_t e) {
+    // coarse cell's least m_ref: a cell whose least rho0 ds^2 is not below
+    // the running minimum of the lane that looked it up is dropped (its
+    // candidates cannot lower the team's minimum, which is at most that
+    // lane's; rounding is monotone in ds).  best: the lane's own minimum
+    // over the candidates it takes; the team's is taken at the end.
+    for_each_candidate_team<T>(a.g, a.d, 0, q.x, q.y, pi.z, 1.0f, tm.lane,
+                               tm.mask, [&](uint32_t s, uint32_t) {
         const double dmin = __ldg(&a.bcmin[s]);
-        if (__dmul_rn(__dmul_rn(a.rho0, dmin), dmin) >= best) return;
-        for (uint32_t b = s + tm.lane; b < e; b += T) {
-            float fx, fy, fr2;
-            if (pred_mixed(a.d, a.an, pi, __ldg(&a.bpk[b]), xi, yi, hi, a.bx,
-                           a.by, a.bh, (int)b, fx, fy, fr2)) {
-                const double ds = __ldg(&a.bds[b]);
-                const double mref = __dmul_rn(__dmul_rn(a.rho0, ds), ds);
-                best = mref < best ? mref : best;
-            }
+        return __dmul_rn(__dmul_rn(a.rho0, dmin), dmin) < best;
+    }, [&](uint32_t b) {
+        float fx, fy, fr2;
+        if (pred_mixed(a.d, a.an, pi, __ldg(&a.bpk[b]), xi, yi, hi, a.bx,
+                       a.by, a.bh, (int)b, fx, fy, fr2)) {
+            const double ds = __ldg(&a.bds[b]);
+            const double mref = __dmul_rn(__dmul_rn(a.rho0, ds), ds);
+            best = mref < best ? mref : best;
         }
     });
     best = team_min<T>(tm.mask, best);

@@ -269,6 +269,95 @@ __device__ __forceinline__ void for_each_cell_team_scaled(
     }
 }
 
+// Candidate form of the team walk with one latency round per batch: for
+// each level the lanes look up up to T cells at once, cell_ok(s, e) (called
+// by the lane that found the cell) may drop a cell, and then the team's
+// lanes take the candidates of all kept cells together, lane t the
+// candidates t, t + T, ... of the concatenated ranges, located by a binary
+// search over the lanes' running counts.  f(j) sees every candidate once,
+// on one lane, with no order promised (for order-free reductions: minima,
+// or sums whose rounding order may vary).  All lanes of the team execute
+// the same iterations, so f and cell_ok may not use team shuffles.
+template <int T, class CellOk, class F>
+__device__ __forceinline__ void for_each_candidate_team(
+    const Grid &g, const Domain &d, int li, float xr, float yr, float hi,
+    float qscale, int lane, unsigned mask, CellOk &&cell_ok, F &&f) {
+    if constexpr (T == 1) {
+        (void)lane;
+        (void)mask;
+        for_each_cell_scaled(g, d, li, xr, yr, hi, qscale,
+                             [&](uint32_t s, uint32_t e) {
+            if (!cell_ok(s, e)) return;
+            for (uint32_t j = s; j < e; ++j) f(j);
+        });
+        return;
+    }
+    const float Ri = 3.0f * hi;
+    const uint32_t lmask = g.level_mask & ~((1u << li) - 1u);
+    for (uint32_t mm = lmask; mm; mm &= mm - 1) {
+        const int l = __ffs(mm) - 1;
+        const int *bb = g.bbox + 4 * l;
+        if (__ldg(&bb[0]) > __ldg(&bb[1])) continue;   // level holds no particle
+        const Level &L = g.lev[l];
+        const float Q = qscale * fmaxf(Ri, L.cf) * (1.0f + 1e-5f);
+        AxisPieces px, py;
+        if (!axis_pieces(d, L, bb, 0, xr, Q, px)) continue;
+        if (!axis_pieces(d, L, bb, 1, yr, Q, py)) continue;
+        const int nx0 = max(0, px.last[0] - px.first[0] + 1);
+        const int nx1 = max(0, px.last[1] - px.first[1] + 1);
+        const int nx2 = max(0, px.last[2] - px.first[2] + 1);
+        const int ny0 = max(0, py.last[0] - py.first[0] + 1);
+        const int ny1 = max(0, py.last[1] - py.first[1] + 1);
+        const int ny2 = max(0, py.last[2] - py.first[2] + 1);
+        const int nx = nx0 + nx1 + nx2, ny = ny0 + ny1 + ny2;
+        const int ncell = nx * ny;
+        const uint64_t lbits = (uint64_t)l << (2 * g.mbits);
+        for (int base = 0; base < ncell; base += T) {
+            const int idx = base + lane;
+            uint32_t s = 0, e = 0;
+            if (idx < ncell) {
+                const int iy = idx / nx, ix = idx - iy * nx;
+                const int kx = ix < nx0 ? 0 : ix < nx0 + nx1 ? 1 : 2;
+                const int ky = iy < ny0 ? 0 : iy < ny0 + ny1 ? 1 : 2;
+                const int cx = kx == 0 ? px.first[0] + ix
+                             : kx == 1 ? px.first[1] + (ix - nx0)
+                                       : px.first[2] + (ix - nx0 - nx1);
+                const int cy = ky == 0 ? py.first[0] + iy
+                             : ky == 1 ? py.first[1] + (iy - ny0)
+                                       : py.first[2] + (iy - ny0 - ny1);
+                const int sx = kx == 0 ? px.shift[0] : kx == 1 ? px.shift[1] : px.shift[2];
+                const int sy = ky == 0 ? py.shift[0] : ky == 1 ? py.shift[1] : py.shift[2];
+                if (!cell_visit(g, d, L, lbits, cx, cy, sx, sy, xr, yr, hi,
+                                qscale, s, e) ||
+                    !(e > s && cell_ok(s, e)))
+                    s = e = 0;
+            }
+            const uint32_t cnt = e - s;
+            uint32_t inc = cnt;
+#pragma unroll
+            for (int o = 1; o < T; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(mask, inc, o, T);
+                if (lane >= o) inc += t;
+            }
+            const uint32_t total = __shfl_sync(mask, inc, T - 1, T);
+            const uint32_t exc = inc - cnt;
+            for (uint32_t q0 = 0; q0 < total; q0 += T) {
+                const uint32_t q = q0 + (uint32_t)lane;
+                const uint32_t qq = min(q, total - 1);
+                int pos = 0;
+#pragma unroll
+                for (int st = T / 2; st; st >>= 1) {
+                    const uint32_t v = __shfl_sync(mask, inc, pos + st - 1, T);
+                    if (v <= qq) pos += st;
+                }
+                const uint32_t s0 = __shfl_sync(mask, s, pos, T);
+                const uint32_t e0 = __shfl_sync(mask, exc, pos, T);
+                if (q < total) f(s0 + (qq - e0));
+            }
+        }
+    }
+}
+
 template <int T, class F>
 __device__ __forceinline__ void for_each_cell_team(const Grid &g,
                                                    const Domain &d, int li,
