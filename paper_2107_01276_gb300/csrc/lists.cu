@@ -64,9 +64,10 @@ __device__ __forceinline__ bool member(const ListArgs &a, const float4 &pi,
 }
 
 // Single-walk list build: a team of T lanes walks particle i's own and
-// coarser levels (cells looked up in parallel, each cell's candidates
-// taken T at a time, one per lane); the team's ballot orders each group,
-// so own entries come in (cell, index) order whatever T is.  They go into
+// coarser levels (per level, up to T cells looked up at once, then the
+// candidates of all of them taken T at a time, one per lane); the team's
+// ballot orders each group, so own entries come in (cell, index) order
+// whatever T is.  They go into
 // a fixed-stride staging row of stage_w entries; particles with more own
 // entries go to a queue that k_list_fill_queue handles with a second walk.
 
@@ -83,21 +84,20 @@ __global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
     const uint32_t W = a.stage_w;
     uint32_t *row = a.stage + (size_t)i * W;
     const unsigned below = tm.mask & ((1u << (threadIdx.x & 31)) - 1u);
-    for_each_cell_team_scaled<T>(a.g, a.d, li, q.x, q.y, pi.z, a.skin, tm.lane,
-                                 tm.mask, [&](uint32_t s, uint32_t e) {
-        for (uint32_t j0 = s; j0 < e; j0 += T) {
-            const uint32_t j = j0 + tm.lane;
-            const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);
-            const unsigned bal = T == 1 ? (in ? 1u : 0u)
-                                        : __ballot_sync(tm.mask, in);
-            if (in) {
-                const uint32_t pos = k + (T == 1 ? 0u : __popc(bal & below));
-                const bool co = __ldg(&a.lev[j]) > li;
-                if (pos < W) row[pos] = co ? (j | STAGE_COARSE) : j;
-                if (co) atomicAdd(&a.rev[j], 1u);
-            }
-            k += __popc(bal);
+    for_each_candidate_team<T, true>(a.g, a.d, li, q.x, q.y, pi.z, a.skin,
+                                     tm.lane, tm.mask,
+                                     [](uint32_t, uint32_t) { return true; },
+                                     [&](uint32_t j, bool valid) {
+        const bool in = valid && member(a, pi, xi, yi, hi, (int)j);
+        const unsigned bal = T == 1 ? (in ? 1u : 0u)
+                                    : __ballot_sync(tm.mask, in);
+        if (in) {
+            const uint32_t pos = k + (T == 1 ? 0u : __popc(bal & below));
+            const bool co = __ldg(&a.lev[j]) > li;
+            if (pos < W) row[pos] = co ? (j | STAGE_COARSE) : j;
+            if (co) atomicAdd(&a.rev[j], 1u);
         }
+        k += __popc(bal);
     });
     if (tm.lane == 0) {
         a.own[i] = k;
@@ -155,23 +155,21 @@ __global__ void __launch_bounds__(128) k_list_fill_queue(ListArgs a) {
         const float2 q = anchor_rel(a.an, pi);
         uint32_t k = a.off[i];
         const uint32_t cap = a.cap;
-        for_each_cell_team_scaled<T>(a.g, a.d, li, q.x, q.y, pi.z, a.skin,
-                                     tm.lane, tm.mask,
-                                     [&](uint32_t s, uint32_t e) {
-            for (uint32_t j0 = s; j0 < e; j0 += T) {
-                const uint32_t j = j0 + tm.lane;
-                const bool in = j < e && member(a, pi, xi, yi, hi, (int)j);
-                const unsigned bal = __ballot_sync(tm.mask, in);
-                if (in) {
-                    const uint32_t pos = k + __popc(bal & below);
-                    if (pos < cap) a.list[pos] = j;
-                    if (__ldg(&a.lev[j]) > li) {
-                        uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
-                        if (rp < cap) a.list[rp] = (uint32_t)i;
-                    }
+        for_each_candidate_team<T, true>(a.g, a.d, li, q.x, q.y, pi.z, a.skin,
+                                         tm.lane, tm.mask,
+                                         [](uint32_t, uint32_t) { return true; },
+                                         [&](uint32_t j, bool valid) {
+            const bool in = valid && member(a, pi, xi, yi, hi, (int)j);
+            const unsigned bal = __ballot_sync(tm.mask, in);
+            if (in) {
+                const uint32_t pos = k + __popc(bal & below);
+                if (pos < cap) a.list[pos] = j;
+                if (__ldg(&a.lev[j]) > li) {
+                    uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
+                    if (rp < cap) a.list[rp] = (uint32_t)i;
                 }
-                k += __popc(bal);
             }
+            k += __popc(bal);
         });
     }
 }

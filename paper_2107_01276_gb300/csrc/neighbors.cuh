@@ -278,7 +278,12 @@ __device__ __forceinline__ void for_each_cell_team_scaled(
 // on one lane, with no order promised (for order-free reductions: minima,
 // or sums whose rounding order may vary).  All lanes of the team execute
 // the same iterations, so f and cell_ok may not use team shuffles.
-template <int T, class CellOk, class F>
+//
+// SYNC = true: f(j, valid) is called on every lane of the team in each
+// batch iteration (valid false past the last candidate), so f may use team
+// ballots; slot order is then the walk order (level, row, column, index),
+// the candidates of one iteration being consecutive in it.
+template <int T, bool SYNC = false, class CellOk, class F>
 __device__ __forceinline__ void for_each_candidate_team(
     const Grid &g, const Domain &d, int li, float xr, float yr, float hi,
     float qscale, int lane, unsigned mask, CellOk &&cell_ok, F &&f) {
@@ -288,7 +293,12 @@ __device__ __forceinline__ void for_each_candidate_team(
         for_each_cell_scaled(g, d, li, xr, yr, hi, qscale,
                              [&](uint32_t s, uint32_t e) {
             if (!cell_ok(s, e)) return;
-            for (uint32_t j = s; j < e; ++j) f(j);
+            for (uint32_t j = s; j < e; ++j) {
+                if constexpr (SYNC)
+                    f(j, true);
+                else
+                    f(j);
+            }
         });
         return;
     }
@@ -352,7 +362,10 @@ __device__ __forceinline__ void for_each_candidate_team(
                 }
                 const uint32_t s0 = __shfl_sync(mask, s, pos, T);
                 const uint32_t e0 = __shfl_sync(mask, exc, pos, T);
-                if (q < total) f(s0 + (qq - e0));
+                if constexpr (SYNC)
+                    f(s0 + (qq - e0), q < total);
+                else if (q < total)
+                    f(s0 + (qq - e0));
             }
         }
     }

@@ -350,13 +350,14 @@ __global__ void __launch_bounds__(128) k_wall_bc(WallBcArgs a) {
     const float4 pw = a.w.pk[k];
     const float2 q = anchor_rel(a.an, pw);
     double sw = 0, su = 0, sv = 0, sp = 0;
-    for_each_cell_team_scaled<T>(a.g, a.d, 0, q.x, q.y, pw.z, a.qscale, tm.lane,
-                                 tm.mask, [&](uint32_t s, uint32_t e) {
-        for (uint32_t f = s + tm.lane; f < e; f += T) {
+    for_each_candidate_team<T>(a.g, a.d, 0, q.x, q.y, pw.z, a.qscale, tm.lane,
+                               tm.mask, [](uint32_t, uint32_t) { return true; },
+                               [&](uint32_t f) {
+        {
             float fx, fy, fr2;
             if (!pred_mixed(a.d, a.an, pw, __ldg(&a.pk[f]), xw, yw, hw, a.x,
                             a.y, a.h, (int)f, fx, fy, fr2))
-                continue;
+                return;
             const double xf = __ldg(&a.x[f]), yf = __ldg(&a.y[f]),
                          hf = __ldg(&a.h[f]);
             const double dx = min_image(a.d, 0, xw - xf);
