@@ -463,6 +463,15 @@ def main():
         tmax, units = tot_ms, float(np.sum(ns))
     value = units / (tmax / 1e3)
 
+    # force on the body after the timed steps (Eq. force-sph, Eq. cdcl);
+    # a diagnostic of the state reached, outside the timed region
+    forces = None
+    if "walls" in d:
+        f = sim.forces()
+        forces = dict(sph.coefficients(f, d["params"]["rho0"], d.get("U", 1.0),
+                                       d.get("D", 1.0)),
+                      t=float(sim.info()["t"]))
+
     # pass-B pairs of the final state (rate of the pair loop)
     sim.rhs()
     nnb = sim.read("nnb")
@@ -628,6 +637,7 @@ def main():
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "kind": pk_kind},
         "neighbours_mean": float(nnb.mean()),
         "mixed_vs_fp64": err_rep,
+        "forces": forces,
     }
     print(json.dumps(line))
     if dist:

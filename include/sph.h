@@ -273,6 +273,28 @@ sph_status sph_adapt(sph_ctx *ctx, sph_adapt_stats *out);
  * bg_capacity; the iterations before that are kept), SPH_ENOMEM. */
 sph_status sph_background(sph_ctx *ctx, int iterations, sph_bg_stats *out);
 
+/* Force on the solid, i.e. on the loaded wall particles, at the current
+ * state (section "Force computation", Eq. force-sph): for each wall
+ * particle w over its fluid neighbours j (r_wj < 3 max(h_w, h_j)),
+ *   f_p,w    = -m_w sum_j m_j (P_w grad W(r_wj, h_w) + P_j grad W(r_wj, h_j))
+ *   f_visc,w =  m_w / beta_w sum_j m_j 4 nu / (rho_w + rho_j)
+ *                 (r_wj . grad W_wj) / (|r_wj|^2 + eta_w) (u_w - u_j)
+ * with P_w = p_w / rho0^2 and P_j = p_j / (rho_j^2 beta_j) (pressures
+ * without the average-pressure offset: a solid's sum sees fluid on one
+ * side only, where the pressure level is the load), rho_w = rho0, beta_w
+ * = 1, eta_w = 0.001 h_w^2, grad W_wj the mean of the two gradients and
+ * u_w the wall's extrapolated velocity; p_w, u_w from the wall condition
+ * and rho_j, beta_j from a pass A, all evaluated here at the current state
+ * (a neighbour build and one right-hand side; the particle state is not
+ * changed and the rates read afterwards are those of this state).  FP64
+ * sums for both precisions.  total[4] = {f_p,x, f_p,y, f_visc,x,
+ * f_visc,y}, summed over the walls in a fixed order; per_wall (may be
+ * NULL) receives 4 doubles per wall particle in load order.  The drag and
+ * lift coefficients of Eq. cdcl are these divided by rho0 U^2 L / 2.
+ * Without walls every output is zero.  Synchronises.  Errors: SPH_EINVAL
+ * (total NULL), SPH_ESTATE (no fluid), SPH_ENOMEM. */
+sph_status sph_forces(sph_ctx *ctx, double *per_wall, double *total);
+
 /* Copy one field of the fluid set to the host buffer dst holding cap
  * elements of the field's type; *n_out (if not NULL) receives the element
  * count.  Synchronises the context's stream.  Errors: SPH_EINVAL (bad

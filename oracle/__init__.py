@@ -173,6 +173,10 @@ def lib():
             L.orc_set_walls.argtypes = [ctypes.c_int] + [_D] * 6
             L.orc_wall_bc.restype = None
             L.orc_wall_bc.argtypes = [_P, ctypes.POINTER(_State), _D, _D, _D]
+            L.orc_forces.restype = None
+            L.orc_forces.argtypes = [_P, ctypes.POINTER(_State), _D, ctypes.c_void_p]
+            L.orc_record_wall_terms.restype = None
+            L.orc_record_wall_terms.argtypes = [ctypes.c_void_p]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
             L.orc_neighbors_classes.restype = ctypes.c_longlong
@@ -511,6 +515,44 @@ def wall_bc(P, st, nw):
     s = _cstate(st)
     lib().orc_wall_bc(ctypes.byref(P), ctypes.byref(s), *[_d(a) for a in out])
     return {"p": out[0][:nw], "ugx": out[1][:nw], "ugy": out[2][:nw]}
+
+
+def forces(P, st, nw: int = 0):
+    """Force on the registered walls at the state (section "Force
+    computation", Eq. force-sph): dict fp (pressure), fv (viscous), each
+    an (x, y) array, and with nw > 0 (the wall count) "per_wall", (nw, 4)."""
+    out = np.zeros(4)
+    pw = np.zeros((nw, 4)) if nw > 0 else None
+    s = _cstate(st)
+    lib().orc_forces(ctypes.byref(P), ctypes.byref(s), _d(out),
+                     pw.ctypes.data if pw is not None else None)
+    r = {"fp": out[:2].copy(), "fv": out[2:].copy()}
+    if pw is not None:
+        r["per_wall"] = pw
+    return r
+
+
+def coefficients(f, rho0, U, L):
+    """Eq. cdcl: pressure drag, skin-friction drag and lift coefficients
+    from a forces() dict, with the dynamic pressure rho0 U^2 / 2 and the
+    characteristic length L."""
+    q = 0.5 * rho0 * U * U * L
+    return {"cd_p": f["fp"][0] / q, "cd_sf": f["fv"][0] / q,
+            "cl": f["fp"][1] / q}
+
+
+def rhs_wall_terms(P, dt_, st):
+    """One right-hand side with each fluid particle's wall terms of its
+    momentum rate: (out dict of rhs, array n x 4 of pressure x, y and
+    viscous x, y wall terms)."""
+    n = st["n"]
+    acc = np.zeros((max(n, 1), 4))
+    lib().orc_record_wall_terms(acc.ctypes.data)
+    try:
+        out = rhs(P, dt_, st)
+    finally:
+        lib().orc_record_wall_terms(None)
+    return out, acc[:n]
 
 
 # ---------------------------------------------------------- background --

@@ -369,6 +369,12 @@ void orc_cell_keys(const orc_params *P, double c0, int n, const double *x,
  * ---------------------------------------------------------------------- */
 static int g_nw = 0;
 static double *g_w = NULL;   /* x, y, h, m, uw, vw, pw, ugx, ugy */
+/* When set, pass B also writes each fluid particle's wall terms:
+ * {pressure x, y, viscous x, y} of its momentum rate (test instrumentation
+ * for the force balance below). */
+static double *g_wall_acc = NULL;
+
+void orc_record_wall_terms(double *acc) { g_wall_acc = acc; }
 
 void orc_set_walls(int n, const double *x, const double *y, const double *h,
                    const double *m, const double *uw, const double *vw) {
@@ -485,6 +491,7 @@ int orc_pass_a(const orc_params *P, int n, const double *x, const double *y,
                 say += fabs(f * dy);
             }
         }
+        double wpx = 0, wpy = 0, wvx = 0, wvy = 0;   /* the walls' share */
         if (g_nw > 0) {
             int wl[2048];
             int nwl = wall_nbrs(P, x[i], y[i], h[i], wl, 2048);
@@ -571,6 +578,9 @@ void orc_pass_b(const orc_params *P, double dt, int n, const double *x,
         if (beta_i == 0.0) {
             o->dpdt[i] = o->dudt[i] = o->dvdt[i] = 0.0;
             o->s_dpdt[i] = o->s_dudt[i] = o->s_dvdt[i] = 0.0;
+            if (g_wall_acc)
+                g_wall_acc[4 * i] = g_wall_acc[4 * i + 1] =
+                    g_wall_acc[4 * i + 2] = g_wall_acc[4 * i + 3] = 0.0;
             continue;
         }
         double rho_i = o->rho[i];
@@ -636,6 +646,7 @@ void orc_pass_b(const orc_params *P, double dt, int n, const double *x,
             s_vx += fabs(visc) * au;
             s_vy += fabs(visc) * av;
         }
+        double wpx = 0, wpy = 0, wvx = 0, wvy = 0;   /* the walls' share */
         if (g_nw > 0) {
             int wl[2048];
             int nwl = wall_nbrs(P, x[i], y[i], h[i], wl, 2048);
@@ -670,12 +681,16 @@ void orc_pass_b(const orc_params *P, double dt, int n, const double *x,
                 tvf += WM(w) * (dux * fx + duy * fy);
                 ax -= WM(w) * fx;
                 ay -= WM(w) * fy;
+                wpx -= WM(w) * fx;
+                wpy -= WM(w) * fy;
                 /* extrapolated wall velocity: no slip */
                 double ug = u[i] - WGX(w), vg = v[i] - WGY(w);
                 double visc = WM(w) * (4.0 * P->nu / (rho_i + P->rho0)) *
                               rdotgbar / (r2 + eta);
                 vx += visc * ug;
                 vy += visc * vg;
+                wvx += visc * ug;
+                wvy += visc * vg;
                 double au = fabs(u[i]) + fabs(WU(w)), av = fabs(v[i]) + fabs(WV(w));
                 s_div += Vj * (au * fabs(gWix) + av * fabs(gWiy));
                 s_diff += Vj * nu_ij * (fabs(p[i]) + fabs(WP(w))) *
@@ -688,6 +703,12 @@ void orc_pass_b(const orc_params *P, double dt, int n, const double *x,
                 s_vx += fabs(visc) * (fabs(u[i]) + fabs(WGX(w)));
                 s_vy += fabs(visc) * (fabs(v[i]) + fabs(WGY(w)));
             }
+        }
+        if (g_wall_acc) {
+            g_wall_acc[4 * i] = wpx;
+            g_wall_acc[4 * i + 1] = wpy;
+            g_wall_acc[4 * i + 2] = wvx / beta_i;
+            g_wall_acc[4 * i + 3] = wvy / beta_i;
         }
         double rf = P->edac_rho_factor ? rho_i : 1.0;
         o->dpdt[i] = (P->rho0 * c2 / beta_i) * div + diff / beta_i + rf * tvf;
@@ -743,6 +764,84 @@ int orc_rhs(const orc_params *P, double dt, const orc_state *s,
     orc_pass_b(P, dt, s->n, s->x, s->y, s->h, s->m, s->p, s->u, s->v, g_off,
                g_nbr, o);
     return deg;
+}
+
+/* ------------------------------------------------------------------------
+ * Force on the solid, section "Force computation", Eq. force-sph: for each
+ * wall particle w over its fluid neighbours j (r_wj < 3 max(h_w, h_j)),
+ * r_wj = r_w - r_j and gradients with respect to r_w,
+ *   f_p,w    = -m_w sum_j m_j (P_w grad W(r_wj, h_w) + P_j grad W(r_wj, h_j))
+ *   f_visc,w =  m_w / beta_w sum_j m_j 4 nu / (rho_w + rho_j)
+ *                 (r_wj . grad W_wj) / (|r_wj|^2 + eta_w) (u_w - u_j)
+ * Reading F1: the pressures enter without the average-pressure offset,
+ * P_w = p_w / rho0^2 and P_j = p_j / (rho_j^2 beta_j).  The offset takes a
+ * constant out of a particle's own pressure gradient, harmless inside the
+ * fluid, but the solid's sum runs over fluid on one side only, where the
+ * pressure level itself is the load (with the offset a uniform pressure
+ * would press on no wall).  The wall has rho_w = rho0, beta_w = 1, eta_w =
+ * 0.001 h_w^2; grad W_wj is the mean of the two gradients (Eq. dw-avg) and
+ * u_w the extrapolated (no-slip) wall velocity of the viscous sum.  p_w, u_w from the wall condition and
+ * rho_j, beta_j from pass A, both at the given state.  out:
+ * {f_p,x, f_p,y, f_visc,x, f_visc,y} summed over the walls in index order;
+ * per_wall (NULL: not wanted) the four components of each wall particle.
+ * ---------------------------------------------------------------------- */
+void orc_forces(const orc_params *P, const orc_state *s, double *out,
+                double *per_wall) {
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    if (g_nw == 0 || s->n == 0) return;
+    wall_bc_update(P, s);
+    neighbors_auto(P, s->n, s->x, s->y, s->h);
+    const int n = s->n;
+    orc_rhs_out o;
+    double **arrs[] = {&o.rho, &o.beta, &o.pavg, &o.drx, &o.dry, &o.dpdt,
+                       &o.dudt, &o.dvdt, &o.s_rho, &o.s_beta, &o.s_pavg,
+                       &o.s_drx, &o.s_dry, &o.s_dpdt, &o.s_dudt, &o.s_dvdt};
+    for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); ++k)
+        *arrs[k] = (double *)calloc((size_t)n, sizeof(double));
+    o.nnb = (int *)calloc((size_t)n, sizeof(int));
+    orc_pass_a(P, n, s->x, s->y, s->h, s->m, s->p, g_off, g_nbr, &o);
+    double *fw = (double *)calloc((size_t)g_nw * 4, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int w = 0; w < g_nw; ++w) {
+        double fpx = 0, fpy = 0, fvx = 0, fvy = 0;
+        const double eta = 0.001 * WH(w) * WH(w);
+        for (int j = 0; j < n; ++j) {
+            if (!orc_is_neighbor(P, WX(w), WY(w), WH(w), s->x[j], s->y[j],
+                                 s->h[j]))
+                continue;
+            const double beta_j = o.beta[j];
+            if (beta_j == 0.0) continue;
+            double dx, dy;
+            separation(P, WX(w), WY(w), s->x[j], s->y[j], &dx, &dy);
+            const double r2 = dx * dx + dy * dy;
+            const double r = sqrt(r2);
+            double gw = 0.0, gj = 0.0;
+            if (r > 0.0) {
+                gw = orc_dWdr(r, WH(w)) / r;
+                gj = orc_dWdr(r, s->h[j]) / r;
+            }
+            const double rho_j = o.rho[j];
+            const double Pw = WP(w) / (P->rho0 * P->rho0);
+            const double Pj = s->p[j] / (rho_j * rho_j * beta_j);
+            fpx -= s->m[j] * (Pw * gw + Pj * gj) * dx;
+            fpy -= s->m[j] * (Pw * gw + Pj * gj) * dy;
+            const double rdotgbar = 0.5 * (gw + gj) * r2;
+            const double visc = s->m[j] * (4.0 * P->nu / (P->rho0 + rho_j)) *
+                                rdotgbar / (r2 + eta);
+            fvx += visc * (WGX(w) - s->u[j]);
+            fvy += visc * (WGY(w) - s->v[j]);
+        }
+        fw[4 * w] = WM(w) * fpx;
+        fw[4 * w + 1] = WM(w) * fpy;
+        fw[4 * w + 2] = WM(w) * fvx;   /* 1 / beta_w = 1 */
+        fw[4 * w + 3] = WM(w) * fvy;
+    }
+    for (int w = 0; w < g_nw; ++w)
+        for (int k = 0; k < 4; ++k) out[k] += fw[4 * w + k];
+    if (per_wall) memcpy(per_wall, fw, sizeof(double) * 4 * (size_t)g_nw);
+    free(fw);
+    for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); ++k) free(*arrs[k]);
+    free(o.nnb);
 }
 
 /* ------------------------------------------------------------------------

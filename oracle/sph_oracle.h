@@ -122,6 +122,14 @@ void orc_set_walls(int n, const double *x, const double *y, const double *h,
                    const double *m, const double *uw, const double *vw);
 /* Wall pressure and extrapolated velocity from the fluid (Eqs. bc-wall,
  * shepard, bc-pre with g = a_w = 0) for the registered walls. */
+/* Force on the solid (walls) at the state: {f_p,x, f_p,y, f_visc,x,
+ * f_visc,y} (section "Force computation", Eq. force-sph, reading F1). */
+void orc_forces(const orc_params *P, const orc_state *s, double *out,
+                double *per_wall);
+/* Test instrumentation: when acc (4 doubles per fluid particle) is set,
+ * pass B writes each particle's wall terms of its momentum rate there
+ * (pressure x, y, viscous x, y); NULL stops it. */
+void orc_record_wall_terms(double *acc);
 void orc_wall_bc(const orc_params *P, const orc_state *s, double *pw,
                  double *ugx, double *ugy);
 

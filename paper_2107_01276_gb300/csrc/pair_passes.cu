@@ -387,6 +387,89 @@ __global__ void __launch_bounds__(128) k_wall_bc(WallBcArgs a) {
     a.ugy[k] = 2.0 * a.w.vw[k] - vh;
 }
 
+// ---------------------------------------------------------- force on solid --
+// Section "Force computation", Eq. force-sph, for wall particle k over its
+// fluid neighbours j; FP64 sums (a team of T lanes per wall particle).
+template <typename R, int T>
+__global__ void __launch_bounds__(128) k_forces(ForceArgs<R> a) {
+    const Team<T> tm;
+    const int k = Team<T>::particle();
+    if (k >= a.w.n) return;
+    const double xw = a.w.x[k], yw = a.w.y[k], hw = a.w.h[k];
+    const float4 pw = a.w.pk[k];
+    const float2 q = anchor_rel(a.an, pw);
+    const double Pw = a.w.p[k] / (a.rho0 * a.rho0);
+    const double ugx = a.w.ugx[k], ugy = a.w.ugy[k];
+    const double eta = 0.001 * hw * hw;
+    const double sw = sigma_norm<double>() / (hw * hw * hw);
+    double fpx = 0, fpy = 0, fvx = 0, fvy = 0;
+    for_each_candidate_team<T>(a.g, a.d, 0, q.x, q.y, pw.z, 1.0f, tm.lane,
+                               tm.mask, [](uint32_t, uint32_t) { return true; },
+                               [&](uint32_t j) {
+        float fx, fy, fr2;
+        if (!pred_mixed(a.d, a.an, pw, __ldg(&a.pk[j]), xw, yw, hw, a.x, a.y,
+                        a.h, (int)j, fx, fy, fr2))
+            return;
+        const double beta_j = (double)a.beta[j];
+        if (beta_j == 0.0) return;
+        const double dx = min_image(a.d, 0, xw - a.x[j]);
+        const double dy = min_image(a.d, 1, yw - a.y[j]);
+        const double r2 = dx * dx + dy * dy;
+        double gw = 0.0, gj = 0.0;
+        if (r2 > 0.0) {
+            const double r = sqrt(r2), hj = a.h[j];
+            gw = sw * qs_dw<double>(r / hw) / r;
+            gj = sigma_norm<double>() / (hj * hj * hj) * qs_dw<double>(r / hj) / r;
+        }
+        const double rho_j = (double)a.rho[j], mj = a.m[j];
+        const double Pj = a.p[j] / (rho_j * rho_j * beta_j);
+        const double fp = mj * (Pw * gw + Pj * gj);
+        fpx -= fp * dx;
+        fpy -= fp * dy;
+        const double visc = mj * (4.0 * a.nu / (a.rho0 + rho_j)) *
+                            (0.5 * (gw + gj) * r2) / (r2 + eta);
+        fvx += visc * (ugx - a.u[j]);
+        fvy += visc * (ugy - a.v[j]);
+    });
+    fpx = team_sum<T>(tm.mask, fpx);
+    fpy = team_sum<T>(tm.mask, fpy);
+    fvx = team_sum<T>(tm.mask, fvx);
+    fvy = team_sum<T>(tm.mask, fvy);
+    if (tm.lane != 0) return;
+    const double mw = a.w.m[k];   // beta_w = 1
+    a.fw[4 * k] = mw * fpx;
+    a.fw[4 * k + 1] = mw * fpy;
+    a.fw[4 * k + 2] = mw * fvx;
+    a.fw[4 * k + 3] = mw * fvy;
+}
+
+// One block: fixed-order sums of the four components (each thread a
+// strided share, then a tree over the threads) and the load-order copy.
+__global__ void __launch_bounds__(256)
+    k_forces_total(int nw, const double *fw, const int64_t *id, double *out,
+                   double *total) {
+    __shared__ double s[4][256];
+    double acc[4] = {0, 0, 0, 0};
+    for (int k = threadIdx.x; k < nw; k += 256) {
+        const int64_t o = id[k];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc[c] += fw[4 * k + c];
+            out[4 * o + c] = fw[4 * k + c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) total[threadIdx.x] = s[threadIdx.x][0];
+}
+
 // ---------------------------------------------------- neighbour CSR dump --
 __global__ void k_nbr_ids(int n, const uint32_t *off, const uint32_t *list,
                           const int64_t *id, int64_t *out) {
@@ -540,6 +623,22 @@ template void launch_pass_b<double>(cudaStream_t, const PassBArgs<double> &);
 template void launch_pass_b<float>(cudaStream_t, const PassBArgs<float> &);
 template void launch_pec<double>(cudaStream_t, const PecArgs<double> &);
 template void launch_pec<float>(cudaStream_t, const PecArgs<float> &);
+
+template <typename R>
+void launch_forces(cudaStream_t s, const ForceArgs<R> &a) {
+    if (a.w.n <= 0) return;
+    with_team(a.w.n, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        k_forces<R, T><<<nblk(a.w.n * T, 128), 128, 0, s>>>(a);
+    });
+}
+template void launch_forces<double>(cudaStream_t, const ForceArgs<double> &);
+template void launch_forces<float>(cudaStream_t, const ForceArgs<float> &);
+
+void launch_forces_total(cudaStream_t s, int nw, const double *fw,
+                         const int64_t *id, double *out, double *total) {
+    k_forces_total<<<1, 256, 0, s>>>(nw, fw, id, out, total);
+}
 
 void launch_wall_bc(cudaStream_t s, const WallBcArgs &a) {
     if (a.w.n <= 0) return;

@@ -72,7 +72,28 @@ struct ConvList {
     int k;
 };
 
+// Force on the walls (Eq. force-sph, pressures without the average
+// offset): per wall particle (sorted wall order) {f_p,x, f_p,y, f_visc,x,
+// f_visc,y} into fw[4 k ..]; fluid rho, beta from pass A (type R).
+template <typename R>
+struct ForceArgs {
+    WallView w;
+    Grid g;                       // fluid cell structure (fresh)
+    Domain d;
+    Anchor an;
+    const float4 *pk;             // fluid anchor data
+    const double *x, *y, *h, *m, *u, *v, *p;
+    const R *rho, *beta;
+    double rho0, nu;
+    double *fw;
+};
+
 template <typename R> void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a);
+template <typename R> void launch_forces(cudaStream_t s, const ForceArgs<R> &a);
+// Deterministic sum of the per-wall forces into total[4] and their copy in
+// load order (id: load index of each sorted wall) into out[4 id ..].
+void launch_forces_total(cudaStream_t s, int nw, const double *fw,
+                         const int64_t *id, double *out, double *total);
 template <typename R> void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a);
 template <typename R> void launch_pec(cudaStream_t s, const PecArgs<R> &a);
 void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,

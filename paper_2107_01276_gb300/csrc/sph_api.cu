@@ -132,6 +132,8 @@ struct sph_ctx {
     uint32_t *tmp_a = nullptr, *tmp_b = nullptr;   // N + 1 each
     int *closest = nullptr;
     float *mh0 = nullptr, *mds = nullptr;   // merge rounds: h at the build, displacement
+    double *d_force = nullptr;   // sph_forces: 8 n_wall + 4 doubles
+    int force_cap = 0;           // walls d_force holds
     double *d_mass = nullptr, *d_mass_part = nullptr;  // [2], [256]
     uint32_t *d_aux = nullptr;                         // [4] adapt counters
     StaticSet bg;     // background particles (section 3.3); extra: ds, m
@@ -654,6 +656,7 @@ static void free_ctx(sph_ctx *c) {
                   c->wugy, c->d_aux};
     for (void *p : ps) cudaFree(p);
     cudaFree(c->omega);
+    cudaFree(c->d_force);
     cudaFree(c->d_wmax);
     cudaFree(c->d_minmax);
     if (c->bgc) {
@@ -1318,6 +1321,29 @@ static sph_status check_overflow(sph_ctx *c, const char *who) {
 }
 
 // ================================================================ C ABI ==
+template <typename R>
+static void forces_launch(sph_ctx *c) {
+    ForceArgs<R> a;
+    a.w = wall_view(c);
+    a.g = grid_for_kernels(c);
+    a.d = c->dom;
+    a.an = c->an;
+    a.pk = c->pk;
+    a.x = c->f[F_X];
+    a.y = c->f[F_Y];
+    a.h = c->f[F_H];
+    a.m = c->f[F_M];
+    a.u = c->f[F_U];
+    a.v = c->f[F_V];
+    a.p = c->f[F_P];
+    a.rho = (const R *)c->rhoR;
+    a.beta = (const R *)c->beta;
+    a.rho0 = c->prm.rho0;
+    a.nu = c->prm.nu;
+    a.fw = c->d_force;
+    launch_forces<R>(c->s, a);
+}
+
 extern "C" {
 
 void sph_default_params(sph_params *p) {
@@ -1470,6 +1496,45 @@ sph_status sph_rhs(sph_ctx *c) {
     store_rho(c);
     c->rhs_valid = true;
     return cuda_check(c, "sph_rhs");
+}
+
+sph_status sph_forces(sph_ctx *c, double *per_wall, double *total) {
+    if (!c) return SPH_EINVAL;
+    c->err.clear();
+    if (!total) return fail(c, SPH_EINVAL, "sph_forces: total is NULL");
+    for (int k = 0; k < 4; ++k) total[k] = 0.0;
+    if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_forces: no fluid particles loaded");
+    const int nw = c->wall.n;
+    if (nw <= 0) return SPH_OK;
+    if (c->force_cap < nw) {
+        cudaFree(c->d_force);
+        c->d_force = nullptr;
+        c->force_cap = 0;
+        if (!dalloc(&c->d_force, (size_t)8 * nw + 4)) {
+            cudaGetLastError();
+            return fail(c, SPH_ENOMEM, "sph_forces: device allocation failed");
+        }
+        c->force_cap = nw;
+    }
+    // the wall condition and pass A at the current state
+    compute_dt(c, nullptr, 0);
+    sph_status st = rebuild(c, false);
+    if (st != SPH_OK) return st;
+    run_passes(c);
+    c->rhs_valid = true;
+    if (is_mixed(c))
+        forces_launch<float>(c);
+    else
+        forces_launch<double>(c);
+    double *out = c->d_force + 4 * (size_t)nw, *tot = c->d_force + 8 * (size_t)nw;
+    launch_forces_total(c->s, nw, c->d_force, c->wall.id, out, tot);
+    c->launches += 2;
+    cudaMemcpyAsync(total, tot, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    if (per_wall)
+        cudaMemcpyAsync(per_wall, out, 4 * sizeof(double) * nw,
+                        cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_forces");
+    return cuda_check(c, "sph_forces");
 }
 
 sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {

@@ -128,6 +128,8 @@ def lib(build_if_missing: bool = True):
     L.sph_adapt.argtypes = [ctx, P(AdaptStats)]
     L.sph_background.restype = ctypes.c_int
     L.sph_background.argtypes = [ctx, ctypes.c_int, P(BgStats)]
+    L.sph_forces.restype = ctypes.c_int
+    L.sph_forces.argtypes = [ctx, ctypes.c_void_p, _D]
     L.sph_read.restype = ctypes.c_int
     L.sph_read.argtypes = [ctx, ctypes.c_int, ctypes.c_void_p,
                            ctypes.c_longlong, P(ctypes.c_longlong)]
@@ -147,6 +149,15 @@ def lib(build_if_missing: bool = True):
         [ctypes.c_void_p] * 6
     _lib = L
     return L
+
+
+def coefficients(f: dict, rho0: float, U: float, L: float) -> dict:
+    """Eq. cdcl: pressure drag, skin-friction drag and lift coefficients of
+    a Simulation.forces() result, with the dynamic pressure rho0 U^2 / 2
+    and the characteristic length L."""
+    q = 0.5 * rho0 * U * U * L
+    return {"cd_p": float(f["fp"][0] / q), "cd_sf": float(f["fv"][0] / q),
+            "cl": float(f["fp"][1] / q)}
 
 
 def cell_sort_noalloc(params: Params, n: int, x_ptr: int, y_ptr: int,
@@ -255,6 +266,21 @@ class Simulation:
         self._check(self._L.sph_background(self._ctx, int(iterations),
                                            ctypes.byref(z)))
         return {k: getattr(z, k) for k, _ in BgStats._fields_}
+
+    def forces(self, per_wall: bool = False) -> dict:
+        """sph_forces: force on the wall particles at the current state,
+        {"fp": (x, y) pressure part, "fv": (x, y) viscous part} and, with
+        per_wall, "per_wall": (n_walls, 4) in load order."""
+        tot = np.zeros(4)
+        nw = self.info()["n_wall"]
+        pw = np.zeros((max(nw, 1), 4)) if per_wall else None
+        self._check(self._L.sph_forces(
+            self._ctx, pw.ctypes.data if per_wall else None,
+            tot.ctypes.data_as(_D)))
+        out = {"fp": tot[:2].copy(), "fv": tot[2:].copy()}
+        if per_wall:
+            out["per_wall"] = pw[:nw]
+        return out
 
     def read_background(self) -> dict:
         """The background set (x, y, h, m, ds, id) in the library's order."""

@@ -404,3 +404,42 @@ def cylinder(D: float = 2.0, Re: float = 40.0, ds_min_over_D: float = 1 / 50,
 
 def subset(parts: dict, idx) -> dict:
     return {k: np.asarray(v)[idx].copy() for k, v in parts.items()}
+
+
+def ring_in_lattice(ds: float = 0.05, R: float = 1.0, box: float = 6.0,
+                    layers: int = 4, hdx: float = 1.2, rho0: float = 1.0,
+                    cs: float = 10.0, nu: float = 0.01, jitter: float = 0.0,
+                    seed: int = 1):
+    """A closed circular body of radius R at the centre of a periodic
+    box x box: `layers` rings of wall particles at spacing ds inside r < R,
+    fluid on the ds lattice outside (optionally jittered), at rest with
+    zero pressure (callers set the fields).  Returns particles, walls,
+    params and the centre."""
+    rng = np.random.default_rng(seed)
+    g = (np.arange(int(round(box / ds))) + 0.5) * ds
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    x, y = X.ravel(), Y.ravel()
+    c = 0.5 * box
+    keep = np.hypot(x - c, y - c) >= R
+    x, y = x[keep], y[keep]
+    if jitter > 0:
+        x = x + jitter * ds * rng.uniform(-1, 1, x.size)
+        y = y + jitter * ds * rng.uniform(-1, 1, y.size)
+    n = x.size
+    fl = dict(x=x, y=y, u=np.zeros(n), v=np.zeros(n), p=np.zeros(n),
+              rho=np.full(n, rho0), m=np.full(n, rho0 * ds * ds),
+              h=np.full(n, hdx * ds))
+    wx, wy = [], []
+    for k in range(layers):
+        r = R - (k + 0.5) * ds
+        nk = 2 * int(round(math.pi * r / ds))   # even: mirror-symmetric
+        t = (np.arange(nk) + 0.5) * (2 * math.pi / nk)
+        wx.append(c + r * np.cos(t))
+        wy.append(c + r * np.sin(t))
+    wx, wy = np.concatenate(wx), np.concatenate(wy)
+    walls = dict(x=wx, y=wy, h=np.full(wx.size, hdx * ds),
+                 m=np.full(wx.size, rho0 * ds * ds))
+    params = _base_params(lo=(0.0, 0.0), hi=(box, box), periodic=(1, 1),
+                          rho0=rho0, cs=cs, nu=nu, U_ref=1.0, hdx=hdx)
+    return {"particles": fl, "walls": walls, "params": params,
+            "center": (c, c), "R": R, "ds": ds}
