@@ -259,3 +259,72 @@ def test_background_errors():
         sim.background(1)
     assert e.value.status == sph.SPH_EINVAL
     sim.close()
+
+
+def test_moving_body_update_parity(oracle_stages):
+    """A moving body (section 3.3: the background is updated by single
+    iterations as the solid moves): the context first holds the walls at
+    their old position, they are reloaded 0.5 further along x, and one
+    iteration from the oracle's state runs against the moved walls.  Both
+    sides take the same decisions: counts, ids and masses exact."""
+    pr = _params()
+    OP = oracle.params(**pr)
+    B = oracle.bg_params(DS_MIN, DS_MAX, CR)
+    b = oracle.make_bgset(oracle_stages[30], cap=200000)
+    nid = int(oracle_stages[30]["id"].max()) + 1
+    r, _, nid = oracle.bg_iteration(OP, B, b, nid, _solid())
+    assert r == 0
+    n = b["n"]
+    s1 = {k: b[k][:n].copy() for k in BG_FIELDS + ("id",)}
+    moved = _solid()
+    moved["x"] = moved["x"] + 0.5
+    r, o, _ = oracle.bg_iteration(OP, B, b, nid, moved)
+    assert r == 0 and o["n_marked"] > 0
+    n = b["n"]
+    order = np.argsort(b["id"][:n], kind="stable")
+    ref = {k: b[k][:n][order] for k in BG_FIELDS + ("id",)}
+
+    P = sph.make_params(pr, precision=sph.SPH_FP64, capacity=1000,
+                        bg_capacity=200000)
+    sim = sph.Simulation(P, stream_handle())
+    sim.load(_solid(), kind=sph.SPH_WALL)
+    sim.load(s1, kind=sph.SPH_BACKGROUND)
+    sim.load(moved, kind=sph.SPH_WALL)          # the body moved
+    g = sim.background(1)
+    got = sim.read_background()
+    sim.close()
+    order = np.argsort(got["id"], kind="stable")
+    got = {k: v[order] for k, v in got.items()}
+    for k in ("n_marked", "n_split", "n_after"):
+        assert g[k] == o[k], (k, g, o)
+    assert np.array_equal(got["id"], ref["id"])
+    assert np.array_equal(got["m"], ref["m"])
+    assert np.abs(got["ds"] / ref["ds"] - 1).max() < 1e-12
+
+
+def test_background_follows_a_moving_body():
+    """The paper's moving-solid experiment in small: after the full
+    construction the body moves 0.05 per step for 20 steps with one
+    background iteration per step; ds_min then sits at the body's new
+    surface and the old position has coarsened."""
+    P = sph.make_params(_params(), precision=sph.SPH_FP64, capacity=1000,
+                        bg_capacity=400000)
+    sim = sph.Simulation(P, stream_handle())
+    sim.load(_solid(), kind=sph.SPH_WALL)
+    sim.load(_lattice_bg(), kind=sph.SPH_BACKGROUND)
+    sim.background()
+    body = _solid()
+    for _ in range(20):
+        body["x"] = body["x"] + 0.05
+        sim.load(body, kind=sph.SPH_WALL)
+        sim.background(1)
+    b = sim.read_background()
+    sim.close()
+    c_new = (LB / 2 + 1.0, LB / 2)
+    r_new = np.hypot(b["x"] - c_new[0], b["y"] - c_new[1])
+    near = (r_new > RAD) & (r_new < RAD + 0.3)
+    assert near.sum() > 0 and np.median(b["ds"][near]) == DS_MIN
+    # behind the body, where its surface was, sizes have grown
+    r_old = np.hypot(b["x"] - (LB / 2 - 1.0), b["y"] - LB / 2)
+    behind = (r_old < 0.3)
+    assert behind.sum() > 0 and np.median(b["ds"][behind]) > DS_MIN
