@@ -353,6 +353,8 @@ def main():
                     choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run sph_autotune on the set-up state (untimed)")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps of the mixed run with "
                          "cudaProfilerStart/Stop (for ncu "
@@ -386,6 +388,8 @@ def main():
     d, desc = make_workload(args.workload)
     pt = d["particles"]
 
+    tuned = {}
+
     def new_sim(precision):
         cap = 400000 if adaptive else int(len(pt["x"]) * 1.1) + 16
         P = sph.make_params(d["params"], precision=precision, capacity=cap)
@@ -399,6 +403,8 @@ def main():
                 s.background()
         for _ in range(wdef.get("refine_calls", 0)):
             s.adapt()
+        if args.autotune:
+            tuned.update(s.autotune())
         return s
 
     def one_step(s):
@@ -638,6 +644,8 @@ def main():
         "neighbours_mean": float(nnb.mean()),
         "mixed_vs_fp64": err_rep,
         "forces": forces,
+        "tuning": ({k: tuned[k] for k in ("cell_scale", "walk", "team_a", "team_b")}
+                   if tuned else None),
     }
     print(json.dumps(line))
     if dist:

@@ -295,6 +295,43 @@ sph_status sph_background(sph_ctx *ctx, int iterations, sph_bg_stats *out);
  * (total NULL), SPH_ESTATE (no fluid), SPH_ENOMEM. */
 sph_status sph_forces(sph_ctx *ctx, double *per_wall, double *total);
 
+/* Launch configuration of a context's hot kernels.  Every choice gives the
+ * same neighbour sets; the team sizes change the summation order of the
+ * pair sums (results equal to rounding, not bit for bit). */
+typedef struct {
+    double cell_scale;   /* level-0 cell side = cell_scale x the default of
+                            sph_params.cell_c0; <= 0: 1 */
+    int walk;            /* list build: 1 per-particle team walk, 2 cell
+                            tiles with 4-lane teams, 3 cell tiles with a
+                            lane per particle; 0: by set size (< 12k: 1,
+                            < 60k: 2, else 3) */
+    int team_a, team_b;  /* lanes per particle in pass A / pass B: 1, 4,
+                            16 or 32; 0: by set size */
+    /* filled by sph_autotune: mean device ms per launch of each candidate
+     * (neighbour build + both passes for cell_scale 1, 1.25, 1.5; the walk
+     * for walk 1..3; pass A / pass B for teams 1, 4, 16, 32) */
+    double ms_cell[3], ms_walk[3], ms_team_a[4], ms_team_b[4];
+} sph_tune;
+
+/* Autotuner (the paper has no counterpart; a launch-configuration search
+ * for this GPU): on the loaded fluid set at its current state, times
+ * neighbour builds and right-hand sides for each level-0 cell size
+ * (x1, x1.25, x1.5), then each list-build kernel, then each team size of
+ * pass A and pass B (CUDA events, a few repetitions after a warm-up), and
+ * keeps the fastest of each for this context; out (may be NULL) receives
+ * the choices and the times.  It ends with a right-hand side as sph_rhs
+ * does (the state re-sorted, its density the summation density, the rates
+ * those of the current state); positions, velocities, pressures, masses
+ * and h are not changed.  Takes a few dozen builds; clears the
+ * sph_kernel_time accumulators; synchronises.  Errors: SPH_ESTATE (no fluid), others
+ * as sph_rhs. */
+sph_status sph_autotune(sph_ctx *ctx, sph_tune *out);
+
+/* Sets a context's launch configuration (for instance one sph_autotune
+ * found for another context of the same kind and size); the ms_* members
+ * are ignored.  Errors: SPH_EINVAL (a value not listed above). */
+sph_status sph_set_tuning(sph_ctx *ctx, const sph_tune *in);
+
 /* Copy one field of the fluid set to the host buffer dst holding cap
  * elements of the field's type; *n_out (if not NULL) receives the element
  * count.  Synchronises the context's stream.  Errors: SPH_EINVAL (bad

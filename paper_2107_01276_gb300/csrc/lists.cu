@@ -659,18 +659,20 @@ void launch_anchor_pack(cudaStream_t s, int n, const double *x,
 // team walk keeps more warps in flight than the cell tiles; from there the
 // tiles win, with teams of 4 lanes up to ~60k particles and one lane per
 // particle beyond (1.6x faster than the per-particle walk on the 1:250
-// graded million, 2.5x at 300k).
-static bool use_tile(int n) { return n >= 12000; }
-static int tile_team(int n) { return n >= 60000 ? 1 : 4; }
+// graded million, 2.5x at 300k).  A.walk overrides it (tuning).
+static int walk_kind(const ListArgs &a) {
+    if (a.walk >= 1 && a.walk <= 3) return a.walk;
+    return a.n < 12000 ? 1 : a.n < 60000 ? 2 : 3;
+}
 
 void launch_list_walk(cudaStream_t s, const ListArgs &a, int *launches) {
     const int n = a.n;
     if (n <= 0) return;
-    if (use_tile(n)) {
-        if (tile_team(n) == 1)
-            k_list_tile<1><<<nblk(n, 128), 128, 0, s>>>(a);
-        else
-            k_list_tile<4><<<nblk(n, 32), 128, 0, s>>>(a);
+    const int kind = walk_kind(a);
+    if (kind == 3) {
+        k_list_tile<1><<<nblk(n, 128), 128, 0, s>>>(a);
+    } else if (kind == 2) {
+        k_list_tile<4><<<nblk(n, 32), 128, 0, s>>>(a);
     } else {
         with_team(n, [&](auto t) {
             constexpr int T = decltype(t)::value;
@@ -708,7 +710,7 @@ void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,
         k_list_place<T><<<nblk(n * T, 128), 128, 0, s>>>(a);
     }, 16);
     if (queue) {
-        if (use_tile(n))
+        if (walk_kind(a) != 1)
             k_list_tile_queue<<<152 * 4, 128, 0, s>>>(a);
         else
             k_list_fill_queue<16><<<152 * 4, 128, 0, s>>>(a);

@@ -49,6 +49,9 @@ struct ListArgs {
     // (a superset of N(i) for particles that move less than the skin
     // allows); 1: exactly N(i)
     float skin;
+    // walk: 1 per-particle team walk, 2 cell tiles with 4-lane teams, 3
+    // cell tiles with a lane per particle, anything else: by set size
+    int walk;
 };
 
 void launch_pack(cudaStream_t s, const PackArgs &a);

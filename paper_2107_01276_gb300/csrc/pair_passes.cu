@@ -598,17 +598,17 @@ __global__ void k_float_to_double(int n, const float *src, double *dst) {
 static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
 
 template <typename R>
-void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a) {
+void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a, int team) {
     if (a.n <= 0) return;
-    with_team(a.n, [&](auto t) {
+    with_team_or(team, a.n, [&](auto t) {
         constexpr int T = decltype(t)::value;
         k_pass_a<R, T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
     });
 }
 template <typename R>
-void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a) {
+void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a, int team) {
     if (a.n <= 0) return;
-    with_team(a.n, [&](auto t) {
+    with_team_or(team, a.n, [&](auto t) {
         constexpr int T = decltype(t)::value;
         k_pass_b<R, T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
     });
@@ -617,10 +617,10 @@ template <typename R>
 void launch_pec(cudaStream_t s, const PecArgs<R> &a) {
     if (a.n > 0) k_pec<R><<<nblk(a.n, 256), 256, 0, s>>>(a);
 }
-template void launch_pass_a<double>(cudaStream_t, const PassAArgs<double> &);
-template void launch_pass_a<float>(cudaStream_t, const PassAArgs<float> &);
-template void launch_pass_b<double>(cudaStream_t, const PassBArgs<double> &);
-template void launch_pass_b<float>(cudaStream_t, const PassBArgs<float> &);
+template void launch_pass_a<double>(cudaStream_t, const PassAArgs<double> &, int);
+template void launch_pass_a<float>(cudaStream_t, const PassAArgs<float> &, int);
+template void launch_pass_b<double>(cudaStream_t, const PassBArgs<double> &, int);
+template void launch_pass_b<float>(cudaStream_t, const PassBArgs<float> &, int);
 template void launch_pec<double>(cudaStream_t, const PecArgs<double> &);
 template void launch_pec<float>(cudaStream_t, const PecArgs<float> &);
 

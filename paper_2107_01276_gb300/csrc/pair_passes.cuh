@@ -88,13 +88,16 @@ struct ForceArgs {
     double *fw;
 };
 
-template <typename R> void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a);
+// team: lanes per particle (1, 4, 16 or 32), anything else: by set size.
+template <typename R> void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a,
+                                         int team = 0);
 template <typename R> void launch_forces(cudaStream_t s, const ForceArgs<R> &a);
 // Deterministic sum of the per-wall forces into total[4] and their copy in
 // load order (id: load index of each sorted wall) into out[4 id ..].
 void launch_forces_total(cudaStream_t s, int nw, const double *fw,
                          const int64_t *id, double *out, double *total);
-template <typename R> void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a);
+template <typename R> void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a,
+                                         int team = 0);
 template <typename R> void launch_pec(cudaStream_t s, const PecArgs<R> &a);
 void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,
                     const uint32_t *list, const int64_t *id, int64_t *out);

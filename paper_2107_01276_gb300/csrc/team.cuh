@@ -67,4 +67,17 @@ inline void with_team(int n, F &&f, int min_t = 1) {
     }
 }
 
+// f(std::integral_constant<int, T>()) with T = t when t is 1, 4, 16 or 32,
+// else team_size(n).
+template <class F>
+inline void with_team_or(int t, int n, F &&f) {
+    if (t != 1 && t != 4 && t != 16 && t != 32) t = team_size(n);
+    switch (t) {
+    case 32: f(std::integral_constant<int, 32>()); break;
+    case 16: f(std::integral_constant<int, 16>()); break;
+    case 4: f(std::integral_constant<int, 4>()); break;
+    default: f(std::integral_constant<int, 1>()); break;
+    }
+}
+
 }  // namespace sph

@@ -67,6 +67,16 @@ class Params(ctypes.Structure):
 _D = ctypes.POINTER(ctypes.c_double)
 
 
+class Tune(ctypes.Structure):
+    """sph_tune: launch configuration of a context (sph.h)."""
+    _fields_ = [("cell_scale", ctypes.c_double), ("walk", ctypes.c_int),
+                ("team_a", ctypes.c_int), ("team_b", ctypes.c_int),
+                ("ms_cell", ctypes.c_double * 3),
+                ("ms_walk", ctypes.c_double * 3),
+                ("ms_team_a", ctypes.c_double * 4),
+                ("ms_team_b", ctypes.c_double * 4)]
+
+
 class Particles(ctypes.Structure):
     _fields_ = [(k, _D) for k in ("x", "y", "u", "v", "p", "rho", "m", "h",
                                   "mmin", "mmax", "ds")] + [
@@ -128,6 +138,10 @@ def lib(build_if_missing: bool = True):
     L.sph_adapt.argtypes = [ctx, P(AdaptStats)]
     L.sph_background.restype = ctypes.c_int
     L.sph_background.argtypes = [ctx, ctypes.c_int, P(BgStats)]
+    L.sph_autotune.restype = ctypes.c_int
+    L.sph_autotune.argtypes = [ctx, P(Tune)]
+    L.sph_set_tuning.restype = ctypes.c_int
+    L.sph_set_tuning.argtypes = [ctx, P(Tune)]
     L.sph_forces.restype = ctypes.c_int
     L.sph_forces.argtypes = [ctx, ctypes.c_void_p, _D]
     L.sph_read.restype = ctypes.c_int
@@ -149,6 +163,13 @@ def lib(build_if_missing: bool = True):
         [ctypes.c_void_p] * 6
     _lib = L
     return L
+
+
+def _tune_dict(t: Tune) -> dict:
+    out = {k: getattr(t, k) for k in ("cell_scale", "walk", "team_a", "team_b")}
+    for k in ("ms_cell", "ms_walk", "ms_team_a", "ms_team_b"):
+        out[k] = list(getattr(t, k))
+    return out
 
 
 def coefficients(f: dict, rho0: float, U: float, L: float) -> dict:
@@ -266,6 +287,20 @@ class Simulation:
         self._check(self._L.sph_background(self._ctx, int(iterations),
                                            ctypes.byref(z)))
         return {k: getattr(z, k) for k, _ in BgStats._fields_}
+
+    def autotune(self) -> dict:
+        """sph_autotune: time the launch configurations on the loaded set
+        and keep the fastest; returns the choices and the times."""
+        t = Tune()
+        self._check(self._L.sph_autotune(self._ctx, ctypes.byref(t)))
+        return _tune_dict(t)
+
+    def set_tuning(self, cell_scale: float = 1.0, walk: int = 0,
+                   team_a: int = 0, team_b: int = 0):
+        """sph_set_tuning (0: the size rule)."""
+        t = Tune()
+        t.cell_scale, t.walk, t.team_a, t.team_b = cell_scale, walk, team_a, team_b
+        self._check(self._L.sph_set_tuning(self._ctx, ctypes.byref(t)))
 
     def forces(self, per_wall: bool = False) -> dict:
         """sph_forces: force on the wall particles at the current state,

@@ -1,0 +1,88 @@
+"""The launch-configuration autotuner (sph_autotune, sph_set_tuning): every
+configuration gives the same neighbour sets and the same right-hand side
+to rounding, so the tuner may pick any; it returns valid choices with the
+times it measured, and a configuration set by hand is used as given."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_01276_gb300 import sph
+from paper_2107_01276_gb300 import workloads as wl
+from tests.helpers import FP64_TOL, MIXED_TOL, by_id, cuda_ok, norm, \
+    neighbour_sets_by_id, stream_handle
+
+pytestmark = pytest.mark.gpu
+RHS = ("rho", "beta", "pavg", "drx", "dry", "dpdt", "dudt", "dvdt")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not cuda_ok():
+        pytest.skip("no CUDA device")
+
+
+def _sim(d, precision):
+    n = len(d["particles"]["x"])
+    P = sph.make_params(d["params"], precision=precision, capacity=n)
+    s = sph.Simulation(P, stream_handle())
+    s.load(d["particles"])
+    return s
+
+
+@pytest.mark.parametrize("precision,tol", [(sph.SPH_FP64, FP64_TOL),
+                                           (sph.SPH_MIXED, MIXED_TOL)])
+def test_every_configuration_matches_the_oracle(precision, tol):
+    """Each walk kernel, cell size and team size on a graded lattice: the
+    neighbour sets equal the oracle's and the rates are within the parity
+    tolerance."""
+    d = wl.perturbed(nx=160, ny=120, h_ratio=4.0, seed=31)
+    pt = d["particles"]
+    P = oracle.params(**d["params"])
+    ref = oracle.rhs(P, oracle.dt(P, pt["h"]), oracle.make_state(pt))
+    ro, rn = oracle.neighbors(P, pt["x"], pt["y"], pt["h"])
+    configs = [dict(walk=1, team_a=32, team_b=16), dict(walk=2, team_a=4, team_b=4),
+               dict(walk=3, team_a=1, team_b=1, cell_scale=1.5),
+               dict(walk=2, team_a=16, team_b=32, cell_scale=1.25)]
+    for cfg in configs:
+        s = _sim(d, precision)
+        s.set_tuning(**cfg)
+        s.rhs()
+        got = by_id(s, list(RHS) + ["nnb"])
+        sets = neighbour_sets_by_id(s)
+        s.close()
+        assert np.array_equal(got["nnb"], ref["nnb"]), cfg
+        for i in range(0, len(pt["x"]), 97):
+            assert np.array_equal(sets[i], rn[ro[i]:ro[i + 1]]), (cfg, i)
+        for f in RHS:
+            assert norm(got[f], ref[f], ref["s_" + f]) <= tol, (cfg, f)
+
+
+def test_autotune_choices_and_results():
+    d = wl.perturbed(nx=200, ny=160, h_ratio=4.0, seed=32)
+    s = _sim(d, sph.SPH_MIXED)
+    s.rhs()
+    before = by_id(s, list(RHS))
+    t = s.autotune()
+    assert t["cell_scale"] in (1.0, 1.25, 1.5)
+    assert t["walk"] in (1, 2, 3)
+    assert t["team_a"] in (1, 4, 16, 32) and t["team_b"] in (1, 4, 16, 32)
+    assert all(v > 0 for v in t["ms_cell"] + t["ms_walk"] + t["ms_team_a"]
+               + t["ms_team_b"])
+    after = by_id(s, list(RHS))          # the rates autotune leaves
+    s.rhs()
+    again = by_id(s, list(RHS))
+    s.step(3)
+    s.close()
+    for f in RHS:
+        sc = np.abs(before[f]).max() + 1e-300
+        assert np.abs(after[f] - before[f]).max() <= 1e-4 * sc, f
+        assert np.array_equal(after[f], again[f]), f
+
+
+def test_set_tuning_rejects_bad_values():
+    d = wl.taylor_green(nx=20)
+    s = _sim(d, sph.SPH_FP64)
+    for bad in (dict(walk=4), dict(team_a=8), dict(team_b=2), dict(cell_scale=9.0)):
+        with pytest.raises(sph.SphError):
+            s.set_tuning(**bad)
+    s.close()
