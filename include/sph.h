@@ -146,6 +146,7 @@ typedef struct {
     long long launches;   /* kernels launched by this context so far */
     long long next_id;    /* id the next split child will receive */
     long long n_region;   /* refinement-region markers */
+    long long graph_steps; /* sph_step steps run as replayed CUDA graphs */
 } sph_info;
 
 /* Counts and masses of one sph_adapt call. */
@@ -307,6 +308,11 @@ typedef struct {
                             < 60k: 2, else 3) */
     int team_a, team_b;  /* lanes per particle in pass A / pass B: 1, 4,
                             16 or 32; 0: by set size */
+    int no_graphs;       /* 0 (default): sph_step replays each step as a
+                            captured CUDA graph when it can (a stream other
+                            than the legacy or per-thread default stream,
+                            timing off, list sizes settled); results are
+                            the same bit for bit.  1: launch by launch */
     /* filled by sph_autotune: mean device ms per launch of each candidate
      * (neighbour build + both passes for cell_scale 1, 1.25, 1.5; the walk
      * for walk 1..3; pass A / pass B for teams 1, 4, 16, 32) */

@@ -170,6 +170,24 @@ struct sph_ctx {
     // launch configuration (sph_set_tuning / sph_autotune)
     double c0_scale = 1.0;
     int walk_choice = 0, team_a = 0, team_b = 0;
+    int use_graphs = 1;
+    long long cfg_version = 0;   // bumped when the loaded sets or the launch
+                                 // configuration change
+    int graph_next_drop = 0;
+    long long graph_launches = 0;
+    long long graph_cfg_seen = -1;   // capture only after two steps with
+    int steps_same_cfg = 0;          // no configuration change
+    // sph_step's step captured as CUDA graphs, one per buffer assignment the
+    // step starts from (a step swaps the state buffers, so two alternate)
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<uintptr_t> key;              // what the launches depend on
+        double *f_after[NF], *falt_after[NF];    // buffers after the step
+        int64_t *id_after = nullptr, *id_alt_after = nullptr;
+        uint32_t tmask = 0;
+        float skin = 1.0f;
+        int launches = 0;
+    } graphs[2];
     Timer tm;
 };
 
@@ -441,8 +459,10 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true,
         queue = max_own > c->stage_w;
         if (max_own > c->stage_w && c->stage_w < 256)
             c->stage_want = std::min<uint32_t>(256, (max_own + max_own / 4 + 15) & ~15u);
-        if ((size_t)total > c->list_cap) {
-            size_t want = (size_t)total + total / 2 + 1024;
+        // twice the entries found: the next builds skip this read-back
+        // (and sph_step can replay its captured graph)
+        if ((size_t)total * 2 > c->list_cap) {
+            size_t want = 2 * (size_t)total + 1024;
             if (want > 0xffffffffull) want = 0xffffffffull;
             if ((size_t)total > want)
                 return fail(c, SPH_ECAPACITY, "neighbour lists exceed 2^32 entries");
@@ -643,6 +663,8 @@ static void compute_dt(sph_ctx *c, double *tacc, int nsteps) {
 }
 
 static void free_ctx(sph_ctx *c) {
+    for (auto &g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (int k = 0; k < NF; ++k) {
         cudaFree(c->f[k]);
         cudaFree(c->falt[k]);
@@ -1349,6 +1371,177 @@ static void forces_launch(sph_ctx *c) {
     launch_forces<R>(c->s, a);
 }
 
+// One PEC step (section 2.4).  Mixed path: one neighbour build per step,
+// with a skin that holds N(i) through the predictor's moves (checked on the
+// device; a particle outrunning it is reported at the next
+// synchronisation).  FP64 path: a fresh build before each evaluation (wider
+// lists would cost more FP64 pair work than the build they save).  exact:
+// the first build may read the list size back.
+static sph_status pec_step(sph_ctx *c, bool exact) {
+    const float step_skin = is_mixed(c) ? 1.1f : 1.0f;
+    compute_dt(c, c->d_t, 1);
+    sph_status st = rebuild(c, false, exact, step_skin);
+    if (st != SPH_OK) return st;
+    run_passes(c);
+    run_pec(c, 0.5);
+    if (step_skin > 1.0f) {
+        pack(c, false);   // anchor records and mirrors at the predicted state
+    } else {
+        st = rebuild(c, true, false);
+        if (st != SPH_OK) return st;
+    }
+    run_passes(c);
+    run_pec(c, 1.0);
+    store_rho(c);
+    c->grid_valid = false;   // positions moved since the last rebuild
+    c->rhs_valid = true;     // rates of the n+1/2 evaluation, current order
+    c->steps += 1;
+    return SPH_OK;
+}
+
+// Everything a step's launches depend on besides the device data: the
+// buffers (the step swaps them), sizes, list storage, the launch
+// configuration and the version of the loaded sets.
+static std::vector<uintptr_t> graph_key(const sph_ctx *c) {
+    std::vector<uintptr_t> k;
+    k.push_back((uintptr_t)c->n);
+    for (int f = 0; f < NF; ++f) {
+        k.push_back((uintptr_t)c->f[f]);
+        k.push_back((uintptr_t)c->falt[f]);
+    }
+    k.push_back((uintptr_t)c->id);
+    k.push_back((uintptr_t)c->id_alt);
+    k.push_back((uintptr_t)c->list);
+    k.push_back((uintptr_t)c->list_cap);
+    k.push_back((uintptr_t)c->stage);
+    k.push_back((uintptr_t)c->stage_w);
+    k.push_back((uintptr_t)c->cfg_version);
+    k.push_back((uintptr_t)c->anchor_version);
+    k.push_back((uintptr_t)c->s);
+    return k;
+}
+
+static void drop_graph(sph_ctx::StepGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.key.clear();
+}
+
+// The step as a CUDA graph: captured the first time a buffer assignment
+// and configuration comes up, replayed after that (the same kernels with
+// the same arguments: results equal the launch-by-launch step bit for
+// bit).  Used only when no host decision can arise inside the step: list
+// sizes settled (no read-back), staging rows wide enough, timing off, and
+// a stream that can be captured.  Returns false (nothing done) when the
+// step must run launch by launch; *st reports an error.
+static bool graph_step(sph_ctx *c, sph_status *st) {
+    *st = SPH_OK;
+    const uintptr_t sh = (uintptr_t)c->s;
+    if (!c->use_graphs || c->timing || sh <= 2) return false;
+    // a configuration that changes every step (adaptation between steps)
+    // would be captured and thrown away each time: wait for two steps
+    if (c->graph_cfg_seen != c->cfg_version) {
+        c->graph_cfg_seen = c->cfg_version;
+        c->steps_same_cfg = 0;
+    }
+    if (++c->steps_same_cfg <= 2) return false;
+    if (c->stage_want > c->stage_w) return false;
+    {   // the build's list size must be known with headroom (no read-back)
+        const bool sk = is_mixed(c);
+        const uint32_t lt = sk ? c->last_total_skin : c->last_total;
+        const int ltn = sk ? c->last_total_skin_n : c->last_total_n;
+        const int n = c->n;
+        if (!(lt > 0 && (size_t)lt * 2 <= c->list_cap &&
+              (long long)n * 10 <= (long long)ltn * 11 &&
+              (long long)n * 10 >= (long long)ltn * 9))
+            return false;
+        if (!is_mixed(c) && !(c->last_total_n > 0)) return false;
+    }
+    ensure_set_pk(c, &c->wall);
+    const std::vector<uintptr_t> key = graph_key(c);
+    sph_ctx::StepGraph *g = nullptr;
+    for (auto &gg : c->graphs)
+        if (gg.exec && gg.key == key) g = &gg;
+    if (!g) {
+        // a free slot, else the one of another configuration
+        sph_ctx::StepGraph *slot = &c->graphs[0];
+        for (auto &gg : c->graphs)
+            if (!gg.exec) { slot = &gg; break; }
+        if (slot->exec) {
+            // both slots hold graphs: keep the one the next step will want
+            // (the assignment after the step, unknown yet): drop the older
+            slot = &c->graphs[c->graph_next_drop];
+            c->graph_next_drop ^= 1;
+        }
+        drop_graph(*slot);
+        // capture one step; the host side runs as usual, the kernels only
+        // run when the graph is launched below
+        double *f0[NF], *fa0[NF];
+        memcpy(f0, c->f, sizeof(f0));
+        memcpy(fa0, c->falt, sizeof(fa0));
+        int64_t *id0 = c->id, *ida0 = c->id_alt;
+        const uint32_t tmask0 = c->tmask;
+        const float skin0 = c->skin;
+        const long long steps0 = c->steps;
+        const bool gv0 = c->grid_valid, rv0 = c->rhs_valid;
+        const int l0 = c->launches;
+        cudaGraph_t gr = nullptr;
+        if (cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->use_graphs = 0;
+            return false;
+        }
+        sph_status s2 = pec_step(c, false);
+        cudaError_t e = cudaStreamEndCapture(c->s, &gr);
+        cudaGraphExec_t ex = nullptr;
+        if (s2 == SPH_OK && e == cudaSuccess && gr)
+            e = cudaGraphInstantiate(&ex, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        if (s2 != SPH_OK || e != cudaSuccess || !ex) {
+            // undo the host side and run the step launch by launch
+            cudaGetLastError();
+            if (ex) cudaGraphExecDestroy(ex);
+            memcpy(c->f, f0, sizeof(f0));
+            memcpy(c->falt, fa0, sizeof(fa0));
+            c->id = id0;
+            c->id_alt = ida0;
+            c->tmask = tmask0;
+            c->skin = skin0;
+            c->steps = steps0;
+            c->grid_valid = gv0;
+            c->rhs_valid = rv0;
+            c->launches = l0;
+            c->use_graphs = 0;
+            c->err.clear();
+            return false;
+        }
+        slot->exec = ex;
+        slot->key = key;
+        memcpy(slot->f_after, c->f, sizeof(c->f));
+        memcpy(slot->falt_after, c->falt, sizeof(c->falt));
+        slot->id_after = c->id;
+        slot->id_alt_after = c->id_alt;
+        slot->tmask = c->tmask;
+        slot->skin = c->skin;
+        slot->launches = c->launches - l0;
+        g = slot;
+    } else {
+        memcpy(c->f, g->f_after, sizeof(c->f));
+        memcpy(c->falt, g->falt_after, sizeof(c->falt));
+        c->id = g->id_after;
+        c->id_alt = g->id_alt_after;
+        c->tmask = g->tmask;
+        c->skin = g->skin;
+        c->launches += g->launches;
+        c->grid_valid = false;
+        c->rhs_valid = true;
+        c->steps += 1;
+    }
+    if (cudaGraphLaunch(g->exec, c->s) != cudaSuccess) *st = cuda_check(c, "sph_step graph");
+    c->graph_launches += 1;
+    return true;
+}
+
 extern "C" {
 
 void sph_default_params(sph_params *p) {
@@ -1411,6 +1604,7 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
 sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
                               const sph_particles *src) {
     if (!c) return SPH_EINVAL;
+    c->cfg_version += 1;
     c->err.clear();
     if (n < 0 || (n > 0 && !src)) return fail(c, SPH_EINVAL, "sph_load_particles: bad n or src");
     if (kind == SPH_BACKGROUND) return load_background(c, n, src);
@@ -1547,30 +1741,14 @@ sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
     c->err.clear();
     if (nsteps < 0) return fail(c, SPH_EINVAL, "sph_step: nsteps < 0");
     if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_step: no fluid particles loaded");
-    // Mixed path: one neighbour build per step, with a skin that holds N(i)
-    // through the predictor's moves (checked on the device; a particle
-    // outrunning it is reported as an error at the next synchronisation).
-    // FP64 path: a fresh build before each evaluation (wider lists would
-    // cost more FP64 pair work than the build they save).
-    const float step_skin = is_mixed(c) ? 1.1f : 1.0f;
     for (int s = 0; s < nsteps; ++s) {
-        compute_dt(c, c->d_t, 1);
-        sph_status st = rebuild(c, false, s == 0, step_skin);
-        if (st != SPH_OK) return st;
-        run_passes(c);
-        run_pec(c, 0.5);
-        if (step_skin > 1.0f) {
-            pack(c, false);   // anchor records and mirrors at the predicted state
-        } else {
-            st = rebuild(c, true, false);
+        sph_status st = SPH_OK;
+        if (!graph_step(c, &st)) {
             if (st != SPH_OK) return st;
+            if ((st = pec_step(c, s == 0)) != SPH_OK) return st;
+        } else if (st != SPH_OK) {
+            return st;
         }
-        run_passes(c);
-        run_pec(c, 1.0);
-        store_rho(c);
-        c->grid_valid = false;   // positions moved since the last rebuild
-        c->rhs_valid = true;     // rates of the n+1/2 evaluation, current order
-        c->steps += 1;
     }
     sph_status st = cuda_check(c, "sph_step");
     if (st != SPH_OK) return st;
@@ -1589,6 +1767,7 @@ sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
 
 sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     if (!c) return SPH_EINVAL;
+    c->cfg_version += 1;
     c->err.clear();
     if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_adapt: no fluid particles loaded");
     if (c->prm.n_bg > 0 && c->bg.n > 0 && ++c->adapt_calls % c->prm.n_bg == 0) {
@@ -1771,6 +1950,7 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
 
 sph_status sph_background(sph_ctx *c, int iterations, sph_bg_stats *out) {
     if (!c) return SPH_EINVAL;
+    c->cfg_version += 1;
     c->err.clear();
     if (c->bg.n <= 0) return fail(c, SPH_ESTATE, "sph_background: no background particles loaded");
     const sph_params &P = c->prm;
@@ -1959,6 +2139,7 @@ sph_status sph_get_info(sph_ctx *c, sph_info *out) {
     out->n_bg = c->bg.n;
     out->n_wall = c->wall.n;
     out->n_region = c->region.n;
+    out->graph_steps = c->graph_launches;
     double t = 0, dt = 0;
     cudaMemcpyAsync(&t, c->d_t, sizeof(double), cudaMemcpyDeviceToHost, c->s);
     if (c->have_dt) cudaMemcpyAsync(&dt, c->d_dt, sizeof(double), cudaMemcpyDeviceToHost, c->s);
@@ -1975,6 +2156,7 @@ sph_status sph_get_info(sph_ctx *c, sph_info *out) {
 
 sph_status sph_set_tuning(sph_ctx *c, const sph_tune *in) {
     if (!c) return SPH_EINVAL;
+    c->cfg_version += 1;
     c->err.clear();
     if (!in) return fail(c, SPH_EINVAL, "sph_set_tuning: in is NULL");
     auto team_ok = [](int t) { return t == 0 || t == 1 || t == 4 || t == 16 || t == 32; };
@@ -1985,6 +2167,7 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tune *in) {
     c->walk_choice = in->walk;
     c->team_a = in->team_a;
     c->team_b = in->team_b;
+    c->use_graphs = in->no_graphs ? 0 : 1;
     if (scale != c->c0_scale) {
         c->c0_scale = scale;
         if (c->n > 0) {
@@ -2005,6 +2188,7 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tune *in) {
 
 sph_status sph_autotune(sph_ctx *c, sph_tune *out) {
     if (!c) return SPH_EINVAL;
+    c->cfg_version += 1;
     c->err.clear();
     if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_autotune: no fluid particles loaded");
     const bool timing_was = c->timing;
@@ -2014,6 +2198,7 @@ sph_status sph_autotune(sph_ctx *c, sph_tune *out) {
     cur.walk = c->walk_choice;
     cur.team_a = c->team_a;
     cur.team_b = c->team_b;
+    cur.no_graphs = c->use_graphs ? 0 : 1;
     sph_tune res = cur;
     // mean ms per launch of families 0 (pass B), 1 (pass A), 2 (build), 5
     // (walk) over `reps` builds + right-hand sides, after one untimed
