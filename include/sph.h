@@ -309,10 +309,16 @@ typedef struct {
     int team_a, team_b;  /* lanes per particle in pass A / pass B: 1, 4,
                             16 or 32; 0: by set size */
     int no_graphs;       /* 0 (default): sph_step replays each step as a
-                            captured CUDA graph when it can (a stream other
-                            than the legacy or per-thread default stream,
-                            timing off, list sizes settled); results are
-                            the same bit for bit.  1: launch by launch */
+                            captured CUDA graph when it can (the only live
+                            context of the process, a stream other than the
+                            legacy or per-thread default stream, timing
+                            off, list sizes settled, two steps since the
+                            particle set or configuration last changed);
+                            results are the same bit for bit.  With several
+                            contexts (the serving loop) capturing would wait
+                            on the others' allocations and synchronisations,
+                            so steps run launch by launch.  1: always launch
+                            by launch */
     /* filled by sph_autotune: mean device ms per launch of each candidate
      * (neighbour build + both passes for cell_scale 1, 1.25, 1.5; the walk
      * for walk 1..3; pass A / pass B for teams 1, 4, 16, 32) */

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -21,6 +22,7 @@ using namespace sph;
 namespace {
 
 thread_local std::string g_create_error;
+static std::atomic<int> g_live_ctx{0};   // contexts made by sph_create, not yet destroyed
 
 // Timed kernel families: 0 pass B, 1 pass A, 2 rebuild, 3 PEC stages,
 // 4 adaptation, 5 the neighbour walk of the rebuild (k_list_gather).
@@ -1438,6 +1440,10 @@ static bool graph_step(sph_ctx *c, sph_status *st) {
     *st = SPH_OK;
     const uintptr_t sh = (uintptr_t)c->s;
     if (!c->use_graphs || c->timing || sh <= 2) return false;
+    // only while this is the one context of the process: capturing and
+    // instantiating a graph wait on other threads' allocations and
+    // synchronisations (up to seconds under the serving loop's load)
+    if (g_live_ctx.load() > 1) return false;
     // a configuration that changes every step (adaptation between steps)
     // would be captured and thrown away each time: wait for two steps
     if (c->graph_cfg_seen != c->cfg_version) {
@@ -1598,6 +1604,7 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
     std::string why2;
     sph_status st = new_ctx(p, (cudaStream_t)stream, false, out, &why2);
     if (st != SPH_OK) g_create_error = "sph_create: " + why2;
+    else g_live_ctx.fetch_add(1);
     return st;
 }
 
@@ -2312,6 +2319,7 @@ sph_status sph_destroy(sph_ctx *c) {
     cudaStreamSynchronize(c->s);
     free_ctx(c);
     delete c;
+    g_live_ctx.fetch_sub(1);
     return SPH_OK;
 }
 

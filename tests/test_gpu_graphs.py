@@ -3,6 +3,8 @@ library captures a step once per buffer assignment and replays it; the
 states it reaches equal those of the launch-by-launch step bit for bit,
 for both precisions, with walls, and across a change of the particle set
 (a new capture)."""
+import gc
+
 import numpy as np
 import pytest
 import torch
@@ -19,6 +21,12 @@ FIELDS = ["x", "y", "u", "v", "p", "rho", "h", "m"]
 def _need_gpu():
     if not cuda_ok():
         pytest.skip("no CUDA device")
+
+
+@pytest.fixture(autouse=True)
+def _no_other_contexts():
+    # graphs are used only while a context is the only live one
+    gc.collect()
 
 
 def _run(d, precision, graphs, steps, stream, cap=None):
