@@ -90,6 +90,15 @@ WORKLOADS = {
     # graded over 1:250 by C_r per column, u,v ~ N(0, 0.1),
     # rho = 1 + U(-0.01, 0.01); PEC steps, no adaptation
     "graded-1M": dict(kind="graded", n_target=1 << 20, ratio=250.0),
+    # solution-adaptive cylinder at Re 1000, spacing D/1000 at the wall to
+    # D/4 (1:250), vorticity marking (k = 0.05) with a background iteration
+    # every 100 adaptations; fluid initialised from the graded ring
+    # background and settled by 6 sph_adapt calls before timing
+    "cylinder-re1000": dict(kind="cylinder", Re=1000.0,
+                            ds_min_over_D=1 / 1000, ds_max_over_D=1 / 4,
+                            background="rings", fluid="rings", vort_k=0.05,
+                            n_bg=100, refine_calls=6, oracle_refine=0,
+                            cpu_steps=1, capacity=2_000_000),
     # a stream of independent adaptive simulations (half
     # cylinders at Re log-uniform in [20, 2000], half Taylor-Green vortices
     # at Re in [50, 500]), Poisson arrivals at 20/s, served concurrently
@@ -102,15 +111,32 @@ DEFAULT_WORKLOAD = "cylinder-re40"
 def make_workload(name):
     w = WORKLOADS[name]
     if w["kind"] == "cylinder":
-        d = wl.cylinder(Re=w["Re"])
+        dmin = w.get("ds_min_over_D", 1 / 50)
+        dmax = w.get("ds_max_over_D", 0.5)
+        d = wl.cylinder(Re=w["Re"], ds_min_over_D=dmin, ds_max_over_D=dmax,
+                        background=w.get("background", "construct"),
+                        fluid=w.get("fluid", "lattice"))
+        d["params"] = dict(d["params"], vort_k=w.get("vort_k", 0.0),
+                           n_bg=w.get("n_bg", 0))
+        if w.get("background", "construct") == "construct":
+            bgdesc = ("background built by sph_background (%d iterations) "
+                      "from a D/%g lattice"
+                      % (3 * math.ceil(math.log(dmax / dmin) / math.log(1.08)),
+                         1 / dmax))
+        else:
+            bgdesc = "C_r-graded ring background"
+        fdesc = ("coarse fluid lattice" if w.get("fluid", "lattice") == "lattice"
+                 else "fluid initialised from the ring background")
+        vdesc = (", vorticity adaptivity k=%g with a background iteration "
+                 "every %d adaptations" % (w["vort_k"], w["n_bg"])
+                 if w.get("vort_k", 0) > 0 else "")
         desc = ("flow past a cylinder, Re %g, D=2, rho0=1000, c_s=10, "
-                "h/dx=1.2, C_r=1.08, spacing D/50 at the wall to D/2 (1:25), "
-                "25D x 15D periodic box, impulsive start; background built "
-                "by sph_background (126 iterations) from a D/2 lattice, "
-                "coarse fluid lattice refined by %d sph_adapt calls before "
-                "timing; a step is sph_adapt (split/merge/shift/h) + one "
-                "PEC step"
-                % (w["Re"], w["refine_calls"]))
+                "h/dx=1.2, C_r=1.08, spacing D/%g at the wall to D/%g "
+                "(1:%g), 25D x 15D periodic box, impulsive start%s; %s, "
+                "%s refined by %d sph_adapt calls before timing; a step is "
+                "sph_adapt (split/merge/shift/h) + one PEC step"
+                % (w["Re"], 1 / dmin, 1 / dmax, round(dmax / dmin), vdesc,
+                   bgdesc, fdesc, w["refine_calls"]))
         return d, desc
     if w["kind"] == "graded":
         d = wl.graded_strip(n_target=w["n_target"], ratio=w["ratio"])
@@ -230,7 +256,7 @@ def oracle_steps(d, state, steps, adaptive):
     return ps, el, oracle.num_threads()
 
 
-def reference_state(d, kind):
+def reference_state(d, kind, w=None):
     """The state the oracle starts from: for the cylinder, the coarse set
     refined by the oracle's own adaptation (as the GPU set-up does) against
     the C_r-graded ring background, standing in for the constructed one
@@ -247,7 +273,9 @@ def reference_state(d, kind):
     oracle.set_walls(d["walls"])
     nid = None
     try:
-        for _ in range(WORKLOADS["cylinder-re40"]["refine_calls"]):
+        refine = (w or {}).get("oracle_refine",
+                               (w or WORKLOADS["cylinder-re40"])["refine_calls"])
+        for _ in range(refine):
             _, _, nid = oracle.adapt(P, st, bg=d["background_rings"],
                                      next_id=nid)
     finally:
@@ -255,10 +283,10 @@ def reference_state(d, kind):
     n = st["n"]
     state = {k: st[k][:n].copy() for k in oracle.STATE_FIELDS}
     state["id"] = st["id"][:n].copy()
-    return d, state, ("the whole workload (%d particles after the oracle's "
-                      "own refinement; ring background of %d particles in "
-                      "place of the constructed one)"
-                      % (n, len(d["background_rings"]["x"])))
+    how = ("after %d adaptations of the oracle's own" % refine if refine
+           else "the generator's state, before any adaptation")
+    return d, state, ("the whole workload (%d particles, %s; ring background "
+                      "of %d particles)" % (n, how, len(d["background_rings"]["x"])))
 
 
 def reference_arm(args):
@@ -272,7 +300,7 @@ def reference_arm(args):
         return 0
     d, desc = make_workload(args.workload)
     kind = WORKLOADS[args.workload]["kind"]
-    dd, state, sample = reference_state(d, kind)
+    dd, state, sample = reference_state(d, kind, WORKLOADS[args.workload])
     adaptive = kind == "cylinder"
     oracle_steps(dd, state, max(args.warmup, 0) and 1, adaptive)
     ps, el, cores = oracle_steps(dd, state, args.steps, adaptive)
@@ -394,7 +422,7 @@ def main():
     tuned = {}
 
     def new_sim(precision):
-        cap = 400000 if adaptive else int(len(pt["x"]) * 1.1) + 16
+        cap = wdef.get("capacity", 400000) if adaptive else int(len(pt["x"]) * 1.1) + 16
         P = sph.make_params(d["params"], precision=precision, capacity=cap)
         s = sph.Simulation(P, stream)
         s.load(pt)
@@ -519,7 +547,7 @@ def main():
     for k in fields_in:
         setattr(src, k, ctypes.cast(pinned[k].data_ptr(), sph._D))
     src.id = ctypes.cast(pid.data_ptr(), ctypes.POINTER(ctypes.c_int64))
-    cap_out = (400000 if adaptive else 0) + 2 * n_e
+    cap_out = (wdef.get("capacity", 400000) if adaptive else 0) + 2 * n_e
     outs = {k: torch.empty(cap_out, dtype=torch.float64).pin_memory()
             for k in ("x", "y", "u", "v", "p")}
     out_np = {k: v.numpy() for k, v in outs.items()}
@@ -600,8 +628,8 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        dd, st0, sample = reference_state(d, kind)
-        steps_cpu = 2
+        dd, st0, sample = reference_state(d, kind, wdef)
+        steps_cpu = wdef.get("cpu_steps", 2)
         ps, el, cores = oracle_steps(dd, st0, steps_cpu, adaptive)
         cpu = {"value": ps / el, "unit": "particle-steps/s", "cores": cores,
                "kind": "oracle",

@@ -173,6 +173,8 @@ def lib():
             L.orc_set_walls.argtypes = [ctypes.c_int] + [_D] * 6
             L.orc_wall_bc.restype = None
             L.orc_wall_bc.argtypes = [_P, ctypes.POINTER(_State), _D, _D, _D]
+            L.orc_wall_bc_store.restype = None
+            L.orc_wall_bc_store.argtypes = [_P, ctypes.POINTER(_State)]
             L.orc_forces.restype = None
             L.orc_forces.argtypes = [_P, ctypes.POINTER(_State), _D, ctypes.c_void_p]
             L.orc_record_wall_terms.restype = None
@@ -507,6 +509,13 @@ def set_walls(walls):
     arrs.append(_f64(walls.get("u", np.zeros(n))))
     arrs.append(_f64(walls.get("v", np.zeros(n))))
     lib().orc_set_walls(n, *[_d(a) for a in arrs])
+
+
+def wall_bc_store(P, st):
+    """Evaluate the wall condition at the state and keep it for the
+    registered walls (before calling pass_a / pass_b with walls)."""
+    s = _cstate(st)
+    lib().orc_wall_bc_store(ctypes.byref(P), ctypes.byref(s))
 
 
 def wall_bc(P, st, nw):

@@ -435,6 +435,10 @@ static void wall_bc_update(const orc_params *P, const orc_state *s) {
         orc_wall_bc(P, s, &WP(0), &WGX(0), &WGY(0));
 }
 
+void orc_wall_bc_store(const orc_params *P, const orc_state *s) {
+    wall_bc_update(P, s);
+}
+
 /* Wall neighbours of fluid particle i, ascending wall index. */
 static int wall_nbrs(const orc_params *P, double xi, double yi, double hi,
                      int *out, int cap) {

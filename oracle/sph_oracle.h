@@ -130,6 +130,9 @@ void orc_forces(const orc_params *P, const orc_state *s, double *out,
  * pass B writes each particle's wall terms of its momentum rate there
  * (pressure x, y, viscous x, y); NULL stops it. */
 void orc_record_wall_terms(double *acc);
+/* The wall condition at the state, kept for the registered walls (what
+ * orc_rhs does first; for callers of orc_pass_a / orc_pass_b). */
+void orc_wall_bc_store(const orc_params *P, const orc_state *s);
 void orc_wall_bc(const orc_params *P, const orc_state *s, double *pw,
                  double *ugx, double *ugy);
 

@@ -316,7 +316,7 @@ def cylinder(D: float = 2.0, Re: float = 40.0, ds_min_over_D: float = 1 / 50,
              rho0: float = 1000.0, cs: float = 10.0, U: float = 1.0,
              hdx: float = 1.2, Cr: float = 1.08, jitter: float = 1e-3,
              wall_layers: int = 4, seed: int = 2,
-             background: str = "construct"):
+             background: str = "construct", fluid: str = "lattice"):
     """Flow past a circular cylinder (section 4.4, Table fpc-params: D = 2,
     rho0 = 1000, c_s = 10, h/dx = 1.2, C_r = 1.08), periodic box of
     25D x 15D, impulsive start u = U.
@@ -331,8 +331,14 @@ def cylinder(D: float = 2.0, Re: float = 40.0, ds_min_over_D: float = 1 / 50,
       ds_min at the wall to ds_max, then a ds_max lattice -- the graded
       layers the construction aims at, given directly;
     - background_rings: the ring background in either case;
-    - fluid: a ds_max lattice outside the cylinder with 1e-3 ds_max
-      position jitter; sph_adapt refines it to the background's sizes.
+    - fluid, `fluid="lattice"` (default): a ds_max lattice outside the
+      cylinder with 1e-3 ds_max position jitter; sph_adapt refines it to
+      the background's sizes.  `fluid="rings"`: one fluid particle at each
+      ring-background particle (m = rho0 ds^2, h = hdx ds, 1e-3 ds jitter),
+      the fluid initialised from the background particles (section 3.4,
+      step 2; for large spacing ratios, where refining a ds_max lattice by
+      splitting piles 7^k children into clusters that shifting cannot
+      spread).
     """
     rng = np.random.default_rng(seed)
     R = 0.5 * D
@@ -387,6 +393,16 @@ def cylinder(D: float = 2.0, Re: float = 40.0, ds_min_over_D: float = 1 / 50,
     fl = dict(x=fx, y=fy, u=np.full(n, U), v=np.zeros(n), p=np.zeros(n),
               rho=np.full(n, rho0), m=np.full(n, rho0 * ds_max * ds_max),
               h=np.full(n, hdx * ds_max))
+    if fluid == "rings":
+        keep = np.hypot(rings["x"] - cx, rings["y"] - cy) >= R
+        ds = rings["ds"][keep]
+        n = int(keep.sum())
+        fx = (rings["x"][keep] + jitter * ds * rng.uniform(-1, 1, n)) % Lx
+        fy = (rings["y"][keep] + jitter * ds * rng.uniform(-1, 1, n)) % Ly
+        fl = dict(x=fx, y=fy, u=np.full(n, U), v=np.zeros(n), p=np.zeros(n),
+                  rho=np.full(n, rho0), m=rho0 * ds * ds, h=hdx * ds)
+    elif fluid != "lattice":
+        raise ValueError("fluid must be 'lattice' or 'rings'")
     params = _base_params(lo=(0.0, 0.0), hi=(Lx, Ly), periodic=(1, 1),
                           rho0=rho0, cs=cs, nu=U * D / Re, U_ref=U, hdx=hdx,
                           ds_min=ds_min, ds_max=ds_max, Cr=Cr)
