@@ -687,7 +687,7 @@ def main():
         "neighbours_mean": float(nnb.mean()),
         "mixed_vs_fp64": err_rep,
         "forces": forces,
-        "tuning": ({k: tuned[k] for k in ("cell_scale", "walk", "team_a", "team_b")}
+        "tuning": ({k: tuned[k] for k in ("cell_scale", "walk", "team_a", "team_b", "walls")}
                    if tuned else None),
     }
     print(json.dumps(line))

@@ -308,6 +308,11 @@ typedef struct {
                             < 60k: 2, else 3) */
     int team_a, team_b;  /* lanes per particle in pass A / pass B: 1, 4,
                             16 or 32; 0: by set size */
+    int walls;           /* walls seen from the fluid: 1 the wall grid's
+                            cells around each fluid particle, 2 wall lists
+                            built with each neighbour build (from the walls'
+                            side); 0: lists when there are at least 2048
+                            wall particles */
     int no_graphs;       /* 0 (default): sph_step replays each step as a
                             captured CUDA graph when it can (the only live
                             context of the process, a stream other than the
@@ -323,13 +328,16 @@ typedef struct {
      * (neighbour build + both passes for cell_scale 1, 1.25, 1.5; the walk
      * for walk 1..3; pass A / pass B for teams 1, 4, 16, 32) */
     double ms_cell[3], ms_walk[3], ms_team_a[4], ms_team_b[4];
+    double ms_walls[2];  /* build + both passes with walls 1, 2 (walls
+                            loaded only) */
 } sph_tune;
 
 /* Autotuner (the paper has no counterpart; a launch-configuration search
  * for this GPU): on the loaded fluid set at its current state, times
  * neighbour builds and right-hand sides for each level-0 cell size
  * (x1, x1.25, x1.5), then each list-build kernel, then each team size of
- * pass A and pass B (CUDA events, a few repetitions after a warm-up), and
+ * pass A and pass B, then (with walls) the two ways the fluid sees the
+ * walls (CUDA events, a few repetitions after a warm-up), and
  * keeps the fastest of each for this context; out (may be NULL) receives
  * the choices and the times.  It ends with a right-hand side as sph_rhs
  * does (the state re-sorted, its density the summation density, the rates

@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(128) k_density_mbar(ShiftArgs a, int want_h) {
         ++cnt;
     }
     if (a.w.n > 0) {
-        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane, tm.mask,
+        for_each_wall<T>(a.w, i, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane, tm.mask,
                       [&](int k, double, double, double r2) {
             rho += (R)a.w.m[k] * qs_w<R>(sqrt((R)r2) * hinv);
         });
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(128) k_shift_compute(ShiftArgs a) {
         gpy += Vg * dp * dy;
     }
     if (a.w.n > 0) {
-        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane, tm.mask,
+        for_each_wall<T>(a.w, i, a.d, a.an, a.pk[i], a.f[S_X][i], a.f[S_Y][i], a.f[S_H][i], tm.lane, tm.mask,
                       [&](int k, double dxd, double dyd, double r2) {
             const R r = sqrt((R)r2);
             if (!(r > R(0))) return;

@@ -85,7 +85,8 @@ __global__ void k_keys(int n, KeysArgs a, const double *__restrict__ x,
                        const double *__restrict__ h,
                        uint64_t *__restrict__ skey,
                        uint32_t *__restrict__ perm, uint32_t *level_mask,
-                       int *bbox, uint32_t *__restrict__ zero) {
+                       int *bbox, uint32_t *__restrict__ zero,
+                       uint32_t *__restrict__ zero2, uint32_t *__restrict__ zero3) {
     __shared__ int sb[MAX_LEVELS * 4];
     __shared__ uint32_t smask;
     for (int t = threadIdx.x; t < MAX_LEVELS * 4; t += blockDim.x)
@@ -102,6 +103,8 @@ __global__ void k_keys(int n, KeysArgs a, const double *__restrict__ x,
         skey[i] = ((uint64_t)l << (2 * a.mbits)) | m;
         perm[i] = (uint32_t)i;
         if (zero) zero[i] = 0;
+        if (zero2) zero2[i] = 0;
+        if (zero3) zero3[i] = 0;
         atomicOr(&smask, 1u << l);
         atomicMin(&sb[l * 4 + 0], ix);
         atomicMax(&sb[l * 4 + 1], ix);
@@ -153,7 +156,7 @@ void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
                  int lmax, int mbits, const Level *lev, const double *x,
                  const double *y, const double *h, uint64_t *skey,
                  uint32_t *perm, uint32_t *level_mask, int *bbox,
-                 uint32_t *zero) {
+                 uint32_t *zero, uint32_t *zero2, uint32_t *zero3) {
     KeysArgs a;
     a.dom = dom;
     a.c0 = c0;
@@ -168,7 +171,7 @@ void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
     if (n <= 0) return;
     int bs = 256;
     k_keys<<<(n + bs - 1) / bs, bs, 0, s>>>(n, a, x, y, h, skey, perm,
-                                            level_mask, bbox, zero);
+                                            level_mask, bbox, zero, zero2, zero3);
 }
 
 // ------------------------------------------------------------ radix sort --

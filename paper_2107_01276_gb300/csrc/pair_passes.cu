@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(128)
         }
     }
     if (a.w.n > 0) {
-        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane, tm.mask,
+        for_each_wall<T>(a.w, i, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane, tm.mask,
                       [&](int k, double dxd, double dyd, double r2d) {
             pair((R)a.w.m[k], (R)a.w.h[k], (R)a.w.p[k], false, (R)dxd,
                  (R)dyd, (R)r2d);
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_B_BLOCKS : 1)
     }
     if (a.w.n > 0) {
         const R rho0 = (R)a.rho0;
-        for_each_wall<T>(a.w, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane, tm.mask,
+        for_each_wall<T>(a.w, i, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane, tm.mask,
                       [&](int k, double dxd, double dyd, double r2d) {
             const R mk = (R)a.w.m[k], pk = (R)a.w.p[k];
             const R pref = literal ? R(0) : pavg_i;
@@ -385,6 +385,52 @@ __global__ void __launch_bounds__(128) k_wall_bc(WallBcArgs a) {
     a.pw[k] = p;
     a.ugx[k] = 2.0 * a.w.uw[k] - uh;
     a.ugy[k] = 2.0 * a.w.vw[k] - vh;
+}
+
+// ------------------------------------------------------------ wall lists --
+template <int T>
+__global__ void __launch_bounds__(128) k_wall_lists(WallListArgs a, int fill) {
+    const Team<T> tm;
+    const int k = Team<T>::particle();
+    if (k >= a.w.n) return;
+    const float4 pw = a.w.pk[k];
+    const float2 q = anchor_rel(a.an, pw);
+    for_each_candidate_team<T>(a.g, a.d, 0, q.x, q.y, pw.z, a.reach, tm.lane,
+                               tm.mask, [](uint32_t, uint32_t) { return true; },
+                               [&](uint32_t j) {
+        const float4 pj = __ldg(&a.pk[j]);
+        float dx, dy;
+        anchor_sep(a.an, pw, pj, dx, dy);
+        const float R = a.reach * 3.0f * fmaxf(pw.z, pj.z);
+        if (!(fmaf(dx, dx, dy * dy) < R * R)) return;
+        if (!fill) {
+            atomicAdd(&a.cnt[j], 1u);
+        } else {
+            const uint32_t p = a.off[j] + atomicAdd(&a.cur[j], 1u);
+            if (p < a.cap)
+                a.list[p] = (uint32_t)k;
+            else
+                atomicOr(a.overflow, 1);
+        }
+    });
+}
+
+// Each fluid particle's wall list in ascending wall index (lists are
+// short: only particles next to a wall have entries).
+__global__ void k_wall_list_sort(int n, const uint32_t *off, uint32_t *list,
+                                 uint32_t cap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t b = off[i], e = min(off[i + 1], cap);
+    for (uint32_t k = b + 1; k < e; ++k) {
+        const uint32_t v = list[k];
+        uint32_t m = k;
+        while (m > b && list[m - 1] > v) {
+            list[m] = list[m - 1];
+            --m;
+        }
+        list[m] = v;
+    }
 }
 
 // ---------------------------------------------------------- force on solid --
@@ -634,6 +680,30 @@ void launch_forces(cudaStream_t s, const ForceArgs<R> &a) {
 }
 template void launch_forces<double>(cudaStream_t, const ForceArgs<double> &);
 template void launch_forces<float>(cudaStream_t, const ForceArgs<float> &);
+
+void launch_wall_lists_count(cudaStream_t s, int n, const WallListArgs &a,
+                             SortScratch &sc, int *launches) {
+    if (n <= 0) return;
+    if (a.w.n > 0) {
+        with_team(a.w.n, [&](auto t) {
+            constexpr int T = decltype(t)::value;
+            k_wall_lists<T><<<nblk(a.w.n * T, 128), 128, 0, s>>>(a, 0);
+        });
+        *launches += 1;
+    }
+    exclusive_scan(s, a.cnt, (uint32_t *)a.off, n + 1, nullptr, sc, launches);
+}
+
+void launch_wall_lists_fill(cudaStream_t s, int n, const WallListArgs &a,
+                            int *launches) {
+    if (n <= 0 || a.w.n <= 0) return;
+    with_team(a.w.n, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        k_wall_lists<T><<<nblk(a.w.n * T, 128), 128, 0, s>>>(a, 1);
+    });
+    k_wall_list_sort<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.list, a.cap);
+    *launches += 2;
+}
 
 void launch_forces_total(cudaStream_t s, int nw, const double *fw,
                          const int64_t *id, double *out, double *total) {

@@ -105,7 +105,8 @@ void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
                  int lmax, int mbits, const Level *lev, const double *x,
                  const double *y, const double *h, uint64_t *skey,
                  uint32_t *perm, uint32_t *level_mask, int *bbox,
-                 uint32_t *zero = nullptr);   // zero[i] = 0 for i < n
+                 uint32_t *zero = nullptr,    // zero[i] = 0 for i < n
+                 uint32_t *zero2 = nullptr, uint32_t *zero3 = nullptr);
 // Stable LSD radix sort of (skey, perm) over the low `bits` bits.
 void radix_sort(cudaStream_t s, int n, int bits, uint64_t *key,
                 uint32_t *val, SortScratch &sc, int *launches);

@@ -71,11 +71,12 @@ class Tune(ctypes.Structure):
     """sph_tune: launch configuration of a context (sph.h)."""
     _fields_ = [("cell_scale", ctypes.c_double), ("walk", ctypes.c_int),
                 ("team_a", ctypes.c_int), ("team_b", ctypes.c_int),
-                ("no_graphs", ctypes.c_int),
+                ("walls", ctypes.c_int), ("no_graphs", ctypes.c_int),
                 ("ms_cell", ctypes.c_double * 3),
                 ("ms_walk", ctypes.c_double * 3),
                 ("ms_team_a", ctypes.c_double * 4),
-                ("ms_team_b", ctypes.c_double * 4)]
+                ("ms_team_b", ctypes.c_double * 4),
+                ("ms_walls", ctypes.c_double * 2)]
 
 
 class Particles(ctypes.Structure):
@@ -169,8 +170,8 @@ def lib(build_if_missing: bool = True):
 
 def _tune_dict(t: Tune) -> dict:
     out = {k: getattr(t, k) for k in ("cell_scale", "walk", "team_a", "team_b",
-                                      "no_graphs")}
-    for k in ("ms_cell", "ms_walk", "ms_team_a", "ms_team_b"):
+                                      "walls", "no_graphs")}
+    for k in ("ms_cell", "ms_walk", "ms_team_a", "ms_team_b", "ms_walls"):
         out[k] = list(getattr(t, k))
     return out
 
@@ -299,11 +300,13 @@ class Simulation:
         return _tune_dict(t)
 
     def set_tuning(self, cell_scale: float = 1.0, walk: int = 0,
-                   team_a: int = 0, team_b: int = 0, graphs: bool = True):
+                   team_a: int = 0, team_b: int = 0, graphs: bool = True,
+                   walls: int = 0):
         """sph_set_tuning (0: the size rule; graphs False: sph_step launch
-        by launch)."""
+        by launch; walls 1 cell walk, 2 wall lists)."""
         t = Tune()
         t.cell_scale, t.walk, t.team_a, t.team_b = cell_scale, walk, team_a, team_b
+        t.walls = walls
         t.no_graphs = 0 if graphs else 1
         self._check(self._L.sph_set_tuning(self._ctx, ctypes.byref(t)))
 
