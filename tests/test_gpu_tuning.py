@@ -86,3 +86,36 @@ def test_set_tuning_rejects_bad_values():
         with pytest.raises(sph.SphError):
             s.set_tuning(**bad)
     s.close()
+
+
+@pytest.mark.parametrize("walls", [1, 2])
+@pytest.mark.parametrize("precision,tol", [(sph.SPH_FP64, FP64_TOL),
+                                           (sph.SPH_MIXED, MIXED_TOL)])
+def test_wall_modes_match_the_oracle(walls, precision, tol):
+    """The fluid sees the walls through the wall grid's cells (1) or through
+    wall lists built with the neighbour lists (2): both give the oracle's
+    right-hand side next to a closed body."""
+    d = wl.ring_in_lattice(ds=0.05, jitter=0.2, seed=12)
+    fl = d["particles"]
+    rng = np.random.default_rng(13)
+    n = fl["x"].size
+    fl["u"][:] = 1.0 + rng.normal(0, 0.1, n)
+    fl["v"][:] = rng.normal(0, 0.1, n)
+    fl["p"][:] = rng.normal(0, 0.5, n)
+    P = sph.make_params(d["params"], precision=precision, capacity=n)
+    s = sph.Simulation(P, stream_handle())
+    s.set_tuning(walls=walls)
+    s.load(fl)
+    s.load(d["walls"], kind=sph.SPH_WALL)
+    s.rhs()
+    got = by_id(s, list(RHS) + ["nnb"])
+    s.close()
+    OP = oracle.params(**d["params"])
+    oracle.set_walls(d["walls"])
+    try:
+        ref = oracle.rhs(OP, oracle.dt(OP, fl["h"]), oracle.make_state(fl))
+    finally:
+        oracle.set_walls(None)
+    assert np.array_equal(got["nnb"], ref["nnb"])
+    for f in RHS:
+        assert norm(got[f], ref[f], ref["s_" + f]) <= tol, f
