@@ -201,18 +201,19 @@ __global__ void __launch_bounds__(128) k_merge_closest(MergeArgs a) {
         for (uint32_t k = a.off[i] + tm.lane; k < a.off[i + 1]; k += T) {
             const int j = (int)a.list[k];
             if (j == i) continue;
-            if (a.alive_in && !a.alive_in[j]) continue;
-            const double mxj = mmax[j], mj = m[j];
-            if (!(mxj > 0.0) || mj > mxj) continue;
-            {   // FP32 pre-test on the anchor separation: its error is
-                // far below the 1e-4 relative margin, so no admissible
-                // pair is dropped; the FP64 test below decides
+            {   // FP32 pre-test on the anchor separation first (most
+                // list entries lie beyond (h_i + h_j)/2): its error is far
+                // below the 1e-4 relative margin, so no admissible pair is
+                // dropped; the FP64 test below decides
                 const float4 pj = __ldg(&a.pk[j]);
                 float fx, fy;
                 anchor_sep(a.an, pi, pj, fx, fy);
                 const float hhf = 0.5f * (pi.z + pj.z);
                 if (fmaf(fx, fx, fy * fy) > 1.0001f * hhf * hhf) continue;
             }
+            if (a.alive_in && !a.alive_in[j]) continue;
+            const double mxj = mmax[j], mj = m[j];
+            if (!(mxj > 0.0) || mj > mxj) continue;
             double dx, dy, r2;
             sep_rn(a.d, xi, yi, x[j], y[j], dx, dy, r2);
             const double hh = __dmul_rn(0.5, __dadd_rn(hi, h[j]));
@@ -352,6 +353,10 @@ __global__ void __launch_bounds__(128) k_density_mbar(ShiftArgs a, int want_h) {
         const int j = (int)a.list[k];
         R dx, dy, r2;
         sp.get(a.d, a.an, a.f[S_X], a.f[S_Y], a.pk, j, dx, dy, r2);
+        // beyond 3 h_i the kernel is exactly zero: for the density alone
+        // the entry adds nothing (lists with a skin hold many such
+        // entries); the h update's mean mass still counts it
+        if (!want_h && !(r2 < R(9) * hi * hi)) continue;
         rho += in.m[j] * qs_w<R>(sqrt(r2) * hinv);   // zero beyond 3 h_i
         if (check) {
             float fx, fy, fr2;
@@ -408,11 +413,17 @@ __global__ void __launch_bounds__(128) k_shift_compute(ShiftArgs a) {
     for (uint32_t k = a.off[i] + tm.lane; k < a.off[i + 1]; k += T) {
         const int j = (int)a.list[k];
         if (j == i) continue;
-        R dx, dy, r2;
-        sp.get(a.d, a.an, a.f[S_X], a.f[S_Y], a.pk, j, dx, dy, r2);
+        R dx, dy, r2, hj;
+        sp.get(a.d, a.an, a.f[S_X], a.f[S_Y], a.f[S_H], a.pk, j, dx, dy, r2, hj);
+        // both kernels vanish beyond 3 max(h_i, h_j): such entries (many in
+        // lists with a skin) add exactly nothing
+        {
+            const R R3 = R(3) * (hi > hj ? hi : hj);
+            if (!(r2 < R3 * R3)) continue;
+        }
         const R r = sqrt(r2);
         if (!(r > R(0))) continue;
-        shift(in.m[j], (R)a.f[S_H][j], dx, dy, r);
+        shift(in.m[j], hj, dx, dy, r);
         const R g = sigma_norm<R>() * hinv * hinv * hinv * qs_dw<R>(r * hinv) / r;
         const R Vg = (in.m[j] / rhoj[j]) * g;
         const R du = in.u[j] - ui, dv = in.v[j] - vi, dp = in.p[j] - pi;

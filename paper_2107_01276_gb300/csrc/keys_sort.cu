@@ -672,7 +672,7 @@ __global__ void k_rebuild_reset(RebuildReset r) {
     const uint32_t st = gridDim.x * blockDim.x;
     if (t0 < MAX_LEVELS * 4) r.bbox[t0] = (t0 & 1) ? -1 : 0x7fffffff;
     if (t0 == 0) *r.level_mask = 0;
-    if (t0 < 4 && r.zero[t0]) *r.zero[t0] = 0;
+    if (t0 < 5 && r.zero[t0]) *r.zero[t0] = 0;
     for (uint32_t k = t0; k < r.tslots; k += st) r.tkey[k] = EMPTY_KEY;
 }
 

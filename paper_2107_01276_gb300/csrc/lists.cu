@@ -563,7 +563,7 @@ __global__ void k_list_sort_rev(int n, const uint32_t *off, const uint32_t *own,
                                 uint32_t *nlong) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t b = off[i] + own[i], e = off[i + 1];
+    const uint32_t b = off[i] + (own ? own[i] : 0u), e = off[i + 1];
     if (e > cap || e <= b + 1) return;
     const uint32_t len = e - b;
     if (len > SORT_REG) {
@@ -598,7 +598,7 @@ __global__ void k_list_sort_long(const uint32_t *off, const uint32_t *own,
     const uint32_t gw = blockIdx.x * 4 + w, nw = gridDim.x * 4;
     for (uint32_t q = gw; q < nq; q += nw) {
         const uint32_t i = longq[q];
-        const uint32_t b = off[i] + own[i], e = off[i + 1];
+        const uint32_t b = off[i] + (own ? own[i] : 0u), e = off[i + 1];
         const uint32_t len = e - b;
         if (len > SORT_SMEM) {
             // rare: plain insertion sort by one lane
@@ -641,6 +641,18 @@ __global__ void k_list_sort_long(const uint32_t *off, const uint32_t *own,
 }
 
 // ------------------------------------------------------------- launchers --
+static inline int nblk_s(int n, int bs) { return (n + bs - 1) / bs; }
+
+void sort_segments(cudaStream_t s, int n, const uint32_t *off, uint32_t *list,
+                   uint32_t cap, uint32_t *longq, uint32_t *nlong,
+                   int *launches) {
+    if (n <= 0) return;
+    k_list_sort_rev<<<nblk_s(n, 256), 256, 0, s>>>(n, off, nullptr, list, cap,
+                                                   longq, nlong);
+    k_list_sort_long<<<std::max(1, std::min(152 * 16, nblk_s(n, 4))), 128, 0, s>>>(
+        off, nullptr, list, longq, nlong);
+    *launches += 2;
+}
 static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
 
 void launch_pack(cudaStream_t s, const PackArgs &a) {

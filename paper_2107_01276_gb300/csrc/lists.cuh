@@ -70,5 +70,11 @@ void list_offsets(cudaStream_t s, const ListArgs &a, SortScratch &sc,
 // caller knows none did).
 void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,
                       int *launches);
+// Each segment [off[i], off[i+1]) of list in ascending order (short ones in
+// registers, long ones queued in longq / *nlong, which must be zero, for a
+// warp sort).
+void sort_segments(cudaStream_t s, int n, const uint32_t *off, uint32_t *list,
+                   uint32_t cap, uint32_t *longq, uint32_t *nlong,
+                   int *launches);
 
 }  // namespace sph

@@ -8,6 +8,7 @@
 #include <float.h>
 
 #include "kernels.cuh"
+#include "lists.cuh"
 #include "neighbors.cuh"
 #include "pair_passes.cuh"
 #include "team.cuh"
@@ -415,24 +416,6 @@ __global__ void __launch_bounds__(128) k_wall_lists(WallListArgs a, int fill) {
     });
 }
 
-// Each fluid particle's wall list in ascending wall index (lists are
-// short: only particles next to a wall have entries).
-__global__ void k_wall_list_sort(int n, const uint32_t *off, uint32_t *list,
-                                 uint32_t cap) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t b = off[i], e = min(off[i + 1], cap);
-    for (uint32_t k = b + 1; k < e; ++k) {
-        const uint32_t v = list[k];
-        uint32_t m = k;
-        while (m > b && list[m - 1] > v) {
-            list[m] = list[m - 1];
-            --m;
-        }
-        list[m] = v;
-    }
-}
-
 // ---------------------------------------------------------- force on solid --
 // Section "Force computation", Eq. force-sph, for wall particle k over its
 // fluid neighbours j; FP64 sums (a team of T lanes per wall particle).
@@ -701,8 +684,8 @@ void launch_wall_lists_fill(cudaStream_t s, int n, const WallListArgs &a,
         constexpr int T = decltype(t)::value;
         k_wall_lists<T><<<nblk(a.w.n * T, 128), 128, 0, s>>>(a, 1);
     });
-    k_wall_list_sort<<<nblk(n, 256), 256, 0, s>>>(n, a.off, a.list, a.cap);
-    *launches += 2;
+    sort_segments(s, n, a.off, a.list, a.cap, a.longq, a.nlong, launches);
+    *launches += 1;
 }
 
 void launch_forces_total(cudaStream_t s, int nw, const double *fw,

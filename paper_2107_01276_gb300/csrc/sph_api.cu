@@ -136,6 +136,7 @@ struct sph_ctx {
     float *mh0 = nullptr, *mds = nullptr;   // merge rounds: h at the build, displacement
     // fluid particles' wall lists (rebuilt with every neighbour build)
     uint32_t *wcnt = nullptr, *woff = nullptr, *wcur = nullptr, *wlist = nullptr;
+    uint32_t *wlongq = nullptr, *d_wnlong = nullptr;
     uint32_t wcap = 0;
     int wall_mode = 0;              // 0: by wall count, 1: cell walk, 2: lists
     bool wall_lists_valid = false;  // the last build made them
@@ -426,6 +427,7 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true,
     rr.zero[2] = c->d_nlong;
     const bool walls = for_walls && want_wall_lists(c);
     rr.zero[3] = walls ? c->wcnt + n : nullptr;
+    rr.zero[4] = walls ? c->d_wnlong : nullptr;
     launch_rebuild_reset(c->s, rr, &c->launches);
     launch_keys(c->s, n, c->dom, c->c0, c->lmax, c->mbits, c->lev, c->f[F_X],
                 c->f[F_Y], c->f[F_H], c->skey, c->perm, c->level_mask, c->bbox,
@@ -477,6 +479,8 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true,
         wa.list = c->wlist;
         wa.cap = c->wcap;
         wa.overflow = c->d_overflow;
+        wa.longq = c->wlongq;
+        wa.nlong = c->d_wnlong;
         launch_wall_lists_count(c->s, n, wa, c->sc, &c->launches);
     }
     bool queue = true;
@@ -743,6 +747,8 @@ static void free_ctx(sph_ctx *c) {
     cudaFree(c->woff);
     cudaFree(c->wcur);
     cudaFree(c->wlist);
+    cudaFree(c->wlongq);
+    cudaFree(c->d_wnlong);
     cudaFree(c->d_wmax);
     cudaFree(c->d_minmax);
     if (c->bgc) {
@@ -1099,6 +1105,7 @@ static sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
     ok = ok && dalloc(&c->tmp_a, N + 1) && dalloc(&c->tmp_b, N + 1) &&
          dalloc(&c->closest, N) && dalloc(&c->mh0, N) && dalloc(&c->mds, N) &&
          dalloc(&c->wcnt, N + 1) && dalloc(&c->woff, N + 1) && dalloc(&c->wcur, N) &&
+         dalloc(&c->wlongq, N) && dalloc(&c->d_wnlong, 1) &&
          dalloc(&c->d_mass, 2) &&
          dalloc(&c->d_mass_part, 256) && dalloc(&c->d_aux, 4);
     c->list_cap = std::min<size_t>(N * 48, 0xffffffffull);

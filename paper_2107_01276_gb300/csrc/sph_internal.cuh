@@ -148,7 +148,7 @@ struct RebuildReset {
     uint32_t *level_mask;
     uint64_t *tkey;
     uint32_t tslots;
-    uint32_t *zero[4];
+    uint32_t *zero[5];
 };
 void launch_rebuild_reset(cudaStream_t s, const RebuildReset &r, int *launches);
 // cmin[start of each cell] = min of v over the cell (sorted set).

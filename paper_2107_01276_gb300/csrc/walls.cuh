@@ -84,6 +84,7 @@ struct WallListArgs {
     uint32_t *list;
     uint32_t cap;
     int *overflow;
+    uint32_t *longq, *nlong;      // segment-sort scratch (nlong zeroed)
 };
 
 // Counting pass and scan (off[n] = total entries); then the filling pass
