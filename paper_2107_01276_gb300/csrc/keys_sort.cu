@@ -676,6 +676,28 @@ __global__ void k_rebuild_reset(RebuildReset r) {
     for (uint32_t k = t0; k < r.tslots; k += st) r.tkey[k] = EMPTY_KEY;
 }
 
+__global__ void k_occupancy(int n, const uint64_t *__restrict__ key,
+                            int lshift, const int *__restrict__ bbox,
+                            uint32_t *occ) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t k = key[i];
+    const int l = (int)(k >> lshift);
+    const uint64_t m = k & ((1ull << lshift) - 1ull);
+    const int ix = (int)compact2(m), iy = (int)compact2(m >> 1);
+    const int *bb = bbox + 4 * l;
+    const int bx = occ_block(ix, bb[0], bb[1]), by = occ_block(iy, bb[2], bb[3]);
+    atomicOr(&occ[(l * OCC_N + by) * (OCC_N / 32) + (bx >> 5)], 1u << (bx & 31));
+}
+
+void launch_occupancy(cudaStream_t s, int n, const uint64_t *key, int lshift,
+                      const int *bbox, uint32_t *occ, int *launches) {
+    cudaMemsetAsync(occ, 0, sizeof(uint32_t) * OCC_WORDS, s);
+    if (n <= 0) return;
+    k_occupancy<<<(n + 255) / 256, 256, 0, s>>>(n, key, lshift, bbox, occ);
+    *launches += 1;
+}
+
 // Smallest value of v over each cell of a sorted set, stored at the cell's
 // first particle (other entries are left as they are).
 __global__ void k_cell_min(int n, const uint64_t *__restrict__ skey,

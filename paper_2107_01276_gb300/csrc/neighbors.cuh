@@ -150,6 +150,37 @@ __device__ __forceinline__ bool axis_pieces(const Domain &d, const Level &L,
     return r.first[1] <= r.last[1];
 }
 
+// Whether the cells of a query (its axis pieces at level l) meet a block
+// of the occupancy map holding particles; true without a map.
+__device__ __forceinline__ bool occ_any(const Grid &g, int l, const int *bb,
+                                        const AxisPieces &px,
+                                        const AxisPieces &py) {
+    if (!g.occ) return true;
+    const int b0 = __ldg(&bb[0]), b1 = __ldg(&bb[1]);
+    const int c0 = __ldg(&bb[2]), c1 = __ldg(&bb[3]);
+    const uint32_t *o = g.occ + (size_t)l * OCC_N * (OCC_N / 32);
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+        if (px.first[kx] > px.last[kx]) continue;
+        const int xlo = occ_block(px.first[kx] + px.shift[kx], b0, b1);
+        const int xhi = occ_block(px.last[kx] + px.shift[kx], b0, b1);
+        const uint64_t mx = (xhi >= 63 ? ~0ull : ((1ull << (xhi + 1)) - 1ull)) &
+                            ~((1ull << xlo) - 1ull);
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+            if (py.first[ky] > py.last[ky]) continue;
+            const int ylo = occ_block(py.first[ky] + py.shift[ky], c0, c1);
+            const int yhi = occ_block(py.last[ky] + py.shift[ky], c0, c1);
+            for (int by = ylo; by <= yhi; ++by) {
+                const uint64_t row = (uint64_t)__ldg(&o[2 * by]) |
+                                     ((uint64_t)__ldg(&o[2 * by + 1]) << 32);
+                if (row & mx) return true;
+            }
+        }
+    }
+    return false;
+}
+
 // Calls f(s, e) for the particle range [s, e) of every occupied cell of
 // levels >= li that intersects the square of half side max(3 h_i, c_l)
 // around (xi, yi).  Cells come in a fixed order (level, then row, then
@@ -177,6 +208,7 @@ __device__ __forceinline__ void for_each_cell_scaled(const Grid &g,
         AxisPieces px, py;
         if (!axis_pieces(d, L, bb, 0, xr, Q, px)) continue;
         if (!axis_pieces(d, L, bb, 1, yr, Q, py)) continue;
+        if (!occ_any(g, l, bb, px, py)) continue;   // no particle in reach
         const uint64_t lbits = (uint64_t)l << (2 * g.mbits);
         // piece loops unrolled so the piece arrays stay in registers
 #pragma unroll
@@ -231,6 +263,7 @@ __device__ __forceinline__ void for_each_cell_team_scaled(
         AxisPieces px, py;
         if (!axis_pieces(d, L, bb, 0, xr, Q, px)) continue;
         if (!axis_pieces(d, L, bb, 1, yr, Q, py)) continue;
+        if (!occ_any(g, l, bb, px, py)) continue;   // no particle in reach
         const int nx0 = max(0, px.last[0] - px.first[0] + 1);
         const int nx1 = max(0, px.last[1] - px.first[1] + 1);
         const int nx2 = max(0, px.last[2] - px.first[2] + 1);
@@ -313,6 +346,7 @@ __device__ __forceinline__ void for_each_candidate_team(
         AxisPieces px, py;
         if (!axis_pieces(d, L, bb, 0, xr, Q, px)) continue;
         if (!axis_pieces(d, L, bb, 1, yr, Q, py)) continue;
+        if (!occ_any(g, l, bb, px, py)) continue;   // no particle in reach
         const int nx0 = max(0, px.last[0] - px.first[0] + 1);
         const int nx1 = max(0, px.last[1] - px.first[1] + 1);
         const int nx2 = max(0, px.last[2] - px.first[2] + 1);

@@ -64,6 +64,7 @@ struct StaticSet {
     float *tmaxh = nullptr;
     int *bbox = nullptr;
     uint32_t *mask = nullptr;
+    uint32_t *occ = nullptr;    // occupancy map (OCC_WORDS words)
     uint32_t tmask = 0;
     double c0 = 0.0;
     int lmax = 0, mbits = 1, lbits = 0;
@@ -72,7 +73,7 @@ struct StaticSet {
 };
 
 static void free_set(StaticSet *S) {
-    void *ps[] = {S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2], S->id, S->pk, S->cmin,
+    void *ps[] = {S->occ, S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2], S->id, S->pk, S->cmin,
                   S->key, S->tkey, S->perm, S->tstart, S->tend, S->tmaxh, S->bbox,
                   S->mask, S->sc.key_alt, S->sc.val_alt, S->sc.counts,
                   S->sc.scan_tmp};
@@ -274,6 +275,7 @@ static int bits_for(long long v) {   // bits to represent 0..v
 
 static Grid make_grid(const sph_ctx *c) {
     Grid g;
+    g.occ = nullptr;
     g.tkey = c->tkey;
     g.tstart = c->tstart;
     g.tend = c->tend;
@@ -801,6 +803,7 @@ static sph_status build_set_sorted(sph_ctx *c, StaticSet *S, long long n,
                   dalloc(&S->id, N) && dalloc(&S->key, N) && dalloc(&S->perm, N) &&
                   dalloc(&S->pk, N) &&
                   dalloc(&S->bbox, MAX_LEVELS * 4) && dalloc(&S->mask, 1) &&
+                  dalloc(&S->occ, OCC_WORDS) &&
                   dalloc(&S->sc.key_alt, N) && dalloc(&S->sc.val_alt, N);
         for (int k = 0; k < nex; ++k) ok = ok && dalloc(&S->ex[k], N);
         ok = ok && dalloc(&S->cmin, N);
@@ -830,6 +833,8 @@ static sph_status build_set_sorted(sph_ctx *c, StaticSet *S, long long n,
     launch_reset_bbox(c->s, S->bbox, S->mask);
     launch_keys(c->s, (int)n, c->dom, c0, lmax, S->mbits, S->lev, tmp, tmp + n,
                 tmp + 2 * n, S->key, S->perm, S->mask, S->bbox);
+    launch_occupancy(c->s, (int)n, S->key, 2 * S->mbits, S->bbox, S->occ,
+                     &c->launches);
     radix_sort(c->s, (int)n, 2 * S->mbits + S->lbits, S->key, S->perm, S->sc,
                &c->launches);
     GatherList gl;
@@ -941,6 +946,7 @@ static void ensure_set_pk(sph_ctx *c, StaticSet *S) {
 
 static Grid set_grid(const StaticSet &S) {
     Grid g;
+    g.occ = S.occ;
     g.tkey = S.tkey;
     g.tstart = S.tstart;
     g.tend = S.tend;

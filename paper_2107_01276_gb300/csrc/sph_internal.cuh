@@ -49,8 +49,36 @@ struct Grid {
     const int *bbox;        // per level: min ix, max ix, min iy, max iy
     const float *tmaxh;     // per table slot: largest h of the cell (rounded
                             // up to float), or NULL
+    // Occupancy map (static sets; NULL for the fluid): per level, the
+    // level's bounding box cut into OCC_N x OCC_N blocks of cells, one bit
+    // per block holding a particle; a query whose cells cover no set bit
+    // skips the level without looking up a cell.
+    const uint32_t *occ;
     Level lev[MAX_LEVELS];
 };
+
+constexpr int OCC_N = 64;                       // blocks per axis
+constexpr int OCC_WORDS = MAX_LEVELS * OCC_N * (OCC_N / 32);
+
+__host__ __device__ inline uint32_t compact2(uint64_t v) {
+    v &= 0x5555555555555555ull;
+    v = (v | (v >> 1)) & 0x3333333333333333ull;
+    v = (v | (v >> 2)) & 0x0f0f0f0f0f0f0f0full;
+    v = (v | (v >> 4)) & 0x00ff00ff00ff00ffull;
+    v = (v | (v >> 8)) & 0x0000ffff0000ffffull;
+    v = (v | (v >> 16)) & 0x00000000ffffffffull;
+    return (uint32_t)v;
+}
+
+// Block of cell index c on an axis whose occupied cells span [b0, b1].
+__host__ __device__ inline int occ_block(int c, int b0, int b1) {
+    return (int)(((long long)(c - b0) * OCC_N) / ((long long)b1 - b0 + 1));
+}
+
+// Sets the occupancy bits of n keyed particles (map zeroed beforehand,
+// bounding boxes final).
+void launch_occupancy(cudaStream_t s, int n, const uint64_t *key, int lshift,
+                      const int *bbox, uint32_t *occ, int *launches);
 
 constexpr uint64_t EMPTY_KEY = ~0ull;
 
