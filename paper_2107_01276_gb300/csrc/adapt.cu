@@ -183,6 +183,20 @@ __global__ void k_split_emit(SplitArgs a) {
 // ------------------------------------------------------------------ merge --
 // closest_i: admissible j in N(i) of least (r^2, id_j); admissible: j != i,
 // neither to be split, r^2 < ((h_i + h_j)/2)^2, m_i + m_j < max(m_max).
+// FP32 bounds for the admissibility test m_i + m_j < max(m_max,i, m_max,j):
+// if rd(m_i) + rd(m_j), rounded down, is not below max(ru(m_max)), the FP64
+// sum (rounding is monotone and the FP32 bounds are doubles) is not below
+// the FP64 maximum either, so the pair is rejected without FP64 work.
+__device__ __forceinline__ float2 merge_bounds(double m, double mx, bool alive) {
+    if (!alive || !(mx > 0.0) || m > mx) return make_float2(INFINITY, -INFINITY);
+    return make_float2(__double2float_rd(m), __double2float_ru(mx));
+}
+
+__global__ void k_merge_prep(MergeArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) a.mq[i] = merge_bounds(a.f[S_M][i], a.f[S_MMAX][i], true);
+}
+
 template <int T>
 __global__ void __launch_bounds__(128) k_merge_closest(MergeArgs a) {
     const Team<T> tm;
@@ -193,16 +207,22 @@ __global__ void __launch_bounds__(128) k_merge_closest(MergeArgs a) {
     int best = -1;
     double br2 = 0.0;
     long long bid = 0;
-    const double mi = m[i], mxi = mmax[i];
+    const float2 qi = a.mq[i];
     const bool alive_i = !a.alive_in || a.alive_in[i];
-    if (alive_i && mxi > 0.0 && !(mi > mxi)) {
+    if (alive_i && qi.y > 0.0f) {
+        const double mi = m[i], mxi = mmax[i];
         const double xi = x[i], yi = y[i], hi = h[i];
         const float4 pi = a.pk[i];
         for (uint32_t k = a.off[i] + tm.lane; k < a.off[i + 1]; k += T) {
             const int j = (int)a.list[k];
             if (j == i) continue;
-            {   // FP32 pre-test on the anchor separation first (most
-                // list entries lie beyond (h_i + h_j)/2): its error is far
+            {   // FP32 mass bound first: it rejects most pairs of a
+                // uniform region exactly (see merge_bounds)
+                const float2 qj = __ldg(&a.mq[j]);
+                if (!(__fadd_rd(qi.x, qj.x) < fmaxf(qi.y, qj.y))) continue;
+            }
+            {   // FP32 pre-test on the anchor separation (most list
+                // entries lie beyond (h_i + h_j)/2): its error is far
                 // below the 1e-4 relative margin, so no admissible pair is
                 // dropped; the FP64 test below decides
                 const float4 pj = __ldg(&a.pk[j]);
@@ -260,6 +280,7 @@ __global__ void k_merge_apply(MergeArgs a) {
     if (j >= 0 && a.closest[j] == i) {
         if (a.id[i] > a.id[j]) {
             alive = 0;
+            a.mq[i] = merge_bounds(0.0, 0.0, false);
         } else {
             double *f[NSTATE];
             for (int k = 0; k < NSTATE; ++k) f[k] = a.f[k];
@@ -289,6 +310,7 @@ __global__ void k_merge_apply(MergeArgs a) {
             f[S_Y][i] = wrap_rn(a.d, 1, ym);
             f[S_M][i] = mm;
             f[S_H][i] = hm;
+            a.mq[i] = merge_bounds(mm, f[S_MMAX][i], true);
             // reach of the lists for the next round (rounded up)
             ds = __fadd_ru(ds, __double2float_ru(ra));
             if (__fadd_ru(0.5f * __double2float_ru(hm), ds) > a.budget * h0)
@@ -536,6 +558,7 @@ void launch_split_emit(cudaStream_t s, const SplitArgs &a) {
 }
 void launch_merge(cudaStream_t s, const MergeArgs &a) {
     if (a.n <= 0) return;
+    if (!a.alive_in) k_merge_prep<<<nblk(a.n, 256), 256, 0, s>>>(a);
     with_team(a.n, [&](auto t) {
         constexpr int T = decltype(t)::value;
         k_merge_closest<T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);

@@ -63,6 +63,11 @@ struct MergeArgs {
     int *stale;
     float4 *pkw;                // anchor records, refreshed for merged particles
     double lo[2], Ad[2], invAd[2];
+    // Per particle {m rounded down, m_max rounded up} in FP32, or
+    // {+inf, -inf} for a particle that cannot merge (dead, m_max <= 0 or
+    // m > m_max): written for every particle in the first round after a
+    // build, refreshed by each round for the particles it changes.
+    float2 *mq;
 };
 
 struct CompactArgs {

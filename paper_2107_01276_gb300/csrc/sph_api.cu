@@ -135,6 +135,7 @@ struct sph_ctx {
     uint32_t *tmp_a = nullptr, *tmp_b = nullptr;   // N + 1 each
     int *closest = nullptr;
     float *mh0 = nullptr, *mds = nullptr;   // merge rounds: h at the build, displacement
+    float2 *mq = nullptr;                   // merge rounds: FP32 mass bounds
     // fluid particles' wall lists (rebuilt with every neighbour build)
     uint32_t *wcnt = nullptr, *woff = nullptr, *wcur = nullptr, *wlist = nullptr;
     uint32_t *wlongq = nullptr, *d_wnlong = nullptr;
@@ -740,7 +741,7 @@ static void free_ctx(sph_ctx *c) {
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
                   c->d_overflow, c->d_skin_err, c->longq, c->d_nlong, c->stage, c->lqueue, c->d_max_own,
                   c->d_nlq, c->tmp_a, c->tmp_b,
-                  c->closest, c->mh0, c->mds, c->d_mass, c->d_mass_part, c->wp, c->wugx,
+                  c->closest, c->mh0, c->mds, c->mq, c->d_mass, c->d_mass_part, c->wp, c->wugx,
                   c->wugy, c->d_aux};
     for (void *p : ps) cudaFree(p);
     cudaFree(c->omega);
@@ -1110,6 +1111,7 @@ static sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
          dalloc(&c->d_nlq, 1) && dalloc(&c->d_max_own, 1);
     ok = ok && dalloc(&c->tmp_a, N + 1) && dalloc(&c->tmp_b, N + 1) &&
          dalloc(&c->closest, N) && dalloc(&c->mh0, N) && dalloc(&c->mds, N) &&
+         dalloc(&c->mq, N) &&
          dalloc(&c->wcnt, N + 1) && dalloc(&c->woff, N + 1) && dalloc(&c->wcur, N) &&
          dalloc(&c->wlongq, N) && dalloc(&c->d_wnlong, 1) &&
          dalloc(&c->d_mass, 2) &&
@@ -1965,6 +1967,7 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
             a.budget = 1.5f * c->skin * (1.0f - 1e-3f);
             a.stale = stale;
             a.pkw = c->pk;
+            a.mq = c->mq;
             for (int ax = 0; ax < 2; ++ax) {
                 a.lo[ax] = c->dom.lo[ax];
                 a.Ad[ax] = c->anchor_A[ax];
@@ -1973,7 +1976,7 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
             first = false;
             launch_merge(c->s, a);
             exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
-            c->launches += 2;
+            c->launches += a.alive_in ? 2 : 3;
             uint32_t keep = 0;
             int is_stale = 0;
             cudaMemcpyAsync(&keep, c->d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
