@@ -227,6 +227,60 @@ sph_status sph_rhs(sph_ctx *ctx);
  * overflow, likewise). */
 sph_status sph_step(sph_ctx *ctx, int nsteps, double *t_out);
 
+/* Batched stepping: several independent simulations (of different sizes,
+ * parameters and precisions, with or without walls) advance one PEC step
+ * together.  A batch holds the device work lists of up to max_instances
+ * contexts per call and the stream its launches go on (a cudaStream_t;
+ * NULL = the legacy default stream); it owns no particle data.
+ * sph_batch_create errors: SPH_EINVAL (out NULL, max_instances outside
+ * 1 .. 2^20), SPH_ENOMEM.  sph_batch_destroy waits for the batch's work and
+ * frees it (SPH_EINVAL for NULL). */
+typedef struct sph_batch sph_batch;
+sph_status sph_batch_create(int max_instances, void *stream, sph_batch **out);
+sph_status sph_batch_destroy(sph_batch *batch);
+
+/* One step of sph_step (nsteps = 1, section 2.4) for each of the k distinct
+ * contexts ctx[0 .. k-1].  Each context's time step and neighbour build run
+ * on its own stream; then every per-particle phase of the step (wall
+ * conditions, pass A, pass B, the predictor and corrector stages, the
+ * mid-step packing of SPH_MIXED contexts, the density store) runs on the
+ * batch's stream as ONE persistent launch over all contexts that share a
+ * precision and a team size, its work list made of (context, block of
+ * particles) items; SPH_FP64 contexts rebuild mid-step on their streams.
+ * Each context's results equal those of sph_step on it alone, bit for bit.
+ * The contexts' streams wait for the batch's launches before their next
+ * work.  t_out (NULL or k entries) receives each context's simulated time
+ * and makes the call synchronise and report the checks sph_step reports.
+ * failed (may be NULL) receives the index of the context an error belongs
+ * to, or -1; its sph_last_error() has the message.  Errors: SPH_EINVAL
+ * (NULL batch, ctx or context, k outside 1 .. max_instances, a context
+ * listed twice: nothing was changed), SPH_ESTATE (a context without fluid:
+ * nothing was changed), and the errors of sph_step (a failed neighbour
+ * build before the predictor leaves every context at its state before the
+ * call; a failed mid-step build of an SPH_FP64 context leaves the batch
+ * between the stages: reload the state). */
+sph_status sph_batch_step(sph_batch *batch, sph_ctx *const *ctx, int k, double *t_out,
+                          int *failed);
+
+/* Kernel launches the batch itself issued so far (one per phase and group
+ * and call; the contexts' own launches count in their sph_info). -1 for
+ * NULL. */
+long long sph_batch_launches(const sph_batch *batch);
+
+/* Captured CUDA graphs of the batched step: once the same contexts (same
+ * order, configuration and particle counts) have come up in three calls in
+ * a row, the whole step -- every context's time step and build on its
+ * stream and the batched phases -- is captured as one graph and replayed
+ * while the batch recurs (two graphs alternate: each step swaps the
+ * contexts' state buffers), with the same launches and results as the
+ * launch-by-launch step.  Needs a batch stream other than the legacy or
+ * per-thread default stream, library timing off on every context, and list
+ * sizes known from earlier builds.  enable = 0 turns graphs off (default
+ * on).  Errors: SPH_EINVAL (NULL batch).  sph_batch_graph_steps: steps
+ * replayed as graphs so far (-1 for NULL). */
+sph_status sph_batch_set_graphs(sph_batch *batch, int enable);
+long long sph_batch_graph_steps(const sph_batch *batch);
+
 /* One adaptation of the fluid particles (section 3, steps ii-iii of the
  * time loop in section 3.4), in FP64 for both precisions:
  *  1. if a background set is loaded, m_ref of each fluid particle is the

@@ -4,6 +4,7 @@
 // neighbor search").  All HBM-bound; no tensor cores.
 #include <algorithm>
 
+#include "batch.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -72,28 +73,26 @@ __device__ __forceinline__ int cell_coord_fast(double x, double lo, double w,
     return c;
 }
 
-struct KeysArgs {
-    Domain dom;
-    double c0, inv_c0;
-    int lmax, mbits;
-    Level lev[MAX_LEVELS];
-    double invw[MAX_LEVELS][2];   // 1 / w per level and axis (FP64)
-};
-
-__global__ void k_keys(int n, KeysArgs a, const double *__restrict__ x,
-                       const double *__restrict__ y,
-                       const double *__restrict__ h,
-                       uint64_t *__restrict__ skey,
-                       uint32_t *__restrict__ perm, uint32_t *level_mask,
-                       int *bbox, uint32_t *__restrict__ zero,
-                       uint32_t *__restrict__ zero2, uint32_t *__restrict__ zero3) {
+__device__ __forceinline__ void keys_at(const KeysRec &r, int vb) {
+    const int n = r.n;
+    const KeysArgs &a = r.a;
+    const double *__restrict__ x = r.x;
+    const double *__restrict__ y = r.y;
+    const double *__restrict__ h = r.h;
+    uint64_t *__restrict__ skey = r.skey;
+    uint32_t *__restrict__ perm = r.perm;
+    uint32_t *level_mask = r.level_mask;
+    int *bbox = r.bbox;
+    uint32_t *__restrict__ zero = r.zero;
+    uint32_t *__restrict__ zero2 = r.zero2;
+    uint32_t *__restrict__ zero3 = r.zero3;
     __shared__ int sb[MAX_LEVELS * 4];
     __shared__ uint32_t smask;
     for (int t = threadIdx.x; t < MAX_LEVELS * 4; t += blockDim.x)
         sb[t] = (t & 1) ? -1 : 0x7fffffff;
     if (threadIdx.x == 0) smask = 0;
     __syncthreads();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = vb * blockDim.x + threadIdx.x;
     if (i < n) {
         int l = level_of_fast(h[i], a.c0, a.inv_c0, a.lmax);
         const Level &L = a.lev[l];
@@ -124,6 +123,8 @@ __global__ void k_keys(int n, KeysArgs a, const double *__restrict__ x,
     if (threadIdx.x == 0 && msk) atomicOr(level_mask, msk);
 }
 
+__global__ void k_keys(KeysRec r) { keys_at(r, blockIdx.x); }
+
 void compute_levels(const Domain &dom, double c0, Level *lev) {
     for (int l = 0; l < MAX_LEVELS; ++l) {
         double c = ldexp(c0, l);
@@ -152,12 +153,14 @@ void compute_levels(const Domain &dom, double c0, Level *lev) {
     }
 }
 
-void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
-                 int lmax, int mbits, const Level *lev, const double *x,
-                 const double *y, const double *h, uint64_t *skey,
-                 uint32_t *perm, uint32_t *level_mask, int *bbox,
-                 uint32_t *zero, uint32_t *zero2, uint32_t *zero3) {
-    KeysArgs a;
+KeysRec make_keys_rec(int n, const Domain &dom, double c0, int lmax, int mbits,
+                      const Level *lev, const double *x, const double *y,
+                      const double *h, uint64_t *skey, uint32_t *perm,
+                      uint32_t *level_mask, int *bbox, uint32_t *zero,
+                      uint32_t *zero2, uint32_t *zero3) {
+    KeysRec r;
+    r.n = n;
+    KeysArgs &a = r.a;
     a.dom = dom;
     a.c0 = c0;
     a.lmax = lmax;
@@ -168,10 +171,29 @@ void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
         a.invw[l][0] = 1.0 / lev[l].w[0];
         a.invw[l][1] = 1.0 / lev[l].w[1];
     }
+    r.x = x;
+    r.y = y;
+    r.h = h;
+    r.skey = skey;
+    r.perm = perm;
+    r.level_mask = level_mask;
+    r.bbox = bbox;
+    r.zero = zero;
+    r.zero2 = zero2;
+    r.zero3 = zero3;
+    return r;
+}
+
+void launch_keys(cudaStream_t s, int n, const Domain &dom, double c0,
+                 int lmax, int mbits, const Level *lev, const double *x,
+                 const double *y, const double *h, uint64_t *skey,
+                 uint32_t *perm, uint32_t *level_mask, int *bbox,
+                 uint32_t *zero, uint32_t *zero2, uint32_t *zero3) {
     if (n <= 0) return;
+    const KeysRec r = make_keys_rec(n, dom, c0, lmax, mbits, lev, x, y, h, skey, perm,
+                                    level_mask, bbox, zero, zero2, zero3);
     int bs = 256;
-    k_keys<<<(n + bs - 1) / bs, bs, 0, s>>>(n, a, x, y, h, skey, perm,
-                                            level_mask, bbox, zero, zero2, zero3);
+    k_keys<<<(n + bs - 1) / bs, bs, 0, s>>>(r);
 }
 
 // ------------------------------------------------------------ radix sort --
@@ -260,9 +282,9 @@ constexpr int RSS_THREADS = 1024;
 constexpr int RSS_WARPS = RSS_THREADS / 32;
 constexpr int RSS_MAX = 16384;
 
-__global__ void __launch_bounds__(RSS_THREADS)
-    k_radix_small(int n, int passes, uint64_t *ka, uint32_t *va, uint64_t *kb,
-                  uint32_t *vb) {
+__device__ __forceinline__ void radix_small_at(int n, int passes, uint64_t *ka,
+                                               uint32_t *va, uint64_t *kb,
+                                               uint32_t *vb) {
     extern __shared__ uint64_t sk[];          // n keys, then n values
     uint32_t *sv = (uint32_t *)(sk + n);
     __shared__ uint32_t cnt[RSS_WARPS][256];
@@ -357,6 +379,12 @@ __global__ void __launch_bounds__(RSS_THREADS)
             __syncthreads();
         }
     }
+}
+
+__global__ void __launch_bounds__(RSS_THREADS)
+    k_radix_small(int n, int passes, uint64_t *ka, uint32_t *va, uint64_t *kb,
+                  uint32_t *vb) {
+    radix_small_at(n, passes, ka, va, kb, vb);
 }
 
 // The dynamic shared-memory limit of k_radix_small, raised once per device.
@@ -514,9 +542,10 @@ static void scan_rec(cudaStream_t s, const uint32_t *in, uint32_t *out, int n,
 constexpr int SS_THREADS = 1024;
 constexpr int SS_MAX = SS_THREADS * 32;
 
-__global__ void __launch_bounds__(SS_THREADS)
-    k_scan_small(const uint32_t *in, uint32_t *rev, uint32_t *out, int n,
-                 uint32_t *total_dev, int write_total_at_n) {
+__device__ __forceinline__ void scan_small_at(const uint32_t *in, uint32_t *rev,
+                                              uint32_t *out, int n,
+                                              uint32_t *total_dev,
+                                              int write_total_at_n) {
     __shared__ uint32_t ws[SS_THREADS / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int chunk = (n + SS_THREADS - 1) / SS_THREADS;   // <= 32
@@ -559,6 +588,12 @@ __global__ void __launch_bounds__(SS_THREADS)
         if (total_dev) *total_dev = ws[SS_THREADS / 32 - 1];
         if (write_total_at_n) out[n] = ws[SS_THREADS / 32 - 1];
     }
+}
+
+__global__ void __launch_bounds__(SS_THREADS)
+    k_scan_small(const uint32_t *in, uint32_t *rev, uint32_t *out, int n,
+                 uint32_t *total_dev, int write_total_at_n) {
+    scan_small_at(in, rev, out, n, total_dev, write_total_at_n);
 }
 
 void exclusive_scan(cudaStream_t s, const uint32_t *in, uint32_t *out, int n,
@@ -632,11 +667,11 @@ __global__ void k_table_end(int n, const uint64_t *__restrict__ skey,
 }
 
 // Gather in sorted order fused with the insertion of each cell's start.
-__global__ void k_gather_insert(int n, const uint32_t *__restrict__ perm,
-                                GatherList g, const uint64_t *__restrict__ skey,
-                                uint64_t *tkey, uint32_t *tstart,
-                                uint32_t tmask) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void gather_insert_at(int i, int n, const uint32_t *__restrict__ perm,
+                                                 const GatherList &g,
+                                                 const uint64_t *__restrict__ skey,
+                                                 uint64_t *tkey, uint32_t *tstart,
+                                                 uint32_t tmask) {
     if (i >= n) return;
     uint32_t src = perm[i];
     for (int k = 0; k < g.nd; ++k) g.dst[k][i] = g.src[k][src];
@@ -656,6 +691,14 @@ __global__ void k_gather_insert(int n, const uint32_t *__restrict__ perm,
     }
 }
 
+__global__ void k_gather_insert(int n, const uint32_t *__restrict__ perm,
+                                GatherList g, const uint64_t *__restrict__ skey,
+                                uint64_t *tkey, uint32_t *tstart,
+                                uint32_t tmask) {
+    gather_insert_at(blockIdx.x * blockDim.x + threadIdx.x, n, perm, g, skey, tkey,
+                     tstart, tmask);
+}
+
 void gather_insert(cudaStream_t s, int n, const uint32_t *perm,
                    const GatherList &g, const uint64_t *skey, uint64_t *tkey,
                    uint32_t *tstart, uint32_t tmask, int *launches) {
@@ -667,14 +710,17 @@ void gather_insert(cudaStream_t s, int n, const uint32_t *perm,
 
 // Reset before a rebuild: level bounding boxes and mask, every table key,
 // and up to four counters.
-__global__ void k_rebuild_reset(RebuildReset r) {
-    const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t st = gridDim.x * blockDim.x;
+__device__ __forceinline__ void rebuild_reset_at(const RebuildReset &r, uint32_t vb,
+                                                 uint32_t nvb) {
+    const uint32_t t0 = vb * blockDim.x + threadIdx.x;
+    const uint32_t st = nvb * blockDim.x;
     if (t0 < MAX_LEVELS * 4) r.bbox[t0] = (t0 & 1) ? -1 : 0x7fffffff;
     if (t0 == 0) *r.level_mask = 0;
     if (t0 < 5 && r.zero[t0]) *r.zero[t0] = 0;
     for (uint32_t k = t0; k < r.tslots; k += st) r.tkey[k] = EMPTY_KEY;
 }
+
+__global__ void k_rebuild_reset(RebuildReset r) { rebuild_reset_at(r, blockIdx.x, gridDim.x); }
 
 __global__ void k_occupancy(int n, const uint64_t *__restrict__ key,
                             int lshift, const int *__restrict__ bbox,
@@ -718,12 +764,106 @@ void launch_cell_min(cudaStream_t s, int n, const uint64_t *skey,
     *launches += 1;
 }
 
+int rebuild_reset_blocks(uint32_t tslots) {
+    int nb = (int)std::min<uint32_t>((tslots + 255) / 256, 608u);
+    return nb < 1 ? 1 : nb;
+}
 void launch_rebuild_reset(cudaStream_t s, const RebuildReset &r, int *launches) {
-    int nb = (int)std::min<uint32_t>((r.tslots + 255) / 256, 608u);
-    if (nb < 1) nb = 1;
-    k_rebuild_reset<<<nb, 256, 0, s>>>(r);
+    k_rebuild_reset<<<rebuild_reset_blocks(r.tslots), 256, 0, s>>>(r);
     *launches += 1;
 }
+
+// ---------------------------------------------- batched small builds ----
+// The same bodies over the work items of several instances (each item one
+// block of the instance's single-launch grid); a block syncs before its
+// next item, whose shared memory it reuses.
+template <class Rec, class F>
+__device__ __forceinline__ void batch_blocks(const Rec *args, const BatchSpan &sp, F &&f) {
+    for (int it = blockIdx.x; it < sp.total; it += gridDim.x) {
+        const BatchItem b = batch_item(sp, it);
+        f(args[b.q], b.vb, b.nvb);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_rebuild_reset_batch(const RebuildReset *args, BatchSpan sp) {
+    batch_blocks(args, sp, [](const RebuildReset &r, int vb, int nvb) {
+        rebuild_reset_at(r, vb, nvb);
+    });
+}
+__global__ void __launch_bounds__(256) k_keys_batch(const KeysRec *args, BatchSpan sp) {
+    batch_blocks(args, sp, [](const KeysRec &r, int vb, int) { keys_at(r, vb); });
+}
+__global__ void __launch_bounds__(RSS_THREADS)
+    k_radix_small_batch(const RadixSmallRec *args, BatchSpan sp) {
+    batch_blocks(args, sp, [](const RadixSmallRec &r, int, int) {
+        radix_small_at(r.n, r.passes, r.ka, r.va, r.kb, r.vb);
+    });
+}
+__global__ void __launch_bounds__(256)
+    k_gather_insert_batch(const GatherInsertRec *args, BatchSpan sp) {
+    batch_blocks(args, sp, [](const GatherInsertRec &r, int vb, int) {
+        gather_insert_at(vb * blockDim.x + threadIdx.x, r.n, r.perm, r.g, r.skey, r.tkey,
+                         r.tstart, r.tmask);
+    });
+}
+__global__ void __launch_bounds__(SS_THREADS)
+    k_scan_small_batch(const ScanSmallRec *args, BatchSpan sp) {
+    batch_blocks(args, sp, [](const ScanSmallRec &r, int, int) {
+        scan_small_at(r.in, r.rev, r.out, r.n, r.total_dev, r.write_total_at_n);
+    });
+}
+
+int radix_small_max() { return RSS_MAX; }
+bool radix_small_available() { return radix_small_ready(); }
+int scan_small_max() { return SS_MAX; }
+
+template <class K>
+static int resident(K kernel, int threads, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+            cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm;
+}
+static int batch_grid(int per_sm, int total) {
+    const long long g = (long long)per_sm * gpu_sms();
+    return (int)(g < total ? g : total);
+}
+void launch_rebuild_reset_batch(cudaStream_t s, const RebuildReset *args, const BatchSpan &sp) {
+    static const int r = resident(k_rebuild_reset_batch, 256, 0);
+    if (sp.total > 0) k_rebuild_reset_batch<<<batch_grid(r, sp.total), 256, 0, s>>>(args, sp);
+}
+void launch_keys_batch(cudaStream_t s, const KeysRec *args, const BatchSpan &sp) {
+    static const int r = resident(k_keys_batch, 256, 0);
+    if (sp.total > 0) k_keys_batch<<<batch_grid(r, sp.total), 256, 0, s>>>(args, sp);
+}
+bool launch_radix_small_batch(cudaStream_t s, const RadixSmallRec *args, const BatchSpan &sp,
+                              int max_n) {
+    static const bool ok = cudaFuncSetAttribute(k_radix_small_batch,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                RSS_MAX * 12) == cudaSuccess;
+    if (!ok || max_n > RSS_MAX) {
+        cudaGetLastError();
+        return false;
+    }
+    if (sp.total > 0)
+        k_radix_small_batch<<<std::min(sp.total, gpu_sms()), RSS_THREADS, (size_t)max_n * 12, s>>>(
+            args, sp);
+    return true;
+}
+void launch_gather_insert_batch(cudaStream_t s, const GatherInsertRec *args, const BatchSpan &sp) {
+    static const int r = resident(k_gather_insert_batch, 256, 0);
+    if (sp.total > 0) k_gather_insert_batch<<<batch_grid(r, sp.total), 256, 0, s>>>(args, sp);
+}
+void launch_scan_small_batch(cudaStream_t s, const ScanSmallRec *args, const BatchSpan &sp) {
+    static const int r = resident(k_scan_small_batch, SS_THREADS, 0);
+    if (sp.total > 0) k_scan_small_batch<<<batch_grid(r, sp.total), SS_THREADS, 0, s>>>(args, sp);
+}
+
 
 void build_cell_table(cudaStream_t s, int n, const uint64_t *skey,
                       uint64_t *tkey, uint32_t *tstart, uint32_t *tend,

@@ -16,9 +16,7 @@
 namespace sph {
 
 // ------------------------------------------------------------------ pack --
-__global__ void k_pack(PackArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+__device__ __forceinline__ void pack_at(const PackArgs &a, int i) {
     a.lev[i] = (uint8_t)(a.skey[i] >> a.lshift);
     a.pk[i] = anchor_record(a.x[i], a.y[i], a.h[i], a.lo, a.Ad, a.invAd, a.an);
     if (a.tend) table_mark_end(i, a.n, a.skey, a.tkey, a.tend, a.tmask, a.h, a.tmaxh);
@@ -27,6 +25,23 @@ __global__ void k_pack(PackArgs a) {
     a.pf[i] = (float)a.p[i];
     a.uf[i] = (float)a.u[i];
     a.vf[i] = (float)a.v[i];
+}
+
+__global__ void k_pack(PackArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    pack_at(a, i);
+}
+
+// The same over the work items of several instances (batched step).
+__global__ void __launch_bounds__(BATCH_THREADS)
+    k_pack_batch(const PackArgs *__restrict__ args, BatchSpan sp) {
+    for (int item = blockIdx.x; item < sp.total; item += gridDim.x) {
+        const int q = sp.find(item);
+        const PackArgs a = args[q];
+        const int i = (item - __ldg(&sp.first[q])) * BATCH_THREADS + (int)threadIdx.x;
+        if (i < a.n) pack_at(a, i);
+    }
 }
 
 // Anchor coordinates of a particle set (static sets: walls, background).
@@ -72,10 +87,7 @@ __device__ __forceinline__ bool member(const ListArgs &a, const float4 &pi,
 // entries go to a queue that k_list_fill_queue handles with a second walk.
 
 template <int T>
-__global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
-    const Team<T> tm;
-    const int i = Team<T>::particle();
-    if (i >= a.n) return;
+__device__ __forceinline__ void list_gather_at(const ListArgs &a, int i, const Team<T> &tm) {
     const int li = a.lev[i];
     const double xi = a.x[i], yi = a.y[i], hi = a.h[i];
     const float4 pi = a.pk[i];
@@ -106,13 +118,18 @@ __global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
     }
 }
 
-// Copies the staged own entries into place and writes the reverse entries
-// (i into the list of each coarser neighbour j); T lanes per particle.
 template <int T>
-__global__ void __launch_bounds__(128) k_list_place(ListArgs a) {
+__global__ void __launch_bounds__(128) k_list_gather(ListArgs a) {
     const Team<T> tm;
     const int i = Team<T>::particle();
     if (i >= a.n) return;
+    list_gather_at<T>(a, i, tm);
+}
+
+// Copies the staged own entries into place and writes the reverse entries
+// (i into the list of each coarser neighbour j); T lanes per particle.
+template <int T>
+__device__ __forceinline__ void list_place_at(const ListArgs &a, int i, const Team<T> &tm) {
     const uint32_t own = a.own[i];
     if (own <= a.stage_w) {               // else handled by k_list_fill_queue
         const uint32_t base = a.off[i];
@@ -132,6 +149,14 @@ __global__ void __launch_bounds__(128) k_list_place(ListArgs a) {
     if (i == a.n - 1 && tm.lane == 0 && a.off[a.n] > a.cap) atomicOr(a.overflow, 1);
 }
 
+template <int T>
+__global__ void __launch_bounds__(128) k_list_place(ListArgs a) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
+    if (i >= a.n) return;
+    list_place_at<T>(a, i, tm);
+}
+
 __global__ void k_list_total(int n, const uint32_t *own, const uint32_t *rev,
                              uint32_t *tot) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,11 +166,11 @@ __global__ void k_list_total(int n, const uint32_t *own, const uint32_t *rev,
 // Second walk for the queued particles (more than stage_w own entries):
 // same order as k_list_gather; teams take queue entries in turn.
 template <int T>
-__global__ void __launch_bounds__(128) k_list_fill_queue(ListArgs a) {
-    const Team<T> tm;
+__device__ __forceinline__ void list_fill_queue_at(const ListArgs &a, uint32_t vb,
+                                                   uint32_t nvb, const Team<T> &tm) {
     const uint32_t nq = *a.nqueue;
-    const uint32_t team = (blockIdx.x * blockDim.x + threadIdx.x) / T;
-    const uint32_t nteam = (gridDim.x * blockDim.x) / T;
+    const uint32_t team = (vb * blockDim.x + threadIdx.x) / T;
+    const uint32_t nteam = (nvb * blockDim.x) / T;
     const unsigned below = tm.mask & ((1u << (threadIdx.x & 31)) - 1u);
     for (uint32_t qi = team; qi < nq; qi += nteam) {
         const int i = (int)a.queue[qi];
@@ -172,6 +197,12 @@ __global__ void __launch_bounds__(128) k_list_fill_queue(ListArgs a) {
             k += __popc(bal);
         });
     }
+}
+
+template <int T>
+__global__ void __launch_bounds__(128) k_list_fill_queue(ListArgs a) {
+    const Team<T> tm;
+    list_fill_queue_at<T>(a, blockIdx.x, gridDim.x, tm);
 }
 
 // ------------------------------------------------------ tiled list build --
@@ -558,10 +589,10 @@ __global__ void __launch_bounds__(128) k_list_tile_queue(ListArgs a) {
 constexpr int SORT_REG = 32;
 constexpr int SORT_SMEM = 1024;
 
-__global__ void k_list_sort_rev(int n, const uint32_t *off, const uint32_t *own,
-                                uint32_t *list, uint32_t cap, uint32_t *longq,
-                                uint32_t *nlong) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void list_sort_rev_at(int i, int n, const uint32_t *off,
+                                                 const uint32_t *own, uint32_t *list,
+                                                 uint32_t cap, uint32_t *longq,
+                                                 uint32_t *nlong) {
     if (i >= n) return;
     const uint32_t b = off[i] + (own ? own[i] : 0u), e = off[i + 1];
     if (e > cap || e <= b + 1) return;
@@ -588,14 +619,22 @@ __global__ void k_list_sort_rev(int n, const uint32_t *off, const uint32_t *own,
         if (t < (int)len) list[b + t] = r[t];
 }
 
-__global__ void k_list_sort_long(const uint32_t *off, const uint32_t *own,
-                                 uint32_t *list, const uint32_t *longq,
-                                 const uint32_t *nlong) {
+__global__ void k_list_sort_rev(int n, const uint32_t *off, const uint32_t *own,
+                                uint32_t *list, uint32_t cap, uint32_t *longq,
+                                uint32_t *nlong) {
+    list_sort_rev_at(blockIdx.x * blockDim.x + threadIdx.x, n, off, own, list, cap, longq,
+                     nlong);
+}
+
+__device__ __forceinline__ void list_sort_long_at(const uint32_t *off, const uint32_t *own,
+                                                  uint32_t *list, const uint32_t *longq,
+                                                  const uint32_t *nlong, uint32_t vb,
+                                                  uint32_t nvb) {
     __shared__ uint32_t buf[4][SORT_SMEM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t *s = buf[w];
     const uint32_t nq = *nlong;
-    const uint32_t gw = blockIdx.x * 4 + w, nw = gridDim.x * 4;
+    const uint32_t gw = vb * 4 + w, nw = nvb * 4;
     for (uint32_t q = gw; q < nq; q += nw) {
         const uint32_t i = longq[q];
         const uint32_t b = off[i] + (own ? own[i] : 0u), e = off[i + 1];
@@ -640,6 +679,60 @@ __global__ void k_list_sort_long(const uint32_t *off, const uint32_t *own,
     }
 }
 
+__global__ void k_list_sort_long(const uint32_t *off, const uint32_t *own,
+                                 uint32_t *list, const uint32_t *longq,
+                                 const uint32_t *nlong) {
+    list_sort_long_at(off, own, list, longq, nlong, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------- batched small builds ----
+// The single-instance bodies over the work items of several instances
+// (one item: one block of the instance's single-launch grid, or of a
+// smaller grid where the body's results do not depend on it).
+template <int T>
+__global__ void __launch_bounds__(128) k_list_gather_batch(const ListArgs *args, BatchSpan sp) {
+    const Team<T> tm;
+    for (int it = blockIdx.x; it < sp.total; it += gridDim.x) {
+        const BatchItem b = batch_item(sp, it);
+        const ListArgs &a = args[b.q];
+        const int i = b.vb * (128 / T) + (int)threadIdx.x / T;
+        if (i < a.n) list_gather_at<T>(a, i, tm);
+    }
+}
+template <int T>
+__global__ void __launch_bounds__(128) k_list_place_batch(const ListArgs *args, BatchSpan sp) {
+    const Team<T> tm;
+    for (int it = blockIdx.x; it < sp.total; it += gridDim.x) {
+        const BatchItem b = batch_item(sp, it);
+        const ListArgs &a = args[b.q];
+        const int i = b.vb * (128 / T) + (int)threadIdx.x / T;
+        if (i < a.n) list_place_at<T>(a, i, tm);
+    }
+}
+__global__ void __launch_bounds__(128) k_list_fill_queue_batch(const ListArgs *args, BatchSpan sp) {
+    const Team<16> tm;
+    for (int it = blockIdx.x; it < sp.total; it += gridDim.x) {
+        const BatchItem b = batch_item(sp, it);
+        list_fill_queue_at<16>(args[b.q], b.vb, b.nvb, tm);
+    }
+}
+__global__ void __launch_bounds__(256) k_list_sort_rev_batch(const SortSegRec *args, BatchSpan sp) {
+    for (int it = blockIdx.x; it < sp.total; it += gridDim.x) {
+        const BatchItem b = batch_item(sp, it);
+        const SortSegRec &r = args[b.q];
+        list_sort_rev_at(b.vb * 256 + (int)threadIdx.x, r.n, r.off, r.own, r.list, r.cap, r.longq,
+                         r.nlong);
+    }
+}
+__global__ void __launch_bounds__(128) k_list_sort_long_batch(const SortSegRec *args, BatchSpan sp) {
+    for (int it = blockIdx.x; it < sp.total; it += gridDim.x) {
+        const BatchItem b = batch_item(sp, it);
+        const SortSegRec &r = args[b.q];
+        list_sort_long_at(r.off, r.own, r.list, r.longq, r.nlong, b.vb, b.nvb);
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------- launchers --
 static inline int nblk_s(int n, int bs) { return (n + bs - 1) / bs; }
 
@@ -655,6 +748,18 @@ void sort_segments(cudaStream_t s, int n, const uint32_t *off, uint32_t *list,
 }
 static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
 
+void launch_pack_batch(cudaStream_t s, const PackArgs *args, const BatchSpan &sp,
+                       int blocks) {
+    if (sp.total > 0)
+        k_pack_batch<<<std::min(blocks, sp.total), BATCH_THREADS, 0, s>>>(args, sp);
+}
+int pack_batch_blocks_per_sm() {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pack_batch, BATCH_THREADS, 0) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return per_sm;
+}
 void launch_pack(cudaStream_t s, const PackArgs &a) {
     if (a.n > 0) k_pack<<<nblk(a.n, 256), 256, 0, s>>>(a);
 }
@@ -675,6 +780,51 @@ void launch_anchor_pack(cudaStream_t s, int n, const double *x,
 static int walk_kind(const ListArgs &a) {
     if (a.walk >= 1 && a.walk <= 3) return a.walk;
     return a.n < 12000 ? 1 : a.n < 60000 ? 2 : 3;
+}
+
+int list_walk_kind(const ListArgs &a) { return walk_kind(a); }
+int list_place_team(int n) { return std::max(team_size(n), 16); }
+int fill_queue_blocks() { return 4; }
+int sort_long_blocks(int n) { return std::max(1, std::min(8, nblk(n, 4))); }
+
+template <class K>
+static int batch_grid_of(K kernel, int threads, int total) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) !=
+            cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long long g = (long long)per_sm * gpu_sms();
+    return (int)(g < total ? g : total);
+}
+void launch_list_gather_batch(cudaStream_t s, int team, const ListArgs *args, const BatchSpan &sp) {
+    if (sp.total <= 0) return;
+    with_team_or(team, 1 << 30, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        static const int g = batch_grid_of(k_list_gather_batch<T>, 128, 1 << 30);
+        k_list_gather_batch<T><<<std::min(g, sp.total), 128, 0, s>>>(args, sp);
+    });
+}
+void launch_list_place_batch(cudaStream_t s, int team, const ListArgs *args, const BatchSpan &sp) {
+    if (sp.total <= 0) return;
+    with_team_or(team, 1 << 30, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        static const int g = batch_grid_of(k_list_place_batch<T>, 128, 1 << 30);
+        k_list_place_batch<T><<<std::min(g, sp.total), 128, 0, s>>>(args, sp);
+    });
+}
+void launch_list_fill_queue_batch(cudaStream_t s, const ListArgs *args, const BatchSpan &sp) {
+    static const int g = batch_grid_of(k_list_fill_queue_batch, 128, 1 << 30);
+    if (sp.total > 0) k_list_fill_queue_batch<<<std::min(g, sp.total), 128, 0, s>>>(args, sp);
+}
+void launch_list_sort_rev_batch(cudaStream_t s, const SortSegRec *args, const BatchSpan &sp) {
+    static const int g = batch_grid_of(k_list_sort_rev_batch, 256, 1 << 30);
+    if (sp.total > 0) k_list_sort_rev_batch<<<std::min(g, sp.total), 256, 0, s>>>(args, sp);
+}
+void launch_list_sort_long_batch(cudaStream_t s, const SortSegRec *args, const BatchSpan &sp) {
+    static const int g = batch_grid_of(k_list_sort_long_batch, 128, 1 << 30);
+    if (sp.total > 0) k_list_sort_long_batch<<<std::min(g, sp.total), 128, 0, s>>>(args, sp);
 }
 
 void launch_list_walk(cudaStream_t s, const ListArgs &a, int *launches) {

@@ -1,6 +1,7 @@
 // Argument blocks of the packing kernel and the neighbour-list build.
 #pragma once
 
+#include "batch.cuh"
 #include "neighbors.cuh"
 #include "sph_internal.cuh"
 
@@ -55,6 +56,35 @@ struct ListArgs {
 };
 
 void launch_pack(cudaStream_t s, const PackArgs &a);
+// packing over the work items of several instances (batched step); blocks:
+// the persistent grid (resident blocks per SM from the function below
+// times the SMs)
+void launch_pack_batch(cudaStream_t s, const PackArgs *args, const BatchSpan &sp,
+                       int blocks);
+int pack_batch_blocks_per_sm();
+
+// Batched builds of small sets (batched step): the per-particle team walk,
+// the placement, the queue walk and the segment sorts over the work items
+// of several instances (one item: one block of the instance's
+// single-launch grid; the queue walk and the long-segment sort take
+// fill_queue_blocks() and sort_long_blocks(n) items an instance, which
+// change no result).
+struct SortSegRec {
+    int n;
+    const uint32_t *off, *own;
+    uint32_t *list;
+    uint32_t cap;
+    uint32_t *longq, *nlong;
+};
+int list_walk_kind(const ListArgs &a);   // 1 team walk, 2 / 3 cell tiles
+int list_place_team(int n);              // lanes per particle of the placement
+int fill_queue_blocks();
+int sort_long_blocks(int n);
+void launch_list_gather_batch(cudaStream_t s, int team, const ListArgs *args, const BatchSpan &sp);
+void launch_list_place_batch(cudaStream_t s, int team, const ListArgs *args, const BatchSpan &sp);
+void launch_list_fill_queue_batch(cudaStream_t s, const ListArgs *args, const BatchSpan &sp);
+void launch_list_sort_rev_batch(cudaStream_t s, const SortSegRec *args, const BatchSpan &sp);
+void launch_list_sort_long_batch(cudaStream_t s, const SortSegRec *args, const BatchSpan &sp);
 void launch_anchor_pack(cudaStream_t s, int n, const double *x,
                         const double *y, const double *h, const double *lo,
                         const double *A, const Anchor &an, float4 *pk);

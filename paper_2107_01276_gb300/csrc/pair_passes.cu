@@ -7,6 +7,9 @@
 // float: mixed path); positions and the neighbour predicate stay FP64.
 #include <float.h>
 
+#include <algorithm>
+
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "lists.cuh"
 #include "neighbors.cuh"
@@ -45,11 +48,8 @@ __device__ __forceinline__ bool skin_member(const Domain &d, const Anchor &an,
 // records pass B gathers: {m, V = m/rho, rho, 1/(rho^2 beta)} and
 // {p, u, v, 1/h}.  A team of T threads shares particle i.
 template <typename R, int T>
-__global__ void __launch_bounds__(128)
-    k_pass_a(PassAArgs<R> a) {
-    const Team<T> tm;
-    const int i = Team<T>::particle();
-    if (i >= a.n) return;
+__device__ __forceinline__ void pass_a_at(const PassAArgs<R> &a, int i,
+                                          const Team<T> &tm) {
     Sep<R> sp;
     sp.init(a.d, a.x, a.y, a.pk, i);
     const R hi = (R)a.h[i];
@@ -171,6 +171,15 @@ __global__ void __launch_bounds__(128)
     a.nbB[i] = B;
 }
 
+template <typename R, int T>
+__global__ void __launch_bounds__(128)
+    k_pass_a(PassAArgs<R> a) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
+    if (i >= a.n) return;
+    pass_a_at<R, T>(a, i, tm);
+}
+
 // ---------------------------------------------------------------- pass B --
 // EDAC pressure rate (Eq. edac:sph) and momentum rate (Eq. mom-sph without
 // the A_i/A_j stresses and third line, unused per the paper's remark):
@@ -187,11 +196,8 @@ __global__ void __launch_bounds__(128)
 // sum, extrapolated velocity in the viscous sum, rho_w = rho0, beta_w = 1.
 // (float: at most 80 registers, six 128-thread blocks per SM)
 template <typename R, int T>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_B_BLOCKS : 1)
-    k_pass_b(PassBArgs<R> a) {
-    const Team<T> tm;
-    const int i = Team<T>::particle();
-    if (i >= a.n) return;
+__device__ __forceinline__ void pass_b_at(const PassBArgs<R> &a, int i,
+                                          const Team<T> &tm) {
     const R rb2i = a.rb2[i];
     const R beta_i = a.beta[i];
     if (beta_i == R(0)) {
@@ -337,16 +343,23 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_B_BLOCKS : 1)
         atomicOr(a.nonfinite, 1);
 }
 
+template <typename R, int T>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_B_BLOCKS : 1)
+    k_pass_b(PassBArgs<R> a) {
+    const Team<T> tm;
+    const int i = Team<T>::particle();
+    if (i >= a.n) return;
+    pass_b_at<R, T>(a, i, tm);
+}
+
 // --------------------------------------------------------- wall BC -----
 // Section 2.2 (Adami dummy walls), per wall particle w over fluid f with
 // W_wf = W(r_wf, (h_w + h_f)/2): u^ = sum u_f W / sum W (Eq. shepard),
 // u_ghost = 2 u_wall - u^ (Eq. bc-wall), p_w = sum p_f W / sum W (Eq.
 // bc-pre with g = a_w = 0); p_w = 0 and u^ = 0 without fluid in range.
 template <int T>
-__global__ void __launch_bounds__(128) k_wall_bc(WallBcArgs a) {
-    const Team<T> tm;
-    const int k = Team<T>::particle();
-    if (k >= a.w.n) return;
+__device__ __forceinline__ void wall_bc_at(const WallBcArgs &a, int k,
+                                           const Team<T> &tm) {
     const double xw = a.w.x[k], yw = a.w.y[k], hw = a.w.h[k];
     const float4 pw = a.w.pk[k];
     const float2 q = anchor_rel(a.an, pw);
@@ -386,6 +399,14 @@ __global__ void __launch_bounds__(128) k_wall_bc(WallBcArgs a) {
     a.pw[k] = p;
     a.ugx[k] = 2.0 * a.w.uw[k] - uh;
     a.ugy[k] = 2.0 * a.w.vw[k] - vh;
+}
+
+template <int T>
+__global__ void __launch_bounds__(128) k_wall_bc(WallBcArgs a) {
+    const Team<T> tm;
+    const int k = Team<T>::particle();
+    if (k >= a.w.n) return;
+    wall_bc_at<T>(a, k, tm);
 }
 
 // ------------------------------------------------------------ wall lists --
@@ -512,9 +533,7 @@ __global__ void k_nbr_ids(int n, const uint32_t *off, const uint32_t *list,
 // p' = p0 + f dt dp/dt, with f = 1/2 (predict) or 1 (correct); FP64,
 // explicitly rounded; periodic axes wrapped back into the box.
 template <typename R>
-__global__ void k_pec(PecArgs<R> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+__device__ __forceinline__ void pec_at(const PecArgs<R> &a, int i) {
     const double dt = *a.dt;
     const double fdt = __dmul_rn(a.f, dt);
     double x0, y0, u0, v0, p0;
@@ -565,6 +584,13 @@ __global__ void k_pec(PecArgs<R> a) {
     a.u[i] = un;
     a.v[i] = vn;
     a.p[i] = __dadd_rn(p0, __dmul_rn(fdt, (double)a.dpdt[i]));
+}
+
+template <typename R>
+__global__ void k_pec(PecArgs<R> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    pec_at<R>(a, i);
 }
 
 // ---------------------------------------------------------- time step ----
@@ -623,8 +649,145 @@ __global__ void k_float_to_double(int n, const float *src, double *dst) {
     if (i < n) dst[i] = (double)src[i];
 }
 
+// ------------------------------------------------------- batched phases --
+// One persistent launch per phase over the work items of several
+// instances (see BatchSpan): each block takes items with the grid's
+// stride, reads the owning instance's argument block and runs the same
+// per-particle body as the single-instance kernel, so an instance's
+// results do not depend on the batch it ran in.
+template <typename R, int T>
+__global__ void __launch_bounds__(BATCH_THREADS)
+    k_pass_a_batch(const PassAArgs<R> *__restrict__ args, BatchSpan sp) {
+    const Team<T> tm;
+    for (int item = blockIdx.x; item < sp.total; item += gridDim.x) {
+        const int q = sp.find(item);
+        const PassAArgs<R> &a = args[q];
+        const int i = (item - __ldg(&sp.first[q])) * batch_rows(T) + (int)threadIdx.x / T;
+        if (i < a.n) pass_a_at<R, T>(a, i, tm);
+    }
+}
+
+template <typename R, int T>
+__global__ void __launch_bounds__(BATCH_THREADS, sizeof(R) == 4 ? PASS_B_BLOCKS - 1 : 1)
+    k_pass_b_batch(const PassBArgs<R> *__restrict__ args, BatchSpan sp) {
+    const Team<T> tm;
+    for (int item = blockIdx.x; item < sp.total; item += gridDim.x) {
+        const int q = sp.find(item);
+        const PassBArgs<R> &a = args[q];
+        const int i = (item - __ldg(&sp.first[q])) * batch_rows(T) + (int)threadIdx.x / T;
+        if (i < a.n) pass_b_at<R, T>(a, i, tm);
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(BATCH_THREADS)
+    k_wall_bc_batch(const WallBcArgs *__restrict__ args, BatchSpan sp) {
+    const Team<T> tm;
+    for (int item = blockIdx.x; item < sp.total; item += gridDim.x) {
+        const int q = sp.find(item);
+        const WallBcArgs &a = args[q];
+        const int k = (item - __ldg(&sp.first[q])) * batch_rows(T) + (int)threadIdx.x / T;
+        if (k < a.w.n) wall_bc_at<T>(a, k, tm);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(BATCH_THREADS)
+    k_pec_batch(const PecArgs<R> *__restrict__ args, BatchSpan sp) {
+    for (int item = blockIdx.x; item < sp.total; item += gridDim.x) {
+        const int q = sp.find(item);
+        const PecArgs<R> &a = args[q];
+        const int i = (item - __ldg(&sp.first[q])) * BATCH_THREADS + (int)threadIdx.x;
+        if (i < a.n) pec_at<R>(a, i);
+    }
+}
+
+__global__ void __launch_bounds__(BATCH_THREADS)
+    k_rho_store_batch(const RhoStoreArgs *__restrict__ args, BatchSpan sp) {
+    for (int item = blockIdx.x; item < sp.total; item += gridDim.x) {
+        const int q = sp.find(item);
+        const RhoStoreArgs &a = args[q];
+        const int i = (item - __ldg(&sp.first[q])) * BATCH_THREADS + (int)threadIdx.x;
+        if (i < a.n) a.dst[i] = (double)a.src[i];
+    }
+}
+
 // ------------------------------------------------------------- launchers --
 static inline int nblk(int n, int bs) { return (n + bs - 1) / bs; }
+
+// Blocks of a persistent launch: what the GPU holds at once (resident
+// blocks per SM by the kernel's occupancy, times the SMs), at most one
+// per work item.
+int gpu_sms() {
+    static const int sms = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            v = 1;
+        return v > 0 ? v : 1;
+    }();
+    return sms;
+}
+template <class K>
+static int persistent_blocks(K kernel, int total) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BATCH_THREADS, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long g = (long long)per_sm * gpu_sms();
+    return (int)(g < total ? g : total);
+}
+
+template <typename R>
+void launch_pass_a_batch(cudaStream_t s, int team, const PassAArgs<R> *args,
+                         const BatchSpan &sp) {
+    if (sp.total <= 0) return;
+    with_team_or(team, 1 << 30, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        auto k = k_pass_a_batch<R, T>;
+        static const int g = persistent_blocks(k, 1 << 30);
+        k<<<std::min(g, sp.total), BATCH_THREADS, 0, s>>>(args, sp);
+    });
+}
+template <typename R>
+void launch_pass_b_batch(cudaStream_t s, int team, const PassBArgs<R> *args,
+                         const BatchSpan &sp) {
+    if (sp.total <= 0) return;
+    with_team_or(team, 1 << 30, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        auto k = k_pass_b_batch<R, T>;
+        static const int g = persistent_blocks(k, 1 << 30);
+        k<<<std::min(g, sp.total), BATCH_THREADS, 0, s>>>(args, sp);
+    });
+}
+void launch_wall_bc_batch(cudaStream_t s, int team, const WallBcArgs *args,
+                          const BatchSpan &sp) {
+    if (sp.total <= 0) return;
+    with_team_or(team, 1 << 30, [&](auto t) {
+        constexpr int T = decltype(t)::value;
+        auto k = k_wall_bc_batch<T>;
+        static const int g = persistent_blocks(k, 1 << 30);
+        k<<<std::min(g, sp.total), BATCH_THREADS, 0, s>>>(args, sp);
+    });
+}
+template <typename R>
+void launch_pec_batch(cudaStream_t s, const PecArgs<R> *args, const BatchSpan &sp) {
+    if (sp.total <= 0) return;
+    static const int g = persistent_blocks(k_pec_batch<R>, 1 << 30);
+    k_pec_batch<R><<<std::min(g, sp.total), BATCH_THREADS, 0, s>>>(args, sp);
+}
+void launch_rho_store_batch(cudaStream_t s, const RhoStoreArgs *args, const BatchSpan &sp) {
+    if (sp.total <= 0) return;
+    static const int g = persistent_blocks(k_rho_store_batch, 1 << 30);
+    k_rho_store_batch<<<std::min(g, sp.total), BATCH_THREADS, 0, s>>>(args, sp);
+}
+template void launch_pass_a_batch<float>(cudaStream_t, int, const PassAArgs<float> *, const BatchSpan &);
+template void launch_pass_a_batch<double>(cudaStream_t, int, const PassAArgs<double> *, const BatchSpan &);
+template void launch_pass_b_batch<float>(cudaStream_t, int, const PassBArgs<float> *, const BatchSpan &);
+template void launch_pass_b_batch<double>(cudaStream_t, int, const PassBArgs<double> *, const BatchSpan &);
+template void launch_pec_batch<float>(cudaStream_t, const PecArgs<float> *, const BatchSpan &);
+template void launch_pec_batch<double>(cudaStream_t, const PecArgs<double> *, const BatchSpan &);
 
 template <typename R>
 void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a, int team) {
@@ -705,10 +868,10 @@ void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,
     if (n > 0) k_nbr_ids<<<nblk(n, 128), 128, 0, s>>>(n, off, list, id, out);
 }
 // One block: h_min and the time step together (small sets).
-__global__ void __launch_bounds__(1024)
-    k_dt_small(int n, const double *__restrict__ h, double U, double cs,
-               double nu, unsigned long long *hmin_bits, double *dt,
-               double *tacc, int nsteps) {
+__device__ __forceinline__ void dt_small_at(int n, const double *__restrict__ h, double U,
+                                            double cs, double nu,
+                                            unsigned long long *hmin_bits, double *dt,
+                                            double *tacc, int nsteps) {
     __shared__ unsigned long long wm[32];
     unsigned long long m = ~0ull;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -729,10 +892,31 @@ __global__ void __launch_bounds__(1024)
     if (threadIdx.x == 0) k_dt_body(hmin_bits, U, cs, nu, dt, tacc, nsteps);
 }
 
+__global__ void __launch_bounds__(1024)
+    k_dt_small(int n, const double *__restrict__ h, double U, double cs,
+               double nu, unsigned long long *hmin_bits, double *dt,
+               double *tacc, int nsteps) {
+    dt_small_at(n, h, U, cs, nu, hmin_bits, dt, tacc, nsteps);
+}
+
+// The same for several small sets, one work item (block) each.
+__global__ void __launch_bounds__(1024) k_dt_small_batch(const DtSmallRec *args, BatchSpan sp) {
+    for (int it = blockIdx.x; it < sp.total; it += gridDim.x) {
+        const DtSmallRec &r = args[sp.find(it)];
+        dt_small_at(r.n, r.h, r.U, r.cs, r.nu, r.hmin_bits, r.dt, r.tacc, r.nsteps);
+        __syncthreads();
+    }
+}
+void launch_dt_small_batch(cudaStream_t s, const DtSmallRec *args, const BatchSpan &sp) {
+    if (sp.total > 0)
+        k_dt_small_batch<<<std::min(sp.total, 2 * gpu_sms()), 1024, 0, s>>>(args, sp);
+}
+int dt_small_max() { return 65536; }
+
 int launch_dt(cudaStream_t s, int n, const double *h,
               unsigned long long *hmin_bits, double U, double cs, double nu,
               double *dt, double *tacc, int nsteps) {
-    if (n <= 65536) {
+    if (n <= dt_small_max()) {
         k_dt_small<<<1, 1024, 0, s>>>(n, h, U, cs, nu, hmin_bits, dt, tacc, nsteps);
         return 1;
     }

@@ -2,6 +2,7 @@
 // time-step reduction (pair_passes.cu).
 #pragma once
 
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "neighbors.cuh"
 #include "sph_internal.cuh"
@@ -99,9 +100,34 @@ void launch_forces_total(cudaStream_t s, int nw, const double *fw,
 template <typename R> void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a,
                                          int team = 0);
 template <typename R> void launch_pec(cudaStream_t s, const PecArgs<R> &a);
+// batched phases: one persistent launch over the work items of several
+// instances (team: threads per particle, 1, 4, 16 or 32)
+template <typename R>
+void launch_pass_a_batch(cudaStream_t s, int team, const PassAArgs<R> *args,
+                         const BatchSpan &sp);
+template <typename R>
+void launch_pass_b_batch(cudaStream_t s, int team, const PassBArgs<R> *args,
+                         const BatchSpan &sp);
+void launch_wall_bc_batch(cudaStream_t s, int team, const WallBcArgs *args,
+                          const BatchSpan &sp);
+template <typename R>
+void launch_pec_batch(cudaStream_t s, const PecArgs<R> *args, const BatchSpan &sp);
+void launch_rho_store_batch(cudaStream_t s, const RhoStoreArgs *args, const BatchSpan &sp);
 void launch_nbr_ids(cudaStream_t s, int n, const uint32_t *off,
                     const uint32_t *list, const int64_t *id, int64_t *out);
 // Returns the number of kernels launched.
+// h_min and the time step of several small sets (n <= dt_small_max()), one
+// block each (batched step).
+struct DtSmallRec {
+    int n;
+    const double *h;
+    double U, cs, nu;
+    unsigned long long *hmin_bits;
+    double *dt, *tacc;
+    int nsteps;
+};
+void launch_dt_small_batch(cudaStream_t s, const DtSmallRec *args, const BatchSpan &sp);
+int dt_small_max();
 int launch_dt(cudaStream_t s, int n, const double *h,
                unsigned long long *hmin_bits, double U, double cs, double nu,
                double *dt, double *tacc, int nsteps);

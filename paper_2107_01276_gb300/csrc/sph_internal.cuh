@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/sph.h"
+#include "batch.cuh"
 
 namespace sph {
 
@@ -179,6 +180,68 @@ struct RebuildReset {
     uint32_t *zero[5];
 };
 void launch_rebuild_reset(cudaStream_t s, const RebuildReset &r, int *launches);
+int rebuild_reset_blocks(uint32_t tslots);   // its grid
+
+// Cell keys of one set (the keys kernel's arguments).
+struct KeysArgs {
+    Domain dom;
+    double c0, inv_c0;
+    int lmax, mbits;
+    Level lev[MAX_LEVELS];
+    double invw[MAX_LEVELS][2];   // 1 / w per level and axis (FP64)
+};
+struct KeysRec {
+    int n;
+    KeysArgs a;
+    const double *x, *y, *h;
+    uint64_t *skey;
+    uint32_t *perm, *level_mask;
+    int *bbox;
+    uint32_t *zero, *zero2, *zero3;   // per-particle counters zeroed (may be NULL)
+};
+KeysRec make_keys_rec(int n, const Domain &dom, double c0, int lmax, int mbits,
+                      const Level *lev, const double *x, const double *y,
+                      const double *h, uint64_t *skey, uint32_t *perm,
+                      uint32_t *level_mask, int *bbox, uint32_t *zero,
+                      uint32_t *zero2, uint32_t *zero3);
+
+// Batched builds of small sets (batched step): the single-block sort and
+// scan, and the per-particle kernels of a build, each as one launch over
+// the work items of several instances (BatchSpan; an item is one block of
+// the instance's single-launch grid).
+struct RadixSmallRec {
+    int n, passes;
+    uint64_t *ka;
+    uint32_t *va;
+    uint64_t *kb;
+    uint32_t *vb;
+};
+struct GatherInsertRec {
+    int n;
+    const uint32_t *perm;
+    GatherList g;
+    const uint64_t *skey;
+    uint64_t *tkey;
+    uint32_t *tstart;
+    uint32_t tmask;
+};
+struct ScanSmallRec {
+    const uint32_t *in;
+    uint32_t *rev, *out;
+    int n;
+    uint32_t *total_dev;
+    int write_total_at_n;
+};
+int radix_small_max();           // largest set the single-block sort takes
+bool radix_small_available();    // its shared-memory limit could be raised
+int scan_small_max();            // largest set the single-block scan takes
+void launch_rebuild_reset_batch(cudaStream_t s, const RebuildReset *args, const BatchSpan &sp);
+void launch_keys_batch(cudaStream_t s, const KeysRec *args, const BatchSpan &sp);
+// false (nothing launched) if the shared-memory limit cannot be raised
+bool launch_radix_small_batch(cudaStream_t s, const RadixSmallRec *args, const BatchSpan &sp,
+                              int max_n);
+void launch_gather_insert_batch(cudaStream_t s, const GatherInsertRec *args, const BatchSpan &sp);
+void launch_scan_small_batch(cudaStream_t s, const ScanSmallRec *args, const BatchSpan &sp);
 // cmin[start of each cell] = min of v over the cell (sorted set).
 void launch_cell_min(cudaStream_t s, int n, const uint64_t *skey,
                      const double *v, double *cmin, int *launches);

@@ -164,6 +164,19 @@ def lib(build_if_missing: bool = True):
     L.sph_cell_sort_noalloc.restype = ctypes.c_int
     L.sph_cell_sort_noalloc.argtypes = [P(Params), ctypes.c_longlong] + \
         [ctypes.c_void_p] * 6
+    L.sph_batch_create.restype = ctypes.c_int
+    L.sph_batch_create.argtypes = [ctypes.c_int, ctypes.c_void_p, P(ctypes.c_void_p)]
+    L.sph_batch_destroy.restype = ctypes.c_int
+    L.sph_batch_destroy.argtypes = [ctypes.c_void_p]
+    L.sph_batch_step.restype = ctypes.c_int
+    L.sph_batch_step.argtypes = [ctypes.c_void_p, P(ctypes.c_void_p), ctypes.c_int,
+                                 _D, P(ctypes.c_int)]
+    L.sph_batch_launches.restype = ctypes.c_longlong
+    L.sph_batch_launches.argtypes = [ctypes.c_void_p]
+    L.sph_batch_graph_steps.restype = ctypes.c_longlong
+    L.sph_batch_graph_steps.argtypes = [ctypes.c_void_p]
+    L.sph_batch_set_graphs.restype = ctypes.c_int
+    L.sph_batch_set_graphs.argtypes = [ctypes.c_void_p, ctypes.c_int]
     _lib = L
     return L
 
@@ -369,6 +382,67 @@ class Simulation:
         if self._ctx:
             self._L.sph_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Several simulations stepped together (sph_batch_*): each context's
+    neighbour build on its own stream, every per-particle phase as one
+    persistent launch over all of them on ``stream``."""
+
+    def __init__(self, max_instances: int, stream: int = 0):
+        self._L = lib()
+        self._b = ctypes.c_void_p()
+        st = self._L.sph_batch_create(int(max_instances), ctypes.c_void_p(int(stream)),
+                                      ctypes.byref(self._b))
+        if st != SPH_OK:
+            raise SphError(st, "sph_batch_create failed")
+        self.max_instances = int(max_instances)
+
+    def step(self, sims, want_time: bool = False):
+        """One PEC step of every Simulation in ``sims``; with want_time the
+        simulated times (one synchronisation)."""
+        k = len(sims)
+        arr = (ctypes.c_void_p * max(k, 1))(*[s._ctx.value for s in sims])
+        t = np.zeros(max(k, 1), np.float64)
+        failed = ctypes.c_int(-1)
+        st = self._L.sph_batch_step(self._b, arr, k,
+                                    t.ctypes.data_as(_D) if want_time else None,
+                                    ctypes.byref(failed))
+        if st != SPH_OK:
+            q = failed.value
+            msg = (self._L.sph_last_error(sims[q]._ctx).decode()
+                   if 0 <= q < k else "sph_batch_step failed")
+            raise SphError(st, msg)
+        return t[:k] if want_time else None
+
+    @property
+    def launches(self) -> int:
+        return int(self._L.sph_batch_launches(self._b))
+
+    @property
+    def graph_steps(self) -> int:
+        return int(self._L.sph_batch_graph_steps(self._b))
+
+    def set_graphs(self, enable: bool):
+        if self._L.sph_batch_set_graphs(self._b, int(bool(enable))) != SPH_OK:
+            raise SphError(SPH_EINVAL, "sph_batch_set_graphs failed")
+
+    def close(self):
+        if self._b:
+            self._L.sph_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
 
     def __del__(self):
         try:
