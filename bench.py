@@ -104,6 +104,16 @@ WORKLOADS = {
     # at Re in [50, 500]), Poisson arrivals at 20/s, served concurrently
     "serving": dict(kind="serving", requests=32, rate=20.0, slots=8,
                     steps=40, sizes=(5000, 50000)),
+    # the same stream of requests with the Taylor-Green half stepped
+    # together by the batch stepper (continuous batching of the steps)
+    "serving-batched": dict(kind="serving", requests=32, rate=20.0, slots=8,
+                            steps=40, sizes=(5000, 50000), batch=True),
+    # 32 resident Taylor-Green vortices (Re uniform in [50, 500], particle
+    # counts log-uniform in [1.6k, 20k]) advanced together by the batched
+    # step (one persistent launch per phase over all of them, replayed as
+    # a captured graph); compared with the same instances stepped one by
+    # one on their own streams
+    "batched-tg32": dict(kind="batch", instances=32, sizes=(1600, 20000)),
 }
 DEFAULT_WORKLOAD = "cylinder-re40"
 
@@ -293,10 +303,11 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    if WORKLOADS[args.workload]["kind"] == "serving":
+    if WORKLOADS[args.workload]["kind"] in ("serving", "batch"):
         print(json.dumps({"impl": "reference", "unavailable":
                           "the oracle runs one simulation at a time; the "
-                          "serving workload has no reference arm"}))
+                          "%s workload has no reference arm"
+                          % WORKLOADS[args.workload]["kind"]}))
         return 0
     d, desc = make_workload(args.workload)
     kind = WORKLOADS[args.workload]["kind"]
@@ -337,7 +348,7 @@ def serving_arm(args):
     w = WORKLOADS[args.workload]
     reqs = serve.c5_requests(n=w["requests"], rate=w["rate"],
                              seed=7 + rank, steps=w["steps"], sizes=w["sizes"])
-    srv = serve.Server(slots=w["slots"])
+    srv = serve.Server(slots=w["slots"], batch=w.get("batch", False))
     clk = ClockSampler(local)
     clk.start()
     rep = srv.run(reqs)
@@ -350,7 +361,8 @@ def serving_arm(args):
         "warmup": 0, "ms_per_step": rep["step_ms_p50"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32-pair/f64-state", "data": "synthetic",
-        "config": {"workload": "serving", "requests": w["requests"],
+        "config": {"workload": args.workload, "requests": w["requests"],
+                   "batched_steps": bool(w.get("batch", False)),
                    "arrival_rate_per_s": w["rate"], "slots": w["slots"],
                    "steps_per_request": w["steps"],
                    "particles": list(w["sizes"]),
@@ -365,6 +377,154 @@ def serving_arm(args):
         "e2e": {"value": rep["particle_steps_per_s"] * world,
                 "unit": "particle-steps/s", "h2d_bytes_per_step": None,
                 "d2h_bytes_per_step": None},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------ batched ----
+def batch_arm(args):
+    """Many small simulations advanced together by sph_batch_step.  value:
+    particle-steps of all instances per second over K timed batch steps
+    (CUDA events on the batch stream, L2 flushed between steps);
+    streams_value: the same instances stepped one by one with sph_step on
+    their own streams (host clock around K steps); e2e: every step loads
+    each instance from pinned host buffers, runs the batch step and reads
+    x, y, u, v, p back."""
+    import ctypes
+
+    import torch
+    from paper_2107_01276_gb300 import sph, workloads as wl
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sph.lib()
+    w = WORKLOADS[args.workload]
+    rng = np.random.default_rng(11 + rank)
+    lo, hi = np.log(w["sizes"][0]), np.log(w["sizes"][1])
+    nxs = [int(round(np.sqrt(np.exp(rng.uniform(lo, hi))))) for _ in range(w["instances"])]
+    Res = [float(rng.uniform(50.0, 500.0)) for _ in nxs]
+    bs = torch.cuda.Stream()
+    own = [torch.cuda.Stream() for _ in nxs]
+    sims, states = [], []
+    for nx, Re, st in zip(nxs, Res, own):
+        d = wl.taylor_green(nx=nx, Re=Re)
+        n = len(d["particles"]["x"])
+        P = sph.make_params(d["params"], precision=sph.SPH_MIXED, capacity=n)
+        sm = sph.Simulation(P, st.cuda_stream)
+        sm.load(d["particles"])
+        sims.append(sm)
+        states.append(d["particles"])
+    ntot = sum(sm.info()["n"] for sm in sims)
+    b = sph.Batch(len(sims), bs.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        b.step(sims)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    l0 = b.launches + sum(sm.info()["launches"] for sm in sims)
+    g0 = b.graph_steps
+    clk = ClockSampler(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(bs):
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(bs)
+            b.step(sims)
+            evs[k][1].record(bs)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    launches = b.launches + sum(sm.info()["launches"] for sm in sims) - l0
+    graph_steps = b.graph_steps - g0
+    ms = [a.elapsed_time(c) for a, c in evs]
+    tmax = torch.tensor([float(np.sum(ms))], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    value = world * ntot * K / (float(tmax.item()) / 1e3)
+    # the same instances, one sph_step each on its own stream
+    for _ in range(W):
+        for sm in sims:
+            sm.step(1, want_time=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        for sm in sims:
+            sm.step(1, want_time=False)
+    torch.cuda.synchronize()
+    streams_value = ntot * K / (time.perf_counter() - t0)
+    # e2e: pinned host state in, batch step, x, y, u, v, p out
+    fields_in = ("x", "y", "u", "v", "p", "rho", "m", "h")
+    keep, srcs, outs = [], [], []
+    h2d = d2h = 0
+    for sm, st0 in zip(sims, states):
+        n = len(st0["x"])
+        src = sph.Particles()
+        for k in fields_in:
+            t = torch.from_numpy(np.ascontiguousarray(st0[k], np.float64)).pin_memory()
+            keep.append(t)
+            setattr(src, k, ctypes.cast(t.data_ptr(), sph._D))
+            h2d += 8 * n
+        srcs.append((n, src))
+        outs.append({k: torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+                     for k in ("x", "y", "u", "v", "p")})
+
+    def e2e_step():
+        for sm, (n, src) in zip(sims, srcs):
+            sm.load_raw(sph.SPH_FLUID, n, src)
+        b.step(sims)
+        nb = 0
+        for sm, o in zip(sims, outs):
+            for k in o:
+                nb += 8 * sm.read_into(k, o[k])
+        return nb
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    ke = max(3, K // 2)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        d2h = e2e_step()
+    torch.cuda.synchronize()
+    e2e_val = world * ntot * ke / (time.perf_counter() - t0)
+    b.close()
+    for sm in sims:
+        sm.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+        "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-pair/f64-state",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "instances": len(sims),
+                   "particles_total": ntot,
+                   "particles_per_instance": [min(x * x for x in nxs), max(x * x for x in nxs)],
+                   "precision": "mixed", "l2": "flushed between steps (256 MiB write)",
+                   "desc": "Taylor-Green vortices, Re uniform [50, 500], periodic unit "
+                           "square, h/dx 1.2; one sph_batch_step per step"},
+        "streams_value": streams_value,
+        "batch_over_streams": value / streams_value,
+        "graph_steps": graph_steps,
+        "roofline": None,
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "cpu_baseline": None,
     }
     print(json.dumps(line))
     return 0
@@ -393,6 +553,8 @@ def main():
         return reference_arm(args)
     if WORKLOADS[args.workload]["kind"] == "serving":
         return serving_arm(args)
+    if WORKLOADS[args.workload]["kind"] == "batch":
+        return batch_arm(args)
 
     import ctypes
 

@@ -1945,7 +1945,6 @@ static void plan_small_build(sph_ctx *c, bool mid_step, float skin, bool with_dt
         B.dt.tacc = c->d_t;
         B.dt.nsteps = 1;
         c->have_dt = true;
-        c->launches += 1;
     }
     uint32_t t = 1;
     while (t < 2u * (uint32_t)n) t <<= 1;
@@ -2008,7 +2007,7 @@ static void plan_small_build(sph_ctx *c, bool mid_step, float skin, bool with_dt
     c->wall_lists_valid = false;
     c->grid_valid = true;
     c->rhs_valid = false;
-    c->launches += 11;   // as rebuild() counts this build
+    // (its launches are the batch's: sph_batch_launches counts them)
 }
 
 namespace {

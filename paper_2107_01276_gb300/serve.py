@@ -9,6 +9,12 @@ device.  As requests finish, their slots and memory go to waiting ones
 (continuous batching).  The report gives per-step latency percentiles
 beside the aggregate throughput.
 
+With batch=True the requests without adaptation step together instead:
+one BatchStepper thread advances all of them in flight by one
+sph_batch_step per tick (every per-particle phase of all of them in one
+persistent launch), members joining as they are admitted and leaving as
+they finish.
+
 Every step of every simulation runs in the library's kernels (sph.py is the
 binding); this module only schedules.  The ctypes calls release the GIL, so
 the workers drive their contexts concurrently.
@@ -47,6 +53,7 @@ class Request:
     precision: int = sph.SPH_MIXED
     capacity: int = 0             # 0: chosen from the workload
     bg_capacity: int = 0
+    team: int = 0                 # pass A / B threads per particle (0: size rule)
     # filled in by the server
     admitted: float = float("nan")
     finished: float = float("nan")
@@ -73,14 +80,17 @@ def estimate_bytes(req: Request) -> int:
     return int(total)
 
 
-def run_alone(req: Request, stream: int, keep_final: bool = True) -> Request:
-    """Run one request to completion on `stream` (the worker body)."""
+def _setup(req: Request, stream: int):
+    """The request's context with its sets loaded, background built and
+    initial refinement done."""
     d = req.workload
     cap = req.capacity or default_capacity(d)
     P = sph.make_params(d["params"], precision=req.precision, capacity=cap,
                         bg_capacity=req.bg_capacity)
     sim = sph.Simulation(P, stream)
     try:
+        if req.team:
+            sim.set_tuning(team_a=req.team, team_b=req.team)
         sim.load(d["particles"])
         if "walls" in d:
             sim.load(d["walls"], kind=sph.SPH_WALL)
@@ -92,6 +102,25 @@ def run_alone(req: Request, stream: int, keep_final: bool = True) -> Request:
                 sim.background()
         for _ in range(req.refine):
             sim.adapt()
+    except Exception:
+        sim.close()
+        raise
+    return sim
+
+
+def _finish(req: Request, sim, keep_final: bool):
+    if keep_final:
+        ids = sim.read("id")
+        order = np.argsort(ids)
+        req.final = {"id": ids[order]}
+        for f in ("x", "y", "u", "v", "p", "m", "h"):
+            req.final[f] = sim.read(f)[order]
+
+
+def run_alone(req: Request, stream: int, keep_final: bool = True) -> Request:
+    """Run one request to completion on `stream` (the worker body)."""
+    sim = _setup(req, stream)
+    try:
         for s in range(req.steps):
             t0 = time.perf_counter()
             if req.adapt_every and s % req.adapt_every == 0:
@@ -99,12 +128,85 @@ def run_alone(req: Request, stream: int, keep_final: bool = True) -> Request:
             sim.step(1, want_time=True)          # synchronises: step done
             req.step_ms.append(1e3 * (time.perf_counter() - t0))
             req.particle_steps += sim.info()["n"]
-        if keep_final:
-            ids = sim.read("id")
-            order = np.argsort(ids)
-            req.final = {"id": ids[order]}
-            for f in ("x", "y", "u", "v", "p", "m", "h"):
-                req.final[f] = sim.read(f)[order]
+        _finish(req, sim, keep_final)
+    finally:
+        sim.close()
+    return req
+
+
+class BatchStepper:
+    """Continuous batching of the steps themselves: simulations without
+    adaptation join one sph_batch_step per tick (every per-particle phase
+    of all of them in one persistent launch) as they are admitted, and
+    leave when their steps are done.  A step's latency is the tick's."""
+
+    def __init__(self, max_instances: int, stream: int):
+        self.batch = sph.Batch(max_instances, stream)
+        # members come and go, and the other workers allocate and
+        # synchronise while a graph would be captured: launch by launch
+        self.batch.set_graphs(False)
+        self.cv = threading.Condition()
+        self.members = []            # [sim, request, steps left, event, n]
+        self.stop = False
+        self.th = threading.Thread(target=self._loop, daemon=True)
+        self.th.start()
+
+    def advance(self, sim, req: Request):
+        """Blocks until `sim` has made req.steps steps in the batch."""
+        if req.steps <= 0:
+            return
+        ev = threading.Event()
+        with self.cv:
+            self.members.append([sim, req, req.steps, ev, sim.info()["n"]])
+            self.cv.notify_all()
+        ev.wait()
+        if req.error:
+            raise RuntimeError(req.error)
+
+    def _loop(self):
+        while True:
+            with self.cv:
+                while not self.members and not self.stop:
+                    self.cv.wait()
+                if not self.members:
+                    return
+                group = list(self.members)
+            t0 = time.perf_counter()
+            err = None
+            try:
+                self.batch.step([m[0] for m in group], want_time=True)
+            except Exception as e:            # every member fails
+                err = "%s: %s" % (type(e).__name__, e)
+            ms = 1e3 * (time.perf_counter() - t0)
+            with self.cv:
+                for m in group:
+                    if err:
+                        m[1].error = err
+                        m[2] = 0
+                    else:
+                        m[1].step_ms.append(ms)
+                        m[1].particle_steps += m[4]
+                        m[2] -= 1
+                    if m[2] <= 0:
+                        self.members.remove(m)
+                        m[3].set()
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify_all()
+        self.th.join()
+        self.batch.close()
+
+
+def run_batched(req: Request, stream: int, stepper: BatchStepper,
+                keep_final: bool = True) -> Request:
+    """A request without adaptation: set up on `stream`, stepped by the
+    batch stepper together with the others in flight."""
+    sim = _setup(req, stream)
+    try:
+        stepper.advance(sim, req)
+        _finish(req, sim, keep_final)
     finally:
         sim.close()
     return req
@@ -117,12 +219,15 @@ class Server:
     handed out; mem_info: callable returning (free, total) bytes (default
     torch.cuda.mem_get_info); runner: callable(request, stream) running one
     request (default run_alone); make_stream: callable returning a stream
-    handle for a worker (default: a new torch CUDA stream)."""
+    handle for a worker (default: a new torch CUDA stream); batch: requests
+    without adaptation step together through one BatchStepper (the others
+    run on their workers as before)."""
 
     def __init__(self, slots: int = 8, reserve: int = 2 << 30,
                  mem_info=None, runner=None, make_stream=None,
-                 keep_final: bool = False):
+                 keep_final: bool = False, batch: bool = False):
         self.slots = slots
+        self.batch = batch
         self.reserve = reserve
         self.keep_final = keep_final
         if mem_info is None:
@@ -156,11 +261,19 @@ class Server:
         cv = threading.Condition(self._lock)
         t_start = time.perf_counter()
 
+        stepper = None
+        if self.batch:
+            bstream = self.make_stream()
+            stepper = BatchStepper(self.slots, bstream[1])
+
         def worker(slot, req):
             t0 = time.perf_counter()
             req.admitted = t0 - t_start
             try:
-                self.runner(req, streams[slot][1])
+                if stepper is not None and not req.adapt_every:
+                    run_batched(req, streams[slot][1], stepper, self.keep_final)
+                else:
+                    self.runner(req, streams[slot][1])
             except Exception as e:            # reported, never fatal
                 req.error = "%s: %s" % (type(e).__name__, e)
             req.finished = time.perf_counter() - t_start
@@ -208,6 +321,8 @@ class Server:
                     cv.wait(timeout=wait if wait is not None else 0.5)
         for th in threads.values():
             th.join()
+        if stepper is not None:
+            stepper.close()
         wall = time.perf_counter() - t_start
         return self.report(requests, wall)
 

@@ -48,3 +48,29 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
     assert rep["steps"] == sum(r.steps for r in mix)
     assert 0 < rep["step_ms_p50"] <= rep["step_ms_p99"]
     assert rep["particle_steps_per_s"] > 0
+
+
+def test_batched_steps_match_alone():
+    """With batch=True the requests without adaptation step together
+    (sph_batch_step, joining and leaving as they are admitted and finish);
+    with their team sizes set, each ends bit for bit where it ends alone."""
+    def reqs():
+        return [
+            serve.Request(0, wl.taylor_green(nx=40, Re=100.0), 12, adapt_every=0, team=4),
+            serve.Request(1, wl.taylor_green(nx=70, Re=400.0), 20, adapt_every=0,
+                          arrival=0.02, team=4),
+            serve.Request(2, wl.gresho_chan(nx=40), 10, adapt_every=2, refine=2,
+                          arrival=0.01),
+            serve.Request(3, wl.taylor_green(nx=55, Re=250.0), 16, adapt_every=0,
+                          arrival=0.03, team=4),
+        ]
+    alone = [serve.run_alone(r, stream_handle()) for r in reqs()]
+    mix = reqs()
+    srv = serve.Server(slots=4, keep_final=True, batch=True)
+    rep = srv.run(mix)
+    assert rep["failed"] == 0, [r.error for r in mix]
+    for a, b in zip(alone, mix):
+        assert a.particle_steps == b.particle_steps
+        assert len(b.step_ms) == b.steps
+        for f, v in a.final.items():
+            assert np.array_equal(v, b.final[f]), (a.rid, f)
