@@ -436,6 +436,8 @@ def batch_arm(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.cudart().cudaProfilerStart()
     with torch.cuda.stream(bs):
         for k in range(K):
             flush.zero_()
@@ -443,6 +445,8 @@ def batch_arm(args):
             b.step(sims)
             evs[k][1].record(bs)
     torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.cudart().cudaProfilerStop()
     if dist:
         dist.barrier()
     clocks = clk.stop()

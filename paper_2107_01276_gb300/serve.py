@@ -140,8 +140,10 @@ class BatchStepper:
     of all of them in one persistent launch) as they are admitted, and
     leave when their steps are done.  A step's latency is the tick's."""
 
-    def __init__(self, max_instances: int, stream: int):
-        self.batch = sph.Batch(max_instances, stream)
+    def __init__(self, max_instances: int, stream: int, batch=None):
+        # batch: an object with step(sims, want_time), set_graphs(bool) and
+        # close() (default: a library sph.Batch)
+        self.batch = batch if batch is not None else sph.Batch(max_instances, stream)
         # members come and go, and the other workers allocate and
         # synchronise while a graph would be captured: launch by launch
         self.batch.set_graphs(False)

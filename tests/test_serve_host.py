@@ -90,3 +90,85 @@ def test_late_arrivals_join_while_others_run():
     # the late one was admitted before the early ones finished
     assert late.admitted < min(r.finished for r in early)
     assert late.admitted >= 0.02
+
+
+class FakeBatch:
+    """Records the members of every tick; fail_at: fails the ticks with
+    that many members."""
+
+    def __init__(self, fail_at=None):
+        self.ticks = []
+        self.fail_at = fail_at
+
+    def set_graphs(self, enable):
+        self.graphs = enable
+
+    def step(self, sims, want_time=False):
+        self.ticks.append([s.name for s in sims])
+        time.sleep(0.001)
+        if self.fail_at is not None and len(sims) == self.fail_at:
+            raise RuntimeError("device error")
+
+    def close(self):
+        self.closed = True
+
+
+class FakeSim:
+    def __init__(self, name, n):
+        self.name, self.n = name, n
+
+    def info(self):
+        return {"n": self.n}
+
+
+def test_batch_stepper_members_join_and_leave():
+    fb = FakeBatch()
+    st = serve.BatchStepper(4, 0, batch=fb)
+    reqs = [serve.Request(k, None, steps, adapt_every=0)
+            for k, steps in enumerate((6, 3, 9))]
+    sims = [FakeSim("s%d" % k, 100 * (k + 1)) for k in range(3)]
+
+    def run(k, delay):
+        time.sleep(delay)
+        st.advance(sims[k], reqs[k])
+
+    th = [threading.Thread(target=run, args=(k, 0.004 * k)) for k in range(3)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    st.close()
+    assert fb.closed and fb.graphs is False
+    for k, r in enumerate(reqs):
+        # one latency per step, every step in a tick of its own
+        assert len(r.step_ms) == r.steps
+        assert r.particle_steps == r.steps * sims[k].n
+        mine = [i for i, t in enumerate(fb.ticks) if sims[k].name in t]
+        assert len(mine) == r.steps
+        assert mine == list(range(mine[0], mine[0] + r.steps))   # consecutive
+    assert max(len(t) for t in fb.ticks) <= 3
+    assert sum(len(t) for t in fb.ticks) == 18
+
+
+def test_batch_stepper_failure_reaches_every_member():
+    fb = FakeBatch(fail_at=2)
+    st = serve.BatchStepper(4, 0, batch=fb)
+    # long enough that the second member joins while the first runs
+    reqs = [serve.Request(k, None, 2000, adapt_every=0) for k in range(2)]
+    sims = [FakeSim("a", 10), FakeSim("b", 20)]
+    errs = []
+
+    def run(k):
+        try:
+            st.advance(sims[k], reqs[k])
+        except RuntimeError as e:
+            errs.append(str(e))
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    st.close()
+    assert len(errs) == 2 and all("device error" in e for e in errs)
+    assert all(r.error for r in reqs)
