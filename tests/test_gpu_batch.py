@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2107_01276_gb300 import sph
 from paper_2107_01276_gb300 import workloads as wl
 from tests.helpers import by_id, cuda_ok
@@ -169,3 +170,39 @@ def test_batch_argument_errors_change_nothing():
     assert s1.info()["steps"] == 0
     for s in (s1, s2, empty):
         s.close()
+
+
+def _oracle_after(d, steps):
+    P = oracle.params(**d["params"])
+    st = oracle.make_state(d["particles"])
+    t = oracle.step(P, st, steps)
+    return t, st
+
+
+def test_batched_steps_match_the_oracle():
+    """Ten batched PEC steps of three jittered Taylor-Green vortices (two
+    mixed, one FP64; the batch's own team sizes) against the oracle's ten
+    steps of each, with the single-instance step test's bounds: 1e-4
+    (mixed) and 1e-10 (FP64) of each field's magnitude, positions of dx."""
+    cases = [(wl.taylor_green(nx=32, jitter=0.1, seed=2, Re=100), sph.SPH_MIXED, 1e-4),
+             (wl.taylor_green(nx=32, jitter=0.1, seed=2, Re=100), sph.SPH_FP64, 1e-10),
+             (wl.taylor_green(nx=24, jitter=0.1, seed=4, Re=200), sph.SPH_MIXED, 1e-4)]
+    bs = torch.cuda.Stream()
+    sims = [_make(d, p, bs.cuda_stream) for d, p, _ in cases]
+    with sph.Batch(len(sims), bs.cuda_stream) as b:
+        t = None
+        for _ in range(10):
+            t = b.step(sims, want_time=True)
+    for q, ((d, prec, tol), sm) in enumerate(zip(cases, sims)):
+        tr, st = _oracle_after(d, 10)
+        assert abs(t[q] - tr) <= 1e-15 * tr, q
+        got = by_id(sm, ["x", "y", "u", "v", "p", "rho"])
+        n = st["n"]
+        for f in ("x", "y"):
+            dxy = got[f] - st[f][:n]
+            dxy -= np.round(dxy)                 # unit periodic square
+            assert np.abs(dxy).max() <= tol * d["dx"], (q, f)
+        for f in ("u", "v", "p", "rho"):
+            scale = max(np.abs(st[f][:n]).max(), 1e-30)
+            assert np.abs(got[f] - st[f][:n]).max() <= tol * scale, (q, f)
+        sm.close()
