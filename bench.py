@@ -216,6 +216,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_totals(dist, time_s, units, device="cuda"):
+    """Whole-job totals of a replica run: the slowest rank's time and the
+    units all ranks processed (all_gather over the process group; the
+    local values without one)."""
+    if dist is None:
+        return float(time_s), float(units)
+    import torch
+    my = torch.tensor([float(time_s), float(units)], dtype=torch.float64,
+                      device=device)
+    t_all = [torch.zeros_like(my) for _ in range(dist.get_world_size())]
+    dist.all_gather(t_all, my)
+    return max(float(t[0]) for t in t_all), sum(float(t[1]) for t in t_all)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -344,6 +358,10 @@ def serving_arm(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     sph.lib()
     w = WORKLOADS[args.workload]
     reqs = serve.c5_requests(n=w["requests"], rate=w["rate"],
@@ -353,10 +371,16 @@ def serving_arm(args):
     clk.start()
     rep = srv.run(reqs)
     clocks = clk.stop()
+    # every rank serves its own stream: the particle-steps of all ranks
+    # over the slowest rank's wall time
+    wall, units = replica_totals(dist, rep["wall_s"], rep["particle_steps"])
+    value = units / wall if wall > 0 else 0.0
+    if dist:
+        dist.destroy_process_group()
     if rank != 0:
         return 0
     line = {
-        "metric": "particle-steps/s", "value": rep["particle_steps_per_s"] * world,
+        "metric": "particle-steps/s", "value": value,
         "unit": "particle-steps/s", "n_gpus": world, "steps": rep["steps"],
         "warmup": 0, "ms_per_step": rep["step_ms_p50"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -374,7 +398,7 @@ def serving_arm(args):
         "latency_ms": {"p50": rep["step_ms_p50"], "p99": rep["step_ms_p99"]},
         "serving": rep,
         "clocks": clocks,
-        "e2e": {"value": rep["particle_steps_per_s"] * world,
+        "e2e": {"value": value,
                 "unit": "particle-steps/s", "h2d_bytes_per_step": None,
                 "d2h_bytes_per_step": None},
     }
@@ -453,10 +477,8 @@ def batch_arm(args):
     launches = b.launches + sum(sm.info()["launches"] for sm in sims) - l0
     graph_steps = b.graph_steps - g0
     ms = [a.elapsed_time(c) for a, c in evs]
-    tmax = torch.tensor([float(np.sum(ms))], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    value = world * ntot * K / (float(tmax.item()) / 1e3)
+    tmax, units = replica_totals(dist, float(np.sum(ms)), ntot * K)
+    value = units / (tmax / 1e3)
     # the same instances, one sph_step each on its own stream
     for _ in range(W):
         for sm in sims:
@@ -506,6 +528,8 @@ def batch_arm(args):
     b.close()
     for sm in sims:
         sm.close()
+    if dist:
+        dist.destroy_process_group()
     if rank != 0:
         return 0
     line = {
@@ -662,15 +686,7 @@ def main():
     k_breakdown = max(5, args.steps // 4)
     _, _, fams, _ = timed_steps(sim, k_breakdown, 1, lib_timing=True)
     tot_ms = float(np.sum(ms))
-    my = torch.tensor([tot_ms, float(np.sum(ns))], dtype=torch.float64,
-                      device="cuda")
-    if dist:
-        t_all = [torch.zeros_like(my) for _ in range(world)]
-        dist.all_gather(t_all, my)
-        tmax = max(float(t[0]) for t in t_all)
-        units = sum(float(t[1]) for t in t_all)
-    else:
-        tmax, units = tot_ms, float(np.sum(ns))
+    tmax, units = replica_totals(dist, tot_ms, float(np.sum(ns)))
     value = units / (tmax / 1e3)
 
     # force on the body after the timed steps (Eq. force-sph, Eq. cdcl);
