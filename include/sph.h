@@ -246,8 +246,15 @@ sph_status sph_batch_destroy(sph_batch *batch);
  * mid-step packing of SPH_MIXED contexts, the density store) runs on the
  * batch's stream as ONE persistent launch over all contexts that share a
  * precision and a team size, its work list made of (context, block of
- * particles) items; SPH_FP64 contexts rebuild mid-step on their streams.
- * Each context's results equal those of sph_step on it alone, bit for bit.
+ * particles) items.  The neighbour build of a context with at most 16384
+ * particles, no wall lists and list sizes known from earlier builds runs
+ * batched the same way (one launch per kernel of the build); other
+ * contexts build on their own streams (SPH_FP64 contexts also mid-step).
+ * Pass A / B thread-team sizes are those set by sph_set_tuning, else the
+ * size rule applied to the batch's total particle count of that
+ * precision; with the team sizes a context uses alone, its results equal
+ * those of sph_step on it alone bit for bit (otherwise they differ by the
+ * order of the pair sums).
  * The contexts' streams wait for the batch's launches before their next
  * work.  t_out (NULL or k entries) receives each context's simulated time
  * and makes the call synchronise and report the checks sph_step reports.
