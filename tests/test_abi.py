@@ -65,3 +65,21 @@ def test_null_and_invalid_arguments_rejected_without_gpu():
         sph.SPH_EINVAL
     assert L.sph_rhs(None) == sph.SPH_EINVAL
     assert L.sph_destroy(None) == sph.SPH_EINVAL
+
+
+def test_batch_arguments_rejected_without_gpu():
+    """The batched step's argument checks come before any CUDA call."""
+    L = sph.lib()
+    out = ctypes.c_void_p(123)
+    assert L.sph_batch_create(0, None, ctypes.byref(out)) == sph.SPH_EINVAL
+    assert out.value is None                     # *out cleared on error
+    assert L.sph_batch_create(1 << 21, None, ctypes.byref(out)) == sph.SPH_EINVAL
+    assert L.sph_batch_create(4, None, None) == sph.SPH_EINVAL
+    failed = ctypes.c_int(7)
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.sph_batch_step(None, arr, 1, None, ctypes.byref(failed)) == sph.SPH_EINVAL
+    assert failed.value == -1
+    assert L.sph_batch_destroy(None) == sph.SPH_EINVAL
+    assert L.sph_batch_launches(None) == -1
+    assert L.sph_batch_graph_steps(None) == -1
+    assert L.sph_batch_set_graphs(None, 1) == sph.SPH_EINVAL
