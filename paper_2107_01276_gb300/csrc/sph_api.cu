@@ -1662,13 +1662,14 @@ static bool graph_step(sph_ctx *c, sph_status *st) {
 }
 
 // ============================================================ batches ==
-// Several independent simulations advance one PEC step together: each
-// instance's neighbour build runs on its own stream, and every
+// Several independent simulations advance one PEC step together.  Every
 // per-particle phase of the step runs on the batch's stream as one
 // persistent launch over the work items of all instances that share a
-// precision and a team size (see BatchSpan).  The per-particle bodies are
-// those of the single-instance kernels, so each instance's results equal
-// those of sph_step on it alone.
+// precision and a team size (see BatchSpan), and so does the whole
+// neighbour build of the small sets whose list sizes are known; the other
+// instances build on their own streams.  The bodies are those of the
+// single-instance kernels, so with the team sizes an instance uses alone
+// its results equal those of sph_step on it alone.
 struct sph_batch {
     cudaStream_t s = nullptr;
     int cap = 0;                   // instances per call
