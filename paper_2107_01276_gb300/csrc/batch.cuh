@@ -1,11 +1,12 @@
 // Work lists of the batched step: several independent simulations advance
 // together, each per-particle phase (wall conditions, pass A, pass B, the
-// PEC stages, the mid-step packing, the density store) as one persistent
-// launch over all of them.  A work item is one block's worth of particles
-// of one instance; instance q owns items first[q] .. first[q + 1] - 1, and
-// its argument block is args[q] in device memory.  The blocks of a launch
-// step through the items with the grid's stride, so uneven instances share
-// the SMs in proportion to their particle counts.
+// PEC stages, the mid-step packing, the density store) and each kernel of
+// a small set's neighbour build as one persistent launch over all of them.
+// A work item is one block of one instance's single-launch grid; instance
+// q owns items first[q] .. first[q + 1] - 1, and its argument block is
+// args[q] in device memory.  The blocks of a launch step through the items
+// with the grid's stride, so uneven instances share the SMs in proportion
+// to their work.
 #pragma once
 
 #include <cuda_runtime.h>
