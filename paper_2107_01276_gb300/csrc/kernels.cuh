@@ -9,22 +9,26 @@ namespace sph {
 // Quintic spline in q (section 2, Eq. kernel) without sigma2, and its
 // q-derivative, branch free: with a = max(3 - q, 0), b = max(2 - q, 0),
 // c = max(1 - q, 0), w = a^5 - 6 b^5 + 15 c^5 and dw/dq = -5 a^4 + 30 b^4
-// - 75 c^4 (every term vanishes where its base is clipped to zero).
+// - 75 c^4 (every term vanishes where its base is clipped to zero).  The
+// clip is one max instruction (a NaN q clips to zero).
 // sigma2 = 7 / (478 pi h^2); dW/dr = sigma2 / h * dw(q).
+__device__ __forceinline__ float clip0(float t) { return fmaxf(t, 0.0f); }
+__device__ __forceinline__ double clip0(double t) { return fmax(t, 0.0); }
+
 template <typename R>
 __device__ __forceinline__ R qs_w(R q) {
-    const R a = q < R(3) ? R(3) - q : R(0);
-    const R b = q < R(2) ? R(2) - q : R(0);
-    const R c = q < R(1) ? R(1) - q : R(0);
+    const R a = clip0(R(3) - q);
+    const R b = clip0(R(2) - q);
+    const R c = clip0(R(1) - q);
     const R a2 = a * a, b2 = b * b, c2 = c * c;
     return a2 * a2 * a - R(6) * (b2 * b2 * b) + R(15) * (c2 * c2 * c);
 }
 
 template <typename R>
 __device__ __forceinline__ R qs_dw(R q) {
-    const R a = q < R(3) ? R(3) - q : R(0);
-    const R b = q < R(2) ? R(2) - q : R(0);
-    const R c = q < R(1) ? R(1) - q : R(0);
+    const R a = clip0(R(3) - q);
+    const R b = clip0(R(2) - q);
+    const R c = clip0(R(1) - q);
     const R a2 = a * a, b2 = b * b, c2 = c * c;
     return R(-5) * (a2 * a2) + R(30) * (b2 * b2) - R(75) * (c2 * c2);
 }

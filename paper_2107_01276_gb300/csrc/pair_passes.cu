@@ -13,166 +13,30 @@
 #include "kernels.cuh"
 #include "lists.cuh"
 #include "neighbors.cuh"
+#include "pair_lanes.cuh"
 #include "pair_passes.cuh"
 #include "team.cuh"
 
 namespace sph {
 
-// List entries whose neighbour records a mixed-path pass loads ahead.
-constexpr int UNROLL_A = 2;
-constexpr int UNROLL_B = 2;
+constexpr int PASS_A_BLOCKS = 6;   // resident blocks of mixed pass A
 constexpr int PASS_B_BLOCKS = 6;   // resident blocks of mixed pass B
 
-// Membership test of a list entry when the lists carry a skin: the exact
-// predicate of N(i) on the separation the pass already has (FP32 band test
-// with the FP64 predicate inside the band on the mixed path; the FP64
-// predicate on the FP64 path).
-template <typename R>
-__device__ __forceinline__ bool skin_member(const Domain &d, const Anchor &an,
-                                            R r2, R hi, R hj, double xi,
-                                            double yi, double hid,
-                                            const double *x, const double *y,
-                                            const double *h, int j) {
-    if constexpr (sizeof(R) == 4) {
-        return member_r2(d, an, r2, hi, hj, xi, yi, hid, x, y, h, j);
-    } else {
-        return pred_fp64(d, xi, yi, hid, __ldg(&x[j]), __ldg(&y[j]), __ldg(&h[j]));
-    }
-}
-
 // ---------------------------------------------------------------- pass A --
-// Summation density (Eq. sd-gather), beta (Eq. beta), p_avg (Eq. pavg,
-// N_i counts i), shift dr (Eq. shift-deltar, volume m_j / rho0, W ratio
-// against the kernel at its inflection point for h_ij = (h_i + h_j)/2),
-// limited to 0.25 h_i (Eq. shift-limit).  Also writes the two per-particle
-// records pass B gathers: {m, V = m/rho, rho, 1/(rho^2 beta)} and
-// {p, u, v, 1/h}.  A team of T threads shares particle i.
+// Pass A of particle i over its list (arithmetic in PassALane): a team of T
+// threads shares particle i.
 template <typename R, int T>
 __device__ __forceinline__ void pass_a_at(const PassAArgs<R> &a, int i,
                                           const Team<T> &tm) {
-    Sep<R> sp;
-    sp.init(a.d, a.x, a.y, a.pk, i);
-    const R hi = (R)a.h[i];
-    const R hinv = R(1) / hi;
-    const R inv_wxi = R(1) / qs_w<R>(R(XI_INFLECTION));
-    R rho = 0, srw = 0, psum = 0, ax = 0, ay = 0;
-    int cnt = 0;
-    auto pair = [&](R mj, R hj, R pj, bool self, R dx, R dy, R r2) {
-        const R rinv = r2 > R(0) ? frsqrt(r2) : R(0);
-        const R r = r2 * rinv;
-        const R q = r * hinv;
-        rho += mj * qs_w<R>(q);
-        srw += mj * r * qs_dw<R>(q);
-        psum += pj;
-        cnt += 1;
-        if (!self && r > R(0)) {
-            const R hbinv = fdiv(R(2), hi + hj);
-            const R qb = r * hbinv;
-            R ratio = qs_w<R>(qb) * inv_wxi;
-            ratio *= ratio;
-            const R f = mj * (R(1) + R(0.24) * ratio * ratio) *
-                        (sigma_norm<R>() * hbinv * hbinv * hbinv) *
-                        qs_dw<R>(qb) * rinv;
-            ax += f * dx;
-            ay += f * dy;
-        }
-    };
-    const uint32_t b = a.off[i], e = a.off[i + 1];
-    const double xid = a.x[i], yid = a.y[i], hid = a.h[i];
-    if constexpr (sizeof(R) == 4) {
-        // U list entries per step, their records loaded before any is used
-        // (more loads in flight per warp)
-        auto body = [&](int j, const float4 &pj, R mj, R pjv) {
-            R dx, dy;
-            anchor_sep(a.an, sp.pi, pj, dx, dy);
-            const R r2 = fmaf(dx, dx, dy * dy);
-            if (a.filter && !skin_member<R>(a.d, a.an, r2, hi, pj.z, xid, yid,
-                                            hid, a.x, a.y, a.h, j))
-                return;
-            pair(mj, pj.z, pjv, j == i, dx, dy, r2);
-        };
-        constexpr int U = UNROLL_A;
-        uint32_t k = b + tm.lane;
-        for (; k + (U - 1) * T < e; k += U * T) {
-            int jj[U];
-            float4 pp[U];
-            R mm[U], qq[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) jj[u] = (int)__ldg(&a.list[k + u * T]);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                pp[u] = __ldg(&a.pk[jj[u]]);
-                mm[u] = a.m[jj[u]];
-                qq[u] = a.p[jj[u]];
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) body(jj[u], pp[u], mm[u], qq[u]);
-        }
-        for (; k < e; k += T) {
-            const int j = (int)__ldg(&a.list[k]);
-            body(j, __ldg(&a.pk[j]), a.m[j], a.p[j]);
-        }
-    } else {
-        for (uint32_t k = b + tm.lane; k < e; k += T) {
-            const int j = (int)__ldg(&a.list[k]);
-            R dx, dy, r2, hj;
-            sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
-            if (a.filter && !skin_member<R>(a.d, a.an, r2, hi, hj, xid, yid, hid,
-                                            a.x, a.y, a.h, j))
-                continue;
-            pair(a.m[j], hj, a.p[j], j == i, dx, dy, r2);
-        }
-    }
-    if (a.w.n > 0) {
-        for_each_wall<T>(a.w, i, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane, tm.mask,
-                      [&](int k, double dxd, double dyd, double r2d) {
-            pair((R)a.w.m[k], (R)a.w.h[k], (R)a.w.p[k], false, (R)dxd,
-                 (R)dyd, (R)r2d);
-        });
-    }
-    rho = team_sum<T>(tm.mask, rho);
-    srw = team_sum<T>(tm.mask, srw);
-    psum = team_sum<T>(tm.mask, psum);
-    ax = team_sum<T>(tm.mask, ax);
-    ay = team_sum<T>(tm.mask, ay);
-    cnt = team_sum<T>(tm.mask, cnt);
-    if (tm.lane != 0) return;
-    const R sig = sigma_norm<R>() * hinv * hinv;
-    rho *= sig;
-    const R beta = -(sig * hinv * srw) / (rho * R(2));
-    R drx = R(0), dry = R(0);
-    if (beta != R(0)) {
-        const R c = R(-0.5) * hi * hi / (R)a.rho0;
-        drx = c * ax;
-        dry = c * ay;
-    }
-    const R mag = sqrt(drx * drx + dry * dry);
-    const R lim = R(0.25) * hi;
-    if (mag > lim) {
-        const R th = lim / mag;
-        drx *= th;
-        dry *= th;
-    }
-    const R mi = a.m[i];
-    const R V = mi / rho;
-    const R rb2 = beta != R(0) ? R(1) / (rho * rho * beta) : R(0);
-    a.rho[i] = rho;
-    a.beta[i] = beta;
-    a.pavg[i] = psum / (R)cnt;
-    a.nnb[i] = cnt;
-    a.drx[i] = drx;
-    a.dry[i] = dry;
-    a.V[i] = V;
-    a.rb2[i] = rb2;
-    typename V4<R>::T A, B;
-    A.x = mi; A.y = V; A.z = rho; A.w = rb2;
-    B.x = a.p[i]; B.y = a.u[i]; B.z = a.v[i]; B.w = hinv;
-    a.nbA[i] = A;
-    a.nbB[i] = B;
+    PassALane<R> L;
+    L.init(a, i);
+    pass_a_list<R, T>(a, i, L, tm, a.off[i], a.off[i + 1]);
+    L.walls(a, i, tm);
+    L.finish(a, i, tm);
 }
 
 template <typename R, int T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_A_BLOCKS : 1)
     k_pass_a(PassAArgs<R> a) {
     const Team<T> tm;
     const int i = Team<T>::particle();
@@ -181,26 +45,13 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---------------------------------------------------------------- pass B --
-// EDAC pressure rate (Eq. edac:sph) and momentum rate (Eq. mom-sph without
-// the A_i/A_j stresses and third line, unused per the paper's remark):
-//   dp/dt = rho0 c^2/beta_i sum V_j u_ij.gW_i
-//         + 1/beta_i sum V_j nu_ij (p_i - p_j) r_ij.gW_ij / (r^2 + eta)
-//         + rho_i sum m_j (dr_i/dt).(P_i gW_i + P_j gW_j)
-//   du/dt = -sum m_j (P_i gW_i + P_j gW_j)
-//         + 1/beta_i sum m_j 4 nu/(rho_i + rho_j) r_ij.gW_ij/(r^2 + eta) u_ij
-// gW_i = grad W(r_ij, h_i), gW_ij the mean of gW_i and gW_j (Eq. dw-avg),
-// nu_ij the Cleary mean 4 nu_i nu_j/(nu_i + nu_j) of nu_e = alpha_e c h / 8
-// (Eqs. edac-alpha, nu-cleary), which equals (alpha_e c / 2) / (1/h_i +
-// 1/h_j); eta = 0.001 h_i^2, P_j = (p_j - p_avg,i) / (rho_j^2 beta_j).
-// Wall neighbours (section 2.2): prescribed wall velocity in the divergence
-// sum, extrapolated velocity in the viscous sum, rho_w = rho0, beta_w = 1.
+// Pass B of particle i over its list (arithmetic in PassBLane).
 // (float: at most 80 registers, six 128-thread blocks per SM)
 template <typename R, int T>
 __device__ __forceinline__ void pass_b_at(const PassBArgs<R> &a, int i,
                                           const Team<T> &tm) {
-    const R rb2i = a.rb2[i];
-    const R beta_i = a.beta[i];
-    if (beta_i == R(0)) {
+    PassBLane<R> L;
+    if (!L.init(a, i)) {
         if (tm.lane == 0) {
             a.dpdt[i] = R(0);
             a.dudt[i] = R(0);
@@ -208,139 +59,9 @@ __device__ __forceinline__ void pass_b_at(const PassBArgs<R> &a, int i,
         }
         return;
     }
-    Sep<R> sp;
-    sp.init(a.d, a.x, a.y, a.pk, i);
-    const typename V4<R>::T Bi = a.nbB[i];
-    const R hinv = Bi.w;
-    const R dsig_i = sigma_norm<R>() * hinv * hinv * hinv;
-    const R rho_i = a.rho[i], pi = Bi.x, ui = Bi.y, vi = Bi.z;
-    const R pavg_i = a.pavg[i];
-    const R Pi = (pi - pavg_i) * rb2i;
-    const R half_ac = R(0.5) * (R)a.alpha_e * (R)a.cs;   // 4 nu_e,i nu_e,j / (..) numerator
-    const R hi = R(1) / hinv;
-    const R eta = R(0.001) * hi * hi;
-    const double dt = *a.dt;
-    const R dux = (R)((double)a.drx[i] / dt), duy = (R)((double)a.dry[i] / dt);
-    const R four_nu = R(4) * (R)a.nu;
-    const bool dden_on = a.diff_denominator != 0;
-    R div = 0, diff = 0, tvf = 0, fax = 0, fay = 0, vx = 0, vy = 0;
-    // one neighbour's contributions; (ujx, ujy): velocity in the divergence
-    // sum, (ugx, ugy): velocity in the viscous sum
-    auto pair = [&](R dx, R dy, R r2, R hjinv, R mj, R Vj, R rho_j, R Pj,
-                    R pj, R ujx, R ujy, R ugx, R ugy) {
-        R gi = 0, gj = 0;
-        if (r2 > R(0)) {
-            const R rinv = frsqrt(r2);
-            const R r = r2 * rinv;
-            gi = dsig_i * qs_dw<R>(r * hinv) * rinv;
-            gj = sigma_norm<R>() * hjinv * hjinv * hjinv *
-                 qs_dw<R>(r * hjinv) * rinv;
-        }
-        const R rdg = R(0.5) * (gi + gj) * r2;
-        const R nu_ij = fdiv(half_ac, hinv + hjinv);
-        const R inv_reta = fdiv(R(1), r2 + eta);
-        const R uij = ui - ujx, vij = vi - ujy;
-        div += Vj * gi * (uij * dx + vij * dy);
-        diff += Vj * nu_ij * (pi - pj) * rdg * (dden_on ? inv_reta : R(1));
-        const R fp = Pi * gi + Pj * gj;
-        const R fx = fp * dx, fy = fp * dy;
-        tvf += mj * (dux * fx + duy * fy);
-        fax -= mj * fx;
-        fay -= mj * fy;
-        const R visc = fdiv(mj * four_nu * rdg * inv_reta, rho_i + rho_j);
-        vx += visc * (ui - ugx);
-        vy += visc * (vi - ugy);
-    };
-    const uint32_t b = a.off[i], e = a.off[i + 1];
-    const bool literal = a.pavg_mode != 0;
-    const double xid = a.x[i], yid = a.y[i], hid = a.h[i];
-    const R hpk = (R)a.pk[i].z;   // h_i as the list builder saw it
-    if constexpr (sizeof(R) == 4) {
-        // U list entries per step, their records loaded before any is used
-        // (more loads in flight per warp)
-        auto body = [&](int j, const float4 &pj, const float4 &A,
-                        const float4 &B) {
-            if (j == i) return;
-            R dx, dy;
-            anchor_sep(a.an, sp.pi, pj, dx, dy);
-            const R r2 = fmaf(dx, dx, dy * dy);
-            if (a.filter && !skin_member<R>(a.d, a.an, r2, hpk, pj.z, xid, yid,
-                                            hid, a.x, a.y, a.h, j))
-                return;
-            const R pref = literal ? a.pavg[j] : pavg_i;
-            pair(dx, dy, r2, B.w, A.x, A.y, A.z, (B.x - pref) * A.w, B.x, B.y,
-                 B.z, B.y, B.z);
-        };
-        constexpr int U = UNROLL_B;
-        uint32_t k = b + tm.lane;
-        for (; k + (U - 1) * T < e; k += U * T) {
-            int jj[U];
-            float4 pp[U], AA[U], BB[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) jj[u] = (int)__ldg(&a.list[k + u * T]);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                pp[u] = __ldg(&a.pk[jj[u]]);
-                AA[u] = a.nbA[jj[u]];
-                BB[u] = a.nbB[jj[u]];
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) body(jj[u], pp[u], AA[u], BB[u]);
-        }
-        for (; k < e; k += T) {
-            const int j = (int)__ldg(&a.list[k]);
-            body(j, __ldg(&a.pk[j]), a.nbA[j], a.nbB[j]);
-        }
-    } else {
-        for (uint32_t k = b + tm.lane; k < e; k += T) {
-            const int j = (int)__ldg(&a.list[k]);
-            if (j == i) continue;
-            R dx, dy, r2;
-            if (a.filter) {
-                R hj;
-                sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
-                if (!skin_member<R>(a.d, a.an, r2, hpk, hj, xid, yid, hid, a.x,
-                                    a.y, a.h, j))
-                    continue;
-            } else {
-                sp.get(a.d, a.an, a.x, a.y, a.pk, j, dx, dy, r2);
-            }
-            const typename V4<R>::T A = a.nbA[j], B = a.nbB[j];
-            const R pref = literal ? a.pavg[j] : pavg_i;
-            pair(dx, dy, r2, B.w, A.x, A.y, A.z, (B.x - pref) * A.w, B.x, B.y,
-                 B.z, B.y, B.z);
-        }
-    }
-    if (a.w.n > 0) {
-        const R rho0 = (R)a.rho0;
-        for_each_wall<T>(a.w, i, a.d, a.an, a.pk[i], a.x[i], a.y[i], a.h[i], tm.lane, tm.mask,
-                      [&](int k, double dxd, double dyd, double r2d) {
-            const R mk = (R)a.w.m[k], pk = (R)a.w.p[k];
-            const R pref = literal ? R(0) : pavg_i;
-            pair((R)dxd, (R)dyd, (R)r2d, R(1) / (R)a.w.h[k], mk, mk / rho0,
-                 rho0, (pk - pref) / (rho0 * rho0), pk, (R)a.w.uw[k],
-                 (R)a.w.vw[k], (R)a.w.ugx[k], (R)a.w.ugy[k]);
-        });
-    }
-    div = team_sum<T>(tm.mask, div);
-    diff = team_sum<T>(tm.mask, diff);
-    tvf = team_sum<T>(tm.mask, tvf);
-    fax = team_sum<T>(tm.mask, fax);
-    fay = team_sum<T>(tm.mask, fay);
-    vx = team_sum<T>(tm.mask, vx);
-    vy = team_sum<T>(tm.mask, vy);
-    if (tm.lane != 0) return;
-    const R rf = a.rho_factor ? rho_i : R(1);
-    const R dpdt = ((R)a.rho0 * (R)a.cs * (R)a.cs / beta_i) * div +
-                   diff / beta_i + rf * tvf;
-    const R dudt = fax + vx / beta_i;
-    const R dvdt = fay + vy / beta_i;
-    a.dpdt[i] = dpdt;
-    a.dudt[i] = dudt;
-    a.dvdt[i] = dvdt;
-    if (!isfinite((double)dpdt) || !isfinite((double)dudt) ||
-        !isfinite((double)dvdt))
-        atomicOr(a.nonfinite, 1);
+    pass_b_list<R, T>(a, i, L, tm, a.off[i], a.off[i + 1]);
+    L.walls(a, i, tm);
+    L.finish(a, i, tm, true);
 }
 
 template <typename R, int T>
@@ -534,7 +255,7 @@ __global__ void k_nbr_ids(int n, const uint32_t *off, const uint32_t *list,
 // explicitly rounded; periodic axes wrapped back into the box.
 template <typename R>
 __device__ __forceinline__ void pec_at(const PecArgs<R> &a, int i) {
-    const double dt = *a.dt;
+    const double dt = a.dt[0], idt = a.dt[1];
     const double fdt = __dmul_rn(a.f, dt);
     double x0, y0, u0, v0, p0;
     if (a.save) {
@@ -557,8 +278,8 @@ __device__ __forceinline__ void pec_at(const PecArgs<R> &a, int i) {
     }
     const double un = __dadd_rn(u0, __dmul_rn(fdt, (double)a.dudt[i]));
     const double vn = __dadd_rn(v0, __dmul_rn(fdt, (double)a.dvdt[i]));
-    const double utx = __dadd_rn(un, __ddiv_rn((double)a.drx[i], dt));
-    const double uty = __dadd_rn(vn, __ddiv_rn((double)a.dry[i], dt));
+    const double utx = __dadd_rn(un, __dmul_rn((double)a.drx[i], idt));
+    const double uty = __dadd_rn(vn, __dmul_rn((double)a.dry[i], idt));
     double xn = __dadd_rn(x0, __dmul_rn(fdt, utx));
     double yn = __dadd_rn(y0, __dmul_rn(fdt, uty));
     if (a.d.periodic[0]) {
@@ -610,7 +331,8 @@ __global__ void k_min_h(int n, const double *__restrict__ h,
     if ((threadIdx.x & 31) == 0) atomicMin(out, m);
 }
 
-// Eq. timestep: dt = min(0.25 h_min/(U + c_s), 0.125 h_min^2/nu).
+// Eq. timestep: dt = min(0.25 h_min/(U + c_s), 0.125 h_min^2/nu) into
+// dt[0], 1 / dt into dt[1].
 __device__ __forceinline__ void k_dt_body(const unsigned long long *hmin_bits,
                                           double U, double cs, double nu,
                                           double *dt, double *tacc, int nsteps) {
@@ -620,7 +342,10 @@ __device__ __forceinline__ void k_dt_body(const unsigned long long *hmin_bits,
         double w = __dmul_rn(0.125, __ddiv_rn(__dmul_rn(hmin, hmin), nu));
         if (w < v) v = w;
     }
-    *dt = v;
+    dt[0] = v;
+    // its reciprocal: the per-particle (u~ - u) = dr / dt of pass B and the
+    // PEC stages multiply by it (FP64 divisions are slow on this GPU)
+    dt[1] = __ddiv_rn(1.0, v);
     if (tacc) {
         for (int s = 0; s < nsteps; ++s) *tacc = __dadd_rn(*tacc, v);
     }

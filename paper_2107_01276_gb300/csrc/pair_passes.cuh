@@ -41,7 +41,7 @@ struct PassBArgs {
     WallView w;
     const R *rho, *beta, *pavg, *drx, *dry, *V, *rb2;
     const typename V4<R>::T *nbA, *nbB;
-    const double *dt;          // device scalar
+    const double *dt;          // device {dt, 1 / dt}
     double rho0, cs, nu, alpha_e;
     int pavg_mode, diff_denominator, rho_factor;
     R *dpdt, *dudt, *dvdt;
@@ -61,7 +61,7 @@ struct PecArgs {
     const double *h;
     double disp_lim;
     int *skin_err;
-    const double *dt;
+    const double *dt;          // device {dt, 1 / dt}
     const double *x0, *y0, *u0, *v0, *p0;
     const R *dudt, *dvdt, *dpdt, *drx, *dry;
     double *x, *y, *u, *v, *p;

@@ -1130,7 +1130,7 @@ static sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
          dalloc(&c->tmaxh, t);
     ok = ok && dalloc(&c->bbox, MAX_LEVELS * 4) && dalloc(&c->level_mask, 1) &&
          dalloc(&c->cnt_tmp, N + 1);
-    ok = ok && dalloc(&c->d_dt, 1) && dalloc(&c->d_t, 1) && dalloc(&c->d_hmin, 1) &&
+    ok = ok && dalloc(&c->d_dt, 2) && dalloc(&c->d_t, 1) && dalloc(&c->d_hmin, 1) &&
          dalloc(&c->d_nonfinite, 1) && dalloc(&c->d_total, 1) &&
          dalloc(&c->d_skin_err, 1) &&
          dalloc(&c->d_overflow, 1);
