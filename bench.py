@@ -39,12 +39,16 @@ PASS_A_FLOP_PER_PAIR = 60
 # entry 4 B (the walk stages own entries and counts reverse ones).
 WALK_BYTES_PER_PARTICLE = 44
 WALK_BYTES_PER_ENTRY = 4
-NFAM = 6   # timed kernel families of the library (sph_kernel_time)
-FAM_NAMES = ["pass_b", "pass_a", "rebuild", "pec", "adapt", "walk"]
+NFAM = 7   # timed kernel families of the library (sph_kernel_time)
+FAM_NAMES = ["pass_b", "pass_a", "rebuild", "pec", "adapt", "walk", "sort"]
 # kernel sources a DRAM-traffic capture is tied to
 WALK_SOURCES = ["paper_2107_01276_gb300/csrc/lists.cu",
                 "paper_2107_01276_gb300/csrc/neighbors.cuh",
                 "paper_2107_01276_gb300/csrc/team.cuh"]
+PASS_SOURCES = ["paper_2107_01276_gb300/csrc/pair_passes.cu",
+                "paper_2107_01276_gb300/csrc/pair_lanes.cuh",
+                "paper_2107_01276_gb300/csrc/kernels.cuh",
+                "paper_2107_01276_gb300/csrc/neighbors.cuh"]
 
 
 def sources_sha(paths):
@@ -67,20 +71,25 @@ def walk_kernel(n):
     return "k_list_gather<T> (neighbour walk, per-particle teams)"
 
 
-def walk_traffic(workload):
-    """DRAM bytes per launch of the neighbour walk from the committed ncu
-    summary, or None if there is none for this workload or the kernel
-    sources changed since it was taken."""
+def committed_traffic(fname, workload, sources):
+    """DRAM bytes per launch of a kernel from a committed ncu summary
+    (profiles/<fname>), or None if there is none for this workload or the
+    kernel's sources changed since it was taken."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                        "profiles", "walk_dram_traffic.json")
+                        "profiles", fname)
     try:
         with open(path) as f:
             rec = json.load(f).get(workload)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("sources_sha") != sources_sha(WALK_SOURCES):
+    if not rec or rec.get("sources_sha") != sources_sha(sources):
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def walk_traffic(workload):
+    """DRAM bytes per launch of the neighbour walk (committed ncu summary)."""
+    return committed_traffic("walk_dram_traffic.json", workload, WALK_SOURCES)
 
 WORKLOADS = {
     # flow past a cylinder at Re 40, spacing graded from D/50 at
@@ -90,6 +99,10 @@ WORKLOADS = {
     # graded over 1:250 by C_r per column, u,v ~ N(0, 0.1),
     # rho = 1 + U(-0.01, 0.01); PEC steps, no adaptation
     "graded-1M": dict(kind="graded", n_target=1 << 20, ratio=250.0),
+    # the pair-kernel sweep at its largest size, 16M particles, with the 1M,
+    # 2M, 4M and 8M points of the sweep measured in the same run
+    "graded-16M": dict(kind="graded", n_target=1 << 24, ratio=250.0,
+                       sweep=(1 << 20, 1 << 21, 1 << 22, 1 << 23)),
     # solution-adaptive cylinder at Re 1000, spacing D/1000 at the wall to
     # D/4 (1:250), vorticity marking (k = 0.05) with a background iteration
     # every 100 adaptations; fluid initialised from the graded ring
@@ -115,7 +128,7 @@ WORKLOADS = {
     # one on their own streams
     "batched-tg32": dict(kind="batch", instances=32, sizes=(1600, 20000)),
 }
-DEFAULT_WORKLOAD = "cylinder-re40"
+DEFAULT_WORKLOAD = "graded-16M"
 
 
 def make_workload(name):
@@ -237,9 +250,15 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def fp32_alu_peak_tflops(sm_mhz):
-    """Non-tensor FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def alu_peaks(stream):
+    """Measured FP32 and FP64 non-tensor FMA rates of this GPU (TFLOP/s) and
+    its SM count, from the library's FMA probe (sph_probe_fma)."""
+    from paper_2107_01276_gb300 import sph
+    f32, sms = sph.probe_fma(False, stream)
+    f64, _ = sph.probe_fma(True, stream)
+    return {"fp32_tflops": f32 / 1e12, "fp64_tflops": f64 / 1e12, "sms": sms,
+            "kind": "measured in this run by the FMA probe (every SM, 8 "
+                    "independent FMA chains a thread, best of 4 launches)"}
 
 
 # ------------------------------------------------------------ reference --
@@ -558,6 +577,406 @@ def batch_arm(args):
     return 0
 
 
+# ------------------------------------------------------ pair-kernel sweep --
+class Steps:
+    """Timed PEC steps of one context on the bench's stream: CUDA events
+    around each step, a 256 MiB write between steps (flushes the 129 MB
+    L2), library timing off (sph_step replays its captured graphs)."""
+
+    def __init__(self, sim, flush):
+        self.sim, self.flush = sim, flush
+
+    def run(self, K, W, lib_timing=False, profile=False, dist=None):
+        import torch
+        sim = self.sim
+        for _ in range(W):
+            sim.step(1, want_time=False)
+        torch.cuda.synchronize()
+        sim.set_timing(lib_timing)
+        for fam in range(NFAM):
+            sim.kernel_time(fam, reset=True)
+        l0 = sim.info()["launches"]
+        evs = [(torch.cuda.Event(enable_timing=True),
+                torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            torch.cuda.cudart().cudaProfilerStart()
+        for k in range(K):
+            self.flush.zero_()
+            evs[k][0].record()
+            sim.step(1, want_time=False)
+            evs[k][1].record()
+        torch.cuda.synchronize()
+        if profile:
+            torch.cuda.cudart().cudaProfilerStop()
+        if dist:
+            dist.barrier()
+        sim.set_timing(False)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        fams = [sim.kernel_time(f) for f in range(NFAM)]
+        return ms, fams, sim.info()["launches"] - l0
+
+    def rhs_ms(self, reps=3):
+        """Device ms of one full right-hand side (exact-list rebuild, both
+        passes) through sph_rhs."""
+        import torch
+        sim = self.sim
+        sim.rhs()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(reps):
+            self.flush.zero_()
+            e0.record()
+            sim.rhs()
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+
+def per_launch(fams):
+    """{family: ms per launch} from sph_kernel_time totals."""
+    return {FAM_NAMES[f]: (fams[f][0] / fams[f][1] if fams[f][1] else None)
+            for f in range(NFAM)}
+
+
+def graded_sim(d, precision, stream):
+    from paper_2107_01276_gb300 import sph
+    n = len(d["particles"]["x"])
+    P = sph.make_params(d["params"], precision=precision,
+                        capacity=int(n * 1.1) + 16)
+    sim = sph.Simulation(P, stream)
+    sim.load(d["particles"])
+    return sim
+
+
+def graded_point(d, precision, K, W, flush, stream):
+    """Particle-steps/s, kernel times per launch, right-hand-side time and
+    pass-B pair rate of one precision on one graded set."""
+    sim = graded_sim(d, precision, stream)
+    st = Steps(sim, flush)
+    ms, _, _ = st.run(K, W)
+    n = sim.info()["n"]
+    _, fams, _ = st.run(max(2, K // 2), 1, lib_timing=True)
+    pl = per_launch(fams)
+    rhs = st.rhs_ms()
+    nnb = sim.read("nnb")
+    pairs = int(nnb.sum()) - len(nnb)
+    sim.close()
+    out = {"particle_steps_per_s": n * K / (float(np.sum(ms)) / 1e3),
+           "ms_per_step": float(np.mean(ms)),
+           "pass_a_ms": pl["pass_a"], "pass_b_ms": pl["pass_b"],
+           "rhs_ms": rhs, "sort_ms": pl["sort"], "walk_ms": pl["walk"],
+           "rebuild_ms": pl["rebuild"], "pec_ms": pl["pec"],
+           "pairs": pairs,
+           "pass_b_pair_interactions_per_s": pairs / (pl["pass_b"] / 1e3)}
+    return n, out
+
+
+def rel_err(a, b, scale=None):
+    """max_i |a_i - b_i| over max_i S_i (scale: S, the sum of |terms|) or
+    over max_i |b_i|."""
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    sc = float(np.max(scale)) if scale is not None else float(np.abs(b).max())
+    return float(np.abs(a - b).max()) / (sc or 1.0)
+
+
+def error_report(stream, with_adapt=True):
+    """Error of each result against the FP64 oracle (the mixed-precision
+    report): (1) the right-hand-side fields on a band of the 1:250 graded
+    strip that holds every resolution, mixed and FP64 GPU paths, each
+    field under the condition-aware norm (S_i = sum of |terms|) and the
+    plain norm (max |b_i|); (2) the Taylor-Green decay over 200 PEC steps
+    against exp(-8 pi^2 t / Re) and against the oracle's own run; (3) the
+    split / merge counts of one adaptation at 1:250 (the solution-adaptive
+    cylinder's fluid from its ring background) against the oracle's."""
+    import oracle
+    from paper_2107_01276_gb300 import sph
+    rep = {}
+    # (1) right-hand side
+    d1 = wl.graded_strip(n_target=1 << 20, ratio=250.0)
+    dd, n_s, frac = cpu_sample(d1)
+    pt = dd["particles"]
+    P = oracle.params(**dd["params"])
+    dt = oracle.dt(P, pt["h"])
+    t0 = time.perf_counter()
+    ref = oracle.rhs(P, dt, oracle.make_state(pt))
+    t_or = time.perf_counter() - t0
+    fields = ("rho", "beta", "pavg", "drx", "dry", "dpdt", "dudt", "dvdt")
+    rhs = {}
+    for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
+        sim = graded_sim(dd, prec, stream)
+        sim.rhs()
+        order = np.argsort(sim.read("id"))
+        got = {f: sim.read(f)[order] for f in fields}
+        nnb = sim.read("nnb")[order]
+        sim.close()
+        rhs[name] = {f: {"cond": rel_err(got[f], ref[f], ref["s_" + f]),
+                         "plain": rel_err(got[f], ref[f])} for f in fields}
+        rhs[name]["nnb_equal"] = bool(np.array_equal(nnb, ref["nnb"]))
+    rep["rhs"] = dict(rhs, sample="band 0 <= y < %.2f of the 1:250 graded strip "
+                      "(%d particles, every resolution)" % (frac, n_s),
+                      oracle_s=t_or)
+    # (2) Taylor-Green decay
+    dtg = wl.taylor_green(nx=50, Re=100.0)
+    Po = oracle.params(**dtg["params"])
+    st = oracle.make_state(dtg["particles"])
+    u0 = float(np.hypot(dtg["particles"]["u"], dtg["particles"]["v"]).max())
+    t_end = oracle.step(Po, st, 200)
+    n_tg = st["n"]
+    uo = float(np.hypot(st["u"][:n_tg], st["v"][:n_tg]).max())
+    exact = math.exp(-8 * math.pi ** 2 * t_end / 100.0)
+    tg = {"steps": 200, "t": t_end, "exact_decay": exact,
+          "oracle_decay_err": uo / u0 / exact - 1}
+    for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
+        sim = graded_sim(dtg, prec, stream)
+        t = sim.step(200)
+        ug = float(np.hypot(sim.read("u"), sim.read("v")).max())
+        sim.close()
+        tg[name] = {"decay_err": ug / u0 / exact - 1,
+                    "vs_oracle": ug / uo - 1, "t_rel_err": t / t_end - 1}
+    rep["taylor_green"] = tg
+    # (3) one adaptation at 1:250
+    if with_adapt:
+        dc = wl.cylinder(Re=1000.0, ds_min_over_D=1 / 1000, ds_max_over_D=1 / 4,
+                         background="rings", fluid="rings")
+        dc["params"] = dict(dc["params"], vort_k=0.0, n_bg=0)
+        ad = {}
+        for name, prec in (("mixed", sph.SPH_MIXED), ("fp64", sph.SPH_FP64)):
+            Ps = sph.make_params(dc["params"], precision=prec, capacity=400000)
+            sim = sph.Simulation(Ps, stream)
+            sim.load(dc["particles"])
+            sim.load(dc["walls"], kind=sph.SPH_WALL)
+            sim.load(dc["background_rings"], kind=sph.SPH_BACKGROUND)
+            g = sim.adapt()
+            sim.close()
+            ad[name] = {k: int(g[k]) for k in ("n_split", "n_merged", "n_after")}
+        Pc = oracle.params(**dc["params"])
+        sto = oracle.make_state(dc["particles"], cap=400000)
+        oracle.set_walls(dc["walls"])
+        try:
+            t0 = time.perf_counter()
+            _, og, _ = oracle.adapt(Pc, sto, bg=dc["background_rings"])
+            ad["oracle_s"] = time.perf_counter() - t0
+        finally:
+            oracle.set_walls(None)
+        ad["oracle"] = {k: int(og[k]) for k in ("n_split", "n_merged", "n_after")}
+        ad["counts_equal"] = all(ad[k] == ad["oracle"] for k in ("mixed", "fp64"))
+        ad["workload"] = ("solution-adaptive cylinder at Re 1000, D/1000 to D/4 "
+                          "(1:250), %d fluid particles from the ring background"
+                          % len(dc["particles"]["x"]))
+        rep["adapt_1_250"] = ad
+    return rep
+
+
+def cpu_oracle_rate(steps=2):
+    """The oracle's PEC particle-steps/s on the host cores, all threads and
+    one thread, on the band of the 1M 1:250 graded strip (every
+    resolution, ~106k particles)."""
+    import oracle
+    d1 = wl.graded_strip(n_target=1 << 20, ratio=250.0)
+    dd, n_s, frac = cpu_sample(d1)
+    cores = oracle.num_threads()
+    ps, el, _ = oracle_steps(dd, dd["particles"], steps, False)
+    oracle.set_num_threads(1)
+    try:
+        ps1, el1, _ = oracle_steps(dd, dd["particles"], 1, False)
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": ps / el, "unit": "particle-steps/s", "cores": cores,
+            "kind": "oracle", "one_thread_value": ps1 / el1,
+            "sample": "band 0 <= y < %.2f of the 1M-particle 1:250 graded strip "
+                      "(%d particles, every resolution, non-periodic in y), %d "
+                      "PEC steps on %d threads and 1 on one thread; the oracle's "
+                      "cost per particle-step does not depend on N"
+                      % (frac, n_s, steps, cores)}
+
+
+def graded_arm(args):
+    """The pair-kernel sweep: mixed (FP32 pairs / FP64 state) PEC steps on
+    the graded 1:250 strip at the workload's size, the plain FP64 form on
+    the same state, and the smaller sizes of the sweep; pass A, pass B, the
+    full right-hand side and the sort timed separately for both."""
+    import ctypes
+
+    import torch
+    from paper_2107_01276_gb300 import sph
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sph.lib()
+    torch.cuda.set_stream(torch.cuda.Stream())
+    stream = torch.cuda.current_stream().cuda_stream
+    wdef = WORKLOADS[args.workload]
+    apk = alu_peaks(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    d, desc = make_workload(args.workload)
+    pt = d["particles"]
+
+    # the headline: mixed PEC steps at full size
+    sim = graded_sim(d, sph.SPH_MIXED, stream)
+    st = Steps(sim, flush)
+    n = sim.info()["n"]
+    clk = ClockSampler(local)
+    clk.start()
+    ms, _, nlaunch = st.run(args.steps, args.warmup, profile=args.profile_region,
+                            dist=dist)
+    clocks = clk.stop()
+    tmax, units = replica_totals(dist, float(np.sum(ms)), float(n * args.steps))
+    value = units / (tmax / 1e3)
+    kb = max(4, args.steps // 4)
+    _, fams, _ = st.run(kb, 1, lib_timing=True)
+    pl = per_launch(fams)
+    rhs_mixed = st.rhs_ms()
+    nnb = sim.read("nnb")
+    pairs = int(nnb.sum()) - len(nnb)
+
+    # e2e through the C ABI with pinned host buffers: H2D of the state, one
+    # PEC step, D2H of x, y, u, v, p
+    fields_in = ("x", "y", "u", "v", "p", "rho", "m", "h", "mmin", "mmax")
+    state = {k: sim.read(k) for k in fields_in}
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(state[k], np.float64)
+                                  ).pin_memory() for k in fields_in}
+    pid = torch.from_numpy(sim.read("id").astype(np.int64)).pin_memory()
+    src = sph.Particles()
+    for k in fields_in:
+        setattr(src, k, ctypes.cast(pinned[k].data_ptr(), sph._D))
+    src.id = ctypes.cast(pid.data_ptr(), ctypes.POINTER(ctypes.c_int64))
+    outs = {k: torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+            for k in ("x", "y", "u", "v", "p")}
+
+    def e2e_step():
+        sim.load_raw(sph.SPH_FLUID, n, src)
+        sim.step(1, want_time=False)
+        nb = 0
+        for k in outs:
+            nb += 8 * sim.read_into(k, outs[k])
+        return nb
+
+    e2e_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ke = 3
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        d2h = e2e_step()
+    torch.cuda.synchronize()
+    e2e_t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64,
+                         device="cuda")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_val = world * n * ke / float(e2e_t.item())
+    del pinned, pid, outs
+    sim.close()
+
+    # the plain FP64 GPU form on the same workload
+    fp64 = None
+    n64 = None
+    if not args.no_fp64:
+        n64, fp64 = graded_point(d, sph.SPH_FP64, 3, 2, flush, stream)
+    mixed = {"particle_steps_per_s": value / world, "ms_per_step": tmax / args.steps,
+             "pass_a_ms": pl["pass_a"], "pass_b_ms": pl["pass_b"],
+             "rhs_ms": rhs_mixed, "sort_ms": pl["sort"], "walk_ms": pl["walk"],
+             "rebuild_ms": pl["rebuild"], "pec_ms": pl["pec"], "pairs": pairs,
+             "pass_b_pair_interactions_per_s": pairs / (pl["pass_b"] / 1e3)}
+    # the smaller sizes of the sweep
+    sweep = []
+    for nt in (() if args.no_sweep else wdef.get("sweep", ())):
+        ds = wl.graded_strip(n_target=nt, ratio=wdef["ratio"])
+        ns, pm = graded_point(ds, sph.SPH_MIXED, 6, 3, flush, stream)
+        row = {"n": ns, "mixed": pm}
+        if not args.no_fp64:
+            _, p64 = graded_point(ds, sph.SPH_FP64, 2, 1, flush, stream)
+            row["fp64"] = p64
+            row["mixed_over_fp64"] = pm["particle_steps_per_s"] / p64["particle_steps_per_s"]
+        sweep.append(row)
+    sweep.append({"n": n, "mixed": mixed, "fp64": fp64,
+                  "mixed_over_fp64": (mixed["particle_steps_per_s"] /
+                                      fp64["particle_steps_per_s"]) if fp64 else None})
+    err = error_report(stream, with_adapt=not args.no_adapt_report) \
+        if world == 1 and not args.no_error_report else None
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = cpu_oracle_rate() if (not args.no_cpu_baseline and world == 1) else None
+
+    peaks, pk_kind = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    fl_b = PASS_B_FLOP_PER_PAIR * pairs
+    ach_b = fl_b / (pl["pass_b"] / 1e3) / 1e12
+    traffic_b = committed_traffic("pass_b_dram_traffic.json", args.workload, PASS_SOURCES)
+    walk_bytes = WALK_BYTES_PER_PARTICLE * n + WALK_BYTES_PER_ENTRY * int(nnb.sum())
+    ach_w = walk_bytes / (pl["walk"] / 1e3) / 1e9
+    line = {
+        "metric": "particle-steps/s", "value": value,
+        "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-pair/f64-state", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": desc, "n_particles": n,
+                   "precision": "mixed (FP32 pair arithmetic, FP64 positions, "
+                                "integration and time step)",
+                   "l2": "flushed between steps (256 MiB write); the state "
+                         "(~1.4 GB) is larger than L2 too",
+                   "timing": "value: CUDA events around each PEC step on the "
+                             "bench's stream, library timing off (steps replay "
+                             "their captured graphs); kernel times: further "
+                             "steps with per-family library events"},
+        "pass_b_pair_interactions_per_s": mixed["pass_b_pair_interactions_per_s"],
+        "fp64_particle_steps_per_s": fp64["particle_steps_per_s"] if fp64 else None,
+        "mixed_over_fp64": (value / world / fp64["particle_steps_per_s"]) if fp64 else None,
+        "kernel_ms_per_launch": pl,
+        "sweep": sweep,
+        "roofline": {"bound": "alu", "kernel": "k_pass_b<float, 1> (pass B, the pair loop)",
+                     "achieved": ach_b, "peak": apk["fp32_tflops"], "unit": "TFLOP/s",
+                     "frac": ach_b / apk["fp32_tflops"],
+                     "traffic": traffic_b,
+                     "dram_gbs": (traffic_b / (pl["pass_b"] / 1e3) / 1e9) if traffic_b else None,
+                     "flop_per_pair": PASS_B_FLOP_PER_PAIR, "pairs_per_launch": pairs,
+                     "ms_per_launch": pl["pass_b"],
+                     "peak_kind": "FP32 FMA rate " + apk["kind"]},
+        "roofline_pass_b_fp64": ({"bound": "alu", "kernel": "k_pass_b<double, 1>",
+                                  "achieved": PASS_B_FLOP_PER_PAIR * fp64["pairs"] /
+                                  (fp64["pass_b_ms"] / 1e3) / 1e12,
+                                  "peak": apk["fp64_tflops"], "unit": "TFLOP/s",
+                                  "frac": PASS_B_FLOP_PER_PAIR * fp64["pairs"] /
+                                  (fp64["pass_b_ms"] / 1e3) / 1e12 / apk["fp64_tflops"],
+                                  "peak_kind": "FP64 FMA rate " + apk["kind"]}
+                                 if fp64 else None),
+        "roofline_walk": {"bound": "hbm", "kernel": "k_list_tile<1> (neighbour walk)",
+                          "achieved": ach_w, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": ach_w / hbm_peak,
+                          "traffic": walk_traffic(args.workload),
+                          "bytes_per_launch": walk_bytes,
+                          "ms_per_launch": pl["walk"],
+                          "peak_kind": "measured copy bandwidth (%s)" % pk_kind},
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": 8 * len(fields_in) * n + 8 * n,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(nlaunch),
+        "cpu_baseline": cpu,
+        "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "kind": pk_kind, "alu": apk},
+        "neighbours_mean": float(nnb.mean()), "neighbours_max": int(nnb.max()),
+        "mixed_vs_oracle": err,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 # ---------------------------------------------------------------- ours ----
 def main():
     ap = argparse.ArgumentParser()
@@ -569,6 +988,12 @@ def main():
                     choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="graded workloads: skip the smaller sizes of the sweep")
+    ap.add_argument("--no-error-report", action="store_true",
+                    help="skip the error report against the oracle")
+    ap.add_argument("--no-adapt-report", action="store_true",
+                    help="skip the 1:250 adaptation counts of the error report")
     ap.add_argument("--autotune", action="store_true",
                     help="run sph_autotune on the set-up state (untimed)")
     ap.add_argument("--profile-region", action="store_true",
@@ -583,6 +1008,8 @@ def main():
         return serving_arm(args)
     if WORKLOADS[args.workload]["kind"] == "batch":
         return batch_arm(args)
+    if WORKLOADS[args.workload]["kind"] == "graded":
+        return graded_arm(args)
 
     import ctypes
 
@@ -705,7 +1132,8 @@ def main():
     pairs = int(nnb.sum()) - n_now
     passb_ms, passb_cnt = fams[0]
     avg_b = passb_ms / max(passb_cnt, 1)
-    peak_alu = fp32_alu_peak_tflops(2070.0)
+    apk = alu_peaks(stream)
+    peak_alu = apk["fp32_tflops"]
     ach_b = PASS_B_FLOP_PER_PAIR * pairs / (avg_b / 1e3) / 1e12
     # the dominant kernel of the step: the neighbour walk
     walk_ms, walk_cnt = fams[5]
@@ -857,15 +1285,14 @@ def main():
         "roofline_pass_b": {"bound": "alu", "kernel": "k_pass_b<float>",
                      "achieved": ach_b, "peak": peak_alu, "unit": "TFLOP/s",
                      "frac": ach_b / peak_alu, "traffic": None,
-                     "peak_kind": "derived FP32 non-tensor peak at 2070 MHz "
-                                  "(152 SM x 128 lanes x 2)"},
+                     "peak_kind": "FP32 FMA rate " + apk["kind"]},
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "particle-steps/s",
                 "h2d_bytes_per_step": 8 * len(fields_in) * n_e + 8 * n_e,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(nlaunch),
         "cpu_baseline": cpu,
-        "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "kind": pk_kind},
+        "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "kind": pk_kind, "alu": apk},
         "neighbours_mean": float(nnb.mean()),
         "mixed_vs_fp64": err_rep,
         "forces": forces,

@@ -429,11 +429,23 @@ sph_status sph_get_info(sph_ctx *ctx, sph_info *out);
  * returns the accumulated device milliseconds and launch count of one
  * family (0: pass B, 1: pass A, 2: neighbour rebuild (keys, sort, gather,
  * table, lists), 3: PEC stages, 4: adaptation (rebuilds inside it
- * included), 5: the neighbour walk of each rebuild alone) and resets them
- * if reset is non-zero.  Synchronises. */
+ * included), 5: the neighbour walk of each rebuild alone, 6: the cell keys,
+ * stable sort and gather of each rebuild alone) and resets them if reset
+ * is non-zero.  Synchronises. */
 sph_status sph_set_timing(sph_ctx *ctx, int enable);
 sph_status sph_kernel_time(sph_ctx *ctx, int family, double *ms,
                            long long *launches, int reset);
+
+/* Measured non-tensor FMA throughput of the current device (the paper has
+ * no counterpart; the denominator of the pair passes' ALU rooflines, which
+ * are plain FP32 / FP64 arithmetic).  Runs, on stream (a cudaStream_t; NULL
+ * the legacy default stream), a few launches of a kernel in which every
+ * thread of every SM's resident blocks advances 8 independent FMA chains
+ * for ~20 ms, and returns the best rate in *flops (FLOP/s, an FMA counting
+ * 2) and, if sms is not NULL, the multiprocessor count read from the
+ * device.  fp64: 0 FP32, 1 FP64.  Allocates a few bytes; synchronises.
+ * Errors: SPH_EINVAL (flops NULL, fp64 not 0/1), SPH_ENOMEM, SPH_ECUDA. */
+sph_status sph_probe_fma(int fp64, void *stream, double *flops, int *sms);
 
 /* Cell keys and stable sort of a particle set, allocating nothing.
  *

@@ -181,6 +181,8 @@ def lib():
             L.orc_record_wall_terms.argtypes = [ctypes.c_void_p]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
+            L.orc_set_num_threads.restype = None
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             L.orc_neighbors_classes.restype = ctypes.c_longlong
             L.orc_neighbors_classes.argtypes = [_P, ctypes.c_int, _D, _D, _D,
                                                 _I, _I, ctypes.c_longlong]
@@ -254,6 +256,12 @@ def _f64(a):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (timing only: the results do
+    not depend on the count)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def W(r, h):

@@ -33,6 +33,16 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the parallel loops from now on (timing only: every per-particle
+ * sum runs in the same order whatever the count). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------
  * Quintic spline, section 2, Eq. (kernel):
  *   W(q) = sigma2 [(3-q)^5 - 6(2-q)^5 + 15(1-q)^5]  for 0 <= q < 1

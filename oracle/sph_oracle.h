@@ -207,6 +207,7 @@ int orc_bg_iteration(const orc_params *P, const orc_bg_params *B,
                      int nf, const double *fx, const double *fy,
                      const double *fh, const double *phi, orc_bg_stats *st);
 int orc_num_threads(void);
+void orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

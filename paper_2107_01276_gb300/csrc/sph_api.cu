@@ -27,14 +27,15 @@ thread_local std::string g_create_error;
 static std::atomic<int> g_live_ctx{0};   // contexts made by sph_create, not yet destroyed
 
 // Timed kernel families: 0 pass B, 1 pass A, 2 rebuild, 3 PEC stages,
-// 4 adaptation, 5 the neighbour walk of the rebuild (k_list_gather).
-constexpr int NFAM = 6;
+// 4 adaptation, 5 the neighbour walk of the rebuild (k_list_gather), 6 the
+// rebuild's keys, sort and gather.
+constexpr int NFAM = 7;
 
 struct Timer {
     std::vector<cudaEvent_t> pool;       // free events
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> open[NFAM];
-    double ms[NFAM] = {0, 0, 0, 0, 0, 0};
-    long long count[NFAM] = {0, 0, 0, 0, 0, 0};
+    double ms[NFAM] = {0, 0, 0, 0, 0, 0, 0};
+    long long count[NFAM] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 }  // namespace
@@ -437,6 +438,8 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true,
     rr.zero[3] = walls ? c->wcnt + n : nullptr;
     rr.zero[4] = walls ? c->d_wnlong : nullptr;
     launch_rebuild_reset(c->s, rr, &c->launches);
+    cudaEvent_t es;
+    t_begin(c, 6, &es);
     launch_keys(c->s, n, c->dom, c->c0, c->lmax, c->mbits, c->lev, c->f[F_X],
                 c->f[F_Y], c->f[F_H], c->skey, c->perm, c->level_mask, c->bbox,
                 c->rev, walls ? c->wcnt : nullptr, walls ? c->wcur : nullptr);
@@ -457,6 +460,7 @@ static sph_status rebuild(sph_ctx *c, bool mid_step, bool exact = true,
     gl.ni = 1;
     gather_insert(c->s, n, c->perm, gl, c->skey, c->tkey, c->tstart, c->tmask,
                   &c->launches);
+    t_end(c, 6, es);
     for (int k = 0; k < last; ++k) std::swap(c->f[k], c->falt[k]);
     std::swap(c->id, c->id_alt);
     pack(c, true);

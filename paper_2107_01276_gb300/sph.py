@@ -33,7 +33,7 @@ _FIELD_DTYPE = {"id": np.int64, "nnb": np.int32, "cellkey": np.uint64,
                 "bg_id": np.int64}
 
 TIMER_PASS_B, TIMER_PASS_A, TIMER_REBUILD, TIMER_PEC, TIMER_ADAPT, \
-    TIMER_WALK = range(6)
+    TIMER_WALK, TIMER_SORT = range(7)
 
 
 class SphError(RuntimeError):
@@ -177,6 +177,8 @@ def lib(build_if_missing: bool = True):
     L.sph_batch_graph_steps.argtypes = [ctypes.c_void_p]
     L.sph_batch_set_graphs.restype = ctypes.c_int
     L.sph_batch_set_graphs.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.sph_probe_fma.restype = ctypes.c_int
+    L.sph_probe_fma.argtypes = [ctypes.c_int, ctypes.c_void_p, _D, P(ctypes.c_int)]
     _lib = L
     return L
 
@@ -196,6 +198,19 @@ def coefficients(f: dict, rho0: float, U: float, L: float) -> dict:
     q = 0.5 * rho0 * U * U * L
     return {"cd_p": float(f["fp"][0] / q), "cd_sf": float(f["fv"][0] / q),
             "cl": float(f["fp"][1] / q)}
+
+
+def probe_fma(fp64: bool = False, stream: int = 0) -> tuple:
+    """sph_probe_fma: measured FMA rate (FLOP/s) of the device and its SM
+    count."""
+    L = lib()
+    fl = ctypes.c_double(0.0)
+    sms = ctypes.c_int(0)
+    st = L.sph_probe_fma(1 if fp64 else 0, ctypes.c_void_p(stream),
+                         ctypes.byref(fl), ctypes.byref(sms))
+    if st != SPH_OK:
+        raise SphError(st, "sph_probe_fma failed")
+    return fl.value, sms.value
 
 
 def cell_sort_noalloc(params: Params, n: int, x_ptr: int, y_ptr: int,
