@@ -98,6 +98,15 @@ typedef struct {
     long long bg_capacity;   /* maximum background particles during the
                                 construction; <= 0: max(100 x the loaded
                                 count, 2^18) */
+    double sponge_width;     /* > 0: a sponge layer of this width at the low-x
+                                end of the box (flow along +x) relaxes u ->
+                                U_ref, v -> 0, p -> 0 at the end of each PEC
+                                step, by the fraction min(1, 10 U_ref dt / w
+                                s^2), s = 1 at the low-x edge falling to 0 at
+                                its downstream edge; the periodic cylinder
+                                stand-in's inflow (the paper's inlet and
+                                outlet are not defined in it).  0
+                                (default): off */
 } sph_params;
 
 /* Host arrays of one particle set, n entries each.  Unused members may be
@@ -133,6 +142,12 @@ typedef enum {
     SPH_F_BG_ID,       /* int64 */
     SPH_F_COUNT
 } sph_field;
+
+/* OR-ed into the field of sph_read: the fluid rows in ascending id order
+ * instead of the library's current (cell-key) order, for comparing results
+ * particle by particle.  Taken by the per-particle fields SPH_F_X ...
+ * SPH_F_CELLKEY and SPH_F_OMEGA. */
+#define SPH_READ_BY_ID 0x100
 
 typedef struct {
     long long n;          /* fluid particles */
@@ -216,14 +231,17 @@ sph_status sph_rhs(sph_ctx *ctx);
  * int-cor; two right-hand sides per step; dt from Eq. timestep).  If
  * t_out is not NULL it receives the simulated time after the steps, which
  * requires one synchronisation.  SPH_MIXED builds the neighbour lists once
- * per step with a skin (radius 1.1 x 3 max(h_i, h_j)) and tests membership
- * in the passes, so both evaluations see exactly N(i); a particle that
- * moves more than 0.15 h in the predictor invalidates that and is
- * reported (the time step and the shift limit keep moves below 0.15 h for
- * speeds up to 0.2 (U_ref + cs), i.e. Mach 0.2).  Errors: SPH_ESTATE,
- * SPH_EINVAL (nsteps < 0), SPH_ENONFINITE (a non-finite rate, or a
- * particle that outran the skin; checked at the end when t_out is given,
- * else at the next synchronising call), SPH_ECAPACITY (neighbour-list
+ * per step with a skin (radius 1.1 x 3 max(h_i, h_j)); pass A tests
+ * membership (N_i and p_avg count members only) and pass B's terms vanish
+ * beyond the kernel support, so both evaluations see exactly N(i); a
+ * particle that moves more than 0.15 h in the predictor invalidates that
+ * and is reported (the time step and the shift limit keep moves below
+ * 0.15 h for speeds up to 0.2 (U_ref + cs), i.e. Mach 0.2).  Errors:
+ * SPH_ESTATE, SPH_EINVAL (nsteps < 0), SPH_ENONFINITE (a non-finite rate,
+ * or a particle that outran the skin; checked at the end when t_out is
+ * given, else at the next synchronising call; reported once: the state
+ * then holds non-finite or invalid values, so load a state with
+ * sph_load_particles before stepping on), SPH_ECAPACITY (neighbour-list
  * overflow, likewise). */
 sph_status sph_step(sph_ctx *ctx, int nsteps, double *t_out);
 
@@ -357,6 +375,16 @@ sph_status sph_background(sph_ctx *ctx, int iterations, sph_bg_stats *out);
  * (total NULL), SPH_ESTATE (no fluid), SPH_ENOMEM. */
 sph_status sph_forces(sph_ctx *ctx, double *per_wall, double *total);
 
+/* Drag and lift coefficients of the solid at the current state (section
+ * "Force computation", Eq. cdcl): with the force of sph_forces and the
+ * dynamic pressure q = rho0 U^2 L / 2 (U: free-stream speed, L:
+ * characteristic length, e.g. the cylinder diameter), out[3] = {c_d
+ * pressure = f_p,x / q, c_d skin friction = f_visc,x / q, c_l = f_p,y /
+ * q}, the flow taken along +x.  Evaluates the state as sph_forces does.
+ * Synchronises.  Errors: SPH_EINVAL (out NULL, U or L not positive), and
+ * those of sph_forces. */
+sph_status sph_force_coefficients(sph_ctx *ctx, double U, double L, double *out);
+
 /* Launch configuration of a context's hot kernels.  Every choice gives the
  * same neighbour sets; the team sizes change the summation order of the
  * pair sums (results equal to rounding, not bit for bit). */
@@ -415,9 +443,11 @@ sph_status sph_set_tuning(sph_ctx *ctx, const sph_tune *in);
 
 /* Copy one field of the fluid set to the host buffer dst holding cap
  * elements of the field's type; *n_out (if not NULL) receives the element
- * count.  Synchronises the context's stream.  Errors: SPH_EINVAL (bad
- * field, dst NULL), SPH_ECAPACITY (cap too small; *n_out still set),
- * SPH_ESTATE (field not computed yet). */
+ * count.  Rows come in the library's current order (read SPH_F_ID for the
+ * identities), or by ascending id with SPH_READ_BY_ID.  Synchronises the
+ * context's stream.  Errors: SPH_EINVAL (bad field, SPH_READ_BY_ID on a
+ * field without per-particle rows, dst NULL), SPH_ECAPACITY (cap too
+ * small; *n_out still set), SPH_ESTATE (field not computed yet). */
 sph_status sph_read(sph_ctx *ctx, sph_field field, void *dst, long long cap,
                     long long *n_out);
 
@@ -455,8 +485,13 @@ sph_status sph_probe_fma(int fp64, void *stream, double *flops, int *sms);
  * own pool (a raw cudaMalloc/cudaFree would bypass that pool's accounting,
  * and cudaFree can stall the whole device), or a latency-critical loop
  * that must not pay for an allocation.  It computes, without a context,
- * the same keys and order as the neighbour rebuild of a context
- * (SPH_F_CELLKEY and SPH_F_ID after sph_rhs).  The scratch it needs is one
+ * the cell keys and stable order of the neighbour rebuild (the level of
+ * each particle, then the Morton order of its cell).  They equal a
+ * context's SPH_F_CELLKEY and SPH_F_ID order after sph_rhs when p->cell_c0
+ * is that context's level-0 cell side (sph_get_info's c0, which includes
+ * any sph_set_tuning / sph_autotune scale and, without ds_min, follows
+ * from the smallest h loaded); the side used here has no tuning scale.
+ * The scratch it needs is one
  * fixed device array inside the library, about 3.2 MB, reserved on every
  * GPU that loads the library until the process exits; the call itself
  * allocates nothing.
@@ -469,14 +504,17 @@ sph_status sph_probe_fma(int fp64, void *stream, double *flops, int *sms);
  * p->ds_min.  The work is enqueued on `stream` (cudaStream_t; NULL = the
  * legacy default stream) and the call returns once it is enqueued.
  *
- * Limits and sharing: n <= 262144 (SPH_EINVAL beyond).  The first call on
- * a device looks up the device address of the fixed array, with that
- * device current; make that first call before any stream capture.  Every
- * call on a device uses the same array and each call resets the parts it
- * relies on, so calls whose work overlaps on the GPU (different streams or
- * host threads) race and must be serialised by the caller.
+ * Limits and sharing: n <= 262144 (SPH_EINVAL beyond).  Every call looks
+ * up the fixed array's address on the current device (so a device reset
+ * between calls is harmless); the first lookup on a device loads the
+ * library's module there, so make the first call before any stream
+ * capture.  Every call on a device uses the same array and each call
+ * resets the parts it relies on, so calls whose work overlaps on the GPU
+ * (different streams or host threads) race and must be serialised by the
+ * caller.
  * Errors: SPH_EINVAL (NULL argument, n out of range, no cell side, bad
- * domain), SPH_ECUDA (device address lookup or launch failure). */
+ * domain), SPH_ECUDA (device address lookup or launch failure); the reason
+ * is then sph_last_error(NULL) on the calling thread. */
 sph_status sph_cell_sort_noalloc(const sph_params *p, long long n,
                                  const double *x, const double *y,
                                  const double *h, uint64_t *key_out,

@@ -6,7 +6,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "pair_passes.cuh"
 #include "sph_internal.cuh"
@@ -35,9 +34,6 @@ constexpr size_t SCRATCH_BYTES =
 // ~3.2 MB, held by every GPU that loads the library until process exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
-std::mutex g_mu;
-void *g_dev_ptr[64] = {};   // device address of the array, per device
-
 __global__ void k_canonical_keys(int n, int lshift, uint64_t *key) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -46,10 +42,9 @@ __global__ void k_canonical_keys(int n, int lshift, uint64_t *key) {
     key[i] = ((k >> lshift) << 58) | (k & mask);
 }
 
-// Status with the reason kept beside it for a debugger; the entry point
-// reports only the status.
+// Status, with its reason kept for sph_last_error(NULL) on this thread.
 sph_status nf(sph_status st, const char *why) {
-    (void)why;
+    set_noctx_error(why);
     return st;
 }
 
@@ -99,26 +94,15 @@ sph_status sph_cell_sort_noalloc(const sph_params *p, long long n,
     while ((1ll << lbits) <= lmax) ++lbits;
     if (n == 0) return SPH_OK;
 
-    // one-time set-up per device, with that device current
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    // the array's address on the current device, looked up on every call
+    // (a device reset or a new primary context may move it); the first
+    // lookup on a device loads the module there
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
         cudaGetLastError();
-        return nf(SPH_ECUDA, "sph_cell_sort_noalloc: no current device");
+        return nf(SPH_ECUDA, "sph_cell_sort_noalloc: cudaGetSymbolAddress failed");
     }
-    unsigned char *base;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_dev_ptr[dev]) {
-            void *ptr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess || !ptr) {
-                cudaGetLastError();
-                return nf(SPH_ECUDA, "sph_cell_sort_noalloc: cudaGetSymbolAddress failed");
-            }
-            g_dev_ptr[dev] = ptr;
-        }
-        base = (unsigned char *)g_dev_ptr[dev];
-    }
+    unsigned char *base = (unsigned char *)ptr;
     SortScratch sc;
     sc.key_alt = (uint64_t *)base;
     sc.val_alt = (uint32_t *)(base + SZ_KEY);
@@ -143,6 +127,7 @@ sph_status sph_cell_sort_noalloc(const sph_params *p, long long n,
                                                              key_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return nf(SPH_ECUDA, "sph_cell_sort_noalloc: launch failed");
+    set_noctx_error("");
     return SPH_OK;
 }
 

@@ -252,7 +252,8 @@ __global__ void k_nbr_ids(int n, const uint32_t *off, const uint32_t *list,
 // ------------------------------------------------------------ PEC stages --
 // Section 2.4: u' = u0 + f dt du/dt; u~' = u' + dr/dt; r' = r0 + f dt u~';
 // p' = p0 + f dt dp/dt, with f = 1/2 (predict) or 1 (correct); FP64,
-// explicitly rounded; periodic axes wrapped back into the box.
+// explicitly rounded; periodic axes wrapped back into the box; then, with
+// a sponge layer, the corrector relaxes u, v, p towards (U, 0, 0) in it.
 template <typename R>
 __device__ __forceinline__ void pec_at(const PecArgs<R> &a, int i) {
     const double dt = a.dt[0], idt = a.dt[1];
@@ -300,11 +301,24 @@ __device__ __forceinline__ void pec_at(const PecArgs<R> &a, int i) {
         const double lim = a.disp_lim * a.h[i];
         if (mx * mx + my * my > lim * lim) atomicOr(a.skin_err, 1);
     }
+    double pn = __dadd_rn(p0, __dmul_rn(fdt, (double)a.dpdt[i]));
+    double ur = un, vr = vn;
+    if (a.sponge_w > 0.0) {
+        // relaxation towards (U, 0, 0), strength (distance from the
+        // sponge's downstream edge / width)^2
+        const double s = (a.sponge_x1 - xn) / a.sponge_w;
+        if (s > 0.0) {
+            const double k = fmin(1.0, 10.0 * a.sponge_U * dt / a.sponge_w * s * s);
+            ur = un + (a.sponge_U - un) * k;
+            vr = vn - vn * k;
+            pn = pn - pn * k;
+        }
+    }
     a.x[i] = xn;
     a.y[i] = yn;
-    a.u[i] = un;
-    a.v[i] = vn;
-    a.p[i] = __dadd_rn(p0, __dmul_rn(fdt, (double)a.dpdt[i]));
+    a.u[i] = ur;
+    a.v[i] = vr;
+    a.p[i] = pn;
 }
 
 template <typename R>

@@ -62,6 +62,9 @@ struct PecArgs {
     double disp_lim;
     int *skin_err;
     const double *dt;          // device {dt, 1 / dt}
+    // sponge layer (sph_params.sponge_width; corrector only): width (0:
+    // off), its downstream edge, the target speed
+    double sponge_w, sponge_x1, sponge_U;
     const double *x0, *y0, *u0, *v0, *p0;
     const R *dudt, *dvdt, *dpdt, *drx, *dry;
     double *x, *y, *u, *v, *p;

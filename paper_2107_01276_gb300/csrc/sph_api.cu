@@ -23,6 +23,8 @@ using namespace sph;
 
 namespace {
 
+// reason of the calling thread's last failed call made without a context
+// (sph_create, sph_cell_sort_noalloc): sph_last_error(NULL)
 thread_local std::string g_create_error;
 static std::atomic<int> g_live_ctx{0};   // contexts made by sph_create, not yet destroyed
 
@@ -702,6 +704,9 @@ static PecArgs<R> pec_args(sph_ctx *c, double f) {
     a.disp_lim = 1.5 * ((double)c->skin - 1.0);
     a.skin_err = (a.save && c->skin > 1.0f) ? c->d_skin_err : nullptr;
     a.dt = c->d_dt;
+    a.sponge_w = c->prm.sponge_width > 0 && f >= 1.0 ? c->prm.sponge_width : 0.0;
+    a.sponge_x1 = c->dom.lo[0] + c->prm.sponge_width;
+    a.sponge_U = c->prm.U_ref;
     a.x0 = c->f[F_X0];
     a.y0 = c->f[F_Y0];
     a.u0 = c->f[F_U0];
@@ -2496,6 +2501,7 @@ void sph_default_params(sph_params *p) {
     p->vort_k = 0.0;
     p->n_bg = 0;
     p->bg_capacity = 0;
+    p->sponge_width = 0.0;
 }
 
 sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out) {
@@ -2565,6 +2571,10 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
     sph_status gst = setup_fluid_grid(c, n, hmin, hmax);
     if (gst != SPH_OK) return gst;
     c->n = (int)n;
+    // a new state: a non-finite rate or skin overrun reported for the old
+    // one no longer applies
+    cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->s);
+    cudaMemsetAsync(c->d_skin_err, 0, sizeof(int), c->s);
 
     std::vector<double> tmp;
     auto put = [&](double *dst, const double *s, double dflt) {
@@ -2661,6 +2671,23 @@ sph_status sph_forces(sph_ctx *c, double *per_wall, double *total) {
     return cuda_check(c, "sph_forces");
 }
 
+sph_status sph_force_coefficients(sph_ctx *c, double U, double L, double *out) {
+    if (!c) return SPH_EINVAL;
+    c->err.clear();
+    if (!out) return fail(c, SPH_EINVAL, "sph_force_coefficients: out is NULL");
+    if (!(U > 0) || !(L > 0) || !isfinite(U) || !isfinite(L))
+        return fail(c, SPH_EINVAL, "sph_force_coefficients: U and L must be positive");
+    double tot[4];
+    sph_status st = sph_forces(c, nullptr, tot);
+    if (st != SPH_OK) return st;
+    // Eq. cdcl: force over the dynamic pressure times the length
+    const double q = 0.5 * c->prm.rho0 * U * U * L;
+    out[0] = tot[0] / q;
+    out[1] = tot[2] / q;
+    out[2] = tot[1] / q;
+    return SPH_OK;
+}
+
 sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
     if (!c) return SPH_EINVAL;
     c->err.clear();
@@ -2685,7 +2712,10 @@ sph_status sph_step(sph_ctx *c, int nsteps, double *t_out) {
         if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_step sync");
         *t_out = t;
         if ((st = check_overflow(c, "sph_step")) != SPH_OK) return st;
-        if (bad) return fail(c, SPH_ENONFINITE, "sph_step: non-finite rate");
+        if (bad) {
+            cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->s);   // reported once
+            return fail(c, SPH_ENONFINITE, "sph_step: non-finite rate");
+        }
     }
     return SPH_OK;
 }
@@ -2806,8 +2836,10 @@ sph_status sph_batch_step(sph_batch *b, sph_ctx *const *ctx, int k, double *t_ou
         cudaMemcpyAsync(&nf, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->s);
         sph_status s2 = check_overflow(c, "sph_batch_step");   // synchronises c->s
         t_out[q] = t;
-        if (s2 == SPH_OK && nf)
+        if (s2 == SPH_OK && nf) {
+            cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->s);   // reported once
             s2 = fail(c, SPH_ENONFINITE, "sph_batch_step: non-finite rate");
+        }
         if (s2 != SPH_OK) {
             if (failed) *failed = q;
             return s2;
@@ -3073,10 +3105,44 @@ static sph_status read_R(sph_ctx *c, const void *src, double *dst, long long n) 
     return SPH_OK;
 }
 
+static sph_status read_field(sph_ctx *c, sph_field field, void *dst, long long cap,
+                             long long *n_out);
+
 sph_status sph_read(sph_ctx *c, sph_field field, void *dst, long long cap,
                     long long *n_out) {
     if (!c) return SPH_EINVAL;
     c->err.clear();
+    const int f = (int)field;
+    if (!(f & SPH_READ_BY_ID)) return read_field(c, field, dst, cap, n_out);
+    // by id: the field and then the ids in the current order (a read that
+    // rebuilds first re-sorts), rows placed by the rank of their id
+    const sph_field base = (sph_field)(f & ~SPH_READ_BY_ID);
+    size_t es = 8;
+    if (base == SPH_F_NNB) {
+        es = 4;
+    } else if (!((base >= SPH_F_X && base <= SPH_F_CELLKEY) || base == SPH_F_OMEGA)) {
+        return fail(c, SPH_EINVAL, "sph_read: SPH_READ_BY_ID needs a per-particle field");
+    }
+    const long long n = c->n;
+    if (n_out) *n_out = n;
+    if (cap < n) return fail(c, SPH_ECAPACITY, "sph_read: buffer too small");
+    if (n == 0) return SPH_OK;
+    std::vector<unsigned char> tmp((size_t)n * es);
+    std::vector<int64_t> ids((size_t)n);
+    sph_status st = read_field(c, base, tmp.data(), n, nullptr);
+    if (st != SPH_OK) return st;
+    if ((st = read_field(c, SPH_F_ID, ids.data(), n, nullptr)) != SPH_OK) return st;
+    std::vector<uint32_t> order((size_t)n);
+    for (long long i = 0; i < n; ++i) order[i] = (uint32_t)i;
+    std::sort(order.begin(), order.end(),
+              [&](uint32_t a, uint32_t b) { return ids[a] < ids[b]; });
+    unsigned char *o = (unsigned char *)dst;
+    for (long long r = 0; r < n; ++r) memcpy(o + r * es, tmp.data() + (size_t)order[r] * es, es);
+    return SPH_OK;
+}
+
+static sph_status read_field(sph_ctx *c, sph_field field, void *dst, long long cap,
+                             long long *n_out) {
     if (!dst && cap > 0) return fail(c, SPH_EINVAL, "sph_read: dst is NULL");
     const long long n = c->n;
     auto need = [&](long long k) -> sph_status {
@@ -3400,5 +3466,13 @@ const char *sph_last_error(const sph_ctx *c) {
     if (!c) return g_create_error.c_str();
     return c->err.c_str();
 }
+
+}  // extern "C"
+
+namespace sph {
+void set_noctx_error(const char *why) { g_create_error = why ? why : ""; }
+}  // namespace sph
+
+extern "C" {
 
 }  // extern "C"

@@ -114,6 +114,10 @@ __device__ __forceinline__ double min_image(const Domain &d, int a,
     return s;
 }
 
+// Records the reason of a failed call made without a context for
+// sph_last_error(NULL) on the calling thread.
+void set_noctx_error(const char *why);
+
 // ------------------------------------------------------------- context --
 struct DeviceState;  // defined in sph_api.cu
 

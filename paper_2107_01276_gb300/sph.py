@@ -22,6 +22,7 @@ STATUS_NAMES = ["SPH_OK", "SPH_EINVAL", "SPH_ENOMEM", "SPH_ECUDA",
                 "SPH_ESTATE"]
 SPH_FLUID, SPH_WALL, SPH_BACKGROUND, SPH_REGION = 0, 1, 2, 3
 SPH_FP64, SPH_MIXED = 0, 1
+SPH_READ_BY_ID = 0x100
 
 FIELDS = ["x", "y", "u", "v", "p", "rho", "m", "h", "mmin", "mmax", "id",
           "beta", "pavg", "drx", "dry", "dpdt", "dudt", "dvdt", "nnb",
@@ -61,6 +62,7 @@ class Params(ctypes.Structure):
         ("bg_Nr", ctypes.c_double), ("bg_smooth_iters", ctypes.c_int),
         ("vort_k", ctypes.c_double), ("n_bg", ctypes.c_int),
         ("bg_capacity", ctypes.c_longlong),
+        ("sponge_width", ctypes.c_double),
     ]
 
 
@@ -177,6 +179,8 @@ def lib(build_if_missing: bool = True):
     L.sph_batch_graph_steps.argtypes = [ctypes.c_void_p]
     L.sph_batch_set_graphs.restype = ctypes.c_int
     L.sph_batch_set_graphs.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.sph_force_coefficients.restype = ctypes.c_int
+    L.sph_force_coefficients.argtypes = [ctx, ctypes.c_double, ctypes.c_double, _D]
     L.sph_probe_fma.restype = ctypes.c_int
     L.sph_probe_fma.argtypes = [ctypes.c_int, ctypes.c_void_p, _D, P(ctypes.c_int)]
     _lib = L
@@ -189,15 +193,6 @@ def _tune_dict(t: Tune) -> dict:
     for k in ("ms_cell", "ms_walk", "ms_team_a", "ms_team_b", "ms_walls"):
         out[k] = list(getattr(t, k))
     return out
-
-
-def coefficients(f: dict, rho0: float, U: float, L: float) -> dict:
-    """Eq. cdcl: pressure drag, skin-friction drag and lift coefficients of
-    a Simulation.forces() result, with the dynamic pressure rho0 U^2 / 2
-    and the characteristic length L."""
-    q = 0.5 * rho0 * U * U * L
-    return {"cd_p": float(f["fp"][0] / q), "cd_sf": float(f["fv"][0] / q),
-            "cl": float(f["fp"][1] / q)}
 
 
 def probe_fma(fp64: bool = False, stream: int = 0) -> tuple:
@@ -222,6 +217,12 @@ def cell_sort_noalloc(params: Params, n: int, x_ptr: int, y_ptr: int,
     return lib().sph_cell_sort_noalloc(ctypes.byref(params), int(n),
                                        v(x_ptr), v(y_ptr), v(h_ptr),
                                        v(key_ptr), v(perm_ptr), v(stream))
+
+
+def last_error() -> str:
+    """sph_last_error(NULL): the reason of the calling thread's last failed
+    call made without a context (sph_create, sph_cell_sort_noalloc)."""
+    return lib().sph_last_error(None).decode()
 
 
 def declared_functions():
@@ -353,12 +354,21 @@ class Simulation:
             out["per_wall"] = pw[:nw]
         return out
 
+    def coefficients(self, U: float, L: float) -> dict:
+        """sph_force_coefficients: pressure drag, skin-friction drag and lift
+        coefficients (Eq. cdcl) at the current state."""
+        out = (ctypes.c_double * 3)()
+        self._check(self._L.sph_force_coefficients(self._ctx, float(U), float(L), out))
+        return {"cd_p": out[0], "cd_sf": out[1], "cl": out[2]}
+
     def read_background(self) -> dict:
         """The background set (x, y, h, m, ds, id) in the library's order."""
         return {k: self.read("bg_" + k) for k in ("x", "y", "h", "m", "ds", "id")}
 
-    def read(self, field: str) -> np.ndarray:
-        f = FIELD[field]
+    def read(self, field: str, by_id: bool = False) -> np.ndarray:
+        """sph_read of one field; by_id: rows in ascending id order
+        (SPH_READ_BY_ID) instead of the library's current order."""
+        f = FIELD[field] | (SPH_READ_BY_ID if by_id else 0)
         dt = _FIELD_DTYPE.get(field, np.float64)
         n = ctypes.c_longlong(0)
         st = self._L.sph_read(self._ctx, f, None, 0, ctypes.byref(n))

@@ -90,7 +90,13 @@ def test_cylinder_coefficients_finite():
     for _ in range(5):
         sim.adapt()
         sim.step(1)
-    c = sph.coefficients(sim.forces(), pr["rho0"], 1.0, d["D"])
+    f = sim.forces()
+    c = sim.coefficients(1.0, d["D"])
     sim.close()
     assert all(math.isfinite(v) for v in c.values())
     assert c["cd_sf"] > 0
+    # Eq. cdcl on the same state: the forces over rho0 U^2 D / 2
+    q = 0.5 * pr["rho0"] * d["D"]
+    assert c["cd_p"] == pytest.approx(f["fp"][0] / q, rel=1e-13)
+    assert c["cd_sf"] == pytest.approx(f["fv"][0] / q, rel=1e-13)
+    assert c["cl"] == pytest.approx(f["fp"][1] / q, rel=1e-13)

@@ -262,3 +262,21 @@ def test_ragged_sizes_and_repeat_determinism():
         ref = _oracle_rhs(d, dt)
         for f in RHS_FIELDS:
             assert norm(a[f], ref[f], ref["s_" + f]) <= FP64_TOL
+
+
+def test_read_by_id():
+    """SPH_READ_BY_ID: rows by ascending id, equal to the host reordering of
+    the current-order rows; fields without per-particle rows refuse it."""
+    d = wl.perturbed(nx=30, ny=25, h_ratio=2.0, seed=13)
+    sim = _sim(d, sph.SPH_MIXED)
+    sim.step(2)
+    ref = by_id(sim, ["x", "u", "dpdt", "nnb"])
+    for f in ("x", "u", "dpdt", "nnb", "id"):
+        assert np.array_equal(sim.read(f, by_id=True), ref[f]), f
+    sim.rhs()    # a fresh build: the cell keys describe the current state
+    ref = by_id(sim, ["cellkey"])
+    assert np.array_equal(sim.read("cellkey", by_id=True), ref["cellkey"])
+    with pytest.raises(sph.SphError) as e:
+        sim.read("neigh_id", by_id=True)
+    assert e.value.status == sph.SPH_EINVAL
+    sim.close()
