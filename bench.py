@@ -112,11 +112,26 @@ WORKLOADS = {
                             background="rings", fluid="rings", vort_k=0.05,
                             n_bg=100, refine_calls=6, oracle_refine=0,
                             cpu_steps=1, capacity=2_000_000),
+    # the same run at its stated length: after the timed steps, 2000
+    # adaptation + PEC steps with the particle count and total mass sampled
+    # every 100 steps and the neighbour-count histogram at the end
+    "cylinder-re1000-2000": dict(kind="cylinder", Re=1000.0,
+                                 ds_min_over_D=1 / 1000, ds_max_over_D=1 / 4,
+                                 background="rings", fluid="rings", vort_k=0.05,
+                                 n_bg=100, refine_calls=6, oracle_refine=0,
+                                 cpu_steps=1, capacity=2_000_000,
+                                 long_run=2000),
     # a stream of independent adaptive simulations (half
     # cylinders at Re log-uniform in [20, 2000], half Taylor-Green vortices
     # at Re in [50, 500]), Poisson arrivals at 20/s, served concurrently
     "serving": dict(kind="serving", requests=32, rate=20.0, slots=8,
                     steps=40, sizes=(5000, 50000)),
+    # the serving stream at its stated shape: 256 requests of 5k-200k
+    # particles (the 32-request stream above is its quick form)
+    "serving-c5": dict(kind="serving", requests=256, rate=20.0, slots=8,
+                       steps=40, sizes=(5000, 200000)),
+    "serving-c5-batched": dict(kind="serving", requests=256, rate=20.0, slots=8,
+                               steps=40, sizes=(5000, 200000), batch=True),
     # the same stream of requests with the Taylor-Green half stepped
     # together by the batch stepper (continuous batching of the steps)
     "serving-batched": dict(kind="serving", requests=32, rate=20.0, slots=8,
@@ -578,6 +593,42 @@ def batch_arm(args):
     }
     print(json.dumps(line))
     return 0
+
+
+def cylinder_long_run(sim, steps, one_step):
+    """`steps` adaptation + PEC steps of a cylinder context: particle count
+    and total mass every 100 steps (mass relative to the first sample; split
+    and merge conserve it to rounding), wall time, and the neighbour counts
+    of the final state (N_i counts i itself; the paper reports neighbours
+    per particle with a mode of 30 and a maximum of 42 for its 1:250 run)."""
+    import torch
+    m0 = math.fsum(sim.read("m"))
+    samples = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        one_step(sim)
+        if (k + 1) % 100 == 0:
+            m = math.fsum(sim.read("m"))
+            samples.append({"step": k + 1, "n": int(sim.info()["n"]),
+                            "mass_rel_err": (m - m0) / m0})
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    sim.rhs()
+    nnb = sim.read("nnb").astype(np.int64)
+    hist = np.bincount(nnb)
+    excl = nnb - 1
+    ok = all(np.isfinite(sim.read(f)).all() for f in ("x", "y", "u", "v", "p"))
+    return {"steps": steps, "wall_s": wall, "t": float(sim.info()["t"]),
+            "samples": samples,
+            "max_mass_rel_err": max(abs(s["mass_rel_err"]) for s in samples),
+            "n_first": samples[0]["n"], "n_last": samples[-1]["n"],
+            "neighbours_incl_self": {"mode": int(np.argmax(hist)),
+                                     "mean": float(nnb.mean()), "max": int(nnb.max())},
+            "neighbours_excl_self": {"mode": int(np.argmax(np.bincount(excl))),
+                                     "mean": float(excl.mean()), "max": int(excl.max())},
+            "histogram_incl_self": {int(k): int(v) for k, v in enumerate(hist) if v},
+            "state_finite": bool(ok)}
 
 
 # ------------------------------------------------------ pair-kernel sweep --
@@ -1117,6 +1168,9 @@ def main():
     _, _, fams, _ = timed_steps(sim, k_breakdown, 1, lib_timing=True)
     tot_ms = float(np.sum(ms))
     tmax, units = replica_totals(dist, tot_ms, float(np.sum(ns)))
+    long_run = None
+    if wdef.get("long_run"):
+        long_run = cylinder_long_run(sim, wdef["long_run"], one_step)
     value = units / (tmax / 1e3)
 
     # force on the body after the timed steps (Eq. force-sph, Eq. cdcl);
@@ -1299,6 +1353,7 @@ def main():
         "forces": forces,
         "tuning": ({k: tuned[k] for k in ("cell_scale", "walk", "team_a", "team_b", "walls")}
                    if tuned else None),
+        "long_run": long_run,
     }
     print(json.dumps(line))
     if dist:

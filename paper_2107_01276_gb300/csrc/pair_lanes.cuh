@@ -13,8 +13,14 @@
 namespace sph {
 
 // List entries whose neighbour records a mixed-path pass loads ahead.
-constexpr int UNROLL_A = 2;
-constexpr int UNROLL_B = 2;
+#ifndef SPH_UNROLL_A
+#define SPH_UNROLL_A 3
+#endif
+#ifndef SPH_UNROLL_B
+#define SPH_UNROLL_B 2
+#endif
+constexpr int UNROLL_A = SPH_UNROLL_A;
+constexpr int UNROLL_B = SPH_UNROLL_B;
 
 // Membership test of a list entry when the lists carry a skin: the exact
 // predicate of N(i) on the separation the pass already has (FP32 band test

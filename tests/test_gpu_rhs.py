@@ -280,3 +280,27 @@ def test_read_by_id():
         sim.read("neigh_id", by_id=True)
     assert e.value.status == sph.SPH_EINVAL
     sim.close()
+
+
+@pytest.mark.slow
+def test_mixed_rhs_plain_norm_on_the_graded_band():
+    """Every mixed-path field, the shift dr included, within 2e-5 of the
+    oracle under the plain norm max |a - b| / max |b| as well as the
+    condition-aware one, on a band of the 1:250 graded strip holding every
+    resolution (~106k particles)."""
+    d = wl.graded_strip(n_target=1 << 20, ratio=250.0)
+    pt = d["particles"]
+    sel = pt["y"] < 0.1
+    sub = {k: v[sel].copy() for k, v in pt.items()}
+    dd = {"particles": sub, "params": dict(d["params"], periodic=(1, 0))}
+    sim = _sim(dd, sph.SPH_MIXED)
+    sim.rhs()
+    got = by_id(sim, list(RHS_FIELDS) + ["nnb"])
+    sim.close()
+    P = oracle.params(**dd["params"])
+    ref = oracle.rhs(P, oracle.dt(P, sub["h"]), oracle.make_state(sub))
+    assert np.array_equal(got["nnb"], ref["nnb"])
+    for f in RHS_FIELDS:
+        plain = float(np.abs(got[f] - ref[f]).max()) / float(np.abs(ref[f]).max())
+        assert plain <= MIXED_TOL, (f, plain)
+        assert norm(got[f], ref[f], ref["s_" + f]) <= MIXED_TOL, f
