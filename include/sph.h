@@ -477,6 +477,17 @@ sph_status sph_kernel_time(sph_ctx *ctx, int family, double *ms,
  * Errors: SPH_EINVAL (flops NULL, fp64 not 0/1), SPH_ENOMEM, SPH_ECUDA. */
 sph_status sph_probe_fma(int fp64, void *stream, double *flops, int *sms);
 
+/* Debug builds (the library compiled with SPH_DEBUG; the paper has no
+ * counterpart): the kernels check the indices of neighbour-list gathers,
+ * the cell ranges of the list build, the sort's gather and the compaction
+ * writes, and a failed check is counted and its access skipped (no trap,
+ * no fault: the context stays usable).  sph_debug_failures returns the
+ * failures counted since its last call on the current device (always 0 in
+ * a release build) and synchronises; sph_debug_build returns 1 in a debug
+ * build, else 0. */
+unsigned long long sph_debug_failures(void);
+int sph_debug_build(void);
+
 /* Cell keys and stable sort of a particle set, allocating nothing.
  *
  * The paper has no counterpart to this entry point.  It serves callers

@@ -4,6 +4,7 @@
 // feeds a decision (split test, merge admissibility and closest partner),
 // so the decisions match the definition bit for bit.
 #include "adapt.cuh"
+#include "debug_checks.cuh"
 #include "kernels.cuh"
 #include "neighbors.cuh"
 #include "team.cuh"
@@ -330,6 +331,8 @@ __global__ void k_compact(int n, const uint32_t *alive, const uint32_t *pos,
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !alive[i]) return;
     const uint32_t d = pos[i];
+    // a survivor never moves up: pos is the exclusive scan of alive
+    if (!SPH_DCHECK(d <= (uint32_t)i)) return;
     for (int k = 0; k < NSTATE; ++k)
         if (c.dst[k]) c.dst[k][d] = c.src[k][i];
     c.idst[d] = c.isrc[i];
@@ -613,5 +616,7 @@ int launch_mass_sum(cudaStream_t s, int n, const double *m, double *part,
     k_mass_final<<<1, 32, 0, s>>>(nb, part, out);
     return 2;
 }
+
+SPH_DEBUG_COUNTER(debug_failures_adapt)
 
 }  // namespace sph

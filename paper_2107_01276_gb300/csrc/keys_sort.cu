@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "batch.cuh"
+#include "debug_checks.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -623,6 +624,7 @@ __global__ void k_gather(int n, const uint32_t *__restrict__ perm, GatherList g)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t src = perm[i];
+    if (!SPH_DCHECK(src < (uint32_t)n)) return;
     for (int k = 0; k < g.nd; ++k) g.dst[k][i] = g.src[k][src];
     for (int k = 0; k < g.ni; ++k) g.idst[k][i] = g.isrc[k][src];
 }
@@ -674,6 +676,7 @@ __device__ __forceinline__ void gather_insert_at(int i, int n, const uint32_t *_
                                                  uint32_t tmask) {
     if (i >= n) return;
     uint32_t src = perm[i];
+    if (!SPH_DCHECK(src < (uint32_t)n)) return;
     for (int k = 0; k < g.nd; ++k) g.dst[k][i] = g.src[k][src];
     for (int k = 0; k < g.ni; ++k) g.idst[k][i] = g.isrc[k][src];
     uint64_t k = skey[i];
@@ -877,5 +880,7 @@ void build_cell_table(cudaStream_t s, int n, const uint64_t *skey,
                                                  tmaxh);
     *launches += 2;
 }
+
+SPH_DEBUG_COUNTER(debug_failures_keys_sort)
 
 }  // namespace sph

@@ -6,6 +6,7 @@
 // entries written into the coarser neighbours' lists) -> sort the reverse
 // segment of each list, so lists are deterministic: own entries in
 // traversal order, then the finer-level entries in ascending index.
+#include "debug_checks.cuh"
 #include "lists.cuh"
 #include "neighbors.cuh"
 #include "team.cuh"
@@ -139,6 +140,7 @@ __device__ __forceinline__ void list_place_at(const ListArgs &a, int i, const Te
         for (uint32_t k = tm.lane; k < own; k += T) {
             const uint32_t ent = row[k];
             const uint32_t j = ent & ~STAGE_COARSE;
+            if (!SPH_DCHECK(j < (uint32_t)a.n)) continue;
             if (base + k < cap) a.list[base + k] = j;
             if (ent & STAGE_COARSE) {
                 const uint32_t rp = a.off[j] + a.own[j] + atomicAdd(&a.rev[j], 1u);
@@ -367,6 +369,7 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
                                  s, e, &hc)) {
                     const float Rc = a.skin * 3.0f * fmaxf(hmx, hc);
                     if (!(g2 < Rc * Rc)) s = e = 0;
+                    if (!SPH_DCHECK(s <= e && e <= (uint32_t)a.n)) s = e = 0;
                 } else {
                     s = e = 0;
                 }
@@ -885,5 +888,7 @@ void build_lists_fill(cudaStream_t s, ListArgs a, bool mixed, bool queue,
         a.off, a.own, a.list, a.longq, a.nlong);
     *launches += 4;
 }
+
+SPH_DEBUG_COUNTER(debug_failures_lists)
 
 }  // namespace sph

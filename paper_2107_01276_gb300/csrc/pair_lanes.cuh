@@ -6,6 +6,7 @@
 // same operations in the same order however it is launched.
 #pragma once
 
+#include "debug_checks.cuh"
 #include "kernels.cuh"
 #include "pair_passes.cuh"
 #include "team.cuh"
@@ -311,7 +312,11 @@ __device__ __forceinline__ void pass_a_list(const PassAArgs<R> &a, int i,
             float4 pp[U];
             R mm[U], qq[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) jj[u] = (int)__ldg(&a.list[k + u * T]);
+            for (int u = 0; u < U; ++u) {
+                jj[u] = (int)__ldg(&a.list[k + u * T]);
+                // an index out of range (debug builds) reads i instead
+                if (!SPH_DCHECK((unsigned)jj[u] < (unsigned)a.n)) jj[u] = i;
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 pp[u] = __ldg(&a.pk[jj[u]]);
@@ -322,12 +327,14 @@ __device__ __forceinline__ void pass_a_list(const PassAArgs<R> &a, int i,
             for (int u = 0; u < U; ++u) body(jj[u], pp[u], mm[u], qq[u]);
         }
         for (; k < e; k += T) {
-            const int j = (int)__ldg(&a.list[k]);
+            int j = (int)__ldg(&a.list[k]);
+            if (!SPH_DCHECK((unsigned)j < (unsigned)a.n)) j = i;
             body(j, __ldg(&a.pk[j]), a.m[j], a.p[j]);
         }
     } else {
         for (uint32_t k = b + tm.lane; k < e; k += T) {
             const int j = (int)__ldg(&a.list[k]);
+            if (!SPH_DCHECK((unsigned)j < (unsigned)a.n)) continue;
             R dx, dy, r2, hj;
             sp.get(a.d, a.an, a.x, a.y, a.h, a.pk, j, dx, dy, r2, hj);
             if (a.filter && !skin_member<R>(a.d, a.an, r2, hi, hj, xid, yid, hid,
@@ -365,7 +372,10 @@ __device__ __forceinline__ void pass_b_list(const PassBArgs<R> &a, int i,
             int jj[U];
             float4 pp[U], AA[U], BB[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) jj[u] = (int)__ldg(&a.list[k + u * T]);
+            for (int u = 0; u < U; ++u) {
+                jj[u] = (int)__ldg(&a.list[k + u * T]);
+                if (!SPH_DCHECK((unsigned)jj[u] < (unsigned)a.n)) jj[u] = i;
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 pp[u] = __ldg(&a.pk[jj[u]]);
@@ -376,12 +386,14 @@ __device__ __forceinline__ void pass_b_list(const PassBArgs<R> &a, int i,
             for (int u = 0; u < U; ++u) body(jj[u], pp[u], AA[u], BB[u]);
         }
         for (; k < e; k += T) {
-            const int j = (int)__ldg(&a.list[k]);
+            int j = (int)__ldg(&a.list[k]);
+            if (!SPH_DCHECK((unsigned)j < (unsigned)a.n)) j = i;
             body(j, __ldg(&a.pk[j]), a.nbA[j], a.nbB[j]);
         }
     } else {
         for (uint32_t k = b + tm.lane; k < e; k += T) {
             const int j = (int)__ldg(&a.list[k]);
+            if (!SPH_DCHECK((unsigned)j < (unsigned)a.n)) continue;
             if (j == i) continue;
             R dx, dy, r2;
             if (a.filter) {

@@ -686,4 +686,6 @@ void launch_float_to_double(cudaStream_t s, int n, const float *src,
     if (n > 0) k_float_to_double<<<nblk(n, 256), 256, 0, s>>>(n, src, dst);
 }
 
+SPH_DEBUG_COUNTER(debug_failures_pairs)
+
 }  // namespace sph

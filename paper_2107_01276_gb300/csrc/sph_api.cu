@@ -3475,4 +3475,17 @@ void set_noctx_error(const char *why) { g_create_error = why ? why : ""; }
 
 extern "C" {
 
+unsigned long long sph_debug_failures(void) {
+    return debug_failures_keys_sort() + debug_failures_adapt() + debug_failures_lists() +
+           debug_failures_pairs();
+}
+
+int sph_debug_build(void) {
+#ifdef SPH_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 }  // extern "C"

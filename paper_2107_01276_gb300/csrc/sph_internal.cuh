@@ -118,6 +118,13 @@ __device__ __forceinline__ double min_image(const Domain &d, int a,
 // sph_last_error(NULL) on the calling thread.
 void set_noctx_error(const char *why);
 
+// Bounds-check failures counted by each translation unit's kernels since
+// its last call (debug builds, debug_checks.cuh; 0 otherwise).
+unsigned long long debug_failures_keys_sort();
+unsigned long long debug_failures_adapt();
+unsigned long long debug_failures_lists();
+unsigned long long debug_failures_pairs();
+
 // ------------------------------------------------------------- context --
 struct DeviceState;  // defined in sph_api.cu
 

@@ -116,13 +116,16 @@ _lib = None
 
 
 def lib(build_if_missing: bool = True):
-    """Load libsph_gb300.so (building it first if asked and needed)."""
+    """Load libsph_gb300.so (building it first if asked and needed); with
+    SPH_GB300_DEBUG_LIB=1 in the environment, the debug build with device
+    bounds checks (libsph_gb300_debug.so) instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    debug = os.environ.get("SPH_GB300_DEBUG_LIB") == "1"
+    path = _build.LIB_DEBUG if debug else _build.LIB
     if build_if_missing:
-        path = _build.build()
+        path = _build.build(debug=debug)
     if not os.path.exists(path):
         raise OSError("libsph_gb300.so not built: %s" % path)
     L = ctypes.CDLL(path)
@@ -181,6 +184,10 @@ def lib(build_if_missing: bool = True):
     L.sph_batch_set_graphs.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.sph_force_coefficients.restype = ctypes.c_int
     L.sph_force_coefficients.argtypes = [ctx, ctypes.c_double, ctypes.c_double, _D]
+    L.sph_debug_failures.restype = ctypes.c_ulonglong
+    L.sph_debug_failures.argtypes = []
+    L.sph_debug_build.restype = ctypes.c_int
+    L.sph_debug_build.argtypes = []
     L.sph_probe_fma.restype = ctypes.c_int
     L.sph_probe_fma.argtypes = [ctypes.c_int, ctypes.c_void_p, _D, P(ctypes.c_int)]
     _lib = L
@@ -217,6 +224,17 @@ def cell_sort_noalloc(params: Params, n: int, x_ptr: int, y_ptr: int,
     return lib().sph_cell_sort_noalloc(ctypes.byref(params), int(n),
                                        v(x_ptr), v(y_ptr), v(h_ptr),
                                        v(key_ptr), v(perm_ptr), v(stream))
+
+
+def debug_failures() -> int:
+    """sph_debug_failures: bounds-check failures counted by a debug build
+    since the last call (always 0 in a release build)."""
+    return int(lib().sph_debug_failures())
+
+
+def debug_build() -> bool:
+    """sph_debug_build: whether the loaded library has the checks."""
+    return bool(lib().sph_debug_build())
 
 
 def last_error() -> str:
