@@ -592,6 +592,27 @@ __global__ void __launch_bounds__(128) k_list_tile_queue(ListArgs a) {
 constexpr int SORT_REG = 32;
 constexpr int SORT_SMEM = 1024;
 
+// Ascending sort of seg[0 .. len) (len <= K) in registers: odd-even
+// transposition over K slots, fixed indices, padding at the top.
+template <int K>
+__device__ __forceinline__ void sort_regs(uint32_t *seg, uint32_t len) {
+    uint32_t r[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) r[t] = t < (int)len ? seg[t] : 0xffffffffu;
+#pragma unroll
+    for (int round = 0; round < K; ++round) {
+#pragma unroll
+        for (int t = round & 1; t + 1 < K; t += 2) {
+            const uint32_t lo = min(r[t], r[t + 1]), hi = max(r[t], r[t + 1]);
+            r[t] = lo;
+            r[t + 1] = hi;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < K; ++t)
+        if (t < (int)len) seg[t] = r[t];
+}
+
 __device__ __forceinline__ void list_sort_rev_at(int i, int n, const uint32_t *off,
                                                  const uint32_t *own, uint32_t *list,
                                                  uint32_t cap, uint32_t *longq,
@@ -604,22 +625,13 @@ __device__ __forceinline__ void list_sort_rev_at(int i, int n, const uint32_t *o
         longq[atomicAdd(nlong, 1u)] = (uint32_t)i;
         return;
     }
-    uint32_t r[SORT_REG];
-#pragma unroll
-    for (int t = 0; t < SORT_REG; ++t) r[t] = t < (int)len ? list[b + t] : 0xffffffffu;
-    // odd-even transposition sort, fixed indices (stays in registers)
-#pragma unroll
-    for (int round = 0; round < SORT_REG; ++round) {
-#pragma unroll
-        for (int t = round & 1; t + 1 < SORT_REG; t += 2) {
-            uint32_t lo = min(r[t], r[t + 1]), hi = max(r[t], r[t + 1]);
-            r[t] = lo;
-            r[t + 1] = hi;
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < SORT_REG; ++t)
-        if (t < (int)len) list[b + t] = r[t];
+    // the network no wider than the segment needs (most are short)
+    if (len <= 8)
+        sort_regs<8>(list + b, len);
+    else if (len <= 16)
+        sort_regs<16>(list + b, len);
+    else
+        sort_regs<SORT_REG>(list + b, len);
 }
 
 __global__ void k_list_sort_rev(int n, const uint32_t *off, const uint32_t *own,

@@ -439,6 +439,7 @@ __device__ __forceinline__ bool pred_fp64(const Domain &d, double xi,
 // Anchor lattice for FP32 separations (mixed path).
 struct Anchor {
     float A[2];      // anchor cell side per axis (float)
+    float iA[2];     // 1 / side, rounded to float
     int n[2];        // anchor cells per axis
     int periodic[2];
 };
@@ -463,25 +464,29 @@ __device__ __forceinline__ void anchor_sep(const Anchor &an, const float4 &pi,
 }
 
 // Anchor record {xl, yl, h, gx | gy << 16} of a position: anchor cell g =
-// floor((x - lo) / A) (by a product with 1/A, clamped to the lattice; any
-// neighbouring cell would do, the offset then stays within about A, which is
-// all the separation error bound assumes) and the offset xl = x - lo - g A
-// rounded to FP32.
+// floor((x - lo) / A) from the FP32 image of x - lo (clamped to the
+// lattice; next to a cell edge it may be the neighbouring cell, which only
+// moves the offset to within A / 256 outside [0, A): the separation error
+// bound assumes an offset within about A) and the offset xl = x - lo - g A
+// in FP64 with one rounding, then rounded to FP32.  One FP64 subtraction,
+// one FMA and three conversions a coordinate (FP64 work is slow on this
+// GPU).
 __device__ __forceinline__ float4 anchor_record(double x, double y, double h,
                                                 const double *lo,
                                                 const double *A,
                                                 const double *invA,
                                                 const Anchor &an) {
+    (void)invA;
     const double q[2] = {x, y};
     int g[2];
     float xl[2];
 #pragma unroll
     for (int ax = 0; ax < 2; ++ax) {
         const double t = __dsub_rn(q[ax], lo[ax]);
-        const double c = floor(t * invA[ax]);
-        const int gi = c < 0.0 ? 0 : (c > (double)(an.n[ax] - 1) ? an.n[ax] - 1 : (int)c);
+        const float c = floorf((float)t * an.iA[ax]);
+        const int gi = c < 0.0f ? 0 : (c > (float)(an.n[ax] - 1) ? an.n[ax] - 1 : (int)c);
         g[ax] = gi;
-        xl[ax] = (float)__dsub_rn(t, __dmul_rn((double)gi, A[ax]));
+        xl[ax] = (float)__fma_rn(-(double)gi, A[ax], t);
     }
     return make_float4(xl[0], xl[1], (float)h,
                        __uint_as_float((unsigned)g[0] | ((unsigned)g[1] << 16)));

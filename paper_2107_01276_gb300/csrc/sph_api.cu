@@ -1217,6 +1217,7 @@ static sph_status setup_fluid_grid(sph_ctx *c, long long n, double hmin,
             if (na > 65535) na = 65535;
         }
         an.A[a] = (float)Ad[a];
+        an.iA[a] = (float)(1.0 / Ad[a]);
         an.n[a] = (int)na;
         an.periodic[a] = c->dom.periodic[a];
     }
