@@ -283,6 +283,8 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
     const float4 pC = __ldg(&a.pk[cs]);
     float rxi = 0.0f, ryi = 0.0f, Ri = 0.0f;
     float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f, hmx = 0.0f;
+    // the chunk's bounding box in reference-relative coordinates
+    float rxlo = 3.0e38f, rxhi = -3.0e38f, rylo = 3.0e38f, ryhi = -3.0e38f;
     if (act) {
         const float4 pi = __ldg(&a.pk[i]);
         anchor_sep(a.an, pi, pC, rxi, ryi);
@@ -291,6 +293,8 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
         xlo = xhi = q.x;
         ylo = yhi = q.y;
         hmx = pi.z;
+        rxlo = rxhi = rxi;
+        rylo = ryhi = ryi;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -299,9 +303,14 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
         ylo = fminf(ylo, __shfl_xor_sync(0xffffffffu, ylo, o));
         yhi = fmaxf(yhi, __shfl_xor_sync(0xffffffffu, yhi, o));
         hmx = fmaxf(hmx, __shfl_xor_sync(0xffffffffu, hmx, o));
+        rxlo = fminf(rxlo, __shfl_xor_sync(0xffffffffu, rxlo, o));
+        rxhi = fmaxf(rxhi, __shfl_xor_sync(0xffffffffu, rxhi, o));
+        rylo = fminf(rylo, __shfl_xor_sync(0xffffffffu, rylo, o));
+        ryhi = fmaxf(ryhi, __shfl_xor_sync(0xffffffffu, ryhi, o));
     }
     const float xc = 0.5f * (xlo + xhi), yc = 0.5f * (ylo + yhi);
     const float bx = 0.5f * (xhi - xlo), by = 0.5f * (yhi - ylo);
+    const float Rmx = a.skin * (3.0f * hmx);   // largest pair radius of a chunk particle
     const uint32_t W = a.stage_w;
     uint32_t k = 0;
     if (DIRECT && act) k = a.off[i];
@@ -384,17 +393,24 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
             const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
             const uint32_t exc = inc - cnt;
             for (uint32_t q0 = 0; q0 < total; q0 += TILE_CAP) {
-                const uint32_t m = min((uint32_t)TILE_CAP, total - q0);
-                // stage: slot u holds candidate q0 + u; its cell is the first
-                // lane whose inclusive count exceeds it (binary search over
-                // the lanes), TILE_LD independent loads per lane in flight
-                for (uint32_t u0 = 0; u0 < m; u0 += 32 * TILE_LD) {
+                const uint32_t mq = min((uint32_t)TILE_CAP, total - q0);
+                // stage: candidate q0 + u; its cell is the first lane whose
+                // inclusive count exceeds it (binary search over the lanes),
+                // TILE_LD independent loads per lane in flight.  Candidates
+                // farther from the chunk's bounding box than the largest
+                // pair radius they could have (with a margin far above FP32
+                // error) are no member of any particle of the chunk and are
+                // not staged; the others keep their order (ballot
+                // compaction), so the test loop sees the same members in the
+                // same order.
+                uint32_t m = 0;
+                for (uint32_t u0 = 0; u0 < mq; u0 += 32 * TILE_LD) {
                     float4 v[TILE_LD];
                     uint32_t jj[TILE_LD];
 #pragma unroll
                     for (int r = 0; r < TILE_LD; ++r) {
                         const uint32_t u = u0 + 32 * r + lane;
-                        const uint32_t qq = q0 + min(u, m - 1);
+                        const uint32_t qq = q0 + min(u, mq - 1);
                         int pos = 0;
 #pragma unroll
                         for (int st = 16; st; st >>= 1) {
@@ -404,17 +420,29 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
                         const uint32_t st0 = __shfl_sync(0xffffffffu, s, pos);
                         const uint32_t ex0 = __shfl_sync(0xffffffffu, exc, pos);
                         jj[r] = st0 + (qq - ex0);
-                        if (u < m) v[r] = __ldg(&a.pk[jj[r]]);
+                        if (u < mq) v[r] = __ldg(&a.pk[jj[r]]);
                     }
 #pragma unroll
                     for (int r = 0; r < TILE_LD; ++r) {
                         const uint32_t u = u0 + 32 * r + lane;
-                        if (u < m) {
-                            float rx, ry;
+                        float rx = 0.0f, ry = 0.0f, Rj = 0.0f;
+                        bool keep = false;
+                        if (u < mq) {
                             anchor_sep(a.an, v[r], pC, rx, ry);
-                            sc[u] = make_float4(rx, ry, a.skin * (3.0f * v[r].z),
-                                                __uint_as_float(jj[r]));
+                            Rj = a.skin * (3.0f * v[r].z);
+                            keep = true;
+                            if (!wrap) {
+                                const float gx = fmaxf(fmaxf(rxlo - rx, rx - rxhi), 0.0f);
+                                const float gy = fmaxf(fmaxf(rylo - ry, ry - ryhi), 0.0f);
+                                const float Rm = fmaxf(Rmx, Rj) * 1.01f;
+                                keep = fmaf(gx, gx, gy * gy) < Rm * Rm;
+                            }
                         }
+                        const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                        if (keep)
+                            sc[m + (uint32_t)__popc(kb & ((1u << lane) - 1u))] =
+                                make_float4(rx, ry, Rj, __uint_as_float(jj[r]));
+                        m += (uint32_t)__popc(kb);
                     }
                 }
                 __syncwarp();
