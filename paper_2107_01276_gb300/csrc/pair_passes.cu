@@ -28,6 +28,13 @@ namespace sph {
 #endif
 constexpr int PASS_A_BLOCKS = SPH_PASS_A_BLOCKS;
 constexpr int PASS_B_BLOCKS = SPH_PASS_B_BLOCKS;
+// Team forms (T > 1: small and walled sets) and the batched forms keep six
+// and five blocks (80 / 96 registers): at the eight-block cap their wall
+// loops spill.
+template <typename R, int T>
+constexpr int pass_blocks(int lane1) {
+    return sizeof(R) == 4 ? (T == 1 ? lane1 : 6) : 1;
+}
 
 // ---------------------------------------------------------------- pass A --
 // Pass A of particle i over its list (arithmetic in PassALane): a team of T
@@ -43,7 +50,7 @@ __device__ __forceinline__ void pass_a_at(const PassAArgs<R> &a, int i,
 }
 
 template <typename R, int T>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_A_BLOCKS : 1)
+__global__ void __launch_bounds__(128, (pass_blocks<R, T>(PASS_A_BLOCKS)))
     k_pass_a(PassAArgs<R> a) {
     const Team<T> tm;
     const int i = Team<T>::particle();
@@ -53,8 +60,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_A_BLOCKS : 1)
 
 // ---------------------------------------------------------------- pass B --
 // Pass B of particle i over its list (arithmetic in PassBLane).
-// (float: at most 64 registers, eight 128-thread blocks per SM, measured
-// faster than six at 80 registers on the graded 1:250 strip)
+// (float, one lane per particle: at most 64 registers, eight 128-thread
+// blocks per SM, measured faster than six at 80 registers on the graded
+// 1:250 strip)
 template <typename R, int T>
 __device__ __forceinline__ void pass_b_at(const PassBArgs<R> &a, int i,
                                           const Team<T> &tm) {
@@ -73,7 +81,7 @@ __device__ __forceinline__ void pass_b_at(const PassBArgs<R> &a, int i,
 }
 
 template <typename R, int T>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? PASS_B_BLOCKS : 1)
+__global__ void __launch_bounds__(128, (pass_blocks<R, T>(PASS_B_BLOCKS)))
     k_pass_b(PassBArgs<R> a) {
     const Team<T> tm;
     const int i = Team<T>::particle();
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(BATCH_THREADS)
 }
 
 template <typename R, int T>
-__global__ void __launch_bounds__(BATCH_THREADS, sizeof(R) == 4 ? PASS_B_BLOCKS - 1 : 1)
+__global__ void __launch_bounds__(BATCH_THREADS, sizeof(R) == 4 ? 5 : 1)
     k_pass_b_batch(const PassBArgs<R> *__restrict__ args, BatchSpan sp) {
     const Team<T> tm;
     for (int item = blockIdx.x; item < sp.total; item += gridDim.x) {
