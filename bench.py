@@ -449,7 +449,9 @@ def batch_arm(args):
     particle-steps of all instances per second over K timed batch steps
     (CUDA events on the batch stream, L2 flushed between steps);
     streams_value: the same instances stepped one by one with sph_step on
-    their own streams (host clock around K steps); e2e: every step loads
+    their own streams (host clock around K steps); fp64_*: the same
+    instances in the plain FP64 form, batched and one by one; e2e: every
+    step loads
     each instance from pinned host buffers, runs the batch step and reads
     x, y, u, v, p back."""
     import ctypes
@@ -480,7 +482,7 @@ def batch_arm(args):
         sm = sph.Simulation(P, st.cuda_stream)
         sm.load(d["particles"])
         sims.append(sm)
-        states.append(d["particles"])
+        states.append((d["params"], d["particles"]))
     ntot = sum(sm.info()["n"] for sm in sims)
     b = sph.Batch(len(sims), bs.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -527,11 +529,48 @@ def batch_arm(args):
             sm.step(1, want_time=False)
     torch.cuda.synchronize()
     streams_value = ntot * K / (time.perf_counter() - t0)
+    # the plain FP64 form of the same instances: batched (CUDA events, L2
+    # flushed, as above) and one by one on their own streams
+    fp64_value = fp64_streams = None
+    if not args.no_fp64:
+        sims64 = []
+        for (prm, parts), st in zip(states, own):
+            P = sph.make_params(prm, precision=sph.SPH_FP64, capacity=len(parts["x"]))
+            sm = sph.Simulation(P, st.cuda_stream)
+            sm.load(parts)
+            sims64.append(sm)
+        b64 = sph.Batch(len(sims64), bs.cuda_stream)
+        for _ in range(W):
+            b64.step(sims64)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(bs):
+            for k in range(K):
+                flush.zero_()
+                evs[k][0].record(bs)
+                b64.step(sims64)
+                evs[k][1].record(bs)
+        torch.cuda.synchronize()
+        ms64 = float(np.sum([a.elapsed_time(c) for a, c in evs]))
+        t64, u64 = replica_totals(dist, ms64, ntot * K)
+        fp64_value = u64 / (t64 / 1e3)
+        for _ in range(W):
+            for sm in sims64:
+                sm.step(1, want_time=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            for sm in sims64:
+                sm.step(1, want_time=False)
+        torch.cuda.synchronize()
+        fp64_streams = ntot * K / (time.perf_counter() - t0)
+        b64.close()
+        for sm in sims64:
+            sm.close()
     # e2e: pinned host state in, batch step, x, y, u, v, p out
     fields_in = ("x", "y", "u", "v", "p", "rho", "m", "h")
     keep, srcs, outs = [], [], []
     h2d = d2h = 0
-    for sm, st0 in zip(sims, states):
+    for sm, (_, st0) in zip(sims, states):
         n = len(st0["x"])
         src = sph.Particles()
         for k in fields_in:
@@ -583,6 +622,10 @@ def batch_arm(args):
                            "square, h/dx 1.2; one sph_batch_step per step"},
         "streams_value": streams_value,
         "batch_over_streams": value / streams_value,
+        "fp64_batched_value": fp64_value,
+        "fp64_streams_value": fp64_streams,
+        "mixed_batched_over_fp64_batched": (value / fp64_value) if fp64_value else None,
+        "mixed_batched_over_fp64_streams": (value / fp64_streams) if fp64_streams else None,
         "graph_steps": graph_steps,
         "roofline": None,
         "clocks": clocks,
