@@ -142,6 +142,12 @@ WORKLOADS = {
     # a captured graph); compared with the same instances stepped one by
     # one on their own streams
     "batched-tg32": dict(kind="batch", instances=32, sizes=(1600, 20000)),
+    # 8 adaptive cylinders (Re log-uniform in [20, 2000], finest spacing
+    # D/25 to D/60, about 3k to 15k fluid particles each, ring background)
+    # adapted and stepped together; compared with the same instances one
+    # by one and on one host thread each
+    "batched-cyl8": dict(kind="batch-adaptive", instances=8, Re=(20.0, 2000.0),
+                         inv=(25.0, 60.0), refine_calls=8),
 }
 DEFAULT_WORKLOAD = "graded-16M"
 
@@ -354,7 +360,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    if WORKLOADS[args.workload]["kind"] in ("serving", "batch"):
+    if WORKLOADS[args.workload]["kind"] in ("serving", "batch", "batch-adaptive"):
         print(json.dumps({"impl": "reference", "unavailable":
                           "the oracle runs one simulation at a time; the "
                           "%s workload has no reference arm"
@@ -631,6 +637,202 @@ def batch_arm(args):
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "particle-steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------- batched adaptation ----
+def batch_adapt_arm(args):
+    """Several adaptive cylinders advanced together: each step is one
+    sph_batch_adapt over all of them (their adaptations in lockstep, one
+    host synchronisation per phase for all) and one sph_batch_step.  The
+    adaptation synchronises with the host, so every step is timed on the
+    host clock around the step and a device synchronisation, the L2 flush
+    outside it.  value: particle-steps (particles after each adaptation)
+    of all instances per second; streams_value: the same instances, each
+    sph_adapt + sph_step in turn from one thread on their own streams;
+    threads_value: one host thread per instance doing the same (the
+    serving loop's workers); fp64_batched_value: the plain FP64 form of the
+    same instances, batched; e2e: the batched step followed by a read of
+    x, y, u, v, p of every instance to pinned host memory."""
+    import threading
+
+    import torch
+    from paper_2107_01276_gb300 import sph, workloads as wl
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sph.lib()
+    w = WORKLOADS[args.workload]
+    rng = np.random.default_rng(13 + rank)
+    specs = []
+    for _ in range(w["instances"]):
+        Re = float(np.exp(rng.uniform(np.log(w["Re"][0]), np.log(w["Re"][1]))))
+        inv = float(np.exp(rng.uniform(np.log(w["inv"][0]), np.log(w["inv"][1]))))
+        specs.append((Re, inv))
+    bs = torch.cuda.Stream()
+    own = [torch.cuda.Stream() for _ in specs]
+
+    def instances(precision):
+        sims = []
+        for (Re, inv), st in zip(specs, own):
+            d = wl.cylinder(Re=Re, ds_min_over_D=1.0 / inv, background="rings")
+            cap = int(4 * 9000 * (inv / 50.0) ** 1.2) + 20000
+            P = sph.make_params(d["params"], precision=precision, capacity=cap)
+            sm = sph.Simulation(P, st.cuda_stream)
+            sm.load(d["particles"])
+            sm.load(d["walls"], kind=sph.SPH_WALL)
+            sm.load(d["background_rings"], kind=sph.SPH_BACKGROUND)
+            for _ in range(w["refine_calls"]):
+                sm.adapt()
+            sims.append(sm)
+        return sims
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K, W = args.steps, args.warmup
+
+    def timed(step, K, W):
+        """(seconds over K steps, particle-steps) with the flush between."""
+        for _ in range(W):
+            step()
+        torch.cuda.synchronize()
+        total, units = 0.0, 0
+        for _ in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            units += step()
+            torch.cuda.synchronize()
+            total += time.perf_counter() - t0
+        return total, units
+
+    sims = instances(sph.SPH_MIXED)
+    b = sph.Batch(len(sims), bs.cuda_stream)
+
+    def batched():
+        z = b.adapt(sims)
+        b.step(sims)
+        return sum(s["n_after"] for s in z)
+
+    l0 = b.launches + sum(sm.info()["launches"] for sm in sims)
+    clk = ClockSampler(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    sec, units = timed(batched, K, W)
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    launches = b.launches + sum(sm.info()["launches"] for sm in sims) - l0
+    tmax, utot = replica_totals(dist, sec, units)
+    value = utot / tmax
+    ms_per_step = 1e3 * sec / K
+    n_now = [sm.info()["n"] for sm in sims]
+    # e2e: the batched step, then x, y, u, v, p of every instance read back
+    outs = [{k: torch.empty(cap_n, dtype=torch.float64).pin_memory().numpy()
+             for k in ("x", "y", "u", "v", "p")}
+            for cap_n in (4 * n + 4096 for n in n_now)]
+    d2h = [0]
+
+    def batched_e2e():
+        u = batched()
+        nb = 0
+        for sm, o in zip(sims, outs):
+            for k in o:
+                nb += 8 * sm.read_into(k, o[k])
+        d2h[0] = nb
+        return u
+
+    sec_e, units_e = timed(batched_e2e, max(3, K // 2), 1)
+    te, ue = replica_totals(dist, sec_e, units_e)
+    e2e_val = ue / te
+    b.close()
+    for sm in sims:
+        sm.close()
+    # the same instances one by one from one thread
+    sims = instances(sph.SPH_MIXED)
+
+    def one_by_one():
+        u = 0
+        for sm in sims:
+            u += sm.adapt()["n_after"]
+            sm.step(1, want_time=False)
+        return u
+
+    sec_s, units_s = timed(one_by_one, K, W)
+    for sm in sims:
+        sm.close()
+    # one host thread per instance
+    sims = instances(sph.SPH_MIXED)
+
+    def threaded():
+        res = [0] * len(sims)
+
+        def run(q):
+            res[q] = sims[q].adapt()["n_after"]
+            sims[q].step(1, want_time=False)
+
+        th = [threading.Thread(target=run, args=(q,)) for q in range(len(sims))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        return sum(res)
+
+    sec_t, units_t = timed(threaded, K, W)
+    for sm in sims:
+        sm.close()
+    fp64_value = None
+    if not args.no_fp64:
+        sims = instances(sph.SPH_FP64)
+        b = sph.Batch(len(sims), bs.cuda_stream)
+        sec64, units64 = timed(batched, K, W)
+        t64, u64 = replica_totals(dist, sec64, units64)
+        fp64_value = u64 / t64
+        b.close()
+        for sm in sims:
+            sm.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    streams_value = units_s / sec_s
+    threads_value = units_t / sec_t
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+        "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-pair/f64-state",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "instances": len(specs),
+                   "particles_per_instance": n_now,
+                   "Re": [round(r, 1) for r, _ in specs],
+                   "D_over_ds_min": [round(v, 1) for _, v in specs],
+                   "precision": "mixed",
+                   "l2": "flushed between steps (256 MiB write), outside the timed window",
+                   "timing": "host clock around each step and a device synchronisation",
+                   "desc": "flow past a cylinder, ring background, spacing "
+                           "D/ds_min to D/2, refined by %d sph_adapt calls; a step "
+                           "is sph_batch_adapt + sph_batch_step over all "
+                           "instances" % w["refine_calls"]},
+        "streams_value": streams_value,
+        "batch_over_streams": value / streams_value,
+        "threads_value": threads_value,
+        "batch_over_threads": value / threads_value,
+        "fp64_batched_value": fp64_value,
+        "mixed_batched_over_fp64_batched": (value / fp64_value) if fp64_value else None,
+        "roofline": None,
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h[0]},
         "gpu_launches": launches,
         "cpu_baseline": None,
     }
@@ -1103,6 +1305,8 @@ def main():
         return reference_arm(args)
     if WORKLOADS[args.workload]["kind"] == "serving":
         return serving_arm(args)
+    if WORKLOADS[args.workload]["kind"] == "batch-adaptive":
+        return batch_adapt_arm(args)
     if WORKLOADS[args.workload]["kind"] == "batch":
         return batch_arm(args)
     if WORKLOADS[args.workload]["kind"] == "graded":

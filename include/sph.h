@@ -327,6 +327,32 @@ long long sph_batch_graph_steps(const sph_batch *batch);
  * m_min/m_max are already refreshed). */
 sph_status sph_adapt(sph_ctx *ctx, sph_adapt_stats *out);
 
+/* sph_adapt for each of the k distinct contexts ctx[0 .. k-1].  The
+ * contexts are shared out, in contiguous runs, over up to as many host
+ * threads as the host has hardware threads (the caller's among them, each
+ * on the caller's current device); each thread adapts its run in
+ * lockstep: every phase of the adaptation (background construction when
+ * due, split, each merge round, the shift rounds with the h update) is
+ * issued for every context of the run still adapting, each on its own
+ * context's stream, before one host synchronisation of all of them
+ * gathers the counts the next phase needs (the split count, a merge
+ * round's survivors, the masses).  So the contexts' kernels overlap on the
+ * device, and a run of adaptations waits on about as many
+ * synchronisations as one.  Each
+ * context receives the kernels, in the order and with the arguments, of
+ * sph_adapt on it alone: its state and stats equal sph_adapt's bit for
+ * bit.  Nothing runs on the batch's stream; the next sph_batch_step orders
+ * itself after the contexts' streams as always.  A context whose
+ * adaptation fails stops where sph_adapt would stop (its message in its
+ * sph_last_error) while the others go on.  stats: NULL or k entries
+ * (zeroed for a failed context); status: NULL or k entries, each
+ * context's own result.  Returns SPH_OK when every adaptation succeeded,
+ * else the first failed context's status.  Errors before any work:
+ * SPH_EINVAL (NULL batch, ctx or context, k outside 1 .. max_instances, a
+ * context listed twice). */
+sph_status sph_batch_adapt(sph_batch *batch, sph_ctx *const *ctx, int k,
+                           sph_adapt_stats *stats, sph_status *status);
+
 /* Background construction (section 3.3): `iterations` iterations over the
  * loaded background (iterations <= 0: 3 ceil(log(ds_max / ds_min) /
  * log Cr), the paper's count for the initial construction), each:
@@ -345,7 +371,9 @@ sph_status sph_adapt(sph_ctx *ctx, sph_adapt_stats *out);
  *  4. bg_smooth_iters times: Eq. h-smoothing with N_r = bg_Nr over N(i)
  *     (i included), then one limited shifting step (Eqs. shift-deltar,
  *     shift-limit, volumes m_j / rho0) of the background alone.
- * FP64 throughout, both precisions.  The refined set replaces the loaded
+ * Marking, sizes, splits and the h-smoothing in FP64; the shifting step's
+ * pair sums in the context's precision (FP32 pair arithmetic over FP64
+ * state for SPH_MIXED, as in sph_adapt).  The refined set replaces the loaded
  * background (read it with SPH_F_BG_*).  Synchronises (split counts).
  * out (may be NULL) receives counts.  Errors: SPH_ESTATE (no background),
  * SPH_EINVAL (ds_min, ds_max, Cr, bg_Nr not usable: need 0 < ds_min <=

@@ -6,16 +6,23 @@
 namespace sph {
 namespace api {
 
-// One split pass (section 3.1): flag m > m_max, scan, rank the parents by
-// id, emit the children.  One synchronisation (the parent count).
-static sph_status split_pass(sph_ctx *c, uint32_t *count_out) {
-    sph_status st = SPH_OK;
-    *count_out = 0;
+// Pinned host words of a context (its h_pin): the counts the adaptation
+// phases read back without blocking in the copy.
+enum { HP_SPLIT = 0, HP_KEEP = 1, HP_STALE = 2, HP_NFB = 3, HP_MASS = 4 };   // HP_MASS: 2 doubles
+
+// Split pass (section 3.1), first half: flag m > m_max, scan; the parent
+// count is queued into h_pin[HP_SPLIT].
+static void split_issue(sph_ctx *c) {
     launch_split_flag(c->s, c->n, c->f[F_M], c->f[F_MMAX], c->tmp_a);
     exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
     c->launches += 1;
-    uint32_t count = read_u32(c, c->d_total, &st);
-    if (st != SPH_OK) return st;
+    cudaMemcpyAsync(c->h_pin + HP_SPLIT, c->d_total, sizeof(uint32_t),
+                    cudaMemcpyDeviceToHost, c->s);
+}
+
+// Second half, once the count has arrived: rank the parents by id, emit
+// the children.
+static sph_status split_apply(sph_ctx *c, uint32_t count) {
     if ((long long)c->n + 6ll * count > c->cap)
         return fail(c, SPH_ECAPACITY, c->has_ds
                         ? "sph_background: split children exceed bg_capacity"
@@ -40,8 +47,18 @@ static sph_status split_pass(sph_ctx *c, uint32_t *count_out) {
         c->next_id += 6ll * count;
         c->grid_valid = false;
     }
-    *count_out = count;
     return SPH_OK;
+}
+
+// The whole split pass with its synchronisation (the parent count).
+static sph_status split_pass(sph_ctx *c, uint32_t *count_out) {
+    *count_out = 0;
+    split_issue(c);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sync");
+    const uint32_t count = c->h_pin[HP_SPLIT];
+    sph_status st = split_apply(c, count);
+    if (st == SPH_OK) *count_out = count;
+    return st;
 }
 
 // Arguments of the shift and h-update kernels over the current lists.
@@ -74,8 +91,8 @@ static ShiftArgs shift_args(sph_ctx *c) {
 
 // ------------------------------------------------ background construction --
 // The background under construction (section 3.3) lives in a context of
-// its own (FP64, ds in F_DS), so the fluid's rebuild, split and shift
-// machinery serves it unchanged.  It is loaded from the context's
+// its own (the owner's precision, ds in F_DS), so the fluid's rebuild,
+// split and shift machinery serves it unchanged.  It is loaded from the context's
 // background set and written back into it after the iterations.
 static sph_status ensure_bgc(sph_ctx *c) {
     const long long n = c->bg.n;
@@ -90,7 +107,6 @@ static sph_status ensure_bgc(sph_ctx *c) {
     }
     if (!c->bgc) {
         sph_params p = c->prm;
-        p.precision = SPH_FP64;
         p.capacity = cap;
         p.cell_c0 = 0.0;
         p.n_bg = 0;
@@ -218,35 +234,63 @@ static sph_status bg_iteration(sph_ctx *c, sph_ctx *b, bool vort,
         std::swap(b->f[F_H], b->falt[F_H]);
         b->grid_valid = false;
         if ((st = rebuild(b, false)) != SPH_OK) return fail(c, st, b->err);
-        launch_shift_round(b->s, shift_args(b), false);
+        launch_shift_round(b->s, shift_args(b), is_mixed(b));
         b->grid_valid = false;
         c->launches += 4;
     }
     return SPH_OK;
 }
 
-}  // namespace api
-}  // namespace sph
+// ------------------------------------------------------------ adaptation --
+static void adapt_stop(AdaptJob &j, sph_status st) {
+    t_end(j.c, 4, j.ev);
+    j.st = st;
+    j.phase = AdaptJob::DONE;
+}
 
-extern "C" {
+// Merged-away particles out of the state (the scan of the last merge
+// round gave each kept one its row).
+static void compact_dead(AdaptJob &j) {
+    sph_ctx *c = j.c;
+    CompactArgs ca;
+    for (int k = 0; k < NSTATE; ++k) {
+        ca.src[k] = c->f[k];
+        ca.dst[k] = c->falt[k];
+    }
+    ca.isrc = c->id;
+    ca.idst = c->id_alt;
+    launch_compact(c->s, c->n, c->tmp_a, c->tmp_b, ca);
+    c->launches += 1;
+    for (int k = 0; k < NSTATE; ++k) std::swap(c->f[k], c->falt[k]);
+    std::swap(c->id, c->id_alt);
+    c->n = j.n_alive;
+    c->grid_valid = false;
+    j.dead = false;
+}
 
-sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
-    if (!c) return SPH_EINVAL;
+// Phase 1: the background construction when due, the mass before, the
+// resolution from the background (section 3.3), the split flags and
+// their count.
+static void adapt_begin(AdaptJob &j) {
+    sph_ctx *c = j.c;
     c->cfg_version += 1;
     c->err.clear();
-    if (c->n <= 0) return fail(c, SPH_ESTATE, "sph_adapt: no fluid particles loaded");
-    if (c->prm.n_bg > 0 && c->bg.n > 0 && ++c->adapt_calls % c->prm.n_bg == 0) {
-        sph_status bs = sph_background(c, 1, nullptr);
-        if (bs != SPH_OK) return bs;
+    memset(&j.z, 0, sizeof(j.z));
+    j.phase = AdaptJob::DONE;
+    if (c->n <= 0) {
+        j.st = fail(c, SPH_ESTATE, "sph_adapt: no fluid particles loaded");
+        return;
     }
-    sph_adapt_stats z;
-    memset(&z, 0, sizeof(z));
-    z.n_before = c->n;
-    sph_status st = SPH_OK;
-    cudaEvent_t ev;
-    t_begin(c, 4, &ev);
+    if (c->prm.n_bg > 0 && c->bg.n > 0 && ++c->adapt_calls % c->prm.n_bg == 0) {
+        const sph_status bs = sph_background(c, 1, nullptr);
+        if (bs != SPH_OK) {
+            j.st = bs;
+            return;
+        }
+    }
+    j.z.n_before = c->n;
+    t_begin(c, 4, &j.ev);
     c->launches += launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass);
-    // resolution from the background (section 3.3)
     ensure_set_pk(c, &c->wall);
     if (c->bg.n > 0) {
         ensure_set_pk(c, &c->bg);
@@ -281,102 +325,83 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
     } else {
         cudaMemsetAsync(c->d_aux, 0, sizeof(uint32_t), c->s);
     }
-    // split pass (section 3.1)
-    uint32_t count = 0;
-    if ((st = split_pass(c, &count)) != SPH_OK) {
-        t_end(c, 4, ev);
-        return st;
-    }
-    z.n_split = count;
-    // merge rounds (section 3.2).  One list build serves several rounds:
-    // merged-away particles stay in place, marked dead, and the kept ones
-    // are updated in place, so the lists of the build still cover every
-    // later partner while each merged particle's h / 2 plus its move since
-    // the build stays within 1.5 h at the build (partners lie within
-    // (h_i + h_j) / 2, the lists reach 3 max(h_i, h_j) at the build); a
-    // merge beyond that flags the lists stale and the next round rebuilds
-    // after compacting.  A round that merges nothing ends the rounds: it
-    // left the state as it found it.
-    {
-        bool lists_ok = false, first = false, dead = false;
-        int n_alive = c->n;
-        auto compact_dead = [&]() {
-            CompactArgs ca;
-            for (int k = 0; k < NSTATE; ++k) {
-                ca.src[k] = c->f[k];
-                ca.dst[k] = c->falt[k];
-            }
-            ca.isrc = c->id;
-            ca.idst = c->id_alt;
-            launch_compact(c->s, c->n, c->tmp_a, c->tmp_b, ca);
-            c->launches += 1;
-            for (int k = 0; k < NSTATE; ++k) std::swap(c->f[k], c->falt[k]);
-            std::swap(c->id, c->id_alt);
-            c->n = n_alive;
-            c->grid_valid = false;
-            dead = false;
-        };
-        int *stale = (int *)(c->d_aux + 1);
-        for (int r = 0; r < c->prm.merge_iters; ++r) {
-            if (!lists_ok) {
-                if (dead) compact_dead();
-                if ((st = rebuild(c, false, true, 1.0f, false)) != SPH_OK) return st;
-                cudaMemsetAsync(stale, 0, sizeof(int), c->s);
-                lists_ok = true;
-                first = true;
-            }
-            MergeArgs a;
-            a.n = c->n;
-            a.d = c->dom;
-            for (int k = 0; k < NSTATE; ++k) a.f[k] = c->f[k];
-            a.id = c->id;
-            a.off = c->off;
-            a.list = c->list;
-            a.closest = c->closest;
-            a.alive = c->tmp_a;
-            a.an = c->an;
-            a.pk = c->pk;
-            a.alive_in = first ? nullptr : c->tmp_a;
-            a.h0 = c->mh0;
-            a.dsum = c->mds;
-            a.budget = 1.5f * c->skin * (1.0f - 1e-3f);
-            a.stale = stale;
-            a.pkw = c->pk;
-            a.mq = c->mq;
-            for (int ax = 0; ax < 2; ++ax) {
-                a.lo[ax] = c->dom.lo[ax];
-                a.Ad[ax] = c->anchor_A[ax];
-                a.invAd[ax] = 1.0 / c->anchor_A[ax];
-            }
-            first = false;
-            launch_merge(c->s, a);
-            exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
-            c->launches += a.alive_in ? 2 : 3;
-            uint32_t keep = 0;
-            int is_stale = 0;
-            cudaMemcpyAsync(&keep, c->d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
-            cudaMemcpyAsync(&is_stale, stale, sizeof(int), cudaMemcpyDeviceToHost, c->s);
-            if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_adapt merge");
-            if ((int)keep == n_alive) break;
-            z.n_merged += n_alive - (int)keep;
-            n_alive = (int)keep;
-            dead = true;
-            c->grid_valid = false;
-            if (is_stale) lists_ok = false;
+    split_issue(c);
+    j.phase = AdaptJob::SPLIT;
+}
+
+// One merge round (section 3.2), issued: its survivors and the stale flag
+// are queued into the pinned words.  One list build serves several
+// rounds: merged-away particles stay in place, marked dead, and the kept
+// ones are updated in place, so the lists of the build still cover every
+// later partner while each merged particle's h / 2 plus its move since
+// the build stays within 1.5 h at the build (partners lie within
+// (h_i + h_j) / 2, the lists reach 3 max(h_i, h_j) at the build); a merge
+// beyond that flags the lists stale and the next round rebuilds after
+// compacting.
+static void merge_issue(AdaptJob &j) {
+    sph_ctx *c = j.c;
+    int *stale = (int *)(c->d_aux + 1);
+    if (!j.lists_ok) {
+        if (j.dead) compact_dead(j);
+        const sph_status st = rebuild(c, false, true, 1.0f, false);
+        if (st != SPH_OK) {
+            adapt_stop(j, st);
+            return;
         }
-        if (dead) compact_dead();
+        cudaMemsetAsync(stale, 0, sizeof(int), c->s);
+        j.lists_ok = true;
+        j.first = true;
     }
-    // shift rounds with Taylor correction, then the h update (3.2, 3.4)
-    // One list build serves every shift round and the h update: a round
-    // moves a particle by at most 0.25 h (Eq. shift-limit), so after k
-    // rounds a pair is at most k (h_i + h_j) / 4 <= k max(h) / 2 closer,
-    // and lists with skin 1 + k / 6 still hold N(i).  The shift sums vanish
-    // outside N(i) (kernel support); the h update counts members only.
-    // (mixed path only: on the FP64 path the wider lists cost more FP64
-    // pair work than the rebuilds they save)
+    MergeArgs a;
+    a.n = c->n;
+    a.d = c->dom;
+    for (int k = 0; k < NSTATE; ++k) a.f[k] = c->f[k];
+    a.id = c->id;
+    a.off = c->off;
+    a.list = c->list;
+    a.closest = c->closest;
+    a.alive = c->tmp_a;
+    a.an = c->an;
+    a.pk = c->pk;
+    a.alive_in = j.first ? nullptr : c->tmp_a;
+    a.h0 = c->mh0;
+    a.dsum = c->mds;
+    a.budget = 1.5f * c->skin * (1.0f - 1e-3f);
+    a.stale = stale;
+    a.pkw = c->pk;
+    a.mq = c->mq;
+    for (int ax = 0; ax < 2; ++ax) {
+        a.lo[ax] = c->dom.lo[ax];
+        a.Ad[ax] = c->anchor_A[ax];
+        a.invAd[ax] = 1.0 / c->anchor_A[ax];
+    }
+    j.first = false;
+    launch_merge(c->s, a);
+    exclusive_scan(c->s, c->tmp_a, c->tmp_b, c->n, c->d_total, c->sc, &c->launches);
+    c->launches += a.alive_in ? 2 : 3;
+    cudaMemcpyAsync(c->h_pin + HP_KEEP, c->d_total, sizeof(uint32_t),
+                    cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(c->h_pin + HP_STALE, stale, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    j.phase = AdaptJob::MERGE;
+}
+
+// Shift rounds with Taylor correction, then the h update (3.2, 3.4), the
+// mass after; the masses and the count of nearest-background fallbacks
+// are queued into the pinned words.  One list build serves every shift
+// round and the h update: a round moves a particle by at most 0.25 h
+// (Eq. shift-limit), so after k rounds a pair is at most
+// k (h_i + h_j) / 4 <= k max(h) / 2 closer, and lists with skin 1 + k / 6
+// still hold N(i).  The shift sums vanish outside N(i) (kernel support);
+// the h update counts members only.  (mixed path only: on the FP64 path
+// the wider lists cost more FP64 pair work than the rebuilds they save)
+static void finish_issue(AdaptJob &j) {
+    sph_ctx *c = j.c;
+    if (j.dead) compact_dead(j);
+    sph_status st;
     const int ns = c->prm.shift_iters;
     if (ns <= 4 && is_mixed(c)) {
-        if ((st = rebuild(c, false, true, 1.0f + ns / 6.0f + 0.01f)) != SPH_OK) return st;
+        if ((st = rebuild(c, false, true, 1.0f + ns / 6.0f + 0.01f)) != SPH_OK)
+            return adapt_stop(j, st);
         for (int r = 0; r < ns; ++r) {
             if (r > 0) pack(c, false);
             launch_shift_round(c->s, shift_args(c), is_mixed(c));
@@ -388,30 +413,108 @@ sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
         launch_h_update(c->s, ha, is_mixed(c));
     } else {
         for (int r = 0; r < ns; ++r) {
-            if ((st = rebuild(c, false)) != SPH_OK) return st;
+            if ((st = rebuild(c, false)) != SPH_OK) return adapt_stop(j, st);
             launch_shift_round(c->s, shift_args(c), is_mixed(c));
             c->launches += 3;
         }
-        if ((st = rebuild(c, false)) != SPH_OK) return st;
+        if ((st = rebuild(c, false)) != SPH_OK) return adapt_stop(j, st);
         launch_h_update(c->s, shift_args(c), is_mixed(c));
     }
     c->launches += 2;
     c->launches += launch_mass_sum(c->s, c->n, c->f[F_M], c->d_mass_part, c->d_mass + 1);
-    t_end(c, 4, ev);
+    t_end(c, 4, j.ev);
     c->grid_valid = false;   // h changed since the last rebuild
     c->rhs_valid = false;
-    double mass[2] = {0, 0};
-    uint32_t nfb = 0;
-    cudaMemcpyAsync(mass, c->d_mass, sizeof(mass), cudaMemcpyDeviceToHost, c->s);
-    cudaMemcpyAsync(&nfb, c->d_aux, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->s);
-    if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_adapt");
-    if ((st = check_overflow(c, "sph_adapt")) != SPH_OK) return st;
-    z.mass_before = mass[0];
-    z.mass_after = mass[1];
-    z.n_bg_nearest = nfb;
-    z.n_after = c->n;
-    if (out) *out = z;
-    return cuda_check(c, "sph_adapt");
+    cudaMemcpyAsync(c->h_pin + HP_MASS, c->d_mass, 2 * sizeof(double),
+                    cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(c->h_pin + HP_NFB, c->d_aux, sizeof(uint32_t),
+                    cudaMemcpyDeviceToHost, c->s);
+    j.phase = AdaptJob::FINISH;
+}
+
+// The next phase of j once its stream has been synchronised.
+static void adapt_advance(AdaptJob &j) {
+    sph_ctx *c = j.c;
+    switch (j.phase) {
+    case AdaptJob::SPLIT: {
+        const uint32_t count = c->h_pin[HP_SPLIT];
+        const sph_status st = split_apply(c, count);
+        if (st != SPH_OK) return adapt_stop(j, st);
+        j.z.n_split = count;
+        j.lists_ok = j.first = j.dead = false;
+        j.n_alive = c->n;
+        j.round = 0;
+        if (c->prm.merge_iters > 0)
+            merge_issue(j);
+        else
+            finish_issue(j);
+        return;
+    }
+    case AdaptJob::MERGE: {
+        // a round that merges nothing ends the rounds: it left the state
+        // as it found it
+        const int keep = (int)c->h_pin[HP_KEEP];
+        const int is_stale = (int)c->h_pin[HP_STALE];
+        if (keep != j.n_alive) {
+            j.z.n_merged += j.n_alive - keep;
+            j.n_alive = keep;
+            j.dead = true;
+            c->grid_valid = false;
+            if (is_stale) j.lists_ok = false;
+            if (++j.round < c->prm.merge_iters) return merge_issue(j);
+        }
+        return finish_issue(j);
+    }
+    case AdaptJob::FINISH: {
+        j.phase = AdaptJob::DONE;
+        if ((j.st = check_overflow(c, "sph_adapt")) != SPH_OK) return;
+        double mass[2];
+        memcpy(mass, c->h_pin + HP_MASS, sizeof(mass));
+        j.z.mass_before = mass[0];
+        j.z.mass_after = mass[1];
+        j.z.n_bg_nearest = c->h_pin[HP_NFB];
+        j.z.n_after = c->n;
+        j.st = cuda_check(c, "sph_adapt");
+        return;
+    }
+    default:
+        return;
+    }
+}
+
+void adapt_run(AdaptJob *jobs, int k) {
+    for (int i = 0; i < k; ++i) adapt_begin(jobs[i]);
+    for (;;) {
+        bool any = false;
+        for (int i = 0; i < k; ++i) {
+            AdaptJob &j = jobs[i];
+            if (j.phase == AdaptJob::DONE) continue;
+            if (cudaStreamSynchronize(j.c->s) != cudaSuccess) {
+                if (j.phase != AdaptJob::FINISH) t_end(j.c, 4, j.ev);
+                j.st = cuda_check(j.c, "sph_adapt");
+                j.phase = AdaptJob::DONE;
+                continue;
+            }
+            any = true;
+        }
+        if (!any) return;
+        for (int i = 0; i < k; ++i)
+            if (jobs[i].phase != AdaptJob::DONE) adapt_advance(jobs[i]);
+    }
+}
+
+}  // namespace api
+}  // namespace sph
+
+extern "C" {
+
+sph_status sph_adapt(sph_ctx *c, sph_adapt_stats *out) {
+    if (!c) return SPH_EINVAL;
+    AdaptJob j;
+    j.c = c;
+    adapt_run(&j, 1);
+    if (j.st == SPH_OK && out) *out = j.z;
+    return j.st;
 }
 
 sph_status sph_background(sph_ctx *c, int iterations, sph_bg_stats *out) {

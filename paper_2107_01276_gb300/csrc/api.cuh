@@ -146,6 +146,7 @@ struct sph_ctx {
     int force_cap = 0;           // walls d_force holds
     double *d_mass = nullptr, *d_mass_part = nullptr;  // [2], [256]
     uint32_t *d_aux = nullptr;                         // [4] adapt counters
+    uint32_t *h_pin = nullptr;   // 16 pinned host words: adaptation read-backs
     StaticSet bg;     // background particles (section 3.3); extra: ds, m
     // background construction: the background as a particle context of its
     // own (ds carried in F_DS), created on the first sph_background call
@@ -237,6 +238,25 @@ bool graph_step(sph_ctx *c, sph_status *st);
 void drop_graph(sph_ctx::StepGraph &g);
 
 sph_status compute_vorticity(sph_ctx *c);
+
+// One context's adaptation (sections 3.1-3.4) as phases.  Each phase
+// issues its kernels on the context's stream and queues the counts the
+// next one needs into the context's pinned words; between phases the
+// caller synchronises the stream.  adapt_run drives several contexts in
+// lockstep, one synchronisation of all their streams per phase; every
+// context gets the kernels, arguments and order of an adaptation of it
+// alone.
+struct AdaptJob {
+    sph_ctx *c = nullptr;
+    sph_adapt_stats z;
+    cudaEvent_t ev = nullptr;
+    sph_status st = SPH_OK;
+    enum { SPLIT, MERGE, FINISH, DONE } phase = DONE;
+    bool lists_ok = false, first = false, dead = false;
+    int n_alive = 0, round = 0;
+};
+void adapt_run(AdaptJob *jobs, int k);
+
 uint32_t read_u32(sph_ctx *c, const uint32_t *dev, sph_status *st);
 sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
                    sph_ctx **out, std::string *why);

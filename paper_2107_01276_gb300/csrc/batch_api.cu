@@ -1,5 +1,7 @@
 // The batched step over several contexts (C ABI sph_batch_*), see
 // include/sph.h.
+#include <thread>
+
 #include "api.cuh"
 
 // ============================================================ batches ==
@@ -114,6 +116,31 @@ static bool stage_phase(Stager &st, const std::vector<sph_ctx *> &cs, Team team,
         if (g.off_args == (size_t)-1 || g.off_first == (size_t)-1) return false;
     }
     return true;
+}
+
+// body(a, e) over contiguous runs [a, e) of [0, k): one run per host
+// thread, up to the host's hardware threads (the caller's among them),
+// each thread on the caller's current device.
+template <class F>
+static void host_runs(int k, F body) {
+    const int nt = std::min(k, std::max(1, (int)std::thread::hardware_concurrency()));
+    if (nt <= 1) {
+        body(0, k);
+        return;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) {
+        const int a = (int)((long long)k * t / nt);
+        const int e = (int)((long long)k * (t + 1) / nt);
+        th.emplace_back([&body, dev, a, e] {
+            cudaSetDevice(dev);
+            body(a, e);
+        });
+    }
+    body(0, (int)((long long)k / nt));
+    for (auto &x : th) x.join();
 }
 
 static BatchSpan span_of(const Stager &st, const PhaseGroup &g) {
@@ -524,15 +551,26 @@ static sph_status batch_body(sph_batch *b, const std::vector<sph_ctx *> &all,
         join_from(b, small);
     }
     fork_to(b, rest);
-    for (sph_ctx *c : rest) {
-        compute_dt(c, c->d_t, 1);
-        sph_status s2 = rebuild(c, false, true, is_mixed(c) ? 1.1f : 1.0f);
-        if (s2 != SPH_OK) {
-            *bad = c;
-            join_from(b, rest);
-            return s2;
+    // their builds issued from host threads (outside a capture, which
+    // takes the launches of the capturing thread only)
+    std::vector<sph_status> bst(rest.size(), SPH_OK);
+    auto build_run = [&](int a, int e) {
+        for (int q = a; q < e; ++q) {
+            sph_ctx *c = rest[q];
+            compute_dt(c, c->d_t, 1);
+            if ((bst[q] = rebuild(c, false, true, is_mixed(c) ? 1.1f : 1.0f)) != SPH_OK) return;
         }
-    }
+    };
+    if (capturing)
+        build_run(0, (int)rest.size());
+    else
+        host_runs((int)rest.size(), build_run);
+    for (size_t q = 0; q < rest.size(); ++q)
+        if (bst[q] != SPH_OK) {
+            *bad = rest[q];
+            join_from(b, rest);
+            return bst[q];
+        }
     if (!launch_small_builds(b, st, sb, true)) {
         join_from(b, rest);
         return fail(all[0], SPH_ECUDA, "sph_batch_step: batched build could not be staged");
@@ -930,6 +968,34 @@ sph_status sph_batch_step(sph_batch *b, sph_ctx *const *ctx, int k, double *t_ou
         }
     }
     return SPH_OK;
+}
+
+sph_status sph_batch_adapt(sph_batch *b, sph_ctx *const *ctx, int k,
+                           sph_adapt_stats *stats, sph_status *status) {
+    if (!b || !ctx || k < 1 || k > b->cap) return SPH_EINVAL;
+    for (int q = 0; q < k; ++q) {
+        if (!ctx[q]) return SPH_EINVAL;
+        for (int r = 0; r < q; ++r)
+            if (ctx[r] == ctx[q])
+                return fail(ctx[q], SPH_EINVAL, "sph_batch_adapt: a context appears twice");
+    }
+    std::vector<AdaptJob> jobs(k);
+    for (int q = 0; q < k; ++q) jobs[q].c = ctx[q];
+    // the host work (launches, read-backs) of the adaptations spread over
+    // host threads, each adapting its run of contexts in lockstep
+    host_runs(k, [&jobs](int a, int e) { adapt_run(jobs.data() + a, e - a); });
+    sph_status first = SPH_OK;
+    for (int q = 0; q < k; ++q) {
+        if (status) status[q] = jobs[q].st;
+        if (stats) {
+            if (jobs[q].st == SPH_OK)
+                stats[q] = jobs[q].z;
+            else
+                memset(&stats[q], 0, sizeof(stats[q]));
+        }
+        if (first == SPH_OK) first = jobs[q].st;
+    }
+    return first;
 }
 
 long long sph_batch_graph_steps(const sph_batch *b) { return b ? b->graph_steps : -1; }

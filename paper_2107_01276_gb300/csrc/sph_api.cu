@@ -482,6 +482,8 @@ void free_ctx(sph_ctx *c) {
     cudaFree(c->d_wnlong);
     cudaFree(c->d_wmax);
     cudaFree(c->d_minmax);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    c->h_pin = nullptr;
     if (c->bgc) {
         free_ctx(c->bgc);
         delete c->bgc;
@@ -847,7 +849,8 @@ sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
          dalloc(&c->wcnt, N + 1) && dalloc(&c->woff, N + 1) && dalloc(&c->wcur, N) &&
          dalloc(&c->wlongq, N) && dalloc(&c->d_wnlong, 1) &&
          dalloc(&c->d_mass, 2) &&
-         dalloc(&c->d_mass_part, 256) && dalloc(&c->d_aux, 4);
+         dalloc(&c->d_mass_part, 256) && dalloc(&c->d_aux, 4) &&
+         cudaMallocHost((void **)&c->h_pin, 16 * sizeof(uint32_t)) == cudaSuccess;
     c->list_cap = std::min<size_t>(N * 48, 0xffffffffull);
     ok = ok && dalloc(&c->list, c->list_cap);
     if (!ok) {

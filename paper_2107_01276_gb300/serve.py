@@ -9,11 +9,13 @@ device.  As requests finish, their slots and memory go to waiting ones
 (continuous batching).  The report gives per-step latency percentiles
 beside the aggregate throughput.
 
-With batch=True the requests without adaptation step together instead:
-one BatchStepper thread advances all of them in flight by one
-sph_batch_step per tick (every per-particle phase of all of them in one
-persistent launch), members joining as they are admitted and leaving as
-they finish.
+With batch=True the requests step together instead, once set up on their
+workers: one BatchStepper thread advances all of them in flight per tick,
+first one sph_batch_adapt over those due for adaptation (their
+adaptations in lockstep, one synchronisation per phase for all of them),
+then one sph_batch_step over all (every per-particle phase of all of them
+in one persistent launch), members joining as they are admitted and
+leaving as they finish.
 
 Every step of every simulation runs in the library's kernels (sph.py is the
 binding); this module only schedules.  The ctypes calls release the GIL, so
@@ -58,6 +60,8 @@ class Request:
     admitted: float = float("nan")
     finished: float = float("nan")
     step_ms: list = field(default_factory=list)
+    setup_s: float = 0.0          # admission to the first step
+    background_s: float = 0.0     # of which: background construction
     particle_steps: int = 0
     final: dict | None = None
     error: str | None = None
@@ -99,7 +103,9 @@ def _setup(req: Request, stream: int):
         if d.get("background") is not None:
             sim.load(d["background"], kind=sph.SPH_BACKGROUND)
             if d.get("construct_background"):
+                t0 = time.perf_counter()
                 sim.background()
+                req.background_s = time.perf_counter() - t0
         for _ in range(req.refine):
             sim.adapt()
     except Exception:
@@ -119,7 +125,9 @@ def _finish(req: Request, sim, keep_final: bool):
 
 def run_alone(req: Request, stream: int, keep_final: bool = True) -> Request:
     """Run one request to completion on `stream` (the worker body)."""
+    t0 = time.perf_counter()
     sim = _setup(req, stream)
+    req.setup_s = time.perf_counter() - t0
     try:
         for s in range(req.steps):
             t0 = time.perf_counter()
@@ -135,20 +143,23 @@ def run_alone(req: Request, stream: int, keep_final: bool = True) -> Request:
 
 
 class BatchStepper:
-    """Continuous batching of the steps themselves: simulations without
-    adaptation join one sph_batch_step per tick (every per-particle phase
-    of all of them in one persistent launch) as they are admitted, and
-    leave when their steps are done.  A step's latency is the tick's."""
+    """Continuous batching of the steps themselves: simulations join the
+    ticks as they are admitted and leave when their steps are done.  A
+    tick adapts the members due for adaptation (step s of a request with
+    adapt_every > 0 and s % adapt_every == 0, as run_alone does) in one
+    sph_batch_adapt, then steps every member in one sph_batch_step.  A
+    step's latency is the tick's; a member whose adaptation fails leaves
+    with its error while the others go on."""
 
     def __init__(self, max_instances: int, stream: int, batch=None):
-        # batch: an object with step(sims, want_time), set_graphs(bool) and
-        # close() (default: a library sph.Batch)
+        # batch: an object with adapt(sims, errors), step(sims, want_time),
+        # set_graphs(bool) and close() (default: a library sph.Batch)
         self.batch = batch if batch is not None else sph.Batch(max_instances, stream)
         # members come and go, and the other workers allocate and
         # synchronise while a graph would be captured: launch by launch
         self.batch.set_graphs(False)
         self.cv = threading.Condition()
-        self.members = []            # [sim, request, steps left, event, n]
+        self.members = []            # [sim, request, steps left, event, n, steps done]
         self.stop = False
         self.th = threading.Thread(target=self._loop, daemon=True)
         self.th.start()
@@ -159,7 +170,7 @@ class BatchStepper:
             return
         ev = threading.Event()
         with self.cv:
-            self.members.append([sim, req, req.steps, ev, sim.info()["n"]])
+            self.members.append([sim, req, req.steps, ev, sim.info()["n"], 0])
             self.cv.notify_all()
         ev.wait()
         if req.error:
@@ -173,22 +184,36 @@ class BatchStepper:
                 if not self.members:
                     return
                 group = list(self.members)
+            due = [m for m in group
+                   if m[1].adapt_every and m[5] % m[1].adapt_every == 0]
             t0 = time.perf_counter()
             err = None
+            bad = {}
             try:
-                self.batch.step([m[0] for m in group], want_time=True)
+                if due:
+                    res = self.batch.adapt([m[0] for m in due], errors="return")
+                    for m, r in zip(due, res):
+                        if isinstance(r, tuple):
+                            bad[id(m)] = "SphError: %s" % r[1]
+                        else:
+                            m[4] = r["n_after"]
+                live = [m for m in group if id(m) not in bad]
+                if live:
+                    self.batch.step([m[0] for m in live], want_time=True)
             except Exception as e:            # every member fails
                 err = "%s: %s" % (type(e).__name__, e)
             ms = 1e3 * (time.perf_counter() - t0)
             with self.cv:
                 for m in group:
-                    if err:
-                        m[1].error = err
+                    e = err or bad.get(id(m))
+                    if e:
+                        m[1].error = e
                         m[2] = 0
                     else:
                         m[1].step_ms.append(ms)
                         m[1].particle_steps += m[4]
                         m[2] -= 1
+                        m[5] += 1
                     if m[2] <= 0:
                         self.members.remove(m)
                         m[3].set()
@@ -203,9 +228,11 @@ class BatchStepper:
 
 def run_batched(req: Request, stream: int, stepper: BatchStepper,
                 keep_final: bool = True) -> Request:
-    """A request without adaptation: set up on `stream`, stepped by the
-    batch stepper together with the others in flight."""
+    """A request set up on `stream`, then adapted and stepped by the batch
+    stepper together with the others in flight."""
+    t0 = time.perf_counter()
     sim = _setup(req, stream)
+    req.setup_s = time.perf_counter() - t0
     try:
         stepper.advance(sim, req)
         _finish(req, sim, keep_final)
@@ -221,9 +248,9 @@ class Server:
     handed out; mem_info: callable returning (free, total) bytes (default
     torch.cuda.mem_get_info); runner: callable(request, stream) running one
     request (default run_alone); make_stream: callable returning a stream
-    handle for a worker (default: a new torch CUDA stream); batch: requests
-    without adaptation step together through one BatchStepper (the others
-    run on their workers as before)."""
+    handle for a worker (default: a new torch CUDA stream); batch: the
+    requests, once set up on their workers, adapt and step together
+    through one BatchStepper."""
 
     def __init__(self, slots: int = 8, reserve: int = 2 << 30,
                  mem_info=None, runner=None, make_stream=None,
@@ -272,7 +299,7 @@ class Server:
             t0 = time.perf_counter()
             req.admitted = t0 - t_start
             try:
-                if stepper is not None and not req.adapt_every:
+                if stepper is not None:
                     run_batched(req, streams[slot][1], stepper, self.keep_final)
                 else:
                     self.runner(req, streams[slot][1])
@@ -344,6 +371,12 @@ class Server:
             "step_ms_p99": float(np.percentile(lat, 99)) if lat.size else None,
             "queue_s_mean": float(np.mean([r.admitted - r.arrival for r in
                                            requests])) if requests else None,
+            "setup_s_mean": float(np.mean([r.setup_s for r in requests]))
+            if requests else None,
+            "background_s_mean": float(np.mean([r.background_s for r in requests
+                                                if r.background_s > 0]))
+            if any(r.background_s > 0 for r in requests) else None,
+            "step_s_total": float(sum(sum(r.step_ms) for r in requests) / 1e3),
             "errors": sorted({r.error for r in requests if r.error}),
         }
 

@@ -176,6 +176,9 @@ def lib(build_if_missing: bool = True):
     L.sph_batch_step.restype = ctypes.c_int
     L.sph_batch_step.argtypes = [ctypes.c_void_p, P(ctypes.c_void_p), ctypes.c_int,
                                  _D, P(ctypes.c_int)]
+    L.sph_batch_adapt.restype = ctypes.c_int
+    L.sph_batch_adapt.argtypes = [ctypes.c_void_p, P(ctypes.c_void_p), ctypes.c_int,
+                                  P(AdaptStats), P(ctypes.c_int)]
     L.sph_batch_launches.restype = ctypes.c_longlong
     L.sph_batch_launches.argtypes = [ctypes.c_void_p]
     L.sph_batch_graph_steps.restype = ctypes.c_longlong
@@ -469,6 +472,29 @@ class Batch:
                    if 0 <= q < k else "sph_batch_step failed")
             raise SphError(st, msg)
         return t[:k] if want_time else None
+
+    def adapt(self, sims, errors: str = "raise"):
+        """One sph_adapt of every Simulation in ``sims``, in lockstep
+        (sph_batch_adapt): a list of stats dicts.  errors="raise" raises the
+        first failed context's error; errors="return" puts (status,
+        message) in a failed context's place instead."""
+        k = len(sims)
+        arr = (ctypes.c_void_p * max(k, 1))(*[s._ctx.value for s in sims])
+        z = (AdaptStats * max(k, 1))()
+        stat = (ctypes.c_int * max(k, 1))()
+        st = self._L.sph_batch_adapt(self._b, arr, k, z, stat)
+        if st == SPH_EINVAL and all(v == 0 for v in stat[:k]):
+            raise SphError(st, "sph_batch_adapt: invalid arguments")
+        out = []
+        for q in range(k):
+            if stat[q] != SPH_OK:
+                msg = self._L.sph_last_error(sims[q]._ctx).decode()
+                if errors == "raise":
+                    raise SphError(stat[q], msg)
+                out.append((stat[q], msg))
+            else:
+                out.append({f: getattr(z[q], f) for f, _ in AdaptStats._fields_})
+        return out
 
     @property
     def launches(self) -> int:

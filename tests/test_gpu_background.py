@@ -91,9 +91,9 @@ def oracle_stages():
     return stages
 
 
-def _one_iteration_both(state, fluid=None, vort_k=0.0):
+def _one_iteration_both(state, fluid=None, vort_k=0.0, precision=sph.SPH_FP64):
     pr = _params()
-    P = sph.make_params(pr, precision=sph.SPH_FP64, capacity=200000,
+    P = sph.make_params(pr, precision=precision, capacity=200000,
                         vort_k=vort_k, bg_capacity=200000)
     sim = sph.Simulation(P, stream_handle())
     if fluid is not None:
@@ -160,13 +160,35 @@ def test_vorticity_marking_parity(oracle_stages):
     assert np.abs(got["ds"] / ref["ds"] - 1).max() < 1e-12
 
 
-def test_full_construction_invariants():
+@pytest.mark.parametrize("stage", [0, 2, 30])
+def test_one_iteration_parity_mixed(oracle_stages, stage):
+    """A mixed context's construction sums the shifting step's pairs in
+    FP32 (state in FP64); marking, sizes, splits and the h-smoothing stay
+    FP64.  One iteration from the oracle's states: counts, ids, masses and
+    sizes as in FP64 (they are decided before the first shift); h and
+    positions within the FP32 pair sums' rounding."""
+    g, o, got, ref = _one_iteration_both(oracle_stages[stage],
+                                         precision=sph.SPH_MIXED)
+    for k in ("n_before", "n_marked", "n_vort", "n_split", "n_after"):
+        assert g[k] == o[k], (k, g, o)
+    assert np.array_equal(got["id"], ref["id"])
+    assert np.array_equal(got["m"], ref["m"])
+    assert np.abs(got["ds"] / ref["ds"] - 1).max() < 1e-12
+    assert np.abs(got["h"] / ref["h"] - 1).max() < 1e-5
+    for k in ("x", "y"):
+        d = got[k] - ref[k]
+        d -= LB * np.round(d / LB)
+        assert np.abs(d).max() < 2e-5 * HDX * DS_MAX, k
+
+
+@pytest.mark.parametrize("precision", [sph.SPH_FP64, sph.SPH_MIXED])
+def test_full_construction_invariants(precision):
     """The whole construction (3 ceil(log 8 / log 1.2) = 36 iterations) on
     the GPU: sizes in [ds_min, ds_max], ds_min next to the solid, sizes of
     neighbours within Cr^3, about N_r neighbours, mass conserved, size
     growing outward; and the same particle count and per-ring sizes as the
-    oracle's construction."""
-    P = sph.make_params(_params(), precision=sph.SPH_FP64, capacity=1000,
+    oracle's construction, for both precisions."""
+    P = sph.make_params(_params(), precision=precision, capacity=1000,
                         bg_capacity=200000)
     sim = sph.Simulation(P, stream_handle())
     sim.load(_solid(), kind=sph.SPH_WALL)

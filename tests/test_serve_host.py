@@ -96,12 +96,25 @@ class FakeBatch:
     """Records the members of every tick; fail_at: fails the ticks with
     that many members."""
 
-    def __init__(self, fail_at=None):
+    def __init__(self, fail_at=None, adapt_fails=()):
         self.ticks = []
+        self.adapts = []
         self.fail_at = fail_at
+        self.adapt_fails = set(adapt_fails)
 
     def set_graphs(self, enable):
         self.graphs = enable
+
+    def adapt(self, sims, errors="raise"):
+        self.adapts.append([s.name for s in sims])
+        out = []
+        for s in sims:
+            if s.name in self.adapt_fails:
+                out.append((4, "split children exceed the capacity"))
+            else:
+                s.n += 1          # one more particle per adaptation
+                out.append({"n_after": s.n})
+        return out
 
     def step(self, sims, want_time=False):
         self.ticks.append([s.name for s in sims])
@@ -172,3 +185,40 @@ def test_batch_stepper_failure_reaches_every_member():
     st.close()
     assert len(errs) == 2 and all("device error" in e for e in errs)
     assert all(r.error for r in reqs)
+
+
+def test_batch_stepper_adapts_members_due_and_drops_failed_ones():
+    """A member with adapt_every = k is adapted before its steps 0, k, 2k,
+    ... (as run_alone does), in the tick's one adapt call; its particle
+    count follows the adaptation.  A member whose adaptation fails leaves
+    with its error; the others step on."""
+    fb = FakeBatch(adapt_fails=("bad",))
+    st = serve.BatchStepper(4, 0, batch=fb)
+    reqs = [serve.Request(0, None, 6, adapt_every=2),
+            serve.Request(1, None, 4, adapt_every=0),
+            serve.Request(2, None, 5, adapt_every=1)]
+    sims = [FakeSim("a", 100), FakeSim("b", 200), FakeSim("bad", 300)]
+    errs = []
+
+    def run(k):
+        try:
+            st.advance(sims[k], reqs[k])
+        except RuntimeError as e:
+            errs.append(str(e))
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(3)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    st.close()
+    assert len(errs) == 1 and "capacity" in errs[0]
+    assert reqs[2].error and not reqs[0].error and not reqs[1].error
+    a_adapts = [i for i, t in enumerate(fb.adapts) if "a" in t]
+    assert len(a_adapts) == 3                      # before steps 0, 2, 4
+    assert all("b" not in t for t in fb.adapts)
+    assert all("bad" not in t for t in fb.ticks)   # never stepped
+    assert len(reqs[0].step_ms) == 6 and len(reqs[1].step_ms) == 4
+    # particle counts after each adaptation: 101, 101, 102, 102, 103, 103
+    assert reqs[0].particle_steps == 2 * (101 + 102 + 103)
+    assert reqs[1].particle_steps == 4 * 200
