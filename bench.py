@@ -48,7 +48,8 @@ WALK_SOURCES = ["paper_2107_01276_gb300/csrc/lists.cu",
 PASS_SOURCES = ["paper_2107_01276_gb300/csrc/pair_passes.cu",
                 "paper_2107_01276_gb300/csrc/pair_lanes.cuh",
                 "paper_2107_01276_gb300/csrc/kernels.cuh",
-                "paper_2107_01276_gb300/csrc/neighbors.cuh"]
+                "paper_2107_01276_gb300/csrc/neighbors.cuh",
+                "paper_2107_01276_gb300/build.py"]   # its per-file flags
 
 
 def sources_sha(paths):

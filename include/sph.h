@@ -194,7 +194,11 @@ typedef struct sph_ctx sph_ctx;
 void sph_default_params(sph_params *p);
 
 /* Validate *p and allocate a context with device storage for
- * p->capacity fluid particles.  stream: cudaStream_t (may be NULL).
+ * p->capacity fluid particles.  stream: cudaStream_t (may be NULL).  The
+ * context's device buffers come from CUDA's stream-ordered allocator on
+ * that stream (cudaMallocAsync / cudaFreeAsync): creating, growing and
+ * destroying a context never synchronise the whole device.  The call
+ * synchronises the stream before it returns.
  * Errors: SPH_EINVAL (dim != 2, empty box, capacity <= 0, non-positive
  * rho0/cs/hdx, negative nu), SPH_ENOMEM, SPH_ECUDA.  *out is NULL on error. */
 sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out);
@@ -559,7 +563,10 @@ sph_status sph_cell_sort_noalloc(const sph_params *p, long long n,
                                  const double *h, uint64_t *key_out,
                                  uint32_t *perm_out, void *stream);
 
-/* Free all device and host storage of the context (synchronises). */
+/* Free all device and host storage of the context: waits for the
+ * context's stream, queues the frees on it and waits again, so the memory
+ * is back with the device when the call returns (synchronises that stream
+ * only). */
 sph_status sph_destroy(sph_ctx *ctx);
 
 /* Message of the last error on this context ("" if none); valid until the

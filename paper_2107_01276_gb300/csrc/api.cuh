@@ -258,16 +258,25 @@ struct AdaptJob {
 void adapt_run(AdaptJob *jobs, int k);
 
 uint32_t read_u32(sph_ctx *c, const uint32_t *dev, sph_status *st);
+uint32_t *pinned_words_get();
+void pinned_words_put(uint32_t *p);
 sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
                    sph_ctx **out, std::string *why);
 sph_status build_set_device(sph_ctx *c, StaticSet *S, long long n,
                                    const double *const *src, int nex,
                                    const int64_t *ids);
 
+// Device buffers of a context come from the stream-ordered allocator on
+// the context's stream: allocating and freeing never synchronise the
+// device, so creating or destroying one context does not stall the work
+// of the others.
 template <typename T>
-inline bool dalloc(T **p, size_t elems) {
+inline bool dalloc(T **p, size_t elems, cudaStream_t s) {
     if (elems == 0) elems = 1;
-    return cudaMalloc((void **)p, elems * sizeof(T)) == cudaSuccess;
+    return cudaMallocAsync((void **)p, elems * sizeof(T), s) == cudaSuccess;
+}
+inline void dfree(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
 }
 
 inline bool is_mixed(const sph_ctx *c) { return c->prm.precision == SPH_MIXED; }

@@ -2,6 +2,8 @@
 // library.  Everything numerical is enqueued on the context's stream as
 // the library's own kernels; the host only validates, sizes launches and
 // moves buffers.
+#include <mutex>
+
 #include "api.cuh"
 
 namespace {
@@ -14,12 +16,12 @@ static std::atomic<int> g_live_ctx{0};   // contexts made by sph_create, not yet
 
 }  // namespace
 
-static void free_set(StaticSet *S) {
+static void free_set(StaticSet *S, cudaStream_t st) {
     void *ps[] = {S->occ, S->x, S->y, S->h, S->ex[0], S->ex[1], S->ex[2], S->id, S->pk, S->cmin,
                   S->key, S->tkey, S->perm, S->tstart, S->tend, S->tmaxh, S->bbox,
                   S->mask, S->sc.key_alt, S->sc.val_alt, S->sc.counts,
                   S->sc.scan_tmp};
-    for (void *p : ps) cudaFree(p);
+    for (void *p : ps) dfree(p, st);
     *S = StaticSet();
 }
 
@@ -221,10 +223,12 @@ sph_status rebuild(sph_ctx *c, bool mid_step, bool exact,
         (long long)n * 10 <= (long long)ltn * 11 &&
         (long long)n * 10 >= (long long)ltn * 9)
         exact = false;
-    if (c->stage_want > c->stage_w) {
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->s, &capturing);
+    if (c->stage_want > c->stage_w && capturing == cudaStreamCaptureStatusNone) {
         uint32_t *ns = nullptr;
-        if (dalloc(&ns, (size_t)c->cap * c->stage_want)) {
-            cudaFree(c->stage);   // waits for the last build's use of it
+        if (dalloc(&ns, (size_t)c->cap * c->stage_want, c->s)) {
+            dfree(c->stage, c->s);   // after the last build's use of it, in stream order
             c->stage = ns;
             c->stage_w = c->stage_want;
         } else {
@@ -317,10 +321,10 @@ sph_status rebuild(sph_ctx *c, bool mid_step, bool exact,
         if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "rebuild sync");
         if (walls && (size_t)wtotal * 2 > c->wcap) {
             const size_t want = std::min<size_t>(2 * (size_t)wtotal + 4096, 0xffffffffull);
-            cudaFree(c->wlist);
+            dfree(c->wlist, c->s);
             c->wlist = nullptr;
             c->wcap = 0;
-            if (!dalloc(&c->wlist, want)) {
+            if (!dalloc(&c->wlist, want, c->s)) {
                 cudaGetLastError();
                 return fail(c, SPH_ENOMEM, "wall list allocation failed");
             }
@@ -348,9 +352,9 @@ sph_status rebuild(sph_ctx *c, bool mid_step, bool exact,
             if (want > 0xffffffffull) want = 0xffffffffull;
             if ((size_t)total > want)
                 return fail(c, SPH_ECAPACITY, "neighbour lists exceed 2^32 entries");
-            cudaFree(c->list);
+            dfree(c->list, c->s);
             c->list = nullptr;
-            if (!dalloc(&c->list, want)) {
+            if (!dalloc(&c->list, want, c->s)) {
                 cudaGetLastError();
                 c->list_cap = 0;
                 return fail(c, SPH_ENOMEM, "neighbour list allocation failed");
@@ -453,12 +457,40 @@ void compute_dt(sph_ctx *c, double *tacc, int nsteps) {
     c->have_dt = true;
 }
 
+// Pinned host words of the contexts, 16 per context, carved from blocks
+// kept for the life of the process: freeing page-locked memory would
+// synchronise the device under every other context's work.
+static std::mutex g_pin_mu;
+static std::vector<uint32_t *> g_pin_free;
+
+uint32_t *pinned_words_get() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        constexpr int SLOTS = 256;
+        uint32_t *blk = nullptr;
+        if (cudaMallocHost((void **)&blk, SLOTS * 16 * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int k = SLOTS - 1; k >= 0; --k) g_pin_free.push_back(blk + 16 * k);
+    }
+    uint32_t *p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+}
+
+void pinned_words_put(uint32_t *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
 void free_ctx(sph_ctx *c) {
     for (auto &g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     for (int k = 0; k < NF; ++k) {
-        cudaFree(c->f[k]);
-        cudaFree(c->falt[k]);
+        dfree(c->f[k], c->s);
+        dfree(c->falt[k], c->s);
     }
     void *ps[] = {c->nbA, c->nbB, c->id, c->id_alt, c->rhoR, c->beta, c->pavg, c->drx,
                   c->dry, c->V, c->rb2, c->dpdt, c->dudt, c->dvdt, c->mf,
@@ -471,27 +503,27 @@ void free_ctx(sph_ctx *c) {
                   c->d_nlq, c->tmp_a, c->tmp_b,
                   c->closest, c->mh0, c->mds, c->mq, c->d_mass, c->d_mass_part, c->wp, c->wugx,
                   c->wugy, c->d_aux};
-    for (void *p : ps) cudaFree(p);
-    cudaFree(c->omega);
-    cudaFree(c->d_force);
-    cudaFree(c->wcnt);
-    cudaFree(c->woff);
-    cudaFree(c->wcur);
-    cudaFree(c->wlist);
-    cudaFree(c->wlongq);
-    cudaFree(c->d_wnlong);
-    cudaFree(c->d_wmax);
-    cudaFree(c->d_minmax);
-    if (c->h_pin) cudaFreeHost(c->h_pin);
+    for (void *p : ps) dfree(p, c->s);
+    dfree(c->omega, c->s);
+    dfree(c->d_force, c->s);
+    dfree(c->wcnt, c->s);
+    dfree(c->woff, c->s);
+    dfree(c->wcur, c->s);
+    dfree(c->wlist, c->s);
+    dfree(c->wlongq, c->s);
+    dfree(c->d_wnlong, c->s);
+    dfree(c->d_wmax, c->s);
+    dfree(c->d_minmax, c->s);
+    pinned_words_put(c->h_pin);
     c->h_pin = nullptr;
     if (c->bgc) {
         free_ctx(c->bgc);
         delete c->bgc;
         c->bgc = nullptr;
     }
-    free_set(&c->bg);
-    free_set(&c->wall);
-    free_set(&c->region);
+    free_set(&c->bg, c->s);
+    free_set(&c->wall, c->s);
+    free_set(&c->region, c->s);
     for (auto e : c->tm.pool) cudaEventDestroy(e);
     for (int f = 0; f < NFAM; ++f)
         for (auto &pr : c->tm.open[f]) {
@@ -511,8 +543,8 @@ static sph_status build_set_sorted(sph_ctx *c, StaticSet *S, long long n,
                                    int64_t *tid) {
     auto done = [&](sph_status st) {
         cudaStreamSynchronize(c->s);
-        cudaFree(tmp);
-        cudaFree(tid);
+        dfree(tmp, c->s);
+        dfree(tid, c->s);
         return st;
     };
     if (n > (1ll << 30)) return done(fail(c, SPH_ECAPACITY, "sph_load_particles: set too large"));
@@ -528,28 +560,28 @@ static sph_status build_set_sorted(sph_ctx *c, StaticSet *S, long long n,
     long long nmax = std::max(lev[0].n[0], lev[0].n[1]);
     if (nmax >= (1ll << MAX_MORTON_BITS)) return done(fail(c, SPH_EINVAL, "set grid too fine"));
     if (n > S->cap || nex != S->nex) {
-        free_set(S);
+        free_set(S, c->s);
         size_t N = (size_t)n;
-        bool ok = dalloc(&S->x, N) && dalloc(&S->y, N) && dalloc(&S->h, N) &&
-                  dalloc(&S->id, N) && dalloc(&S->key, N) && dalloc(&S->perm, N) &&
-                  dalloc(&S->pk, N) &&
-                  dalloc(&S->bbox, MAX_LEVELS * 4) && dalloc(&S->mask, 1) &&
-                  dalloc(&S->occ, OCC_WORDS) &&
-                  dalloc(&S->sc.key_alt, N) && dalloc(&S->sc.val_alt, N);
-        for (int k = 0; k < nex; ++k) ok = ok && dalloc(&S->ex[k], N);
-        ok = ok && dalloc(&S->cmin, N);
+        bool ok = dalloc(&S->x, N, c->s) && dalloc(&S->y, N, c->s) && dalloc(&S->h, N, c->s) &&
+                  dalloc(&S->id, N, c->s) && dalloc(&S->key, N, c->s) && dalloc(&S->perm, N, c->s) &&
+                  dalloc(&S->pk, N, c->s) &&
+                  dalloc(&S->bbox, MAX_LEVELS * 4, c->s) && dalloc(&S->mask, 1, c->s) &&
+                  dalloc(&S->occ, OCC_WORDS, c->s) &&
+                  dalloc(&S->sc.key_alt, N, c->s) && dalloc(&S->sc.val_alt, N, c->s);
+        for (int k = 0; k < nex; ++k) ok = ok && dalloc(&S->ex[k], N, c->s);
+        ok = ok && dalloc(&S->cmin, N, c->s);
         size_t tiles = (N + 2047) / 2048;
         S->sc.counts_cap = 256 * tiles;
         S->sc.scan_cap = scan_scratch_elems(S->sc.counts_cap);
-        ok = ok && dalloc(&S->sc.counts, S->sc.counts_cap) &&
-             dalloc(&S->sc.scan_tmp, S->sc.scan_cap);
+        ok = ok && dalloc(&S->sc.counts, S->sc.counts_cap, c->s) &&
+             dalloc(&S->sc.scan_tmp, S->sc.scan_cap, c->s);
         uint32_t t = 1;
         while (t < 2u * (uint32_t)N) t <<= 1;
-        ok = ok && dalloc(&S->tkey, t) && dalloc(&S->tstart, t) && dalloc(&S->tend, t) &&
-             dalloc(&S->tmaxh, t);
+        ok = ok && dalloc(&S->tkey, t, c->s) && dalloc(&S->tstart, t, c->s) && dalloc(&S->tend, t, c->s) &&
+             dalloc(&S->tmaxh, t, c->s);
         if (!ok) {
             cudaGetLastError();
-            free_set(S);
+            free_set(S, c->s);
             return done(fail(c, SPH_ENOMEM, "particle set allocation failed"));
         }
         S->cap = (int)n;
@@ -611,9 +643,9 @@ static sph_status build_set(sph_ctx *c, StaticSet *S, long long n,
     const int nf = 3 + nex;
     double *tmp = nullptr;
     int64_t *tid = nullptr;
-    if (!dalloc(&tmp, (size_t)nf * n) || !dalloc(&tid, (size_t)n)) {
+    if (!dalloc(&tmp, (size_t)nf * n, c->s) || !dalloc(&tid, (size_t)n, c->s)) {
         cudaGetLastError();
-        cudaFree(tmp);
+        dfree(tmp, c->s);
         return fail(c, SPH_ENOMEM, "particle set staging allocation failed");
     }
     std::vector<int64_t> idv;
@@ -642,9 +674,9 @@ sph_status build_set_device(sph_ctx *c, StaticSet *S, long long n,
     const int nf = 3 + nex;
     double *tmp = nullptr;
     int64_t *tid = nullptr;
-    if (!dalloc(&tmp, (size_t)nf * n) || !dalloc(&tid, (size_t)n)) {
+    if (!dalloc(&tmp, (size_t)nf * n, c->s) || !dalloc(&tid, (size_t)n, c->s)) {
         cudaGetLastError();
-        cudaFree(tmp);
+        dfree(tmp, c->s);
         return fail(c, SPH_ENOMEM, "particle set staging allocation failed");
     }
     for (int k = 0; k < nf; ++k)
@@ -656,8 +688,8 @@ sph_status build_set_device(sph_ctx *c, StaticSet *S, long long n,
     unsigned long long mm[2] = {0, 0};
     cudaMemcpyAsync(mm, c->d_minmax, sizeof(mm), cudaMemcpyDeviceToHost, c->s);
     if (cudaStreamSynchronize(c->s) != cudaSuccess) {
-        cudaFree(tmp);
-        cudaFree(tid);
+        dfree(tmp, c->s);
+        dfree(tid, c->s);
         return cuda_check(c, "build_set_device");
     }
     double hmin;
@@ -763,16 +795,16 @@ static sph_status load_walls(sph_ctx *c, long long n, const sph_particles *src) 
                               n ? src->y : nullptr, n ? src->h : nullptr, ex, 3,
                               nullptr);
     if (st != SPH_OK) return st;
-    cudaFree(c->wp);
-    cudaFree(c->wugx);
-    cudaFree(c->wugy);
+    dfree(c->wp, c->s);
+    dfree(c->wugx, c->s);
+    dfree(c->wugy, c->s);
     c->wp = c->wugx = c->wugy = nullptr;
-    cudaFree(c->wlist);
+    dfree(c->wlist, c->s);
     c->wlist = nullptr;
     c->wcap = 0;
     const size_t wcap = std::max<size_t>(4096, 256 * (size_t)n);
-    if (n > 0 && !(dalloc(&c->wp, n) && dalloc(&c->wugx, n) && dalloc(&c->wugy, n) &&
-                   dalloc(&c->wlist, wcap))) {
+    if (n > 0 && !(dalloc(&c->wp, n, c->s) && dalloc(&c->wugx, n, c->s) && dalloc(&c->wugy, n, c->s) &&
+                   dalloc(&c->wlist, wcap, c->s))) {
         cudaGetLastError();
         c->wall.n = 0;
         return fail(c, SPH_ENOMEM, "wall allocation failed");
@@ -809,50 +841,50 @@ sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
     const size_t N = (size_t)c->cap;
     bool ok = true;
     for (int k = 0; k < NF; ++k)
-        if (k != F_DS || has_ds) ok = ok && dalloc(&c->f[k], N) && dalloc(&c->falt[k], N);
-    ok = ok && dalloc(&c->omega, N) && dalloc(&c->d_wmax, 1) && dalloc(&c->d_minmax, 2);
-    ok = ok && dalloc(&c->id, N) && dalloc(&c->id_alt, N);
+        if (k != F_DS || has_ds) ok = ok && dalloc(&c->f[k], N, c->s) && dalloc(&c->falt[k], N, c->s);
+    ok = ok && dalloc(&c->omega, N, c->s) && dalloc(&c->d_wmax, 1, c->s) && dalloc(&c->d_minmax, 2, c->s);
+    ok = ok && dalloc(&c->id, N, c->s) && dalloc(&c->id_alt, N, c->s);
     double **rs[] = {(double **)&c->rhoR, (double **)&c->beta, (double **)&c->pavg,
                      (double **)&c->drx, (double **)&c->dry, (double **)&c->V,
                      (double **)&c->rb2, (double **)&c->dpdt, (double **)&c->dudt,
                      (double **)&c->dvdt};
-    for (auto pp : rs) ok = ok && dalloc(pp, N);
-    ok = ok && dalloc((double4_32a **)&c->nbA, N) && dalloc((double4_32a **)&c->nbB, N);
-    ok = ok && dalloc(&c->mf, N) && dalloc(&c->pf, N) && dalloc(&c->uf, N) &&
-         dalloc(&c->vf, N) && dalloc(&c->nnb, N);
-    ok = ok && dalloc(&c->skey, N) && dalloc(&c->perm, N) &&
-         dalloc(&c->sc.key_alt, N) && dalloc(&c->sc.val_alt, N);
+    for (auto pp : rs) ok = ok && dalloc(pp, N, c->s);
+    ok = ok && dalloc((double4_32a **)&c->nbA, N, c->s) && dalloc((double4_32a **)&c->nbB, N, c->s);
+    ok = ok && dalloc(&c->mf, N, c->s) && dalloc(&c->pf, N, c->s) && dalloc(&c->uf, N, c->s) &&
+         dalloc(&c->vf, N, c->s) && dalloc(&c->nnb, N, c->s);
+    ok = ok && dalloc(&c->skey, N, c->s) && dalloc(&c->perm, N, c->s) &&
+         dalloc(&c->sc.key_alt, N, c->s) && dalloc(&c->sc.val_alt, N, c->s);
     size_t tiles = (N + 2047) / 2048;
     c->sc.counts_cap = 256 * tiles;
     c->sc.scan_cap = scan_scratch_elems(std::max(c->sc.counts_cap, N + 1));
-    ok = ok && dalloc(&c->sc.counts, c->sc.counts_cap) &&
-         dalloc(&c->sc.scan_tmp, c->sc.scan_cap);
+    ok = ok && dalloc(&c->sc.counts, c->sc.counts_cap, c->s) &&
+         dalloc(&c->sc.scan_tmp, c->sc.scan_cap, c->s);
     uint32_t t = 1;
     while (t < 2u * (uint32_t)N) t <<= 1;
     c->tcap = t;
-    ok = ok && dalloc(&c->tkey, t) && dalloc(&c->tstart, t) && dalloc(&c->tend, t) &&
-         dalloc(&c->tmaxh, t);
-    ok = ok && dalloc(&c->bbox, MAX_LEVELS * 4) && dalloc(&c->level_mask, 1) &&
-         dalloc(&c->cnt_tmp, N + 1);
-    ok = ok && dalloc(&c->d_dt, 2) && dalloc(&c->d_t, 1) && dalloc(&c->d_hmin, 1) &&
-         dalloc(&c->d_nonfinite, 1) && dalloc(&c->d_total, 1) &&
-         dalloc(&c->d_skin_err, 1) &&
-         dalloc(&c->d_overflow, 1);
-    ok = ok && dalloc(&c->lvl, N) && dalloc(&c->pk, N) && dalloc(&c->own, N) &&
-         dalloc(&c->rev, N) && dalloc(&c->off, N + 1) &&
-         dalloc(&c->longq, N) && dalloc(&c->d_nlong, 1) &&
-         dalloc(&c->stage, N * c->stage_w) && dalloc(&c->lqueue, N) &&
-         dalloc(&c->d_nlq, 1) && dalloc(&c->d_max_own, 1);
-    ok = ok && dalloc(&c->tmp_a, N + 1) && dalloc(&c->tmp_b, N + 1) &&
-         dalloc(&c->closest, N) && dalloc(&c->mh0, N) && dalloc(&c->mds, N) &&
-         dalloc(&c->mq, N) &&
-         dalloc(&c->wcnt, N + 1) && dalloc(&c->woff, N + 1) && dalloc(&c->wcur, N) &&
-         dalloc(&c->wlongq, N) && dalloc(&c->d_wnlong, 1) &&
-         dalloc(&c->d_mass, 2) &&
-         dalloc(&c->d_mass_part, 256) && dalloc(&c->d_aux, 4) &&
-         cudaMallocHost((void **)&c->h_pin, 16 * sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && dalloc(&c->tkey, t, c->s) && dalloc(&c->tstart, t, c->s) && dalloc(&c->tend, t, c->s) &&
+         dalloc(&c->tmaxh, t, c->s);
+    ok = ok && dalloc(&c->bbox, MAX_LEVELS * 4, c->s) && dalloc(&c->level_mask, 1, c->s) &&
+         dalloc(&c->cnt_tmp, N + 1, c->s);
+    ok = ok && dalloc(&c->d_dt, 2, c->s) && dalloc(&c->d_t, 1, c->s) && dalloc(&c->d_hmin, 1, c->s) &&
+         dalloc(&c->d_nonfinite, 1, c->s) && dalloc(&c->d_total, 1, c->s) &&
+         dalloc(&c->d_skin_err, 1, c->s) &&
+         dalloc(&c->d_overflow, 1, c->s);
+    ok = ok && dalloc(&c->lvl, N, c->s) && dalloc(&c->pk, N, c->s) && dalloc(&c->own, N, c->s) &&
+         dalloc(&c->rev, N, c->s) && dalloc(&c->off, N + 1, c->s) &&
+         dalloc(&c->longq, N, c->s) && dalloc(&c->d_nlong, 1, c->s) &&
+         dalloc(&c->stage, N * c->stage_w, c->s) && dalloc(&c->lqueue, N, c->s) &&
+         dalloc(&c->d_nlq, 1, c->s) && dalloc(&c->d_max_own, 1, c->s);
+    ok = ok && dalloc(&c->tmp_a, N + 1, c->s) && dalloc(&c->tmp_b, N + 1, c->s) &&
+         dalloc(&c->closest, N, c->s) && dalloc(&c->mh0, N, c->s) && dalloc(&c->mds, N, c->s) &&
+         dalloc(&c->mq, N, c->s) &&
+         dalloc(&c->wcnt, N + 1, c->s) && dalloc(&c->woff, N + 1, c->s) && dalloc(&c->wcur, N, c->s) &&
+         dalloc(&c->wlongq, N, c->s) && dalloc(&c->d_wnlong, 1, c->s) &&
+         dalloc(&c->d_mass, 2, c->s) &&
+         dalloc(&c->d_mass_part, 256, c->s) && dalloc(&c->d_aux, 4, c->s) &&
+         (c->h_pin = pinned_words_get()) != nullptr;
     c->list_cap = std::min<size_t>(N * 48, 0xffffffffull);
-    ok = ok && dalloc(&c->list, c->list_cap);
+    ok = ok && dalloc(&c->list, c->list_cap, c->s);
     if (!ok) {
         cudaGetLastError();
         free_ctx(c);
@@ -864,7 +896,8 @@ sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
     cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->s);
     cudaMemsetAsync(c->d_overflow, 0, sizeof(int), c->s);
     cudaMemsetAsync(c->d_skin_err, 0, sizeof(int), c->s);
-    if (cudaGetLastError() != cudaSuccess) {
+    // the stream-ordered buffers become usable on every stream
+    if (cudaStreamSynchronize(c->s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         free_ctx(c);
         delete c;
         *why = "CUDA error";
@@ -1321,10 +1354,10 @@ sph_status sph_forces(sph_ctx *c, double *per_wall, double *total) {
     const int nw = c->wall.n;
     if (nw <= 0) return SPH_OK;
     if (c->force_cap < nw) {
-        cudaFree(c->d_force);
+        dfree(c->d_force, c->s);
         c->d_force = nullptr;
         c->force_cap = 0;
-        if (!dalloc(&c->d_force, (size_t)8 * nw + 4)) {
+        if (!dalloc(&c->d_force, (size_t)8 * nw + 4, c->s)) {
             cudaGetLastError();
             return fail(c, SPH_ENOMEM, "sph_forces: device allocation failed");
         }
@@ -1532,7 +1565,7 @@ static sph_status read_field(sph_ctx *c, sph_field field, void *dst, long long c
         }
         if ((st = need(total)) != SPH_OK) return st;
         int64_t *dev = nullptr;
-        if (cudaMalloc((void **)&dev, sizeof(int64_t) * std::max<uint32_t>(total, 1)) != cudaSuccess) {
+        if (!dalloc(&dev, std::max<uint32_t>(total, 1), c->s)) {
             cudaGetLastError();
             return fail(c, SPH_ENOMEM, "sph_read: neighbour list allocation failed");
         }
@@ -1540,7 +1573,7 @@ static sph_status read_field(sph_ctx *c, sph_field field, void *dst, long long c
         c->launches += 1;
         cudaMemcpyAsync(dst, dev, sizeof(int64_t) * total, cudaMemcpyDeviceToHost, c->s);
         cudaError_t e = cudaStreamSynchronize(c->s);
-        cudaFree(dev);
+        dfree(dev, c->s);
         if (e != cudaSuccess) return cuda_check(c, "sph_read");
         return SPH_OK;
     }
@@ -1609,9 +1642,13 @@ sph_status sph_kernel_time(sph_ctx *c, int family, double *ms,
 
 sph_status sph_destroy(sph_ctx *c) {
     if (!c) return SPH_EINVAL;
-    cudaStreamSynchronize(c->s);
+    const cudaStream_t s = c->s;
+    cudaStreamSynchronize(s);
     free_ctx(c);
     delete c;
+    // the frees run in stream order; the pool hands the memory back to the
+    // device at this synchronisation
+    cudaStreamSynchronize(s);
     g_live_ctx.fetch_sub(1);
     return SPH_OK;
 }

@@ -10,12 +10,13 @@ device.  As requests finish, their slots and memory go to waiting ones
 beside the aggregate throughput.
 
 With batch=True the requests step together instead, once set up on their
-workers: one BatchStepper thread advances all of them in flight per tick,
+workers: a BatchStepper thread advances all of them in flight per tick,
 first one sph_batch_adapt over those due for adaptation (their
 adaptations in lockstep, one synchronisation per phase for all of them),
 then one sph_batch_step over all (every per-particle phase of all of them
 in one persistent launch), members joining as they are admitted and
-leaving as they finish.
+leaving as they finish.  Requests with and without adaptation have a
+stepper each, so a plain step never waits for an adaptation.
 
 Every step of every simulation runs in the library's kernels (sph.py is the
 binding); this module only schedules.  The ctypes calls release the GIL, so
@@ -250,7 +251,8 @@ class Server:
     request (default run_alone); make_stream: callable returning a stream
     handle for a worker (default: a new torch CUDA stream); batch: the
     requests, once set up on their workers, adapt and step together
-    through one BatchStepper."""
+    through two BatchSteppers, one for the requests with adaptation and
+    one for those without."""
 
     def __init__(self, slots: int = 8, reserve: int = 2 << 30,
                  mem_info=None, runner=None, make_stream=None,
@@ -290,17 +292,20 @@ class Server:
         cv = threading.Condition(self._lock)
         t_start = time.perf_counter()
 
-        stepper = None
+        # two steppers: the requests with adaptation tick apart from those
+        # without, so that a plain step never waits for an adaptation
+        steppers = None
         if self.batch:
-            bstream = self.make_stream()
-            stepper = BatchStepper(self.slots, bstream[1])
+            steppers = {flag: BatchStepper(self.slots, self.make_stream()[1])
+                        for flag in (False, True)}
 
         def worker(slot, req):
             t0 = time.perf_counter()
             req.admitted = t0 - t_start
             try:
-                if stepper is not None:
-                    run_batched(req, streams[slot][1], stepper, self.keep_final)
+                if steppers is not None:
+                    run_batched(req, streams[slot][1], steppers[bool(req.adapt_every)],
+                                self.keep_final)
                 else:
                     self.runner(req, streams[slot][1])
             except Exception as e:            # reported, never fatal
@@ -350,8 +355,9 @@ class Server:
                     cv.wait(timeout=wait if wait is not None else 0.5)
         for th in threads.values():
             th.join()
-        if stepper is not None:
-            stepper.close()
+        if steppers is not None:
+            for st in steppers.values():
+                st.close()
         wall = time.perf_counter() - t_start
         return self.report(requests, wall)
 

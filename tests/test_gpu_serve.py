@@ -51,8 +51,9 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 
 
 def test_batched_steps_match_alone():
-    """With batch=True the requests without adaptation step together
-    (sph_batch_step, joining and leaving as they are admitted and finish);
+    """With batch=True the requests step together (sph_batch_step, joining
+    and leaving as they are admitted and finish), the adaptive one through
+    the adaptive requests' stepper (sph_batch_adapt, then sph_batch_step);
     with their team sizes set, each ends bit for bit where it ends alone."""
     def reqs():
         return [
