@@ -215,7 +215,11 @@ sph_status sph_create(const sph_params *p, void *stream, sph_ctx **out);
  * regions): x, y, h of marker particles that act as a solid for the
  * background construction's boundary marking only; they take no part in
  * the flow.
- * Fluid positions must lie in the box (periodic axes: [lo, hi)).
+ * Fluid positions must lie in the box (periodic axes: [lo, hi)).  A fluid
+ * set is copied into the context's spare buffers and checked there on the
+ * device (h and m positive and finite, positions finite and in the box,
+ * the least and largest h, the largest id); only a set that passes
+ * replaces the current one, so on SPH_EINVAL the context keeps its state.
  * Synchronous with respect to the host buffers (they may be reused on
  * return).  Errors: SPH_EINVAL (NULL required array, n < 0, h or m not
  * positive and finite, position outside the box), SPH_ECAPACITY

@@ -19,6 +19,7 @@
 #include "adapt.cuh"
 #include "background.cuh"
 #include "lists.cuh"
+#include "load_check.cuh"
 #include "pair_passes.cuh"
 #include "sph_internal.cuh"
 #include "team.cuh"
@@ -147,6 +148,7 @@ struct sph_ctx {
     double *d_mass = nullptr, *d_mass_part = nullptr;  // [2], [256]
     uint32_t *d_aux = nullptr;                         // [4] adapt counters
     uint32_t *h_pin = nullptr;   // 16 pinned host words: adaptation read-backs
+    LoadCheckOut *d_load = nullptr;   // checks of a loaded fluid set
     StaticSet bg;     // background particles (section 3.3); extra: ds, m
     // background construction: the background as a particle context of its
     // own (ds carried in F_DS), created on the first sph_background call

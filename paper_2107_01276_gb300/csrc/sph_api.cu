@@ -502,7 +502,7 @@ void free_ctx(sph_ctx *c) {
                   c->d_overflow, c->d_skin_err, c->longq, c->d_nlong, c->stage, c->lqueue, c->d_max_own,
                   c->d_nlq, c->tmp_a, c->tmp_b,
                   c->closest, c->mh0, c->mds, c->mq, c->d_mass, c->d_mass_part, c->wp, c->wugx,
-                  c->wugy, c->d_aux};
+                  c->wugy, c->d_aux, c->d_load};
     for (void *p : ps) dfree(p, c->s);
     dfree(c->omega, c->s);
     dfree(c->d_force, c->s);
@@ -882,6 +882,7 @@ sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
          dalloc(&c->wlongq, N, c->s) && dalloc(&c->d_wnlong, 1, c->s) &&
          dalloc(&c->d_mass, 2, c->s) &&
          dalloc(&c->d_mass_part, 256, c->s) && dalloc(&c->d_aux, 4, c->s) &&
+         dalloc(&c->d_load, 1, c->s) &&
          (c->h_pin = pinned_words_get()) != nullptr;
     c->list_cap = std::min<size_t>(N * 48, 0xffffffffull);
     ok = ok && dalloc(&c->list, c->list_cap, c->s);
@@ -1265,30 +1266,8 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
     if (n > c->cap) return fail(c, SPH_ECAPACITY, "sph_load_particles: n exceeds capacity");
     if (n > 0 && (!src->x || !src->y || !src->m || !src->h))
         return fail(c, SPH_EINVAL, "sph_load_particles: x, y, m, h are required");
-    double hmin = INFINITY;
-    for (long long i = 0; i < n; ++i) {
-        double h = src->h[i], m = src->m[i];
-        if (!(h > 0) || !isfinite(h) || !(m > 0) || !isfinite(m))
-            return fail(c, SPH_EINVAL, "sph_load_particles: h and m must be positive and finite");
-        hmin = std::min(hmin, h);
-        for (int a = 0; a < 2; ++a) {
-            double q = a == 0 ? src->x[i] : src->y[i];
-            bool in = c->dom.periodic[a] ? (q >= c->dom.lo[a] && q < c->dom.hi[a])
-                                         : (q >= c->dom.lo[a] && q <= c->dom.hi[a]);
-            if (!in || !isfinite(q))
-                return fail(c, SPH_EINVAL, "sph_load_particles: position outside the box");
-        }
-    }
-    double hmax = 0.0;
-    for (long long i = 0; i < n; ++i) hmax = std::max(hmax, src->h[i]);
-    sph_status gst = setup_fluid_grid(c, n, hmin, hmax);
-    if (gst != SPH_OK) return gst;
-    c->n = (int)n;
-    // a new state: a non-finite rate or skin overrun reported for the old
-    // one no longer applies
-    cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->s);
-    cudaMemsetAsync(c->d_skin_err, 0, sizeof(int), c->s);
-
+    // the set goes into the alternate buffers and is checked there on the
+    // device; only a set that passes replaces the state
     std::vector<double> tmp;
     auto put = [&](double *dst, const double *s, double dflt) {
         if (n == 0) return;
@@ -1300,33 +1279,53 @@ sph_status sph_load_particles(sph_ctx *c, sph_kind kind, long long n,
             cudaStreamSynchronize(c->s);
         }
     };
-    put(c->f[F_X], src ? src->x : nullptr, 0);
-    put(c->f[F_Y], src ? src->y : nullptr, 0);
-    put(c->f[F_U], src ? src->u : nullptr, 0);
-    put(c->f[F_V], src ? src->v : nullptr, 0);
-    put(c->f[F_P], src ? src->p : nullptr, 0);
-    put(c->f[F_RHO], src ? src->rho : nullptr, c->prm.rho0);
-    put(c->f[F_M], src ? src->m : nullptr, 0);
-    put(c->f[F_H], src ? src->h : nullptr, 0);
-    put(c->f[F_MMIN], src ? src->mmin : nullptr, 0);
-    put(c->f[F_MMAX], src ? src->mmax : nullptr, 0);
-    if (c->f[F_DS]) put(c->f[F_DS], src ? src->ds : nullptr, c->prm.ds_max);
-    c->next_id = n;
-    if (n > 0 && src->id) {
-        long long mx = -1;
-        for (long long i = 0; i < n; ++i) mx = std::max<long long>(mx, src->id[i]);
-        c->next_id = mx + 1;
-    }
+    put(c->falt[F_X], src ? src->x : nullptr, 0);
+    put(c->falt[F_Y], src ? src->y : nullptr, 0);
+    put(c->falt[F_U], src ? src->u : nullptr, 0);
+    put(c->falt[F_V], src ? src->v : nullptr, 0);
+    put(c->falt[F_P], src ? src->p : nullptr, 0);
+    put(c->falt[F_RHO], src ? src->rho : nullptr, c->prm.rho0);
+    put(c->falt[F_M], src ? src->m : nullptr, 0);
+    put(c->falt[F_H], src ? src->h : nullptr, 0);
+    put(c->falt[F_MMIN], src ? src->mmin : nullptr, 0);
+    put(c->falt[F_MMAX], src ? src->mmax : nullptr, 0);
+    if (c->f[F_DS]) put(c->falt[F_DS], src ? src->ds : nullptr, c->prm.ds_max);
     if (n > 0) {
         if (src->id) {
-            cudaMemcpyAsync(c->id, src->id, sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
+            cudaMemcpyAsync(c->id_alt, src->id, sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
         } else {
             std::vector<int64_t> ids((size_t)n);
             for (long long i = 0; i < n; ++i) ids[i] = i;
-            cudaMemcpyAsync(c->id, ids.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
+            cudaMemcpyAsync(c->id_alt, ids.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->s);
             cudaStreamSynchronize(c->s);
         }
     }
+    launch_load_check(c->s, n, c->falt[F_X], c->falt[F_Y], c->falt[F_H], c->falt[F_M],
+                      n > 0 && src->id ? c->id_alt : nullptr, c->dom, c->d_load);
+    c->launches += n > 0 ? 1 : 0;
+    LoadCheckOut chk;
+    cudaMemcpyAsync(c->h_pin, c->d_load, sizeof(LoadCheckOut), cudaMemcpyDeviceToHost, c->s);
+    if (cudaStreamSynchronize(c->s) != cudaSuccess) return cuda_check(c, "sph_load_particles");
+    memcpy(&chk, c->h_pin, sizeof(chk));
+    if (chk.bad & LOAD_BAD_HM)
+        return fail(c, SPH_EINVAL, "sph_load_particles: h and m must be positive and finite");
+    if (chk.bad & LOAD_BAD_POS)
+        return fail(c, SPH_EINVAL, "sph_load_particles: position outside the box");
+    double hmin = INFINITY, hmax = 0.0;
+    if (n > 0) {
+        memcpy(&hmin, &chk.hmin, sizeof(double));
+        memcpy(&hmax, &chk.hmax, sizeof(double));
+    }
+    sph_status gst = setup_fluid_grid(c, n, hmin, hmax);
+    if (gst != SPH_OK) return gst;
+    for (int k = 0; k < NSTATE; ++k) std::swap(c->f[k], c->falt[k]);   // F_DS included
+    std::swap(c->id, c->id_alt);
+    c->n = (int)n;
+    c->next_id = n > 0 && src->id ? chk.idmax + 1 : n;
+    // a new state: a non-finite rate or skin overrun reported for the old
+    // one no longer applies
+    cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->s);
+    cudaMemsetAsync(c->d_skin_err, 0, sizeof(int), c->s);
     cudaStreamSynchronize(c->s);
     c->grid_valid = c->rhs_valid = c->have_dt = false;
     return cuda_check(c, "sph_load_particles");

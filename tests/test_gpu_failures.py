@@ -104,3 +104,27 @@ def test_checkpoint_restore_bit_identical(case, precision):
     assert _same(_state(a), _state(b))
     a.close()
     b.close()
+
+
+def test_rejected_load_keeps_the_state():
+    """A fluid set refused by the device-side checks (here one particle
+    outside the box) leaves the context's state, ids and time untouched:
+    the next steps are those of a context that never saw it."""
+    d = wl.taylor_green(nx=32, jitter=0.1, seed=9)
+    a = _sim(d, sph.SPH_MIXED)
+    b = _sim(d, sph.SPH_MIXED)
+    a.step(2)
+    b.step(2)
+    before = _state(a)
+    bad = {k: v.copy() for k, v in d["particles"].items()}
+    bad["x"][11] = 5.0
+    with pytest.raises(sph.SphError) as e:
+        a.load(bad)
+    assert e.value.status == sph.SPH_EINVAL
+    assert "outside the box" in str(e.value)
+    assert _same(_state(a), before)
+    ta, tb = a.step(3), b.step(3)
+    assert ta == tb
+    assert _same(_state(a), _state(b))
+    a.close()
+    b.close()

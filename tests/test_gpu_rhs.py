@@ -228,11 +228,17 @@ def test_edge_cases():
     with pytest.raises(sph.SphError) as e:
         sim.load(big)
     assert e.value.status == sph.SPH_ECAPACITY
-    # outside the box
-    bad = dict(d["particles"], x=d["particles"]["x"] + 2.0)
-    with pytest.raises(sph.SphError) as e:
-        sim.load(bad)
-    assert e.value.status == sph.SPH_EINVAL
+    # outside the box, a non-finite position, a zero mass: refused on the
+    # device, the previous state (empty here) kept
+    for bad in (dict(d["particles"], x=d["particles"]["x"] + 2.0),
+                dict(d["particles"], y=np.where(np.arange(len(d["particles"]["y"])) == 7,
+                                                np.nan, d["particles"]["y"])),
+                dict(d["particles"], m=np.where(np.arange(len(d["particles"]["m"])) == 3,
+                                                0.0, d["particles"]["m"]))):
+        with pytest.raises(sph.SphError) as e:
+            sim.load(bad)
+        assert e.value.status == sph.SPH_EINVAL
+        assert len(sim.read("x")) == 0
     # a lone particle: density m W(0, h), beta 0, no shift, zero rates
     one = {k: v[:1].copy() for k, v in d["particles"].items()}
     sim.load(one)
