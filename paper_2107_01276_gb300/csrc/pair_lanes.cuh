@@ -15,7 +15,7 @@ namespace sph {
 
 // List entries whose neighbour records a mixed-path pass loads ahead.
 #ifndef SPH_UNROLL_A
-#define SPH_UNROLL_A 3
+#define SPH_UNROLL_A 4
 #endif
 #ifndef SPH_UNROLL_B
 #define SPH_UNROLL_B 2

@@ -38,24 +38,26 @@ constexpr int pass_blocks(int lane1) {
 
 // ---------------------------------------------------------------- pass A --
 // Pass A of particle i over its list (arithmetic in PassALane): a team of T
-// threads shares particle i.
-template <typename R, int T>
+// threads shares particle i.  WALLS = false: a set without wall particles,
+// compiled without the wall loop (whose registers made the one-lane pass B
+// spill at the eight-block bound).
+template <typename R, int T, bool WALLS = true>
 __device__ __forceinline__ void pass_a_at(const PassAArgs<R> &a, int i,
                                           const Team<T> &tm) {
     PassALane<R> L;
     L.init(a, i);
     pass_a_list<R, T>(a, i, L, tm, a.off[i], a.off[i + 1]);
-    L.walls(a, i, tm);
+    if constexpr (WALLS) L.walls(a, i, tm);
     L.finish(a, i, tm);
 }
 
-template <typename R, int T>
+template <typename R, int T, bool WALLS>
 __global__ void __launch_bounds__(128, (pass_blocks<R, T>(PASS_A_BLOCKS)))
     k_pass_a(PassAArgs<R> a) {
     const Team<T> tm;
     const int i = Team<T>::particle();
     if (i >= a.n) return;
-    pass_a_at<R, T>(a, i, tm);
+    pass_a_at<R, T, WALLS>(a, i, tm);
 }
 
 // ---------------------------------------------------------------- pass B --
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(128, (pass_blocks<R, T>(PASS_A_BLOCKS)))
 // (float, one lane per particle: at most 64 registers, eight 128-thread
 // blocks per SM, measured faster than six at 80 registers on the graded
 // 1:250 strip)
-template <typename R, int T>
+template <typename R, int T, bool WALLS = true>
 __device__ __forceinline__ void pass_b_at(const PassBArgs<R> &a, int i,
                                           const Team<T> &tm) {
     PassBLane<R> L;
@@ -76,17 +78,17 @@ __device__ __forceinline__ void pass_b_at(const PassBArgs<R> &a, int i,
         return;
     }
     pass_b_list<R, T>(a, i, L, tm, a.off[i], a.off[i + 1]);
-    L.walls(a, i, tm);
+    if constexpr (WALLS) L.walls(a, i, tm);
     L.finish(a, i, tm, true);
 }
 
-template <typename R, int T>
+template <typename R, int T, bool WALLS>
 __global__ void __launch_bounds__(128, (pass_blocks<R, T>(PASS_B_BLOCKS)))
     k_pass_b(PassBArgs<R> a) {
     const Team<T> tm;
     const int i = Team<T>::particle();
     if (i >= a.n) return;
-    pass_b_at<R, T>(a, i, tm);
+    pass_b_at<R, T, WALLS>(a, i, tm);
 }
 
 // --------------------------------------------------------- wall BC -----
@@ -549,7 +551,10 @@ void launch_pass_a(cudaStream_t s, const PassAArgs<R> &a, int team) {
     if (a.n <= 0) return;
     with_team_or(team, a.n, [&](auto t) {
         constexpr int T = decltype(t)::value;
-        k_pass_a<R, T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
+        if (a.w.n > 0)
+            k_pass_a<R, T, true><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
+        else
+            k_pass_a<R, T, false><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
     });
 }
 template <typename R>
@@ -557,7 +562,10 @@ void launch_pass_b(cudaStream_t s, const PassBArgs<R> &a, int team) {
     if (a.n <= 0) return;
     with_team_or(team, a.n, [&](auto t) {
         constexpr int T = decltype(t)::value;
-        k_pass_b<R, T><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
+        if (a.w.n > 0)
+            k_pass_b<R, T, true><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
+        else
+            k_pass_b<R, T, false><<<nblk(a.n * T, 128), 128, 0, s>>>(a);
     });
 }
 template <typename R>
