@@ -18,10 +18,12 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert not missing, missing
 
 
-def test_abi_covers_the_survey_entry_points():
+def test_abi_covers_the_core_entry_points():
     names = set(sph.declared_functions())
     for n in ("sph_create", "sph_load_particles", "sph_rhs", "sph_step",
-              "sph_read", "sph_destroy", "sph_last_error"):
+              "sph_adapt", "sph_background", "sph_forces", "sph_read",
+              "sph_batch_step", "sph_batch_adapt", "sph_destroy",
+              "sph_last_error"):
         assert n in names
 
 
