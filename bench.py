@@ -1238,7 +1238,7 @@ def graded_arm(args):
         "mixed_over_fp64": (value / world / fp64["particle_steps_per_s"]) if fp64 else None,
         "kernel_ms_per_launch": pl,
         "sweep": sweep,
-        "roofline": {"bound": "alu", "kernel": "k_pass_b<float, 1> (pass B, the pair loop)",
+        "roofline": {"bound": "alu", "kernel": "k_pass_b<float, 1, false> (pass B, the pair loop; no walls)",
                      "achieved": ach_b, "peak": apk["fp32_tflops"], "unit": "TFLOP/s",
                      "frac": ach_b / apk["fp32_tflops"],
                      "traffic": traffic_b,
@@ -1246,7 +1246,7 @@ def graded_arm(args):
                      "flop_per_pair": PASS_B_FLOP_PER_PAIR, "pairs_per_launch": pairs,
                      "ms_per_launch": pl["pass_b"],
                      "peak_kind": "FP32 FMA rate " + apk["kind"]},
-        "roofline_pass_b_fp64": ({"bound": "alu", "kernel": "k_pass_b<double, 1>",
+        "roofline_pass_b_fp64": ({"bound": "alu", "kernel": "k_pass_b<double, 1, false>",
                                   "achieved": PASS_B_FLOP_PER_PAIR * fp64["pairs"] /
                                   (fp64["pass_b_ms"] / 1e3) / 1e12,
                                   "peak": apk["fp64_tflops"], "unit": "TFLOP/s",
@@ -1544,7 +1544,8 @@ def main():
                        "at resolution changes, so max |dr| is far below the "
                        "terms' magnitude S: the FP32 rounding of each term "
                        "(about 1e-7 of it) gives a plain-norm error of that "
-                       "rounding times S / max|dr|")
+                       "rounding times S / max|dr|; dp/dt inherits it through "
+                       "its transport term rho_i (dr/dt) . (pressure force)")
         return out
 
     err_rep = error_report() if world == 1 else None
