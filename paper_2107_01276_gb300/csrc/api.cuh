@@ -237,6 +237,7 @@ sph_status check_overflow(sph_ctx *c, const char *who);
 std::vector<uintptr_t> graph_key(const sph_ctx *c);
 sph_status pec_step(sph_ctx *c, bool exact);
 bool graph_step(sph_ctx *c, sph_status *st);
+int live_contexts();
 void drop_graph(sph_ctx::StepGraph &g);
 
 sph_status compute_vorticity(sph_ctx *c);
