@@ -301,16 +301,18 @@ def cpu_sample(d, frac=0.1):
     return {"particles": sub, "params": prm}, int(sel.sum()), frac
 
 
-def oracle_steps(d, state, steps, adaptive):
+def oracle_steps(d, state, steps, adaptive, budget_s=None):
     """Time `steps` steps of the oracle (adaptation + PEC step when
-    adaptive) from `state`; returns (particle-steps, seconds, threads)."""
+    adaptive) from `state`, stopping early once `budget_s` seconds have
+    been spent (at least one step); returns (particle-steps, seconds,
+    threads, steps run)."""
     import oracle
     P = oracle.params(**d["params"])
     st = oracle.make_state(state, cap=max(4 * len(state["x"]), 1000))
     oracle.set_walls(d.get("walls"))
     bg = d.get("background_rings", d.get("background"))
     nid = int(np.max(state["id"])) + 1 if "id" in state else None
-    ps, el = 0, 0.0
+    ps, el, run = 0, 0.0, 0
     try:
         for _ in range(steps):
             t0 = time.perf_counter()
@@ -319,12 +321,15 @@ def oracle_steps(d, state, steps, adaptive):
             oracle.step(P, st, 1)
             el += time.perf_counter() - t0
             ps += st["n"]
+            run += 1
+            if budget_s is not None and el > budget_s:
+                break
     finally:
         oracle.set_walls(None)
-    return ps, el, oracle.num_threads()
+    return ps, el, oracle.num_threads(), run
 
 
-def reference_state(d, kind, w=None):
+def reference_state(d, kind, w=None, frac=0.1):
     """The state the oracle starts from: for the cylinder, the coarse set
     refined by the oracle's own adaptation (as the GPU set-up does) against
     the C_r-graded ring background, standing in for the constructed one
@@ -332,7 +337,7 @@ def reference_state(d, kind, w=None):
     brute force over the background, so the smaller ring set makes the
     oracle's step faster, not slower)."""
     if kind != "cylinder":
-        sd, n, frac = cpu_sample(d)
+        sd, n, frac = cpu_sample(d, frac)
         return sd, sd["particles"], "band 0 <= y < %.2f L of the workload " \
             "(%d particles, all resolutions, non-periodic in y)" % (frac, n)
     import oracle
@@ -357,6 +362,9 @@ def reference_state(d, kind, w=None):
                       "of %d particles)" % (n, how, len(d["background_rings"]["x"])))
 
 
+REF_BUDGET_S = 120.0   # seconds of timed oracle steps in the reference arm
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -369,15 +377,25 @@ def reference_arm(args):
         return 0
     d, desc = make_workload(args.workload)
     kind = WORKLOADS[args.workload]["kind"]
-    dd, state, sample = reference_state(d, kind, WORKLOADS[args.workload])
+    # a band of about 300k particles of the graded sets (at least 2 % of
+    # the box height, so that most particles have whole neighbourhoods):
+    # one oracle step of it takes ~15 s on 16 host threads
+    n_all = len(d["particles"]["x"])
+    frac = min(0.1, max(0.02, 3e5 / max(n_all, 1)))
+    dd, state, sample = reference_state(d, kind, WORKLOADS[args.workload], frac)
     adaptive = kind == "cylinder"
     oracle_steps(dd, state, max(args.warmup, 0) and 1, adaptive)
-    ps, el, cores = oracle_steps(dd, state, args.steps, adaptive)
+    # the timed steps stop after REF_BUDGET_S seconds (the oracle's cost
+    # per particle-step does not change from step to step)
+    ps, el, cores, run = oracle_steps(dd, state, args.steps, adaptive,
+                                      budget_s=REF_BUDGET_S)
     v = ps / el
+    sample += "; %d of the %d requested steps timed (%.0f s budget), 1 warm-up" % (
+        run, args.steps, REF_BUDGET_S)
     line = {"impl": "reference", "metric": "particle-steps/s", "value": v,
             "unit": "particle-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * el / args.steps,
+            "steps": run, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / run,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc},
@@ -1080,10 +1098,10 @@ def cpu_oracle_rate(steps=2):
     d1 = wl.graded_strip(n_target=1 << 20, ratio=250.0)
     dd, n_s, frac = cpu_sample(d1)
     cores = oracle.num_threads()
-    ps, el, _ = oracle_steps(dd, dd["particles"], steps, False)
+    ps, el, _, _ = oracle_steps(dd, dd["particles"], steps, False)
     oracle.set_num_threads(1)
     try:
-        ps1, el1, _ = oracle_steps(dd, dd["particles"], 1, False)
+        ps1, el1, _, _ = oracle_steps(dd, dd["particles"], 1, False)
     finally:
         oracle.set_num_threads(cores)
     return {"value": ps / el, "unit": "particle-steps/s", "cores": cores,
@@ -1567,7 +1585,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         dd, st0, sample = reference_state(d, kind, wdef)
         steps_cpu = wdef.get("cpu_steps", 2)
-        ps, el, cores = oracle_steps(dd, st0, steps_cpu, adaptive)
+        ps, el, cores, _ = oracle_steps(dd, st0, steps_cpu, adaptive)
         cpu = {"value": ps / el, "unit": "particle-steps/s", "cores": cores,
                "kind": "oracle",
                "sample": "%s, %d oracle steps (%s)" % (
