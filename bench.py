@@ -70,7 +70,7 @@ def walk_kernel(n):
     """Name of the neighbour-walk kernel the library launches for n
     particles (the size rule of the list build)."""
     if n >= 60000:
-        return "k_list_tile<1> (neighbour walk, cell tiles)"
+        return "k_list_tile<1, true> (neighbour walk, merged cell tiles)"
     if n >= 12000:
         return "k_list_tile<4> (neighbour walk, cell tiles)"
     return "k_list_gather<T> (neighbour walk, per-particle teams)"
@@ -1279,7 +1279,7 @@ def graded_arm(args):
                                   (fp64["pass_b_ms"] / 1e3) / 1e12 / apk["fp64_tflops"],
                                   "peak_kind": "FP64 FMA rate " + apk["kind"]}
                                  if fp64 else None),
-        "roofline_walk": {"bound": "hbm", "kernel": "k_list_tile<1> (neighbour walk)",
+        "roofline_walk": {"bound": "hbm", "kernel": "k_list_tile<1, true> (neighbour walk, merged cell tiles)",
                           "achieved": ach_w, "peak": hbm_peak, "unit": "GB/s",
                           "frac": ach_w / hbm_peak,
                           "traffic": walk_traffic(args.workload),

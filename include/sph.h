@@ -429,8 +429,10 @@ typedef struct {
                             sph_params.cell_c0; <= 0: 1 */
     int walk;            /* list build: 1 per-particle team walk, 2 cell
                             tiles with 4-lane teams, 3 cell tiles with a
-                            lane per particle; 0: by set size (< 12k: 1,
-                            < 60k: 2, else 3) */
+                            lane per particle, 4 the same with neighbouring
+                            cells of a level merged into one chunk of at
+                            most 32 particles (the same lists as 3); 0: by
+                            set size (< 12k: 1, < 60k: 2, else 4) */
     int team_a, team_b;  /* lanes per particle in pass A / pass B: 1, 4,
                             16 or 32; 0: by set size */
     int walls;           /* walls seen from the fluid: 1 the wall grid's
@@ -451,7 +453,7 @@ typedef struct {
                             by launch */
     /* filled by sph_autotune: mean device ms per launch of each candidate
      * (neighbour build + both passes for cell_scale 1, 1.25, 1.5; the walk
-     * for walk 1..3; pass A / pass B for teams 1, 4, 16, 32) */
+     * for walk 1, 2, 4; pass A / pass B for teams 1, 4, 16, 32) */
     double ms_cell[3], ms_walk[3], ms_team_a[4], ms_team_b[4];
     double ms_walls[2];  /* build + both passes with walls 1, 2 (walls
                             loaded only) */

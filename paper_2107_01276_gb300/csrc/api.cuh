@@ -124,6 +124,7 @@ struct sph_ctx {
     int *d_overflow = nullptr;
     uint32_t *longq = nullptr, *d_nlong = nullptr;
     uint32_t *stage = nullptr, *lqueue = nullptr, *d_nlq = nullptr;
+    uint32_t *lqref = nullptr;      // queued particles' chunk references
     uint32_t stage_w = 64;          // staging row width (entries)
     uint32_t stage_want = 0;        // width to switch to at the next build
     uint32_t *d_max_own = nullptr;  // largest own-entry count of a build

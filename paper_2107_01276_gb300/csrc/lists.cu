@@ -271,10 +271,16 @@ __device__ __forceinline__ float box_gap2(const Domain &d, const Level &L,
 // (its gap exceeds the pair radius by the pruning margin).
 // sc: the warp's staging buffer (TILE_CAP entries); pcs: 20 ints of the
 // warp's shared memory for the query's cell pieces.
+// span: 2 when the chunk's particles lie in up to 2 x 2 neighbouring cells
+// of level lc (merged chunks), else 1; the distance bound G of the FP32
+// error analysis grows with it.  A particle queued for the direct pass
+// records its chunk's reference and span, so that pass takes the same
+// decisions with the same arithmetic.
 template <bool DIRECT, int T>
 __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
                                            int *pcs, int lc, uint32_t cs,
-                                           uint32_t pe, uint32_t p0, int only) {
+                                           uint32_t pe, uint32_t p0, int only,
+                                           int span = 1) {
     static_assert(T == 1 || T == 4 || T == 16, "team of 1, 4 or 16 lanes");
     const int lane = threadIdx.x & 31;
     const int sub = lane & (T - 1);           // lane within the particle's team
@@ -332,7 +338,7 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
         if (!axis_pieces(a.d, L, bb, 0, xc, bx + Q, px)) continue;
         if (!axis_pieces(a.d, L, bb, 1, yc, by + Q, py)) continue;
         // per-level constants (functions of lc and l only)
-        const float reach = a.skin * L.cf + fmaxf(LC.wf[0], LC.wf[1]) +
+        const float reach = a.skin * L.cf + (float)span * fmaxf(LC.wf[0], LC.wf[1]) +
                             fmaxf(L.wf[0], L.wf[1]);
         const bool wrapx = a.d.periodic[0] && 2.0f * (reach + 4.0f * a.an.A[0]) >= Lx;
         const bool wrapy = a.d.periodic[1] && 2.0f * (reach + 4.0f * a.an.A[1]) >= Ly;
@@ -545,7 +551,11 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
         for (int o = 16; o; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
         if (act && sub == 0) {
             a.own[i] = k;
-            if (k > W) a.queue[atomicAdd(a.nqueue, 1u)] = i;
+            if (k > W) {
+                const uint32_t q = atomicAdd(a.nqueue, 1u);
+                a.queue[q] = i;
+                a.qref[q] = cs | (span > 1 ? 0x80000000u : 0u);
+            }
         }
         if (lane == 0 && km > 0) atomicMax(a.max_own, km);
     }
@@ -556,8 +566,16 @@ __device__ __forceinline__ void tile_chunk(const ListArgs &a, float4 *sc,
 // time.  T > 1 (small sets, where that leaves most of the GPU idle): warp w
 // takes the 32 / T particles [w P, w P + P), P = 32 / T, one piece per cell
 // they fall in.
-template <int T>
-__global__ void __launch_bounds__(128) k_list_tile(ListArgs a) {
+// resident 128-thread blocks per SM the merged-chunk walk is compiled for
+// (80 registers; measured 23 % faster than the unbounded 94 and 4-6 %
+// faster than seven or eight blocks, which spill); the cell-per-chunk
+// forms keep the 72 / 80 registers they were measured at
+#ifndef SPH_TILE_MERGE_BLOCKS
+#define SPH_TILE_MERGE_BLOCKS 6
+#endif
+template <int T, bool MERGE = false>
+__global__ void __launch_bounds__(128, MERGE ? SPH_TILE_MERGE_BLOCKS : (T == 1 ? 7 : 6))
+    k_list_tile(ListArgs a) {
     __shared__ float4 sbuf[4][TILE_CAP];
     __shared__ int spcs[4][20];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -569,6 +587,7 @@ __global__ void __launch_bounds__(128) k_list_tile(ListArgs a) {
         const uint32_t i = base + lane;
         const bool head = i < n && (i == 0 || a.skey[i] != a.skey[i - 1]);
         unsigned heads = __ballot_sync(0xffffffffu, head);
+        const uint64_t cmask = (1ull << (2 * a.g.mbits)) - 1ull;
         while (heads) {
             const uint32_t hd = base + (uint32_t)(__ffs(heads) - 1);
             heads &= heads - 1;
@@ -576,8 +595,30 @@ __global__ void __launch_bounds__(128) k_list_tile(ListArgs a) {
             uint32_t cs = hd, ce = hd + 1;
             table_lookup(a.g, K, cs, ce);
             const int lc = a.lev[hd];
+            int span = 1;
+            if constexpr (MERGE) {
+                // the following cells of this warp's range join the chunk
+                // while they are of the same level, within one cell of the
+                // first on both axes (no wrap) and the chunk holds at most
+                // 32 particles
+                const uint32_t fx = compact2(K & cmask), fy = compact2((K & cmask) >> 1);
+                while (ce - cs < 32 && ce < base + 32 && ce < n) {
+                    const uint64_t K2 = a.skey[ce];
+                    if ((K2 >> (2 * a.g.mbits)) != (K >> (2 * a.g.mbits))) break;
+                    const int dx = (int)compact2(K2 & cmask) - (int)fx;
+                    const int dy = (int)compact2((K2 & cmask) >> 1) - (int)fy;
+                    if (dx < -1 || dx > 1 || dy < -1 || dy > 1) break;
+                    uint32_t s2 = ce, e2 = ce + 1;
+                    table_lookup(a.g, K2, s2, e2);
+                    if (e2 - cs > 32) break;
+                    heads &= ~(1u << (ce - base));
+                    ce = e2;
+                    span = 2;
+                }
+            }
             for (uint32_t p0 = cs; p0 < ce; p0 += 32)
-                tile_chunk<false, 1>(a, sbuf[w], spcs[w], lc, cs, min(ce, p0 + 32), p0, -1);
+                tile_chunk<false, 1>(a, sbuf[w], spcs[w], lc, cs, min(ce, p0 + 32), p0, -1,
+                                     span);
         }
     } else {
         constexpr uint32_t P = 32 / T;
@@ -606,10 +647,11 @@ __global__ void __launch_bounds__(128) k_list_tile_queue(ListArgs a) {
     const uint32_t gw = blockIdx.x * 4u + (uint32_t)w, nw = gridDim.x * 4u;
     for (uint32_t q = gw; q < nq; q += nw) {
         const uint32_t i = a.queue[q];
-        const uint64_t K = a.skey[i];
-        uint32_t cs = i, ce = i + 1;
-        table_lookup(a.g, K, cs, ce);
-        tile_chunk<true, 16>(a, sbuf[w], spcs[w], a.lev[i], cs, i + 1, i, (int)i);
+        // the reference and span of the chunk that queued it
+        const uint32_t r = a.qref[q];
+        const uint32_t cs = r & 0x7fffffffu;
+        tile_chunk<true, 16>(a, sbuf[w], spcs[w], a.lev[i], cs, i + 1, i, (int)i,
+                             (r & 0x80000000u) ? 2 : 1);
     }
 }
 
@@ -821,8 +863,8 @@ void launch_anchor_pack(cudaStream_t s, int n, const double *x,
 // particle beyond (1.6x faster than the per-particle walk on the 1:250
 // graded million, 2.5x at 300k).  A.walk overrides it (tuning).
 static int walk_kind(const ListArgs &a) {
-    if (a.walk >= 1 && a.walk <= 3) return a.walk;
-    return a.n < 12000 ? 1 : a.n < 60000 ? 2 : 3;
+    if (a.walk >= 1 && a.walk <= 4) return a.walk;
+    return a.n < 12000 ? 1 : a.n < 60000 ? 2 : 4;
 }
 
 int list_walk_kind(const ListArgs &a) { return walk_kind(a); }
@@ -876,6 +918,8 @@ void launch_list_walk(cudaStream_t s, const ListArgs &a, int *launches) {
     const int kind = walk_kind(a);
     if (kind == 3) {
         k_list_tile<1><<<nblk(n, 128), 128, 0, s>>>(a);
+    } else if (kind == 4) {
+        k_list_tile<1, true><<<nblk(n, 128), 128, 0, s>>>(a);
     } else if (kind == 2) {
         k_list_tile<4><<<nblk(n, 32), 128, 0, s>>>(a);
     } else {

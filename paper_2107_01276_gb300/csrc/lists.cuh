@@ -46,12 +46,17 @@ struct ListArgs {
     uint32_t stage_w;           // row width (entries)
     uint32_t *max_own;          // largest own-entry count of the build
     uint32_t *queue, *nqueue;   // particles whose own entries overflow a row
+    uint32_t *qref;             // per queued particle: its chunk's reference
+                                // particle | 2^31 when the chunk spans two
+                                // cells (cell-tile walks)
     // skin >= 1: lists hold every pair with r_ij < skin * 3 max(h_i, h_j)
     // (a superset of N(i) for particles that move less than the skin
     // allows); 1: exactly N(i)
     float skin;
     // walk: 1 per-particle team walk, 2 cell tiles with 4-lane teams, 3
-    // cell tiles with a lane per particle, anything else: by set size
+    // cell tiles with a lane per particle, 4 the same with neighbouring
+    // cells of a level merged into one chunk while they hold at most 32
+    // particles, anything else: by set size
     int walk;
 };
 

@@ -147,6 +147,7 @@ ListArgs list_args(sph_ctx *c) {
     la.walk = c->walk_choice;
     la.max_own = c->d_max_own;
     la.queue = c->lqueue;
+    la.qref = c->lqref;
     la.nqueue = c->d_nlq;
     return la;
 }
@@ -499,7 +500,7 @@ void free_ctx(sph_ctx *c) {
                   c->tkey, c->tstart, c->tend, c->tmaxh, c->bbox, c->level_mask,
                   c->cnt_tmp, c->d_dt, c->d_t, c->d_hmin, c->d_nonfinite,
                   c->d_total, c->lvl, c->pk, c->own, c->rev, c->off, c->list,
-                  c->d_overflow, c->d_skin_err, c->longq, c->d_nlong, c->stage, c->lqueue, c->d_max_own,
+                  c->d_overflow, c->d_skin_err, c->longq, c->d_nlong, c->stage, c->lqueue, c->lqref, c->d_max_own,
                   c->d_nlq, c->tmp_a, c->tmp_b,
                   c->closest, c->mh0, c->mds, c->mq, c->d_mass, c->d_mass_part, c->wp, c->wugx,
                   c->wugy, c->d_aux, c->d_load};
@@ -873,7 +874,7 @@ sph_status new_ctx(const sph_params *p, cudaStream_t stream, bool has_ds,
     ok = ok && dalloc(&c->lvl, N, c->s) && dalloc(&c->pk, N, c->s) && dalloc(&c->own, N, c->s) &&
          dalloc(&c->rev, N, c->s) && dalloc(&c->off, N + 1, c->s) &&
          dalloc(&c->longq, N, c->s) && dalloc(&c->d_nlong, 1, c->s) &&
-         dalloc(&c->stage, N * c->stage_w, c->s) && dalloc(&c->lqueue, N, c->s) &&
+         dalloc(&c->stage, N * c->stage_w, c->s) && dalloc(&c->lqueue, N, c->s) && dalloc(&c->lqref, N, c->s) &&
          dalloc(&c->d_nlq, 1, c->s) && dalloc(&c->d_max_own, 1, c->s);
     ok = ok && dalloc(&c->tmp_a, N + 1, c->s) && dalloc(&c->tmp_b, N + 1, c->s) &&
          dalloc(&c->closest, N, c->s) && dalloc(&c->mh0, N, c->s) && dalloc(&c->mds, N, c->s) &&

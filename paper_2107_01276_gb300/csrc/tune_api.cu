@@ -10,10 +10,10 @@ sph_status sph_set_tuning(sph_ctx *c, const sph_tune *in) {
     c->err.clear();
     if (!in) return fail(c, SPH_EINVAL, "sph_set_tuning: in is NULL");
     auto team_ok = [](int t) { return t == 0 || t == 1 || t == 4 || t == 16 || t == 32; };
-    if (!(in->walk >= 0 && in->walk <= 3) || !team_ok(in->team_a) || !team_ok(in->team_b) ||
+    if (!(in->walk >= 0 && in->walk <= 4) || !team_ok(in->team_a) || !team_ok(in->team_b) ||
         !(in->walls >= 0 && in->walls <= 2) ||
         !(in->cell_scale <= 0 || (in->cell_scale >= 0.5 && in->cell_scale <= 4.0)))
-        return fail(c, SPH_EINVAL, "sph_set_tuning: walk 0-3, teams 0/1/4/16/32, walls 0-2, cell_scale <= 0 or in [0.5, 4]");
+        return fail(c, SPH_EINVAL, "sph_set_tuning: walk 0-4, teams 0/1/4/16/32, walls 0-2, cell_scale <= 0 or in [0.5, 4]");
     const double scale = in->cell_scale > 0 ? in->cell_scale : 1.0;
     c->walk_choice = in->walk;
     c->team_a = in->team_a;
@@ -100,14 +100,16 @@ sph_status sph_autotune(sph_ctx *c, sph_tune *out) {
     // 2. list build
     if (st == SPH_OK) {
         best = -1;
-        for (int w = 1; w <= 3 && st == SPH_OK; ++w) {
-            c->walk_choice = w;
+        // the team walk, the 4-lane cell tiles, the merged cell tiles
+        const int walks[3] = {1, 2, 4};
+        for (int q = 0; q < 3 && st == SPH_OK; ++q) {
+            c->walk_choice = walks[q];
             if ((st = measure(reps, fm)) != SPH_OK) break;
-            res.ms_walk[w - 1] = fm[5];
-            if (best < 0 || fm[5] < res.ms_walk[best - 1]) best = w;
+            res.ms_walk[q] = fm[5];
+            if (best < 0 || fm[5] < res.ms_walk[best]) best = q;
         }
-        cur.walk = best;
-        c->walk_choice = best;
+        cur.walk = walks[best < 0 ? 0 : best];
+        c->walk_choice = cur.walk;
     }
     // 3. pass teams (both passes measured in the same runs)
     if (st == SPH_OK) {

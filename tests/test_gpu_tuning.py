@@ -42,6 +42,7 @@ def test_every_configuration_matches_the_oracle(precision, tol):
     ro, rn = oracle.neighbors(P, pt["x"], pt["y"], pt["h"])
     configs = [dict(walk=1, team_a=32, team_b=16), dict(walk=2, team_a=4, team_b=4),
                dict(walk=3, team_a=1, team_b=1, cell_scale=1.5),
+               dict(walk=4, team_a=1, team_b=4),
                dict(walk=2, team_a=16, team_b=32, cell_scale=1.25)]
     for cfg in configs:
         s = _sim(d, precision)
@@ -64,7 +65,7 @@ def test_autotune_choices_and_results():
     before = by_id(s, list(RHS))
     t = s.autotune()
     assert t["cell_scale"] in (1.0, 1.25, 1.5)
-    assert t["walk"] in (1, 2, 3)
+    assert t["walk"] in (1, 2, 4)
     assert t["team_a"] in (1, 4, 16, 32) and t["team_b"] in (1, 4, 16, 32)
     assert all(v > 0 for v in t["ms_cell"] + t["ms_walk"] + t["ms_team_a"]
                + t["ms_team_b"])
@@ -82,7 +83,7 @@ def test_autotune_choices_and_results():
 def test_set_tuning_rejects_bad_values():
     d = wl.taylor_green(nx=20)
     s = _sim(d, sph.SPH_FP64)
-    for bad in (dict(walk=4), dict(team_a=8), dict(team_b=2), dict(cell_scale=9.0)):
+    for bad in (dict(walk=5), dict(team_a=8), dict(team_b=2), dict(cell_scale=9.0)):
         with pytest.raises(sph.SphError):
             s.set_tuning(**bad)
     s.close()
