@@ -69,7 +69,7 @@ def sources_sha(paths):
 def walk_kernel(n):
     """Name of the neighbour-walk kernel the library launches for n
     particles (the size rule of the list build)."""
-    if n >= 60000:
+    if n >= 48000:
         return "k_list_tile<1, true> (neighbour walk, merged cell tiles)"
     if n >= 12000:
         return "k_list_tile<4> (neighbour walk, cell tiles)"

@@ -432,8 +432,7 @@ typedef struct {
                             lane per particle, 4 the same with neighbouring
                             cells of a level merged into one chunk of at
                             most 32 particles (the same exact lists as 3);
-                            0: by
-                            set size (< 12k: 1, < 60k: 2, else 4) */
+                            0: by set size (< 12k: 1, < 48k: 2, else 4) */
     int team_a, team_b;  /* lanes per particle in pass A / pass B: 1, 4,
                             16 or 32; 0: by set size */
     int walls;           /* walls seen from the fluid: 1 the wall grid's

@@ -857,14 +857,15 @@ void launch_anchor_pack(cudaStream_t s, int n, const double *x,
 }
 
 // Walk choice by set size (measured on GB300 over uniform and graded
-// lattices of 5k to 1M particles): below ~12k particles the per-particle
+// lattices of 5k to 16M particles): below ~12k particles the per-particle
 // team walk keeps more warps in flight than the cell tiles; from there the
-// tiles win, with teams of 4 lanes up to ~60k particles and one lane per
-// particle beyond (1.6x faster than the per-particle walk on the 1:250
-// graded million, 2.5x at 300k).  A.walk overrides it (tuning).
+// tiles win, with teams of 4 lanes up to 48k particles (1.5x faster than
+// the merged one-lane tiles at 12k-26k on uniform vortices, even at
+// 36k-50k) and merged one-lane tiles beyond (0.78x the 4-lane tiles at
+// 70k, 0.5x at 290k).  A.walk overrides it (tuning).
 static int walk_kind(const ListArgs &a) {
     if (a.walk >= 1 && a.walk <= 4) return a.walk;
-    return a.n < 12000 ? 1 : a.n < 60000 ? 2 : 4;
+    return a.n < 12000 ? 1 : a.n < 48000 ? 2 : 4;
 }
 
 int list_walk_kind(const ListArgs &a) { return walk_kind(a); }
