@@ -252,13 +252,20 @@ class Server:
     handle for a worker (default: a new torch CUDA stream); batch: the
     requests, once set up on their workers, adapt and step together
     through two BatchSteppers, one for the requests with adaptation and
-    one for those without."""
+    one for those without; make_stepper: callable(max_instances, stream)
+    returning such a stepper (default BatchStepper), and batch_runner:
+    callable(request, stream, stepper) running one request through it
+    (default run_batched)."""
 
     def __init__(self, slots: int = 8, reserve: int = 2 << 30,
                  mem_info=None, runner=None, make_stream=None,
-                 keep_final: bool = False, batch: bool = False):
+                 keep_final: bool = False, batch: bool = False,
+                 make_stepper=None, batch_runner=None):
         self.slots = slots
         self.batch = batch
+        self.make_stepper = make_stepper or BatchStepper
+        self.batch_runner = batch_runner or \
+            (lambda r, s, st: run_batched(r, s, st, self.keep_final))
         self.reserve = reserve
         self.keep_final = keep_final
         if mem_info is None:
@@ -296,7 +303,7 @@ class Server:
         # without, so that a plain step never waits for an adaptation
         steppers = None
         if self.batch:
-            steppers = {flag: BatchStepper(self.slots, self.make_stream()[1])
+            steppers = {flag: self.make_stepper(self.slots, self.make_stream()[1])
                         for flag in (False, True)}
 
         def worker(slot, req):
@@ -304,8 +311,8 @@ class Server:
             req.admitted = t0 - t_start
             try:
                 if steppers is not None:
-                    run_batched(req, streams[slot][1], steppers[bool(req.adapt_every)],
-                                self.keep_final)
+                    self.batch_runner(req, streams[slot][1],
+                                      steppers[bool(req.adapt_every)])
                 else:
                     self.runner(req, streams[slot][1])
             except Exception as e:            # reported, never fatal

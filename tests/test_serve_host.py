@@ -222,3 +222,33 @@ def test_batch_stepper_adapts_members_due_and_drops_failed_ones():
     # particle counts after each adaptation: 101, 101, 102, 102, 103, 103
     assert reqs[0].particle_steps == 2 * (101 + 102 + 103)
     assert reqs[1].particle_steps == 4 * 200
+
+
+def test_batched_server_routes_adaptive_and_plain_requests_apart():
+    """With batch=True the requests with adaptation go through one stepper
+    and those without through the other, each request once."""
+    made = []
+
+    def make_stepper(k, stream):
+        st = serve.BatchStepper(k, stream, batch=FakeBatch())
+        made.append(st)
+        return st
+
+    def runner(req, stream, stepper):
+        stepper.advance(FakeSim("r%d" % req.rid, 50), req)
+
+    dev = FakeDevice(1 << 40)
+    srv = serve.Server(slots=4, reserve=0, mem_info=dev.mem_info,
+                       make_stream=lambda: (None, 0), batch=True,
+                       make_stepper=make_stepper, batch_runner=runner)
+    reqs = [serve.Request(k, wl.taylor_green(nx=8), 3 + k, adapt_every=k % 2,
+                          arrival=0.001 * k) for k in range(6)]
+    rep = srv.run(reqs)
+    assert rep["failed"] == 0 and len(made) == 2
+    plain, adaptive = made        # created for flags False, True
+    seen_plain = {n for t in plain.batch.ticks for n in t}
+    seen_adapt = {n for t in adaptive.batch.ticks for n in t}
+    assert seen_plain == {"r0", "r2", "r4"} and seen_adapt == {"r1", "r3", "r5"}
+    assert not plain.batch.adapts
+    assert {n for t in adaptive.batch.adapts for n in t} == seen_adapt
+    assert all(len(r.step_ms) == r.steps for r in reqs)
